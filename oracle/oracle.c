@@ -1,0 +1,518 @@
+/*
+ * oracle.c -- plain, slow, sequential CPU oracle for the load-weighted peeling
+ * of Greedy++ (arXiv 2311.04333) in its sorting form (GreedySorting++, the
+ * ordering behind PaRSorting++) and its round-peeling form (ParallelGreedy++,
+ * the ordering behind PaRGreedy++).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may call this file:
+ * only the tests, the smoke check and the CPU-baseline leg of the benchmark
+ * link it.  It shares no code, header, table or helper with the CUDA library.
+ *
+ * Everything is exact integer arithmetic.  Densities are (edges, vertices)
+ * pairs compared by cross-multiplication in 128 bits.
+ *
+ * Structure (each function names the passage it follows):
+ *   - ordering functions O (Alg. 2 line 6): sort by load (Sec. 3.2,
+ *     "GreedySorting++"), simultaneous round peeling (Sec. 3.3,
+ *     "ParallelGreedy++"), and the one-at-a-time load ordering (Sec. 2,
+ *     "load ordering"; Greedy++ proper);
+ *   - the peel of one iteration in that order, one vertex at a time, exactly
+ *     as Alg. 2 lines 7-11 state it (density check, load += induced degree at
+ *     peel time, remove the vertex).  This is deliberately NOT Alg. 3's
+ *     parallel A[min(j,k)] formulation, so the GPU's Alg. 3 path is checked
+ *     against the sequential definition;
+ *   - exact checkers used to pin the oracle: brute force over all subsets,
+ *     Goldberg-style max-flow densest subgraph, Batagelj-Zaversnik coreness,
+ *     and the textbook k-core by repeated deletion (Sec. 2, Definitions of
+ *     k-core and core number).
+ *
+ * Readings of the paper taken here (where it is silent or ambiguous):
+ *   - ties in the load sort are broken by ascending vertex id;
+ *   - H is reset to G at the start of every iteration (Alg. 2 writes H <- G
+ *     once, before the loop; peeling an empty H afterwards would be vacuous);
+ *   - within one ParallelGreedy++ round the peeled vertices are ordered by
+ *     ascending id, so deg* of a vertex is its number of neighbours later in
+ *     the (round, id) order;
+ *   - a round peels every alive v with key(v)*q <= min_key*(p+q), eps = p/q
+ *     (eps = 0 is the paper's exact bucket peel of the minimum key only);
+ *   - the best subgraph starts as S = G and is replaced only on a strictly
+ *     higher density (Alg. 2 lines 5, 8-9), so ties keep the earliest
+ *     (iteration, position); the empty suffix is never a candidate.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+typedef __int128 i128;
+
+#define OR_OK 0
+#define OR_ERR_INVALID 1
+#define OR_ERR_NOMEM 2
+
+/* rho(e1/v1) > rho(e2/v2) with v1, v2 > 0 (Sec. 2: rho(G) = |E|/|V|). */
+static int density_gt(int64_t e1, int64_t v1, int64_t e2, int64_t v2)
+{
+    return (i128)e1 * (i128)v2 > (i128)e2 * (i128)v1;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Ordering O for GreedySorting++ (Sec. 3.2): l(v_1) <= ... <= l(v_n), ties
+ * by vertex id.  A library sort (qsort) on the total order (load, id).      */
+
+static const int64_t *g_sort_loads;
+
+static int cmp_load_id(const void *a, const void *b)
+{
+    int64_t x = *(const int64_t *)a, y = *(const int64_t *)b;
+    int64_t lx = g_sort_loads[x], ly = g_sort_loads[y];
+    if (lx != ly) return lx < ly ? -1 : 1;
+    return x < y ? -1 : (x > y ? 1 : 0);
+}
+
+int oracle_sorting_order(int64_t n, const int64_t *loads, int64_t *order)
+{
+    if (n < 0) return OR_ERR_INVALID;
+    for (int64_t i = 0; i < n; ++i) order[i] = i;
+    g_sort_loads = loads;
+    qsort(order, (size_t)n, sizeof(int64_t), cmp_load_id);
+    return OR_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Ordering O for ParallelGreedy++ (Sec. 3.3): bucketed peeling by the key
+ * l(v) + deg_H(v).  Each round takes every alive vertex whose key is within a
+ * (1 + p/q) factor of the current minimum key, appends them in ascending id,
+ * and only then applies their degree decrements to the vertices that stay
+ * alive ("this effect is delayed until the end of the peeling step").
+ * round_of[v] receives the round index (may be NULL); returns the number of
+ * rounds (the peeling complexity c_p of this iteration), or -1 on error.    */
+int64_t oracle_round_order(int64_t n, const int64_t *off, const int32_t *adj,
+                           const int64_t *loads, int64_t p, int64_t q,
+                           int64_t *order, int64_t *round_of, int64_t *round_min)
+{
+    if (n < 0 || q <= 0 || p < 0) return -1;
+    int64_t *deg = malloc(sizeof(int64_t) * (size_t)(n ? n : 1));
+    int64_t *alive = malloc(sizeof(int64_t) * (size_t)(n ? n : 1));
+    unsigned char *state = calloc((size_t)(n ? n : 1), 1); /* 0 alive, 1 in F, 2 peeled */
+    if (!deg || !alive || !state) { free(deg); free(alive); free(state); return -1; }
+    for (int64_t v = 0; v < n; ++v) { deg[v] = off[v + 1] - off[v]; alive[v] = v; }
+    int64_t n_alive = n, pos = 0, r = 0;
+    while (n_alive > 0) {
+        int64_t mn = INT64_MAX;
+        for (int64_t i = 0; i < n_alive; ++i) {
+            int64_t v = alive[i];
+            int64_t k = loads[v] + deg[v];
+            if (k < mn) mn = k;
+        }
+        if (round_min) round_min[r] = mn;
+        int64_t start = pos, keep = 0;
+        for (int64_t i = 0; i < n_alive; ++i) {   /* alive[] stays in id order */
+            int64_t v = alive[i];
+            int64_t k = loads[v] + deg[v];
+            if ((i128)k * q <= (i128)mn * (i128)(p + q)) {
+                order[pos++] = v;
+                state[v] = 1;
+                if (round_of) round_of[v] = r;
+            } else {
+                alive[keep++] = v;
+            }
+        }
+        for (int64_t j = start; j < pos; ++j) {
+            int64_t v = order[j];
+            for (int64_t e = off[v]; e < off[v + 1]; ++e)
+                if (state[adj[e]] == 0) deg[adj[e]] -= 1;
+        }
+        for (int64_t j = start; j < pos; ++j) state[order[j]] = 2;
+        n_alive = keep;
+        ++r;
+    }
+    free(deg); free(alive); free(state);
+    return r;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Ordering O for sequential Greedy++ (Sec. 2 "load ordering", Sec. 3.2):
+ * repeatedly peel the vertex minimising l(v) + deg_H(v) (ties: smallest id),
+ * one vertex at a time, degrees updated immediately.  O(n^2): small inputs. */
+int oracle_load_order(int64_t n, const int64_t *off, const int32_t *adj,
+                      const int64_t *loads, int64_t *order)
+{
+    int64_t *deg = malloc(sizeof(int64_t) * (size_t)(n ? n : 1));
+    unsigned char *gone = calloc((size_t)(n ? n : 1), 1);
+    if (!deg || !gone) { free(deg); free(gone); return OR_ERR_NOMEM; }
+    for (int64_t v = 0; v < n; ++v) deg[v] = off[v + 1] - off[v];
+    for (int64_t j = 0; j < n; ++j) {
+        int64_t best = -1, bk = 0;
+        for (int64_t v = 0; v < n; ++v) {
+            if (gone[v]) continue;
+            int64_t k = loads[v] + deg[v];
+            if (best < 0 || k < bk) { best = v; bk = k; }
+        }
+        order[j] = best;
+        gone[best] = 1;
+        for (int64_t e = off[best]; e < off[best + 1]; ++e)
+            if (!gone[adj[e]]) deg[adj[e]] -= 1;
+    }
+    free(deg); free(gone);
+    return OR_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* One iteration of Alg. 2 lines 7-11 for a given order v_1..v_n, with H
+ * reset to G: for j = 1..n, if rho(H) > rho(best) then best <- H; then
+ * l(v_j) += deg*_H(v_j) (degree of v_j in H when it is peeled) and peel v_j.
+ *
+ * degstar[j] receives deg*_H(v_j) (this is A[j] of Alg. 3).
+ * it_best[0..2] receives the densest suffix of this iteration alone
+ *   (edges, vertices, position j of its first vertex), first one on ties.
+ * *best_e / *best_v hold the running best; *improved_at receives the
+ *   position j at which the running best was last replaced in this
+ *   iteration, or -1.  width receives max_j deg*_H(v_j).                   */
+int oracle_peel_iteration(int64_t n, const int64_t *off, const int32_t *adj,
+                          const int64_t *order, int64_t *loads,
+                          int64_t *degstar, int64_t *it_best,
+                          int64_t *best_e, int64_t *best_v,
+                          int64_t *improved_at, int64_t *width)
+{
+    int64_t *deg = malloc(sizeof(int64_t) * (size_t)(n ? n : 1));
+    unsigned char *inH = malloc((size_t)(n ? n : 1));
+    if (!deg || !inH) { free(deg); free(inH); return OR_ERR_NOMEM; }
+    int64_t eH = 0;
+    for (int64_t v = 0; v < n; ++v) {
+        deg[v] = off[v + 1] - off[v];
+        eH += deg[v];
+        inH[v] = 1;
+    }
+    eH /= 2;
+    int64_t vH = n;
+    int64_t ie = -1, iv = 1, ij = -1, w = 0;
+    *improved_at = -1;
+    for (int64_t j = 0; j < n; ++j) {
+        int64_t v = order[j];
+        /* this iteration's own densest suffix: first maximum */
+        if (ij < 0 || density_gt(eH, vH, ie, iv)) { ie = eH; iv = vH; ij = j; }
+        /* Alg. 2 line 8: the running best, strict comparison */
+        if (density_gt(eH, vH, *best_e, *best_v)) {
+            *best_e = eH; *best_v = vH; *improved_at = j;
+        }
+        int64_t ds = deg[v];                 /* deg*_H(v_j) */
+        degstar[j] = ds;
+        if (ds > w) w = ds;
+        loads[v] += ds;                      /* Alg. 2 line 10 */
+        inH[v] = 0;                          /* Alg. 2 line 11 */
+        for (int64_t e = off[v]; e < off[v + 1]; ++e)
+            if (inH[adj[e]]) deg[adj[e]] -= 1;
+        eH -= ds;
+        vH -= 1;
+    }
+    if (it_best) { it_best[0] = ie < 0 ? 0 : ie; it_best[1] = ie < 0 ? 0 : iv; it_best[2] = ij; }
+    if (width) *width = w;
+    free(deg); free(inH);
+    return OR_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* T iterations of Alg. 2 with the chosen ordering function.
+ *   variant 0: GreedySorting++ order (PaRSorting++ refine step)
+ *   variant 1: ParallelGreedy++ round order with eps = p/q (PaRGreedy++)
+ *   variant 2: sequential Greedy++ load order
+ * init_loads may be NULL (Alg. 2 lines 1-2: l = 0).  On return loads[n]
+ * holds the final loads, best_e/best_v/best_iter the best density (iteration
+ * 0 means S = G was never beaten), set[] the best subgraph's vertex ids in
+ * ascending order (set_size of them), and trace[3*t..3*t+2] (if not NULL)
+ * the densest suffix of iteration t+1 (edges, vertices) and its width.
+ * best_pos receives the position of the best suffix in its iteration.      */
+int oracle_run(int64_t n, const int64_t *off, const int32_t *adj,
+               int variant, int64_t T, int64_t p, int64_t q,
+               const int64_t *init_loads, int64_t *loads,
+               int64_t *best, int64_t *set, int64_t *trace)
+{
+    if (n < 1 || T < 0 || q <= 0 || p < 0 || variant < 0 || variant > 2)
+        return OR_ERR_INVALID;
+    int64_t *order = malloc(sizeof(int64_t) * (size_t)n);
+    int64_t *border = malloc(sizeof(int64_t) * (size_t)n);
+    int64_t *degstar = malloc(sizeof(int64_t) * (size_t)n);
+    int64_t *start = malloc(sizeof(int64_t) * (size_t)n);
+    if (!order || !border || !degstar || !start) {
+        free(order); free(border); free(degstar); free(start);
+        return OR_ERR_NOMEM;
+    }
+    for (int64_t v = 0; v < n; ++v) loads[v] = init_loads ? init_loads[v] : 0;
+    int64_t m = off[n] / 2;
+    int64_t be = m, bv = n, biter = 0, bpos = 0;        /* S <- G (Alg. 2 line 5) */
+    for (int64_t t = 1; t <= T; ++t) {
+        memcpy(start, loads, sizeof(int64_t) * (size_t)n);
+        if (variant == 0) oracle_sorting_order(n, start, order);
+        else if (variant == 1) {
+            if (oracle_round_order(n, off, adj, start, p, q, order, NULL, NULL) < 0) {
+                free(order); free(border); free(degstar); free(start);
+                return OR_ERR_NOMEM;
+            }
+        } else oracle_load_order(n, off, adj, start, order);
+        int64_t it_best[3], at = -1, w = 0;
+        oracle_peel_iteration(n, off, adj, order, loads, degstar, it_best,
+                              &be, &bv, &at, &w);
+        if (at >= 0) {
+            biter = t; bpos = at;
+            memcpy(border, order, sizeof(int64_t) * (size_t)n);
+        }
+        if (trace) {
+            trace[3 * (t - 1) + 0] = it_best[0];
+            trace[3 * (t - 1) + 1] = it_best[1];
+            trace[3 * (t - 1) + 2] = w;
+        }
+    }
+    /* best subgraph as ascending ids */
+    int64_t k = 0;
+    if (biter == 0) {
+        for (int64_t v = 0; v < n; ++v) set[k++] = v;
+    } else {
+        unsigned char *in = calloc((size_t)n, 1);
+        if (!in) { free(order); free(border); free(degstar); free(start); return OR_ERR_NOMEM; }
+        for (int64_t j = bpos; j < n; ++j) in[border[j]] = 1;
+        for (int64_t v = 0; v < n; ++v) if (in[v]) set[k++] = v;
+        free(in);
+    }
+    best[0] = be; best[1] = bv; best[2] = biter; best[3] = k; best[4] = bpos;
+    free(order); free(border); free(degstar); free(start);
+    return OR_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Exact checkers used to pin the oracle.                                    */
+
+/* Brute force over all 2^n - 1 non-empty vertex subsets (n <= 24): the
+ * densest subgraph by its definition (Sec. 2).  First subset in increasing
+ * bitmask order among the densest; returns (edges, vertices, mask).        */
+int oracle_brute_force(int64_t n, const int64_t *off, const int32_t *adj,
+                       int64_t *out)
+{
+    if (n < 1 || n > 24) return OR_ERR_INVALID;
+    uint32_t nb[24];
+    for (int64_t v = 0; v < n; ++v) {
+        nb[v] = 0;
+        for (int64_t e = off[v]; e < off[v + 1]; ++e) nb[v] |= 1u << adj[e];
+    }
+    int64_t be = 0, bv = 1, bm = 0;
+    uint32_t full = (n == 32) ? 0xffffffffu : ((1u << n) - 1u);
+    for (uint32_t S = 1; S <= full && S != 0; ++S) {
+        int64_t twice = 0, vs = 0;
+        for (int64_t v = 0; v < n; ++v)
+            if (S >> v & 1u) { ++vs; twice += __builtin_popcount(nb[v] & S); }
+        if (bm == 0 || density_gt(twice / 2, vs, be, bv)) { be = twice / 2; bv = vs; bm = S; }
+        if (S == full) break;
+    }
+    out[0] = be; out[1] = bv; out[2] = bm;
+    return OR_OK;
+}
+
+/* Dinic max-flow on a small network, int64 capacities. */
+typedef struct { int64_t to, cap, next; } arc_t;
+typedef struct {
+    int64_t nv, na, cap_arcs;
+    arc_t *a;
+    int64_t *head, *level, *it, *queue;
+} flow_t;
+
+static int flow_init(flow_t *f, int64_t nv, int64_t max_arcs)
+{
+    f->nv = nv; f->na = 0; f->cap_arcs = max_arcs;
+    f->a = malloc(sizeof(arc_t) * (size_t)max_arcs);
+    f->head = malloc(sizeof(int64_t) * (size_t)nv);
+    f->level = malloc(sizeof(int64_t) * (size_t)nv);
+    f->it = malloc(sizeof(int64_t) * (size_t)nv);
+    f->queue = malloc(sizeof(int64_t) * (size_t)nv);
+    if (!f->a || !f->head || !f->level || !f->it || !f->queue) return -1;
+    for (int64_t i = 0; i < nv; ++i) f->head[i] = -1;
+    return 0;
+}
+static void flow_free(flow_t *f)
+{
+    free(f->a); free(f->head); free(f->level); free(f->it); free(f->queue);
+}
+static void flow_add(flow_t *f, int64_t u, int64_t v, int64_t c)
+{
+    f->a[f->na] = (arc_t){v, c, f->head[u]}; f->head[u] = f->na++;
+    f->a[f->na] = (arc_t){u, 0, f->head[v]}; f->head[v] = f->na++;
+}
+static int flow_bfs(flow_t *f, int64_t s, int64_t t)
+{
+    for (int64_t i = 0; i < f->nv; ++i) f->level[i] = -1;
+    int64_t qh = 0, qt = 0;
+    f->queue[qt++] = s; f->level[s] = 0;
+    while (qh < qt) {
+        int64_t u = f->queue[qh++];
+        for (int64_t e = f->head[u]; e >= 0; e = f->a[e].next)
+            if (f->a[e].cap > 0 && f->level[f->a[e].to] < 0) {
+                f->level[f->a[e].to] = f->level[u] + 1;
+                f->queue[qt++] = f->a[e].to;
+            }
+    }
+    return f->level[t] >= 0;
+}
+/* iterative blocking-flow DFS */
+static int64_t flow_dfs(flow_t *f, int64_t s, int64_t t)
+{
+    int64_t total = 0;
+    int64_t *stack = malloc(sizeof(int64_t) * (size_t)f->nv);   /* arcs on path */
+    for (;;) {
+        int64_t depth = 0, u = s;
+        for (;;) {
+            if (u == t) {
+                int64_t push = INT64_MAX;
+                for (int64_t i = 0; i < depth; ++i)
+                    if (f->a[stack[i]].cap < push) push = f->a[stack[i]].cap;
+                for (int64_t i = 0; i < depth; ++i) {
+                    f->a[stack[i]].cap -= push;
+                    f->a[stack[i] ^ 1].cap += push;
+                }
+                total += push;
+                depth = 0; u = s;
+                continue;
+            }
+            int64_t e;
+            for (e = f->it[u]; e >= 0; e = f->a[e].next)
+                if (f->a[e].cap > 0 && f->level[f->a[e].to] == f->level[u] + 1) break;
+            f->it[u] = e;
+            if (e >= 0) {
+                stack[depth++] = e;
+                u = f->a[e].to;
+            } else {
+                if (depth == 0) { free(stack); return total; }
+                f->level[u] = -1;                 /* dead end */
+                int64_t back = stack[--depth];
+                u = f->a[back ^ 1].to;
+                f->it[u] = f->a[f->it[u]].next;
+            }
+        }
+    }
+}
+static int64_t flow_max(flow_t *f, int64_t s, int64_t t)
+{
+    int64_t total = 0;
+    while (flow_bfs(f, s, t)) {
+        for (int64_t i = 0; i < f->nv; ++i) f->it[i] = f->head[i];
+        total += flow_dfs(f, s, t);
+    }
+    return total;
+}
+
+/* Exact densest subgraph by parametric min cut (the flow approach the paper
+ * cites for exact solutions, Sec. 1 and Sec. 3).  For a guess g = a/b the
+ * maximum of b|E(S)| - a|V(S)| over vertex sets S is m*b - mincut of the
+ * network  s -> edge node (cap b),  edge node -> both endpoints (cap inf),
+ * vertex -> t (cap a)  (the selection / closure problem).  Starting from
+ * g = rho(G), a positive maximum yields a set S' of higher density; repeat
+ * with g = rho(S') (Dinkelbach) until the maximum is 0, at which point
+ * g = rho*.  out = (edges, vertices) of rho*; set_out (optional, n bytes)
+ * marks a densest subgraph.                                                  */
+int oracle_maxflow_densest(int64_t n, const int64_t *off, const int32_t *adj,
+                           int64_t *out, unsigned char *set_out)
+{
+    if (n < 1) return OR_ERR_INVALID;
+    int64_t m = off[n] / 2;
+    if (m == 0) {
+        out[0] = 0; out[1] = n;
+        if (set_out) for (int64_t v = 0; v < n; ++v) set_out[v] = 1;
+        return OR_OK;
+    }
+    int64_t *eu = malloc(sizeof(int64_t) * (size_t)m), *ev = malloc(sizeof(int64_t) * (size_t)m);
+    unsigned char *side = malloc((size_t)n);
+    if (!eu || !ev || !side) { free(eu); free(ev); free(side); return OR_ERR_NOMEM; }
+    int64_t k = 0;
+    for (int64_t u = 0; u < n; ++u)
+        for (int64_t e = off[u]; e < off[u + 1]; ++e)
+            if (adj[e] > u) { eu[k] = u; ev[k] = adj[e]; ++k; }
+    int64_t ga = m, gb = n;                     /* g = rho(G) */
+    for (int v = 0; v < n; ++v) side[v] = 1;
+    const int64_t INF = (int64_t)1 << 60;
+    for (int rounds = 0; rounds < 10000; ++rounds) {
+        flow_t f;
+        int64_t s = n + m, t = n + m + 1;
+        if (flow_init(&f, n + m + 2, 2 * (m + 2 * m + n))) { flow_free(&f); free(eu); free(ev); free(side); return OR_ERR_NOMEM; }
+        for (int64_t i = 0; i < m; ++i) {
+            flow_add(&f, s, n + i, gb);
+            flow_add(&f, n + i, eu[i], INF);
+            flow_add(&f, n + i, ev[i], INF);
+        }
+        for (int64_t v = 0; v < n; ++v) flow_add(&f, v, t, ga);
+        int64_t cut = flow_max(&f, s, t);
+        int64_t val = m * gb - cut;             /* max_S b|E(S)| - a|V(S)| */
+        if (val <= 0) { flow_free(&f); break; }
+        /* source side of the min cut: reachable from s in the residual graph */
+        flow_bfs(&f, s, t);
+        int64_t vs = 0, es = 0;
+        for (int64_t v = 0; v < n; ++v) { side[v] = f.level[v] >= 0; vs += side[v]; }
+        for (int64_t i = 0; i < m; ++i) es += side[eu[i]] && side[ev[i]];
+        flow_free(&f);
+        ga = es; gb = vs;
+    }
+    out[0] = ga; out[1] = gb;
+    if (set_out) for (int64_t v = 0; v < n; ++v) set_out[v] = side[v];
+    free(eu); free(ev); free(side);
+    return OR_OK;
+}
+
+/* Core numbers by the Batagelj-Zaversnik bin-sort algorithm (O(m)):
+ * process vertices in non-decreasing current degree; each processed vertex
+ * fixes its core number and lowers the degree of unprocessed neighbours
+ * whose degree is larger (Sec. 2, Definition of core number).              */
+int oracle_coreness(int64_t n, const int64_t *off, const int32_t *adj, int64_t *core)
+{
+    int64_t md = 0;
+    int64_t *deg = malloc(sizeof(int64_t) * (size_t)n);
+    int64_t *vert = malloc(sizeof(int64_t) * (size_t)n);
+    int64_t *pos = malloc(sizeof(int64_t) * (size_t)n);
+    if (!deg || !vert || !pos) { free(deg); free(vert); free(pos); return OR_ERR_NOMEM; }
+    for (int64_t v = 0; v < n; ++v) { deg[v] = off[v + 1] - off[v]; if (deg[v] > md) md = deg[v]; }
+    int64_t *bin = calloc((size_t)(md + 2), sizeof(int64_t));
+    if (!bin) { free(deg); free(vert); free(pos); return OR_ERR_NOMEM; }
+    for (int64_t v = 0; v < n; ++v) bin[deg[v]]++;
+    int64_t s = 0;
+    for (int64_t d = 0; d <= md; ++d) { int64_t c = bin[d]; bin[d] = s; s += c; }
+    for (int64_t v = 0; v < n; ++v) { pos[v] = bin[deg[v]]; vert[pos[v]] = v; bin[deg[v]]++; }
+    for (int64_t d = md; d >= 1; --d) bin[d] = bin[d - 1];
+    bin[0] = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t v = vert[i];
+        for (int64_t e = off[v]; e < off[v + 1]; ++e) {
+            int64_t u = adj[e];
+            if (deg[u] > deg[v]) {
+                int64_t du = deg[u], pu = pos[u], pw = bin[du], w = vert[pw];
+                if (u != w) { pos[u] = pw; vert[pu] = w; pos[w] = pu; vert[pw] = u; }
+                bin[du]++;
+                deg[u]--;
+            }
+        }
+    }
+    for (int64_t v = 0; v < n; ++v) core[v] = deg[v];
+    free(deg); free(vert); free(pos); free(bin);
+    return OR_OK;
+}
+
+/* k-core by its definition (Sec. 2): for each k, repeatedly delete vertices
+ * of degree < k; core(v) is the largest k for which v survives.  O(n m k). */
+int oracle_coreness_by_deletion(int64_t n, const int64_t *off, const int32_t *adj, int64_t *core)
+{
+    unsigned char *in = malloc((size_t)n);
+    if (!in) return OR_ERR_NOMEM;
+    for (int64_t v = 0; v < n; ++v) core[v] = 0;
+    for (int64_t k = 1;; ++k) {
+        for (int64_t v = 0; v < n; ++v) in[v] = 1;
+        int changed = 1;
+        while (changed) {
+            changed = 0;
+            for (int64_t v = 0; v < n; ++v) {
+                if (!in[v]) continue;
+                int64_t d = 0;
+                for (int64_t e = off[v]; e < off[v + 1]; ++e) d += in[adj[e]];
+                if (d < k) { in[v] = 0; changed = 1; }
+            }
+        }
+        int any = 0;
+        for (int64_t v = 0; v < n; ++v) if (in[v]) { core[v] = k; any = 1; }
+        if (!any) break;
+    }
+    free(in);
+    return OR_OK;
+}

@@ -1,0 +1,55 @@
+"""Plant plausible mistakes in a copy of the oracle (CPU only) and check that
+the pins in test_oracle_pins.py catch every one of them."""
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "oracle.c")
+
+MUTANTS = {
+    "density_tie_nonstrict": ("return (i128)e1 * (i128)v2 > (i128)e2 * (i128)v1;",
+                              "return (i128)e1 * (i128)v2 >= (i128)e2 * (i128)v1;"),
+    "degstar_uses_deg_G": ("int64_t ds = deg[v];                 /* deg*_H(v_j) */",
+                           "int64_t ds = off[v + 1] - off[v];"),
+    "peel_no_decrement": ("if (inH[adj[e]]) deg[adj[e]] -= 1;", ";"),
+    "sort_descending": ("if (lx != ly) return lx < ly ? -1 : 1;", "if (lx != ly) return lx > ly ? -1 : 1;"),
+    "sort_ties_by_reverse_id": ("return x < y ? -1 : (x > y ? 1 : 0);", "return x > y ? -1 : (x < y ? 1 : 0);"),
+    "round_rule_strict": ("if ((i128)k * q <= (i128)mn * (i128)(p + q)) {",
+                          "if ((i128)k * q < (i128)mn * (i128)(p + q) || k == mn) {"),
+    "round_rule_eps_dropped": ("if ((i128)k * q <= (i128)mn * (i128)(p + q)) {",
+                               "if ((i128)k * q <= (i128)mn * (i128)q) {"),
+    "round_key_without_degree": ("int64_t k = loads[v] + deg[v];\n            if ((i128)k",
+                                 "int64_t k = loads[v];\n            if ((i128)k"),
+    "round_decrement_immediate_skip": ("if (state[adj[e]] == 0) deg[adj[e]] -= 1;", ";"),
+    "best_set_off_by_one": ("for (int64_t j = bpos; j < n; ++j) in[border[j]] = 1;",
+                            "for (int64_t j = bpos + 1; j < n; ++j) in[border[j]] = 1;"),
+    "load_update_dropped": ("loads[v] += ds;                      /* Alg. 2 line 10 */", ";"),
+    "iteration_best_last_max": ("if (ij < 0 || density_gt(eH, vH, ie, iv))",
+                                "if (ij < 0 || !density_gt(ie, iv, eH, vH))"),
+    "bz_nonstrict": ("if (deg[u] > deg[v]) {", "if (deg[u] >= deg[v]) {"),
+    "maxflow_capacity": ("for (int64_t v = 0; v < n; ++v) flow_add(&f, v, t, ga);",
+                         "for (int64_t v = 0; v < n; ++v) flow_add(&f, v, t, ga + 1);"),
+    "brute_force_double_count": ("if (bm == 0 || density_gt(twice / 2, vs, be, bv)) { be = twice / 2;",
+                                 "if (bm == 0 || density_gt(twice, vs, be, bv)) { be = twice;"),
+    "deletion_core_off_by_one": ("if (d < k) { in[v] = 0; changed = 1; }", "if (d <= k) { in[v] = 0; changed = 1; }"),
+}
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_pins_catch_mutant(name, tmp_path):
+    old, new = MUTANTS[name]
+    src = open(SRC).read()
+    assert src.count(old) == 1, f"mutation site for {name} not unique"
+    mut = tmp_path / "oracle_mut.c"
+    mut.write_text(src.replace(old, new))
+    so = tmp_path / "liboracle_mut.so"
+    subprocess.check_call(["gcc", "-O1", "-std=c11", "-shared", "-fPIC", "-o", str(so), str(mut)])
+    env = dict(os.environ, DSG_ORACLE_SO=str(so))
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                        os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                       env=env, cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert r.returncode != 0, f"mutant {name} survived the pins:\n{r.stdout[-2000:]}"
