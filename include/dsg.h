@@ -1,0 +1,163 @@
+/*
+ * dsg.h -- C ABI of libdsg, the GB300 (sm_103a) implementation of the
+ * per-iteration load-weighted peeling of Greedy++ in its two parallel forms
+ * (arXiv 2311.04333, "Practical Parallel Algorithms for Near-Optimal
+ * Densest Subgraphs on Massive Graphs"):
+ *
+ *   DSG_SORTING  PaRSorting++ refine step (Sec. 3.2 "GreedySorting++" and
+ *                Sec. 3.3 "ParallelGreedySorting++"): each iteration orders
+ *                the vertices by their load at the start of the iteration
+ *                (ties by vertex id), gives every vertex the number of its
+ *                neighbours later in the order (Alg. 3 lines 2-3), adds it
+ *                to its load (Alg. 3 lines 8-9) and takes the densest suffix
+ *                of the order (Alg. 3 lines 4-7).
+ *   DSG_PEELING  PaRGreedy++ refine step (Sec. 3.3 "ParallelGreedy++"): the
+ *                order comes from bucketed peeling by l(v) + deg_H(v); each
+ *                round peels every alive vertex whose key is within a factor
+ *                (1 + p/q) of the minimum key, in ascending id, and applies
+ *                the degree decrements at the end of the round.
+ *
+ * No pruning (Alg. 1) is applied: the refine step runs on the given graph.
+ * The problem (Sec. 2): given an undirected unweighted graph G = (V, E),
+ * find S maximising |E(S)| / |V(S)|.  All arithmetic is exact integer;
+ * densities are returned as (edges, vertices) pairs.
+ *
+ * Conventions:
+ *   - every call returns a dsg_status; no C++ exception crosses the ABI;
+ *     dsg_last_error(ctx) describes the last failure on that context;
+ *   - uploads COPY the caller's arrays into library-owned device memory;
+ *     the caller may free or reuse its buffers as soon as the call returns;
+ *   - result buffers are owned by the caller;
+ *   - all device work is ordered on the context's CUDA stream; dsg_run and
+ *     dsg_run_batch synchronise that stream before they return;
+ *   - a context is not thread-safe: use one context per host thread.
+ */
+#ifndef DSG_H
+#define DSG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dsg_ctx dsg_ctx;
+typedef struct dsg_graph dsg_graph;
+typedef struct dsg_batch dsg_batch;
+
+typedef enum {
+    DSG_OK = 0,
+    DSG_ERR_INVALID = 1,   /* malformed argument or graph */
+    DSG_ERR_NOMEM = 2,     /* device or host allocation failed */
+    DSG_ERR_CUDA = 3,      /* a CUDA call failed (context may be unusable) */
+    DSG_ERR_OVERFLOW = 4,  /* loads or sizes would exceed the device types */
+    DSG_ERR_TIMEOUT = 5,   /* a bounded device-side wait gave up */
+    DSG_ERR_BUSY = 6       /* resource in use (e.g. serving slots full) */
+} dsg_status;
+
+typedef enum {
+    DSG_SORTING = 0,       /* PaRSorting++ refine step */
+    DSG_PEELING = 1        /* PaRGreedy++ refine step, eps = p/q */
+} dsg_variant;
+
+/* dsg_upload_csr / dsg_upload_batch flags */
+#define DSG_VALIDATE   0x1u  /* check symmetry, no self-loops, no duplicates */
+#define DSG_SRC_DEVICE 0x2u  /* offsets/adj are device pointers (else host) */
+
+/* dsg_result.flags */
+#define DSG_DST_DEVICE  0x1u /* loads/best_set/trace are device pointers */
+#define DSG_INIT_DEVICE 0x2u /* init_loads (dsg_run) is a device pointer */
+
+/* Output of one run.  The caller sets `flags` and the three buffer
+ * pointers (each may be NULL to skip that output); the library fills the
+ * scalar fields.
+ *   best_edges/best_vertices: |E(S)| and |V(S)| of the best subgraph found
+ *     (S = G initially, replaced only by a strictly denser suffix; ties keep
+ *     the earliest iteration and, within it, the largest suffix);
+ *   best_iter: iteration (1..T) that produced S, 0 if S = G was never beaten;
+ *   best_set_size: |V(S)|;
+ *   loads[n]: the loads after the last iteration (int64);
+ *   best_set[n]: the ids of S in ascending order (first best_set_size used);
+ *   trace[3*T]: per iteration t (0-based row t), the densest suffix of that
+ *     iteration alone (edges, vertices; largest suffix on ties) and its width
+ *     max_v deg*(v) (the per-iteration load increase bound, Sec. 4.4).   */
+typedef struct {
+    uint32_t flags;
+    int32_t best_iter;
+    int64_t best_edges;
+    int64_t best_vertices;
+    int64_t best_set_size;
+    int64_t *loads;
+    int32_t *best_set;
+    int64_t *trace;
+} dsg_result;
+
+/* Create a context on CUDA device `device`, issuing all work on
+ * `cuda_stream` (a cudaStream_t; NULL = the legacy default stream).  The
+ * stream is borrowed, not owned.  Returns DSG_ERR_CUDA if the device cannot
+ * be used and DSG_ERR_INVALID if the library was not built for it. */
+int dsg_create(int device, void *cuda_stream, dsg_ctx **out);
+
+/* Release a context.  Graphs and batches created on it must be freed first. */
+void dsg_destroy(dsg_ctx *ctx);
+
+/* Text of the last error on `ctx` ("" if none).  Valid until the next call
+ * on the same context. */
+const char *dsg_last_error(const dsg_ctx *ctx);
+
+/* Upload an undirected simple graph in CSR form (Sec. 2: G = (V, E)).
+ *   n: number of vertices, 1 <= n < 2^31;
+ *   offsets[n+1]: int64, offsets[0] = 0, non-decreasing, offsets[n] = 2m
+ *     (each undirected edge appears in both endpoint lists), 2m < 2^40;
+ *   adj[2m]: int32 neighbour ids in [0, n).
+ * With DSG_VALIDATE the library also checks that every list has no self-loop
+ * and no repeated neighbour and that the graph is symmetric; otherwise the
+ * caller guarantees it.  Lists need not be sorted.  The graph is copied to
+ * device memory together with the tile schedule of the edge scan.
+ * Errors: DSG_ERR_INVALID for a malformed graph, DSG_ERR_NOMEM. */
+int dsg_upload_csr(dsg_ctx *ctx, int64_t n, const int64_t *offsets, const int32_t *adj,
+                   uint32_t flags, dsg_graph **out);
+
+/* Basic facts about an uploaded graph (any pointer may be NULL). */
+int dsg_graph_info(const dsg_graph *g, int64_t *n, int64_t *m, int64_t *max_degree);
+
+/* Run T >= 1 iterations of the refine step `variant` on `g` (Alg. 2 with
+ * the ordering of `variant`, the density/load update of Alg. 3).
+ *   eps_num/eps_den: eps = p/q for DSG_PEELING (p >= 0, q >= 1, p+q < 2^31);
+ *     ignored by DSG_SORTING;
+ *   init_loads[n]: loads before iteration 1 (NULL: all zero, Alg. 2 lines
+ *     1-2); host memory unless out->flags has DSG_INIT_DEVICE.  Passing the
+ *     loads of an earlier run resumes it: T1 then T2 iterations give the
+ *     loads of T1 + T2 iterations.
+ * Loads are kept as 32-bit unsigned integers on the device:
+ * DSG_ERR_OVERFLOW if max(init_loads) + T * max_degree >= 2^32.
+ * Synchronises the context stream before returning. */
+int dsg_run(dsg_graph *g, int variant, int32_t T, int64_t eps_num, int64_t eps_den,
+            const int64_t *init_loads, dsg_result *out);
+
+/* Free an uploaded graph (stream-ordered release of its device memory). */
+void dsg_free_graph(dsg_graph *g);
+
+/* ---- instrumentation ---------------------------------------------------- */
+
+/* Kernel phases timed when profiling is on (dsg_set_profiling). */
+typedef enum {
+    DSG_PHASE_EDGE_SCAN = 0,  /* later-neighbour counts (Alg. 3 lines 2-3) */
+    DSG_PHASE_SORT = 1,       /* radix passes + fused densest suffix */
+    DSG_PHASE_OTHER = 2,      /* plan, snapshot, best-set, peeling rounds */
+    DSG_PHASE_COUNT = 3
+} dsg_phase;
+
+/* Turn per-phase CUDA-event timing on (1) or off (0) for later runs on ctx. */
+int dsg_set_profiling(dsg_ctx *ctx, int on);
+
+/* Accumulated statistics since the last reset (reset != 0 clears them):
+ *   ms[DSG_PHASE_COUNT]: device milliseconds per phase (profiling on);
+ *   launches[DSG_PHASE_COUNT]: kernels launched per phase (always counted);
+ *   bytes[DSG_PHASE_COUNT]: algorithmic bytes moved per phase (always). */
+int dsg_get_stats(dsg_ctx *ctx, double *ms, int64_t *launches, int64_t *bytes, int reset);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DSG_H */

@@ -1,0 +1,48 @@
+"""GB300-native densest subgraph refinement: PaRSorting++ and PaRGreedy++
+(arXiv 2311.04333), per-iteration load-weighted peeling of Greedy++.
+
+The compute path is libdsg (hand-written sm_103a CUDA behind the C ABI of
+include/dsg.h); this package is its Python binding.  Importing it loads the
+library and raises if it is missing or was not built: there is no CPU path.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+
+from ._dsg import (DSG_DST_DEVICE, DSG_INIT_DEVICE, DSG_PEELING, DSG_SORTING, DSG_SRC_DEVICE,
+                   DSG_VALIDATE, DsgError, LIB_PATH, dsg_create, dsg_destroy, dsg_free_graph,
+                   dsg_get_stats, dsg_graph_info, dsg_last_error, dsg_run, dsg_set_profiling,
+                   dsg_upload_csr)
+
+__all__ = ["DSG_SORTING", "DSG_PEELING", "DSG_VALIDATE", "DSG_SRC_DEVICE", "DSG_DST_DEVICE",
+           "DSG_INIT_DEVICE", "DsgError", "LIB_PATH", "dsg_create", "dsg_destroy",
+           "dsg_free_graph", "dsg_get_stats", "dsg_graph_info", "dsg_last_error", "dsg_run",
+           "dsg_set_profiling", "dsg_upload_csr", "Result", "densest"]
+
+
+@dataclass
+class Result:
+    best_edges: int
+    best_vertices: int
+    best_iter: int
+    best_set: np.ndarray      # int32 ascending ids
+    loads: np.ndarray         # int64[n]
+    trace: np.ndarray         # int64[T, 3]
+
+
+def densest(ctx, n: int, offsets: np.ndarray, adj: np.ndarray, variant: int = DSG_SORTING,
+            T: int = 10, eps: tuple[int, int] = (1, 10), init_loads=None,
+            validate: bool = True) -> Result:
+    """Upload a host CSR graph, run T refine iterations and read back."""
+    g = dsg_upload_csr(ctx, n, offsets, adj, DSG_VALIDATE if validate else 0)
+    try:
+        loads = np.zeros(n, dtype=np.int64)
+        bset = np.zeros(n, dtype=np.int32)
+        trace = np.zeros(3 * T, dtype=np.int64)
+        r = dsg_run(ctx, g, variant, T, eps[0], eps[1], init_loads, loads, bset, trace)
+    finally:
+        dsg_free_graph(g)
+    return Result(r["best_edges"], r["best_vertices"], r["best_iter"],
+                  bset[: r["best_set_size"]].copy(), loads, trace.reshape(T, 3))

@@ -1,0 +1,163 @@
+"""ctypes binding of libdsg (include/dsg.h): argument marshalling only.
+
+Every function keeps the C name.  Arrays may be numpy arrays (host memory)
+or torch tensors (host or CUDA); the binding passes their data pointers and
+sets DSG_SRC_DEVICE / DSG_DST_DEVICE / DSG_INIT_DEVICE from where they live.
+All computation happens in libdsg's CUDA kernels; if the library cannot be
+loaded, importing this module raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+DSG_OK, DSG_ERR_INVALID, DSG_ERR_NOMEM, DSG_ERR_CUDA, DSG_ERR_OVERFLOW, DSG_ERR_TIMEOUT, DSG_ERR_BUSY = range(7)
+DSG_SORTING, DSG_PEELING = 0, 1
+DSG_VALIDATE, DSG_SRC_DEVICE = 0x1, 0x2
+DSG_DST_DEVICE, DSG_INIT_DEVICE = 0x1, 0x2
+DSG_PHASE_EDGE_SCAN, DSG_PHASE_SORT, DSG_PHASE_OTHER, DSG_PHASE_COUNT = 0, 1, 2, 3
+
+STATUS_NAMES = {0: "DSG_OK", 1: "DSG_ERR_INVALID", 2: "DSG_ERR_NOMEM", 3: "DSG_ERR_CUDA",
+                4: "DSG_ERR_OVERFLOW", 5: "DSG_ERR_TIMEOUT", 6: "DSG_ERR_BUSY"}
+
+
+class DsgError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class dsg_result(ctypes.Structure):
+    _fields_ = [("flags", ctypes.c_uint32), ("best_iter", ctypes.c_int32),
+                ("best_edges", ctypes.c_int64), ("best_vertices", ctypes.c_int64),
+                ("best_set_size", ctypes.c_int64), ("loads", ctypes.c_void_p),
+                ("best_set", ctypes.c_void_p), ("trace", ctypes.c_void_p)]
+
+
+def _load():
+    path = os.environ.get("DSG_LIB") or _build.build()
+    lib = ctypes.CDLL(path)
+    P, I64, I32, U32, I = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint32, ctypes.c_int
+    lib.dsg_create.argtypes = [I, P, ctypes.POINTER(P)]
+    lib.dsg_destroy.argtypes = [P]
+    lib.dsg_destroy.restype = None
+    lib.dsg_last_error.argtypes = [P]
+    lib.dsg_last_error.restype = ctypes.c_char_p
+    lib.dsg_upload_csr.argtypes = [P, I64, P, P, U32, ctypes.POINTER(P)]
+    lib.dsg_graph_info.argtypes = [P, P, P, P]
+    lib.dsg_run.argtypes = [P, I, I32, I64, I64, P, ctypes.POINTER(dsg_result)]
+    lib.dsg_free_graph.argtypes = [P]
+    lib.dsg_free_graph.restype = None
+    lib.dsg_set_profiling.argtypes = [P, I]
+    lib.dsg_get_stats.argtypes = [P, P, P, P, I]
+    return lib
+
+
+LIB = _load()
+LIB_PATH = LIB._name
+
+
+def _is_torch(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+def _ptr(x, dtype) -> tuple[int | None, bool]:
+    """(data pointer, is_device) of a numpy array or torch tensor of `dtype`."""
+    if x is None:
+        return None, False
+    if _is_torch(x):
+        import torch
+        tdt = {np.int64: torch.int64, np.int32: torch.int32}[dtype]
+        if x.dtype != tdt or not x.is_contiguous():
+            raise TypeError(f"expected a contiguous {tdt} tensor")
+        return x.data_ptr(), x.is_cuda
+    if not isinstance(x, np.ndarray) or x.dtype != dtype or not x.flags.c_contiguous:
+        raise TypeError(f"expected a contiguous numpy {np.dtype(dtype)} array")
+    return x.ctypes.data, False
+
+
+def _check(ctx, rc: int) -> None:
+    if rc != DSG_OK:
+        raise DsgError(rc, LIB.dsg_last_error(ctx).decode())
+
+
+def dsg_create(device: int = 0, stream: int | None = None):
+    """Create a context on `device`; `stream` is a cudaStream_t handle (int)."""
+    out = ctypes.c_void_p()
+    rc = LIB.dsg_create(device, stream, ctypes.byref(out))
+    if rc != DSG_OK:
+        raise DsgError(rc, f"dsg_create(device={device}) failed")
+    return out.value
+
+
+def dsg_destroy(ctx) -> None:
+    LIB.dsg_destroy(ctx)
+
+
+def dsg_last_error(ctx) -> str:
+    return LIB.dsg_last_error(ctx).decode()
+
+
+def dsg_upload_csr(ctx, n: int, offsets, adj, flags: int = 0):
+    po, do = _ptr(offsets, np.int64)
+    pa, da = _ptr(adj, np.int32)
+    if do != da and pa is not None and int(offsets[-1]) > 0:
+        raise ValueError("offsets and adj must both live on the host or both on the device")
+    if do:
+        flags |= DSG_SRC_DEVICE
+    out = ctypes.c_void_p()
+    _check(ctx, LIB.dsg_upload_csr(ctx, n, po, pa, flags, ctypes.byref(out)))
+    return out.value
+
+
+def dsg_graph_info(graph) -> tuple[int, int, int]:
+    n, m, d = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    rc = LIB.dsg_graph_info(graph, ctypes.byref(n), ctypes.byref(m), ctypes.byref(d))
+    if rc != DSG_OK:
+        raise DsgError(rc, "dsg_graph_info")
+    return n.value, m.value, d.value
+
+
+def dsg_run(ctx, graph, variant: int, T: int, eps_num: int = 0, eps_den: int = 1,
+            init_loads=None, loads=None, best_set=None, trace=None) -> dict:
+    """Run T iterations.  `loads` (int64[n]), `best_set` (int32[n]) and
+    `trace` (int64[T*3]) are optional output buffers, all on the host or all
+    on the device; `init_loads` (int64[n]) may live on either side."""
+    res = dsg_result()
+    pl, dl = _ptr(loads, np.int64)
+    ps, ds = _ptr(best_set, np.int32)
+    pt, dt = _ptr(trace, np.int64)
+    pi, di = _ptr(init_loads, np.int64)
+    dev = {d for p, d in ((pl, dl), (ps, ds), (pt, dt)) if p is not None}
+    if len(dev) > 1:
+        raise ValueError("output buffers must all be host or all device")
+    res.flags = (DSG_DST_DEVICE if dev == {True} else 0) | (DSG_INIT_DEVICE if di else 0)
+    res.loads, res.best_set, res.trace = pl, ps, pt
+    _check(ctx, LIB.dsg_run(graph, variant, T, eps_num, eps_den, pi, ctypes.byref(res)))
+    return dict(best_edges=res.best_edges, best_vertices=res.best_vertices,
+                best_iter=res.best_iter, best_set_size=res.best_set_size)
+
+
+def dsg_free_graph(graph) -> None:
+    LIB.dsg_free_graph(graph)
+
+
+def dsg_set_profiling(ctx, on: bool) -> None:
+    _check(ctx, LIB.dsg_set_profiling(ctx, int(bool(on))))
+
+
+def dsg_get_stats(ctx, reset: bool = False) -> dict:
+    ms = (ctypes.c_double * DSG_PHASE_COUNT)()
+    la = (ctypes.c_int64 * DSG_PHASE_COUNT)()
+    by = (ctypes.c_int64 * DSG_PHASE_COUNT)()
+    _check(ctx, LIB.dsg_get_stats(ctx, ms, la, by, int(bool(reset))))
+    names = ["edge_scan", "sort", "other"]
+    return {nm: dict(ms=ms[i], launches=la[i], bytes=by[i]) for i, nm in enumerate(names)}
+
+
+EXPORTED = ["dsg_create", "dsg_destroy", "dsg_last_error", "dsg_upload_csr", "dsg_graph_info",
+            "dsg_run", "dsg_free_graph", "dsg_set_profiling", "dsg_get_stats"]

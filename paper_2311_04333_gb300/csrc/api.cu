@@ -1,0 +1,486 @@
+// api.cu -- the C ABI of libdsg (include/dsg.h): contexts, graph upload and
+// the host orchestration of one run of T refine iterations.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "dsg.h"
+#include "internal.h"
+#include "peeling.h"
+
+using namespace dsg;
+
+struct dsg_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int sm_count = 0;
+    std::string err;
+    bool profiling = false;
+    double ms[DSG_PHASE_COUNT] = {0, 0, 0};
+    int64_t launches[DSG_PHASE_COUNT] = {0, 0, 0};
+    int64_t bytes[DSG_PHASE_COUNT] = {0, 0, 0};
+    std::vector<cudaEvent_t> ev;     // event pool for profiling
+    size_t ev_used = 0;
+    struct Pending { size_t a, b; int phase; };
+    std::vector<Pending> pending;
+    int32_t *err_flags = nullptr;    // device scratch for validation
+    unsigned long long *red = nullptr;  // device scratch for reductions
+};
+
+struct dsg_graph {
+    dsg_ctx *ctx = nullptr;
+    GraphDev g{};
+    int64_t *off = nullptr;
+    int32_t *adj = nullptr;
+    WorkItem *items = nullptr;
+    uint32_t *heavy_mem = nullptr;
+    // run buffers, allocated on first use
+    bool rb_ready = false;
+    RunBufs rb{};
+    void *rb_mem = nullptr;
+    int64_t trace_cap = 0;
+    int32_t *npass_log = nullptr;
+    PeelBufs pb{};
+    bool pb_ready = false;
+};
+
+namespace {
+
+int fail(dsg_ctx *c, int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (c) c->err = buf;
+    return code;
+}
+
+int cuda_fail(dsg_ctx *c, cudaError_t e, const char *what)
+{
+    return fail(c, e == cudaErrorMemoryAllocation ? DSG_ERR_NOMEM : DSG_ERR_CUDA, "%s: %s", what,
+                cudaGetErrorString(e));
+}
+
+#define CK(call, what)                                            \
+    do {                                                          \
+        cudaError_t e_ = (call);                                  \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, what);   \
+    } while (0)
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+cudaEvent_t ev_get(dsg_ctx *c)
+{
+    if (c->ev_used == c->ev.size()) {
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        c->ev.push_back(e);
+    }
+    return c->ev[c->ev_used++];
+}
+
+struct PhaseTimer {
+    dsg_ctx *c;
+    size_t a = 0;
+    int phase;
+    PhaseTimer(dsg_ctx *ctx, int ph) : c(ctx), phase(ph)
+    {
+        if (c->profiling) {
+            a = c->ev_used;
+            cudaEventRecord(ev_get(c), c->stream);
+        }
+    }
+    ~PhaseTimer()
+    {
+        if (c->profiling) {
+            size_t b = c->ev_used;
+            cudaEventRecord(ev_get(c), c->stream);
+            c->pending.push_back({a, b, phase});
+        }
+    }
+};
+
+void collect_timings(dsg_ctx *c)
+{
+    for (auto &p : c->pending) {
+        float ms = 0;
+        if (cudaEventElapsedTime(&ms, c->ev[p.a], c->ev[p.b]) == cudaSuccess) c->ms[p.phase] += ms;
+    }
+    c->pending.clear();
+    c->ev_used = 0;
+}
+
+int ensure_run_bufs(dsg_ctx *ctx, dsg_graph *G, int32_t T)
+{
+    const int64_t n = G->g.n;
+    RunBufs &b = G->rb;
+    if (!G->rb_ready) {
+        const int64_t ntiles = (n + kPassTile - 1) / kPassTile;
+        const int64_t nblk = (n + 4095) / 4096 + 1;
+        size_t sz[12] = {
+            (size_t)n * 4,                      // loads
+            (size_t)n * 4,                      // A
+            (size_t)n * 16,                     // keys[2], vals[2] (also output staging)
+            (size_t)n * 4,                      // best_loads
+            (size_t)ntiles * kBuckets * 8,      // status
+            (size_t)ntiles * kBuckets * 16,     // status_sum
+            (size_t)ntiles * sizeof(Candidate), // cand
+            sizeof(Control),                    // ctl
+            (size_t)nblk * 8,                   // blk_a
+            (size_t)nblk * 8,                   // blk_b
+            0, 0};
+        size_t total = 0;
+        for (size_t s : sz) total += align256(s);
+        char *mem = nullptr;
+        CK(cudaMallocAsync((void **)&mem, total, ctx->stream), "run buffers");
+        char *p = mem;
+        auto take = [&](size_t s) { char *q = p; p += align256(s); return (void *)q; };
+        b.loads = (uint32_t *)take(sz[0]);
+        b.A = (uint32_t *)take(sz[1]);
+        uint32_t *kv = (uint32_t *)take(sz[2]);
+        b.keys[0] = kv;
+        b.keys[1] = kv + n;
+        b.vals[0] = kv + 2 * n;
+        b.vals[1] = kv + 3 * n;
+        b.scratch = kv;
+        b.best_loads = (uint32_t *)take(sz[3]);
+        b.status = (unsigned long long *)take(sz[4]);
+        b.status_sum = (unsigned long long *)take(sz[5]);
+        b.cand = (Candidate *)take(sz[6]);
+        b.ctl = (Control *)take(sz[7]);
+        b.blk_a = (int64_t *)take(sz[8]);
+        b.blk_b = (int64_t *)take(sz[9]);
+        b.ntiles = ntiles;
+        b.nblk64 = nblk;
+        CK(cudaMemsetAsync(b.status, 0, sz[4], ctx->stream), "status init");
+        CK(cudaMemsetAsync(b.ctl, 0, sizeof(Control), ctx->stream), "ctl init");
+        CK(cudaMemsetAsync(b.A, 0, sz[1], ctx->stream), "A init");
+        G->rb_mem = mem;
+        G->rb_ready = true;
+    }
+    if (G->trace_cap < T) {
+        if (b.trace) cudaFreeAsync(b.trace, ctx->stream);
+        if (G->npass_log) cudaFreeAsync(G->npass_log, ctx->stream);
+        b.trace = nullptr;
+        G->npass_log = nullptr;
+        CK(cudaMallocAsync((void **)&b.trace, sizeof(int64_t) * 3 * (size_t)T, ctx->stream), "trace");
+        CK(cudaMallocAsync((void **)&G->npass_log, sizeof(int32_t) * (size_t)T, ctx->stream), "npass log");
+        G->trace_cap = T;
+    }
+    return DSG_OK;
+}
+
+__global__ void k_log_npass(const Control *ctl, int32_t *log, int t) { log[t - 1] = ctl->npass; }
+
+}  // namespace
+
+extern "C" {
+
+int dsg_create(int device, void *cuda_stream, dsg_ctx **out)
+{
+    if (!out) return DSG_ERR_INVALID;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return DSG_ERR_CUDA;
+    if (device < 0 || device >= ndev) return DSG_ERR_INVALID;
+    if (cudaSetDevice(device) != cudaSuccess) return DSG_ERR_CUDA;
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) return DSG_ERR_CUDA;
+    if (prop.major * 10 + prop.minor < 100) return DSG_ERR_INVALID;   // built for sm_103a only
+    dsg_ctx *ctx = new (std::nothrow) dsg_ctx;
+    if (!ctx) return DSG_ERR_NOMEM;
+    ctx->device = device;
+    ctx->stream = (cudaStream_t)cuda_stream;
+    ctx->sm_count = prop.multiProcessorCount;
+    if (cudaMalloc((void **)&ctx->err_flags, 64) != cudaSuccess ||
+        cudaMalloc((void **)&ctx->red, 64) != cudaSuccess) {
+        cudaFree(ctx->err_flags);
+        delete ctx;
+        return DSG_ERR_NOMEM;
+    }
+    *out = ctx;
+    return DSG_OK;
+}
+
+void dsg_destroy(dsg_ctx *ctx)
+{
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    for (auto e : ctx->ev) cudaEventDestroy(e);
+    cudaFree(ctx->err_flags);
+    cudaFree(ctx->red);
+    delete ctx;
+}
+
+const char *dsg_last_error(const dsg_ctx *ctx) { return ctx ? ctx->err.c_str() : "no context"; }
+
+int dsg_upload_csr(dsg_ctx *ctx, int64_t n, const int64_t *offsets, const int32_t *adj,
+                   uint32_t flags, dsg_graph **out)
+{
+    if (!ctx || !out) return DSG_ERR_INVALID;
+    *out = nullptr;
+    if (n < 1 || n >= ((int64_t)1 << 31)) return fail(ctx, DSG_ERR_INVALID, "n = %lld out of [1, 2^31)", (long long)n);
+    if (!offsets) return fail(ctx, DSG_ERR_INVALID, "offsets is NULL");
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    const bool dev_src = flags & DSG_SRC_DEVICE;
+    int64_t ends[2];
+    if (dev_src) {
+        CK(cudaMemcpyAsync(&ends[0], offsets, 8, cudaMemcpyDeviceToHost, ctx->stream), "read offsets");
+        CK(cudaMemcpyAsync(&ends[1], offsets + n, 8, cudaMemcpyDeviceToHost, ctx->stream), "read offsets");
+        CK(cudaStreamSynchronize(ctx->stream), "sync");
+    } else {
+        ends[0] = offsets[0];
+        ends[1] = offsets[n];
+    }
+    if (ends[0] != 0) return fail(ctx, DSG_ERR_INVALID, "offsets[0] = %lld, expected 0", (long long)ends[0]);
+    const int64_t arcs = ends[1];
+    if (arcs < 0 || (arcs & 1) || arcs >= ((int64_t)1 << 40))
+        return fail(ctx, DSG_ERR_INVALID, "offsets[n] = %lld must be even and in [0, 2^40)", (long long)arcs);
+    if (arcs > 0 && !adj) return fail(ctx, DSG_ERR_INVALID, "adj is NULL");
+
+    dsg_graph *G = new (std::nothrow) dsg_graph;
+    if (!G) return fail(ctx, DSG_ERR_NOMEM, "host allocation");
+    G->ctx = ctx;
+    auto bail = [&](int code) {
+        if (G->off) cudaFreeAsync(G->off, ctx->stream);
+        if (G->adj) cudaFreeAsync(G->adj, ctx->stream);
+        if (G->items) cudaFreeAsync(G->items, ctx->stream);
+        if (G->heavy_mem) cudaFreeAsync(G->heavy_mem, ctx->stream);
+        cudaStreamSynchronize(ctx->stream);
+        delete G;
+        return code;
+    };
+    cudaError_t e;
+    const cudaMemcpyKind kind = dev_src ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    if ((e = cudaMallocAsync((void **)&G->off, sizeof(int64_t) * (size_t)(n + 1), ctx->stream)) != cudaSuccess)
+        return bail(cuda_fail(ctx, e, "offsets allocation"));
+    if ((e = cudaMallocAsync((void **)&G->adj, sizeof(int32_t) * (size_t)(arcs > 0 ? arcs : 1), ctx->stream)) != cudaSuccess)
+        return bail(cuda_fail(ctx, e, "adjacency allocation"));
+    if ((e = cudaMemcpyAsync(G->off, offsets, sizeof(int64_t) * (size_t)(n + 1), kind, ctx->stream)) != cudaSuccess)
+        return bail(cuda_fail(ctx, e, "offsets copy"));
+    if (arcs > 0 && (e = cudaMemcpyAsync(G->adj, adj, sizeof(int32_t) * (size_t)arcs, kind, ctx->stream)) != cudaSuccess)
+        return bail(cuda_fail(ctx, e, "adjacency copy"));
+    G->g.n = n;
+    G->g.arcs = arcs;
+    G->g.off = G->off;
+    G->g.adj = G->adj;
+    // validation (monotone offsets, ids in range, no self-loops; with
+    // DSG_VALIDATE also strictly ascending lists and symmetry)
+    int32_t h_err[8];
+    if ((e = launch_validate(G->g, (flags & DSG_VALIDATE) ? 1 : 0, ctx->err_flags, ctx->stream)) != cudaSuccess)
+        return bail(cuda_fail(ctx, e, "validate"));
+    if ((e = cudaMemsetAsync(ctx->red, 0, 8, ctx->stream)) != cudaSuccess) return bail(cuda_fail(ctx, e, "memset"));
+    if ((e = launch_degree_max(G->off, n, ctx->red, ctx->stream)) != cudaSuccess)
+        return bail(cuda_fail(ctx, e, "degree max"));
+    unsigned long long h_maxdeg = 0;
+    cudaMemcpyAsync(h_err, ctx->err_flags, sizeof(h_err), cudaMemcpyDeviceToHost, ctx->stream);
+    cudaMemcpyAsync(&h_maxdeg, ctx->red, 8, cudaMemcpyDeviceToHost, ctx->stream);
+    if ((e = cudaStreamSynchronize(ctx->stream)) != cudaSuccess) return bail(cuda_fail(ctx, e, "upload"));
+    static const char *what[5] = {"offsets are not non-decreasing", "a neighbour id is out of [0, n)",
+                                  "the graph has a self-loop",
+                                  "an adjacency list is not strictly ascending (duplicate or unsorted)",
+                                  "the graph is not symmetric"};
+    for (int i = 0; i < 5; ++i)
+        if (h_err[i]) return bail(fail(ctx, DSG_ERR_INVALID, "invalid graph: %s", what[i]));
+    G->g.max_degree = (int64_t)h_maxdeg;
+    // edge-scan tile schedule
+    const int64_t nwin = arcs / kWin + 1;
+    void *tmp = nullptr;
+    const size_t tmp_bytes = (size_t)(2 * nwin + 4) * sizeof(int64_t);
+    if ((e = cudaMallocAsync(&tmp, tmp_bytes, ctx->stream)) != cudaSuccess) return bail(cuda_fail(ctx, e, "schedule scratch"));
+    e = build_schedule(G->g, tmp, tmp_bytes, ctx->stream, &G->g.n_items, &G->g.n_heavy, &G->items, &G->heavy_mem);
+    cudaFreeAsync(tmp, ctx->stream);
+    if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "schedule"));
+    G->g.items = G->items;
+    G->g.heavy_acc = G->heavy_mem;
+    G->g.heavy_done = G->heavy_mem + (G->g.n_heavy > 0 ? G->g.n_heavy : 1);
+    if ((e = cudaStreamSynchronize(ctx->stream)) != cudaSuccess) return bail(cuda_fail(ctx, e, "upload"));
+    ctx->launches[DSG_PHASE_OTHER] += 7;
+    *out = G;
+    return DSG_OK;
+}
+
+int dsg_graph_info(const dsg_graph *G, int64_t *n, int64_t *m, int64_t *max_degree)
+{
+    if (!G) return DSG_ERR_INVALID;
+    if (n) *n = G->g.n;
+    if (m) *m = G->g.arcs / 2;
+    if (max_degree) *max_degree = G->g.max_degree;
+    return DSG_OK;
+}
+
+void dsg_free_graph(dsg_graph *G)
+{
+    if (!G) return;
+    dsg_ctx *ctx = G->ctx;
+    cudaSetDevice(ctx->device);
+    cudaFreeAsync(G->off, ctx->stream);
+    cudaFreeAsync(G->adj, ctx->stream);
+    if (G->items) cudaFreeAsync(G->items, ctx->stream);
+    if (G->heavy_mem) cudaFreeAsync(G->heavy_mem, ctx->stream);
+    if (G->rb_mem) cudaFreeAsync(G->rb_mem, ctx->stream);
+    if (G->rb.trace) cudaFreeAsync(G->rb.trace, ctx->stream);
+    if (G->npass_log) cudaFreeAsync(G->npass_log, ctx->stream);
+    peel_free(G->pb, ctx->stream);
+    cudaStreamSynchronize(ctx->stream);
+    delete G;
+}
+
+int dsg_set_profiling(dsg_ctx *ctx, int on)
+{
+    if (!ctx) return DSG_ERR_INVALID;
+    ctx->profiling = on != 0;
+    return DSG_OK;
+}
+
+int dsg_get_stats(dsg_ctx *ctx, double *ms, int64_t *launches, int64_t *bytes, int reset)
+{
+    if (!ctx) return DSG_ERR_INVALID;
+    for (int i = 0; i < DSG_PHASE_COUNT; ++i) {
+        if (ms) ms[i] = ctx->ms[i];
+        if (launches) launches[i] = ctx->launches[i];
+        if (bytes) bytes[i] = ctx->bytes[i];
+    }
+    if (reset)
+        for (int i = 0; i < DSG_PHASE_COUNT; ++i) ctx->ms[i] = 0, ctx->launches[i] = 0, ctx->bytes[i] = 0;
+    return DSG_OK;
+}
+
+int dsg_run(dsg_graph *G, int variant, int32_t T, int64_t eps_num, int64_t eps_den,
+            const int64_t *init_loads, dsg_result *out)
+{
+    if (!G || !out) return DSG_ERR_INVALID;
+    dsg_ctx *ctx = G->ctx;
+    if (variant != DSG_SORTING && variant != DSG_PEELING)
+        return fail(ctx, DSG_ERR_INVALID, "unknown variant %d", variant);
+    if (T < 1) return fail(ctx, DSG_ERR_INVALID, "T = %d must be >= 1", T);
+    if (eps_den < 1 || eps_num < 0) return fail(ctx, DSG_ERR_INVALID, "eps = %lld/%lld: need p >= 0, q >= 1",
+                                                (long long)eps_num, (long long)eps_den);
+    if (eps_num + eps_den >= ((int64_t)1 << 31))
+        return fail(ctx, DSG_ERR_OVERFLOW, "p + q must be < 2^31");
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    const int64_t n = G->g.n;
+    const bool init_dev = out->flags & DSG_INIT_DEVICE;
+    const bool dst_dev = out->flags & DSG_DST_DEVICE;
+    // overflow check: loads stay below 2^32
+    unsigned long long max_init = 0;
+    if (init_loads) {
+        if (init_dev) {
+            int *neg = (int *)(ctx->red + 1);
+            CK(cudaMemsetAsync(ctx->red, 0, 16, ctx->stream), "memset");
+            CK(launch_max_u64_of_i64(init_loads, n, ctx->red, neg, ctx->stream), "init max");
+            unsigned long long h[2];
+            CK(cudaMemcpyAsync(h, ctx->red, 16, cudaMemcpyDeviceToHost, ctx->stream), "init max");
+            CK(cudaStreamSynchronize(ctx->stream), "sync");
+            if ((int)(h[1] & 0xffffffffu)) return fail(ctx, DSG_ERR_INVALID, "negative initial load");
+            max_init = h[0];
+            ctx->launches[DSG_PHASE_OTHER] += 1;
+        } else {
+            for (int64_t v = 0; v < n; ++v) {
+                if (init_loads[v] < 0) return fail(ctx, DSG_ERR_INVALID, "negative initial load at %lld", (long long)v);
+                if ((unsigned long long)init_loads[v] > max_init) max_init = init_loads[v];
+            }
+        }
+    }
+    if (max_init + (unsigned long long)T * (unsigned long long)G->g.max_degree >= (1ull << 32))
+        return fail(ctx, DSG_ERR_OVERFLOW, "max(init) + T * max_degree = %llu does not fit 32-bit loads",
+                    max_init + (unsigned long long)T * (unsigned long long)G->g.max_degree);
+    int rc = ensure_run_bufs(ctx, G, T);
+    if (rc) return rc;
+    RunBufs &b = G->rb;
+    cudaStream_t s = ctx->stream;
+    const int64_t *init_ptr = nullptr;
+    if (init_loads) {
+        if (init_dev) init_ptr = init_loads;
+        else {
+            CK(cudaMemcpyAsync(b.scratch, init_loads, sizeof(int64_t) * (size_t)n, cudaMemcpyHostToDevice, s),
+               "init loads copy");
+            init_ptr = (const int64_t *)b.scratch;
+        }
+    }
+    const int64_t m = G->g.arcs / 2;
+    {
+        PhaseTimer pt(ctx, DSG_PHASE_OTHER);
+        CK(launch_init(G->g, b, init_ptr, 0, s), "init");
+        ctx->launches[DSG_PHASE_OTHER] += 2;
+    }
+    if (variant == DSG_SORTING) {
+        const int es_grid = ctx->sm_count * edge_scan_sm_count();
+        for (int t = 1; t <= T; ++t) {
+            {
+                PhaseTimer pt(ctx, DSG_PHASE_OTHER);
+                CK(launch_plan(G->g, b, t, s), "plan");
+                k_log_npass<<<1, 1, 0, s>>>(b.ctl, G->npass_log, t);
+            }
+            {
+                PhaseTimer pt(ctx, DSG_PHASE_EDGE_SCAN);
+                CK(launch_edge_scan(G->g, b, es_grid, s), "edge scan");
+            }
+            {
+                PhaseTimer pt(ctx, DSG_PHASE_SORT);
+                for (int k = 0; k < kMaxPasses; ++k) CK(launch_radix_pass(G->g, b, k, t, s), "radix pass");
+            }
+            {
+                PhaseTimer pt(ctx, DSG_PHASE_OTHER);
+                CK(launch_snapshot(G->g, b, s), "snapshot");
+            }
+            ctx->launches[DSG_PHASE_OTHER] += 3;
+            ctx->launches[DSG_PHASE_EDGE_SCAN] += 1;
+            ctx->launches[DSG_PHASE_SORT] += kMaxPasses;
+            ctx->bytes[DSG_PHASE_EDGE_SCAN] += 16 * m + 16 * n;
+        }
+    } else {
+        PhaseTimer pt(ctx, DSG_PHASE_OTHER);
+        int nl = 0;
+        rc = peel_run(ctx->stream, G->g, b, G->pb, G->pb_ready, ctx->sm_count, T, eps_num, eps_den, &nl,
+                      ctx->err);
+        ctx->launches[DSG_PHASE_OTHER] += nl;
+        if (rc) return rc;
+    }
+    // outputs: best set, loads, trace
+    int nl = 0;
+    int32_t *set_dst = nullptr;
+    if (out->best_set) set_dst = dst_dev ? out->best_set : (int32_t *)((char *)b.scratch + 8 * (size_t)n);
+    {
+        PhaseTimer pt(ctx, DSG_PHASE_OTHER);
+        CK(launch_best_set(G->g, b, set_dst, s, &nl), "best set");
+        if (out->loads) {
+            int64_t *ldst = dst_dev ? out->loads : (int64_t *)b.scratch;
+            CK(launch_loads_out(G->g, b, ldst, s), "loads out");
+            ++nl;
+            if (!dst_dev) CK(cudaMemcpyAsync(out->loads, ldst, sizeof(int64_t) * (size_t)n, cudaMemcpyDeviceToHost, s), "loads D2H");
+        }
+        if (out->trace)
+            CK(cudaMemcpyAsync(out->trace, b.trace, sizeof(int64_t) * 3 * (size_t)T,
+                               dst_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s), "trace copy");
+    }
+    ctx->launches[DSG_PHASE_OTHER] += nl;
+    Control h;
+    CK(cudaMemcpyAsync(&h, b.ctl, sizeof(Control), cudaMemcpyDeviceToHost, s), "control D2H");
+    std::vector<int32_t> np(variant == DSG_SORTING ? T : 0);
+    if (variant == DSG_SORTING)
+        CK(cudaMemcpyAsync(np.data(), G->npass_log, sizeof(int32_t) * T, cudaMemcpyDeviceToHost, s), "npass D2H");
+    CK(cudaStreamSynchronize(s), "run");
+    if (h.err) return fail(ctx, h.err, "device-side failure %d at site %d (a bounded wait gave up)", h.err, h.err_where);
+    for (int32_t p : np) {
+        // pass 0 reads (l, A) and writes l + A; scatter passes read and write
+        // (key, value); the last pass reads only.
+        int64_t by = 12 * n + (p > 1 ? 8 * n : 0) + (p > 2 ? 16 * n * (p - 2) : 0) + (p > 1 ? 8 * n : 0);
+        ctx->bytes[DSG_PHASE_SORT] += by;
+    }
+    if (!dst_dev && out->best_set && h.set_size > 0)
+        CK(cudaMemcpy(out->best_set, set_dst, sizeof(int32_t) * (size_t)h.set_size, cudaMemcpyDeviceToHost), "set D2H");
+    out->best_edges = h.best_e;
+    out->best_vertices = h.best_v;
+    out->best_iter = h.best_iter;
+    out->best_set_size = h.set_size;
+    if (ctx->profiling) collect_timings(ctx);
+    return DSG_OK;
+}
+
+}  // extern "C"

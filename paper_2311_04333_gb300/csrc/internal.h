@@ -1,0 +1,127 @@
+// internal.h -- layouts shared by the host orchestration (api.cu) and the
+// kernels of libdsg.  Not part of the C ABI.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace dsg {
+
+// ---- edge-scan tile schedule ----------------------------------------------
+// The arc array is cut into windows of kWin arcs.  Window b owns the
+// vertices whose first arc lies in [b*kWin, (b+1)*kWin).  Its light
+// vertices (degree <= kWin) form up to ceil(count/kTileV) light tiles of
+// consecutive ids (at most 2*kWin arcs each); a heavy vertex (degree > kWin)
+// is always the last vertex of its window and is split into chunks of kWin
+// arcs, one work item each.
+constexpr int kWin = 4096;
+constexpr int kTileV = 4096;
+constexpr uint32_t kHeavyBit = 0x80000000u;
+
+struct WorkItem {
+    int64_t a0;      // first arc
+    uint32_t u;      // first vertex (light) or the heavy vertex
+    uint32_t info;   // light: vertex count; heavy: kHeavyBit | heavy index
+};
+
+// ---- radix passes -----------------------------------------------------------
+constexpr int kRadixBits = 8;
+constexpr int kBuckets = 1 << kRadixBits;
+constexpr int kMaxPasses = 4;          // 32-bit keys
+constexpr int kPassThreads = 256;      // == kBuckets (one lookback lane per bucket)
+constexpr int kPassIpt = 16;           // items per thread
+constexpr int kPassTile = kPassThreads * kPassIpt;
+
+// status word of the decoupled look-back: [epoch:16][flag:2][count:46]
+constexpr uint64_t kFlagAgg = 1, kFlagIncl = 2, kFlagAbort = 3;
+
+// candidate densest suffix of one tile: density edges/vertices, position of
+// the suffix's first vertex in the order, and its load key.
+struct Candidate {
+    int64_t e;
+    int64_t v;
+    int64_t pos;
+    int64_t key;
+};
+
+// Per-run control block in device memory.
+struct Control {
+    // best so far (Alg. 2: S <- G, replaced only on a strictly higher density)
+    int64_t best_e, best_v, best_pos;
+    int64_t best_key;        // load (at the start of best_iter) of the suffix's first vertex
+    int32_t best_iter;
+    int32_t improved;        // set by the last pass when this iteration beat the best
+    int32_t err;             // dsg_status of a device-side failure (0 = none)
+    int32_t err_where;
+    // per-iteration plan (written by the plan kernel)
+    uint32_t lmin;           // minimum load at the start of the iteration
+    int32_t npass;           // number of radix passes (>= 1)
+    int32_t shift[kMaxPasses];
+    uint32_t epoch;          // look-back epoch of pass 0 of this iteration
+    // min/max of the next iteration's loads, double-buffered by iteration parity
+    uint32_t mm_min[2], mm_max[2];
+    // counters
+    uint32_t item_ctr;       // edge-scan work-item dispenser
+    uint32_t tile_ctr[kMaxPasses];
+    uint32_t done_ctr;       // last-tile detection of the final pass
+    uint32_t width;          // max deg* of the iteration (empirical width)
+    // histograms of the iteration (written by the edge scan)
+    uint32_t hist[kMaxPasses][kBuckets];    // counts per digit of (l - lmin)
+    unsigned long long asum[kBuckets];       // sum of deg* per digit of the last pass
+    // best-set materialisation
+    int64_t thr_id;          // id of the best suffix's first vertex
+    int64_t cnt_less;        // #{v : L(v) < best_key}
+    int64_t set_size;
+};
+
+// ---- host launchers (implemented in kernels_*.cu) --------------------------
+struct GraphDev {
+    int64_t n, arcs;         // arcs = 2m
+    int64_t max_degree;
+    const int64_t *off;
+    const int32_t *adj;
+    const WorkItem *items;
+    int64_t n_items;
+    int64_t n_heavy;
+    uint32_t *heavy_acc;     // [n_heavy]
+    uint32_t *heavy_done;    // [n_heavy]
+};
+
+struct RunBufs {
+    uint32_t *loads;         // l_t (overwritten by l_{t+1} in pass 0)
+    uint32_t *A;             // deg* by vertex id
+    uint32_t *keys[2];
+    uint32_t *vals[2];
+    uint32_t *best_loads;    // l_{t*} snapshot of the best iteration
+    unsigned long long *status;      // [ntiles * kBuckets]
+    unsigned long long *status_sum;  // [ntiles * kBuckets]
+    Candidate *cand;         // [ntiles]
+    int64_t ntiles;
+    Control *ctl;
+    int64_t *trace;          // [T * 3] device
+    int64_t *blk_a, *blk_b;  // scratch for block-level counts (size nblk64)
+    int64_t nblk64;
+    void *scratch;           // >= 8n bytes (output staging)
+};
+
+int edge_scan_sm_count();
+cudaError_t launch_validate(const GraphDev &g, int full, int32_t *err_flags, cudaStream_t s);
+cudaError_t build_schedule(GraphDev &g, void *tmp, size_t tmp_bytes, cudaStream_t s,
+                           int64_t *n_items_out, int64_t *n_heavy_out, WorkItem **items_out,
+                           uint32_t **heavy_mem_out);
+cudaError_t launch_init(const GraphDev &g, RunBufs &b, const int64_t *init_dev, int init_is_u32,
+                        cudaStream_t s);
+cudaError_t launch_plan(const GraphDev &g, RunBufs &b, int t, cudaStream_t s);
+cudaError_t launch_edge_scan(const GraphDev &g, RunBufs &b, int grid, cudaStream_t s);
+// pass k of the radix sort of (key, A); pass 0 reads key0 (default: the
+// loads) and, if update_loads, writes loads += A.
+cudaError_t launch_radix_pass(const GraphDev &g, RunBufs &b, int k, int t, cudaStream_t s,
+                              const uint32_t *key0 = nullptr, bool update_loads = true);
+cudaError_t launch_snapshot(const GraphDev &g, RunBufs &b, cudaStream_t s);
+cudaError_t launch_best_set(const GraphDev &g, RunBufs &b, int32_t *set_dev, cudaStream_t s,
+                            int *launches);
+cudaError_t launch_loads_out(const GraphDev &g, RunBufs &b, int64_t *dst, cudaStream_t s);
+cudaError_t launch_max_u64_of_i64(const int64_t *src, int64_t n, unsigned long long *dst,
+                                  int *neg_flag, cudaStream_t s);
+cudaError_t launch_degree_max(const int64_t *off, int64_t n, unsigned long long *dst, cudaStream_t s);
+
+}  // namespace dsg

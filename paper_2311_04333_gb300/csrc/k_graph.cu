@@ -1,0 +1,233 @@
+// k_graph.cu -- upload-time kernels: CSR validation and the tile schedule
+// of the edge scan, plus small reductions used by the host orchestration.
+#include "common.cuh"
+
+namespace dsg {
+
+// ============================================================ validation
+// err_flags[0]: offsets not monotone; [1]: neighbour out of range;
+// [2]: self-loop; [3]: list not strictly ascending (duplicate);
+// [4]: asymmetric edge (full validation only).
+
+__device__ __forceinline__ bool has_arc(const int64_t *off, const int32_t *adj, int32_t w, int32_t u)
+{
+    int64_t lo = off[w], hi = off[w + 1];
+    while (lo < hi) {
+        const int64_t mid = lo + (hi - lo) / 2;
+        const int32_t x = adj[mid];
+        if (x == u) return true;
+        if (x < u) lo = mid + 1; else hi = mid;
+    }
+    return false;
+}
+
+__global__ void k_validate(const int64_t *__restrict__ off, const int32_t *__restrict__ adj,
+                           int64_t n, int64_t arcs, int full, int32_t *err)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t u = wid; u < n; u += nw) {
+        const int64_t s = off[u], e = off[u + 1];
+        if (s < 0 || e > arcs || e < s) { if (lane == 0) atomicExch(&err[0], 1); continue; }
+        for (int64_t j = s + lane; j < e; j += 32) {
+            const int32_t w = adj[j];
+            if (w < 0 || w >= n) { atomicExch(&err[1], 1); continue; }
+            if (w == (int32_t)u) atomicExch(&err[2], 1);
+            if (full) {
+                if (j > s && adj[j - 1] >= w) atomicExch(&err[3], 1);
+                if (!has_arc(off, adj, w, (int32_t)u)) atomicExch(&err[4], 1);
+            }
+        }
+    }
+}
+
+cudaError_t launch_validate(const GraphDev &g, int full, int32_t *err_flags, cudaStream_t s)
+{
+    cudaMemsetAsync(err_flags, 0, 8 * sizeof(int32_t), s);
+    int64_t warps = g.n;
+    int grid = (int)imin64((warps * 32 + 255) / 256, 152 * 16);
+    if (grid < 1) grid = 1;
+    k_validate<<<grid, 256, 0, s>>>(g.off, g.adj, g.n, g.arcs, full, err_flags);
+    return cudaGetLastError();
+}
+
+// ============================================================ tile schedule
+
+__device__ __forceinline__ int64_t lower_bound_off(const int64_t *off, int64_t n, int64_t x)
+{
+    // first u in [0, n] with off[u] >= x, or n + 1
+    int64_t lo = 0, hi = n + 1;
+    while (lo < hi) {
+        const int64_t mid = lo + (hi - lo) / 2;
+        if (off[mid] >= x) hi = mid; else lo = mid + 1;
+    }
+    return lo;
+}
+
+struct WinInfo {
+    int64_t lo, nv;      // vertices [lo, lo + nv) start in the window
+    int heavy;           // the last one is heavy
+    int64_t hdeg;
+};
+
+__device__ __forceinline__ WinInfo window_info(const int64_t *off, int64_t n, int64_t b)
+{
+    WinInfo w;
+    int64_t lo = lower_bound_off(off, n, b * (int64_t)kWin);
+    int64_t hi = lower_bound_off(off, n, (b + 1) * (int64_t)kWin);
+    if (lo > n) lo = n;
+    if (hi > n) hi = n;
+    w.lo = lo;
+    w.nv = hi - lo;
+    w.heavy = 0;
+    w.hdeg = 0;
+    if (w.nv > 0) {
+        const int64_t last = hi - 1;
+        const int64_t d = off[last + 1] - off[last];
+        if (d > kWin) { w.heavy = 1; w.hdeg = d; }
+    }
+    return w;
+}
+
+__global__ void k_sched_count(const int64_t *__restrict__ off, int64_t n, int64_t nwin,
+                              int64_t *cnt_items, int64_t *cnt_heavy)
+{
+    for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < nwin;
+         b += (int64_t)gridDim.x * blockDim.x) {
+        const WinInfo w = window_info(off, n, b);
+        const int64_t nlight = w.nv - w.heavy;
+        int64_t c = (nlight + kTileV - 1) / kTileV;
+        if (w.heavy) c += (w.hdeg + kWin - 1) / kWin;
+        cnt_items[b] = c;
+        cnt_heavy[b] = w.heavy;
+    }
+}
+
+__global__ void k_sched_write(const int64_t *__restrict__ off, int64_t n, int64_t nwin,
+                              const int64_t *item_off, const int64_t *heavy_off, WorkItem *items)
+{
+    for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < nwin;
+         b += (int64_t)gridDim.x * blockDim.x) {
+        const WinInfo w = window_info(off, n, b);
+        const int64_t nlight = w.nv - w.heavy;
+        int64_t o = item_off[b];
+        for (int64_t s = 0; s < nlight; s += kTileV) {
+            WorkItem it;
+            it.u = (uint32_t)(w.lo + s);
+            it.a0 = off[w.lo + s];
+            it.info = (uint32_t)imin64(kTileV, nlight - s);
+            items[o++] = it;
+        }
+        if (w.heavy) {
+            const int64_t hv = w.lo + w.nv - 1;
+            const int64_t base = off[hv];
+            for (int64_t c = 0; c * kWin < w.hdeg; ++c) {
+                WorkItem it;
+                it.u = (uint32_t)hv;
+                it.a0 = base + c * kWin;
+                it.info = kHeavyBit | (uint32_t)heavy_off[b];
+                items[o++] = it;
+            }
+        }
+    }
+}
+
+// exclusive scan of int64 in place, single block, chunked; writes the total
+__global__ void k_scan_single(int64_t *x, int64_t count, int64_t *total)
+{
+    __shared__ unsigned long long red[33];
+    int64_t carry = 0;
+    for (int64_t c0 = 0; c0 < count; c0 += blockDim.x) {
+        const int64_t i = c0 + threadIdx.x;
+        const uint64_t v = i < count ? (uint64_t)x[i] : 0;
+        uint64_t tot;
+        const uint64_t ex = block_excl_sum_u64(v, red, &tot);
+        if (i < count) x[i] = carry + (int64_t)ex;
+        carry += (int64_t)tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *total = carry;
+}
+
+// tmp must hold 2*(nwin+1) int64 + 2 totals
+cudaError_t build_schedule(GraphDev &g, void *tmp, size_t tmp_bytes, cudaStream_t s,
+                           int64_t *n_items_out, int64_t *n_heavy_out, WorkItem **items_out,
+                           uint32_t **heavy_mem_out)
+{
+    const int64_t nwin = g.arcs / kWin + 1;
+    if (tmp_bytes < (size_t)(2 * nwin + 4) * sizeof(int64_t)) return cudaErrorInvalidValue;
+    int64_t *ci = (int64_t *)tmp, *ch = ci + nwin, *tot = ch + nwin;
+    int grid = (int)imin64((nwin + 255) / 256, 152 * 8);
+    k_sched_count<<<grid, 256, 0, s>>>(g.off, g.n, nwin, ci, ch);
+    k_scan_single<<<1, 1024, 0, s>>>(ci, nwin, tot);
+    k_scan_single<<<1, 1024, 0, s>>>(ch, nwin, tot + 1);
+    int64_t h_tot[2];
+    cudaError_t e = cudaMemcpyAsync(h_tot, tot, sizeof(h_tot), cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+    WorkItem *items = nullptr;
+    uint32_t *hm = nullptr;
+    if ((e = cudaMallocAsync((void **)&items, sizeof(WorkItem) * (size_t)imax64(h_tot[0], 1), s)) != cudaSuccess)
+        return e;
+    if ((e = cudaMallocAsync((void **)&hm, sizeof(uint32_t) * 2 * (size_t)imax64(h_tot[1], 1), s)) != cudaSuccess) {
+        cudaFreeAsync(items, s);
+        return e;
+    }
+    cudaMemsetAsync(hm, 0, sizeof(uint32_t) * 2 * (size_t)imax64(h_tot[1], 1), s);
+    k_sched_write<<<grid, 256, 0, s>>>(g.off, g.n, nwin, ci, ch, items);
+    *n_items_out = h_tot[0];
+    *n_heavy_out = h_tot[1];
+    *items_out = items;
+    *heavy_mem_out = hm;
+    return cudaGetLastError();
+}
+
+// ============================================================ reductions
+
+__global__ void k_max_i64(const int64_t *__restrict__ src, int64_t n, unsigned long long *dst, int *neg)
+{
+    unsigned long long mx = 0;
+    int ng = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t x = src[i];
+        if (x < 0) ng = 1; else mx = max(mx, (unsigned long long)x);
+    }
+    #pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(kFull, mx, o));
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(dst, mx);
+        if (ng) atomicExch(neg, 1);
+    }
+}
+
+cudaError_t launch_max_u64_of_i64(const int64_t *src, int64_t n, unsigned long long *dst,
+                                  int *neg_flag, cudaStream_t s)
+{
+    int grid = (int)imin64((n + 255) / 256, 152 * 8);
+    if (grid < 1) grid = 1;
+    k_max_i64<<<grid, 256, 0, s>>>(src, n, dst, neg_flag);
+    return cudaGetLastError();
+}
+
+__global__ void k_degree_max(const int64_t *__restrict__ off, int64_t n, unsigned long long *dst)
+{
+    unsigned long long mx = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        mx = max(mx, (unsigned long long)(off[i + 1] - off[i]));
+    #pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(kFull, mx, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(dst, mx);
+}
+
+cudaError_t launch_degree_max(const int64_t *off, int64_t n, unsigned long long *dst, cudaStream_t s)
+{
+    int grid = (int)imin64((n + 255) / 256, 152 * 8);
+    if (grid < 1) grid = 1;
+    k_degree_max<<<grid, 256, 0, s>>>(off, n, dst);
+    return cudaGetLastError();
+}
+
+}  // namespace dsg

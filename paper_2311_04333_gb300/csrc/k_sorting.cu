@@ -1,0 +1,851 @@
+// k_sorting.cu -- kernels of one PaRSorting++ iteration (arXiv 2311.04333,
+// Sec. 3.2 GreedySorting++ and Sec. 3.3 ParallelGreedySorting++ with the
+// density and load computation of Alg. 3), plus the once-per-run kernels.
+//
+// Iteration t, given loads l_t (uint32, by vertex id):
+//   plan       : digit layout of (l_t - min l_t) from the min/max reduced by
+//                the previous iteration; resets counters.
+//   edge scan  : A[u] = #{w in N(u) : (l_t[w], w) > (l_t[u], u)}, the number
+//                of neighbours of u later in the (load, id) order.  Because
+//                this comparison does not depend on the sorted positions it
+//                runs before the sort (Alg. 3 lines 2-3 without ranks).
+//                Also builds the digit histograms of the sort and the
+//                per-digit sums of A used by the fused scan.
+//   radix pass : stable LSD onesweep passes over (key = l_t, value = A) with
+//                decoupled look-back; pass 0 also writes l_{t+1} = l_t + A
+//                (Alg. 3 lines 8-9).  The LAST pass does not scatter: it
+//                obtains every element's final position i and its prefix sum
+//                of A from the look-back, so the suffix (n - i vertices,
+//                m - prefix edges) of Alg. 3 lines 4-7 is evaluated in place
+//                and reduced to the iteration's first densest suffix.
+//   snapshot   : when the iteration beat the best, keeps l_t for the set.
+#include "common.cuh"
+
+namespace dsg {
+
+// ============================================================ init / plan
+
+__global__ void k_init_ctl(Control *ctl, int64_t m, int64_t n)
+{
+    ctl->best_e = m;
+    ctl->best_v = n;
+    ctl->best_pos = 0;
+    ctl->best_key = 0;
+    ctl->best_iter = 0;
+    ctl->improved = 0;
+    ctl->err = 0;
+    ctl->err_where = 0;
+    ctl->mm_min[1] = 0xffffffffu;
+    ctl->mm_max[1] = 0;
+    ctl->done_ctr = 0;
+}
+
+__global__ void k_init_loads(uint32_t *loads, const int64_t *init, int64_t n, Control *ctl)
+{
+    uint32_t mn = 0xffffffffu, mx = 0;
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t l = init ? (uint32_t)init[v] : 0u;
+        loads[v] = l;
+        mn = min(mn, l);
+        mx = max(mx, l);
+    }
+    #pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        mn = min(mn, __shfl_xor_sync(kFull, mn, o));
+        mx = max(mx, __shfl_xor_sync(kFull, mx, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMin(&ctl->mm_min[1], mn);
+        atomicMax(&ctl->mm_max[1], mx);
+    }
+}
+
+__global__ void k_plan(Control *ctl, int t)
+{
+    const int tid = threadIdx.x;
+    const uint32_t lmin = ctl->mm_min[t & 1], lmax = ctl->mm_max[t & 1];
+    const uint32_t range = lmax - lmin;
+    const int bits = range ? 32 - __clz(range) : 0;
+    const int np = bits ? (bits + kRadixBits - 1) / kRadixBits : 1;
+    for (int i = tid; i < kMaxPasses * kBuckets; i += blockDim.x) (&ctl->hist[0][0])[i] = 0;
+    for (int i = tid; i < kBuckets; i += blockDim.x) ctl->asum[i] = 0;
+    if (tid == 0) {
+        ctl->lmin = lmin;
+        ctl->npass = np;
+        for (int p = 0; p < kMaxPasses; ++p) ctl->shift[p] = p * kRadixBits;
+        ctl->item_ctr = 0;
+        for (int p = 0; p < kMaxPasses; ++p) ctl->tile_ctr[p] = 0;
+        ctl->done_ctr = 0;
+        ctl->width = 0;
+        ctl->improved = 0;
+        ctl->mm_min[(t + 1) & 1] = 0xffffffffu;
+        ctl->mm_max[(t + 1) & 1] = 0;
+        ctl->epoch += kMaxPasses;
+    }
+}
+
+cudaError_t launch_init(const GraphDev &g, RunBufs &b, const int64_t *init_dev, int,
+                        cudaStream_t s)
+{
+    k_init_ctl<<<1, 1, 0, s>>>(b.ctl, g.arcs / 2, g.n);
+    int grid = (int)imin64((g.n + 255) / 256, 4096);
+    k_init_loads<<<grid, 256, 0, s>>>(b.loads, init_dev, g.n, b.ctl);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_plan(const GraphDev &, RunBufs &b, int t, cudaStream_t s)
+{
+    k_plan<<<1, 256, 0, s>>>(b.ctl, t);
+    return cudaGetLastError();
+}
+
+// ============================================================ edge scan
+
+constexpr int kEsThreads = 256;
+constexpr int kEsArcs = 8;                       // arcs per thread per round
+constexpr int kEsRound = kEsThreads * kEsArcs;   // arcs per round
+
+struct EsSmem {
+    int32_t off[kTileV + 1];
+    uint32_t l[kTileV];
+    uint32_t cnt[kTileV];
+    uint16_t src[2 * kWin];
+    uint32_t hist[kMaxPasses][kBuckets];
+    unsigned long long asum[kBuckets];
+    uint32_t scan[kEsThreads / 32];
+    uint32_t item;
+    uint32_t red[kEsThreads / 32];
+};
+
+// per-thread run-length accumulation of the digit histograms
+struct HistAcc {
+    uint32_t b[kMaxPasses], c[kMaxPasses];
+    uint32_t sb;
+    unsigned long long ss;
+};
+
+__device__ __forceinline__ void hist_add(HistAcc &h, EsSmem &S, uint32_t key, uint32_t a,
+                                         uint32_t lmin, int np)
+{
+    const uint32_t x = key - lmin;
+    #pragma unroll
+    for (int p = 0; p < kMaxPasses; ++p) {
+        if (p < np) {
+            uint32_t d = (x >> (p * kRadixBits)) & (kBuckets - 1);
+            if (d != h.b[p]) {
+                if (h.c[p]) atomicAdd(&S.hist[p][h.b[p]], h.c[p]);
+                h.b[p] = d;
+                h.c[p] = 0;
+            }
+            h.c[p] += 1;
+        }
+    }
+    uint32_t dl = (x >> ((np - 1) * kRadixBits)) & (kBuckets - 1);
+    if (dl != h.sb) {
+        if (h.ss) atomicAdd(&S.asum[h.sb], h.ss);
+        h.sb = dl;
+        h.ss = 0;
+    }
+    h.ss += a;
+}
+
+__device__ __forceinline__ void hist_flush(HistAcc &h, EsSmem &S, int np)
+{
+    #pragma unroll
+    for (int p = 0; p < kMaxPasses; ++p)
+        if (p < np && h.c[p]) atomicAdd(&S.hist[p][h.b[p]], h.c[p]);
+    if (h.ss) atomicAdd(&S.asum[h.sb], h.ss);
+}
+
+// fill-forward of the source marks: s[j] = max(s[0..j]) over na slots
+__device__ __forceinline__ void block_fill_forward(uint16_t *s, int na, EsSmem &S)
+{
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int per = (na + kEsThreads - 1) / kEsThreads;
+    const int b = tid * per, e = min(b + per, na);
+    uint32_t run = 0;
+    for (int j = b; j < e; ++j) run = max(run, (uint32_t)s[j]);
+    uint32_t inc = run;
+    #pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(kFull, inc, o);
+        if (lane >= o) inc = max(inc, y);
+    }
+    if (lane == 31) S.scan[w] = inc;
+    __syncthreads();
+    uint32_t pre = 0;
+    for (int i = 0; i < w; ++i) pre = max(pre, S.scan[i]);
+    uint32_t ex = __shfl_up_sync(kFull, inc, 1);
+    if (lane == 0) ex = 0;
+    uint32_t cur = max(pre, ex);
+    for (int j = b; j < e; ++j) {
+        cur = max(cur, (uint32_t)s[j]);
+        s[j] = (uint16_t)cur;
+    }
+}
+
+__global__ void __launch_bounds__(kEsThreads)
+k_edge_scan(const int64_t *__restrict__ off, const int32_t *__restrict__ adj,
+            const WorkItem *__restrict__ items, int64_t n_items,
+            const uint32_t *__restrict__ loads, uint32_t *__restrict__ A,
+            uint32_t *heavy_acc, uint32_t *heavy_done, Control *ctl)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    EsSmem &S = *reinterpret_cast<EsSmem *>(smem_raw);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t lmin = ctl->lmin;
+    const int np = ctl->npass;
+
+    for (int i = tid; i < kMaxPasses * kBuckets; i += kEsThreads) (&S.hist[0][0])[i] = 0;
+    for (int i = tid; i < kBuckets; i += kEsThreads) S.asum[i] = 0;
+    HistAcc h;
+    #pragma unroll
+    for (int p = 0; p < kMaxPasses; ++p) { h.b[p] = 0; h.c[p] = 0; }
+    h.sb = 0;
+    h.ss = 0;
+    uint32_t width = 0;
+    __syncthreads();
+
+    for (;;) {
+        if (tid == 0) S.item = atomicAdd(&ctl->item_ctr, 1u);
+        __syncthreads();
+        const uint32_t it_idx = S.item;
+        if (it_idx >= n_items) break;
+        const WorkItem it = items[it_idx];
+
+        if (it.info & kHeavyBit) {
+            // ---- one chunk of kWin arcs of a heavy vertex (block per chunk)
+            const uint32_t u = it.u, hidx = it.info & ~kHeavyBit;
+            const int64_t s0 = off[u], s1 = off[u + 1];
+            const int64_t a0 = it.a0, a1 = min(a0 + (int64_t)kWin, s1);
+            const uint32_t lu = loads[u];
+            uint32_t c = 0;
+            #pragma unroll 4
+            for (int64_t j = a0 + tid; j < a1; j += kEsThreads) {
+                const uint32_t w = (uint32_t)__ldg(adj + j);
+                const uint32_t lw = __ldg(loads + w);
+                c += (lw > lu) || (lw == lu && w > u);
+            }
+            c = __reduce_add_sync(kFull, c);
+            if (lane == 0) S.red[warp] = c;
+            __syncthreads();
+            if (tid == 0) {
+                uint32_t tot = 0;
+                for (int i = 0; i < kEsThreads / 32; ++i) tot += S.red[i];
+                atomicAdd(&heavy_acc[hidx], tot);
+                __threadfence();
+                const uint32_t nch = (uint32_t)((s1 - s0 + kWin - 1) / kWin);
+                if (atomicAdd(&heavy_done[hidx], 1u) == nch - 1) {
+                    __threadfence();
+                    const uint32_t total = atomicExch(&heavy_acc[hidx], 0u);
+                    heavy_done[hidx] = 0;
+                    A[u] = total;
+                    width = max(width, total);
+                    hist_add(h, S, lu, total, lmin, np);
+                }
+            }
+            __syncthreads();
+            continue;
+        }
+
+        // ---- light tile: consecutive vertices u0 .. u0+nv-1, arcs contiguous
+        const uint32_t u0 = it.u, nv = it.info;
+        const int64_t a0 = it.a0;
+        for (uint32_t i = tid; i <= nv; i += kEsThreads) S.off[i] = (int32_t)(off[u0 + i] - a0);
+        for (uint32_t i = tid; i < nv; i += kEsThreads) {
+            S.l[i] = loads[u0 + i];
+            S.cnt[i] = 0;
+        }
+        __syncthreads();
+        const int na = S.off[nv];
+        for (int j = tid; j < na; j += kEsThreads) S.src[j] = 0;
+        __syncthreads();
+        for (uint32_t i = tid; i < nv; i += kEsThreads)
+            if (S.off[i + 1] > S.off[i]) S.src[S.off[i]] = (uint16_t)i;
+        __syncthreads();
+        block_fill_forward(S.src, na, S);
+        __syncthreads();
+
+        for (int base = 0; base < na; base += kEsRound) {
+            const int wb = base + warp * (32 * kEsArcs);
+            int32_t wv[kEsArcs];
+            uint32_t lw[kEsArcs];
+            #pragma unroll
+            for (int k = 0; k < kEsArcs; ++k) {
+                const int j = wb + k * 32 + lane;
+                wv[k] = (j < na) ? __ldg(adj + a0 + j) : 0;
+            }
+            #pragma unroll
+            for (int k = 0; k < kEsArcs; ++k) {
+                const int j = wb + k * 32 + lane;
+                lw[k] = (j < na) ? __ldg(loads + wv[k]) : 0u;
+            }
+            #pragma unroll
+            for (int k = 0; k < kEsArcs; ++k) {
+                const int j = wb + k * 32 + lane;
+                const bool valid = j < na;
+                const uint32_t src = valid ? S.src[j] : 0xffffu;
+                const uint32_t prev = __shfl_up_sync(kFull, src, 1);
+                const bool head = valid && (lane == 0 || prev != src);
+                bool cmp = false;
+                if (valid) {
+                    const uint32_t lu = S.l[src];
+                    const uint32_t w = (uint32_t)wv[k];
+                    cmp = (lw[k] > lu) || (lw[k] == lu && w > u0 + src);
+                }
+                const uint32_t H = __ballot_sync(kFull, head);
+                const uint32_t C = __ballot_sync(kFull, cmp);
+                if (head) {
+                    const uint32_t above = H & ~((2u << lane) - 1u);
+                    const int nxt = above ? (__ffs(above) - 1) : 32;
+                    const uint32_t seg = (nxt == 32 ? kFull : ((1u << nxt) - 1u)) & ~((1u << lane) - 1u);
+                    const uint32_t c = __popc(C & seg);
+                    if (c) atomicAdd(&S.cnt[src], c);
+                }
+            }
+        }
+        __syncthreads();
+        for (uint32_t i = tid; i < nv; i += kEsThreads) {
+            const uint32_t c = S.cnt[i];
+            A[u0 + i] = c;
+            width = max(width, c);
+            hist_add(h, S, S.l[i], c, lmin, np);
+        }
+        __syncthreads();
+    }
+
+    hist_flush(h, S, np);
+    width = __reduce_max_sync(kFull, width);
+    if (lane == 0 && width) atomicMax(&ctl->width, width);
+    __syncthreads();
+    for (int i = tid; i < kBuckets; i += kEsThreads) {
+        for (int p = 0; p < np; ++p)
+            if (S.hist[p][i]) atomicAdd(&ctl->hist[p][i], S.hist[p][i]);
+        if (S.asum[i]) atomicAdd(&ctl->asum[i], S.asum[i]);
+    }
+}
+
+static int g_es_blocks_per_sm = -1;
+
+int edge_scan_sm_count()
+{
+    if (g_es_blocks_per_sm < 0) {
+        cudaFuncSetAttribute(k_edge_scan, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sizeof(EsSmem));
+        int nb = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_edge_scan, kEsThreads, sizeof(EsSmem));
+        g_es_blocks_per_sm = nb > 0 ? nb : 1;
+    }
+    return g_es_blocks_per_sm;
+}
+
+cudaError_t launch_edge_scan(const GraphDev &g, RunBufs &b, int grid, cudaStream_t s)
+{
+    edge_scan_sm_count();
+    k_edge_scan<<<grid, kEsThreads, sizeof(EsSmem), s>>>(g.off, g.adj, g.items, g.n_items,
+                                                         b.loads, b.A, g.heavy_acc,
+                                                         g.heavy_done, b.ctl);
+    return cudaGetLastError();
+}
+
+// ============================================================ radix passes
+
+struct PassSmem {
+    uint32_t keys[kPassTile];
+    uint32_t vals[kPassTile];
+    uint32_t wcnt[kPassThreads / 32][kBuckets];
+    uint32_t toff[kBuckets + 1];
+    uint32_t boff[kBuckets];
+    uint32_t gbase[kBuckets];
+    unsigned long long aoff[kBuckets];
+    unsigned long long gsum[kBuckets];
+    unsigned long long dscan[kBuckets];
+    unsigned long long dend[kBuckets];
+    unsigned long long red[33];
+    Candidate cred[32];
+    uint32_t tile;
+    uint32_t last_block;
+    uint32_t mn[kPassThreads / 32], mx[kPassThreads / 32];
+};
+
+__device__ __forceinline__ unsigned long long status_word(uint32_t epoch, uint64_t flag, uint64_t cnt)
+{
+    return ((unsigned long long)epoch << 48) | (flag << 46) | (cnt & ((1ull << 46) - 1));
+}
+
+__global__ void __launch_bounds__(kPassThreads)
+k_radix_pass(const uint32_t *kin, const uint32_t *vin,
+             uint32_t *__restrict__ kout, uint32_t *__restrict__ vout,
+             uint32_t *loads_next, unsigned long long *status, unsigned long long *status_sum,
+             Candidate *cand, int64_t ntiles, int64_t n, int64_t m, Control *ctl, int k, int t,
+             int64_t *trace)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    PassSmem &S = *reinterpret_cast<PassSmem *>(smem_raw);
+    const int np = ctl->npass;
+    if (k >= np) return;
+    const bool last = (k == np - 1);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t lmin = ctl->lmin;
+    const int shift = ctl->shift[k];
+    const uint32_t epoch = (uint32_t)(((ctl->epoch + (uint32_t)k) % 65535u) + 1u);
+
+    if (tid == 0) {
+        S.tile = atomicAdd(&ctl->tile_ctr[k], 1u);
+        S.last_block = 0;
+    }
+    // global bucket offsets of this pass's digit (exclusive scan of the histogram)
+    {
+        const uint32_t hcount = ctl->hist[k][tid];
+        uint64_t tot;
+        const uint64_t ex = block_excl_sum_u64(hcount, S.red, &tot);
+        S.boff[tid] = (uint32_t)ex;
+        if (last) {
+            const unsigned long long as = ctl->asum[tid];
+            const uint64_t exs = block_excl_sum_u64(as, S.red, &tot);
+            S.aoff[tid] = exs;
+        }
+    }
+    for (int i = tid; i < (kPassThreads / 32) * kBuckets; i += kPassThreads) (&S.wcnt[0][0])[i] = 0;
+    __syncthreads();
+    const uint32_t tile = S.tile;
+    const int64_t tbase = (int64_t)tile * kPassTile;
+
+    // ---- load 16 rounds of 32 consecutive items per warp; warp-level stable ranks
+    uint32_t key_r[kPassIpt], val_r[kPassIpt], dw_r[kPassIpt];
+    uint32_t lmn = 0xffffffffu, lmx = 0;
+    const int64_t wbase = tbase + warp * (32 * kPassIpt);
+    #pragma unroll
+    for (int r = 0; r < kPassIpt; ++r) {
+        const int64_t idx = wbase + r * 32 + lane;
+        const bool valid = idx < n;
+        uint32_t key = 0, val = 0;
+        if (valid) {
+            key = kin[idx];
+            val = vin[idx];
+            if (k == 0 && loads_next) {
+                const uint32_t nl = key + val;
+                loads_next[idx] = nl;
+                lmn = min(lmn, nl);
+                lmx = max(lmx, nl);
+            }
+        }
+        const uint32_t d = ((key - lmin) >> shift) & (kBuckets - 1);
+        uint32_t peers = __ballot_sync(kFull, valid);
+        #pragma unroll
+        for (int bit = 0; bit < kRadixBits; ++bit) {
+            const uint32_t bb = __ballot_sync(kFull, (d >> bit) & 1u);
+            peers &= ((d >> bit) & 1u) ? bb : ~bb;
+        }
+        const uint32_t rank = __popc(peers & lanemask_lt());
+        uint32_t before = 0;
+        if (valid) before = S.wcnt[warp][d];
+        __syncwarp();
+        if (valid && (peers >> lane) == 1u) S.wcnt[warp][d] = before + __popc(peers);
+        __syncwarp();
+        key_r[r] = key;
+        val_r[r] = val;
+        dw_r[r] = valid ? (d | ((before + rank) << 8)) : 0xffffffffu;
+    }
+    if (k == 0 && loads_next) {
+        lmn = __reduce_min_sync(kFull, lmn);
+        lmx = __reduce_max_sync(kFull, lmx);
+        if (lane == 0) { S.mn[warp] = lmn; S.mx[warp] = lmx; }
+    }
+    __syncthreads();
+    if (k == 0 && loads_next && tid == 0) {
+        uint32_t a = 0xffffffffu, b = 0;
+        for (int i = 0; i < kPassThreads / 32; ++i) { a = min(a, S.mn[i]); b = max(b, S.mx[i]); }
+        if (b >= a || a != 0xffffffffu) {
+            atomicMin(&ctl->mm_min[(t + 1) & 1], a);
+            atomicMax(&ctl->mm_max[(t + 1) & 1], b);
+        }
+    }
+    // per-digit tile counts, exclusive per-warp prefixes, tile-local digit offsets
+    uint32_t tcount;
+    {
+        const int d = tid;
+        uint32_t sum = 0;
+        #pragma unroll
+        for (int w = 0; w < kPassThreads / 32; ++w) {
+            const uint32_t c = S.wcnt[w][d];
+            S.wcnt[w][d] = sum;
+            sum += c;
+        }
+        tcount = sum;
+        uint64_t tot;
+        const uint64_t ex = block_excl_sum_u64(sum, S.red, &tot);
+        S.toff[d] = (uint32_t)ex;
+        if (d == 0) S.toff[kBuckets] = (uint32_t)tot;
+    }
+    __syncthreads();
+    // local stable sort of the tile into shared memory
+    #pragma unroll
+    for (int r = 0; r < kPassIpt; ++r) {
+        if (dw_r[r] != 0xffffffffu) {
+            const uint32_t d = dw_r[r] & 0xffu, wr = dw_r[r] >> 8;
+            const uint32_t lp = S.toff[d] + S.wcnt[warp][d] + wr;
+            S.keys[lp] = key_r[r];
+            S.vals[lp] = val_r[r];
+        }
+    }
+    __syncthreads();
+    const uint32_t tn = S.toff[kBuckets];
+
+    // last pass: inclusive scan of A over the locally sorted tile
+    uint64_t scan_r[kPassIpt];
+    if (last) {
+        uint64_t run = 0;
+        #pragma unroll
+        for (int i = 0; i < kPassIpt; ++i) {
+            const uint32_t lp = tid * kPassIpt + i;
+            const uint64_t v = lp < tn ? S.vals[lp] : 0;
+            scan_r[i] = run;          // exclusive within thread
+            run += v;
+        }
+        uint64_t tot;
+        const uint64_t ex = block_excl_sum_u64(run, S.red, &tot);
+        #pragma unroll
+        for (int i = 0; i < kPassIpt; ++i) {
+            const uint32_t lp = tid * kPassIpt + i;
+            scan_r[i] += ex;          // exclusive prefix over the sorted tile
+            if (lp < tn) {
+                const uint32_t d = ((S.keys[lp] - lmin) >> shift) & (kBuckets - 1);
+                if (lp == S.toff[d]) S.dscan[d] = scan_r[i];
+                if (lp + 1 == S.toff[d + 1] || lp + 1 == tn) S.dend[d] = scan_r[i] + S.vals[lp];
+            }
+        }
+        __syncthreads();
+    }
+
+    // ---- decoupled look-back: thread d resolves digit d
+    {
+        const int d = tid;
+        const uint64_t tsum = (last && tcount) ? (uint64_t)(S.dend[d] - S.dscan[d]) : 0ull;
+        unsigned long long *st = status + (int64_t)tile * kBuckets + d;
+        unsigned long long *ss = status_sum + 2 * ((int64_t)tile * kBuckets + d);
+        uint64_t excl = 0, excl_sum = 0;
+        bool abort = false;
+        if (tile > 0) {
+            if (last) st_relaxed(ss, tsum);
+            st_release(st, status_word(epoch, kFlagAgg, tcount));
+            int64_t j = (int64_t)tile - 1;
+            uint32_t polls = 0, ns = 8;
+            while (j >= 0) {
+                const unsigned long long w = ld_acquire(status + j * kBuckets + d);
+                const uint32_t ep = (uint32_t)(w >> 48);
+                const uint32_t fl = (uint32_t)((w >> 46) & 3u);
+                if (ep != epoch || fl == 0) {
+                    if (++polls > kSpinLimit) { abort = true; set_error(ctl, 5, 100 + k); break; }
+                    __nanosleep(ns);
+                    if (ns < 256) ns <<= 1;
+                    continue;
+                }
+                if (fl == kFlagAbort) { abort = true; break; }
+                excl += w & ((1ull << 46) - 1);
+                if (last) excl_sum += ld_relaxed(status_sum + 2 * (j * kBuckets + d) + (fl == kFlagIncl ? 1 : 0));
+                if (fl == kFlagIncl) break;
+                --j;
+            }
+        }
+        if (abort) {
+            st_release(st, status_word(epoch, kFlagAbort, 0));
+        } else {
+            if (last) st_relaxed(ss + 1, excl_sum + tsum);
+            st_release(st, status_word(epoch, kFlagIncl, excl + tcount));
+        }
+        S.gbase[d] = S.boff[d] + (uint32_t)excl;
+        if (last) S.gsum[d] = S.aoff[d] + excl_sum;
+        if (abort) S.last_block = 0xdeadu;
+    }
+    __syncthreads();
+    if (S.last_block == 0xdeadu) return;
+
+    if (!last) {
+        // scatter the locally sorted tile: consecutive threads write consecutive
+        // positions of a bucket
+        #pragma unroll 4
+        for (int r = 0; r < kPassIpt; ++r) {
+            const uint32_t lp = r * kPassThreads + tid;
+            if (lp < tn) {
+                const uint32_t key = S.keys[lp];
+                const uint32_t d = ((key - lmin) >> shift) & (kBuckets - 1);
+                const uint32_t gp = S.gbase[d] + (lp - S.toff[d]);
+                if (gp < (uint64_t)n) {
+                    kout[gp] = key;
+                    vout[gp] = S.vals[lp];
+                } else {
+                    set_error(ctl, 3, 300 + k);
+                }
+            }
+        }
+        return;
+    }
+
+    // ---- final pass: evaluate every suffix (Alg. 3 lines 4-7) without scattering
+    Candidate best{0, 0, 0, 0};
+    #pragma unroll
+    for (int i = 0; i < kPassIpt; ++i) {
+        const uint32_t lp = tid * kPassIpt + i;
+        if (lp < tn) {
+            const uint32_t key = S.keys[lp];
+            const uint32_t d = ((key - lmin) >> shift) & (kBuckets - 1);
+            const int64_t pos = (int64_t)S.gbase[d] + (lp - S.toff[d]);
+            const uint64_t prefix = S.gsum[d] + (scan_r[i] - S.dscan[d]);
+            Candidate c{(int64_t)((uint64_t)m - prefix), n - pos, pos, (int64_t)key};
+            if (cand_better(c, best)) best = c;
+        }
+    }
+    best = block_best(best, S.cred);
+    if (tid == 0) {
+        cand[tile] = best;
+        __threadfence();
+        S.last_block = (atomicAdd(&ctl->done_ctr, 1u) == (uint32_t)(ntiles - 1)) ? 1u : 0u;
+    }
+    __syncthreads();
+    if (!S.last_block) return;
+    __threadfence();
+    Candidate b2{0, 0, 0, 0};
+    for (int64_t i = tid; i < ntiles; i += kPassThreads) {
+        Candidate c;
+        c.e = __ldcg(&cand[i].e);
+        c.v = __ldcg(&cand[i].v);
+        c.pos = __ldcg(&cand[i].pos);
+        c.key = __ldcg(&cand[i].key);
+        if (cand_better(c, b2)) b2 = c;
+    }
+    b2 = block_best(b2, S.cred);
+    if (tid == 0) {
+        if (trace) {
+            trace[3 * (t - 1) + 0] = b2.e;
+            trace[3 * (t - 1) + 1] = b2.v;
+            trace[3 * (t - 1) + 2] = (int64_t)ctl->width;
+        }
+        if (b2.v > 0 && dens_gt((uint64_t)b2.e, (uint64_t)b2.v, (uint64_t)ctl->best_e,
+                                (uint64_t)ctl->best_v)) {
+            ctl->best_e = b2.e;
+            ctl->best_v = b2.v;
+            ctl->best_pos = b2.pos;
+            ctl->best_key = b2.key;
+            ctl->best_iter = t;
+            ctl->improved = 1;
+        } else {
+            ctl->improved = 0;
+        }
+    }
+}
+
+static bool g_pass_attr = false;
+
+cudaError_t launch_radix_pass(const GraphDev &g, RunBufs &b, int k, int t, cudaStream_t s,
+                              const uint32_t *key0, bool update_loads)
+{
+    if (!g_pass_attr) {
+        cudaFuncSetAttribute(k_radix_pass, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sizeof(PassSmem));
+        g_pass_attr = true;
+    }
+    // pass k reads: k == 0 -> (loads, A) by id; else buffer (k-1)&1; writes buffer k&1
+    const uint32_t *kin = k == 0 ? (key0 ? key0 : b.loads) : b.keys[(k - 1) & 1];
+    const uint32_t *vin = k == 0 ? b.A : b.vals[(k - 1) & 1];
+    k_radix_pass<<<(unsigned)b.ntiles, kPassThreads, sizeof(PassSmem), s>>>(
+        kin, vin, b.keys[k & 1], b.vals[k & 1], update_loads ? b.loads : nullptr, b.status,
+        b.status_sum, b.cand,
+        b.ntiles, g.n, g.arcs / 2, b.ctl, k, t, b.trace);
+    return cudaGetLastError();
+}
+
+// ============================================================ snapshot
+
+__global__ void k_snapshot(const uint32_t *__restrict__ loads, const uint32_t *__restrict__ A,
+                           uint32_t *__restrict__ best_loads, int64_t n, const Control *ctl)
+{
+    if (!ctl->improved) return;
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x)
+        best_loads[v] = loads[v] - A[v];
+}
+
+cudaError_t launch_snapshot(const GraphDev &g, RunBufs &b, cudaStream_t s)
+{
+    int grid = (int)imin64((g.n + 255) / 256, 152 * 8);
+    k_snapshot<<<grid, 256, 0, s>>>(b.loads, b.A, b.best_loads, g.n, b.ctl);
+    return cudaGetLastError();
+}
+
+// ============================================================ best set (once per run)
+// S = the last best_v vertices of the (L, id) order of the best iteration,
+// L = its starting loads: {v : L(v) > key*} plus the equal-load vertices from
+// the (pos* - #{L < key*})-th smallest id on.
+
+constexpr int kBsBlock = 4096;   // ids per block
+constexpr int kBsThreads = 256;
+
+__global__ void k_bs_count(const uint32_t *__restrict__ L, int64_t n, Control *ctl, int64_t *cnt_eq)
+{
+    if (ctl->best_iter == 0) return;
+    const uint32_t key = (uint32_t)ctl->best_key;
+    const int64_t b0 = (int64_t)blockIdx.x * kBsBlock;
+    uint32_t eq = 0, lt = 0;
+    for (int i = threadIdx.x; i < kBsBlock; i += kBsThreads) {
+        const int64_t v = b0 + i;
+        if (v < n) {
+            const uint32_t l = L[v];
+            eq += l == key;
+            lt += l < key;
+        }
+    }
+    eq = __reduce_add_sync(kFull, eq);
+    lt = __reduce_add_sync(kFull, lt);
+    __shared__ uint32_t se[kBsThreads / 32], sl[kBsThreads / 32];
+    if ((threadIdx.x & 31) == 0) { se[threadIdx.x >> 5] = eq; sl[threadIdx.x >> 5] = lt; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t a = 0, b = 0;
+        for (int i = 0; i < kBsThreads / 32; ++i) { a += se[i]; b += sl[i]; }
+        cnt_eq[blockIdx.x] = a;
+        atomicAdd((unsigned long long *)&ctl->cnt_less, (unsigned long long)b);
+    }
+}
+
+// single block: find the block and id of the r-th equal-load vertex
+__global__ void k_bs_select(const uint32_t *__restrict__ L, int64_t n, Control *ctl,
+                            const int64_t *cnt_eq, int64_t nblk)
+{
+    if (ctl->best_iter == 0) return;
+    __shared__ unsigned long long red[33];
+    __shared__ int64_t s_blk, s_base;
+    const uint32_t key = (uint32_t)ctl->best_key;
+    const int64_t r = ctl->best_pos - ctl->cnt_less;
+    if (threadIdx.x == 0) { s_blk = -1; s_base = 0; }
+    // scan the block counts in chunks of blockDim.x
+    int64_t carry = 0;
+    for (int64_t c0 = 0; c0 < nblk; c0 += blockDim.x) {
+        const int64_t i = c0 + threadIdx.x;
+        const uint64_t x = i < nblk ? (uint64_t)cnt_eq[i] : 0;
+        uint64_t tot;
+        const uint64_t ex = block_excl_sum_u64(x, red, &tot);
+        const int64_t lo = carry + (int64_t)ex, hi = lo + (int64_t)x;
+        if (i < nblk && r >= lo && r < hi) { s_blk = i; s_base = lo; }
+        carry += (int64_t)tot;
+        __syncthreads();
+    }
+    __syncthreads();
+    const int64_t blk = s_blk;
+    if (blk < 0) { if (threadIdx.x == 0) set_error(ctl, 3, 200); return; }
+    // within block blk: ordered scan over ids
+    int64_t seen = s_base;
+    const int64_t b0 = blk * kBsBlock;
+    for (int c0 = 0; c0 < kBsBlock; c0 += blockDim.x) {
+        const int64_t v = b0 + c0 + threadIdx.x;
+        const uint64_t x = (v < n && L[v] == key) ? 1 : 0;
+        uint64_t tot;
+        const uint64_t ex = block_excl_sum_u64(x, red, &tot);
+        if (x && seen + (int64_t)ex == r) ctl->thr_id = v;
+        seen += (int64_t)tot;
+        __syncthreads();
+    }
+}
+
+__device__ __forceinline__ bool bs_member(uint32_t l, int64_t v, uint32_t key, int64_t thr)
+{
+    return l > key || (l == key && v >= thr);
+}
+
+__global__ void k_bs_flagcount(const uint32_t *__restrict__ L, int64_t n, const Control *ctl,
+                               int64_t *cnt)
+{
+    const bool all = ctl->best_iter == 0;
+    const uint32_t key = (uint32_t)ctl->best_key;
+    const int64_t thr = ctl->thr_id;
+    const int64_t b0 = (int64_t)blockIdx.x * kBsBlock;
+    uint32_t c = 0;
+    for (int i = threadIdx.x; i < kBsBlock; i += kBsThreads) {
+        const int64_t v = b0 + i;
+        if (v < n) c += all || bs_member(L[v], v, key, thr);
+    }
+    c = __reduce_add_sync(kFull, c);
+    __shared__ uint32_t s[kBsThreads / 32];
+    if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t a = 0;
+        for (int i = 0; i < kBsThreads / 32; ++i) a += s[i];
+        cnt[blockIdx.x] = a;
+    }
+}
+
+__global__ void k_bs_scan(int64_t *cnt, int64_t nblk, Control *ctl)
+{
+    __shared__ unsigned long long red[33];
+    int64_t carry = 0;
+    for (int64_t c0 = 0; c0 < nblk; c0 += blockDim.x) {
+        const int64_t i = c0 + threadIdx.x;
+        const uint64_t x = i < nblk ? (uint64_t)cnt[i] : 0;
+        uint64_t tot;
+        const uint64_t ex = block_excl_sum_u64(x, red, &tot);
+        if (i < nblk) cnt[i] = carry + (int64_t)ex;
+        carry += (int64_t)tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) ctl->set_size = carry;
+}
+
+__global__ void k_bs_write(const uint32_t *__restrict__ L, int64_t n, const Control *ctl,
+                           const int64_t *offs, int32_t *__restrict__ set)
+{
+    __shared__ unsigned long long red[33];
+    const bool all = ctl->best_iter == 0;
+    const uint32_t key = (uint32_t)ctl->best_key;
+    const int64_t thr = ctl->thr_id;
+    const int64_t b0 = (int64_t)blockIdx.x * kBsBlock;
+    int64_t base = offs[blockIdx.x];
+    for (int c0 = 0; c0 < kBsBlock; c0 += kBsThreads) {
+        const int64_t v = b0 + c0 + threadIdx.x;
+        const uint64_t x = (v < n && (all || bs_member(L[v], v, key, thr))) ? 1 : 0;
+        uint64_t tot;
+        const uint64_t ex = block_excl_sum_u64(x, red, &tot);
+        if (x) set[base + (int64_t)ex] = (int32_t)v;
+        base += (int64_t)tot;
+        __syncthreads();
+    }
+}
+
+__global__ void k_zero_i64(int64_t *p) { *p = 0; }
+
+cudaError_t launch_best_set(const GraphDev &g, RunBufs &b, int32_t *set_dev, cudaStream_t s,
+                            int *launches)
+{
+    const int64_t nblk = (g.n + kBsBlock - 1) / kBsBlock;
+    k_zero_i64<<<1, 1, 0, s>>>(&b.ctl->cnt_less);
+    k_bs_count<<<(unsigned)nblk, kBsThreads, 0, s>>>(b.best_loads, g.n, b.ctl, b.blk_a);
+    k_bs_select<<<1, 1024, 0, s>>>(b.best_loads, g.n, b.ctl, b.blk_a, nblk);
+    k_bs_flagcount<<<(unsigned)nblk, kBsThreads, 0, s>>>(b.best_loads, g.n, b.ctl, b.blk_b);
+    k_bs_scan<<<1, 1024, 0, s>>>(b.blk_b, nblk, b.ctl);
+    int nl = 5;
+    if (set_dev) {
+        k_bs_write<<<(unsigned)nblk, kBsThreads, 0, s>>>(b.best_loads, g.n, b.ctl, b.blk_b, set_dev);
+        ++nl;
+    }
+    if (launches) *launches += nl;
+    return cudaGetLastError();
+}
+
+// ============================================================ outputs
+
+__global__ void k_loads_out(const uint32_t *__restrict__ loads, int64_t *__restrict__ dst, int64_t n)
+{
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x)
+        dst[v] = (int64_t)loads[v];
+}
+
+cudaError_t launch_loads_out(const GraphDev &g, RunBufs &b, int64_t *dst, cudaStream_t s)
+{
+    int grid = (int)imin64((g.n + 255) / 256, 152 * 8);
+    k_loads_out<<<grid, 256, 0, s>>>(b.loads, dst, g.n);
+    return cudaGetLastError();
+}
+
+}  // namespace dsg

@@ -1,0 +1,182 @@
+"""Parity of the CUDA PaRSorting++ path (through the C ABI) with the oracle.
+
+Every comparison is exact: final loads, best (edges, vertices, iteration),
+best vertex set and the per-iteration trace must be identical.
+"""
+import numpy as np
+import pytest
+
+import graphgen as gg
+import oracle as orc
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dsg():
+    import paper_2311_04333_gb300 as m
+    return m
+
+
+@pytest.fixture(scope="module")
+def ctx(dsg):
+    import torch
+    c = dsg.dsg_create(0, torch.cuda.current_stream().cuda_stream)
+    yield c
+    dsg.dsg_destroy(c)
+
+
+def check(dsg, ctx, g, variant=orc.SORTING, T=10, p=1, q=10, init=None):
+    r = dsg.densest(ctx, g.n, g.off, g.adj, variant, T, (p, q), init)
+    o = orc.run(g, variant, T, p, q, init)
+    assert (r.best_edges, r.best_vertices, r.best_iter) == (o.best_edges, o.best_vertices, o.best_iter)
+    bad = np.flatnonzero(r.loads != o.loads)
+    assert bad.size == 0, f"{bad.size} loads differ, first at {bad[:5]}"
+    assert np.array_equal(r.best_set.astype(np.int64), o.best_set)
+    assert np.array_equal(r.trace, o.trace)
+    return r, o
+
+
+def test_planted_clique_config(dsg, ctx):
+    """ER(2000, 0.005) + K_30, T = 10."""
+    g = gg.er_planted_clique()
+    r, _ = check(dsg, ctx, g, T=10)
+    assert (r.best_edges, r.best_vertices) == (435, 30)
+
+
+@pytest.mark.parametrize("n,d,seed", [(20000, 8, 1), (9001, 30, 2), (4096, 5, 3), (4097, 3, 4),
+                                      (50000, 12, 5)])
+def test_random_graphs_several_tiles(dsg, ctx, n, d, seed):
+    check(dsg, ctx, gg.er_m(n, d, seed), T=7)
+
+
+def test_power_law(dsg, ctx):
+    check(dsg, ctx, gg.chung_lu(30000, 16, 2.1, 7), T=12)
+
+
+def test_heavy_vertices(dsg, ctx):
+    """Stars of degree > 4096 are processed as heavy chunks."""
+    big = gg.star(10000)
+    g = gg.disjoint_union(gg.er_m(3000, 10, 9), big, gg.complete(40), gg.star(4096), gg.star(4097))
+    check(dsg, ctx, g, T=6)
+
+
+def test_rmat_small(dsg, ctx):
+    check(dsg, ctx, gg.rmat(16, 16, 11), T=10)
+
+
+def test_complete_graph_closed_form(dsg, ctx):
+    n = 300
+    g = gg.complete(n)
+    for T in (1, 2, 5):
+        r, _ = check(dsg, ctx, g, T=T)
+        k = np.arange(n)
+        exp = ((T - 1) // 2) * (n - 1) + (n - 1 - k) if T % 2 else np.full(n, (T // 2) * (n - 1))
+        assert np.array_equal(r.loads, exp)
+        assert (r.best_edges, r.best_vertices, r.best_iter) == (n * (n - 1) // 2, n, 0)
+
+
+def test_single_vertex_and_isolated(dsg, ctx):
+    check(dsg, ctx, gg.from_edges(1, []), T=3)
+    check(dsg, ctx, gg.from_edges(7, []), T=2)
+    # zero-degree vertices interleaved with edges, ragged tail
+    g = gg.from_edges(9000, [(i, i + 3) for i in range(0, 8990, 7)])
+    check(dsg, ctx, g, T=5)
+
+
+def test_many_ties_and_large_loads(dsg, ctx):
+    g = gg.er_m(12000, 10, 21)
+    rng = np.random.default_rng(0)
+    init = rng.integers(0, 4, size=g.n).astype(np.int64)          # many ties
+    check(dsg, ctx, g, T=4, init=init)
+    init = rng.integers(0, 2**31, size=g.n).astype(np.int64)      # four radix passes
+    check(dsg, ctx, g, T=4, init=init)
+
+
+def test_resume_equals_one_run(dsg, ctx):
+    g = gg.er_m(15000, 9, 31)
+    full = dsg.densest(ctx, g.n, g.off, g.adj, dsg.DSG_SORTING, 9)
+    a = dsg.densest(ctx, g.n, g.off, g.adj, dsg.DSG_SORTING, 4)
+    b = dsg.densest(ctx, g.n, g.off, g.adj, dsg.DSG_SORTING, 5, init_loads=a.loads)
+    assert np.array_equal(b.loads, full.loads)
+    assert np.array_equal(np.concatenate([a.trace, b.trace]), full.trace)
+
+
+def test_rmat20_config(dsg, ctx):
+    """R-MAT scale 20, edge factor 16, T = 20 (the full second workload)."""
+    g = gg.rmat(20, 16, 2)
+    check(dsg, ctx, g, T=20)
+
+
+def test_device_buffers(dsg, ctx):
+    import torch
+    g = gg.er_m(30000, 10, 41)
+    off = torch.from_numpy(g.off).cuda()
+    adj = torch.from_numpy(g.adj).cuda()
+    gr = dsg.dsg_upload_csr(ctx, g.n, off, adj, dsg.DSG_VALIDATE)
+    try:
+        T = 6
+        init = torch.arange(g.n, dtype=torch.int64, device="cuda") % 5
+        loads = torch.empty(g.n, dtype=torch.int64, device="cuda")
+        bset = torch.empty(g.n, dtype=torch.int32, device="cuda")
+        trace = torch.empty(3 * T, dtype=torch.int64, device="cuda")
+        r = dsg.dsg_run(ctx, gr, dsg.DSG_SORTING, T, 0, 1, init, loads, bset, trace)
+    finally:
+        dsg.dsg_free_graph(gr)
+    o = orc.run(g, orc.SORTING, T, 0, 1, init.cpu().numpy())
+    assert np.array_equal(loads.cpu().numpy(), o.loads)
+    assert (r["best_edges"], r["best_vertices"], r["best_iter"]) == (o.best_edges, o.best_vertices, o.best_iter)
+    assert np.array_equal(bset[: r["best_set_size"]].cpu().numpy().astype(np.int64), o.best_set)
+    assert np.array_equal(trace.cpu().numpy().reshape(T, 3), o.trace)
+
+
+def test_invalid_inputs(dsg, ctx):
+    ok = gg.complete(4)
+    with pytest.raises(dsg.DsgError, match="INVALID"):
+        dsg.dsg_upload_csr(ctx, 0, np.zeros(1, np.int64), np.zeros(0, np.int32))
+    # odd arc count
+    with pytest.raises(dsg.DsgError, match="even"):
+        dsg.dsg_upload_csr(ctx, 2, np.array([0, 1, 1], np.int64), np.array([1], np.int32))
+    # asymmetric (0->1, 1->2)
+    with pytest.raises(dsg.DsgError, match="symmetric"):
+        dsg.dsg_upload_csr(ctx, 3, np.array([0, 1, 2, 2], np.int64), np.array([1, 2], np.int32),
+                           dsg.DSG_VALIDATE)
+    # self-loop (checked even without DSG_VALIDATE)
+    with pytest.raises(dsg.DsgError, match="self-loop"):
+        dsg.dsg_upload_csr(ctx, 2, np.array([0, 2, 2], np.int64), np.array([0, 1], np.int32), 0)
+    # out of range
+    with pytest.raises(dsg.DsgError, match="out of"):
+        dsg.dsg_upload_csr(ctx, 2, np.array([0, 1, 2], np.int64), np.array([5, 0], np.int32), 0)
+    # duplicate neighbour
+    with pytest.raises(dsg.DsgError, match="ascending"):
+        dsg.dsg_upload_csr(ctx, 2, np.array([0, 2, 4], np.int64), np.array([1, 1, 0, 0], np.int32),
+                           dsg.DSG_VALIDATE)
+    g = dsg.dsg_upload_csr(ctx, ok.n, ok.off, ok.adj, dsg.DSG_VALIDATE)
+    try:
+        with pytest.raises(dsg.DsgError, match="INVALID"):
+            dsg.dsg_run(ctx, g, dsg.DSG_SORTING, 0)
+        with pytest.raises(dsg.DsgError, match="INVALID"):
+            dsg.dsg_run(ctx, g, 7, 3)
+        with pytest.raises(dsg.DsgError, match="OVERFLOW"):
+            dsg.dsg_run(ctx, g, dsg.DSG_SORTING, 2, init_loads=np.full(4, 2**32 - 3, np.int64))
+        with pytest.raises(dsg.DsgError, match="INVALID"):
+            dsg.dsg_run(ctx, g, dsg.DSG_SORTING, 2, init_loads=np.array([0, -1, 0, 0], np.int64))
+        # the context still works after the errors
+        r = dsg.dsg_run(ctx, g, dsg.DSG_SORTING, 2)
+        assert (r["best_edges"], r["best_vertices"]) == (6, 4)
+    finally:
+        dsg.dsg_free_graph(g)
+
+
+def test_profiling_stats(dsg, ctx):
+    g = gg.er_m(20000, 8, 51)
+    dsg.dsg_get_stats(ctx, reset=True)
+    dsg.dsg_set_profiling(ctx, True)
+    try:
+        dsg.densest(ctx, g.n, g.off, g.adj, dsg.DSG_SORTING, 3)
+    finally:
+        dsg.dsg_set_profiling(ctx, False)
+    st = dsg.dsg_get_stats(ctx, reset=True)
+    assert st["edge_scan"]["launches"] == 3 and st["sort"]["launches"] == 12
+    assert st["edge_scan"]["ms"] > 0 and st["sort"]["ms"] > 0
+    assert st["edge_scan"]["bytes"] == 3 * (16 * g.m + 16 * g.n)
