@@ -1,0 +1,323 @@
+"""Benchmark: GTEPS per PaRSorting++ iteration on R-MAT scale 27 (+ 10 planted
+G(s, 1/2) blocks, s = 200..2000), T = 20 iterations per step, one GB300.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+A step is one dsg_run of T iterations (all of: load sort, edge scan, fused
+densest-suffix scan, best-set materialisation) on the graph resident in HBM.
+value = m * T * K * N / (max over ranks of the timed region) / 1e9 (GTEPS).
+e2e   = the same metric through the C ABI with host buffers: each step
+        uploads the CSR from pinned host memory, runs, and reads back the
+        loads and the best set.
+Multi-GPU: the path does not shard (replicas only); each rank runs its own
+replica of the workload and value aggregates the replicas.
+--impl reference times the CPU oracle (the only reference this build has)
+on a bounded sample of the workload (same recipe at a smaller scale).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+SCALE = 27
+EDGE_FACTOR = 16
+SEED = 3
+BLOCKS = [200 * (i + 1) for i in range(10)]
+T_ITERS = 20
+SAMPLE_SCALE = 21          # CPU baseline sample: same recipe, smaller scale
+METRIC = "GTEPS per Greedy++ iteration (HBM roofline %); batched graphs/s vs one-per-launch"
+UNIT = "GTEPS"
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _max_over_ranks(x: float, ws: int) -> float:
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64,
+                     device="cuda" if dist.get_backend() == "nccl" else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _barrier(ws: int):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.lines: list[str] = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self) -> dict:
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[4:8]):
+                if val.lower() in ("active", "1"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _peak_hbm() -> tuple[float, str]:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def _traffic(kernel: str, workload: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it
+    was taken on the current source of the kernel's file (else None)."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            rec = json.load(f)[kernel]
+        src = os.path.join(ROOT, rec["source"])
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        if sha != rec["source_sha"] or rec.get("workload") != workload:
+            return None
+        return rec["dram_bytes_per_launch"]
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+def cpu_baseline(budget_s: float = 20.0) -> dict:
+    """The oracle as it stands (sequential C, one core) on a bounded sample:
+    the same R-MAT recipe at scale SAMPLE_SCALE, PaRSorting++ iterations until
+    about budget_s seconds have been spent."""
+    import graphgen as gg
+    import oracle as orc
+    g = gg.rmat(SAMPLE_SCALE, EDGE_FACTOR, SEED)
+    t0 = time.perf_counter()
+    r = orc.run(g, orc.SORTING, 1)
+    one = time.perf_counter() - t0
+    T = max(1, min(T_ITERS, int(budget_s / max(one, 1e-3))))
+    t0 = time.perf_counter()
+    r = orc.run(g, orc.SORTING, T)
+    dt = time.perf_counter() - t0
+    return {"value": g.m * T / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"R-MAT scale {SAMPLE_SCALE} (same recipe, no planted blocks), n={g.n}, "
+                      f"m={g.m}, PaRSorting++ T={T}, {dt:.1f} s, sequential C oracle"}
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    import graphgen as gg
+    import oracle as orc
+    g = gg.rmat(SAMPLE_SCALE - 1, EDGE_FACTOR, SEED)
+    T = 2
+    for _ in range(args.warmup):
+        orc.run(g, orc.SORTING, 1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        orc.run(g, orc.SORTING, T)
+    dt = time.perf_counter() - t0
+    v = g.m * T * args.steps / dt / 1e9
+    sample = (f"R-MAT scale {SAMPLE_SCALE - 1} (same recipe as the GPU workload, no planted blocks), "
+              f"n={g.n}, m={g.m}, PaRSorting++ T={T} per step, sequential C oracle")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "i64",
+        "data": "synthetic",
+        "config": {"workload": f"rmat{SAMPLE_SCALE - 1}_ef{EDGE_FACTOR} PaRSorting++ sample",
+                   "T": T},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--scale", type=int, default=SCALE)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    import graphgen as gg
+    import paper_2311_04333_gb300 as dsg
+
+    stream = torch.cuda.current_stream()
+    ctx = dsg.dsg_create(local, stream.cuda_stream)
+    blocks = BLOCKS if args.scale == SCALE else [max(4, s >> (SCALE - args.scale)) for s in BLOCKS]
+    workload = f"rmat{args.scale}_ef{EDGE_FACTOR}_seed{SEED}+10blocks({blocks[0]}..{blocks[-1]},p=1/2)"
+    n, off, adj = gg.rmat_cuda(args.scale, EDGE_FACTOR, SEED, blocks=blocks)
+    g = dsg.dsg_upload_csr(ctx, n, off, adj, 0)
+    _, m, maxdeg = dsg.dsg_graph_info(g)
+    T = T_ITERS
+    loads = torch.empty(n, dtype=torch.int64, device="cuda")
+    bset = torch.empty(n, dtype=torch.int32, device="cuda")
+    trace = torch.empty(3 * T, dtype=torch.int64, device="cuda")
+
+    def step():
+        return dsg.dsg_run(ctx, g, dsg.DSG_SORTING, T, 0, 1, None, loads, bset, trace)
+
+    for _ in range(args.warmup):
+        r = step()
+    # ---- timed region: device-resident inputs
+    dsg.dsg_get_stats(ctx, reset=True)
+    dsg.dsg_set_profiling(ctx, True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    _barrier(ws)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            r = step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    _barrier(ws)
+    dsg.dsg_set_profiling(ctx, False)
+    ms_total = ev0.elapsed_time(ev1)
+    ms_total = _max_over_ranks(ms_total, ws)
+    st = dsg.dsg_get_stats(ctx, reset=True)
+    launches = sum(v["launches"] for v in st.values())
+    value = m * T * args.steps * ws / (ms_total * 1e-3) / 1e9
+    es_ms = st["edge_scan"]["ms"] / (args.steps * T)
+    es_bytes = 16 * m + 16 * n          # algorithmic bytes per edge-scan launch
+    peak, peak_kind = _peak_hbm()
+    achieved = es_bytes / (es_ms * 1e-3) / 1e9
+    sort_ms = st["sort"]["ms"] / (args.steps * T)
+    sort_bytes = st["sort"]["bytes"] / (args.steps * T)
+
+    # ---- end to end through the C ABI with host buffers
+    off_h = torch.empty(off.numel(), dtype=torch.int64, pin_memory=True)
+    adj_h = torch.empty(adj.numel(), dtype=torch.int32, pin_memory=True)
+    off_h.copy_(off)
+    adj_h.copy_(adj)
+    loads_h = torch.empty(n, dtype=torch.int64, pin_memory=True)
+    bset_h = torch.empty(n, dtype=torch.int32, pin_memory=True)
+    dsg.dsg_free_graph(g)
+    del off, adj, loads, bset
+    torch.cuda.empty_cache()
+
+    def e2e_step():
+        gh = dsg.dsg_upload_csr(ctx, n, off_h, adj_h, 0)
+        try:
+            return dsg.dsg_run(ctx, gh, dsg.DSG_SORTING, T, 0, 1, None, loads_h, bset_h)
+        finally:
+            dsg.dsg_free_graph(gh)
+
+    re = e2e_step()
+    assert (re["best_edges"], re["best_vertices"]) == (r["best_edges"], r["best_vertices"])
+    _barrier(ws)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        re = e2e_step()
+    torch.cuda.synchronize()
+    e2e_s = _max_over_ranks(time.perf_counter() - t0, ws)
+    e2e_value = m * T * args.e2e_steps * ws / e2e_s / 1e9
+    h2d = 8 * (n + 1) + 4 * 2 * m
+    d2h = 8 * n + 4 * re["best_set_size"]
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = cpu_baseline()
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_total / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": workload, "variant": "PaRSorting++", "T": T, "n": n, "m": m,
+                       "max_degree": maxdeg, "step": f"one dsg_run of T={T} iterations",
+                       "l2": "inputs larger than L2 (adjacency %.1f GB)" % (8 * m / 1e9),
+                       "parallelism": "replicas" if ws > 1 else "single GPU",
+                       "best": [r["best_edges"], r["best_vertices"], r["best_iter"]]},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "peak_kind": peak_kind,
+                         "kernel": "k_edge_scan", "ms_per_launch": es_ms,
+                         "algorithmic_bytes_per_launch": es_bytes,
+                         "traffic": _traffic("k_edge_scan", workload)},
+            "phases": {"edge_scan_ms": es_ms, "sort_ms": sort_ms,
+                       "sort_gbs": sort_bytes / (sort_ms * 1e-3) / 1e9 if sort_ms else None,
+                       "other_ms": st["other"]["ms"] / (args.steps * T)},
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h, "steps": args.e2e_steps},
+            "gpu_launches": launches,
+            "clocks": clk.summary(),
+        }
+        print(json.dumps(out))
+    dsg.dsg_destroy(ctx)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

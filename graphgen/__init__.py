@@ -303,3 +303,110 @@ def _py_sample(seed: int, n: int, k: int) -> list[int]:
         j = i + _py_draw(seed, 102, i) % (n - i)
         perm[i], perm[j] = perm[j], perm[i]
     return perm[:k]
+
+
+# ---------------------------------------------------------------- GPU generator
+
+_SO_CUDA = os.path.join(_BUILD, "libgraphgen_cuda.so")
+_cuda_handle = None
+
+
+def build_cuda() -> str:
+    """Compile the GPU R-MAT generator (nvcc, sm_103a) into _build/."""
+    os.makedirs(_BUILD, exist_ok=True)
+    src = os.path.join(_HERE, "graphgen_cuda.cu")
+    deps = [src, os.path.join(_HERE, "graphgen.h")]
+    if os.path.exists(_SO_CUDA) and all(os.path.getmtime(_SO_CUDA) >= os.path.getmtime(d) for d in deps):
+        return _SO_CUDA
+    nvcc = "/usr/local/cuda/bin/nvcc" if os.path.exists("/usr/local/cuda/bin/nvcc") else "nvcc"
+    tmp = _SO_CUDA + f".tmp{os.getpid()}"
+    subprocess.check_call([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-shared",
+                           "-Xcompiler", "-fPIC", "-o", tmp, src])
+    os.replace(tmp, _SO_CUDA)
+    return _SO_CUDA
+
+
+def _cuda_lib():
+    global _cuda_handle
+    if _cuda_handle is None:
+        lib = ctypes.CDLL(build_cuda())
+        u64, p, i = ctypes.c_uint64, ctypes.c_void_p, ctypes.c_int
+        lib.gg_cuda_count.argtypes = [u64, i, u64, p, p, u64, p, p]
+        lib.gg_cuda_fill.argtypes = [u64, i, u64, p, p, u64, p, p, p, p]
+        _cuda_handle = lib
+    return _cuda_handle
+
+
+def rmat_cuda(scale: int, edge_factor: int = 16, seed: int = 2, blocks: list[int] | None = None,
+              chunk_arcs: int = 1 << 29):
+    """The `rmat` recipe generated on the current CUDA device.  Returns
+    (n, off, adj) with off int64[n+1] and adj int32[2m] torch tensors on the
+    device; the CSR equals the one `rmat` builds on the CPU."""
+    import torch
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream().cuda_stream
+    lib = _cuda_lib()
+    E = edge_factor << scale
+    n_raw = 1 << scale
+    if blocks:
+        extra = sum(s * (s - 1) // 2 for s in blocks)
+        cap = int(extra / 2 + 10 * math.sqrt(extra) + 100)
+        eu = np.zeros(cap, dtype=np.uint32)
+        ev = np.zeros(cap, dtype=np.uint32)
+        sz = np.asarray(blocks, dtype=np.int64)
+        c = _lib().gg_planted_blocks(scale, len(blocks), _ptr(sz), seed, _ptr(eu), _ptr(ev), 0, cap)
+        if c < 0:
+            raise RuntimeError("edge buffer too small")
+        xu = torch.from_numpy(eu[:c].view(np.int32)).to(dev)
+        xv = torch.from_numpy(ev[:c].view(np.int32)).to(dev)
+    else:
+        c = 0
+        xu = xv = torch.zeros(1, dtype=torch.int32, device=dev)
+    deg = torch.zeros(n_raw, dtype=torch.int32, device=dev)
+    if lib.gg_cuda_count(seed, scale, E, xu.data_ptr(), xv.data_ptr(), c, deg.data_ptr(), stream):
+        raise RuntimeError("gg_cuda_count failed")
+    off = torch.zeros(n_raw + 1, dtype=torch.int64, device=dev)
+    torch.cumsum(deg, 0, out=off[1:])
+    arcs_raw = int(off[-1].item())
+    adj_raw = torch.empty(max(arcs_raw, 1), dtype=torch.int32, device=dev)
+    cursor = torch.zeros(n_raw, dtype=torch.int32, device=dev)
+    if lib.gg_cuda_fill(seed, scale, E, xu.data_ptr(), xv.data_ptr(), c, off.data_ptr(),
+                        cursor.data_ptr(), adj_raw.data_ptr(), stream):
+        raise RuntimeError("gg_cuda_fill failed")
+    del cursor, xu, xv
+    # sort and deduplicate each list, vertex ranges of at most chunk_arcs arcs
+    new_deg = torch.zeros(n_raw, dtype=torch.int64, device=dev)
+    off_h = off.cpu().numpy()
+    pieces = []
+    lo = 0
+    while lo < n_raw:
+        hi = int(np.searchsorted(off_h, off_h[lo] + chunk_arcs, side="right")) - 1
+        hi = max(min(hi, n_raw), lo + 1)
+        a, b = int(off_h[lo]), int(off_h[hi])
+        if b > a:
+            seg = adj_raw[a:b].long()
+            src = torch.repeat_interleave(torch.arange(hi - lo, device=dev), deg[lo:hi].long())
+            keys = torch.sort((src << 32) | seg).values
+            del seg, src
+            keep = torch.ones_like(keys, dtype=torch.bool)
+            keep[1:] = keys[1:] != keys[:-1]
+            keys = keys[keep]
+            del keep
+            new_deg[lo:hi] = torch.bincount(keys >> 32, minlength=hi - lo)
+            pieces.append((keys & 0xFFFFFFFF).to(torch.int32))
+            del keys
+        lo = hi
+    del adj_raw, deg
+    adj = torch.cat(pieces) if pieces else torch.zeros(1, dtype=torch.int32, device=dev)
+    del pieces
+    keepv = new_deg > 0
+    newid = torch.cumsum(keepv, 0) - 1
+    for a in range(0, adj.numel(), chunk_arcs):
+        b = min(a + chunk_arcs, adj.numel())
+        adj[a:b] = newid[adj[a:b].long()].to(torch.int32)
+    n = int(keepv.sum().item())
+    off_new = torch.zeros(n + 1, dtype=torch.int64, device=dev)
+    torch.cumsum(new_deg[keepv], 0, out=off_new[1:])
+    m2 = int(off_new[-1].item())
+    torch.cuda.synchronize()
+    return n, off_new, adj[:m2]
