@@ -157,6 +157,45 @@ int dsg_set_profiling(dsg_ctx *ctx, int on);
  *   bytes[DSG_PHASE_COUNT]: algorithmic bytes moved per phase (always). */
 int dsg_get_stats(dsg_ctx *ctx, double *ms, int64_t *launches, int64_t *bytes, int reset);
 
+/* ---- allocation-free entry point ---------------------------------------- */
+
+/* Largest n accepted by dsg_densest_suffix_noalloc. */
+#define DSG_NOALLOC_MAX_VERTICES 262144
+
+/* The densest suffix of the (load, id) order, computed without allocating
+ * any memory.  This entry point has no counterpart in the paper; it exists
+ * for callers that must not call cudaMalloc: code that runs while a CUDA
+ * graph is being captured, code that owns a fixed memory arena and may not
+ * grow it (a serving process that reserves its memory at start-up, a plugin
+ * living under another framework's allocator), and callers without a
+ * dsg_ctx (dsg_create itself allocates).
+ *
+ * Given loads[n] and A[n] (device pointers, uint32, by vertex id) it orders
+ * the vertices by (loads[v], v) and returns the first densest suffix of that
+ * order, where a suffix's edge count is the sum of A over it (Alg. 3 lines
+ * 4-7 with B = SuffixSum(A)).  When A is the later-neighbour count of the
+ * order (the edge scan of dsg_run), m = sum(A) is the graph's edge count.
+ *   m: sum of A[0..n-1] (the edges of the whole graph);
+ *   result: device pointer to int64[5], written on `cuda_stream`:
+ *     (edges, vertices) of the densest suffix (largest suffix on ties),
+ *     the position of its first vertex in the order, that vertex's load,
+ *     and a device status (0, or DSG_ERR_TIMEOUT if a bounded wait gave up).
+ * The call is asynchronous: it only enqueues kernels on `cuda_stream` and
+ * never synchronises.  It returns DSG_ERR_INVALID when n < 1,
+ * n > DSG_NOALLOC_MAX_VERTICES, m < 0 or a pointer is NULL, and DSG_ERR_CUDA
+ * when a launch fails.  loads and A are read only.
+ *
+ * Scratch memory: one static device array of about 4.4 MB inside libdsg,
+ * held by every GPU that loads the library until the process exits.  Every
+ * call uses the same array and leaves its contents behind (the next call
+ * resets what must start from zero), so calls whose work overlaps on the GPU
+ * (on different streams or from different host threads) race and must be
+ * ordered by the caller.  The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress) with that device current; make that
+ * first call before any stream capture. */
+int dsg_densest_suffix_noalloc(const uint32_t *loads, const uint32_t *A, int64_t n, int64_t m,
+                               int64_t *result, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

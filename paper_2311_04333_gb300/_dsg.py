@@ -54,6 +54,7 @@ def _load():
     lib.dsg_free_graph.restype = None
     lib.dsg_set_profiling.argtypes = [P, I]
     lib.dsg_get_stats.argtypes = [P, P, P, P, I]
+    lib.dsg_densest_suffix_noalloc.argtypes = [P, P, I64, I64, P, P]
     return lib
 
 
@@ -159,5 +160,21 @@ def dsg_get_stats(ctx, reset: bool = False) -> dict:
     return {nm: dict(ms=ms[i], launches=la[i], bytes=by[i]) for i, nm in enumerate(names)}
 
 
+def dsg_densest_suffix_noalloc(loads, A, n: int, m: int, result, stream: int | None = None) -> None:
+    """Enqueue the allocation-free densest-suffix computation.  loads/A are
+    uint32 (or int32 bit patterns) CUDA tensors of n entries; result is an
+    int64 CUDA tensor of 5 entries; nothing is synchronised."""
+    for t in (loads, A, result):
+        if not (_is_torch(t) and t.is_cuda and t.is_contiguous()):
+            raise TypeError("dsg_densest_suffix_noalloc takes contiguous CUDA tensors")
+    rc = LIB.dsg_densest_suffix_noalloc(loads.data_ptr(), A.data_ptr(), n, m, result.data_ptr(), stream)
+    if rc != DSG_OK:
+        raise DsgError(rc, f"dsg_densest_suffix_noalloc(n={n}, m={m}) rejected "
+                           f"(n must be in [1, {DSG_NOALLOC_MAX_VERTICES}])")
+
+
+DSG_NOALLOC_MAX_VERTICES = 262144
+
 EXPORTED = ["dsg_create", "dsg_destroy", "dsg_last_error", "dsg_upload_csr", "dsg_graph_info",
-            "dsg_run", "dsg_free_graph", "dsg_set_profiling", "dsg_get_stats"]
+            "dsg_run", "dsg_free_graph", "dsg_set_profiling", "dsg_get_stats",
+            "dsg_densest_suffix_noalloc"]
