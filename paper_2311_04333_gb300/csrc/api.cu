@@ -289,9 +289,8 @@ int dsg_upload_csr(dsg_ctx *ctx, int64_t n, const int64_t *offsets, const int32_
         if (h_err[i]) return bail(fail(ctx, DSG_ERR_INVALID, "invalid graph: %s", what[i]));
     G->g.max_degree = (int64_t)h_maxdeg;
     // edge-scan tile schedule
-    const int64_t nwin = arcs / kWin + 1;
     void *tmp = nullptr;
-    const size_t tmp_bytes = (size_t)(2 * nwin + 4) * sizeof(int64_t);
+    const size_t tmp_bytes = (size_t)schedule_tmp_count(n) * sizeof(int64_t);
     if ((e = cudaMallocAsync(&tmp, tmp_bytes, ctx->stream)) != cudaSuccess) return bail(cuda_fail(ctx, e, "schedule scratch"));
     e = build_schedule(G->g, tmp, tmp_bytes, ctx->stream, &G->g.n_items, &G->g.n_heavy, &G->items, &G->heavy_mem);
     cudaFreeAsync(tmp, ctx->stream);

@@ -6,21 +6,17 @@
 
 namespace dsg {
 
-// ---- edge-scan tile schedule ----------------------------------------------
-// The arc array is cut into windows of kWin arcs.  Window b owns the
-// vertices whose first arc lies in [b*kWin, (b+1)*kWin).  Its light
-// vertices (degree <= kWin) form up to ceil(count/kTileV) light tiles of
-// consecutive ids (at most 2*kWin arcs each); a heavy vertex (degree > kWin)
-// is always the last vertex of its window and is split into chunks of kWin
-// arcs, one work item each.
-constexpr int kWin = 4096;
-constexpr int kTileV = 4096;
-constexpr uint32_t kHeavyBit = 0x80000000u;
+// ---- edge-scan schedule -----------------------------------------------------
+// Vertices of degree > kHeavyDeg are split into chunks of kChunk arcs, one
+// work item each (built at upload); all other vertices are taken in groups
+// of 32 consecutive ids by single warps, without a list.
+constexpr int64_t kHeavyDeg = 1024;
+constexpr int kChunk = 1024;
 
 struct WorkItem {
-    int64_t a0;      // first arc
-    uint32_t u;      // first vertex (light) or the heavy vertex
-    uint32_t info;   // light: vertex count; heavy: kHeavyBit | heavy index
+    int64_t a0;      // first arc of the chunk
+    uint32_t u;      // the heavy vertex
+    uint32_t info;   // its heavy index (accumulator slot)
 };
 
 // ---- radix passes -----------------------------------------------------------
@@ -105,6 +101,7 @@ struct RunBufs {
 
 int edge_scan_sm_count();
 cudaError_t launch_validate(const GraphDev &g, int full, int32_t *err_flags, cudaStream_t s);
+int64_t schedule_tmp_count(int64_t n);
 cudaError_t build_schedule(GraphDev &g, void *tmp, size_t tmp_bytes, cudaStream_t s,
                            int64_t *n_items_out, int64_t *n_heavy_out, WorkItem **items_out,
                            uint32_t **heavy_mem_out);

@@ -52,84 +52,65 @@ cudaError_t launch_validate(const GraphDev &g, int full, int32_t *err_flags, cud
     return cudaGetLastError();
 }
 
-// ============================================================ tile schedule
+// ============================================================ heavy-chunk schedule
+// Vertices of degree > kHeavyDeg get ceil(deg / kChunk) work items of
+// kChunk arcs each; heavy index h (their accumulator slot) follows id order.
 
-__device__ __forceinline__ int64_t lower_bound_off(const int64_t *off, int64_t n, int64_t x)
+constexpr int kSchedBlock = 4096;                 // vertices per block
+constexpr int kSchedPer = kSchedBlock / 256;      // vertices per thread
+
+__device__ __forceinline__ void sched_counts(const int64_t *off, int64_t n, int64_t v0,
+                                             uint64_t &h, uint64_t &c)
 {
-    // first u in [0, n] with off[u] >= x, or n + 1
-    int64_t lo = 0, hi = n + 1;
-    while (lo < hi) {
-        const int64_t mid = lo + (hi - lo) / 2;
-        if (off[mid] >= x) hi = mid; else lo = mid + 1;
-    }
-    return lo;
-}
-
-struct WinInfo {
-    int64_t lo, nv;      // vertices [lo, lo + nv) start in the window
-    int heavy;           // the last one is heavy
-    int64_t hdeg;
-};
-
-__device__ __forceinline__ WinInfo window_info(const int64_t *off, int64_t n, int64_t b)
-{
-    WinInfo w;
-    int64_t lo = lower_bound_off(off, n, b * (int64_t)kWin);
-    int64_t hi = lower_bound_off(off, n, (b + 1) * (int64_t)kWin);
-    if (lo > n) lo = n;
-    if (hi > n) hi = n;
-    w.lo = lo;
-    w.nv = hi - lo;
-    w.heavy = 0;
-    w.hdeg = 0;
-    if (w.nv > 0) {
-        const int64_t last = hi - 1;
-        const int64_t d = off[last + 1] - off[last];
-        if (d > kWin) { w.heavy = 1; w.hdeg = d; }
-    }
-    return w;
-}
-
-__global__ void k_sched_count(const int64_t *__restrict__ off, int64_t n, int64_t nwin,
-                              int64_t *cnt_items, int64_t *cnt_heavy)
-{
-    for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < nwin;
-         b += (int64_t)gridDim.x * blockDim.x) {
-        const WinInfo w = window_info(off, n, b);
-        const int64_t nlight = w.nv - w.heavy;
-        int64_t c = (nlight + kTileV - 1) / kTileV;
-        if (w.heavy) c += (w.hdeg + kWin - 1) / kWin;
-        cnt_items[b] = c;
-        cnt_heavy[b] = w.heavy;
+    h = 0;
+    c = 0;
+    for (int i = 0; i < kSchedPer; ++i) {
+        const int64_t v = v0 + i;
+        if (v >= n) break;
+        const int64_t d = off[v + 1] - off[v];
+        if (d > kHeavyDeg) {
+            h += 1;
+            c += (uint64_t)((d + kChunk - 1) / kChunk);
+        }
     }
 }
 
-__global__ void k_sched_write(const int64_t *__restrict__ off, int64_t n, int64_t nwin,
-                              const int64_t *item_off, const int64_t *heavy_off, WorkItem *items)
+__global__ void k_sched_count(const int64_t *__restrict__ off, int64_t n, int64_t *cnt_h,
+                              int64_t *cnt_c)
 {
-    for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < nwin;
-         b += (int64_t)gridDim.x * blockDim.x) {
-        const WinInfo w = window_info(off, n, b);
-        const int64_t nlight = w.nv - w.heavy;
-        int64_t o = item_off[b];
-        for (int64_t s = 0; s < nlight; s += kTileV) {
+    __shared__ unsigned long long red[33];
+    uint64_t h, c, th, tc;
+    sched_counts(off, n, (int64_t)blockIdx.x * kSchedBlock + threadIdx.x * kSchedPer, h, c);
+    block_excl_sum_u64(h, red, &th);
+    block_excl_sum_u64(c, red, &tc);
+    if (threadIdx.x == 0) {
+        cnt_h[blockIdx.x] = (int64_t)th;
+        cnt_c[blockIdx.x] = (int64_t)tc;
+    }
+}
+
+__global__ void k_sched_write(const int64_t *__restrict__ off, int64_t n, const int64_t *hoff,
+                              const int64_t *coff, WorkItem *items)
+{
+    __shared__ unsigned long long red[33];
+    const int64_t v0 = (int64_t)blockIdx.x * kSchedBlock + threadIdx.x * kSchedPer;
+    uint64_t h, c, th, tc;
+    sched_counts(off, n, v0, h, c);
+    int64_t hi = hoff[blockIdx.x] + (int64_t)block_excl_sum_u64(h, red, &th);
+    int64_t ci = coff[blockIdx.x] + (int64_t)block_excl_sum_u64(c, red, &tc);
+    for (int i = 0; i < kSchedPer; ++i) {
+        const int64_t v = v0 + i;
+        if (v >= n) break;
+        const int64_t s = off[v], d = off[v + 1] - s;
+        if (d <= kHeavyDeg) continue;
+        for (int64_t a = 0; a < d; a += kChunk) {
             WorkItem it;
-            it.u = (uint32_t)(w.lo + s);
-            it.a0 = off[w.lo + s];
-            it.info = (uint32_t)imin64(kTileV, nlight - s);
-            items[o++] = it;
+            it.a0 = s + a;
+            it.u = (uint32_t)v;
+            it.info = (uint32_t)hi;
+            items[ci++] = it;
         }
-        if (w.heavy) {
-            const int64_t hv = w.lo + w.nv - 1;
-            const int64_t base = off[hv];
-            for (int64_t c = 0; c * kWin < w.hdeg; ++c) {
-                WorkItem it;
-                it.u = (uint32_t)hv;
-                it.a0 = base + c * kWin;
-                it.info = kHeavyBit | (uint32_t)heavy_off[b];
-                items[o++] = it;
-            }
-        }
+        ++hi;
     }
 }
 
@@ -150,34 +131,35 @@ __global__ void k_scan_single(int64_t *x, int64_t count, int64_t *total)
     if (threadIdx.x == 0) *total = carry;
 }
 
-// tmp must hold 2*(nwin+1) int64 + 2 totals
+int64_t schedule_tmp_count(int64_t n) { return 2 * ((n + kSchedBlock - 1) / kSchedBlock) + 4; }
+
+// tmp must hold schedule_tmp_count(n) int64
 cudaError_t build_schedule(GraphDev &g, void *tmp, size_t tmp_bytes, cudaStream_t s,
                            int64_t *n_items_out, int64_t *n_heavy_out, WorkItem **items_out,
                            uint32_t **heavy_mem_out)
 {
-    const int64_t nwin = g.arcs / kWin + 1;
-    if (tmp_bytes < (size_t)(2 * nwin + 4) * sizeof(int64_t)) return cudaErrorInvalidValue;
-    int64_t *ci = (int64_t *)tmp, *ch = ci + nwin, *tot = ch + nwin;
-    int grid = (int)imin64((nwin + 255) / 256, 152 * 8);
-    k_sched_count<<<grid, 256, 0, s>>>(g.off, g.n, nwin, ci, ch);
-    k_scan_single<<<1, 1024, 0, s>>>(ci, nwin, tot);
-    k_scan_single<<<1, 1024, 0, s>>>(ch, nwin, tot + 1);
+    const int64_t nblk = (g.n + kSchedBlock - 1) / kSchedBlock;
+    if (tmp_bytes < (size_t)schedule_tmp_count(g.n) * sizeof(int64_t)) return cudaErrorInvalidValue;
+    int64_t *ch = (int64_t *)tmp, *cc = ch + nblk, *tot = cc + nblk;
+    k_sched_count<<<(unsigned)nblk, 256, 0, s>>>(g.off, g.n, ch, cc);
+    k_scan_single<<<1, 1024, 0, s>>>(ch, nblk, tot);
+    k_scan_single<<<1, 1024, 0, s>>>(cc, nblk, tot + 1);
     int64_t h_tot[2];
     cudaError_t e = cudaMemcpyAsync(h_tot, tot, sizeof(h_tot), cudaMemcpyDeviceToHost, s);
     if (e != cudaSuccess) return e;
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
     WorkItem *items = nullptr;
     uint32_t *hm = nullptr;
-    if ((e = cudaMallocAsync((void **)&items, sizeof(WorkItem) * (size_t)imax64(h_tot[0], 1), s)) != cudaSuccess)
+    if ((e = cudaMallocAsync((void **)&items, sizeof(WorkItem) * (size_t)imax64(h_tot[1], 1), s)) != cudaSuccess)
         return e;
-    if ((e = cudaMallocAsync((void **)&hm, sizeof(uint32_t) * 2 * (size_t)imax64(h_tot[1], 1), s)) != cudaSuccess) {
+    if ((e = cudaMallocAsync((void **)&hm, sizeof(uint32_t) * 2 * (size_t)imax64(h_tot[0], 1), s)) != cudaSuccess) {
         cudaFreeAsync(items, s);
         return e;
     }
-    cudaMemsetAsync(hm, 0, sizeof(uint32_t) * 2 * (size_t)imax64(h_tot[1], 1), s);
-    k_sched_write<<<grid, 256, 0, s>>>(g.off, g.n, nwin, ci, ch, items);
-    *n_items_out = h_tot[0];
-    *n_heavy_out = h_tot[1];
+    cudaMemsetAsync(hm, 0, sizeof(uint32_t) * 2 * (size_t)imax64(h_tot[0], 1), s);
+    k_sched_write<<<(unsigned)nblk, 256, 0, s>>>(g.off, g.n, ch, cc, items);
+    *n_items_out = h_tot[1];
+    *n_heavy_out = h_tot[0];
     *items_out = items;
     *heavy_mem_out = hm;
     return cudaGetLastError();

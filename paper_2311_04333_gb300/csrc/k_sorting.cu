@@ -101,21 +101,24 @@ cudaError_t launch_plan(const GraphDev &, RunBufs &b, int t, cudaStream_t s)
 }
 
 // ============================================================ edge scan
+// Warp-centric, no block barriers.  Work units come from an atomic dispenser:
+//   units [0, n_items): one chunk of kChunk arcs of a heavy vertex
+//     (degree > kHeavyDeg); per-vertex totals meet in an atomic accumulator
+//     and the warp finishing the last chunk writes A[u];
+//   units after that: a light group of 32 consecutive vertices, one per lane.
+//     Vertices of degree >= kMidDeg are taken one at a time by the whole warp;
+//     the arcs of the smaller ones are packed across the lanes, each arc
+//     finding its source lane by a 5-step shuffle binary search.
+// Adjacency is streamed (L1 no-allocate, L2 evict-first) so that it does not
+// evict the gathered loads; gathers go through L1.
 
 constexpr int kEsThreads = 256;
-constexpr int kEsArcs = 8;                       // arcs per thread per round
-constexpr int kEsRound = kEsThreads * kEsArcs;   // arcs per round
+constexpr int kEsUnroll = 8;                    // rounds of 32 arcs in flight per warp
+constexpr int64_t kMidDeg = 64;
 
 struct EsSmem {
-    int32_t off[kTileV + 1];
-    uint32_t l[kTileV];
-    uint32_t cnt[kTileV];
-    uint16_t src[2 * kWin];
     uint32_t hist[kMaxPasses][kBuckets];
     unsigned long long asum[kBuckets];
-    uint32_t scan[kEsThreads / 32];
-    uint32_t item;
-    uint32_t red[kEsThreads / 32];
 };
 
 // per-thread run-length accumulation of the digit histograms
@@ -158,44 +161,69 @@ __device__ __forceinline__ void hist_flush(HistAcc &h, EsSmem &S, int np)
     if (h.ss) atomicAdd(&S.asum[h.sb], h.ss);
 }
 
-// fill-forward of the source marks: s[j] = max(s[0..j]) over na slots
-__device__ __forceinline__ void block_fill_forward(uint16_t *s, int na, EsSmem &S)
+__device__ __forceinline__ uint64_t policy_evict_first()
 {
-    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    const int per = (na + kEsThreads - 1) / kEsThreads;
-    const int b = tid * per, e = min(b + per, na);
-    uint32_t run = 0;
-    for (int j = b; j < e; ++j) run = max(run, (uint32_t)s[j]);
-    uint32_t inc = run;
-    #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        uint32_t y = __shfl_up_sync(kFull, inc, o);
-        if (lane >= o) inc = max(inc, y);
-    }
-    if (lane == 31) S.scan[w] = inc;
-    __syncthreads();
-    uint32_t pre = 0;
-    for (int i = 0; i < w; ++i) pre = max(pre, S.scan[i]);
-    uint32_t ex = __shfl_up_sync(kFull, inc, 1);
-    if (lane == 0) ex = 0;
-    uint32_t cur = max(pre, ex);
-    for (int j = b; j < e; ++j) {
-        cur = max(cur, (uint32_t)s[j]);
-        s[j] = (uint16_t)cur;
-    }
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
 }
 
-__global__ void __launch_bounds__(kEsThreads)
+// streamed read of one adjacency entry
+__device__ __forceinline__ int32_t ld_adj(const int32_t *p, uint64_t pol)
+{
+    int32_t v;
+    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.b32 %0, [%1], %2;"
+                 : "=r"(v) : "l"(p), "l"(pol));
+    return v;
+}
+
+// (l[w], w) > (l[u], u): w is later than u in the (load, id) order
+__device__ __forceinline__ bool later(uint32_t lw, uint32_t w, uint32_t lu, uint32_t u)
+{
+    return lw > lu || (lw == lu && w > u);
+}
+
+// the warp counts the later neighbours among arcs [a0, a1) of vertex (lu, u);
+// returns this lane's share
+__device__ __forceinline__ uint32_t warp_count_arcs(const int32_t *__restrict__ adj,
+                                                    const uint32_t *__restrict__ loads, int64_t a0,
+                                                    int64_t a1, uint32_t lu, uint32_t u, int lane,
+                                                    uint64_t pol)
+{
+    uint32_t c = 0;
+    for (int64_t j0 = a0; j0 < a1; j0 += 32 * kEsUnroll) {
+        uint32_t w[kEsUnroll], lw[kEsUnroll];
+        #pragma unroll
+        for (int k = 0; k < kEsUnroll; ++k) {
+            const int64_t j = j0 + k * 32 + lane;
+            w[k] = j < a1 ? (uint32_t)ld_adj(adj + j, pol) : 0u;
+        }
+        #pragma unroll
+        for (int k = 0; k < kEsUnroll; ++k) {
+            const int64_t j = j0 + k * 32 + lane;
+            lw[k] = j < a1 ? __ldg(loads + w[k]) : 0u;
+        }
+        #pragma unroll
+        for (int k = 0; k < kEsUnroll; ++k) {
+            const int64_t j = j0 + k * 32 + lane;
+            c += (j < a1) && later(lw[k], w[k], lu, u);
+        }
+    }
+    return c;
+}
+
+__global__ void __launch_bounds__(kEsThreads, 4)
 k_edge_scan(const int64_t *__restrict__ off, const int32_t *__restrict__ adj,
-            const WorkItem *__restrict__ items, int64_t n_items,
+            const WorkItem *__restrict__ items, int64_t n_items, int64_t n,
             const uint32_t *__restrict__ loads, uint32_t *__restrict__ A,
             uint32_t *heavy_acc, uint32_t *heavy_done, Control *ctl)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    EsSmem &S = *reinterpret_cast<EsSmem *>(smem_raw);
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    __shared__ EsSmem S;
+    const int tid = threadIdx.x, lane = tid & 31;
     const uint32_t lmin = ctl->lmin;
     const int np = ctl->npass;
+    const uint64_t pol = policy_evict_first();
+    const int64_t n_units = n_items + (n + 31) / 32;
 
     for (int i = tid; i < kMaxPasses * kBuckets; i += kEsThreads) (&S.hist[0][0])[i] = 0;
     for (int i = tid; i < kBuckets; i += kEsThreads) S.asum[i] = 0;
@@ -208,34 +236,24 @@ k_edge_scan(const int64_t *__restrict__ off, const int32_t *__restrict__ adj,
     __syncthreads();
 
     for (;;) {
-        if (tid == 0) S.item = atomicAdd(&ctl->item_ctr, 1u);
-        __syncthreads();
-        const uint32_t it_idx = S.item;
-        if (it_idx >= n_items) break;
-        const WorkItem it = items[it_idx];
+        uint32_t unit = 0;
+        if (lane == 0) unit = atomicAdd(&ctl->item_ctr, 1u);
+        unit = __shfl_sync(kFull, unit, 0);
+        if ((int64_t)unit >= n_units) break;
 
-        if (it.info & kHeavyBit) {
-            // ---- one chunk of kWin arcs of a heavy vertex (block per chunk)
-            const uint32_t u = it.u, hidx = it.info & ~kHeavyBit;
+        if ((int64_t)unit < n_items) {
+            // ---- one chunk of a heavy vertex
+            const WorkItem it = items[unit];
+            const uint32_t u = it.u, hidx = it.info;
             const int64_t s0 = off[u], s1 = off[u + 1];
-            const int64_t a0 = it.a0, a1 = min(a0 + (int64_t)kWin, s1);
+            const int64_t a1 = imin64(it.a0 + (int64_t)kChunk, s1);
             const uint32_t lu = loads[u];
-            uint32_t c = 0;
-            #pragma unroll 4
-            for (int64_t j = a0 + tid; j < a1; j += kEsThreads) {
-                const uint32_t w = (uint32_t)__ldg(adj + j);
-                const uint32_t lw = __ldg(loads + w);
-                c += (lw > lu) || (lw == lu && w > u);
-            }
+            uint32_t c = warp_count_arcs(adj, loads, it.a0, a1, lu, u, lane, pol);
             c = __reduce_add_sync(kFull, c);
-            if (lane == 0) S.red[warp] = c;
-            __syncthreads();
-            if (tid == 0) {
-                uint32_t tot = 0;
-                for (int i = 0; i < kEsThreads / 32; ++i) tot += S.red[i];
-                atomicAdd(&heavy_acc[hidx], tot);
+            if (lane == 0) {
+                atomicAdd(&heavy_acc[hidx], c);
                 __threadfence();
-                const uint32_t nch = (uint32_t)((s1 - s0 + kWin - 1) / kWin);
+                const uint32_t nch = (uint32_t)((s1 - s0 + kChunk - 1) / kChunk);
                 if (atomicAdd(&heavy_done[hidx], 1u) == nch - 1) {
                     __threadfence();
                     const uint32_t total = atomicExch(&heavy_acc[hidx], 0u);
@@ -245,74 +263,84 @@ k_edge_scan(const int64_t *__restrict__ off, const int32_t *__restrict__ adj,
                     hist_add(h, S, lu, total, lmin, np);
                 }
             }
-            __syncthreads();
             continue;
         }
 
-        // ---- light tile: consecutive vertices u0 .. u0+nv-1, arcs contiguous
-        const uint32_t u0 = it.u, nv = it.info;
-        const int64_t a0 = it.a0;
-        for (uint32_t i = tid; i <= nv; i += kEsThreads) S.off[i] = (int32_t)(off[u0 + i] - a0);
-        for (uint32_t i = tid; i < nv; i += kEsThreads) {
-            S.l[i] = loads[u0 + i];
-            S.cnt[i] = 0;
-        }
-        __syncthreads();
-        const int na = S.off[nv];
-        for (int j = tid; j < na; j += kEsThreads) S.src[j] = 0;
-        __syncthreads();
-        for (uint32_t i = tid; i < nv; i += kEsThreads)
-            if (S.off[i + 1] > S.off[i]) S.src[S.off[i]] = (uint16_t)i;
-        __syncthreads();
-        block_fill_forward(S.src, na, S);
-        __syncthreads();
+        // ---- light group: vertices 32*g .. 32*g+31
+        const int64_t g0 = ((int64_t)unit - n_items) * 32;
+        const int64_t uu = g0 + lane;
+        const bool valid = uu < n;
+        const int64_t s = valid ? off[uu] : 0;
+        int64_t e = __shfl_down_sync(kFull, s, 1);
+        if (lane == 31 || uu + 1 >= n) e = valid ? off[uu + 1] : 0;
+        const int64_t deg = e - s;
+        const bool heavy = deg > kHeavyDeg;
+        const bool mid = !heavy && deg >= kMidDeg;
+        const uint32_t lu = valid ? loads[uu] : 0u;
+        uint32_t cnt = 0;
 
-        for (int base = 0; base < na; base += kEsRound) {
-            const int wb = base + warp * (32 * kEsArcs);
-            int32_t wv[kEsArcs];
-            uint32_t lw[kEsArcs];
+        // vertices of medium degree: the whole warp, one at a time
+        uint32_t mm = __ballot_sync(kFull, mid);
+        while (mm) {
+            const int l = __ffs(mm) - 1;
+            mm &= mm - 1;
+            const int64_t vs = __shfl_sync(kFull, s, l), ve = __shfl_sync(kFull, e, l);
+            const uint32_t vl = __shfl_sync(kFull, lu, l);
+            uint32_t c = warp_count_arcs(adj, loads, vs, ve, vl, (uint32_t)(g0 + l), lane, pol);
+            c = __reduce_add_sync(kFull, c);
+            if (lane == l) cnt = c;
+        }
+
+        // small vertices: arcs packed across the lanes
+        const uint32_t sdeg = (valid && !heavy && !mid) ? (uint32_t)deg : 0u;
+        uint32_t incl = sdeg;
+        #pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const uint32_t total = __shfl_sync(kFull, incl, 31);
+        const uint32_t start = incl - sdeg;
+        for (uint32_t base = 0; base < total; base += 32 * kEsUnroll) {
+            uint32_t w[kEsUnroll], lw[kEsUnroll], sl_r[kEsUnroll];
             #pragma unroll
-            for (int k = 0; k < kEsArcs; ++k) {
-                const int j = wb + k * 32 + lane;
-                wv[k] = (j < na) ? __ldg(adj + a0 + j) : 0;
-            }
-            #pragma unroll
-            for (int k = 0; k < kEsArcs; ++k) {
-                const int j = wb + k * 32 + lane;
-                lw[k] = (j < na) ? __ldg(loads + wv[k]) : 0u;
-            }
-            #pragma unroll
-            for (int k = 0; k < kEsArcs; ++k) {
-                const int j = wb + k * 32 + lane;
-                const bool valid = j < na;
-                const uint32_t src = valid ? S.src[j] : 0xffffu;
-                const uint32_t prev = __shfl_up_sync(kFull, src, 1);
-                const bool head = valid && (lane == 0 || prev != src);
-                bool cmp = false;
-                if (valid) {
-                    const uint32_t lu = S.l[src];
-                    const uint32_t w = (uint32_t)wv[k];
-                    cmp = (lw[k] > lu) || (lw[k] == lu && w > u0 + src);
+            for (int k = 0; k < kEsUnroll; ++k) {
+                const uint32_t j = base + k * 32 + lane;
+                uint32_t sl = 0;
+                #pragma unroll
+                for (int step = 16; step >= 1; step >>= 1) {
+                    const uint32_t x = __shfl_sync(kFull, incl, sl + step - 1);
+                    if (x <= j) sl += step;
                 }
-                const uint32_t H = __ballot_sync(kFull, head);
+                const int64_t so = __shfl_sync(kFull, s, sl);
+                const uint32_t st = __shfl_sync(kFull, start, sl);
+                sl_r[k] = sl;
+                w[k] = j < total ? (uint32_t)ld_adj(adj + so + (j - st), pol) : 0u;
+            }
+            #pragma unroll
+            for (int k = 0; k < kEsUnroll; ++k) {
+                const uint32_t j = base + k * 32 + lane;
+                lw[k] = j < total ? __ldg(loads + w[k]) : 0u;
+            }
+            #pragma unroll
+            for (int k = 0; k < kEsUnroll; ++k) {
+                const uint32_t j = base + k * 32 + lane;
+                const uint32_t l_src = __shfl_sync(kFull, lu, sl_r[k]);
+                const bool cmp = j < total && later(lw[k], w[k], l_src, (uint32_t)(g0 + sl_r[k]));
                 const uint32_t C = __ballot_sync(kFull, cmp);
-                if (head) {
-                    const uint32_t above = H & ~((2u << lane) - 1u);
-                    const int nxt = above ? (__ffs(above) - 1) : 32;
-                    const uint32_t seg = (nxt == 32 ? kFull : ((1u << nxt) - 1u)) & ~((1u << lane) - 1u);
-                    const uint32_t c = __popc(C & seg);
-                    if (c) atomicAdd(&S.cnt[src], c);
+                const int jb = (int)(base + k * 32);
+                const int lo = max((int)start - jb, 0), hi = min((int)incl - jb, 32);
+                if (hi > lo) {
+                    const uint32_t mhi = hi == 32 ? kFull : ((1u << hi) - 1u);
+                    cnt += __popc(C & mhi & ~((1u << lo) - 1u));
                 }
             }
         }
-        __syncthreads();
-        for (uint32_t i = tid; i < nv; i += kEsThreads) {
-            const uint32_t c = S.cnt[i];
-            A[u0 + i] = c;
-            width = max(width, c);
-            hist_add(h, S, S.l[i], c, lmin, np);
+        if (valid && !heavy) {
+            A[uu] = cnt;
+            width = max(width, cnt);
+            hist_add(h, S, lu, cnt, lmin, np);
         }
-        __syncthreads();
     }
 
     hist_flush(h, S, np);
@@ -331,10 +359,8 @@ static int g_es_blocks_per_sm = -1;
 int edge_scan_sm_count()
 {
     if (g_es_blocks_per_sm < 0) {
-        cudaFuncSetAttribute(k_edge_scan, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)sizeof(EsSmem));
         int nb = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_edge_scan, kEsThreads, sizeof(EsSmem));
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_edge_scan, kEsThreads, 0);
         g_es_blocks_per_sm = nb > 0 ? nb : 1;
     }
     return g_es_blocks_per_sm;
@@ -342,10 +368,8 @@ int edge_scan_sm_count()
 
 cudaError_t launch_edge_scan(const GraphDev &g, RunBufs &b, int grid, cudaStream_t s)
 {
-    edge_scan_sm_count();
-    k_edge_scan<<<grid, kEsThreads, sizeof(EsSmem), s>>>(g.off, g.adj, g.items, g.n_items,
-                                                         b.loads, b.A, g.heavy_acc,
-                                                         g.heavy_done, b.ctl);
+    k_edge_scan<<<grid, kEsThreads, 0, s>>>(g.off, g.adj, g.items, g.n_items, g.n, b.loads, b.A,
+                                            g.heavy_acc, g.heavy_done, b.ctl);
     return cudaGetLastError();
 }
 
