@@ -247,7 +247,7 @@ def main():
     launches = sum(v["launches"] for v in st.values())
     value = m * T * args.steps * ws / (ms_total * 1e-3) / 1e9
     es_ms = st["edge_scan"]["ms"] / (args.steps * T)
-    es_bytes = 16 * m + 16 * n          # algorithmic bytes per edge-scan launch
+    es_bytes = 8 * m + 16 * n           # algorithmic bytes per edge-scan launch (oriented scan)
     peak, peak_kind = _peak_hbm()
     achieved = es_bytes / (es_ms * 1e-3) / 1e9
     sort_ms = st["sort"]["ms"] / (args.steps * T)

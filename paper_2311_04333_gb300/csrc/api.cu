@@ -36,6 +36,9 @@ struct dsg_graph {
     int32_t *adj = nullptr;
     WorkItem *items = nullptr;
     uint32_t *heavy_mem = nullptr;
+    int64_t *ooff = nullptr;         // degree-oriented copy (sorting edge scan)
+    uint32_t *oadj = nullptr;
+    uint32_t *hub = nullptr;
     // run buffers, allocated on first use
     bool rb_ready = false;
     RunBufs rb{};
@@ -251,6 +254,9 @@ int dsg_upload_csr(dsg_ctx *ctx, int64_t n, const int64_t *offsets, const int32_
         if (G->adj) cudaFreeAsync(G->adj, ctx->stream);
         if (G->items) cudaFreeAsync(G->items, ctx->stream);
         if (G->heavy_mem) cudaFreeAsync(G->heavy_mem, ctx->stream);
+        if (G->ooff) cudaFreeAsync(G->ooff, ctx->stream);
+        if (G->oadj) cudaFreeAsync(G->oadj, ctx->stream);
+        if (G->hub) cudaFreeAsync(G->hub, ctx->stream);
         cudaStreamSynchronize(ctx->stream);
         delete G;
         return code;
@@ -288,11 +294,19 @@ int dsg_upload_csr(dsg_ctx *ctx, int64_t n, const int64_t *offsets, const int32_
     for (int i = 0; i < 5; ++i)
         if (h_err[i]) return bail(fail(ctx, DSG_ERR_INVALID, "invalid graph: %s", what[i]));
     G->g.max_degree = (int64_t)h_maxdeg;
-    // edge-scan tile schedule
+    // degree-oriented copy for the sorting edge scan, and the chunk schedule
+    // of its vertices of large out-degree
+    if ((e = build_orientation(G->g, ctx->stream, &G->ooff, &G->oadj, &G->hub, &G->g.n_hub)) != cudaSuccess)
+        return bail(cuda_fail(ctx, e, "orientation"));
+    G->g.ooff = G->ooff;
+    G->g.oadj = G->oadj;
+    G->g.hub_id = G->hub;
     void *tmp = nullptr;
     const size_t tmp_bytes = (size_t)schedule_tmp_count(n) * sizeof(int64_t);
     if ((e = cudaMallocAsync(&tmp, tmp_bytes, ctx->stream)) != cudaSuccess) return bail(cuda_fail(ctx, e, "schedule scratch"));
-    e = build_schedule(G->g, tmp, tmp_bytes, ctx->stream, &G->g.n_items, &G->g.n_heavy, &G->items, &G->heavy_mem);
+    GraphDev og = G->g;
+    og.off = G->ooff;
+    e = build_schedule(og, tmp, tmp_bytes, ctx->stream, &G->g.n_items, &G->g.n_heavy, &G->items, &G->heavy_mem);
     cudaFreeAsync(tmp, ctx->stream);
     if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "schedule"));
     G->g.items = G->items;
@@ -322,6 +336,9 @@ void dsg_free_graph(dsg_graph *G)
     cudaFreeAsync(G->adj, ctx->stream);
     if (G->items) cudaFreeAsync(G->items, ctx->stream);
     if (G->heavy_mem) cudaFreeAsync(G->heavy_mem, ctx->stream);
+    if (G->ooff) cudaFreeAsync(G->ooff, ctx->stream);
+    if (G->oadj) cudaFreeAsync(G->oadj, ctx->stream);
+    if (G->hub) cudaFreeAsync(G->hub, ctx->stream);
     if (G->rb_mem) cudaFreeAsync(G->rb_mem, ctx->stream);
     if (G->rb.trace) cudaFreeAsync(G->rb.trace, ctx->stream);
     if (G->npass_log) cudaFreeAsync(G->npass_log, ctx->stream);
@@ -422,7 +439,9 @@ int dsg_run(dsg_graph *G, int variant, int32_t T, int64_t eps_num, int64_t eps_d
             }
             {
                 PhaseTimer pt(ctx, DSG_PHASE_SORT);
-                for (int k = 0; k < kMaxPasses; ++k) CK(launch_radix_pass(G->g, b, k, t, s), "radix pass");
+                CK(launch_asum_single_pass(G->g, b, s), "digit sums");
+                for (int k = 0; k < kMaxPasses; ++k)
+                    CK(launch_radix_pass(G->g, b, k, t, s, nullptr, true, true), "radix pass");
             }
             {
                 PhaseTimer pt(ctx, DSG_PHASE_OTHER);
@@ -430,8 +449,10 @@ int dsg_run(dsg_graph *G, int variant, int32_t T, int64_t eps_num, int64_t eps_d
             }
             ctx->launches[DSG_PHASE_OTHER] += 3;
             ctx->launches[DSG_PHASE_EDGE_SCAN] += 1;
-            ctx->launches[DSG_PHASE_SORT] += kMaxPasses;
-            ctx->bytes[DSG_PHASE_EDGE_SCAN] += 16 * m + 16 * n;
+            ctx->launches[DSG_PHASE_SORT] += kMaxPasses + 1;
+            // oriented arcs (4m) + one target load per arc (4m) + oriented
+            // offsets (8n) + own loads (4n) + A (4n)
+            ctx->bytes[DSG_PHASE_EDGE_SCAN] += 8 * m + 16 * n;
         }
     } else {
         PhaseTimer pt(ctx, DSG_PHASE_OTHER);

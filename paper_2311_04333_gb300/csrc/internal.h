@@ -12,6 +12,10 @@ namespace dsg {
 // of 32 consecutive ids by single warps, without a list.
 constexpr int64_t kHeavyDeg = 1024;
 constexpr int kChunk = 1024;
+// degree orientation: at most kHubs largest-degree vertices get a hub slot;
+// oriented arc targets that are hubs are stored as kHubBit | slot
+constexpr int kHubs = 4096;
+constexpr uint32_t kHubBit = 0x80000000u;
 
 struct WorkItem {
     int64_t a0;      // first arc of the chunk
@@ -80,6 +84,11 @@ struct GraphDev {
     int64_t n_heavy;
     uint32_t *heavy_acc;     // [n_heavy]
     uint32_t *heavy_done;    // [n_heavy]
+    // degree-oriented copy used by the sorting edge scan
+    const int64_t *ooff;     // [n + 1]
+    const uint32_t *oadj;    // [m], targets (hub targets encoded)
+    const uint32_t *hub_id;  // [n_hub]
+    int64_t n_hub;
 };
 
 struct RunBufs {
@@ -111,12 +120,18 @@ cudaError_t launch_plan(const GraphDev &g, RunBufs &b, int t, cudaStream_t s);
 cudaError_t launch_edge_scan(const GraphDev &g, RunBufs &b, int grid, cudaStream_t s);
 // pass k of the radix sort of (key, A); pass 0 reads key0 (default: the
 // loads) and, if update_loads, writes loads += A.
+// accumulate: pass 0 also reduces the width (max A) and, when it is not the
+// last pass, the per-digit sums of A for the last pass.
 cudaError_t launch_radix_pass(const GraphDev &g, RunBufs &b, int k, int t, cudaStream_t s,
-                              const uint32_t *key0 = nullptr, bool update_loads = true);
+                              const uint32_t *key0 = nullptr, bool update_loads = true,
+                              bool accumulate = false);
 cudaError_t launch_snapshot(const GraphDev &g, RunBufs &b, cudaStream_t s);
 cudaError_t launch_best_set(const GraphDev &g, RunBufs &b, int32_t *set_dev, cudaStream_t s,
                             int *launches);
 cudaError_t launch_loads_out(const GraphDev &g, RunBufs &b, int64_t *dst, cudaStream_t s);
+cudaError_t build_orientation(GraphDev &g, cudaStream_t s, int64_t **ooff_out, uint32_t **oadj_out,
+                              uint32_t **hub_out, int64_t *n_hub_out);
+cudaError_t launch_asum_single_pass(const GraphDev &g, RunBufs &b, cudaStream_t s);
 cudaError_t launch_max_u64_of_i64(const int64_t *src, int64_t n, unsigned long long *dst,
                                   int *neg_flag, cudaStream_t s);
 cudaError_t launch_degree_max(const int64_t *off, int64_t n, unsigned long long *dst, cudaStream_t s);

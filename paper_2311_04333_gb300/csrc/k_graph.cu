@@ -165,6 +165,206 @@ cudaError_t build_schedule(GraphDev &g, void *tmp, size_t tmp_bytes, cudaStream_
     return cudaGetLastError();
 }
 
+// ============================================================ generic scan
+// exclusive scan of int64[count] in place (multi-block): per-chunk sums,
+// a single-block scan of the chunk sums, then per-chunk rescans with base.
+constexpr int kScanChunk = 4096;
+constexpr int kScanPer = kScanChunk / 256;
+
+__global__ void k_scan_chunksum(const int64_t *__restrict__ x, int64_t count, int64_t *sums)
+{
+    __shared__ unsigned long long red[33];
+    const int64_t b = (int64_t)blockIdx.x * kScanChunk + threadIdx.x * kScanPer;
+    uint64_t t = 0;
+    for (int i = 0; i < kScanPer; ++i)
+        if (b + i < count) t += (uint64_t)x[b + i];
+    uint64_t tot;
+    block_excl_sum_u64(t, red, &tot);
+    if (threadIdx.x == 0) sums[blockIdx.x] = (int64_t)tot;
+}
+
+__global__ void k_scan_apply(int64_t *x, int64_t count, const int64_t *base)
+{
+    __shared__ unsigned long long red[33];
+    const int64_t b = (int64_t)blockIdx.x * kScanChunk + threadIdx.x * kScanPer;
+    int64_t v[kScanPer];
+    uint64_t t = 0;
+    for (int i = 0; i < kScanPer; ++i) {
+        v[i] = (b + i < count) ? x[b + i] : 0;
+        t += (uint64_t)v[i];
+    }
+    uint64_t tot;
+    int64_t run = base[blockIdx.x] + (int64_t)block_excl_sum_u64(t, red, &tot);
+    for (int i = 0; i < kScanPer; ++i) {
+        if (b + i < count) x[b + i] = run;
+        run += v[i];
+    }
+}
+
+int64_t scan_tmp_count(int64_t count) { return (count + kScanChunk - 1) / kScanChunk + 2; }
+
+// x[count] -> exclusive prefix sums; *total_dev receives the sum.
+cudaError_t scan_exclusive_i64(int64_t *x, int64_t count, int64_t *total_dev, int64_t *tmp,
+                               cudaStream_t s)
+{
+    const int64_t nch = (count + kScanChunk - 1) / kScanChunk;
+    if (nch == 0) {
+        cudaMemsetAsync(total_dev, 0, sizeof(int64_t), s);
+        return cudaGetLastError();
+    }
+    k_scan_chunksum<<<(unsigned)nch, 256, 0, s>>>(x, count, tmp);
+    k_scan_single<<<1, 1024, 0, s>>>(tmp, nch, total_dev);
+    k_scan_apply<<<(unsigned)nch, 256, 0, s>>>(x, count, tmp);
+    return cudaGetLastError();
+}
+
+// ============================================================ degree orientation
+// Each undirected edge {u, w} is stored once, at the endpoint with the
+// smaller (degree, id); the other endpoint is the arc's target.  Targets
+// among the hubs (the at most kHubs vertices of largest degree, chosen by a
+// degree threshold) are encoded as kHubBit | hub slot, slots in id order.
+
+__global__ void k_count_ge(const int64_t *__restrict__ off, int64_t n, int64_t D,
+                           unsigned long long *cnt)
+{
+    unsigned long long c = 0;
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x)
+        c += (off[v + 1] - off[v]) >= D;
+    c = __reduce_add_sync(kFull, (unsigned)c);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(cnt, c);
+}
+
+__global__ void k_hub_flags(const int64_t *__restrict__ off, int64_t n, int64_t D, int64_t *flag)
+{
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x)
+        flag[v] = (off[v + 1] - off[v]) >= D;
+}
+
+// flag[] holds exclusive slot offsets now; hubs are the vertices whose degree
+// passes the threshold
+__global__ void k_hub_slots(const int64_t *__restrict__ off, int64_t n, int64_t D,
+                            const int64_t *slot_pre, int32_t *slot_of, uint32_t *hub_id)
+{
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        const bool hub = (off[v + 1] - off[v]) >= D;
+        slot_of[v] = hub ? (int32_t)slot_pre[v] : -1;
+        if (hub) hub_id[slot_pre[v]] = (uint32_t)v;
+    }
+}
+
+__device__ __forceinline__ bool oriented_keep(int64_t du, uint32_t u, int64_t dw, uint32_t w)
+{
+    return dw > du || (dw == du && w > u);
+}
+
+// warp per vertex: out-degree in the oriented graph
+__global__ void k_orient_count(const int64_t *__restrict__ off, const int32_t *__restrict__ adj,
+                               int64_t n, int64_t *ocnt)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t u = wid; u < n; u += nw) {
+        const int64_t s = off[u], e = off[u + 1], du = e - s;
+        uint32_t c = 0;
+        for (int64_t j = s + lane; j < e; j += 32) {
+            const uint32_t w = (uint32_t)adj[j];
+            c += oriented_keep(du, (uint32_t)u, off[w + 1] - off[w], w);
+        }
+        c = __reduce_add_sync(kFull, c);
+        if (lane == 0) ocnt[u] = c;
+    }
+}
+
+// warp per vertex: write the kept targets in list order, hub targets encoded
+__global__ void k_orient_fill(const int64_t *__restrict__ off, const int32_t *__restrict__ adj,
+                              int64_t n, const int64_t *__restrict__ ooff,
+                              const int32_t *__restrict__ slot_of, uint32_t *oadj)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t u = wid; u < n; u += nw) {
+        const int64_t s = off[u], e = off[u + 1], du = e - s;
+        int64_t o = ooff[u];
+        for (int64_t j0 = s; j0 < e; j0 += 32) {
+            const int64_t j = j0 + lane;
+            bool keep = false;
+            uint32_t w = 0;
+            if (j < e) {
+                w = (uint32_t)adj[j];
+                keep = oriented_keep(du, (uint32_t)u, off[w + 1] - off[w], w);
+            }
+            const uint32_t m = __ballot_sync(kFull, keep);
+            if (keep) {
+                const int32_t sl = slot_of[w];
+                oadj[o + __popc(m & lanemask_lt())] = sl >= 0 ? (kHubBit | (uint32_t)sl) : w;
+            }
+            o += __popc(m);
+        }
+    }
+}
+
+// Builds ooff, oadj and hub_id (allocated here, stream-ordered).
+cudaError_t build_orientation(GraphDev &g, cudaStream_t s, int64_t **ooff_out, uint32_t **oadj_out,
+                              uint32_t **hub_out, int64_t *n_hub_out)
+{
+    const int64_t n = g.n;
+    cudaError_t e;
+    const int grid = (int)imin64((n + 255) / 256, 152 * 16);
+    // hub threshold: the smallest D >= 2 with #{deg >= D} <= kHubs
+    unsigned long long *cnt = nullptr;
+    int64_t *tmp = nullptr, *flag = nullptr;
+    int32_t *slot_of = nullptr;
+    const int64_t ntmp = scan_tmp_count(n + 1);
+    if ((e = cudaMallocAsync((void **)&cnt, 8, s)) != cudaSuccess) return e;
+    if ((e = cudaMallocAsync((void **)&tmp, 8 * (size_t)(ntmp + 2), s)) != cudaSuccess) return e;
+    if ((e = cudaMallocAsync((void **)&flag, 8 * (size_t)(n + 1), s)) != cudaSuccess) return e;
+    if ((e = cudaMallocAsync((void **)&slot_of, 4 * (size_t)n, s)) != cudaSuccess) return e;
+    int64_t lo = 2, hi = g.max_degree + 1;            // count(deg >= hi) == 0
+    while (lo < hi) {
+        const int64_t mid = lo + (hi - lo) / 2;
+        unsigned long long h = 0;
+        cudaMemsetAsync(cnt, 0, 8, s);
+        k_count_ge<<<grid, 256, 0, s>>>(g.off, n, mid, cnt);
+        cudaMemcpyAsync(&h, cnt, 8, cudaMemcpyDeviceToHost, s);
+        if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+        if ((int64_t)h <= kHubs) hi = mid; else lo = mid + 1;
+    }
+    const int64_t D = lo;
+    k_hub_flags<<<grid, 256, 0, s>>>(g.off, n, D, flag);
+    int64_t *total = tmp + ntmp;
+    if ((e = scan_exclusive_i64(flag, n, total, tmp, s)) != cudaSuccess) return e;
+    int64_t n_hub = 0;
+    cudaMemcpyAsync(&n_hub, total, 8, cudaMemcpyDeviceToHost, s);
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+    uint32_t *hub = nullptr;
+    if ((e = cudaMallocAsync((void **)&hub, 4 * (size_t)imax64(n_hub, 1), s)) != cudaSuccess) return e;
+    k_hub_slots<<<grid, 256, 0, s>>>(g.off, n, D, flag, slot_of, hub);
+    // oriented offsets
+    const int wgrid = (int)imin64((n * 32 + 255) / 256, 152 * 32);
+    k_orient_count<<<wgrid, 256, 0, s>>>(g.off, g.adj, n, flag);
+    cudaMemsetAsync(flag + n, 0, 8, s);
+    if ((e = scan_exclusive_i64(flag, n + 1, total, tmp, s)) != cudaSuccess) return e;
+    int64_t oarcs = 0;
+    cudaMemcpyAsync(&oarcs, total, 8, cudaMemcpyDeviceToHost, s);
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+    uint32_t *oadj = nullptr;
+    if ((e = cudaMallocAsync((void **)&oadj, 4 * (size_t)imax64(oarcs, 1), s)) != cudaSuccess) return e;
+    k_orient_fill<<<wgrid, 256, 0, s>>>(g.off, g.adj, n, flag, slot_of, oadj);
+    cudaFreeAsync(cnt, s);
+    cudaFreeAsync(tmp, s);
+    cudaFreeAsync(slot_of, s);
+    *ooff_out = flag;         // n + 1 exclusive prefix sums = oriented offsets
+    *oadj_out = oadj;
+    *hub_out = hub;
+    *n_hub_out = n_hub;
+    return cudaGetLastError();
+}
+
 // ============================================================ reductions
 
 __global__ void k_max_i64(const int64_t *__restrict__ src, int64_t n, unsigned long long *dst, int *neg)

@@ -101,16 +101,22 @@ cudaError_t launch_plan(const GraphDev &, RunBufs &b, int t, cudaStream_t s)
 }
 
 // ============================================================ edge scan
-// Warp-centric, no block barriers.  Work units come from an atomic dispenser:
-//   units [0, n_items): one chunk of kChunk arcs of a heavy vertex
-//     (degree > kHeavyDeg); per-vertex totals meet in an atomic accumulator
-//     and the warp finishing the last chunk writes A[u];
-//   units after that: a light group of 32 consecutive vertices, one per lane.
-//     Vertices of degree >= kMidDeg are taken one at a time by the whole warp;
-//     the arcs of the smaller ones are packed across the lanes, each arc
-//     finding its source lane by a 5-step shuffle binary search.
-// Adjacency is streamed (L1 no-allocate, L2 evict-first) so that it does not
-// evict the gathered loads; gathers go through L1.
+// Runs on the degree-oriented copy of the graph: every undirected edge
+// {u, w} is stored once, at the endpoint u of smaller (degree, id), so the
+// edge is compared once: if w is later than u in the (load, id) order the
+// edge counts for u (a register count), otherwise for w (an atomic add to
+// A[w]; A is zeroed before the kernel).  Targets among the hubs (the
+// largest-degree vertices, most of the targets of a power-law graph) read
+// their load from a shared-memory copy and add into shared-memory counters
+// that are flushed once per block.
+// Work units come from an atomic dispenser:
+//   units [0, n_items): one chunk of kChunk oriented arcs of a vertex of
+//     out-degree > kHeavyDeg;
+//   units after that: a light group of 32 consecutive vertices, one per
+//     lane.  Out-degrees >= kMidDeg are taken one at a time by the whole
+//     warp; the arcs of the smaller ones are packed across the lanes, each
+//     arc finding its source lane by a 5-step shuffle binary search.
+// The group's lanes also accumulate the digit histograms of (l - lmin).
 
 constexpr int kEsThreads = 256;
 constexpr int kEsUnroll = 8;                    // rounds of 32 arcs in flight per warp
@@ -118,18 +124,16 @@ constexpr int64_t kMidDeg = 64;
 
 struct EsSmem {
     uint32_t hist[kMaxPasses][kBuckets];
-    unsigned long long asum[kBuckets];
+    uint32_t hub_l[kHubs];      // loads of the hubs
+    uint32_t hub_c[kHubs];      // counts for the hubs from this block
 };
 
-// per-thread run-length accumulation of the digit histograms
+// per-thread run-length accumulation of the digit count histograms
 struct HistAcc {
     uint32_t b[kMaxPasses], c[kMaxPasses];
-    uint32_t sb;
-    unsigned long long ss;
 };
 
-__device__ __forceinline__ void hist_add(HistAcc &h, EsSmem &S, uint32_t key, uint32_t a,
-                                         uint32_t lmin, int np)
+__device__ __forceinline__ void hist_add(HistAcc &h, EsSmem &S, uint32_t key, uint32_t lmin, int np)
 {
     const uint32_t x = key - lmin;
     #pragma unroll
@@ -144,13 +148,6 @@ __device__ __forceinline__ void hist_add(HistAcc &h, EsSmem &S, uint32_t key, ui
             h.c[p] += 1;
         }
     }
-    uint32_t dl = (x >> ((np - 1) * kRadixBits)) & (kBuckets - 1);
-    if (dl != h.sb) {
-        if (h.ss) atomicAdd(&S.asum[h.sb], h.ss);
-        h.sb = dl;
-        h.ss = 0;
-    }
-    h.ss += a;
 }
 
 __device__ __forceinline__ void hist_flush(HistAcc &h, EsSmem &S, int np)
@@ -158,7 +155,6 @@ __device__ __forceinline__ void hist_flush(HistAcc &h, EsSmem &S, int np)
     #pragma unroll
     for (int p = 0; p < kMaxPasses; ++p)
         if (p < np && h.c[p]) atomicAdd(&S.hist[p][h.b[p]], h.c[p]);
-    if (h.ss) atomicAdd(&S.asum[h.sb], h.ss);
 }
 
 __device__ __forceinline__ uint64_t policy_evict_first()
@@ -168,55 +164,74 @@ __device__ __forceinline__ uint64_t policy_evict_first()
     return pol;
 }
 
-// streamed read of one adjacency entry
-__device__ __forceinline__ int32_t ld_adj(const int32_t *p, uint64_t pol)
+// streamed read of one oriented arc
+__device__ __forceinline__ uint32_t ld_arc(const uint32_t *p, uint64_t pol)
 {
-    int32_t v;
+    uint32_t v;
     asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.b32 %0, [%1], %2;"
                  : "=r"(v) : "l"(p), "l"(pol));
     return v;
 }
 
-// (l[w], w) > (l[u], u): w is later than u in the (load, id) order
-__device__ __forceinline__ bool later(uint32_t lw, uint32_t w, uint32_t lu, uint32_t u)
+// load of an arc target: shared-memory copy for hubs, gather otherwise
+__device__ __forceinline__ uint32_t target_load(uint32_t t, const uint32_t *__restrict__ loads,
+                                                const EsSmem &S)
 {
-    return lw > lu || (lw == lu && w > u);
+    return (t & kHubBit) ? S.hub_l[t & ~kHubBit] : __ldg(loads + t);
 }
 
-// the warp counts the later neighbours among arcs [a0, a1) of vertex (lu, u);
-// returns this lane's share
-__device__ __forceinline__ uint32_t warp_count_arcs(const int32_t *__restrict__ adj,
-                                                    const uint32_t *__restrict__ loads, int64_t a0,
-                                                    int64_t a1, uint32_t lu, uint32_t u, int lane,
-                                                    uint64_t pol)
+// compare target t (load lw) with source (lu, u): count for u, or add one
+// to the target's count
+__device__ __forceinline__ void settle(uint32_t t, uint32_t lw, uint32_t lu, uint32_t u,
+                                       const uint32_t *__restrict__ hub_id, EsSmem &S,
+                                       uint32_t *A, uint32_t &c)
+{
+    const bool hub = t & kHubBit;
+    bool later = lw > lu;
+    if (lw == lu) {
+        const uint32_t w = hub ? __ldg(hub_id + (t & ~kHubBit)) : t;
+        later = w > u;
+    }
+    if (later) ++c;
+    else if (hub) atomicAdd(&S.hub_c[t & ~kHubBit], 1u);
+    else atomicAdd(&A[t], 1u);
+}
+
+// the warp processes oriented arcs [a0, a1) of source (lu, u); returns this
+// lane's count for u
+__device__ __forceinline__ uint32_t warp_arcs(const uint32_t *__restrict__ oadj,
+                                              const uint32_t *__restrict__ loads,
+                                              const uint32_t *__restrict__ hub_id, EsSmem &S,
+                                              uint32_t *A, int64_t a0, int64_t a1, uint32_t lu,
+                                              uint32_t u, int lane, uint64_t pol)
 {
     uint32_t c = 0;
     for (int64_t j0 = a0; j0 < a1; j0 += 32 * kEsUnroll) {
-        uint32_t w[kEsUnroll], lw[kEsUnroll];
+        uint32_t t[kEsUnroll], lw[kEsUnroll];
         #pragma unroll
         for (int k = 0; k < kEsUnroll; ++k) {
             const int64_t j = j0 + k * 32 + lane;
-            w[k] = j < a1 ? (uint32_t)ld_adj(adj + j, pol) : 0u;
+            t[k] = j < a1 ? ld_arc(oadj + j, pol) : 0u;
         }
         #pragma unroll
         for (int k = 0; k < kEsUnroll; ++k) {
             const int64_t j = j0 + k * 32 + lane;
-            lw[k] = j < a1 ? __ldg(loads + w[k]) : 0u;
+            lw[k] = j < a1 ? target_load(t[k], loads, S) : 0u;
         }
         #pragma unroll
         for (int k = 0; k < kEsUnroll; ++k) {
             const int64_t j = j0 + k * 32 + lane;
-            c += (j < a1) && later(lw[k], w[k], lu, u);
+            if (j < a1) settle(t[k], lw[k], lu, u, hub_id, S, A, c);
         }
     }
     return c;
 }
 
 __global__ void __launch_bounds__(kEsThreads, 4)
-k_edge_scan(const int64_t *__restrict__ off, const int32_t *__restrict__ adj,
+k_edge_scan(const int64_t *__restrict__ ooff, const uint32_t *__restrict__ oadj,
+            const uint32_t *__restrict__ hub_id, int64_t n_hub,
             const WorkItem *__restrict__ items, int64_t n_items, int64_t n,
-            const uint32_t *__restrict__ loads, uint32_t *__restrict__ A,
-            uint32_t *heavy_acc, uint32_t *heavy_done, Control *ctl)
+            const uint32_t *__restrict__ loads, uint32_t *A, Control *ctl)
 {
     __shared__ EsSmem S;
     const int tid = threadIdx.x, lane = tid & 31;
@@ -226,13 +241,13 @@ k_edge_scan(const int64_t *__restrict__ off, const int32_t *__restrict__ adj,
     const int64_t n_units = n_items + (n + 31) / 32;
 
     for (int i = tid; i < kMaxPasses * kBuckets; i += kEsThreads) (&S.hist[0][0])[i] = 0;
-    for (int i = tid; i < kBuckets; i += kEsThreads) S.asum[i] = 0;
+    for (int i = tid; i < n_hub; i += kEsThreads) {
+        S.hub_l[i] = loads[hub_id[i]];
+        S.hub_c[i] = 0;
+    }
     HistAcc h;
     #pragma unroll
     for (int p = 0; p < kMaxPasses; ++p) { h.b[p] = 0; h.c[p] = 0; }
-    h.sb = 0;
-    h.ss = 0;
-    uint32_t width = 0;
     __syncthreads();
 
     for (;;) {
@@ -242,27 +257,13 @@ k_edge_scan(const int64_t *__restrict__ off, const int32_t *__restrict__ adj,
         if ((int64_t)unit >= n_units) break;
 
         if ((int64_t)unit < n_items) {
-            // ---- one chunk of a heavy vertex
+            // ---- one chunk of a vertex of large out-degree
             const WorkItem it = items[unit];
-            const uint32_t u = it.u, hidx = it.info;
-            const int64_t s0 = off[u], s1 = off[u + 1];
-            const int64_t a1 = imin64(it.a0 + (int64_t)kChunk, s1);
-            const uint32_t lu = loads[u];
-            uint32_t c = warp_count_arcs(adj, loads, it.a0, a1, lu, u, lane, pol);
+            const uint32_t u = it.u;
+            const int64_t a1 = imin64(it.a0 + (int64_t)kChunk, ooff[u + 1]);
+            uint32_t c = warp_arcs(oadj, loads, hub_id, S, A, it.a0, a1, loads[u], u, lane, pol);
             c = __reduce_add_sync(kFull, c);
-            if (lane == 0) {
-                atomicAdd(&heavy_acc[hidx], c);
-                __threadfence();
-                const uint32_t nch = (uint32_t)((s1 - s0 + kChunk - 1) / kChunk);
-                if (atomicAdd(&heavy_done[hidx], 1u) == nch - 1) {
-                    __threadfence();
-                    const uint32_t total = atomicExch(&heavy_acc[hidx], 0u);
-                    heavy_done[hidx] = 0;
-                    A[u] = total;
-                    width = max(width, total);
-                    hist_add(h, S, lu, total, lmin, np);
-                }
-            }
+            if (lane == 0 && c) atomicAdd(&A[u], c);
             continue;
         }
 
@@ -270,28 +271,29 @@ k_edge_scan(const int64_t *__restrict__ off, const int32_t *__restrict__ adj,
         const int64_t g0 = ((int64_t)unit - n_items) * 32;
         const int64_t uu = g0 + lane;
         const bool valid = uu < n;
-        const int64_t s = valid ? off[uu] : 0;
+        const int64_t s = valid ? ooff[uu] : 0;
         int64_t e = __shfl_down_sync(kFull, s, 1);
-        if (lane == 31 || uu + 1 >= n) e = valid ? off[uu + 1] : 0;
+        if (lane == 31 || uu + 1 >= n) e = valid ? ooff[uu + 1] : 0;
         const int64_t deg = e - s;
         const bool heavy = deg > kHeavyDeg;
         const bool mid = !heavy && deg >= kMidDeg;
         const uint32_t lu = valid ? loads[uu] : 0u;
+        if (valid) hist_add(h, S, lu, lmin, np);
         uint32_t cnt = 0;
 
-        // vertices of medium degree: the whole warp, one at a time
+        // out-degree kMidDeg..kHeavyDeg: the whole warp, one vertex at a time
         uint32_t mm = __ballot_sync(kFull, mid);
         while (mm) {
             const int l = __ffs(mm) - 1;
             mm &= mm - 1;
             const int64_t vs = __shfl_sync(kFull, s, l), ve = __shfl_sync(kFull, e, l);
             const uint32_t vl = __shfl_sync(kFull, lu, l);
-            uint32_t c = warp_count_arcs(adj, loads, vs, ve, vl, (uint32_t)(g0 + l), lane, pol);
+            uint32_t c = warp_arcs(oadj, loads, hub_id, S, A, vs, ve, vl, (uint32_t)(g0 + l), lane, pol);
             c = __reduce_add_sync(kFull, c);
             if (lane == l) cnt = c;
         }
 
-        // small vertices: arcs packed across the lanes
+        // smaller out-degrees: arcs packed across the lanes
         const uint32_t sdeg = (valid && !heavy && !mid) ? (uint32_t)deg : 0u;
         uint32_t incl = sdeg;
         #pragma unroll
@@ -302,7 +304,7 @@ k_edge_scan(const int64_t *__restrict__ off, const int32_t *__restrict__ adj,
         const uint32_t total = __shfl_sync(kFull, incl, 31);
         const uint32_t start = incl - sdeg;
         for (uint32_t base = 0; base < total; base += 32 * kEsUnroll) {
-            uint32_t w[kEsUnroll], lw[kEsUnroll], sl_r[kEsUnroll];
+            uint32_t t[kEsUnroll], lw[kEsUnroll], sl_r[kEsUnroll];
             #pragma unroll
             for (int k = 0; k < kEsUnroll; ++k) {
                 const uint32_t j = base + k * 32 + lane;
@@ -315,19 +317,20 @@ k_edge_scan(const int64_t *__restrict__ off, const int32_t *__restrict__ adj,
                 const int64_t so = __shfl_sync(kFull, s, sl);
                 const uint32_t st = __shfl_sync(kFull, start, sl);
                 sl_r[k] = sl;
-                w[k] = j < total ? (uint32_t)ld_adj(adj + so + (j - st), pol) : 0u;
+                t[k] = j < total ? ld_arc(oadj + so + (j - st), pol) : 0u;
             }
             #pragma unroll
             for (int k = 0; k < kEsUnroll; ++k) {
                 const uint32_t j = base + k * 32 + lane;
-                lw[k] = j < total ? __ldg(loads + w[k]) : 0u;
+                lw[k] = j < total ? target_load(t[k], loads, S) : 0u;
             }
             #pragma unroll
             for (int k = 0; k < kEsUnroll; ++k) {
                 const uint32_t j = base + k * 32 + lane;
                 const uint32_t l_src = __shfl_sync(kFull, lu, sl_r[k]);
-                const bool cmp = j < total && later(lw[k], w[k], l_src, (uint32_t)(g0 + sl_r[k]));
-                const uint32_t C = __ballot_sync(kFull, cmp);
+                uint32_t one = 0;
+                if (j < total) settle(t[k], lw[k], l_src, (uint32_t)(g0 + sl_r[k]), hub_id, S, A, one);
+                const uint32_t C = __ballot_sync(kFull, one != 0);
                 const int jb = (int)(base + k * 32);
                 const int lo = max((int)start - jb, 0), hi = min((int)incl - jb, 32);
                 if (hi > lo) {
@@ -336,22 +339,16 @@ k_edge_scan(const int64_t *__restrict__ off, const int32_t *__restrict__ adj,
                 }
             }
         }
-        if (valid && !heavy) {
-            A[uu] = cnt;
-            width = max(width, cnt);
-            hist_add(h, S, lu, cnt, lmin, np);
-        }
+        if (valid && cnt) atomicAdd(&A[uu], cnt);
     }
 
     hist_flush(h, S, np);
-    width = __reduce_max_sync(kFull, width);
-    if (lane == 0 && width) atomicMax(&ctl->width, width);
     __syncthreads();
-    for (int i = tid; i < kBuckets; i += kEsThreads) {
+    for (int i = tid; i < kBuckets; i += kEsThreads)
         for (int p = 0; p < np; ++p)
             if (S.hist[p][i]) atomicAdd(&ctl->hist[p][i], S.hist[p][i]);
-        if (S.asum[i]) atomicAdd(&ctl->asum[i], S.asum[i]);
-    }
+    for (int i = tid; i < n_hub; i += kEsThreads)
+        if (S.hub_c[i]) atomicAdd(&A[hub_id[i]], S.hub_c[i]);
 }
 
 static int g_es_blocks_per_sm = -1;
@@ -368,8 +365,34 @@ int edge_scan_sm_count()
 
 cudaError_t launch_edge_scan(const GraphDev &g, RunBufs &b, int grid, cudaStream_t s)
 {
-    k_edge_scan<<<grid, kEsThreads, 0, s>>>(g.off, g.adj, g.items, g.n_items, g.n, b.loads, b.A,
-                                            g.heavy_acc, g.heavy_done, b.ctl);
+    cudaMemsetAsync(b.A, 0, sizeof(uint32_t) * (size_t)g.n, s);
+    k_edge_scan<<<grid, kEsThreads, 0, s>>>(g.ooff, g.oadj, g.hub_id, g.n_hub, g.items, g.n_items,
+                                            g.n, b.loads, b.A, b.ctl);
+    return cudaGetLastError();
+}
+
+// per-digit sums of A for a sort of a single pass (pass 0 accumulates them
+// itself when it is not the last pass)
+__global__ void k_asum_single_pass(const uint32_t *__restrict__ loads,
+                                   const uint32_t *__restrict__ A, int64_t n, Control *ctl)
+{
+    if (ctl->npass != 1) return;
+    __shared__ unsigned long long as[kBuckets];
+    const uint32_t lmin = ctl->lmin;
+    for (int i = threadIdx.x; i < kBuckets; i += blockDim.x) as[i] = 0;
+    __syncthreads();
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(&as[(loads[v] - lmin) & (kBuckets - 1)], (unsigned long long)A[v]);
+    __syncthreads();
+    for (int i = threadIdx.x; i < kBuckets; i += blockDim.x)
+        if (as[i]) atomicAdd(&ctl->asum[i], as[i]);
+}
+
+cudaError_t launch_asum_single_pass(const GraphDev &g, RunBufs &b, cudaStream_t s)
+{
+    const int grid = (int)imin64((g.n + 255) / 256, 152 * 4);
+    k_asum_single_pass<<<grid, 256, 0, s>>>(b.loads, b.A, g.n, b.ctl);
     return cudaGetLastError();
 }
 
@@ -386,6 +409,7 @@ struct PassSmem {
     unsigned long long gsum[kBuckets];
     unsigned long long dscan[kBuckets];
     unsigned long long dend[kBuckets];
+    unsigned long long asum_acc[kBuckets];
     unsigned long long red[33];
     Candidate cred[32];
     uint32_t tile;
@@ -403,7 +427,7 @@ k_radix_pass(const uint32_t *kin, const uint32_t *vin,
              uint32_t *__restrict__ kout, uint32_t *__restrict__ vout,
              uint32_t *loads_next, unsigned long long *status, unsigned long long *status_sum,
              Candidate *cand, int64_t ntiles, int64_t n, int64_t m, Control *ctl, int k, int t,
-             int64_t *trace)
+             int64_t *trace, int accumulate)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     PassSmem &S = *reinterpret_cast<PassSmem *>(smem_raw);
@@ -432,6 +456,7 @@ k_radix_pass(const uint32_t *kin, const uint32_t *vin,
         }
     }
     for (int i = tid; i < (kPassThreads / 32) * kBuckets; i += kPassThreads) (&S.wcnt[0][0])[i] = 0;
+    S.asum_acc[tid] = 0;
     __syncthreads();
     const uint32_t tile = S.tile;
     const int64_t tbase = (int64_t)tile * kPassTile;
@@ -439,6 +464,10 @@ k_radix_pass(const uint32_t *kin, const uint32_t *vin,
     // ---- load 16 rounds of 32 consecutive items per warp; warp-level stable ranks
     uint32_t key_r[kPassIpt], val_r[kPassIpt], dw_r[kPassIpt];
     uint32_t lmn = 0xffffffffu, lmx = 0;
+    const bool acc = accumulate && k == 0;
+    const int shift_last = ctl->shift[np - 1];
+    uint32_t amax = 0, rb = 0;
+    unsigned long long rs = 0;
     const int64_t wbase = tbase + warp * (32 * kPassIpt);
     #pragma unroll
     for (int r = 0; r < kPassIpt; ++r) {
@@ -453,6 +482,18 @@ k_radix_pass(const uint32_t *kin, const uint32_t *vin,
                 loads_next[idx] = nl;
                 lmn = min(lmn, nl);
                 lmx = max(lmx, nl);
+            }
+            if (acc) {
+                amax = max(amax, val);
+                if (!last) {
+                    const uint32_t dl = ((key - lmin) >> shift_last) & (kBuckets - 1);
+                    if (dl != rb) {
+                        if (rs) atomicAdd(&S.asum_acc[rb], rs);
+                        rb = dl;
+                        rs = 0;
+                    }
+                    rs += val;
+                }
             }
         }
         const uint32_t d = ((key - lmin) >> shift) & (kBuckets - 1);
@@ -472,12 +513,17 @@ k_radix_pass(const uint32_t *kin, const uint32_t *vin,
         val_r[r] = val;
         dw_r[r] = valid ? (d | ((before + rank) << 8)) : 0xffffffffu;
     }
+    if (acc && rs) atomicAdd(&S.asum_acc[rb], rs);
     if (k == 0 && loads_next) {
         lmn = __reduce_min_sync(kFull, lmn);
         lmx = __reduce_max_sync(kFull, lmx);
         if (lane == 0) { S.mn[warp] = lmn; S.mx[warp] = lmx; }
     }
     __syncthreads();
+    if (acc) {
+        amax = __reduce_max_sync(kFull, amax);
+        if (lane == 0 && amax) atomicMax(&ctl->width, amax);
+    }
     if (k == 0 && loads_next && tid == 0) {
         uint32_t a = 0xffffffffu, b = 0;
         for (int i = 0; i < kPassThreads / 32; ++i) { a = min(a, S.mn[i]); b = max(b, S.mx[i]); }
@@ -486,6 +532,7 @@ k_radix_pass(const uint32_t *kin, const uint32_t *vin,
             atomicMax(&ctl->mm_max[(t + 1) & 1], b);
         }
     }
+    if (acc && !last && S.asum_acc[tid]) atomicAdd(&ctl->asum[tid], S.asum_acc[tid]);
     // per-digit tile counts, exclusive per-warp prefixes, tile-local digit offsets
     uint32_t tcount;
     {
@@ -663,7 +710,7 @@ k_radix_pass(const uint32_t *kin, const uint32_t *vin,
 static bool g_pass_attr = false;
 
 cudaError_t launch_radix_pass(const GraphDev &g, RunBufs &b, int k, int t, cudaStream_t s,
-                              const uint32_t *key0, bool update_loads)
+                              const uint32_t *key0, bool update_loads, bool accumulate)
 {
     if (!g_pass_attr) {
         cudaFuncSetAttribute(k_radix_pass, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -676,7 +723,7 @@ cudaError_t launch_radix_pass(const GraphDev &g, RunBufs &b, int k, int t, cudaS
     k_radix_pass<<<(unsigned)b.ntiles, kPassThreads, sizeof(PassSmem), s>>>(
         kin, vin, b.keys[k & 1], b.vals[k & 1], update_loads ? b.loads : nullptr, b.status,
         b.status_sum, b.cand,
-        b.ntiles, g.n, g.arcs / 2, b.ctl, k, t, b.trace);
+        b.ntiles, g.n, g.arcs / 2, b.ctl, k, t, b.trace, accumulate ? 1 : 0);
     return cudaGetLastError();
 }
 

@@ -177,6 +177,6 @@ def test_profiling_stats(dsg, ctx):
     finally:
         dsg.dsg_set_profiling(ctx, False)
     st = dsg.dsg_get_stats(ctx, reset=True)
-    assert st["edge_scan"]["launches"] == 3 and st["sort"]["launches"] == 12
+    assert st["edge_scan"]["launches"] == 3 and st["sort"]["launches"] == 15
     assert st["edge_scan"]["ms"] > 0 and st["sort"]["ms"] > 0
-    assert st["edge_scan"]["bytes"] == 3 * (16 * g.m + 16 * g.n)
+    assert st["edge_scan"]["bytes"] == 3 * (8 * g.m + 16 * g.n)
