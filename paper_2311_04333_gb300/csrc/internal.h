@@ -10,11 +10,21 @@ namespace dsg {
 // Vertices of degree > kHeavyDeg are split into chunks of kChunk arcs, one
 // work item each (built at upload); all other vertices are taken in groups
 // of 32 consecutive ids by single warps, without a list.
+// Tuning knobs (compile-time; the defaults are the measured best on GB300).
+#ifndef DSG_HUBS
+#define DSG_HUBS 4096
+#endif
+#ifndef DSG_ES_UNROLL
+#define DSG_ES_UNROLL 8
+#endif
+#ifndef DSG_MID_DEG
+#define DSG_MID_DEG 64
+#endif
 constexpr int64_t kHeavyDeg = 1024;
 constexpr int kChunk = 1024;
 // degree orientation: at most kHubs largest-degree vertices get a hub slot;
 // oriented arc targets that are hubs are stored as kHubBit | slot
-constexpr int kHubs = 4096;
+constexpr int kHubs = DSG_HUBS;
 constexpr uint32_t kHubBit = 0x80000000u;
 
 struct WorkItem {

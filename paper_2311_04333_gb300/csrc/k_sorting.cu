@@ -119,13 +119,15 @@ cudaError_t launch_plan(const GraphDev &, RunBufs &b, int t, cudaStream_t s)
 // The group's lanes also accumulate the digit histograms of (l - lmin).
 
 constexpr int kEsThreads = 256;
-constexpr int kEsUnroll = 8;                    // rounds of 32 arcs in flight per warp
-constexpr int64_t kMidDeg = 64;
+constexpr int kEsUnroll = DSG_ES_UNROLL;        // rounds of 32 arcs in flight per warp
+constexpr int64_t kMidDeg = DSG_MID_DEG;
 
 struct EsSmem {
     uint32_t hist[kMaxPasses][kBuckets];
     uint32_t hub_l[kHubs];      // loads of the hubs
     uint32_t hub_c[kHubs];      // counts for the hubs from this block
+    // per warp: source lane (+1) of each of the 256 arcs of a packed batch
+    uint8_t srcmap[kEsThreads / 32][32 * kEsUnroll];
 };
 
 // per-thread run-length accumulation of the digit count histograms
@@ -303,40 +305,74 @@ k_edge_scan(const int64_t *__restrict__ ooff, const uint32_t *__restrict__ oadj,
         }
         const uint32_t total = __shfl_sync(kFull, incl, 31);
         const uint32_t start = incl - sdeg;
-        for (uint32_t base = 0; base < total; base += 32 * kEsUnroll) {
-            uint32_t t[kEsUnroll], lw[kEsUnroll], sl_r[kEsUnroll];
-            #pragma unroll
-            for (int k = 0; k < kEsUnroll; ++k) {
-                const uint32_t j = base + k * 32 + lane;
-                uint32_t sl = 0;
+        if (total) {
+            // arc j (packed index) of lane L's vertex is at oadj[sg + j + dofs_L]
+            const int64_t sg = __shfl_sync(kFull, s, 0);
+            const int32_t dofs = (int32_t)(s - sg) - (int32_t)start;
+            uint8_t *map = S.srcmap[tid >> 5];
+            uint32_t carry = 0;
+            for (uint32_t base = 0; base < total; base += 32 * kEsUnroll) {
+                // source map of this batch: mark first slots, then fill forward
+                reinterpret_cast<uint2 *>(map)[lane] = make_uint2(0u, 0u);
+                __syncwarp();
+                if (sdeg && start >= base && start < base + 32 * kEsUnroll)
+                    map[start - base] = (uint8_t)(lane + 1);
+                __syncwarp();
+                uint2 v = reinterpret_cast<uint2 *>(map)[lane];
+                uint32_t lm = 0;
                 #pragma unroll
-                for (int step = 16; step >= 1; step >>= 1) {
-                    const uint32_t x = __shfl_sync(kFull, incl, sl + step - 1);
-                    if (x <= j) sl += step;
+                for (int b = 0; b < 4; ++b) lm = max(lm, max((v.x >> (8 * b)) & 0xffu, (v.y >> (8 * b)) & 0xffu));
+                uint32_t im = lm;
+                #pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t y = __shfl_up_sync(kFull, im, o);
+                    if (lane >= o) im = max(im, y);
                 }
-                const int64_t so = __shfl_sync(kFull, s, sl);
-                const uint32_t st = __shfl_sync(kFull, start, sl);
-                sl_r[k] = sl;
-                t[k] = j < total ? ld_arc(oadj + so + (j - st), pol) : 0u;
-            }
-            #pragma unroll
-            for (int k = 0; k < kEsUnroll; ++k) {
-                const uint32_t j = base + k * 32 + lane;
-                lw[k] = j < total ? target_load(t[k], loads, S) : 0u;
-            }
-            #pragma unroll
-            for (int k = 0; k < kEsUnroll; ++k) {
-                const uint32_t j = base + k * 32 + lane;
-                const uint32_t l_src = __shfl_sync(kFull, lu, sl_r[k]);
-                uint32_t one = 0;
-                if (j < total) settle(t[k], lw[k], l_src, (uint32_t)(g0 + sl_r[k]), hub_id, S, A, one);
-                const uint32_t C = __ballot_sync(kFull, one != 0);
-                const int jb = (int)(base + k * 32);
-                const int lo = max((int)start - jb, 0), hi = min((int)incl - jb, 32);
-                if (hi > lo) {
-                    const uint32_t mhi = hi == 32 ? kFull : ((1u << hi) - 1u);
-                    cnt += __popc(C & mhi & ~((1u << lo) - 1u));
+                uint32_t cur = __shfl_up_sync(kFull, im, 1);
+                cur = max(lane ? cur : 0u, carry);
+                uint32_t nx = 0, ny = 0;
+                #pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    cur = max(cur, (v.x >> (8 * b)) & 0xffu);
+                    nx |= cur << (8 * b);
                 }
+                #pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    cur = max(cur, (v.y >> (8 * b)) & 0xffu);
+                    ny |= cur << (8 * b);
+                }
+                reinterpret_cast<uint2 *>(map)[lane] = make_uint2(nx, ny);
+                carry = __shfl_sync(kFull, cur, 31);
+                __syncwarp();
+                uint32_t t[kEsUnroll], lw[kEsUnroll], sl_r[kEsUnroll];
+                #pragma unroll
+                for (int k = 0; k < kEsUnroll; ++k) {
+                    const uint32_t j = base + k * 32 + lane;
+                    const uint32_t sl = (uint32_t)map[k * 32 + lane] - 1u;
+                    const int32_t dsrc = __shfl_sync(kFull, dofs, sl & 31);
+                    sl_r[k] = sl & 31;
+                    t[k] = j < total ? ld_arc(oadj + sg + (int64_t)j + dsrc, pol) : 0u;
+                }
+                #pragma unroll
+                for (int k = 0; k < kEsUnroll; ++k) {
+                    const uint32_t j = base + k * 32 + lane;
+                    lw[k] = j < total ? target_load(t[k], loads, S) : 0u;
+                }
+                #pragma unroll
+                for (int k = 0; k < kEsUnroll; ++k) {
+                    const uint32_t j = base + k * 32 + lane;
+                    const uint32_t l_src = __shfl_sync(kFull, lu, sl_r[k]);
+                    uint32_t one = 0;
+                    if (j < total) settle(t[k], lw[k], l_src, (uint32_t)(g0 + sl_r[k]), hub_id, S, A, one);
+                    const uint32_t C = __ballot_sync(kFull, one != 0);
+                    const int jb = (int)(base + k * 32);
+                    const int lo = max((int)start - jb, 0), hi = min((int)incl - jb, 32);
+                    if (hi > lo) {
+                        const uint32_t mhi = hi == 32 ? kFull : ((1u << hi) - 1u);
+                        cnt += __popc(C & mhi & ~((1u << lo) - 1u));
+                    }
+                }
+                __syncwarp();
             }
         }
         if (valid && cnt) atomicAdd(&A[uu], cnt);
@@ -398,9 +434,14 @@ cudaError_t launch_asum_single_pass(const GraphDev &g, RunBufs &b, cudaStream_t 
 
 // ============================================================ radix passes
 
+constexpr int kPassTilePad = kPassTile + kPassTile / 32;
+// one pad word every 32 entries: thread-contiguous and striped accesses
+// to the tile are both free of bank conflicts
+__device__ __forceinline__ uint32_t pad(uint32_t lp) { return lp + (lp >> 5); }
+
 struct PassSmem {
-    uint32_t keys[kPassTile];
-    uint32_t vals[kPassTile];
+    uint32_t keys[kPassTilePad];
+    uint32_t vals[kPassTilePad];
     uint32_t wcnt[kPassThreads / 32][kBuckets];
     uint32_t toff[kBuckets + 1];
     uint32_t boff[kBuckets];
@@ -422,7 +463,7 @@ __device__ __forceinline__ unsigned long long status_word(uint32_t epoch, uint64
     return ((unsigned long long)epoch << 48) | (flag << 46) | (cnt & ((1ull << 46) - 1));
 }
 
-__global__ void __launch_bounds__(kPassThreads)
+__global__ void __launch_bounds__(kPassThreads, 4)
 k_radix_pass(const uint32_t *kin, const uint32_t *vin,
              uint32_t *__restrict__ kout, uint32_t *__restrict__ vout,
              uint32_t *loads_next, unsigned long long *status, unsigned long long *status_sum,
@@ -472,11 +513,15 @@ k_radix_pass(const uint32_t *kin, const uint32_t *vin,
     #pragma unroll
     for (int r = 0; r < kPassIpt; ++r) {
         const int64_t idx = wbase + r * 32 + lane;
+        key_r[r] = idx < n ? kin[idx] : 0u;
+        val_r[r] = idx < n ? vin[idx] : 0u;
+    }
+    #pragma unroll
+    for (int r = 0; r < kPassIpt; ++r) {
+        const int64_t idx = wbase + r * 32 + lane;
         const bool valid = idx < n;
-        uint32_t key = 0, val = 0;
+        const uint32_t key = key_r[r], val = val_r[r];
         if (valid) {
-            key = kin[idx];
-            val = vin[idx];
             if (k == 0 && loads_next) {
                 const uint32_t nl = key + val;
                 loads_next[idx] = nl;
@@ -509,8 +554,6 @@ k_radix_pass(const uint32_t *kin, const uint32_t *vin,
         __syncwarp();
         if (valid && (peers >> lane) == 1u) S.wcnt[warp][d] = before + __popc(peers);
         __syncwarp();
-        key_r[r] = key;
-        val_r[r] = val;
         dw_r[r] = valid ? (d | ((before + rank) << 8)) : 0xffffffffu;
     }
     if (acc && rs) atomicAdd(&S.asum_acc[rb], rs);
@@ -557,8 +600,8 @@ k_radix_pass(const uint32_t *kin, const uint32_t *vin,
         if (dw_r[r] != 0xffffffffu) {
             const uint32_t d = dw_r[r] & 0xffu, wr = dw_r[r] >> 8;
             const uint32_t lp = S.toff[d] + S.wcnt[warp][d] + wr;
-            S.keys[lp] = key_r[r];
-            S.vals[lp] = val_r[r];
+            S.keys[pad(lp)] = key_r[r];
+            S.vals[pad(lp)] = val_r[r];
         }
     }
     __syncthreads();
@@ -571,7 +614,7 @@ k_radix_pass(const uint32_t *kin, const uint32_t *vin,
         #pragma unroll
         for (int i = 0; i < kPassIpt; ++i) {
             const uint32_t lp = tid * kPassIpt + i;
-            const uint64_t v = lp < tn ? S.vals[lp] : 0;
+            const uint64_t v = lp < tn ? S.vals[pad(lp)] : 0;
             scan_r[i] = run;          // exclusive within thread
             run += v;
         }
@@ -582,9 +625,9 @@ k_radix_pass(const uint32_t *kin, const uint32_t *vin,
             const uint32_t lp = tid * kPassIpt + i;
             scan_r[i] += ex;          // exclusive prefix over the sorted tile
             if (lp < tn) {
-                const uint32_t d = ((S.keys[lp] - lmin) >> shift) & (kBuckets - 1);
+                const uint32_t d = ((S.keys[pad(lp)] - lmin) >> shift) & (kBuckets - 1);
                 if (lp == S.toff[d]) S.dscan[d] = scan_r[i];
-                if (lp + 1 == S.toff[d + 1] || lp + 1 == tn) S.dend[d] = scan_r[i] + S.vals[lp];
+                if (lp + 1 == S.toff[d + 1] || lp + 1 == tn) S.dend[d] = scan_r[i] + S.vals[pad(lp)];
             }
         }
         __syncthreads();
@@ -640,12 +683,12 @@ k_radix_pass(const uint32_t *kin, const uint32_t *vin,
         for (int r = 0; r < kPassIpt; ++r) {
             const uint32_t lp = r * kPassThreads + tid;
             if (lp < tn) {
-                const uint32_t key = S.keys[lp];
+                const uint32_t key = S.keys[pad(lp)];
                 const uint32_t d = ((key - lmin) >> shift) & (kBuckets - 1);
                 const uint32_t gp = S.gbase[d] + (lp - S.toff[d]);
                 if (gp < (uint64_t)n) {
                     kout[gp] = key;
-                    vout[gp] = S.vals[lp];
+                    vout[gp] = S.vals[pad(lp)];
                 } else {
                     set_error(ctl, 3, 300 + k);
                 }
@@ -660,7 +703,7 @@ k_radix_pass(const uint32_t *kin, const uint32_t *vin,
     for (int i = 0; i < kPassIpt; ++i) {
         const uint32_t lp = tid * kPassIpt + i;
         if (lp < tn) {
-            const uint32_t key = S.keys[lp];
+            const uint32_t key = S.keys[pad(lp)];
             const uint32_t d = ((key - lmin) >> shift) & (kBuckets - 1);
             const int64_t pos = (int64_t)S.gbase[d] + (lp - S.toff[d]);
             const uint64_t prefix = S.gsum[d] + (scan_r[i] - S.dscan[d]);
