@@ -294,6 +294,7 @@ int dsg_upload_csr(dsg_ctx *ctx, int64_t n, const int64_t *offsets, const int32_
     for (int i = 0; i < 5; ++i)
         if (h_err[i]) return bail(fail(ctx, DSG_ERR_INVALID, "invalid graph: %s", what[i]));
     G->g.max_degree = (int64_t)h_maxdeg;
+    G->g.sorted = h_err[5] ? 0 : 1;
     // degree-oriented copy for the sorting edge scan, and the chunk schedule
     // of its vertices of large out-degree
     if ((e = build_orientation(G->g, ctx->stream, &G->ooff, &G->oadj, &G->hub, &G->g.n_hub)) != cudaSuccess)
@@ -437,6 +438,7 @@ int dsg_run(dsg_graph *G, int variant, int32_t T, int64_t eps_num, int64_t eps_d
                 PhaseTimer pt(ctx, DSG_PHASE_EDGE_SCAN);
                 CK(launch_edge_scan(G->g, b, es_grid, s), "edge scan");
             }
+            ctx->launches[DSG_PHASE_EDGE_SCAN] += 1;   // the equal-loads variant (one of the two exits at once)
             {
                 PhaseTimer pt(ctx, DSG_PHASE_SORT);
                 CK(launch_asum_single_pass(G->g, b, s), "digit sums");

@@ -12,7 +12,7 @@ namespace dsg {
 // of 32 consecutive ids by single warps, without a list.
 // Tuning knobs (compile-time; the defaults are the measured best on GB300).
 #ifndef DSG_HUBS
-#define DSG_HUBS 4096
+#define DSG_HUBS 2048
 #endif
 #ifndef DSG_ES_UNROLL
 #define DSG_ES_UNROLL 8
@@ -64,6 +64,7 @@ struct Control {
     int32_t err_where;
     // per-iteration plan (written by the plan kernel)
     uint32_t lmin;           // minimum load at the start of the iteration
+    uint32_t lrange;         // max - min load at the start of the iteration
     int32_t npass;           // number of radix passes (>= 1)
     int32_t shift[kMaxPasses];
     uint32_t epoch;          // look-back epoch of pass 0 of this iteration
@@ -99,6 +100,7 @@ struct GraphDev {
     const uint32_t *oadj;    // [m], targets (hub targets encoded)
     const uint32_t *hub_id;  // [n_hub]
     int64_t n_hub;
+    int sorted;              // every adjacency list is strictly ascending
 };
 
 struct RunBufs {

@@ -34,6 +34,7 @@ __global__ void k_validate(const int64_t *__restrict__ off, const int32_t *__res
             const int32_t w = adj[j];
             if (w < 0 || w >= n) { atomicExch(&err[1], 1); continue; }
             if (w == (int32_t)u) atomicExch(&err[2], 1);
+            if (j > s && adj[j - 1] >= w) atomicExch(&err[5], 1);   // not strictly ascending
             if (full) {
                 if (j > s && adj[j - 1] >= w) atomicExch(&err[3], 1);
                 if (!has_arc(off, adj, w, (int32_t)u)) atomicExch(&err[4], 1);

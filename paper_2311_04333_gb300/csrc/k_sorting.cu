@@ -72,6 +72,7 @@ __global__ void k_plan(Control *ctl, int t)
     for (int i = tid; i < kBuckets; i += blockDim.x) ctl->asum[i] = 0;
     if (tid == 0) {
         ctl->lmin = lmin;
+        ctl->lrange = range;
         ctl->npass = np;
         for (int p = 0; p < kMaxPasses; ++p) ctl->shift[p] = p * kRadixBits;
         ctl->item_ctr = 0;
@@ -121,11 +122,14 @@ cudaError_t launch_plan(const GraphDev &, RunBufs &b, int t, cudaStream_t s)
 constexpr int kEsThreads = 256;
 constexpr int kEsUnroll = DSG_ES_UNROLL;        // rounds of 32 arcs in flight per warp
 constexpr int64_t kMidDeg = DSG_MID_DEG;
+static_assert(kEsUnroll >= 4 && kEsUnroll % 4 == 0, "source map words hold 4 slots");
+constexpr int kMapWords = kEsUnroll / 4;        // source-map words per lane
 
 struct EsSmem {
     uint32_t hist[kMaxPasses][kBuckets];
     uint32_t hub_l[kHubs];      // loads of the hubs
     uint32_t hub_c[kHubs];      // counts for the hubs from this block
+    uint32_t hub_v[kHubs];      // ids of the hubs
     // per warp: source lane (+1) of each of the 256 arcs of a packed batch
     uint8_t srcmap[kEsThreads / 32][32 * kEsUnroll];
 };
@@ -191,7 +195,7 @@ __device__ __forceinline__ void settle(uint32_t t, uint32_t lw, uint32_t lu, uin
     const bool hub = t & kHubBit;
     bool later = lw > lu;
     if (lw == lu) {
-        const uint32_t w = hub ? __ldg(hub_id + (t & ~kHubBit)) : t;
+        const uint32_t w = hub ? S.hub_v[t & ~kHubBit] : t;
         later = w > u;
     }
     if (later) ++c;
@@ -233,9 +237,10 @@ __global__ void __launch_bounds__(kEsThreads, 4)
 k_edge_scan(const int64_t *__restrict__ ooff, const uint32_t *__restrict__ oadj,
             const uint32_t *__restrict__ hub_id, int64_t n_hub,
             const WorkItem *__restrict__ items, int64_t n_items, int64_t n,
-            const uint32_t *__restrict__ loads, uint32_t *A, Control *ctl)
+            const uint32_t *__restrict__ loads, uint32_t *A, Control *ctl, int sorted)
 {
     __shared__ EsSmem S;
+    if (sorted && ctl->lrange == 0) return;    // k_edge_scan_equal does this iteration
     const int tid = threadIdx.x, lane = tid & 31;
     const uint32_t lmin = ctl->lmin;
     const int np = ctl->npass;
@@ -244,7 +249,9 @@ k_edge_scan(const int64_t *__restrict__ ooff, const uint32_t *__restrict__ oadj,
 
     for (int i = tid; i < kMaxPasses * kBuckets; i += kEsThreads) (&S.hist[0][0])[i] = 0;
     for (int i = tid; i < n_hub; i += kEsThreads) {
-        S.hub_l[i] = loads[hub_id[i]];
+        const uint32_t v = hub_id[i];
+        S.hub_v[i] = v;
+        S.hub_l[i] = loads[v];
         S.hub_c[i] = 0;
     }
     HistAcc h;
@@ -312,16 +319,24 @@ k_edge_scan(const int64_t *__restrict__ ooff, const uint32_t *__restrict__ oadj,
             uint8_t *map = S.srcmap[tid >> 5];
             uint32_t carry = 0;
             for (uint32_t base = 0; base < total; base += 32 * kEsUnroll) {
-                // source map of this batch: mark first slots, then fill forward
-                reinterpret_cast<uint2 *>(map)[lane] = make_uint2(0u, 0u);
+                // source map of this batch: mark first slots, then fill forward.
+                // Each lane owns kMapWords 32-bit words (4 slots each) of the
+                // warp's 32 * kEsUnroll slots.
+                uint32_t *mw = reinterpret_cast<uint32_t *>(map) + lane * kMapWords;
+                #pragma unroll
+                for (int i = 0; i < kMapWords; ++i) mw[i] = 0u;
                 __syncwarp();
                 if (sdeg && start >= base && start < base + 32 * kEsUnroll)
                     map[start - base] = (uint8_t)(lane + 1);
                 __syncwarp();
-                uint2 v = reinterpret_cast<uint2 *>(map)[lane];
+                uint32_t wv[kMapWords];
                 uint32_t lm = 0;
                 #pragma unroll
-                for (int b = 0; b < 4; ++b) lm = max(lm, max((v.x >> (8 * b)) & 0xffu, (v.y >> (8 * b)) & 0xffu));
+                for (int i = 0; i < kMapWords; ++i) {
+                    wv[i] = mw[i];
+                    #pragma unroll
+                    for (int b = 0; b < 4; ++b) lm = max(lm, (wv[i] >> (8 * b)) & 0xffu);
+                }
                 uint32_t im = lm;
                 #pragma unroll
                 for (int o = 1; o < 32; o <<= 1) {
@@ -330,18 +345,16 @@ k_edge_scan(const int64_t *__restrict__ ooff, const uint32_t *__restrict__ oadj,
                 }
                 uint32_t cur = __shfl_up_sync(kFull, im, 1);
                 cur = max(lane ? cur : 0u, carry);
-                uint32_t nx = 0, ny = 0;
                 #pragma unroll
-                for (int b = 0; b < 4; ++b) {
-                    cur = max(cur, (v.x >> (8 * b)) & 0xffu);
-                    nx |= cur << (8 * b);
+                for (int i = 0; i < kMapWords; ++i) {
+                    uint32_t nw = 0;
+                    #pragma unroll
+                    for (int b = 0; b < 4; ++b) {
+                        cur = max(cur, (wv[i] >> (8 * b)) & 0xffu);
+                        nw |= cur << (8 * b);
+                    }
+                    mw[i] = nw;
                 }
-                #pragma unroll
-                for (int b = 0; b < 4; ++b) {
-                    cur = max(cur, (v.y >> (8 * b)) & 0xffu);
-                    ny |= cur << (8 * b);
-                }
-                reinterpret_cast<uint2 *>(map)[lane] = make_uint2(nx, ny);
                 carry = __shfl_sync(kFull, cur, 31);
                 __syncwarp();
                 uint32_t t[kEsUnroll], lw[kEsUnroll], sl_r[kEsUnroll];
@@ -399,11 +412,39 @@ int edge_scan_sm_count()
     return g_es_blocks_per_sm;
 }
 
+// All loads equal (e.g. iteration 1 from zero loads): the order is the id
+// order, so A[u] = #{w in N(u) : w > u}, read off u's ascending adjacency
+// list by a binary search for u.  Exits unless the loads are all equal.
+__global__ void k_edge_scan_equal(const int64_t *__restrict__ off, const int32_t *__restrict__ adj,
+                                  int64_t n, uint32_t *A, Control *ctl)
+{
+    if (ctl->lrange != 0) return;
+    uint32_t cnt = 0;
+    for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < n;
+         u += (int64_t)gridDim.x * blockDim.x) {
+        int64_t lo = off[u];
+        const int64_t e = off[u + 1];
+        int64_t hi = e;
+        while (lo < hi) {                    // first position with adj > u
+            const int64_t mid = lo + (hi - lo) / 2;
+            if (adj[mid] > (int32_t)u) hi = mid; else lo = mid + 1;
+        }
+        A[u] = (uint32_t)(e - lo);
+        ++cnt;
+    }
+    cnt = __reduce_add_sync(kFull, cnt);
+    if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(&ctl->hist[0][0], cnt);   // range 0: one bucket
+}
+
 cudaError_t launch_edge_scan(const GraphDev &g, RunBufs &b, int grid, cudaStream_t s)
 {
     cudaMemsetAsync(b.A, 0, sizeof(uint32_t) * (size_t)g.n, s);
+    if (g.sorted) {
+        const int eg = (int)imin64((g.n + 255) / 256, 152 * 16);
+        k_edge_scan_equal<<<eg, 256, 0, s>>>(g.off, g.adj, g.n, b.A, b.ctl);
+    }
     k_edge_scan<<<grid, kEsThreads, 0, s>>>(g.ooff, g.oadj, g.hub_id, g.n_hub, g.items, g.n_items,
-                                            g.n, b.loads, b.A, b.ctl);
+                                            g.n, b.loads, b.A, b.ctl, g.sorted);
     return cudaGetLastError();
 }
 
@@ -417,9 +458,19 @@ __global__ void k_asum_single_pass(const uint32_t *__restrict__ loads,
     const uint32_t lmin = ctl->lmin;
     for (int i = threadIdx.x; i < kBuckets; i += blockDim.x) as[i] = 0;
     __syncthreads();
-    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
-         v += (int64_t)gridDim.x * blockDim.x)
-        atomicAdd(&as[(loads[v] - lmin) & (kBuckets - 1)], (unsigned long long)A[v]);
+    for (int64_t v0 = blockIdx.x * (int64_t)blockDim.x; v0 < n; v0 += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t v = v0 + threadIdx.x;
+        const bool ok = v < n;
+        const uint32_t bk = ok ? (loads[v] - lmin) & (kBuckets - 1) : kBuckets;
+        const uint32_t a = ok ? A[v] : 0u;
+        // lanes with the same bucket add together (16-bit halves keep the
+        // 32-bit warp sums exact)
+        const uint32_t peers = __match_any_sync(kFull, bk);
+        const uint32_t lo = __reduce_add_sync(peers, a & 0xffffu);
+        const uint32_t hi = __reduce_add_sync(peers, a >> 16);
+        if (ok && (threadIdx.x & 31) == (unsigned)(__ffs(peers) - 1))
+            atomicAdd(&as[bk], (unsigned long long)lo + ((unsigned long long)hi << 16));
+    }
     __syncthreads();
     for (int i = threadIdx.x; i < kBuckets; i += blockDim.x)
         if (as[i]) atomicAdd(&ctl->asum[i], as[i]);

@@ -177,6 +177,31 @@ def test_profiling_stats(dsg, ctx):
     finally:
         dsg.dsg_set_profiling(ctx, False)
     st = dsg.dsg_get_stats(ctx, reset=True)
-    assert st["edge_scan"]["launches"] == 3 and st["sort"]["launches"] == 15
+    assert st["edge_scan"]["launches"] == 6 and st["sort"]["launches"] == 15
     assert st["edge_scan"]["ms"] > 0 and st["sort"]["ms"] > 0
     assert st["edge_scan"]["bytes"] == 3 * (8 * g.m + 16 * g.n)
+
+
+def test_unsorted_adjacency_lists(dsg, ctx):
+    """Lists need not be sorted without DSG_VALIDATE: the equal-loads shortcut
+    (binary search in a sorted list) is then off and the general scan runs."""
+    g = gg.er_m(20000, 10, 71)
+    rng = np.random.default_rng(1)
+    adj = g.adj.copy()
+    for u in range(0, g.n, 3):
+        a, b = g.off[u], g.off[u + 1]
+        adj[a:b] = rng.permutation(adj[a:b])
+    gr = dsg.dsg_upload_csr(ctx, g.n, g.off, adj, 0)
+    try:
+        T = 5
+        loads = np.zeros(g.n, np.int64)
+        bset = np.zeros(g.n, np.int32)
+        trace = np.zeros(3 * T, np.int64)
+        r = dsg.dsg_run(ctx, gr, dsg.DSG_SORTING, T, 0, 1, None, loads, bset, trace)
+    finally:
+        dsg.dsg_free_graph(gr)
+    o = orc.run(g, orc.SORTING, T)
+    assert np.array_equal(loads, o.loads)
+    assert (r["best_edges"], r["best_vertices"], r["best_iter"]) == (o.best_edges, o.best_vertices, o.best_iter)
+    assert np.array_equal(bset[: r["best_set_size"]].astype(np.int64), o.best_set)
+    assert np.array_equal(trace.reshape(T, 3), o.trace)
