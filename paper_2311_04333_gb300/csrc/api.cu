@@ -39,6 +39,7 @@ struct dsg_graph {
     int64_t *ooff = nullptr;         // degree-oriented copy (sorting edge scan)
     uint32_t *oadj = nullptr;
     uint32_t *hub = nullptr;
+    uint32_t *hot = nullptr;
     // run buffers, allocated on first use
     bool rb_ready = false;
     RunBufs rb{};
@@ -135,7 +136,8 @@ int ensure_run_bufs(dsg_ctx *ctx, dsg_graph *G, int32_t T)
             sizeof(Control),                    // ctl
             (size_t)nblk * 8,                   // blk_a
             (size_t)nblk * 8,                   // blk_b
-            0, 0};
+            (size_t)(G->g.n_hot > 0 ? G->g.n_hot : 1) * 4,  // hot_l
+            0};
         size_t total = 0;
         for (size_t s : sz) total += align256(s);
         char *mem = nullptr;
@@ -157,6 +159,7 @@ int ensure_run_bufs(dsg_ctx *ctx, dsg_graph *G, int32_t T)
         b.ctl = (Control *)take(sz[7]);
         b.blk_a = (int64_t *)take(sz[8]);
         b.blk_b = (int64_t *)take(sz[9]);
+        b.hot_l = (uint32_t *)take(sz[10]);
         b.ntiles = ntiles;
         b.nblk64 = nblk;
         CK(cudaMemsetAsync(b.status, 0, sz[4], ctx->stream), "status init");
@@ -257,6 +260,7 @@ int dsg_upload_csr(dsg_ctx *ctx, int64_t n, const int64_t *offsets, const int32_
         if (G->ooff) cudaFreeAsync(G->ooff, ctx->stream);
         if (G->oadj) cudaFreeAsync(G->oadj, ctx->stream);
         if (G->hub) cudaFreeAsync(G->hub, ctx->stream);
+        if (G->hot) cudaFreeAsync(G->hot, ctx->stream);
         cudaStreamSynchronize(ctx->stream);
         delete G;
         return code;
@@ -297,11 +301,13 @@ int dsg_upload_csr(dsg_ctx *ctx, int64_t n, const int64_t *offsets, const int32_
     G->g.sorted = h_err[5] ? 0 : 1;
     // degree-oriented copy for the sorting edge scan, and the chunk schedule
     // of its vertices of large out-degree
-    if ((e = build_orientation(G->g, ctx->stream, &G->ooff, &G->oadj, &G->hub, &G->g.n_hub)) != cudaSuccess)
+    if ((e = build_orientation(G->g, ctx->stream, &G->ooff, &G->oadj, &G->hub, &G->g.n_hub, &G->hot,
+                               &G->g.n_hot)) != cudaSuccess)
         return bail(cuda_fail(ctx, e, "orientation"));
     G->g.ooff = G->ooff;
     G->g.oadj = G->oadj;
     G->g.hub_id = G->hub;
+    G->g.hot_id = G->hot;
     void *tmp = nullptr;
     const size_t tmp_bytes = (size_t)schedule_tmp_count(n) * sizeof(int64_t);
     if ((e = cudaMallocAsync(&tmp, tmp_bytes, ctx->stream)) != cudaSuccess) return bail(cuda_fail(ctx, e, "schedule scratch"));
@@ -340,6 +346,7 @@ void dsg_free_graph(dsg_graph *G)
     if (G->ooff) cudaFreeAsync(G->ooff, ctx->stream);
     if (G->oadj) cudaFreeAsync(G->oadj, ctx->stream);
     if (G->hub) cudaFreeAsync(G->hub, ctx->stream);
+    if (G->hot) cudaFreeAsync(G->hot, ctx->stream);
     if (G->rb_mem) cudaFreeAsync(G->rb_mem, ctx->stream);
     if (G->rb.trace) cudaFreeAsync(G->rb.trace, ctx->stream);
     if (G->npass_log) cudaFreeAsync(G->npass_log, ctx->stream);
@@ -427,7 +434,7 @@ int dsg_run(dsg_graph *G, int variant, int32_t T, int64_t eps_num, int64_t eps_d
         ctx->launches[DSG_PHASE_OTHER] += 2;
     }
     if (variant == DSG_SORTING) {
-        const int es_grid = ctx->sm_count * edge_scan_sm_count();
+        const int es_grid = ctx->sm_count * edge_scan_sm_count();   // also sets the kernel attributes
         for (int t = 1; t <= T; ++t) {
             {
                 PhaseTimer pt(ctx, DSG_PHASE_OTHER);

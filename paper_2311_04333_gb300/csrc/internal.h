@@ -12,7 +12,7 @@ namespace dsg {
 // of 32 consecutive ids by single warps, without a list.
 // Tuning knobs (compile-time; the defaults are the measured best on GB300).
 #ifndef DSG_HUBS
-#define DSG_HUBS 2048
+#define DSG_HUBS 12288
 #endif
 #ifndef DSG_ES_UNROLL
 #define DSG_ES_UNROLL 8
@@ -20,12 +20,25 @@ namespace dsg {
 #ifndef DSG_MID_DEG
 #define DSG_MID_DEG 64
 #endif
+#ifndef DSG_ES_THREADS
+#define DSG_ES_THREADS 1024
+#endif
 constexpr int64_t kHeavyDeg = 1024;
 constexpr int kChunk = 1024;
 // degree orientation: at most kHubs largest-degree vertices get a hub slot;
 // oriented arc targets that are hubs are stored as kHubBit | slot
 constexpr int kHubs = DSG_HUBS;
 constexpr uint32_t kHubBit = 0x80000000u;
+// the next tier: at most kHot largest-degree vertices (hubs included) get a
+// slot in a dense copy of their loads that stays resident in L2; targets
+// outside the hubs but inside it are stored as kHotBit | slot (only when
+// n < 2^30, so that plain ids never carry the bit)
+#ifndef DSG_HOT
+#define DSG_HOT (1 << 22)
+#endif
+constexpr int64_t kHot = DSG_HOT;
+constexpr uint32_t kHotBit = 0x40000000u;
+constexpr uint32_t kSlotMask = 0x3fffffffu;
 
 struct WorkItem {
     int64_t a0;      // first arc of the chunk
@@ -100,6 +113,8 @@ struct GraphDev {
     const uint32_t *oadj;    // [m], targets (hub targets encoded)
     const uint32_t *hub_id;  // [n_hub]
     int64_t n_hub;
+    const uint32_t *hot_id;  // [n_hot]
+    int64_t n_hot;
     int sorted;              // every adjacency list is strictly ascending
 };
 
@@ -116,6 +131,7 @@ struct RunBufs {
     Control *ctl;
     int64_t *trace;          // [T * 3] device
     int64_t *blk_a, *blk_b;  // scratch for block-level counts (size nblk64)
+    uint32_t *hot_l;         // [n_hot] loads of the hot tier (refreshed per iteration)
     int64_t nblk64;
     void *scratch;           // >= 8n bytes (output staging)
 };
@@ -142,7 +158,8 @@ cudaError_t launch_best_set(const GraphDev &g, RunBufs &b, int32_t *set_dev, cud
                             int *launches);
 cudaError_t launch_loads_out(const GraphDev &g, RunBufs &b, int64_t *dst, cudaStream_t s);
 cudaError_t build_orientation(GraphDev &g, cudaStream_t s, int64_t **ooff_out, uint32_t **oadj_out,
-                              uint32_t **hub_out, int64_t *n_hub_out);
+                              uint32_t **hub_out, int64_t *n_hub_out, uint32_t **hot_out,
+                              int64_t *n_hot_out);
 cudaError_t launch_asum_single_pass(const GraphDev &g, RunBufs &b, cudaStream_t s);
 cudaError_t launch_max_u64_of_i64(const int64_t *src, int64_t n, unsigned long long *dst,
                                   int *neg_flag, cudaStream_t s);

@@ -280,10 +280,12 @@ __global__ void k_orient_count(const int64_t *__restrict__ off, const int32_t *_
     }
 }
 
-// warp per vertex: write the kept targets in list order, hub targets encoded
+// warp per vertex: write the kept targets in list order, hub and hot targets
+// encoded
 __global__ void k_orient_fill(const int64_t *__restrict__ off, const int32_t *__restrict__ adj,
                               int64_t n, const int64_t *__restrict__ ooff,
-                              const int32_t *__restrict__ slot_of, uint32_t *oadj)
+                              const int32_t *__restrict__ slot_of,
+                              const int32_t *__restrict__ hot_of, uint32_t *oadj)
 {
     const int lane = threadIdx.x & 31;
     const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -302,16 +304,38 @@ __global__ void k_orient_fill(const int64_t *__restrict__ off, const int32_t *__
             const uint32_t m = __ballot_sync(kFull, keep);
             if (keep) {
                 const int32_t sl = slot_of[w];
-                oadj[o + __popc(m & lanemask_lt())] = sl >= 0 ? (kHubBit | (uint32_t)sl) : w;
+                const int32_t hs = hot_of ? hot_of[w] : -1;
+                oadj[o + __popc(m & lanemask_lt())] =
+                    sl >= 0 ? (kHubBit | (uint32_t)sl) : (hs >= 0 ? (kHotBit | (uint32_t)hs) : w);
             }
             o += __popc(m);
         }
     }
 }
 
-// Builds ooff, oadj and hub_id (allocated here, stream-ordered).
+// smallest D >= 2 with #{deg >= D} <= cap (count(deg >= max_degree + 1) = 0)
+static cudaError_t degree_threshold(const GraphDev &g, int64_t cap, unsigned long long *cnt,
+                                    int grid, cudaStream_t s, int64_t *D_out)
+{
+    int64_t lo = 2, hi = g.max_degree + 1;
+    cudaError_t e;
+    while (lo < hi) {
+        const int64_t mid = lo + (hi - lo) / 2;
+        unsigned long long h = 0;
+        cudaMemsetAsync(cnt, 0, 8, s);
+        k_count_ge<<<grid, 256, 0, s>>>(g.off, g.n, mid, cnt);
+        cudaMemcpyAsync(&h, cnt, 8, cudaMemcpyDeviceToHost, s);
+        if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+        if ((int64_t)h <= cap) hi = mid; else lo = mid + 1;
+    }
+    *D_out = lo;
+    return cudaSuccess;
+}
+
+// Builds ooff, oadj, hub_id and hot_id (allocated here, stream-ordered).
 cudaError_t build_orientation(GraphDev &g, cudaStream_t s, int64_t **ooff_out, uint32_t **oadj_out,
-                              uint32_t **hub_out, int64_t *n_hub_out)
+                              uint32_t **hub_out, int64_t *n_hub_out, uint32_t **hot_out,
+                              int64_t *n_hot_out)
 {
     const int64_t n = g.n;
     cudaError_t e;
@@ -325,17 +349,8 @@ cudaError_t build_orientation(GraphDev &g, cudaStream_t s, int64_t **ooff_out, u
     if ((e = cudaMallocAsync((void **)&tmp, 8 * (size_t)(ntmp + 2), s)) != cudaSuccess) return e;
     if ((e = cudaMallocAsync((void **)&flag, 8 * (size_t)(n + 1), s)) != cudaSuccess) return e;
     if ((e = cudaMallocAsync((void **)&slot_of, 4 * (size_t)n, s)) != cudaSuccess) return e;
-    int64_t lo = 2, hi = g.max_degree + 1;            // count(deg >= hi) == 0
-    while (lo < hi) {
-        const int64_t mid = lo + (hi - lo) / 2;
-        unsigned long long h = 0;
-        cudaMemsetAsync(cnt, 0, 8, s);
-        k_count_ge<<<grid, 256, 0, s>>>(g.off, n, mid, cnt);
-        cudaMemcpyAsync(&h, cnt, 8, cudaMemcpyDeviceToHost, s);
-        if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
-        if ((int64_t)h <= kHubs) hi = mid; else lo = mid + 1;
-    }
-    const int64_t D = lo;
+    int64_t D = 0;
+    if ((e = degree_threshold(g, kHubs, cnt, grid, s, &D)) != cudaSuccess) return e;
     k_hub_flags<<<grid, 256, 0, s>>>(g.off, n, D, flag);
     int64_t *total = tmp + ntmp;
     if ((e = scan_exclusive_i64(flag, n, total, tmp, s)) != cudaSuccess) return e;
@@ -345,6 +360,21 @@ cudaError_t build_orientation(GraphDev &g, cudaStream_t s, int64_t **ooff_out, u
     uint32_t *hub = nullptr;
     if ((e = cudaMallocAsync((void **)&hub, 4 * (size_t)imax64(n_hub, 1), s)) != cudaSuccess) return e;
     k_hub_slots<<<grid, 256, 0, s>>>(g.off, n, D, flag, slot_of, hub);
+    // hot tier (only when plain ids stay below kHotBit)
+    int32_t *hot_of = nullptr;
+    uint32_t *hot = nullptr;
+    int64_t n_hot = 0;
+    if (n < (int64_t)kHotBit && kHot > 0) {
+        int64_t Dh = 0;
+        if ((e = degree_threshold(g, kHot, cnt, grid, s, &Dh)) != cudaSuccess) return e;
+        if ((e = cudaMallocAsync((void **)&hot_of, 4 * (size_t)n, s)) != cudaSuccess) return e;
+        k_hub_flags<<<grid, 256, 0, s>>>(g.off, n, Dh, flag);
+        if ((e = scan_exclusive_i64(flag, n, total, tmp, s)) != cudaSuccess) return e;
+        cudaMemcpyAsync(&n_hot, total, 8, cudaMemcpyDeviceToHost, s);
+        if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+        if ((e = cudaMallocAsync((void **)&hot, 4 * (size_t)imax64(n_hot, 1), s)) != cudaSuccess) return e;
+        k_hub_slots<<<grid, 256, 0, s>>>(g.off, n, Dh, flag, hot_of, hot);
+    }
     // oriented offsets
     const int wgrid = (int)imin64((n * 32 + 255) / 256, 152 * 32);
     k_orient_count<<<wgrid, 256, 0, s>>>(g.off, g.adj, n, flag);
@@ -355,14 +385,17 @@ cudaError_t build_orientation(GraphDev &g, cudaStream_t s, int64_t **ooff_out, u
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
     uint32_t *oadj = nullptr;
     if ((e = cudaMallocAsync((void **)&oadj, 4 * (size_t)imax64(oarcs, 1), s)) != cudaSuccess) return e;
-    k_orient_fill<<<wgrid, 256, 0, s>>>(g.off, g.adj, n, flag, slot_of, oadj);
+    k_orient_fill<<<wgrid, 256, 0, s>>>(g.off, g.adj, n, flag, slot_of, hot_of, oadj);
     cudaFreeAsync(cnt, s);
     cudaFreeAsync(tmp, s);
     cudaFreeAsync(slot_of, s);
+    if (hot_of) cudaFreeAsync(hot_of, s);
     *ooff_out = flag;         // n + 1 exclusive prefix sums = oriented offsets
     *oadj_out = oadj;
     *hub_out = hub;
     *n_hub_out = n_hub;
+    *hot_out = hot;
+    *n_hot_out = n_hot;
     return cudaGetLastError();
 }
 

@@ -119,7 +119,8 @@ cudaError_t launch_plan(const GraphDev &, RunBufs &b, int t, cudaStream_t s)
 //     arc finding its source lane by a 5-step shuffle binary search.
 // The group's lanes also accumulate the digit histograms of (l - lmin).
 
-constexpr int kEsThreads = 256;
+constexpr int kEsThreads = DSG_ES_THREADS;
+constexpr int kEsMinBlocks = 1024 / kEsThreads;
 constexpr int kEsUnroll = DSG_ES_UNROLL;        // rounds of 32 arcs in flight per warp
 constexpr int64_t kMidDeg = DSG_MID_DEG;
 static_assert(kEsUnroll >= 4 && kEsUnroll % 4 == 0, "source map words hold 4 slots");
@@ -130,6 +131,7 @@ struct EsSmem {
     uint32_t hub_l[kHubs];      // loads of the hubs
     uint32_t hub_c[kHubs];      // counts for the hubs from this block
     uint32_t hub_v[kHubs];      // ids of the hubs
+    uint32_t hot_bit;           // kHotBit when the hot tier exists, else 0
     // per warp: source lane (+1) of each of the 256 arcs of a packed batch
     uint8_t srcmap[kEsThreads / 32][32 * kEsUnroll];
 };
@@ -179,35 +181,40 @@ __device__ __forceinline__ uint32_t ld_arc(const uint32_t *p, uint64_t pol)
     return v;
 }
 
-// load of an arc target: shared-memory copy for hubs, gather otherwise
+// load of an arc target: shared-memory copy for hubs, the L2-resident hot
+// copy for the next tier, the load array otherwise
 __device__ __forceinline__ uint32_t target_load(uint32_t t, const uint32_t *__restrict__ loads,
-                                                const EsSmem &S)
+                                                const uint32_t *__restrict__ hot_l, const EsSmem &S)
 {
-    return (t & kHubBit) ? S.hub_l[t & ~kHubBit] : __ldg(loads + t);
+    if (t & kHubBit) return S.hub_l[t & ~kHubBit];
+    if (t & S.hot_bit) return __ldg(hot_l + (t & kSlotMask));
+    return __ldg(loads + t);
 }
 
 // compare target t (load lw) with source (lu, u): count for u, or add one
 // to the target's count
 __device__ __forceinline__ void settle(uint32_t t, uint32_t lw, uint32_t lu, uint32_t u,
-                                       const uint32_t *__restrict__ hub_id, EsSmem &S,
+                                       const uint32_t *__restrict__ hot_id, EsSmem &S,
                                        uint32_t *A, uint32_t &c)
 {
     const bool hub = t & kHubBit;
+    const bool hot = !hub && (t & S.hot_bit);
     bool later = lw > lu;
     if (lw == lu) {
-        const uint32_t w = hub ? S.hub_v[t & ~kHubBit] : t;
+        const uint32_t w = hub ? S.hub_v[t & ~kHubBit] : (hot ? __ldg(hot_id + (t & kSlotMask)) : t);
         later = w > u;
     }
     if (later) ++c;
     else if (hub) atomicAdd(&S.hub_c[t & ~kHubBit], 1u);
-    else atomicAdd(&A[t], 1u);
+    else atomicAdd(&A[hot ? __ldg(hot_id + (t & kSlotMask)) : t], 1u);
 }
 
 // the warp processes oriented arcs [a0, a1) of source (lu, u); returns this
 // lane's count for u
 __device__ __forceinline__ uint32_t warp_arcs(const uint32_t *__restrict__ oadj,
                                               const uint32_t *__restrict__ loads,
-                                              const uint32_t *__restrict__ hub_id, EsSmem &S,
+                                              const uint32_t *__restrict__ hot_l,
+                                              const uint32_t *__restrict__ hot_id, EsSmem &S,
                                               uint32_t *A, int64_t a0, int64_t a1, uint32_t lu,
                                               uint32_t u, int lane, uint64_t pol)
 {
@@ -222,24 +229,26 @@ __device__ __forceinline__ uint32_t warp_arcs(const uint32_t *__restrict__ oadj,
         #pragma unroll
         for (int k = 0; k < kEsUnroll; ++k) {
             const int64_t j = j0 + k * 32 + lane;
-            lw[k] = j < a1 ? target_load(t[k], loads, S) : 0u;
+            lw[k] = j < a1 ? target_load(t[k], loads, hot_l, S) : 0u;
         }
         #pragma unroll
         for (int k = 0; k < kEsUnroll; ++k) {
             const int64_t j = j0 + k * 32 + lane;
-            if (j < a1) settle(t[k], lw[k], lu, u, hub_id, S, A, c);
+            if (j < a1) settle(t[k], lw[k], lu, u, hot_id, S, A, c);
         }
     }
     return c;
 }
 
-__global__ void __launch_bounds__(kEsThreads, 4)
+__global__ void __launch_bounds__(kEsThreads, kEsMinBlocks)
 k_edge_scan(const int64_t *__restrict__ ooff, const uint32_t *__restrict__ oadj,
             const uint32_t *__restrict__ hub_id, int64_t n_hub,
+            const uint32_t *__restrict__ hot_l, const uint32_t *__restrict__ hot_id,
             const WorkItem *__restrict__ items, int64_t n_items, int64_t n,
             const uint32_t *__restrict__ loads, uint32_t *A, Control *ctl, int sorted)
 {
-    __shared__ EsSmem S;
+    extern __shared__ __align__(16) unsigned char es_smem_raw[];
+    EsSmem &S = *reinterpret_cast<EsSmem *>(es_smem_raw);
     if (sorted && ctl->lrange == 0) return;    // k_edge_scan_equal does this iteration
     const int tid = threadIdx.x, lane = tid & 31;
     const uint32_t lmin = ctl->lmin;
@@ -248,6 +257,7 @@ k_edge_scan(const int64_t *__restrict__ ooff, const uint32_t *__restrict__ oadj,
     const int64_t n_units = n_items + (n + 31) / 32;
 
     for (int i = tid; i < kMaxPasses * kBuckets; i += kEsThreads) (&S.hist[0][0])[i] = 0;
+    if (tid == 0) S.hot_bit = hot_id ? kHotBit : 0u;
     for (int i = tid; i < n_hub; i += kEsThreads) {
         const uint32_t v = hub_id[i];
         S.hub_v[i] = v;
@@ -270,7 +280,7 @@ k_edge_scan(const int64_t *__restrict__ ooff, const uint32_t *__restrict__ oadj,
             const WorkItem it = items[unit];
             const uint32_t u = it.u;
             const int64_t a1 = imin64(it.a0 + (int64_t)kChunk, ooff[u + 1]);
-            uint32_t c = warp_arcs(oadj, loads, hub_id, S, A, it.a0, a1, loads[u], u, lane, pol);
+            uint32_t c = warp_arcs(oadj, loads, hot_l, hot_id, S, A, it.a0, a1, loads[u], u, lane, pol);
             c = __reduce_add_sync(kFull, c);
             if (lane == 0 && c) atomicAdd(&A[u], c);
             continue;
@@ -297,7 +307,7 @@ k_edge_scan(const int64_t *__restrict__ ooff, const uint32_t *__restrict__ oadj,
             mm &= mm - 1;
             const int64_t vs = __shfl_sync(kFull, s, l), ve = __shfl_sync(kFull, e, l);
             const uint32_t vl = __shfl_sync(kFull, lu, l);
-            uint32_t c = warp_arcs(oadj, loads, hub_id, S, A, vs, ve, vl, (uint32_t)(g0 + l), lane, pol);
+            uint32_t c = warp_arcs(oadj, loads, hot_l, hot_id, S, A, vs, ve, vl, (uint32_t)(g0 + l), lane, pol);
             c = __reduce_add_sync(kFull, c);
             if (lane == l) cnt = c;
         }
@@ -369,14 +379,14 @@ k_edge_scan(const int64_t *__restrict__ ooff, const uint32_t *__restrict__ oadj,
                 #pragma unroll
                 for (int k = 0; k < kEsUnroll; ++k) {
                     const uint32_t j = base + k * 32 + lane;
-                    lw[k] = j < total ? target_load(t[k], loads, S) : 0u;
+                    lw[k] = j < total ? target_load(t[k], loads, hot_l, S) : 0u;
                 }
                 #pragma unroll
                 for (int k = 0; k < kEsUnroll; ++k) {
                     const uint32_t j = base + k * 32 + lane;
                     const uint32_t l_src = __shfl_sync(kFull, lu, sl_r[k]);
                     uint32_t one = 0;
-                    if (j < total) settle(t[k], lw[k], l_src, (uint32_t)(g0 + sl_r[k]), hub_id, S, A, one);
+                    if (j < total) settle(t[k], lw[k], l_src, (uint32_t)(g0 + sl_r[k]), hot_id, S, A, one);
                     const uint32_t C = __ballot_sync(kFull, one != 0);
                     const int jb = (int)(base + k * 32);
                     const int lo = max((int)start - jb, 0), hi = min((int)incl - jb, 32);
@@ -405,8 +415,9 @@ static int g_es_blocks_per_sm = -1;
 int edge_scan_sm_count()
 {
     if (g_es_blocks_per_sm < 0) {
+        cudaFuncSetAttribute(k_edge_scan, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(EsSmem));
         int nb = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_edge_scan, kEsThreads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_edge_scan, kEsThreads, sizeof(EsSmem));
         g_es_blocks_per_sm = nb > 0 ? nb : 1;
     }
     return g_es_blocks_per_sm;
@@ -436,15 +447,29 @@ __global__ void k_edge_scan_equal(const int64_t *__restrict__ off, const int32_t
     if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(&ctl->hist[0][0], cnt);   // range 0: one bucket
 }
 
+// dense copy of the hot tier's loads for this iteration
+__global__ void k_hot_refresh(const uint32_t *__restrict__ loads, const uint32_t *__restrict__ hot_id,
+                              int64_t n_hot, uint32_t *__restrict__ hot_l)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_hot;
+         i += (int64_t)gridDim.x * blockDim.x)
+        hot_l[i] = loads[hot_id[i]];
+}
+
 cudaError_t launch_edge_scan(const GraphDev &g, RunBufs &b, int grid, cudaStream_t s)
 {
     cudaMemsetAsync(b.A, 0, sizeof(uint32_t) * (size_t)g.n, s);
+    if (g.n_hot > 0) {
+        const int hg = (int)imin64((g.n_hot + 255) / 256, 152 * 8);
+        k_hot_refresh<<<hg, 256, 0, s>>>(b.loads, g.hot_id, g.n_hot, b.hot_l);
+    }
     if (g.sorted) {
         const int eg = (int)imin64((g.n + 255) / 256, 152 * 16);
         k_edge_scan_equal<<<eg, 256, 0, s>>>(g.off, g.adj, g.n, b.A, b.ctl);
     }
-    k_edge_scan<<<grid, kEsThreads, 0, s>>>(g.ooff, g.oadj, g.hub_id, g.n_hub, g.items, g.n_items,
-                                            g.n, b.loads, b.A, b.ctl, g.sorted);
+    k_edge_scan<<<grid, kEsThreads, sizeof(EsSmem), s>>>(g.ooff, g.oadj, g.hub_id, g.n_hub, b.hot_l,
+                                            g.n_hot > 0 ? g.hot_id : nullptr,
+                                            g.items, g.n_items, g.n, b.loads, b.A, b.ctl, g.sorted);
     return cudaGetLastError();
 }
 
@@ -456,12 +481,13 @@ __global__ void k_asum_single_pass(const uint32_t *__restrict__ loads,
     if (ctl->npass != 1) return;
     __shared__ unsigned long long as[kBuckets];
     const uint32_t lmin = ctl->lmin;
+    const int sh = ctl->shift[ctl->npass - 1];
     for (int i = threadIdx.x; i < kBuckets; i += blockDim.x) as[i] = 0;
     __syncthreads();
     for (int64_t v0 = blockIdx.x * (int64_t)blockDim.x; v0 < n; v0 += (int64_t)gridDim.x * blockDim.x) {
         const int64_t v = v0 + threadIdx.x;
         const bool ok = v < n;
-        const uint32_t bk = ok ? (loads[v] - lmin) & (kBuckets - 1) : kBuckets;
+        const uint32_t bk = ok ? ((loads[v] - lmin) >> sh) & (kBuckets - 1) : kBuckets;
         const uint32_t a = ok ? A[v] : 0u;
         // lanes with the same bucket add together (16-bit halves keep the
         // 32-bit warp sums exact)
@@ -478,7 +504,7 @@ __global__ void k_asum_single_pass(const uint32_t *__restrict__ loads,
 
 cudaError_t launch_asum_single_pass(const GraphDev &g, RunBufs &b, cudaStream_t s)
 {
-    const int grid = (int)imin64((g.n + 255) / 256, 152 * 4);
+    const int grid = (int)imin64((g.n + 255) / 256, 152 * 8);
     k_asum_single_pass<<<grid, 256, 0, s>>>(b.loads, b.A, g.n, b.ctl);
     return cudaGetLastError();
 }
@@ -500,7 +526,7 @@ struct PassSmem {
     unsigned long long aoff[kBuckets];
     unsigned long long gsum[kBuckets];
     unsigned long long dscan[kBuckets];
-    unsigned long long dend[kBuckets];
+    unsigned long long dsum[kBuckets];       // per-digit sum of the tile's values (last pass)
     unsigned long long asum_acc[kBuckets];
     unsigned long long red[33];
     Candidate cred[32];
@@ -509,12 +535,21 @@ struct PassSmem {
     uint32_t mn[kPassThreads / 32], mx[kPassThreads / 32];
 };
 
+#ifndef DSG_PASS_MINBLOCKS
+#define DSG_PASS_MINBLOCKS 4
+#endif
 __device__ __forceinline__ unsigned long long status_word(uint32_t epoch, uint64_t flag, uint64_t cnt)
 {
     return ((unsigned long long)epoch << 48) | (flag << 46) | (cnt & ((1ull << 46) - 1));
 }
 
-__global__ void __launch_bounds__(kPassThreads, 4)
+// One LSD pass (digit k of key - lmin) over (key, value) pairs, stable.
+// Each tile of kPassTile elements: load, rank within warps by ballots,
+// publish its per-digit counts (and, in the last pass, value sums) at once,
+// sort locally in shared memory, then resolve its global offsets by
+// decoupled look-back.  Non-last passes scatter; the last pass evaluates the
+// suffix starting at every element's final position (Alg. 3 lines 4-7).
+__global__ void __launch_bounds__(kPassThreads, DSG_PASS_MINBLOCKS)
 k_radix_pass(const uint32_t *kin, const uint32_t *vin,
              uint32_t *__restrict__ kout, uint32_t *__restrict__ vout,
              uint32_t *loads_next, unsigned long long *status, unsigned long long *status_sum,
@@ -535,31 +570,15 @@ k_radix_pass(const uint32_t *kin, const uint32_t *vin,
         S.tile = atomicAdd(&ctl->tile_ctr[k], 1u);
         S.last_block = 0;
     }
-    // global bucket offsets of this pass's digit (exclusive scan of the histogram)
-    {
-        const uint32_t hcount = ctl->hist[k][tid];
-        uint64_t tot;
-        const uint64_t ex = block_excl_sum_u64(hcount, S.red, &tot);
-        S.boff[tid] = (uint32_t)ex;
-        if (last) {
-            const unsigned long long as = ctl->asum[tid];
-            const uint64_t exs = block_excl_sum_u64(as, S.red, &tot);
-            S.aoff[tid] = exs;
-        }
-    }
     for (int i = tid; i < (kPassThreads / 32) * kBuckets; i += kPassThreads) (&S.wcnt[0][0])[i] = 0;
     S.asum_acc[tid] = 0;
+    S.dsum[tid] = 0;
     __syncthreads();
     const uint32_t tile = S.tile;
     const int64_t tbase = (int64_t)tile * kPassTile;
 
-    // ---- load 16 rounds of 32 consecutive items per warp; warp-level stable ranks
+    // ---- load 16 rounds of 32 consecutive items per warp (all loads first)
     uint32_t key_r[kPassIpt], val_r[kPassIpt], dw_r[kPassIpt];
-    uint32_t lmn = 0xffffffffu, lmx = 0;
-    const bool acc = accumulate && k == 0;
-    const int shift_last = ctl->shift[np - 1];
-    uint32_t amax = 0, rb = 0;
-    unsigned long long rs = 0;
     const int64_t wbase = tbase + warp * (32 * kPassIpt);
     #pragma unroll
     for (int r = 0; r < kPassIpt; ++r) {
@@ -567,6 +586,20 @@ k_radix_pass(const uint32_t *kin, const uint32_t *vin,
         key_r[r] = idx < n ? kin[idx] : 0u;
         val_r[r] = idx < n ? vin[idx] : 0u;
     }
+    // global bucket offsets of this pass's digit (overlaps the loads)
+    {
+        const uint32_t hcount = ctl->hist[k][tid];
+        uint64_t tot;
+        S.boff[tid] = (uint32_t)block_excl_sum_u64(hcount, S.red, &tot);
+        if (last) S.aoff[tid] = block_excl_sum_u64(ctl->asum[tid], S.red, &tot);
+    }
+
+    // ---- warp-level stable ranks (bit-sliced match of the digit)
+    uint32_t lmn = 0xffffffffu, lmx = 0;
+    const bool acc = accumulate && k == 0;
+    const int shift_last = ctl->shift[np - 1];
+    uint32_t amax = 0, rb = 0;
+    unsigned long long rs = 0;
     #pragma unroll
     for (int r = 0; r < kPassIpt; ++r) {
         const int64_t idx = wbase + r * 32 + lane;
@@ -599,11 +632,20 @@ k_radix_pass(const uint32_t *kin, const uint32_t *vin,
             const uint32_t bb = __ballot_sync(kFull, (d >> bit) & 1u);
             peers &= ((d >> bit) & 1u) ? bb : ~bb;
         }
+        if (!valid) peers = 0;
         const uint32_t rank = __popc(peers & lanemask_lt());
+        const bool leader = valid && (peers >> lane) == 1u;
+        if (last) {
+            // per-digit value sums of the tile (16-bit halves keep warp sums exact)
+            const uint32_t pm = valid ? peers : (1u << lane);
+            const uint32_t lo = __reduce_add_sync(pm, val & 0xffffu);
+            const uint32_t hi = __reduce_add_sync(pm, val >> 16);
+            if (leader) atomicAdd(&S.dsum[d], (unsigned long long)lo + ((unsigned long long)hi << 16));
+        }
         uint32_t before = 0;
         if (valid) before = S.wcnt[warp][d];
         __syncwarp();
-        if (valid && (peers >> lane) == 1u) S.wcnt[warp][d] = before + __popc(peers);
+        if (leader) S.wcnt[warp][d] = before + __popc(peers);
         __syncwarp();
         dw_r[r] = valid ? (d | ((before + rank) << 8)) : 0xffffffffu;
     }
@@ -614,43 +656,51 @@ k_radix_pass(const uint32_t *kin, const uint32_t *vin,
         if (lane == 0) { S.mn[warp] = lmn; S.mx[warp] = lmx; }
     }
     __syncthreads();
+
+    // ---- per-digit tile counts; publish the aggregate at once
+    const int d = tid;
+    uint32_t tcount = 0;
+    #pragma unroll
+    for (int w = 0; w < kPassThreads / 32; ++w) {
+        const uint32_t c = S.wcnt[w][d];
+        S.wcnt[w][d] = tcount;
+        tcount += c;
+    }
+    const uint64_t tsum = last ? (uint64_t)S.dsum[d] : 0ull;
+    unsigned long long *st = status + (int64_t)tile * kBuckets + d;
+    unsigned long long *ss = status_sum + 2 * ((int64_t)tile * kBuckets + d);
+    if (tile == 0) {
+        if (last) st_relaxed(ss + 1, tsum);
+        st_release(st, status_word(epoch, kFlagIncl, tcount));
+    } else {
+        if (last) st_relaxed(ss, tsum);
+        st_release(st, status_word(epoch, kFlagAgg, tcount));
+    }
     if (acc) {
         amax = __reduce_max_sync(kFull, amax);
         if (lane == 0 && amax) atomicMax(&ctl->width, amax);
+        if (!last && S.asum_acc[tid]) atomicAdd(&ctl->asum[tid], S.asum_acc[tid]);
     }
     if (k == 0 && loads_next && tid == 0) {
         uint32_t a = 0xffffffffu, b = 0;
         for (int i = 0; i < kPassThreads / 32; ++i) { a = min(a, S.mn[i]); b = max(b, S.mx[i]); }
-        if (b >= a || a != 0xffffffffu) {
-            atomicMin(&ctl->mm_min[(t + 1) & 1], a);
-            atomicMax(&ctl->mm_max[(t + 1) & 1], b);
-        }
+        atomicMin(&ctl->mm_min[(t + 1) & 1], a);
+        atomicMax(&ctl->mm_max[(t + 1) & 1], b);
     }
-    if (acc && !last && S.asum_acc[tid]) atomicAdd(&ctl->asum[tid], S.asum_acc[tid]);
-    // per-digit tile counts, exclusive per-warp prefixes, tile-local digit offsets
-    uint32_t tcount;
     {
-        const int d = tid;
-        uint32_t sum = 0;
-        #pragma unroll
-        for (int w = 0; w < kPassThreads / 32; ++w) {
-            const uint32_t c = S.wcnt[w][d];
-            S.wcnt[w][d] = sum;
-            sum += c;
-        }
-        tcount = sum;
         uint64_t tot;
-        const uint64_t ex = block_excl_sum_u64(sum, S.red, &tot);
+        const uint64_t ex = block_excl_sum_u64(tcount, S.red, &tot);
         S.toff[d] = (uint32_t)ex;
         if (d == 0) S.toff[kBuckets] = (uint32_t)tot;
     }
     __syncthreads();
-    // local stable sort of the tile into shared memory
+
+    // ---- local stable sort of the tile into shared memory
     #pragma unroll
     for (int r = 0; r < kPassIpt; ++r) {
         if (dw_r[r] != 0xffffffffu) {
-            const uint32_t d = dw_r[r] & 0xffu, wr = dw_r[r] >> 8;
-            const uint32_t lp = S.toff[d] + S.wcnt[warp][d] + wr;
+            const uint32_t dd = dw_r[r] & 0xffu, wr = dw_r[r] >> 8;
+            const uint32_t lp = S.toff[dd] + S.wcnt[warp][dd] + wr;
             S.keys[pad(lp)] = key_r[r];
             S.vals[pad(lp)] = val_r[r];
         }
@@ -658,43 +708,36 @@ k_radix_pass(const uint32_t *kin, const uint32_t *vin,
     __syncthreads();
     const uint32_t tn = S.toff[kBuckets];
 
-    // last pass: inclusive scan of A over the locally sorted tile
-    uint64_t scan_r[kPassIpt];
+    // last pass: exclusive scan of the values over the locally sorted tile;
+    // each thread keeps only its chunk's offset (the per-element values are
+    // recomputed after the look-back)
+    uint64_t chunk_ex = 0;
     if (last) {
         uint64_t run = 0;
         #pragma unroll
         for (int i = 0; i < kPassIpt; ++i) {
             const uint32_t lp = tid * kPassIpt + i;
-            const uint64_t v = lp < tn ? S.vals[pad(lp)] : 0;
-            scan_r[i] = run;          // exclusive within thread
-            run += v;
+            run += lp < tn ? S.vals[pad(lp)] : 0u;
         }
         uint64_t tot;
-        const uint64_t ex = block_excl_sum_u64(run, S.red, &tot);
+        chunk_ex = block_excl_sum_u64(run, S.red, &tot);
+        run = chunk_ex;
         #pragma unroll
         for (int i = 0; i < kPassIpt; ++i) {
             const uint32_t lp = tid * kPassIpt + i;
-            scan_r[i] += ex;          // exclusive prefix over the sorted tile
             if (lp < tn) {
-                const uint32_t d = ((S.keys[pad(lp)] - lmin) >> shift) & (kBuckets - 1);
-                if (lp == S.toff[d]) S.dscan[d] = scan_r[i];
-                if (lp + 1 == S.toff[d + 1] || lp + 1 == tn) S.dend[d] = scan_r[i] + S.vals[pad(lp)];
+                const uint32_t dd = ((S.keys[pad(lp)] - lmin) >> shift) & (kBuckets - 1);
+                if (lp == S.toff[dd]) S.dscan[dd] = run;
+                run += S.vals[pad(lp)];
             }
         }
-        __syncthreads();
     }
 
     // ---- decoupled look-back: thread d resolves digit d
     {
-        const int d = tid;
-        const uint64_t tsum = (last && tcount) ? (uint64_t)(S.dend[d] - S.dscan[d]) : 0ull;
-        unsigned long long *st = status + (int64_t)tile * kBuckets + d;
-        unsigned long long *ss = status_sum + 2 * ((int64_t)tile * kBuckets + d);
         uint64_t excl = 0, excl_sum = 0;
         bool abort = false;
         if (tile > 0) {
-            if (last) st_relaxed(ss, tsum);
-            st_release(st, status_word(epoch, kFlagAgg, tcount));
             int64_t j = (int64_t)tile - 1;
             uint32_t polls = 0, ns = 8;
             while (j >= 0) {
@@ -713,12 +756,12 @@ k_radix_pass(const uint32_t *kin, const uint32_t *vin,
                 if (fl == kFlagIncl) break;
                 --j;
             }
-        }
-        if (abort) {
-            st_release(st, status_word(epoch, kFlagAbort, 0));
-        } else {
-            if (last) st_relaxed(ss + 1, excl_sum + tsum);
-            st_release(st, status_word(epoch, kFlagIncl, excl + tcount));
+            if (abort) {
+                st_release(st, status_word(epoch, kFlagAbort, 0));
+            } else {
+                if (last) st_relaxed(ss + 1, excl_sum + tsum);
+                st_release(st, status_word(epoch, kFlagIncl, excl + tcount));
+            }
         }
         S.gbase[d] = S.boff[d] + (uint32_t)excl;
         if (last) S.gsum[d] = S.aoff[d] + excl_sum;
@@ -735,8 +778,8 @@ k_radix_pass(const uint32_t *kin, const uint32_t *vin,
             const uint32_t lp = r * kPassThreads + tid;
             if (lp < tn) {
                 const uint32_t key = S.keys[pad(lp)];
-                const uint32_t d = ((key - lmin) >> shift) & (kBuckets - 1);
-                const uint32_t gp = S.gbase[d] + (lp - S.toff[d]);
+                const uint32_t dd = ((key - lmin) >> shift) & (kBuckets - 1);
+                const uint32_t gp = S.gbase[dd] + (lp - S.toff[dd]);
                 if (gp < (uint64_t)n) {
                     kout[gp] = key;
                     vout[gp] = S.vals[pad(lp)];
@@ -750,16 +793,18 @@ k_radix_pass(const uint32_t *kin, const uint32_t *vin,
 
     // ---- final pass: evaluate every suffix (Alg. 3 lines 4-7) without scattering
     Candidate best{0, 0, 0, 0};
+    uint64_t run = chunk_ex;
     #pragma unroll
     for (int i = 0; i < kPassIpt; ++i) {
         const uint32_t lp = tid * kPassIpt + i;
         if (lp < tn) {
             const uint32_t key = S.keys[pad(lp)];
-            const uint32_t d = ((key - lmin) >> shift) & (kBuckets - 1);
-            const int64_t pos = (int64_t)S.gbase[d] + (lp - S.toff[d]);
-            const uint64_t prefix = S.gsum[d] + (scan_r[i] - S.dscan[d]);
+            const uint32_t dd = ((key - lmin) >> shift) & (kBuckets - 1);
+            const int64_t pos = (int64_t)S.gbase[dd] + (lp - S.toff[dd]);
+            const uint64_t prefix = S.gsum[dd] + (run - S.dscan[dd]);
             Candidate c{(int64_t)((uint64_t)m - prefix), n - pos, pos, (int64_t)key};
             if (cand_better(c, best)) best = c;
+            run += S.vals[pad(lp)];
         }
     }
     best = block_best(best, S.cred);
