@@ -279,8 +279,9 @@ int dsg_upload_csr(dsg_ctx *ctx, int64_t n, const int64_t *offsets, const int32_
     G->g.arcs = arcs;
     G->g.off = G->off;
     G->g.adj = G->adj;
-    // validation (monotone offsets, ids in range, no self-loops; with
-    // DSG_VALIDATE also strictly ascending lists and symmetry)
+    // validation: offsets first (monotone, inside [0, 2m]); the adjacency
+    // (ids in range, no self-loops; with DSG_VALIDATE also strictly ascending
+    // lists and symmetry) is checked in the pass that orients the graph
     int32_t h_err[8];
     if ((e = launch_validate(G->g, (flags & DSG_VALIDATE) ? 1 : 0, ctx->err_flags, ctx->stream)) != cudaSuccess)
         return bail(cuda_fail(ctx, e, "validate"));
@@ -298,12 +299,16 @@ int dsg_upload_csr(dsg_ctx *ctx, int64_t n, const int64_t *offsets, const int32_
     for (int i = 0; i < 5; ++i)
         if (h_err[i]) return bail(fail(ctx, DSG_ERR_INVALID, "invalid graph: %s", what[i]));
     G->g.max_degree = (int64_t)h_maxdeg;
-    G->g.sorted = h_err[5] ? 0 : 1;
     // degree-oriented copy for the sorting edge scan, and the chunk schedule
     // of its vertices of large out-degree
-    if ((e = build_orientation(G->g, ctx->stream, &G->ooff, &G->oadj, &G->hub, &G->g.n_hub, &G->hot,
+    if ((e = build_orientation(G->g, ctx->stream, (flags & DSG_VALIDATE) ? 1 : 0, ctx->err_flags,
+                               &G->g.sorted, &G->ooff, &G->oadj, &G->hub, &G->g.n_hub, &G->hot,
                                &G->g.n_hot)) != cudaSuccess)
         return bail(cuda_fail(ctx, e, "orientation"));
+    cudaMemcpyAsync(h_err, ctx->err_flags, sizeof(h_err), cudaMemcpyDeviceToHost, ctx->stream);
+    if ((e = cudaStreamSynchronize(ctx->stream)) != cudaSuccess) return bail(cuda_fail(ctx, e, "upload"));
+    for (int i = 0; i < 5; ++i)
+        if (h_err[i]) return bail(fail(ctx, DSG_ERR_INVALID, "invalid graph: %s", what[i]));
     G->g.ooff = G->ooff;
     G->g.oadj = G->oadj;
     G->g.hub_id = G->hub;

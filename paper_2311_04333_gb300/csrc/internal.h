@@ -157,9 +157,12 @@ cudaError_t launch_snapshot(const GraphDev &g, RunBufs &b, cudaStream_t s);
 cudaError_t launch_best_set(const GraphDev &g, RunBufs &b, int32_t *set_dev, cudaStream_t s,
                             int *launches);
 cudaError_t launch_loads_out(const GraphDev &g, RunBufs &b, int64_t *dst, cudaStream_t s);
-cudaError_t build_orientation(GraphDev &g, cudaStream_t s, int64_t **ooff_out, uint32_t **oadj_out,
-                              uint32_t **hub_out, int64_t *n_hub_out, uint32_t **hot_out,
-                              int64_t *n_hot_out);
+// Validates the adjacency (err[1..5] as in launch_validate; full = symmetry
+// and strict order too) while counting the degree-oriented out-degrees, then
+// builds the oriented copy unless an error was found.
+cudaError_t build_orientation(GraphDev &g, cudaStream_t s, int full, int32_t *err, int *sorted_out,
+                              int64_t **ooff_out, uint32_t **oadj_out, uint32_t **hub_out,
+                              int64_t *n_hub_out, uint32_t **hot_out, int64_t *n_hot_out);
 cudaError_t launch_asum_single_pass(const GraphDev &g, RunBufs &b, cudaStream_t s);
 cudaError_t launch_max_u64_of_i64(const int64_t *src, int64_t n, unsigned long long *dst,
                                   int *neg_flag, cudaStream_t s);

@@ -21,35 +21,38 @@ __device__ __forceinline__ bool has_arc(const int64_t *off, const int32_t *adj, 
     return false;
 }
 
-__global__ void k_validate(const int64_t *__restrict__ off, const int32_t *__restrict__ adj,
-                           int64_t n, int64_t arcs, int full, int32_t *err)
+// Vertices of degree > kBigDeg are processed by a whole block (the list of
+// them is built first), the others by one warp each.
+constexpr int64_t kBigDeg = 4096;
+
+__device__ __forceinline__ void check_arc(const int64_t *off, const int32_t *adj, int64_t n,
+                                          int64_t u, int64_t s, int64_t j, int full, int32_t *err)
 {
-    const int lane = threadIdx.x & 31;
-    const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t u = wid; u < n; u += nw) {
+    const int32_t w = adj[j];
+    if (w < 0 || w >= n) { atomicExch(&err[1], 1); return; }
+    if (w == (int32_t)u) atomicExch(&err[2], 1);
+    if (j > s && adj[j - 1] >= w) atomicExch(&err[5], 1);   // not strictly ascending
+    if (full) {
+        if (j > s && adj[j - 1] >= w) atomicExch(&err[3], 1);
+        if (!has_arc(off, adj, w, (int32_t)u)) atomicExch(&err[4], 1);
+    }
+}
+
+// offsets monotone and inside [0, arcs]: checked before anything reads adj
+__global__ void k_validate_offsets(const int64_t *__restrict__ off, int64_t n, int64_t arcs, int32_t *err)
+{
+    for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < n;
+         u += (int64_t)gridDim.x * blockDim.x) {
         const int64_t s = off[u], e = off[u + 1];
-        if (s < 0 || e > arcs || e < s) { if (lane == 0) atomicExch(&err[0], 1); continue; }
-        for (int64_t j = s + lane; j < e; j += 32) {
-            const int32_t w = adj[j];
-            if (w < 0 || w >= n) { atomicExch(&err[1], 1); continue; }
-            if (w == (int32_t)u) atomicExch(&err[2], 1);
-            if (j > s && adj[j - 1] >= w) atomicExch(&err[5], 1);   // not strictly ascending
-            if (full) {
-                if (j > s && adj[j - 1] >= w) atomicExch(&err[3], 1);
-                if (!has_arc(off, adj, w, (int32_t)u)) atomicExch(&err[4], 1);
-            }
-        }
+        if (s < 0 || e > arcs || e < s) atomicExch(&err[0], 1);
     }
 }
 
 cudaError_t launch_validate(const GraphDev &g, int full, int32_t *err_flags, cudaStream_t s)
 {
     cudaMemsetAsync(err_flags, 0, 8 * sizeof(int32_t), s);
-    int64_t warps = g.n;
-    int grid = (int)imin64((warps * 32 + 255) / 256, 152 * 16);
-    if (grid < 1) grid = 1;
-    k_validate<<<grid, 256, 0, s>>>(g.off, g.adj, g.n, g.arcs, full, err_flags);
+    const int grid = (int)imin64((g.n + 255) / 256, 152 * 16);
+    k_validate_offsets<<<grid, 256, 0, s>>>(g.off, g.n, g.arcs, err_flags);
     return cudaGetLastError();
 }
 
@@ -256,42 +259,89 @@ __global__ void k_hub_slots(const int64_t *__restrict__ off, int64_t n, int64_t 
     }
 }
 
-__device__ __forceinline__ bool oriented_keep(int64_t du, uint32_t u, int64_t dw, uint32_t w)
+__device__ __forceinline__ bool oriented_keep(uint32_t du, uint32_t u, uint32_t dw, uint32_t w)
 {
     return dw > du || (dw == du && w > u);
 }
 
-// warp per vertex: out-degree in the oriented graph
+// deg32[v] and the encoded arc target enc[v] (hub slot, hot slot or id)
+__global__ void k_deg_enc(const int64_t *__restrict__ off, int64_t n, const int32_t *__restrict__ hub_of,
+                          const int32_t *__restrict__ hot_of, uint32_t *deg32, uint32_t *enc)
+{
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        deg32[v] = (uint32_t)(off[v + 1] - off[v]);
+        const int32_t hs = hub_of[v];
+        const int32_t ts = hot_of ? hot_of[v] : -1;
+        enc[v] = hs >= 0 ? (kHubBit | (uint32_t)hs) : (ts >= 0 ? (kHotBit | (uint32_t)ts) : (uint32_t)v);
+    }
+}
+
+// validation of the adjacency (ids, self-loops, order, symmetry) fused with
+// the oriented out-degree: warp per vertex of degree <= kBigDeg
 __global__ void k_orient_count(const int64_t *__restrict__ off, const int32_t *__restrict__ adj,
-                               int64_t n, int64_t *ocnt)
+                               int64_t n, const uint32_t *__restrict__ deg32, int full, int32_t *err,
+                               int64_t *ocnt)
 {
     const int lane = threadIdx.x & 31;
     const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t u = wid; u < n; u += nw) {
-        const int64_t s = off[u], e = off[u + 1], du = e - s;
+        const int64_t s = off[u], e = off[u + 1];
+        const uint32_t du = (uint32_t)(e - s);
+        if (du > kBigDeg) continue;                         // k_orient_count_big
         uint32_t c = 0;
         for (int64_t j = s + lane; j < e; j += 32) {
-            const uint32_t w = (uint32_t)adj[j];
-            c += oriented_keep(du, (uint32_t)u, off[w + 1] - off[w], w);
+            check_arc(off, adj, n, u, s, j, full, err);
+            const int32_t w = adj[j];
+            if (w >= 0 && w < n) c += oriented_keep(du, (uint32_t)u, deg32[w], (uint32_t)w);
         }
         c = __reduce_add_sync(kFull, c);
         if (lane == 0) ocnt[u] = c;
     }
 }
 
-// warp per vertex: write the kept targets in list order, hub and hot targets
-// encoded
+// the same, one block per vertex of degree > kBigDeg
+__global__ void k_orient_count_big(const int64_t *__restrict__ off, const int32_t *__restrict__ adj,
+                                   int64_t n, const uint32_t *__restrict__ deg32,
+                                   const uint32_t *__restrict__ big, int64_t n_big, int full,
+                                   int32_t *err, int64_t *ocnt)
+{
+    __shared__ uint32_t red[32];
+    for (int64_t b = blockIdx.x; b < n_big; b += gridDim.x) {
+        const int64_t u = big[b], s = off[u], e = off[u + 1];
+        const uint32_t du = (uint32_t)(e - s);
+        uint32_t c = 0;
+        for (int64_t j = s + threadIdx.x; j < e; j += blockDim.x) {
+            check_arc(off, adj, n, u, s, j, full, err);
+            const int32_t w = adj[j];
+            if (w >= 0 && w < n) c += oriented_keep(du, (uint32_t)u, deg32[w], (uint32_t)w);
+        }
+        c = __reduce_add_sync(kFull, c);
+        __syncthreads();
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = c;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint32_t t = 0;
+            for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[i];
+            ocnt[u] = t;
+        }
+    }
+}
+
+// warp per vertex of degree <= kBigDeg: the kept targets in list order
 __global__ void k_orient_fill(const int64_t *__restrict__ off, const int32_t *__restrict__ adj,
                               int64_t n, const int64_t *__restrict__ ooff,
-                              const int32_t *__restrict__ slot_of,
-                              const int32_t *__restrict__ hot_of, uint32_t *oadj)
+                              const uint32_t *__restrict__ deg32, const uint32_t *__restrict__ enc,
+                              uint32_t *oadj)
 {
     const int lane = threadIdx.x & 31;
     const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t u = wid; u < n; u += nw) {
-        const int64_t s = off[u], e = off[u + 1], du = e - s;
+        const int64_t s = off[u], e = off[u + 1];
+        const uint32_t du = (uint32_t)(e - s);
+        if (du > kBigDeg) continue;
         int64_t o = ooff[u];
         for (int64_t j0 = s; j0 < e; j0 += 32) {
             const int64_t j = j0 + lane;
@@ -299,16 +349,47 @@ __global__ void k_orient_fill(const int64_t *__restrict__ off, const int32_t *__
             uint32_t w = 0;
             if (j < e) {
                 w = (uint32_t)adj[j];
-                keep = oriented_keep(du, (uint32_t)u, off[w + 1] - off[w], w);
+                keep = oriented_keep(du, (uint32_t)u, deg32[w], w);
             }
             const uint32_t m = __ballot_sync(kFull, keep);
-            if (keep) {
-                const int32_t sl = slot_of[w];
-                const int32_t hs = hot_of ? hot_of[w] : -1;
-                oadj[o + __popc(m & lanemask_lt())] =
-                    sl >= 0 ? (kHubBit | (uint32_t)sl) : (hs >= 0 ? (kHotBit | (uint32_t)hs) : w);
-            }
+            if (keep) oadj[o + __popc(m & lanemask_lt())] = enc[w];
             o += __popc(m);
+        }
+    }
+}
+
+// one block per vertex of degree > kBigDeg
+__global__ void k_orient_fill_big(const int64_t *__restrict__ off, const int32_t *__restrict__ adj,
+                                  const int64_t *__restrict__ ooff, const uint32_t *__restrict__ deg32,
+                                  const uint32_t *__restrict__ enc, const uint32_t *__restrict__ big,
+                                  int64_t n_big, uint32_t *oadj)
+{
+    __shared__ uint32_t wc[33];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    for (int64_t b = blockIdx.x; b < n_big; b += gridDim.x) {
+        const int64_t u = big[b], s = off[u], e = off[u + 1];
+        const uint32_t du = (uint32_t)(e - s);
+        int64_t o = ooff[u];
+        for (int64_t j0 = s; j0 < e; j0 += blockDim.x) {
+            const int64_t j = j0 + threadIdx.x;
+            bool keep = false;
+            uint32_t w = 0;
+            if (j < e) {
+                w = (uint32_t)adj[j];
+                keep = oriented_keep(du, (uint32_t)u, deg32[w], w);
+            }
+            const uint32_t m = __ballot_sync(kFull, keep);
+            __syncthreads();
+            if (lane == 0) wc[warp] = __popc(m);
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                uint32_t t = 0;
+                for (int i = 0; i < nwarp; ++i) { const uint32_t c = wc[i]; wc[i] = t; t += c; }
+                wc[32] = t;
+            }
+            __syncthreads();
+            if (keep) oadj[o + wc[warp] + __popc(m & lanemask_lt())] = enc[w];
+            o += wc[32];
         }
     }
 }
@@ -333,9 +414,9 @@ static cudaError_t degree_threshold(const GraphDev &g, int64_t cap, unsigned lon
 }
 
 // Builds ooff, oadj, hub_id and hot_id (allocated here, stream-ordered).
-cudaError_t build_orientation(GraphDev &g, cudaStream_t s, int64_t **ooff_out, uint32_t **oadj_out,
-                              uint32_t **hub_out, int64_t *n_hub_out, uint32_t **hot_out,
-                              int64_t *n_hot_out)
+cudaError_t build_orientation(GraphDev &g, cudaStream_t s, int full, int32_t *err, int *sorted_out,
+                              int64_t **ooff_out, uint32_t **oadj_out, uint32_t **hub_out,
+                              int64_t *n_hub_out, uint32_t **hot_out, int64_t *n_hot_out)
 {
     const int64_t n = g.n;
     cudaError_t e;
@@ -343,12 +424,13 @@ cudaError_t build_orientation(GraphDev &g, cudaStream_t s, int64_t **ooff_out, u
     // hub threshold: the smallest D >= 2 with #{deg >= D} <= kHubs
     unsigned long long *cnt = nullptr;
     int64_t *tmp = nullptr, *flag = nullptr;
-    int32_t *slot_of = nullptr;
+    int32_t *slot_of = nullptr, *slot_of_scratch = nullptr;
     const int64_t ntmp = scan_tmp_count(n + 1);
     if ((e = cudaMallocAsync((void **)&cnt, 8, s)) != cudaSuccess) return e;
     if ((e = cudaMallocAsync((void **)&tmp, 8 * (size_t)(ntmp + 2), s)) != cudaSuccess) return e;
     if ((e = cudaMallocAsync((void **)&flag, 8 * (size_t)(n + 1), s)) != cudaSuccess) return e;
     if ((e = cudaMallocAsync((void **)&slot_of, 4 * (size_t)n, s)) != cudaSuccess) return e;
+    if ((e = cudaMallocAsync((void **)&slot_of_scratch, 4 * (size_t)n, s)) != cudaSuccess) return e;
     int64_t D = 0;
     if ((e = degree_threshold(g, kHubs, cnt, grid, s, &D)) != cudaSuccess) return e;
     k_hub_flags<<<grid, 256, 0, s>>>(g.off, n, D, flag);
@@ -375,20 +457,47 @@ cudaError_t build_orientation(GraphDev &g, cudaStream_t s, int64_t **ooff_out, u
         if ((e = cudaMallocAsync((void **)&hot, 4 * (size_t)imax64(n_hot, 1), s)) != cudaSuccess) return e;
         k_hub_slots<<<grid, 256, 0, s>>>(g.off, n, Dh, flag, hot_of, hot);
     }
-    // oriented offsets
-    const int wgrid = (int)imin64((n * 32 + 255) / 256, 152 * 32);
-    k_orient_count<<<wgrid, 256, 0, s>>>(g.off, g.adj, n, flag);
-    cudaMemsetAsync(flag + n, 0, 8, s);
-    if ((e = scan_exclusive_i64(flag, n + 1, total, tmp, s)) != cudaSuccess) return e;
-    int64_t oarcs = 0;
-    cudaMemcpyAsync(&oarcs, total, 8, cudaMemcpyDeviceToHost, s);
+    // 32-bit degrees and encoded targets; list of vertices of degree > kBigDeg
+    uint32_t *deg32 = nullptr, *enc = nullptr, *big = nullptr;
+    if ((e = cudaMallocAsync((void **)&deg32, 4 * (size_t)n, s)) != cudaSuccess) return e;
+    if ((e = cudaMallocAsync((void **)&enc, 4 * (size_t)n, s)) != cudaSuccess) return e;
+    k_deg_enc<<<grid, 256, 0, s>>>(g.off, n, slot_of, hot_of, deg32, enc);
+    k_hub_flags<<<grid, 256, 0, s>>>(g.off, n, kBigDeg + 1, flag);
+    if ((e = scan_exclusive_i64(flag, n, total, tmp, s)) != cudaSuccess) return e;
+    int64_t n_big = 0;
+    cudaMemcpyAsync(&n_big, total, 8, cudaMemcpyDeviceToHost, s);
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+    if ((e = cudaMallocAsync((void **)&big, 4 * (size_t)imax64(n_big, 1), s)) != cudaSuccess) return e;
+    k_hub_slots<<<grid, 256, 0, s>>>(g.off, n, kBigDeg + 1, flag, slot_of_scratch, big);
+    // validation fused with the oriented out-degrees
+    const int wgrid = (int)imin64((n * 32 + 255) / 256, 152 * 32);
+    const int bgrid = (int)imin64(imax64(n_big, 1), 152 * 2);
+    k_orient_count<<<wgrid, 256, 0, s>>>(g.off, g.adj, n, deg32, full, err, flag);
+    if (n_big) k_orient_count_big<<<bgrid, 1024, 0, s>>>(g.off, g.adj, n, deg32, big, n_big, full, err, flag);
+    int32_t h_err[8];
+    cudaMemcpyAsync(h_err, err, sizeof(h_err), cudaMemcpyDeviceToHost, s);
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+    bool bad = false;
+    for (int i = 0; i < 5; ++i) bad |= h_err[i] != 0;
+    *sorted_out = h_err[5] ? 0 : 1;
+    int64_t oarcs = 0;
     uint32_t *oadj = nullptr;
-    if ((e = cudaMallocAsync((void **)&oadj, 4 * (size_t)imax64(oarcs, 1), s)) != cudaSuccess) return e;
-    k_orient_fill<<<wgrid, 256, 0, s>>>(g.off, g.adj, n, flag, slot_of, hot_of, oadj);
+    if (!bad) {
+        cudaMemsetAsync(flag + n, 0, 8, s);
+        if ((e = scan_exclusive_i64(flag, n + 1, total, tmp, s)) != cudaSuccess) return e;
+        cudaMemcpyAsync(&oarcs, total, 8, cudaMemcpyDeviceToHost, s);
+        if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+        if ((e = cudaMallocAsync((void **)&oadj, 4 * (size_t)imax64(oarcs, 1), s)) != cudaSuccess) return e;
+        k_orient_fill<<<wgrid, 256, 0, s>>>(g.off, g.adj, n, flag, deg32, enc, oadj);
+        if (n_big) k_orient_fill_big<<<bgrid, 1024, 0, s>>>(g.off, g.adj, flag, deg32, enc, big, n_big, oadj);
+    }
+    cudaFreeAsync(deg32, s);
+    cudaFreeAsync(enc, s);
+    cudaFreeAsync(big, s);
     cudaFreeAsync(cnt, s);
     cudaFreeAsync(tmp, s);
     cudaFreeAsync(slot_of, s);
+    cudaFreeAsync(slot_of_scratch, s);
     if (hot_of) cudaFreeAsync(hot_of, s);
     *ooff_out = flag;         // n + 1 exclusive prefix sums = oriented offsets
     *oadj_out = oadj;
