@@ -36,6 +36,9 @@ BLOCKS = [200 * (i + 1) for i in range(10)]
 T_ITERS = 20
 SAMPLE_SCALE = 21          # CPU baseline sample: same recipe, smaller scale
 METRIC = "GTEPS per Greedy++ iteration (HBM roofline %); batched graphs/s vs one-per-launch"
+BATCH_G = 4096
+BATCH_SEED = 4
+BATCH_T = 32
 UNIT = "GTEPS"
 
 
@@ -159,6 +162,47 @@ def cpu_baseline(budget_s: float = 20.0) -> dict:
                       f"m={g.m}, PaRSorting++ T={T}, {dt:.1f} s, sequential C oracle"}
 
 
+def bench_batch(dsg, ctx, graphs, args) -> dict:
+    """Graphs/s of the batched launch (autotuned block size) against one
+    dsg_run per graph on the same GPU, with identical per-graph results."""
+    import numpy as np
+    import torch
+    from paper_2311_04333_gb300 import tune
+    G = len(graphs)
+    T = np.full(G, BATCH_T, np.int32)
+    b = dsg.dsg_upload_batch(ctx, [(g.n, g.off, g.adj) for g in graphs], 0)
+    Gb, N, M = dsg.dsg_batch_info(b)
+    rec = tune.tune_batch(ctx, b, T, force=True)
+    th = rec["threads"]
+    best_b = np.zeros(4 * G, np.int64)
+    dsg.dsg_run_batch(ctx, b, dsg.DSG_SORTING, T, th, best_b)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.batch_steps):
+        dsg.dsg_run_batch(ctx, b, dsg.DSG_SORTING, T, th, best_b)
+    tb = (time.perf_counter() - t0) / args.batch_steps
+    dsg.dsg_free_batch(b)
+    # one graph per launch (graphs resident, outputs: the best triple)
+    hs = [dsg.dsg_upload_csr(ctx, g.n, g.off, g.adj, 0) for g in graphs]
+    best_1 = np.zeros((G, 4), np.int64)
+    dsg.dsg_run(ctx, hs[0], dsg.DSG_SORTING, BATCH_T)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i, h in enumerate(hs):
+        r = dsg.dsg_run(ctx, h, dsg.DSG_SORTING, BATCH_T)
+        best_1[i] = (r["best_edges"], r["best_vertices"], r["best_iter"], r["best_set_size"])
+    t1 = time.perf_counter() - t0
+    for h in hs:
+        dsg.dsg_free_graph(h)
+    same = bool(np.array_equal(best_b.reshape(G, 4), best_1))
+    return {"workload": f"{G} graphs, n log-uniform in [50, 50000] (ER / R-MAT / planted clique), "
+                        f"N={N}, M={M}, PaRSorting++ T={BATCH_T} each",
+            "graphs_per_s": G / tb, "ms_per_batch": tb * 1e3, "threads_per_graph": th,
+            "autotune_ms": rec["ms"], "one_per_launch_graphs_per_s": G / t1,
+            "one_per_launch_ms": t1 * 1e3, "speedup": t1 / tb, "identical_results": same,
+            "gteps_batched": M * BATCH_T / tb / 1e9}
+
+
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
@@ -197,9 +241,19 @@ def main():
     ap.add_argument("--scale", type=int, default=SCALE)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--batch-steps", type=int, default=3)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+
+    # the batched workload is generated before CUDA starts (process pool)
+    graphs_batch = None
+    if not args.no_batch:
+        import graphgen as gg
+        t0 = time.perf_counter()
+        graphs_batch = gg.batch_mix(BATCH_G, BATCH_SEED, processes=max(1, min(16, os.cpu_count() or 1)))
+        print(f"batch generated in {time.perf_counter() - t0:.1f} s", file=sys.stderr)
 
     import torch
     ws, rank, local = _dist()
@@ -284,6 +338,11 @@ def main():
     h2d = 8 * (n + 1) + 4 * 2 * m
     d2h = 8 * n + 4 * re["best_set_size"]
 
+    # ---- batched form: 4,096 graphs, one persistent launch vs one graph per launch
+    batched = None
+    if not args.no_batch:
+        batched = bench_batch(dsg, ctx, graphs_batch, args)
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline()
@@ -310,6 +369,7 @@ def main():
                     "d2h_bytes_per_step": d2h, "steps": args.e2e_steps},
             "gpu_launches": launches,
             "clocks": clk.summary(),
+            "batched": batched,
         }
         print(json.dumps(out))
     dsg.dsg_destroy(ctx)

@@ -194,47 +194,60 @@ def chung_lu(n: int, avg_degree: float, gamma: float, seed: int, drop_isolated: 
                           dict(recipe="chung_lu"))
 
 
-def batch_mix(G: int = 4096, seed: int = 4, n_lo: int = 50, n_hi: int = 50000) -> list[Graph]:
+def _batch_one(args):
+    g, seed, n_lo, n_hi = args
+    return _batch_graph(g, seed, n_lo, n_hi)
+
+
+def batch_mix(G: int = 4096, seed: int = 4, n_lo: int = 50, n_hi: int = 50000,
+              processes: int = 1) -> list[Graph]:
+    """The batched workload (see _batch_graph); `processes` > 1 generates the
+    graphs in a spawn-started process pool (safe after CUDA is initialised)."""
+    if processes > 1:
+        import multiprocessing as mp
+        with mp.get_context("spawn").Pool(processes) as pool:
+            return pool.map(_batch_one, [(g, seed, n_lo, n_hi) for g in range(G)], chunksize=16)
+    return [_batch_graph(g, seed, n_lo, n_hi) for g in range(G)]
+
+
+def _batch_graph(g: int, seed: int, n_lo: int, n_hi: int) -> Graph:
     """The batched workload: n = floor(exp(U(ln n_lo, ln n_hi))); type by index
     mod 3: ER with average degree U[4, 32]; R-MAT at scale ceil(log2 n) with
     edge factor 8 restricted to ids < n; ER with average degree 8 plus a
     planted clique of ceil(2 sqrt(n)) vertices.  Draws come from SplitMix64
     stream 100 of the seed (n) and stream 101 (degree)."""
-    graphs = []
-    for g in range(G):
-        u = _py_draw(seed, 100, g) / 2.0**64
-        n = int(math.floor(math.exp(math.log(n_lo) + u * (math.log(n_hi) - math.log(n_lo)))))
-        n = max(n_lo, min(n_hi, n))
-        kind = g % 3
-        gseed = seed * 1_000_003 + g
-        if kind == 0:
-            d = 4 + 28 * (_py_draw(seed, 101, g) / 2.0**64)
-            gr = er_m(n, d, gseed, drop_isolated=True)
-        elif kind == 1:
-            sc = max(1, math.ceil(math.log2(n)))
-            E = 8 * n
-            eu = np.zeros(E * 2, dtype=np.uint32)
-            ev = np.zeros(E * 2, dtype=np.uint32)
-            lib = _lib()
-            c = lib.gg_rmat(sc, 2 * E, gseed, _ptr(eu), _ptr(ev), 2 * E)
-            keep = (eu[:c] < n) & (ev[:c] < n)
-            eu2, ev2 = eu[:c][keep][:E], ev[:c][keep][:E]
-            gr = csr_from_pairs(n, eu2, ev2, True, f"rmatb{n}_s{gseed}", dict(recipe="rmat_batch"))
-        else:
-            k = int(math.ceil(2 * math.sqrt(n)))
-            M = n * 4
-            eu = np.zeros(M + k * (k - 1) // 2, dtype=np.uint32)
-            ev = np.zeros_like(eu)
-            lib = _lib()
-            lib.gg_er_m(n, M, gseed, _ptr(eu), _ptr(ev), M)
-            kk = np.array(_py_sample(gseed, n, k), dtype=np.uint32)
-            ia, ib = np.triu_indices(k, 1)
-            eu[M:] = kk[ia]
-            ev[M:] = kk[ib]
-            gr = csr_from_pairs(n, eu, ev, True, f"erk{n}_s{gseed}", dict(recipe="er_clique"))
-        gr.meta["index"] = g
-        graphs.append(gr)
-    return graphs
+    u = _py_draw(seed, 100, g) / 2.0**64
+    n = int(math.floor(math.exp(math.log(n_lo) + u * (math.log(n_hi) - math.log(n_lo)))))
+    n = max(n_lo, min(n_hi, n))
+    kind = g % 3
+    gseed = seed * 1_000_003 + g
+    if kind == 0:
+        d = 4 + 28 * (_py_draw(seed, 101, g) / 2.0**64)
+        gr = er_m(n, d, gseed, drop_isolated=True)
+    elif kind == 1:
+        sc = max(1, math.ceil(math.log2(n)))
+        E = 8 * n
+        eu = np.zeros(E * 2, dtype=np.uint32)
+        ev = np.zeros(E * 2, dtype=np.uint32)
+        lib = _lib()
+        c = lib.gg_rmat(sc, 2 * E, gseed, _ptr(eu), _ptr(ev), 2 * E)
+        keep = (eu[:c] < n) & (ev[:c] < n)
+        eu2, ev2 = eu[:c][keep][:E], ev[:c][keep][:E]
+        gr = csr_from_pairs(n, eu2, ev2, True, f"rmatb{n}_s{gseed}", dict(recipe="rmat_batch"))
+    else:
+        k = int(math.ceil(2 * math.sqrt(n)))
+        M = n * 4
+        eu = np.zeros(M + k * (k - 1) // 2, dtype=np.uint32)
+        ev = np.zeros_like(eu)
+        lib = _lib()
+        lib.gg_er_m(n, M, gseed, _ptr(eu), _ptr(ev), M)
+        kk = np.array(_py_sample(gseed, n, k), dtype=np.uint32)
+        ia, ib = np.triu_indices(k, 1)
+        eu[M:] = kk[ia]
+        ev[M:] = kk[ib]
+        gr = csr_from_pairs(n, eu, ev, True, f"erk{n}_s{gseed}", dict(recipe="er_clique"))
+    gr.meta["index"] = g
+    return gr
 
 
 # small deterministic graphs (closed-form test inputs)

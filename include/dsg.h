@@ -138,6 +138,50 @@ int dsg_run(dsg_graph *g, int variant, int32_t T, int64_t eps_num, int64_t eps_d
 /* Free an uploaded graph (stream-ordered release of its device memory). */
 void dsg_free_graph(dsg_graph *g);
 
+/* ---- batches of small graphs --------------------------------------------- */
+
+/* Per-graph outputs of dsg_run_batch.  The caller sets the pointers (loads,
+ * sets and trace may be NULL; best may not) and flags:
+ *   best[4*g .. 4*g+3]: best edges, best vertices, best iteration (0 = S = G
+ *     never beaten) and best-set size of graph g (the fields of dsg_result);
+ *   loads[N]: final loads, graph g's at positions vbase(g) .. vbase(g)+n_g-1
+ *     where vbase(g) = n_0 + ... + n_{g-1} (the packing order);
+ *   sets[N]: graph g's best set (ascending local ids) from position vbase(g);
+ *   trace[3*(g*Tmax + t)]: as dsg_result.trace, Tmax = max_g T[g]. */
+typedef struct {
+    uint32_t flags;       /* DSG_DST_DEVICE: pointers below are device pointers */
+    int64_t *best;
+    int64_t *loads;
+    int32_t *sets;
+    int64_t *trace;
+} dsg_batch_result;
+
+/* Upload G >= 1 graphs as one packed batch (copied; host arrays).  Graph g
+ * has n_per[g] >= 1 vertices, offsets[g][0..n_per[g]] (int64, starting at 0)
+ * and adj[g] (int32 local ids); the same rules as dsg_upload_csr apply to
+ * each (DSG_VALIDATE adds the strict-order and symmetry checks).  The total
+ * vertex count must stay below 2^31.  Errors: DSG_ERR_INVALID, DSG_ERR_NOMEM. */
+int dsg_upload_batch(dsg_ctx *ctx, int32_t G, const int64_t *n_per, const int64_t *const *offsets,
+                     const int32_t *const *adj, uint32_t flags, dsg_batch **out);
+
+/* Number of graphs, total vertices and total edges of a batch. */
+int dsg_batch_info(const dsg_batch *b, int32_t *G, int64_t *total_n, int64_t *total_m);
+
+/* Run T[g] >= 1 PaRSorting++ iterations on every graph g of the batch in one
+ * persistent launch: each thread block takes whole graphs, largest first,
+ * and runs all their iterations (loads start at zero).  The results of
+ * graph g are those dsg_run(DSG_SORTING, T[g]) gives on it alone.
+ *   variant: DSG_SORTING only (DSG_PEELING: DSG_ERR_INVALID);
+ *   threads_per_graph: 256, 512 or 1024 threads per block, 0 = default
+ *     (the tuning knob an autotuner sets).
+ * DSG_ERR_OVERFLOW if a graph's T * max_degree reaches 2^32.  Synchronises
+ * the context stream before returning. */
+int dsg_run_batch(dsg_batch *b, int variant, const int32_t *T, int32_t threads_per_graph,
+                  dsg_batch_result *out);
+
+/* Free a batch. */
+void dsg_free_batch(dsg_batch *b);
+
 /* ---- instrumentation ---------------------------------------------------- */
 
 /* Kernel phases timed when profiling is on (dsg_set_profiling). */

@@ -13,7 +13,8 @@ import numpy as np
 
 from ._dsg import (DSG_DST_DEVICE, DSG_INIT_DEVICE, DSG_NOALLOC_MAX_VERTICES, DSG_PEELING,
                    DSG_SORTING, DSG_SRC_DEVICE, DSG_VALIDATE, DsgError, LIB_PATH, dsg_create,
-                   dsg_densest_suffix_noalloc, dsg_destroy, dsg_free_graph,
+                   dsg_batch_info, dsg_densest_suffix_noalloc, dsg_destroy, dsg_free_batch,
+                   dsg_free_graph, dsg_run_batch, dsg_upload_batch,
                    dsg_get_stats, dsg_graph_info, dsg_last_error, dsg_run, dsg_set_profiling,
                    dsg_upload_csr)
 
@@ -21,7 +22,8 @@ __all__ = ["DSG_SORTING", "DSG_PEELING", "DSG_VALIDATE", "DSG_SRC_DEVICE", "DSG_
            "DSG_INIT_DEVICE", "DsgError", "LIB_PATH", "dsg_create", "dsg_destroy",
            "dsg_free_graph", "dsg_get_stats", "dsg_graph_info", "dsg_last_error", "dsg_run",
            "dsg_set_profiling", "dsg_upload_csr", "dsg_densest_suffix_noalloc",
-           "DSG_NOALLOC_MAX_VERTICES", "Result", "densest"]
+           "DSG_NOALLOC_MAX_VERTICES", "dsg_upload_batch", "dsg_batch_info", "dsg_run_batch",
+           "dsg_free_batch", "Result", "densest"]
 
 
 @dataclass

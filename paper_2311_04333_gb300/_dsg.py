@@ -38,6 +38,11 @@ class dsg_result(ctypes.Structure):
                 ("best_set", ctypes.c_void_p), ("trace", ctypes.c_void_p)]
 
 
+class dsg_batch_result(ctypes.Structure):
+    _fields_ = [("flags", ctypes.c_uint32), ("best", ctypes.c_void_p), ("loads", ctypes.c_void_p),
+                ("sets", ctypes.c_void_p), ("trace", ctypes.c_void_p)]
+
+
 def _load():
     path = os.environ.get("DSG_LIB") or _build.build()
     lib = ctypes.CDLL(path)
@@ -55,6 +60,11 @@ def _load():
     lib.dsg_set_profiling.argtypes = [P, I]
     lib.dsg_get_stats.argtypes = [P, P, P, P, I]
     lib.dsg_densest_suffix_noalloc.argtypes = [P, P, I64, I64, P, P]
+    lib.dsg_upload_batch.argtypes = [P, I32, P, P, P, U32, ctypes.POINTER(P)]
+    lib.dsg_batch_info.argtypes = [P, P, P, P]
+    lib.dsg_run_batch.argtypes = [P, I, P, I32, ctypes.POINTER(dsg_batch_result)]
+    lib.dsg_free_batch.argtypes = [P]
+    lib.dsg_free_batch.restype = None
     return lib
 
 
@@ -173,8 +183,52 @@ def dsg_densest_suffix_noalloc(loads, A, n: int, m: int, result, stream: int | N
                            f"(n must be in [1, {DSG_NOALLOC_MAX_VERTICES}])")
 
 
+def dsg_upload_batch(ctx, graphs, flags: int = 0):
+    """graphs: sequence of (n, offsets int64[n+1], adj int32[2m]) host arrays."""
+    G = len(graphs)
+    n_per = np.array([int(g[0]) for g in graphs], dtype=np.int64)
+    offs = [np.ascontiguousarray(g[1], dtype=np.int64) for g in graphs]
+    adjs = [np.ascontiguousarray(g[2], dtype=np.int32) for g in graphs]
+    poff = (ctypes.c_void_p * G)(*[o.ctypes.data for o in offs])
+    padj = (ctypes.c_void_p * G)(*[a.ctypes.data for a in adjs])
+    out = ctypes.c_void_p()
+    _check(ctx, LIB.dsg_upload_batch(ctx, G, n_per.ctypes.data, poff, padj, flags, ctypes.byref(out)))
+    return out.value
+
+
+def dsg_batch_info(batch) -> tuple[int, int, int]:
+    G, n, m = ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int64()
+    rc = LIB.dsg_batch_info(batch, ctypes.byref(G), ctypes.byref(n), ctypes.byref(m))
+    if rc != DSG_OK:
+        raise DsgError(rc, "dsg_batch_info")
+    return G.value, n.value, m.value
+
+
+def dsg_run_batch(ctx, batch, variant: int, T, threads_per_graph: int = 0, best=None, loads=None,
+                  sets=None, trace=None) -> None:
+    """T: int32[G]; best: int64[4G] (required); loads int64[N], sets int32[N],
+    trace int64[3*G*Tmax] optional; all host or all device."""
+    T = np.ascontiguousarray(T, dtype=np.int32)
+    res = dsg_batch_result()
+    pb, db = _ptr(best, np.int64)
+    pl, dl = _ptr(loads, np.int64)
+    ps, ds = _ptr(sets, np.int32)
+    pt, dt = _ptr(trace, np.int64)
+    dev = {d for p, d in ((pb, db), (pl, dl), (ps, ds), (pt, dt)) if p is not None}
+    if len(dev) > 1:
+        raise ValueError("output buffers must all be host or all device")
+    res.flags = DSG_DST_DEVICE if dev == {True} else 0
+    res.best, res.loads, res.sets, res.trace = pb, pl, ps, pt
+    _check(ctx, LIB.dsg_run_batch(batch, variant, T.ctypes.data, threads_per_graph, ctypes.byref(res)))
+
+
+def dsg_free_batch(batch) -> None:
+    LIB.dsg_free_batch(batch)
+
+
 DSG_NOALLOC_MAX_VERTICES = 262144
 
 EXPORTED = ["dsg_create", "dsg_destroy", "dsg_last_error", "dsg_upload_csr", "dsg_graph_info",
             "dsg_run", "dsg_free_graph", "dsg_set_profiling", "dsg_get_stats",
-            "dsg_densest_suffix_noalloc"]
+            "dsg_densest_suffix_noalloc", "dsg_upload_batch", "dsg_batch_info", "dsg_run_batch",
+            "dsg_free_batch"]

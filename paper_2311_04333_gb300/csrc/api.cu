@@ -6,6 +6,10 @@
 #include <string>
 #include <vector>
 
+#include <algorithm>
+#include <numeric>
+
+#include "batch.h"
 #include "dsg.h"
 #include "internal.h"
 #include "peeling.h"
@@ -48,6 +52,18 @@ struct dsg_graph {
     int32_t *npass_log = nullptr;
     PeelBufs pb{};
     bool pb_ready = false;
+};
+
+struct dsg_batch {
+    dsg_ctx *ctx = nullptr;
+    int32_t G = 0;
+    int64_t N = 0, arcs = 0;
+    std::vector<int64_t> maxdeg;     // per graph
+    int64_t *vbase = nullptr, *off = nullptr;
+    int32_t *adj = nullptr, *order = nullptr, *T = nullptr;
+    uint32_t *graph_ctr = nullptr;
+    void *run_mem = nullptr;         // loads, A, keys, ids, best_loads, staging
+    size_t run_bytes = 0;
 };
 
 namespace {
@@ -515,6 +531,188 @@ int dsg_run(dsg_graph *G, int variant, int32_t T, int64_t eps_num, int64_t eps_d
     out->best_set_size = h.set_size;
     if (ctx->profiling) collect_timings(ctx);
     return DSG_OK;
+}
+
+int dsg_upload_batch(dsg_ctx *ctx, int32_t G, const int64_t *n_per, const int64_t *const *offsets,
+                     const int32_t *const *adj, uint32_t flags, dsg_batch **out)
+{
+    if (!ctx || !out) return DSG_ERR_INVALID;
+    *out = nullptr;
+    if (G < 1 || !n_per || !offsets || !adj) return fail(ctx, DSG_ERR_INVALID, "G = %d: need G >= 1 and arrays", G);
+    if (flags & DSG_SRC_DEVICE) return fail(ctx, DSG_ERR_INVALID, "dsg_upload_batch takes host arrays");
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    std::vector<int64_t> vbase(G + 1, 0), abase(G + 1, 0);
+    std::vector<int64_t> maxdeg(G, 0);
+    for (int32_t g = 0; g < G; ++g) {
+        const int64_t n = n_per[g];
+        if (n < 1) return fail(ctx, DSG_ERR_INVALID, "graph %d: n = %lld", g, (long long)n);
+        if (!offsets[g] || offsets[g][0] != 0)
+            return fail(ctx, DSG_ERR_INVALID, "graph %d: offsets must start at 0", g);
+        const int64_t a = offsets[g][n];
+        if (a < 0 || (a & 1)) return fail(ctx, DSG_ERR_INVALID, "graph %d: offsets[n] = %lld must be even", g, (long long)a);
+        if (a > 0 && !adj[g]) return fail(ctx, DSG_ERR_INVALID, "graph %d: adj is NULL", g);
+        for (int64_t v = 0; v < n; ++v) {
+            const int64_t d = offsets[g][v + 1] - offsets[g][v];
+            if (d < 0) return fail(ctx, DSG_ERR_INVALID, "graph %d: offsets are not non-decreasing", g);
+            maxdeg[g] = std::max(maxdeg[g], d);
+        }
+        vbase[g + 1] = vbase[g] + n;
+        abase[g + 1] = abase[g] + a;
+    }
+    const int64_t N = vbase[G], arcs = abase[G];
+    if (N >= ((int64_t)1 << 31)) return fail(ctx, DSG_ERR_INVALID, "total vertices %lld >= 2^31", (long long)N);
+    std::vector<int64_t> off(N + 1);
+    std::vector<int32_t> adjp((size_t)std::max<int64_t>(arcs, 1));
+    for (int32_t g = 0; g < G; ++g) {
+        const int64_t n = n_per[g];
+        for (int64_t v = 0; v < n; ++v) off[vbase[g] + v] = abase[g] + offsets[g][v];
+        if (abase[g + 1] > abase[g])
+            std::memcpy(adjp.data() + abase[g], adj[g], sizeof(int32_t) * (size_t)(abase[g + 1] - abase[g]));
+    }
+    off[N] = arcs;
+    std::vector<int32_t> order(G);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+        return (abase[a + 1] - abase[a]) + (vbase[a + 1] - vbase[a]) > (abase[b + 1] - abase[b]) + (vbase[b + 1] - vbase[b]);
+    });
+    dsg_batch *B = new (std::nothrow) dsg_batch;
+    if (!B) return fail(ctx, DSG_ERR_NOMEM, "host allocation");
+    B->ctx = ctx;
+    B->G = G;
+    B->N = N;
+    B->arcs = arcs;
+    B->maxdeg = maxdeg;
+    auto bail = [&](int code) { dsg_free_batch(B); return code; };
+    cudaError_t e;
+    cudaStream_t st = ctx->stream;
+    if ((e = cudaMallocAsync((void **)&B->vbase, 8 * (size_t)(G + 1), st)) != cudaSuccess ||
+        (e = cudaMallocAsync((void **)&B->off, 8 * (size_t)(N + 1), st)) != cudaSuccess ||
+        (e = cudaMallocAsync((void **)&B->adj, 4 * adjp.size(), st)) != cudaSuccess ||
+        (e = cudaMallocAsync((void **)&B->order, 4 * (size_t)G, st)) != cudaSuccess ||
+        (e = cudaMallocAsync((void **)&B->T, 4 * (size_t)G, st)) != cudaSuccess ||
+        (e = cudaMallocAsync((void **)&B->graph_ctr, 4, st)) != cudaSuccess)
+        return bail(cuda_fail(ctx, e, "batch allocation"));
+    cudaMemcpyAsync(B->vbase, vbase.data(), 8 * (size_t)(G + 1), cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(B->off, off.data(), 8 * (size_t)(N + 1), cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(B->adj, adjp.data(), 4 * adjp.size(), cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(B->order, order.data(), 4 * (size_t)G, cudaMemcpyHostToDevice, st);
+    BatchDev bd{};
+    bd.G = G;
+    bd.vbase = B->vbase;
+    bd.off = B->off;
+    bd.adj = B->adj;
+    if ((e = launch_batch_validate(bd, (flags & DSG_VALIDATE) ? 1 : 0, ctx->err_flags, st)) != cudaSuccess)
+        return bail(cuda_fail(ctx, e, "batch validation"));
+    int32_t h_err[8];
+    cudaMemcpyAsync(h_err, ctx->err_flags, sizeof(h_err), cudaMemcpyDeviceToHost, st);
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return bail(cuda_fail(ctx, e, "batch upload"));
+    static const char *what[5] = {"offsets are not non-decreasing", "a neighbour id is out of [0, n)",
+                                  "a graph has a self-loop",
+                                  "an adjacency list is not strictly ascending (duplicate or unsorted)",
+                                  "a graph is not symmetric"};
+    for (int i = 0; i < 5; ++i)
+        if (h_err[i]) return bail(fail(ctx, DSG_ERR_INVALID, "invalid batch: %s", what[i]));
+    ctx->launches[DSG_PHASE_OTHER] += 1;
+    *out = B;
+    return DSG_OK;
+}
+
+int dsg_batch_info(const dsg_batch *b, int32_t *G, int64_t *total_n, int64_t *total_m)
+{
+    if (!b) return DSG_ERR_INVALID;
+    if (G) *G = b->G;
+    if (total_n) *total_n = b->N;
+    if (total_m) *total_m = b->arcs / 2;
+    return DSG_OK;
+}
+
+int dsg_run_batch(dsg_batch *Bt, int variant, const int32_t *T, int32_t threads_per_graph,
+                  dsg_batch_result *out)
+{
+    if (!Bt || !out) return DSG_ERR_INVALID;
+    dsg_ctx *ctx = Bt->ctx;
+    if (variant != DSG_SORTING) return fail(ctx, DSG_ERR_INVALID, "batches run DSG_SORTING only");
+    if (!T || !out->best) return fail(ctx, DSG_ERR_INVALID, "T and out->best are required");
+    const int threads = threads_per_graph ? threads_per_graph : 512;
+    if (threads != 256 && threads != 512 && threads != 1024)
+        return fail(ctx, DSG_ERR_INVALID, "threads_per_graph = %d: use 256, 512 or 1024", threads_per_graph);
+    int32_t Tmax = 0;
+    for (int32_t g = 0; g < Bt->G; ++g) {
+        if (T[g] < 1) return fail(ctx, DSG_ERR_INVALID, "T[%d] = %d must be >= 1", g, T[g]);
+        if ((unsigned long long)T[g] * (unsigned long long)Bt->maxdeg[g] >= (1ull << 32))
+            return fail(ctx, DSG_ERR_OVERFLOW, "graph %d: T * max_degree does not fit 32-bit loads", g);
+        Tmax = std::max(Tmax, T[g]);
+    }
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    cudaStream_t st = ctx->stream;
+    const int64_t N = Bt->N, G = Bt->G;
+    const bool dev = out->flags & DSG_DST_DEVICE;
+    // run state (+ staging for host outputs)
+    const size_t need = align256(4 * (size_t)N) * 3 + align256(8 * (size_t)N) * 2 + align256(8 * (size_t)N)
+                      + align256(4 * (size_t)N) + align256(32 * (size_t)G) + align256(24 * (size_t)G * Tmax);
+    if (Bt->run_bytes < need) {
+        if (Bt->run_mem) cudaFreeAsync(Bt->run_mem, st);
+        Bt->run_mem = nullptr;
+        Bt->run_bytes = 0;
+        CK(cudaMallocAsync(&Bt->run_mem, need, st), "batch run buffers");
+        Bt->run_bytes = need;
+    }
+    char *p = (char *)Bt->run_mem;
+    auto take = [&](size_t b) { char *q = p; p += align256(b); return (void *)q; };
+    BatchDev bd{};
+    bd.G = (int32_t)G;
+    bd.Tmax = Tmax;
+    bd.vbase = Bt->vbase;
+    bd.off = Bt->off;
+    bd.adj = Bt->adj;
+    bd.order = Bt->order;
+    bd.T = Bt->T;
+    bd.init = nullptr;
+    bd.loads = (uint32_t *)take(4 * (size_t)N);
+    bd.A = (uint32_t *)take(4 * (size_t)N);
+    bd.best_loads = (uint32_t *)take(4 * (size_t)N);
+    bd.keys = (uint32_t *)take(8 * (size_t)N);
+    bd.ids = (uint32_t *)take(8 * (size_t)N);
+    int64_t *st_loads = (int64_t *)take(8 * (size_t)N);
+    int32_t *st_sets = (int32_t *)take(4 * (size_t)N);
+    int64_t *st_best = (int64_t *)take(32 * (size_t)G);
+    int64_t *st_trace = (int64_t *)take(24 * (size_t)G * Tmax);
+    bd.loads_out = out->loads ? (dev ? out->loads : st_loads) : nullptr;
+    bd.sets = out->sets ? (dev ? out->sets : st_sets) : nullptr;
+    bd.best = dev ? out->best : st_best;
+    bd.trace = out->trace ? (dev ? out->trace : st_trace) : nullptr;
+    CK(cudaMemcpyAsync(Bt->T, T, 4 * (size_t)G, cudaMemcpyHostToDevice, st), "T copy");
+    {
+        PhaseTimer pt(ctx, DSG_PHASE_OTHER);
+        CK(launch_batch_sorting(bd, threads, ctx->sm_count, Bt->graph_ctr, st), "batch kernel");
+    }
+    ctx->launches[DSG_PHASE_OTHER] += 1;
+    if (!dev) {
+        CK(cudaMemcpyAsync(out->best, st_best, 32 * (size_t)G, cudaMemcpyDeviceToHost, st), "best D2H");
+        if (out->loads) CK(cudaMemcpyAsync(out->loads, st_loads, 8 * (size_t)N, cudaMemcpyDeviceToHost, st), "loads D2H");
+        if (out->sets) CK(cudaMemcpyAsync(out->sets, st_sets, 4 * (size_t)N, cudaMemcpyDeviceToHost, st), "sets D2H");
+        if (out->trace) CK(cudaMemcpyAsync(out->trace, st_trace, 24 * (size_t)G * Tmax, cudaMemcpyDeviceToHost, st), "trace D2H");
+    }
+    CK(cudaStreamSynchronize(st), "batch run");
+    if (ctx->profiling) collect_timings(ctx);
+    return DSG_OK;
+}
+
+void dsg_free_batch(dsg_batch *B)
+{
+    if (!B) return;
+    dsg_ctx *ctx = B->ctx;
+    cudaSetDevice(ctx->device);
+    cudaStream_t st = ctx->stream;
+    if (B->vbase) cudaFreeAsync(B->vbase, st);
+    if (B->off) cudaFreeAsync(B->off, st);
+    if (B->adj) cudaFreeAsync(B->adj, st);
+    if (B->order) cudaFreeAsync(B->order, st);
+    if (B->T) cudaFreeAsync(B->T, st);
+    if (B->graph_ctr) cudaFreeAsync(B->graph_ctr, st);
+    if (B->run_mem) cudaFreeAsync(B->run_mem, st);
+    cudaStreamSynchronize(st);
+    delete B;
 }
 
 }  // extern "C"

@@ -1,0 +1,332 @@
+// k_batch.cu -- batched PaRSorting++ (the refine step of arXiv 2311.04333,
+// Sec. 3.2-3.3 with Alg. 3) for many small graphs packed into one segmented
+// CSR.  One persistent launch: every block takes whole graphs from an atomic
+// queue (largest first) and runs all T iterations of a graph by itself:
+//   edge scan  A[u] = #{w in N(u) : (l[w], w) > (l[u], u)}    (warp per vertex)
+//   sort       stable LSD radix sort of the ids by l - min l (8-bit digits);
+//              the block's warps own contiguous segments: count, scan in
+//              (digit, warp) order, ranked scatter
+//   suffix     B[i] = sum_{j >= i} A[v_j]; first maximum of B[i] / (n - i)
+//              (Alg. 3 lines 4-7); strict update of the graph's best (Alg. 2)
+//   loads      l += A                                       (Alg. 3 lines 8-9)
+// and finally extracts the best vertex set.  Graph g owns vertices
+// [vbase[g], vbase[g+1]) and arcs [off[vbase[g]], off[vbase[g+1]]) of the
+// packed arrays; adjacency entries are local ids.
+#include "batch.h"
+#include "common.cuh"
+
+namespace dsg {
+namespace {
+
+template <int NT>
+struct BatchSmem {
+    uint32_t cnt[NT / 32][kBuckets];     // per-warp digit counts, then write cursors
+    uint32_t base[kBuckets];
+    unsigned long long red[33];
+    Candidate cred[32];
+    uint32_t wred[32];
+    uint32_t graph;
+};
+
+template <int NT>
+__device__ __forceinline__ uint32_t block_reduce_u32(uint32_t x, bool is_max, BatchSmem<NT> &S)
+{
+    x = is_max ? __reduce_max_sync(kFull, x) : __reduce_min_sync(kFull, x);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) S.wred[threadIdx.x >> 5] = x;
+    __syncthreads();
+    uint32_t r = is_max ? 0u : 0xffffffffu;
+    for (int i = 0; i < NT / 32; ++i) r = is_max ? max(r, S.wred[i]) : min(r, S.wred[i]);
+    __syncthreads();
+    return r;
+}
+
+// lanes (among the valid ones) holding the same 8-bit digit (bit-sliced match)
+__device__ __forceinline__ uint32_t digit_peers(uint32_t d, bool valid)
+{
+    uint32_t peers = __ballot_sync(kFull, valid);
+    #pragma unroll
+    for (int bit = 0; bit < kRadixBits; ++bit) {
+        const uint32_t bb = __ballot_sync(kFull, (d >> bit) & 1u);
+        peers &= ((d >> bit) & 1u) ? bb : ~bb;
+    }
+    return valid ? peers : 0u;
+}
+
+// One stable LSD pass over elements 0..n-1: (kin, iin) -> (kout, iout) by
+// the digit (key >> shift) & 255.  kin == nullptr: keys are L[i] - lmin and
+// ids are i (the loads read in id order).
+template <int NT>
+__device__ void block_radix_pass(const uint32_t *kin, const uint32_t *iin, const uint32_t *L,
+                                 uint32_t lmin, uint32_t *kout, uint32_t *iout, uint32_t n,
+                                 int shift, BatchSmem<NT> &S)
+{
+    constexpr int NW = NT / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t seg = (n + NW - 1) / NW;
+    const uint32_t b0 = min(n, warp * seg), b1 = min(n, b0 + seg);
+    for (int i = threadIdx.x; i < NW * kBuckets; i += NT) (&S.cnt[0][0])[i] = 0;
+    __syncthreads();
+    for (uint32_t r = b0; r < b1; r += 32) {
+        const uint32_t i = r + lane;
+        const bool valid = i < b1;
+        const uint32_t key = valid ? (kin ? kin[i] : L[i] - lmin) : 0u;
+        const uint32_t d = (key >> shift) & (kBuckets - 1);
+        const uint32_t peers = digit_peers(d, valid);
+        if (valid && (peers >> lane) == 1u) S.cnt[warp][d] += __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    // per digit: exclusive prefix over the warps, and the digit's total
+    uint32_t total = 0;
+    if (threadIdx.x < kBuckets) {
+        const int d = threadIdx.x;
+        for (int w = 0; w < NW; ++w) {
+            const uint32_t c = S.cnt[w][d];
+            S.cnt[w][d] = total;
+            total += c;
+        }
+    }
+    uint64_t all;
+    const uint64_t ex = block_excl_sum_u64(threadIdx.x < kBuckets ? total : 0u, S.red, &all);
+    if (threadIdx.x < kBuckets) S.base[threadIdx.x] = (uint32_t)ex;
+    __syncthreads();
+    for (int i = threadIdx.x; i < NW * kBuckets; i += NT) (&S.cnt[0][0])[i] += S.base[i % kBuckets];
+    __syncthreads();
+    // ranked scatter of the warp's segment, in order
+    for (uint32_t r = b0; r < b1; r += 32) {
+        const uint32_t i = r + lane;
+        const bool valid = i < b1;
+        const uint32_t key = valid ? (kin ? kin[i] : L[i] - lmin) : 0u;
+        const uint32_t id = valid ? (iin ? iin[i] : i) : 0u;
+        const uint32_t d = (key >> shift) & (kBuckets - 1);
+        const uint32_t peers = digit_peers(d, valid);
+        uint32_t cur = 0;
+        if (valid) cur = S.cnt[warp][d];
+        __syncwarp();
+        if (valid) {
+            const uint32_t p = cur + __popc(peers & lanemask_lt());
+            kout[p] = key;
+            iout[p] = id;
+            if ((peers >> lane) == 1u) S.cnt[warp][d] = cur + __popc(peers);
+        }
+        __syncwarp();
+    }
+    __syncthreads();
+}
+
+template <int NT>
+__global__ void __launch_bounds__(NT, 1024 / NT)
+k_batch_sorting(BatchDev B, uint32_t *graph_ctr)
+{
+    __shared__ BatchSmem<NT> S;
+    constexpr int NW = NT / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (;;) {
+        if (threadIdx.x == 0) S.graph = atomicAdd(graph_ctr, 1u);
+        __syncthreads();
+        const uint32_t qi = S.graph;
+        __syncthreads();
+        if (qi >= (uint32_t)B.G) break;
+        const int g = B.order[qi];
+        const int64_t vb = B.vbase[g];
+        const uint32_t n = (uint32_t)(B.vbase[g + 1] - vb);
+        const int64_t *off = B.off + vb;          // global arc indices
+        const int32_t *adj = B.adj;
+        const int64_t m = (off[n] - off[0]) / 2;
+        const int T = B.T[g];
+        uint32_t *L = B.loads + vb;
+        uint32_t *A = B.A + vb;
+        uint32_t *K0 = B.keys + 2 * vb, *K1 = K0 + n;
+        uint32_t *I0 = B.ids + 2 * vb, *I1 = I0 + n;
+        uint32_t *BL = B.best_loads + vb;
+        for (uint32_t v = threadIdx.x; v < n; v += NT) L[v] = B.init ? (uint32_t)B.init[vb + v] : 0u;
+        int64_t best_e = m, best_v = n, best_pos = 0;
+        uint32_t best_key = 0, best_id = 0;
+        int best_iter = 0;
+        __syncthreads();
+        for (int t = 1; t <= T; ++t) {
+            // ---- edge scan: warp per vertex
+            uint32_t width = 0, lmn = 0xffffffffu, lmx = 0;
+            for (uint32_t u = warp; u < n; u += NW) {
+                const int64_t s = off[u], e = off[u + 1];
+                const uint32_t lu = L[u];
+                uint32_t c = 0;
+                for (int64_t j = s + lane; j < e; j += 32) {
+                    const uint32_t w = (uint32_t)adj[j];
+                    const uint32_t lw = L[w];
+                    c += (lw > lu) || (lw == lu && w > u);
+                }
+                c = __reduce_add_sync(kFull, c);
+                if (lane == 0) A[u] = c;
+                width = max(width, c);
+                lmn = min(lmn, lu);
+                lmx = max(lmx, lu);
+            }
+            width = block_reduce_u32<NT>(width, true, S);
+            const uint32_t lmin = block_reduce_u32<NT>(lmn, false, S);
+            const uint32_t lmax = block_reduce_u32<NT>(lmx, true, S);
+            // ---- sort ids by (l, id): stable LSD passes on l - lmin
+            const uint32_t range = lmax - lmin;
+            const int bits = range ? 32 - __clz(range) : 0;
+            const int np = bits ? (bits + kRadixBits - 1) / kRadixBits : 0;
+            const uint32_t *ids;
+            const uint32_t *keys;
+            if (np == 0) {
+                for (uint32_t v = threadIdx.x; v < n; v += NT) { I0[v] = v; K0[v] = 0; }
+                __syncthreads();
+                ids = I0;
+                keys = K0;
+            } else {
+                const uint32_t *kin = nullptr, *iin = nullptr;
+                for (int p = 0; p < np; ++p) {
+                    uint32_t *ko = (p & 1) ? K1 : K0, *io = (p & 1) ? I1 : I0;
+                    block_radix_pass<NT>(kin, iin, L, lmin, ko, io, n, p * kRadixBits, S);
+                    kin = ko;
+                    iin = io;
+                }
+                ids = iin;
+                keys = kin;
+            }
+            // ---- densest suffix: scan of A in order, first maximum
+            Candidate best{0, 0, 0, 0};
+            uint64_t carry = 0;
+            for (uint32_t c0 = 0; c0 < n; c0 += NT) {
+                const uint32_t pos = c0 + threadIdx.x;
+                const uint64_t a = pos < n ? A[ids[pos]] : 0u;
+                uint64_t tot;
+                const uint64_t ex = block_excl_sum_u64(a, S.red, &tot);
+                if (pos < n) {
+                    Candidate cd{(int64_t)((uint64_t)m - (carry + ex)), (int64_t)(n - pos), (int64_t)pos, 0};
+                    if (cand_better(cd, best)) best = cd;
+                }
+                carry += tot;
+            }
+            best = block_best(best, S.cred);
+            if (B.trace) {
+                if (threadIdx.x == 0) {
+                    int64_t *tr = B.trace + ((int64_t)g * B.Tmax + (t - 1)) * 3;
+                    tr[0] = best.e;
+                    tr[1] = best.v;
+                    tr[2] = width;
+                }
+            }
+            const bool improved = best.v > 0 && dens_gt((uint64_t)best.e, (uint64_t)best.v,
+                                                        (uint64_t)best_e, (uint64_t)best_v);
+            if (improved) {
+                best_e = best.e;
+                best_v = best.v;
+                best_pos = best.pos;
+                best_iter = t;
+                best_key = keys[best_pos] + lmin;
+                best_id = ids[best_pos];
+                for (uint32_t v = threadIdx.x; v < n; v += NT) BL[v] = L[v];
+            }
+            __syncthreads();
+            for (uint32_t v = threadIdx.x; v < n; v += NT) L[v] += A[v];
+            __syncthreads();
+        }
+        // ---- outputs: loads, best set (ascending ids), summary
+        if (B.loads_out)
+            for (uint32_t v = threadIdx.x; v < n; v += NT) B.loads_out[vb + v] = (int64_t)L[v];
+        uint64_t set_size = 0;
+        {
+            uint64_t base = 0;
+            for (uint32_t c0 = 0; c0 < n; c0 += NT) {
+                const uint32_t v = c0 + threadIdx.x;
+                bool in = false;
+                if (v < n) {
+                    if (best_iter == 0) in = true;
+                    else {
+                        const uint32_t l = BL[v];
+                        in = l > best_key || (l == best_key && v >= best_id);
+                    }
+                }
+                uint64_t tot;
+                const uint64_t ex = block_excl_sum_u64(in ? 1u : 0u, S.red, &tot);
+                if (in && B.sets) B.sets[vb + base + ex] = (int32_t)v;
+                base += tot;
+            }
+            set_size = base;
+        }
+        if (threadIdx.x == 0) {
+            int64_t *o = B.best + 4 * (int64_t)g;
+            o[0] = best_e;
+            o[1] = best_v;
+            o[2] = best_iter;
+            o[3] = (int64_t)set_size;
+        }
+        (void)best_pos;
+        __syncthreads();
+    }
+}
+
+// validation of one graph per block: local ids in range, no self-loop,
+// (full) strictly ascending and symmetric lists
+__global__ void k_batch_validate(BatchDev B, int full, int32_t *err)
+{
+    for (int g = blockIdx.x; g < B.G; g += gridDim.x) {
+        const int64_t vb = B.vbase[g];
+        const int64_t n = B.vbase[g + 1] - vb;
+        const int64_t *off = B.off + vb;
+        for (int64_t u = threadIdx.x; u < n; u += blockDim.x) {
+            const int64_t s = off[u], e = off[u + 1];
+            if (e < s) { atomicExch(&err[0], 1); continue; }
+            for (int64_t j = s; j < e; ++j) {
+                const int32_t w = B.adj[j];
+                if (w < 0 || w >= n) { atomicExch(&err[1], 1); continue; }
+                if (w == (int32_t)u) atomicExch(&err[2], 1);
+                if (full) {
+                    if (j > s && B.adj[j - 1] >= w) atomicExch(&err[3], 1);
+                    int64_t lo = off[w], hi = off[w + 1];
+                    bool found = false;
+                    while (lo < hi) {
+                        const int64_t mid = lo + (hi - lo) / 2;
+                        const int32_t x = B.adj[mid];
+                        if (x == (int32_t)u) { found = true; break; }
+                        if (x < (int32_t)u) lo = mid + 1; else hi = mid;
+                    }
+                    if (!found) atomicExch(&err[4], 1);
+                }
+            }
+        }
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_batch_validate(const BatchDev &B, int full, int32_t *err, cudaStream_t s)
+{
+    cudaMemsetAsync(err, 0, 8 * sizeof(int32_t), s);
+    k_batch_validate<<<(unsigned)imin64(B.G, 152 * 8), 256, 0, s>>>(B, full, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_sorting(const BatchDev &B, int threads, int sm_count, uint32_t *graph_ctr,
+                                 cudaStream_t s)
+{
+    cudaMemsetAsync(graph_ctr, 0, sizeof(uint32_t), s);
+    int grid = 0, nb = 0;
+    switch (threads) {
+    case 256:
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_sorting<256>, 256, 0);
+        grid = (int)imin64((int64_t)sm_count * (nb > 0 ? nb : 1), B.G);
+        k_batch_sorting<256><<<grid, 256, 0, s>>>(B, graph_ctr);
+        break;
+    case 512:
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_sorting<512>, 512, 0);
+        grid = (int)imin64((int64_t)sm_count * (nb > 0 ? nb : 1), B.G);
+        k_batch_sorting<512><<<grid, 512, 0, s>>>(B, graph_ctr);
+        break;
+    case 1024:
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_sorting<1024>, 1024, 0);
+        grid = (int)imin64((int64_t)sm_count * (nb > 0 ? nb : 1), B.G);
+        k_batch_sorting<1024><<<grid, 1024, 0, s>>>(B, graph_ctr);
+        break;
+    default:
+        return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace dsg

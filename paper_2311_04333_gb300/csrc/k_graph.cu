@@ -400,6 +400,7 @@ static cudaError_t degree_threshold(const GraphDev &g, int64_t cap, unsigned lon
 {
     int64_t lo = 2, hi = g.max_degree + 1;
     cudaError_t e;
+    if (g.n <= cap) hi = lo;                    // every vertex of degree >= 2 fits
     while (lo < hi) {
         const int64_t mid = lo + (hi - lo) / 2;
         unsigned long long h = 0;

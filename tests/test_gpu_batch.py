@@ -1,0 +1,90 @@
+"""Batched PaRSorting++ (one persistent launch over a packed batch of graphs)
+against the oracle run on each graph alone, and against dsg_run per graph."""
+import numpy as np
+import pytest
+
+import graphgen as gg
+import oracle as orc
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    import paper_2311_04333_gb300 as dsg
+    ctx = dsg.dsg_create(0, torch.cuda.current_stream().cuda_stream)
+    yield dsg, ctx
+    dsg.dsg_destroy(ctx)
+
+
+def _run_batch(dsg, ctx, graphs, T, threads=0):
+    b = dsg.dsg_upload_batch(ctx, [(g.n, g.off, g.adj) for g in graphs], dsg.DSG_VALIDATE)
+    try:
+        G, N, M = dsg.dsg_batch_info(b)
+        assert G == len(graphs) and N == sum(g.n for g in graphs) and M == sum(g.m for g in graphs)
+        Tmax = int(max(T))
+        best = np.zeros(4 * G, np.int64)
+        loads = np.zeros(N, np.int64)
+        sets = np.zeros(N, np.int32)
+        trace = np.zeros(3 * G * Tmax, np.int64)
+        dsg.dsg_run_batch(ctx, b, dsg.DSG_SORTING, T, threads, best, loads, sets, trace)
+    finally:
+        dsg.dsg_free_batch(b)
+    return best.reshape(G, 4), loads, sets, trace.reshape(G, Tmax, 3)
+
+
+def _check(graphs, T, best, loads, sets, trace):
+    base = 0
+    for i, g in enumerate(graphs):
+        o = orc.run(g, orc.SORTING, int(T[i]))
+        assert tuple(best[i, :3]) == (o.best_edges, o.best_vertices, o.best_iter), f"graph {i}"
+        assert best[i, 3] == len(o.best_set)
+        assert np.array_equal(loads[base:base + g.n], o.loads), f"graph {i} loads"
+        assert np.array_equal(sets[base:base + best[i, 3]].astype(np.int64), o.best_set), f"graph {i} set"
+        assert np.array_equal(trace[i, :T[i]], o.trace), f"graph {i} trace"
+        base += g.n
+
+
+@pytest.mark.parametrize("threads", [256, 512, 1024])
+def test_batch_mixed_graphs(env, threads):
+    dsg, ctx = env
+    graphs = [gg.er_m(300, 6, 1), gg.complete(40), gg.from_edges(1, []), gg.star(500),
+              gg.er_planted_clique(n=700, p=(1, 100), k=20, seed=3), gg.rmat(11, 8, 5),
+              gg.from_edges(9, [(0, 1), (2, 3)]), gg.chung_lu(2000, 10, 2.1, 4), gg.path(257)]
+    T = np.array([5, 3, 2, 4, 8, 6, 1, 7, 3], np.int32)
+    _check(graphs, T, *_run_batch(dsg, ctx, graphs, T, threads))
+
+
+def test_batch_mix_recipe_sample(env):
+    dsg, ctx = env
+    graphs = gg.batch_mix(G=48, seed=4, n_hi=5000)
+    T = np.full(len(graphs), 32, np.int32)
+    _check(graphs, T, *_run_batch(dsg, ctx, graphs, T))
+
+
+def test_batch_equals_one_graph_per_launch(env):
+    dsg, ctx = env
+    graphs = gg.batch_mix(G=24, seed=9, n_hi=20000)
+    T = np.full(len(graphs), 12, np.int32)
+    best, loads, sets, trace = _run_batch(dsg, ctx, graphs, T)
+    base = 0
+    for i, g in enumerate(graphs):
+        r = dsg.densest(ctx, g.n, g.off, g.adj, dsg.DSG_SORTING, 12)
+        assert (r.best_edges, r.best_vertices, r.best_iter) == tuple(best[i, :3])
+        assert np.array_equal(r.loads, loads[base:base + g.n])
+        base += g.n
+
+
+def test_batch_rejects_bad_input(env):
+    dsg, ctx = env
+    with pytest.raises(dsg.DsgError, match="INVALID"):
+        dsg.dsg_upload_batch(ctx, [(2, np.array([0, 1, 2], np.int64), np.array([1, 5], np.int32))])
+    b = dsg.dsg_upload_batch(ctx, [(3, gg.path(3).off, gg.path(3).adj)])
+    try:
+        with pytest.raises(dsg.DsgError, match="INVALID"):
+            dsg.dsg_run_batch(ctx, b, dsg.DSG_PEELING, [3], 0, np.zeros(4, np.int64))
+        with pytest.raises(dsg.DsgError, match="INVALID"):
+            dsg.dsg_run_batch(ctx, b, dsg.DSG_SORTING, [0], 0, np.zeros(4, np.int64))
+    finally:
+        dsg.dsg_free_batch(b)
