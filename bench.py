@@ -9,6 +9,9 @@ value = m * T * K * N / (max over ranks of the timed region) / 1e9 (GTEPS).
 e2e   = the same metric through the C ABI with host buffers: each step
         uploads the CSR from pinned host memory, runs, and reads back the
         loads and the best set.
+The line also carries the batched form (4,096 small graphs in one persistent
+launch against one dsg_run per graph) and serving (Poisson arrivals through
+the native request loop: p50/p99 latency and throughput).
 Multi-GPU: the path does not shard (replicas only); each rank runs its own
 replica of the workload and value aggregates the replicas.
 --impl reference times the CPU oracle (the only reference this build has)
@@ -39,6 +42,9 @@ METRIC = "GTEPS per Greedy++ iteration (HBM roofline %); batched graphs/s vs one
 BATCH_G = 4096
 BATCH_SEED = 4
 BATCH_T = 32
+SERVE_POOL = 48        # request graphs of the serving workload
+SERVE_SEED = 5
+SERVE_SLOTS = 4
 UNIT = "GTEPS"
 
 
@@ -203,6 +209,36 @@ def bench_batch(dsg, ctx, graphs, args) -> dict:
             "gteps_batched": M * BATCH_T / tb / 1e9}
 
 
+def bench_serving(dsg, pool, device, args) -> dict:
+    """The native request loop under Poisson arrivals: capacity from a
+    closed burst of the whole request pool, then an open-loop run at 70% of
+    that capacity; latency percentiles are per request, submit to results on
+    the host."""
+    import numpy as np
+    from paper_2311_04333_gb300 import serve
+    srv = dsg.dsg_server_create(device, SERVE_SLOTS, 0)
+    try:
+        rng = np.random.default_rng(SERVE_SEED)
+        burst = []
+        t0 = time.perf_counter()
+        for g in pool:
+            burst.append(dsg.dsg_server_submit(srv, g.n, g.off, g.adj, int(rng.integers(2)),
+                                               int(rng.choice([8, 16, 32])), 1, int(rng.choice([10, 100]))))
+        ok = all(dsg.dsg_server_wait(srv, tk)["status"] == 0 for tk in burst)
+        cap = len(pool) / (time.perf_counter() - t0)
+        rate = 0.7 * cap
+        res = serve.poisson_run(srv, pool, rate, args.serve_seconds, warmup=1.0, seed=SERVE_SEED)
+    finally:
+        dsg.dsg_server_destroy(srv)
+    ms = [g.m for g in pool]
+    res.update({"workload": f"pool of {len(pool)} graphs, m log-uniform in [1e3, 1e7] "
+                            f"(R-MAT ef 8 / Chung-Lu gamma 2.1 avg degree 16, m {min(ms)}..{max(ms)}), "
+                            "T in {8,16,32}, eps in {1/10,1/100}, PaRSorting++ / PaRGreedy++ 50/50, "
+                            "host CSR in, loads and best set out",
+                "slots": SERVE_SLOTS, "burst_capacity_req_s": cap, "burst_ok": ok})
+    return res
+
+
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
@@ -243,6 +279,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--batch-steps", type=int, default=3)
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-seconds", type=float, default=8.0)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -254,6 +292,13 @@ def main():
         t0 = time.perf_counter()
         graphs_batch = gg.batch_mix(BATCH_G, BATCH_SEED, processes=max(1, min(16, os.cpu_count() or 1)))
         print(f"batch generated in {time.perf_counter() - t0:.1f} s", file=sys.stderr)
+    serve_pool = None
+    if not args.no_serve:
+        from paper_2311_04333_gb300 import serve
+        t0 = time.perf_counter()
+        serve_pool = serve.request_pool(SERVE_POOL, SERVE_SEED,
+                                        processes=max(1, min(16, os.cpu_count() or 1)))
+        print(f"request pool generated in {time.perf_counter() - t0:.1f} s", file=sys.stderr)
 
     import torch
     ws, rank, local = _dist()
@@ -343,6 +388,11 @@ def main():
     if not args.no_batch:
         batched = bench_batch(dsg, ctx, graphs_batch, args)
 
+    # ---- serving: Poisson arrivals through the native request loop
+    serving = None
+    if not args.no_serve:
+        serving = bench_serving(dsg, serve_pool, local, args)
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline()
@@ -370,6 +420,7 @@ def main():
             "gpu_launches": launches,
             "clocks": clk.summary(),
             "batched": batched,
+            "serving": serving,
         }
         print(json.dumps(out))
     dsg.dsg_destroy(ctx)

@@ -182,6 +182,54 @@ int dsg_run_batch(dsg_batch *b, int variant, const int32_t *T, int32_t threads_p
 /* Free a batch. */
 void dsg_free_batch(dsg_batch *b);
 
+/* ---- serving: continuous batching of requests --------------------------- */
+
+typedef struct dsg_server dsg_server;
+
+/* Outcome of one request (dsg_server_wait). */
+typedef struct {
+    int32_t status;          /* dsg_status of the request */
+    int32_t best_iter;       /* as in dsg_result */
+    int64_t best_edges, best_vertices, best_set_size;
+    int64_t n, m;
+    int32_t slot;            /* worker that ran it */
+    double queue_ms;         /* submit -> admitted to a slot */
+    double run_ms;           /* admitted -> results on the host */
+    double latency_ms;       /* submit -> results on the host */
+    char error[256];         /* dsg_last_error text when status != DSG_OK */
+} dsg_server_result;
+
+/* Start a server on `device` with `slots` workers (1..64), each with its own
+ * CUDA stream and context, and an HBM budget in bytes (0 = half the free
+ * device memory).  A request is admitted, in arrival order, when a worker is
+ * free and its device-memory estimate (about 24m + 128n bytes) fits what the
+ * running requests leave of the budget; admitted requests run concurrently
+ * on the GPU, and each gives exactly what dsg_run gives on it alone. */
+int dsg_server_create(int device, int32_t slots, int64_t hbm_budget_bytes, dsg_server **out);
+
+/* Queue one request: a host CSR graph (copied; same rules as dsg_upload_csr),
+ * the variant, T and eps = eps_num/eps_den.  *ticket identifies it.
+ * DSG_ERR_NOMEM if its estimate exceeds the whole budget, DSG_ERR_INVALID for
+ * bad arguments.  The graph itself is checked in full (as with DSG_VALIDATE)
+ * when it runs; a bad graph fails its own request only. */
+int dsg_server_submit(dsg_server *s, int64_t n, const int64_t *offsets, const int32_t *adj,
+                      int variant, int32_t T, int64_t eps_num, int64_t eps_den, uint64_t *ticket);
+
+/* Wait up to timeout_ms (< 0: forever) for a request; DSG_ERR_BUSY if it is
+ * not finished in time.  On return the result is filled (loads[n] and
+ * best_set[best_set_size] are copied if the pointers are not NULL) and the
+ * ticket is released. */
+int dsg_server_wait(dsg_server *s, uint64_t ticket, int64_t timeout_ms, dsg_server_result *out,
+                    int64_t *loads, int32_t *best_set);
+
+/* Queue length, running requests, finished requests, device bytes held by
+ * running requests and the budget (any pointer may be NULL). */
+int dsg_server_stats(dsg_server *s, int64_t *queued, int64_t *running, int64_t *done,
+                     int64_t *bytes_in_use, int64_t *budget);
+
+/* Stop the workers (running requests finish, queued ones are dropped). */
+void dsg_server_destroy(dsg_server *s);
+
 /* ---- instrumentation ---------------------------------------------------- */
 
 /* Kernel phases timed when profiling is on (dsg_set_profiling). */

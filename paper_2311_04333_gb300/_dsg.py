@@ -38,6 +38,14 @@ class dsg_result(ctypes.Structure):
                 ("best_set", ctypes.c_void_p), ("trace", ctypes.c_void_p)]
 
 
+class dsg_server_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("best_iter", ctypes.c_int32),
+                ("best_edges", ctypes.c_int64), ("best_vertices", ctypes.c_int64),
+                ("best_set_size", ctypes.c_int64), ("n", ctypes.c_int64), ("m", ctypes.c_int64),
+                ("slot", ctypes.c_int32), ("queue_ms", ctypes.c_double), ("run_ms", ctypes.c_double),
+                ("latency_ms", ctypes.c_double), ("error", ctypes.c_char * 256)]
+
+
 class dsg_batch_result(ctypes.Structure):
     _fields_ = [("flags", ctypes.c_uint32), ("best", ctypes.c_void_p), ("loads", ctypes.c_void_p),
                 ("sets", ctypes.c_void_p), ("trace", ctypes.c_void_p)]
@@ -65,6 +73,12 @@ def _load():
     lib.dsg_run_batch.argtypes = [P, I, P, I32, ctypes.POINTER(dsg_batch_result)]
     lib.dsg_free_batch.argtypes = [P]
     lib.dsg_free_batch.restype = None
+    lib.dsg_server_create.argtypes = [I, I32, I64, ctypes.POINTER(P)]
+    lib.dsg_server_submit.argtypes = [P, I64, P, P, I, I32, I64, I64, ctypes.POINTER(ctypes.c_uint64)]
+    lib.dsg_server_wait.argtypes = [P, ctypes.c_uint64, I64, ctypes.POINTER(dsg_server_result), P, P]
+    lib.dsg_server_stats.argtypes = [P, P, P, P, P, P]
+    lib.dsg_server_destroy.argtypes = [P]
+    lib.dsg_server_destroy.restype = None
     return lib
 
 
@@ -226,9 +240,55 @@ def dsg_free_batch(batch) -> None:
     LIB.dsg_free_batch(batch)
 
 
+def dsg_server_create(device: int = 0, slots: int = 4, hbm_budget_bytes: int = 0):
+    out = ctypes.c_void_p()
+    rc = LIB.dsg_server_create(device, slots, hbm_budget_bytes, ctypes.byref(out))
+    if rc != DSG_OK:
+        raise DsgError(rc, "dsg_server_create")
+    return out.value
+
+
+def dsg_server_submit(server, n: int, offsets, adj, variant: int, T: int, eps_num: int = 0,
+                      eps_den: int = 1) -> int:
+    po, _ = _ptr(offsets, np.int64)
+    pa, _ = _ptr(adj, np.int32)
+    t = ctypes.c_uint64(0)
+    rc = LIB.dsg_server_submit(server, n, po, pa, variant, T, eps_num, eps_den, ctypes.byref(t))
+    if rc != DSG_OK:
+        raise DsgError(rc, "dsg_server_submit")
+    return t.value
+
+
+def dsg_server_wait(server, ticket: int, timeout_ms: int = -1, loads=None, best_set=None) -> dict | None:
+    """Result dict, or None if the request is not finished within timeout_ms."""
+    res = dsg_server_result()
+    pl, _ = _ptr(loads, np.int64)
+    ps, _ = _ptr(best_set, np.int32)
+    rc = LIB.dsg_server_wait(server, ticket, timeout_ms, ctypes.byref(res), pl, ps)
+    if rc == DSG_ERR_BUSY:
+        return None
+    if rc != DSG_OK:
+        raise DsgError(rc, "dsg_server_wait")
+    return {f: (getattr(res, f).decode() if f == "error" else getattr(res, f))
+            for f, _ in dsg_server_result._fields_}
+
+
+def dsg_server_stats(server) -> dict:
+    v = [ctypes.c_int64() for _ in range(5)]
+    rc = LIB.dsg_server_stats(server, *[ctypes.byref(x) for x in v])
+    if rc != DSG_OK:
+        raise DsgError(rc, "dsg_server_stats")
+    return dict(zip(["queued", "running", "done", "bytes_in_use", "budget"], [x.value for x in v]))
+
+
+def dsg_server_destroy(server) -> None:
+    LIB.dsg_server_destroy(server)
+
+
 DSG_NOALLOC_MAX_VERTICES = 262144
 
 EXPORTED = ["dsg_create", "dsg_destroy", "dsg_last_error", "dsg_upload_csr", "dsg_graph_info",
             "dsg_run", "dsg_free_graph", "dsg_set_profiling", "dsg_get_stats",
             "dsg_densest_suffix_noalloc", "dsg_upload_batch", "dsg_batch_info", "dsg_run_batch",
-            "dsg_free_batch"]
+            "dsg_free_batch", "dsg_server_create", "dsg_server_submit", "dsg_server_wait",
+            "dsg_server_stats", "dsg_server_destroy"]

@@ -523,8 +523,11 @@ int dsg_run(dsg_graph *G, int variant, int32_t T, int64_t eps_num, int64_t eps_d
         int64_t by = 12 * n + (p > 1 ? 8 * n : 0) + (p > 2 ? 16 * n * (p - 2) : 0) + (p > 1 ? 8 * n : 0);
         ctx->bytes[DSG_PHASE_SORT] += by;
     }
-    if (!dst_dev && out->best_set && h.set_size > 0)
-        CK(cudaMemcpy(out->best_set, set_dst, sizeof(int32_t) * (size_t)h.set_size, cudaMemcpyDeviceToHost), "set D2H");
+    if (!dst_dev && out->best_set && h.set_size > 0) {
+        CK(cudaMemcpyAsync(out->best_set, set_dst, sizeof(int32_t) * (size_t)h.set_size, cudaMemcpyDeviceToHost, s),
+           "set D2H");
+        CK(cudaStreamSynchronize(s), "set D2H");
+    }
     out->best_edges = h.best_e;
     out->best_vertices = h.best_v;
     out->best_iter = h.best_iter;

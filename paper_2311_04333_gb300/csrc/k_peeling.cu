@@ -15,6 +15,8 @@
 //      the alive neighbours.
 // The densest suffix of the (round, id) order then reuses the radix passes
 // of the sorting path with key = round and value = A (Alg. 3 lines 4-7).
+#include <mutex>
+
 #include "common.cuh"
 #include "dsg.h"
 #include "peeling.h"
@@ -300,6 +302,7 @@ void peel_free(PeelBufs &pb, cudaStream_t s)
 }
 
 static int g_peel_blocks_per_sm = -1;
+static std::once_flag g_peel_once;
 
 int peel_run(cudaStream_t s, const GraphDev &g, RunBufs &b, PeelBufs &pb, bool &pb_ready,
              int sm_count, int T, int64_t p, int64_t q, int *launches, std::string &err)
@@ -328,11 +331,11 @@ int peel_run(cudaStream_t s, const GraphDev &g, RunBufs &b, PeelBufs &pb, bool &
     unsigned long long *keybuf = (unsigned long long *)(m + sz_deg + sz_round + 3 * sz_list);
     PeelCtl *pc = (PeelCtl *)(m + sz_deg + sz_round + 3 * sz_list + sz_key);
 
-    if (g_peel_blocks_per_sm < 0) {
+    std::call_once(g_peel_once, [] {
         int nb = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_peel, kPeelThreads, 0);
         g_peel_blocks_per_sm = nb > 0 ? (nb < 4 ? nb : 4) : 1;
-    }
+    });
     const int grid = sm_count * g_peel_blocks_per_sm;
     const int igrid = (int)imin64((n + 255) / 256, (int64_t)sm_count * 8);
     int nl = 0;

@@ -19,6 +19,8 @@
 //                m - prefix edges) of Alg. 3 lines 4-7 is evaluated in place
 //                and reduced to the iteration's first densest suffix.
 //   snapshot   : when the iteration beat the best, keeps l_t for the set.
+#include <mutex>
+
 #include "common.cuh"
 
 namespace dsg {
@@ -411,15 +413,16 @@ k_edge_scan(const int64_t *__restrict__ ooff, const uint32_t *__restrict__ oadj,
 }
 
 static int g_es_blocks_per_sm = -1;
+static std::once_flag g_es_once;
 
 int edge_scan_sm_count()
 {
-    if (g_es_blocks_per_sm < 0) {
+    std::call_once(g_es_once, [] {
         cudaFuncSetAttribute(k_edge_scan, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(EsSmem));
         int nb = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_edge_scan, kEsThreads, sizeof(EsSmem));
         g_es_blocks_per_sm = nb > 0 ? nb : 1;
-    }
+    });
     return g_es_blocks_per_sm;
 }
 
@@ -846,16 +849,15 @@ k_radix_pass(const uint32_t *kin, const uint32_t *vin,
     }
 }
 
-static bool g_pass_attr = false;
+static std::once_flag g_pass_once;
 
 cudaError_t launch_radix_pass(const GraphDev &g, RunBufs &b, int k, int t, cudaStream_t s,
                               const uint32_t *key0, bool update_loads, bool accumulate)
 {
-    if (!g_pass_attr) {
+    std::call_once(g_pass_once, [] {
         cudaFuncSetAttribute(k_radix_pass, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)sizeof(PassSmem));
-        g_pass_attr = true;
-    }
+    });
     // pass k reads: k == 0 -> (loads, A) by id; else buffer (k-1)&1; writes buffer k&1
     const uint32_t *kin = k == 0 ? (key0 ? key0 : b.loads) : b.keys[(k - 1) & 1];
     const uint32_t *vin = k == 0 ? b.A : b.vals[(k - 1) & 1];
