@@ -42,6 +42,7 @@ METRIC = "GTEPS per Greedy++ iteration (HBM roofline %); batched graphs/s vs one
 BATCH_G = 4096
 BATCH_SEED = 4
 BATCH_T = 32
+BATCH_T_PEEL = 16
 SERVE_POOL = 48        # request graphs of the serving workload
 SERVE_SEED = 5
 SERVE_SLOTS = 4
@@ -201,12 +202,59 @@ def bench_batch(dsg, ctx, graphs, args) -> dict:
     for h in hs:
         dsg.dsg_free_graph(h)
     same = bool(np.array_equal(best_b.reshape(G, 4), best_1))
-    return {"workload": f"{G} graphs, n log-uniform in [50, 50000] (ER / R-MAT / planted clique), "
-                        f"N={N}, M={M}, PaRSorting++ T={BATCH_T} each",
+    out = {"workload": f"{G} graphs, n log-uniform in [50, 50000] (ER / R-MAT / planted clique), "
+                       f"N={N}, M={M}, PaRSorting++ T={BATCH_T} each",
+           "graphs_per_s": G / tb, "ms_per_batch": tb * 1e3, "threads_per_graph": th,
+           "autotune_ms": rec["ms"], "one_per_launch_graphs_per_s": G / t1,
+           "one_per_launch_ms": t1 * 1e3, "speedup": t1 / tb, "identical_results": same,
+           "gteps_batched": M * BATCH_T / tb / 1e9}
+    out["peeling"] = bench_batch_peeling(dsg, ctx, graphs, args)
+    return out
+
+
+def bench_batch_peeling(dsg, ctx, graphs, args) -> dict:
+    """Batched PaRGreedy++ (eps = 1/10, T = BATCH_T_PEEL) on the same batch;
+    one dsg_run per graph is timed on a seeded sample of the graphs (it takes
+    minutes on all of them) and compared with the batch's results there."""
+    import numpy as np
+    import torch
+    from paper_2311_04333_gb300 import tune
+    G = len(graphs)
+    T = np.full(G, BATCH_T_PEEL, np.int32)
+    p = np.ones(G, np.int64)
+    q = np.full(G, 10, np.int64)
+    b = dsg.dsg_upload_batch(ctx, [(g.n, g.off, g.adj) for g in graphs], 0)
+    Gb, N, M = dsg.dsg_batch_info(b)
+    rec = tune.tune_batch(ctx, b, T, force=True, variant=dsg.DSG_PEELING, eps_num=p, eps_den=q)
+    th = rec["threads"]
+    best_b = np.zeros(4 * G, np.int64)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.batch_steps):
+        dsg.dsg_run_batch(ctx, b, dsg.DSG_PEELING, T, th, best_b, eps_num=p, eps_den=q)
+    tb = (time.perf_counter() - t0) / args.batch_steps
+    dsg.dsg_free_batch(b)
+    sample = np.random.default_rng(BATCH_SEED).choice(G, size=min(G, 128), replace=False)
+    hs = [dsg.dsg_upload_csr(ctx, graphs[i].n, graphs[i].off, graphs[i].adj, 0) for i in sample]
+    dsg.dsg_run(ctx, hs[0], dsg.DSG_PEELING, BATCH_T_PEEL, 1, 10)
+    best_1 = np.zeros((len(sample), 4), np.int64)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k, h in enumerate(hs):
+        r = dsg.dsg_run(ctx, h, dsg.DSG_PEELING, BATCH_T_PEEL, 1, 10)
+        best_1[k] = (r["best_edges"], r["best_vertices"], r["best_iter"], r["best_set_size"])
+    t1 = time.perf_counter() - t0
+    for h in hs:
+        dsg.dsg_free_graph(h)
+    m_sample = sum(graphs[i].m for i in sample)
+    same = bool(np.array_equal(best_b.reshape(G, 4)[sample], best_1))
+    return {"workload": f"same {G} graphs, PaRGreedy++ eps=1/10, T={BATCH_T_PEEL} each",
             "graphs_per_s": G / tb, "ms_per_batch": tb * 1e3, "threads_per_graph": th,
-            "autotune_ms": rec["ms"], "one_per_launch_graphs_per_s": G / t1,
-            "one_per_launch_ms": t1 * 1e3, "speedup": t1 / tb, "identical_results": same,
-            "gteps_batched": M * BATCH_T / tb / 1e9}
+            "autotune_ms": rec["ms"], "gteps_batched": M * BATCH_T_PEEL / tb / 1e9,
+            "one_per_launch_sample": len(sample),
+            "one_per_launch_graphs_per_s": len(sample) / t1,
+            "one_per_launch_gteps": m_sample * BATCH_T_PEEL / t1 / 1e9,
+            "identical_results_on_sample": same}
 
 
 def bench_serving(dsg, pool, device, args) -> dict:

@@ -167,17 +167,21 @@ int dsg_upload_batch(dsg_ctx *ctx, int32_t G, const int64_t *n_per, const int64_
 /* Number of graphs, total vertices and total edges of a batch. */
 int dsg_batch_info(const dsg_batch *b, int32_t *G, int64_t *total_n, int64_t *total_m);
 
-/* Run T[g] >= 1 PaRSorting++ iterations on every graph g of the batch in one
- * persistent launch: each thread block takes whole graphs, largest first,
- * and runs all their iterations (loads start at zero).  The results of
- * graph g are those dsg_run(DSG_SORTING, T[g]) gives on it alone.
- *   variant: DSG_SORTING only (DSG_PEELING: DSG_ERR_INVALID);
+/* Run T[g] >= 1 iterations of the refine step `variant` on every graph g of
+ * the batch in one persistent launch: each thread block takes whole graphs,
+ * largest first, and runs all their iterations (loads start at zero).  The
+ * results of graph g are those dsg_run(variant, T[g], eps_num[g],
+ * eps_den[g]) gives on it alone.
+ *   variant: DSG_SORTING (PaRSorting++) or DSG_PEELING (PaRGreedy++, whose
+ *     rounds a block peels by itself with block-wide barriers);
+ *   eps_num[G], eps_den[G]: eps = p/q per graph for DSG_PEELING (NULL:
+ *     p = 0, q = 1); p >= 0, q >= 1, p + q < 2^31; ignored by DSG_SORTING;
  *   threads_per_graph: 256, 512 or 1024 threads per block, 0 = default
  *     (the tuning knob an autotuner sets).
- * DSG_ERR_OVERFLOW if a graph's T * max_degree reaches 2^32.  Synchronises
- * the context stream before returning. */
-int dsg_run_batch(dsg_batch *b, int variant, const int32_t *T, int32_t threads_per_graph,
-                  dsg_batch_result *out);
+ * DSG_ERR_OVERFLOW if a graph's T * max_degree reaches 2^32 or p + q
+ * reaches 2^31.  Synchronises the context stream before returning. */
+int dsg_run_batch(dsg_batch *b, int variant, const int32_t *T, const int64_t *eps_num,
+                  const int64_t *eps_den, int32_t threads_per_graph, dsg_batch_result *out);
 
 /* Free a batch. */
 void dsg_free_batch(dsg_batch *b);

@@ -70,7 +70,7 @@ def _load():
     lib.dsg_densest_suffix_noalloc.argtypes = [P, P, I64, I64, P, P]
     lib.dsg_upload_batch.argtypes = [P, I32, P, P, P, U32, ctypes.POINTER(P)]
     lib.dsg_batch_info.argtypes = [P, P, P, P]
-    lib.dsg_run_batch.argtypes = [P, I, P, I32, ctypes.POINTER(dsg_batch_result)]
+    lib.dsg_run_batch.argtypes = [P, I, P, P, P, I32, ctypes.POINTER(dsg_batch_result)]
     lib.dsg_free_batch.argtypes = [P]
     lib.dsg_free_batch.restype = None
     lib.dsg_server_create.argtypes = [I, I32, I64, ctypes.POINTER(P)]
@@ -219,10 +219,14 @@ def dsg_batch_info(batch) -> tuple[int, int, int]:
 
 
 def dsg_run_batch(ctx, batch, variant: int, T, threads_per_graph: int = 0, best=None, loads=None,
-                  sets=None, trace=None) -> None:
+                  sets=None, trace=None, eps_num=None, eps_den=None) -> None:
     """T: int32[G]; best: int64[4G] (required); loads int64[N], sets int32[N],
-    trace int64[3*G*Tmax] optional; all host or all device."""
+    trace int64[3*G*Tmax] optional; all host or all device.  eps_num/eps_den:
+    int64[G] (or scalars) for DSG_PEELING, default 0/1."""
     T = np.ascontiguousarray(T, dtype=np.int32)
+    G = T.size
+    en = None if eps_num is None else np.ascontiguousarray(np.broadcast_to(eps_num, (G,)), dtype=np.int64)
+    ed = None if eps_den is None else np.ascontiguousarray(np.broadcast_to(eps_den, (G,)), dtype=np.int64)
     res = dsg_batch_result()
     pb, db = _ptr(best, np.int64)
     pl, dl = _ptr(loads, np.int64)
@@ -233,7 +237,10 @@ def dsg_run_batch(ctx, batch, variant: int, T, threads_per_graph: int = 0, best=
         raise ValueError("output buffers must all be host or all device")
     res.flags = DSG_DST_DEVICE if dev == {True} else 0
     res.best, res.loads, res.sets, res.trace = pb, pl, ps, pt
-    _check(ctx, LIB.dsg_run_batch(batch, variant, T.ctypes.data, threads_per_graph, ctypes.byref(res)))
+    _check(ctx, LIB.dsg_run_batch(batch, variant, T.ctypes.data,
+                                  None if en is None else en.ctypes.data,
+                                  None if ed is None else ed.ctypes.data,
+                                  threads_per_graph, ctypes.byref(res)))
 
 
 def dsg_free_batch(batch) -> None:

@@ -61,6 +61,7 @@ struct dsg_batch {
     std::vector<int64_t> maxdeg;     // per graph
     int64_t *vbase = nullptr, *off = nullptr;
     int32_t *adj = nullptr, *order = nullptr, *T = nullptr;
+    int64_t *pq = nullptr;           // per graph eps = p / q
     uint32_t *graph_ctr = nullptr;
     void *run_mem = nullptr;         // loads, A, keys, ids, best_loads, staging
     size_t run_bytes = 0;
@@ -593,6 +594,7 @@ int dsg_upload_batch(dsg_ctx *ctx, int32_t G, const int64_t *n_per, const int64_
         (e = cudaMallocAsync((void **)&B->adj, 4 * adjp.size(), st)) != cudaSuccess ||
         (e = cudaMallocAsync((void **)&B->order, 4 * (size_t)G, st)) != cudaSuccess ||
         (e = cudaMallocAsync((void **)&B->T, 4 * (size_t)G, st)) != cudaSuccess ||
+        (e = cudaMallocAsync((void **)&B->pq, 16 * (size_t)G, st)) != cudaSuccess ||
         (e = cudaMallocAsync((void **)&B->graph_ctr, 4, st)) != cudaSuccess)
         return bail(cuda_fail(ctx, e, "batch allocation"));
     cudaMemcpyAsync(B->vbase, vbase.data(), 8 * (size_t)(G + 1), cudaMemcpyHostToDevice, st);
@@ -629,29 +631,38 @@ int dsg_batch_info(const dsg_batch *b, int32_t *G, int64_t *total_n, int64_t *to
     return DSG_OK;
 }
 
-int dsg_run_batch(dsg_batch *Bt, int variant, const int32_t *T, int32_t threads_per_graph,
-                  dsg_batch_result *out)
+int dsg_run_batch(dsg_batch *Bt, int variant, const int32_t *T, const int64_t *eps_num,
+                  const int64_t *eps_den, int32_t threads_per_graph, dsg_batch_result *out)
 {
     if (!Bt || !out) return DSG_ERR_INVALID;
     dsg_ctx *ctx = Bt->ctx;
-    if (variant != DSG_SORTING) return fail(ctx, DSG_ERR_INVALID, "batches run DSG_SORTING only");
+    if (variant != DSG_SORTING && variant != DSG_PEELING)
+        return fail(ctx, DSG_ERR_INVALID, "variant %d: use DSG_SORTING or DSG_PEELING", variant);
     if (!T || !out->best) return fail(ctx, DSG_ERR_INVALID, "T and out->best are required");
     const int threads = threads_per_graph ? threads_per_graph : 512;
     if (threads != 256 && threads != 512 && threads != 1024)
         return fail(ctx, DSG_ERR_INVALID, "threads_per_graph = %d: use 256, 512 or 1024", threads_per_graph);
     int32_t Tmax = 0;
+    std::vector<int64_t> pq(2 * (size_t)Bt->G);
     for (int32_t g = 0; g < Bt->G; ++g) {
         if (T[g] < 1) return fail(ctx, DSG_ERR_INVALID, "T[%d] = %d must be >= 1", g, T[g]);
         if ((unsigned long long)T[g] * (unsigned long long)Bt->maxdeg[g] >= (1ull << 32))
             return fail(ctx, DSG_ERR_OVERFLOW, "graph %d: T * max_degree does not fit 32-bit loads", g);
         Tmax = std::max(Tmax, T[g]);
+        const int64_t p = eps_num ? eps_num[g] : 0, q = eps_den ? eps_den[g] : 1;
+        if (variant == DSG_PEELING) {
+            if (p < 0 || q < 1) return fail(ctx, DSG_ERR_INVALID, "graph %d: eps = %lld/%lld", g, (long long)p, (long long)q);
+            if (p + q >= (1ll << 31)) return fail(ctx, DSG_ERR_OVERFLOW, "graph %d: p + q must stay below 2^31", g);
+        }
+        pq[2 * g] = p;
+        pq[2 * g + 1] = q;
     }
     CK(cudaSetDevice(ctx->device), "cudaSetDevice");
     cudaStream_t st = ctx->stream;
     const int64_t N = Bt->N, G = Bt->G;
     const bool dev = out->flags & DSG_DST_DEVICE;
     // run state (+ staging for host outputs)
-    const size_t need = align256(4 * (size_t)N) * 3 + align256(8 * (size_t)N) * 2 + align256(8 * (size_t)N)
+    const size_t need = align256(4 * (size_t)N) * 4 + align256(8 * (size_t)N) * 2 + align256(8 * (size_t)N)
                       + align256(4 * (size_t)N) + align256(32 * (size_t)G) + align256(24 * (size_t)G * Tmax);
     if (Bt->run_bytes < need) {
         if (Bt->run_mem) cudaFreeAsync(Bt->run_mem, st);
@@ -670,10 +681,12 @@ int dsg_run_batch(dsg_batch *Bt, int variant, const int32_t *T, int32_t threads_
     bd.adj = Bt->adj;
     bd.order = Bt->order;
     bd.T = Bt->T;
+    bd.pq = Bt->pq;
     bd.init = nullptr;
     bd.loads = (uint32_t *)take(4 * (size_t)N);
     bd.A = (uint32_t *)take(4 * (size_t)N);
     bd.best_loads = (uint32_t *)take(4 * (size_t)N);
+    bd.round = (uint32_t *)take(4 * (size_t)N);
     bd.keys = (uint32_t *)take(8 * (size_t)N);
     bd.ids = (uint32_t *)take(8 * (size_t)N);
     int64_t *st_loads = (int64_t *)take(8 * (size_t)N);
@@ -685,9 +698,10 @@ int dsg_run_batch(dsg_batch *Bt, int variant, const int32_t *T, int32_t threads_
     bd.best = dev ? out->best : st_best;
     bd.trace = out->trace ? (dev ? out->trace : st_trace) : nullptr;
     CK(cudaMemcpyAsync(Bt->T, T, 4 * (size_t)G, cudaMemcpyHostToDevice, st), "T copy");
+    CK(cudaMemcpyAsync(Bt->pq, pq.data(), 16 * (size_t)G, cudaMemcpyHostToDevice, st), "eps copy");
     {
         PhaseTimer pt(ctx, DSG_PHASE_OTHER);
-        CK(launch_batch_sorting(bd, threads, ctx->sm_count, Bt->graph_ctr, st), "batch kernel");
+        CK(launch_batch(bd, variant, threads, ctx->sm_count, Bt->graph_ctr, st), "batch kernel");
     }
     ctx->launches[DSG_PHASE_OTHER] += 1;
     if (!dev) {
@@ -712,6 +726,7 @@ void dsg_free_batch(dsg_batch *B)
     if (B->adj) cudaFreeAsync(B->adj, st);
     if (B->order) cudaFreeAsync(B->order, st);
     if (B->T) cudaFreeAsync(B->T, st);
+    if (B->pq) cudaFreeAsync(B->pq, st);
     if (B->graph_ctr) cudaFreeAsync(B->graph_ctr, st);
     if (B->run_mem) cudaFreeAsync(B->run_mem, st);
     cudaStreamSynchronize(st);

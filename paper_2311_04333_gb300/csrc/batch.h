@@ -14,12 +14,14 @@ struct BatchDev {
     const int32_t *adj;       // [arcs] local ids
     const int32_t *order;     // [G] processing order (largest graph first)
     const int32_t *T;         // [G] iterations per graph
+    const int64_t *pq;        // [2G] eps = pq[2g] / pq[2g+1] (PaRGreedy++)
     const int64_t *init;      // [N] initial loads or nullptr
     uint32_t *loads;          // [N]
     uint32_t *A;              // [N]
     uint32_t *keys;           // [2N]
     uint32_t *ids;            // [2N]
-    uint32_t *best_loads;     // [N]
+    uint32_t *best_loads;     // [N] loads (PaRSorting++) or rounds (PaRGreedy++) of the best iteration
+    uint32_t *round;          // [N] PaRGreedy++ round of each vertex
     int64_t *loads_out;       // [N] or nullptr
     int32_t *sets;            // [N] or nullptr (graph g's set at vbase[g])
     int64_t *best;            // [G][4]: edges, vertices, iteration, set size
@@ -27,7 +29,8 @@ struct BatchDev {
 };
 
 cudaError_t launch_batch_validate(const BatchDev &B, int full, int32_t *err, cudaStream_t s);
-cudaError_t launch_batch_sorting(const BatchDev &B, int threads, int sm_count, uint32_t *graph_ctr,
-                                 cudaStream_t s);
+// variant: DSG_SORTING or DSG_PEELING
+cudaError_t launch_batch(const BatchDev &B, int variant, int threads, int sm_count, uint32_t *graph_ctr,
+                         cudaStream_t s);
 
 }  // namespace dsg

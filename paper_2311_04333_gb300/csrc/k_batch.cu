@@ -1,18 +1,24 @@
-// k_batch.cu -- batched PaRSorting++ (the refine step of arXiv 2311.04333,
-// Sec. 3.2-3.3 with Alg. 3) for many small graphs packed into one segmented
-// CSR.  One persistent launch: every block takes whole graphs from an atomic
-// queue (largest first) and runs all T iterations of a graph by itself:
-//   edge scan  A[u] = #{w in N(u) : (l[w], w) > (l[u], u)}    (warp per vertex)
-//   sort       stable LSD radix sort of the ids by l - min l (8-bit digits);
-//              the block's warps own contiguous segments: count, scan in
-//              (digit, warp) order, ranked scatter
+// k_batch.cu -- batched refine step (arXiv 2311.04333, Sec. 3.2-3.3 with
+// Alg. 3), PaRSorting++ or PaRGreedy++, for many small graphs packed into one
+// segmented CSR.  One persistent launch: every block takes whole graphs from
+// an atomic queue (largest first) and runs all T iterations of a graph by
+// itself:
+//   order      PaRSorting++: edge scan A[u] = #{w in N(u) : (l[w], w) >
+//              (l[u], u)} (warp per vertex), keys = loads;
+//              PaRGreedy++: rounds of bucketed peeling with the count of
+//              later neighbours fused (block_peel), keys = rounds
+//   sort       stable LSD radix sort of the ids by key - min key (8-bit
+//              digits); the block's warps own contiguous segments: count,
+//              scan in (digit, warp) order, ranked scatter
 //   suffix     B[i] = sum_{j >= i} A[v_j]; first maximum of B[i] / (n - i)
 //              (Alg. 3 lines 4-7); strict update of the graph's best (Alg. 2)
-//   loads      l += A                                       (Alg. 3 lines 8-9)
+//   loads      l += A (Alg. 3 lines 8-9; PaRGreedy++ adds each count as its
+//              vertex is peeled)
 // and finally extracts the best vertex set.  Graph g owns vertices
 // [vbase[g], vbase[g+1]) and arcs [off[vbase[g]], off[vbase[g+1]]) of the
 // packed arrays; adjacency entries are local ids.
 #include "batch.h"
+#include "dsg.h"
 #include "common.cuh"
 
 namespace dsg {
@@ -26,6 +32,8 @@ struct BatchSmem {
     Candidate cred[32];
     uint32_t wred[32];
     uint32_t graph;
+    uint32_t na_next, nf, nbig;          // PaRGreedy++ round counters
+    uint32_t big[64];                    // the round's F vertices of high degree
 };
 
 template <int NT>
@@ -115,9 +123,140 @@ __device__ void block_radix_pass(const uint32_t *kin, const uint32_t *iin, const
     __syncthreads();
 }
 
+constexpr uint32_t kNotPeeled = 0xffffffffu;
+constexpr int64_t kBlockScanDeg = 1024;  // F vertices above this degree: whole-block scan
+constexpr int kBigCap = 64;
+
 template <int NT>
+__device__ __forceinline__ unsigned long long block_min_u64(unsigned long long x, BatchSmem<NT> &S)
+{
+    #pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x = min(x, __shfl_xor_sync(kFull, x, o));
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) S.red[threadIdx.x >> 5] = x;
+    __syncthreads();
+    unsigned long long r = ~0ull;
+    for (int i = 0; i < NT / 32; ++i) r = min(r, S.red[i]);
+    __syncthreads();
+    return r;
+}
+
+// warp-aggregated slot claim on a shared counter (all lanes call it)
+__device__ __forceinline__ uint32_t warp_claim(bool pred, uint32_t *cnt)
+{
+    const uint32_t m = __ballot_sync(kFull, pred);
+    if (!m) return 0;
+    const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
+    uint32_t base = 0;
+    if (lane == leader) base = atomicAdd(cnt, (uint32_t)__popc(m));
+    base = __shfl_sync(kFull, base, leader);
+    return base + __popc(m & lanemask_lt());
+}
+
+// PaRGreedy++ ordering of one graph by one block (Sec. 3.3): rounds peel
+// F = {alive v : (l(v) + deg_H(v)) * q <= min * (p + q)}; the decrements of
+// deg_H caused by F are applied after F is fixed.  Fused with the count of
+// later neighbours in the (round, id) order: A[v] = alive neighbours not in
+// F, plus neighbours in F with a larger id; l(v) += A[v] (Alg. 3 lines 8-9).
+// R[v] receives v's round; returns the number of rounds.
+template <int NT>
+__device__ uint32_t block_peel(const int64_t *off, const int32_t *adj, uint32_t n, uint64_t p, uint64_t q,
+                               uint32_t *L, uint32_t *A, uint32_t *R, uint32_t *deg, uint32_t *cur,
+                               uint32_t *nxt, uint32_t &width, BatchSmem<NT> &S)
+{
+    constexpr int NW = NT / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (uint32_t v = threadIdx.x; v < n; v += NT) {
+        deg[v] = (uint32_t)(off[v + 1] - off[v]);
+        R[v] = kNotPeeled;
+        cur[v] = v;
+    }
+    uint32_t na = n, r = 0;
+    for (; na > 0; ++r) {
+        // keys of the alive vertices and their minimum
+        unsigned long long mn = ~0ull;
+        for (uint32_t i = threadIdx.x; i < na; i += NT) {
+            const uint32_t v = cur[i];
+            mn = min(mn, (unsigned long long)L[v] + deg[v]);
+        }
+        if (threadIdx.x == 0) {
+            S.na_next = 0;
+            S.nf = 0;
+            S.nbig = 0;
+        }
+        mn = block_min_u64<NT>(mn, S);
+        const unsigned long long thr = mn * (p + q);
+        // the round's set F (back of nxt, or S.big) and the survivors (front of nxt)
+        for (uint32_t i0 = warp * 32; i0 < na; i0 += NT) {
+            const uint32_t i = i0 + lane;
+            const bool valid = i < na;
+            const uint32_t v = valid ? cur[i] : 0u;
+            const bool inF = valid && ((unsigned long long)L[v] + deg[v]) * q <= thr;
+            if (inF) R[v] = r;
+            const bool big = inF && off[v + 1] - off[v] > kBlockScanDeg;
+            const uint32_t bs = warp_claim(big, &S.nbig);
+            const bool stored = big && bs < (uint32_t)kBigCap;
+            if (stored) S.big[bs] = v;
+            const uint32_t fs = warp_claim(inF && !stored, &S.nf);
+            if (inF && !stored) nxt[n - 1 - fs] = v;
+            const uint32_t ns = warp_claim(valid && !inF, &S.na_next);
+            if (valid && !inF) nxt[ns] = v;
+        }
+        __syncthreads();
+        const uint32_t nf = S.nf, nbig = min(S.nbig, (uint32_t)kBigCap), na_next = S.na_next;
+        for (uint32_t j = warp; j < nf; j += NW) {
+            const uint32_t v = nxt[n - 1 - j];
+            uint32_t c = 0;
+            for (int64_t k = off[v] + lane; k < off[v + 1]; k += 32) {
+                const uint32_t w = (uint32_t)adj[k];
+                const uint32_t rw = R[w];
+                if (rw == kNotPeeled) {
+                    ++c;
+                    atomicSub(&deg[w], 1u);
+                } else if (rw == r && w > v) {
+                    ++c;
+                }
+            }
+            c = __reduce_add_sync(kFull, c);
+            if (lane == 0) {
+                A[v] = c;
+                L[v] += c;
+            }
+            width = max(width, c);
+        }
+        for (uint32_t b = 0; b < nbig; ++b) {
+            const uint32_t v = S.big[b];
+            uint32_t c = 0;
+            for (int64_t k = off[v] + threadIdx.x; k < off[v + 1]; k += NT) {
+                const uint32_t w = (uint32_t)adj[k];
+                const uint32_t rw = R[w];
+                if (rw == kNotPeeled) {
+                    ++c;
+                    atomicSub(&deg[w], 1u);
+                } else if (rw == r && w > v) {
+                    ++c;
+                }
+            }
+            uint64_t tot;
+            block_excl_sum_u64(c, S.red, &tot);
+            if (threadIdx.x == 0) {
+                A[v] = (uint32_t)tot;
+                L[v] += (uint32_t)tot;
+            }
+            width = max(width, (uint32_t)tot);
+        }
+        __syncthreads();
+        uint32_t *t = cur;
+        cur = nxt;
+        nxt = t;
+        na = na_next;
+    }
+    return r;
+}
+
+template <int NT, bool PEEL>
 __global__ void __launch_bounds__(NT, 1024 / NT)
-k_batch_sorting(BatchDev B, uint32_t *graph_ctr)
+k_batch_run(BatchDev B, uint32_t *graph_ctr)
 {
     __shared__ BatchSmem<NT> S;
     constexpr int NW = NT / 32;
@@ -140,34 +279,45 @@ k_batch_sorting(BatchDev B, uint32_t *graph_ctr)
         uint32_t *K0 = B.keys + 2 * vb, *K1 = K0 + n;
         uint32_t *I0 = B.ids + 2 * vb, *I1 = I0 + n;
         uint32_t *BL = B.best_loads + vb;
+        uint32_t *R = B.round + vb;
+        const uint64_t pp = PEEL ? (uint64_t)B.pq[2 * g] : 0u, qq = PEEL ? (uint64_t)B.pq[2 * g + 1] : 1u;
         for (uint32_t v = threadIdx.x; v < n; v += NT) L[v] = B.init ? (uint32_t)B.init[vb + v] : 0u;
         int64_t best_e = m, best_v = n, best_pos = 0;
         uint32_t best_key = 0, best_id = 0;
         int best_iter = 0;
         __syncthreads();
         for (int t = 1; t <= T; ++t) {
-            // ---- edge scan: warp per vertex
-            uint32_t width = 0, lmn = 0xffffffffu, lmx = 0;
-            for (uint32_t u = warp; u < n; u += NW) {
-                const int64_t s = off[u], e = off[u + 1];
-                const uint32_t lu = L[u];
-                uint32_t c = 0;
-                for (int64_t j = s + lane; j < e; j += 32) {
-                    const uint32_t w = (uint32_t)adj[j];
-                    const uint32_t lw = L[w];
-                    c += (lw > lu) || (lw == lu && w > u);
+            uint32_t width = 0, lmin = 0, range = 0;
+            const uint32_t *src = L;              // sort keys: loads, or rounds
+            if (PEEL) {
+                // ---- ordering by rounds of peeling, later-neighbour counts fused
+                const uint32_t rounds = block_peel<NT>(off, adj, n, pp, qq, L, A, R, K0, I0, I1, width, S);
+                width = block_reduce_u32<NT>(width, true, S);
+                range = rounds - 1;
+                src = R;
+            } else {
+                // ---- edge scan: warp per vertex
+                uint32_t lmn = 0xffffffffu, lmx = 0;
+                for (uint32_t u = warp; u < n; u += NW) {
+                    const int64_t s = off[u], e = off[u + 1];
+                    const uint32_t lu = L[u];
+                    uint32_t c = 0;
+                    for (int64_t j = s + lane; j < e; j += 32) {
+                        const uint32_t w = (uint32_t)adj[j];
+                        const uint32_t lw = L[w];
+                        c += (lw > lu) || (lw == lu && w > u);
+                    }
+                    c = __reduce_add_sync(kFull, c);
+                    if (lane == 0) A[u] = c;
+                    width = max(width, c);
+                    lmn = min(lmn, lu);
+                    lmx = max(lmx, lu);
                 }
-                c = __reduce_add_sync(kFull, c);
-                if (lane == 0) A[u] = c;
-                width = max(width, c);
-                lmn = min(lmn, lu);
-                lmx = max(lmx, lu);
+                width = block_reduce_u32<NT>(width, true, S);
+                lmin = block_reduce_u32<NT>(lmn, false, S);
+                range = block_reduce_u32<NT>(lmx, true, S) - lmin;
             }
-            width = block_reduce_u32<NT>(width, true, S);
-            const uint32_t lmin = block_reduce_u32<NT>(lmn, false, S);
-            const uint32_t lmax = block_reduce_u32<NT>(lmx, true, S);
-            // ---- sort ids by (l, id): stable LSD passes on l - lmin
-            const uint32_t range = lmax - lmin;
+            // ---- sort ids by (key, id): stable LSD passes on key - lmin
             const int bits = range ? 32 - __clz(range) : 0;
             const int np = bits ? (bits + kRadixBits - 1) / kRadixBits : 0;
             const uint32_t *ids;
@@ -181,7 +331,7 @@ k_batch_sorting(BatchDev B, uint32_t *graph_ctr)
                 const uint32_t *kin = nullptr, *iin = nullptr;
                 for (int p = 0; p < np; ++p) {
                     uint32_t *ko = (p & 1) ? K1 : K0, *io = (p & 1) ? I1 : I0;
-                    block_radix_pass<NT>(kin, iin, L, lmin, ko, io, n, p * kRadixBits, S);
+                    block_radix_pass<NT>(kin, iin, src, lmin, ko, io, n, p * kRadixBits, S);
                     kin = ko;
                     iin = io;
                 }
@@ -220,11 +370,13 @@ k_batch_sorting(BatchDev B, uint32_t *graph_ctr)
                 best_iter = t;
                 best_key = keys[best_pos] + lmin;
                 best_id = ids[best_pos];
-                for (uint32_t v = threadIdx.x; v < n; v += NT) BL[v] = L[v];
+                for (uint32_t v = threadIdx.x; v < n; v += NT) BL[v] = src[v];
             }
             __syncthreads();
-            for (uint32_t v = threadIdx.x; v < n; v += NT) L[v] += A[v];
-            __syncthreads();
+            if (!PEEL) {
+                for (uint32_t v = threadIdx.x; v < n; v += NT) L[v] += A[v];
+                __syncthreads();
+            }
         }
         // ---- outputs: loads, best set (ascending ids), summary
         if (B.loads_out)
@@ -302,31 +454,27 @@ cudaError_t launch_batch_validate(const BatchDev &B, int full, int32_t *err, cud
     return cudaGetLastError();
 }
 
-cudaError_t launch_batch_sorting(const BatchDev &B, int threads, int sm_count, uint32_t *graph_ctr,
-                                 cudaStream_t s)
+template <int NT, bool PEEL>
+static cudaError_t launch_one(const BatchDev &B, int sm_count, uint32_t *graph_ctr, cudaStream_t s)
+{
+    int nb = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_run<NT, PEEL>, NT, 0);
+    const int grid = (int)imin64((int64_t)sm_count * (nb > 0 ? nb : 1), B.G);
+    k_batch_run<NT, PEEL><<<grid, NT, 0, s>>>(B, graph_ctr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch(const BatchDev &B, int variant, int threads, int sm_count, uint32_t *graph_ctr,
+                         cudaStream_t s)
 {
     cudaMemsetAsync(graph_ctr, 0, sizeof(uint32_t), s);
-    int grid = 0, nb = 0;
+    const bool peel = variant == DSG_PEELING;
     switch (threads) {
-    case 256:
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_sorting<256>, 256, 0);
-        grid = (int)imin64((int64_t)sm_count * (nb > 0 ? nb : 1), B.G);
-        k_batch_sorting<256><<<grid, 256, 0, s>>>(B, graph_ctr);
-        break;
-    case 512:
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_sorting<512>, 512, 0);
-        grid = (int)imin64((int64_t)sm_count * (nb > 0 ? nb : 1), B.G);
-        k_batch_sorting<512><<<grid, 512, 0, s>>>(B, graph_ctr);
-        break;
-    case 1024:
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_sorting<1024>, 1024, 0);
-        grid = (int)imin64((int64_t)sm_count * (nb > 0 ? nb : 1), B.G);
-        k_batch_sorting<1024><<<grid, 1024, 0, s>>>(B, graph_ctr);
-        break;
-    default:
-        return cudaErrorInvalidValue;
+    case 256: return peel ? launch_one<256, true>(B, sm_count, graph_ctr, s) : launch_one<256, false>(B, sm_count, graph_ctr, s);
+    case 512: return peel ? launch_one<512, true>(B, sm_count, graph_ctr, s) : launch_one<512, false>(B, sm_count, graph_ctr, s);
+    case 1024: return peel ? launch_one<1024, true>(B, sm_count, graph_ctr, s) : launch_one<1024, false>(B, sm_count, graph_ctr, s);
+    default: return cudaErrorInvalidValue;
     }
-    return cudaGetLastError();
 }
 
 }  // namespace dsg

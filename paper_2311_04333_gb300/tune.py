@@ -31,10 +31,11 @@ def _gpu_name() -> str:
 
 
 def tune_batch(ctx, batch, T, cache_path: str | None = DEFAULT_CACHE, reps: int = 1,
-               candidates=CANDIDATES, force: bool = False) -> dict:
+               candidates=CANDIDATES, force: bool = False, variant: int = _dsg.DSG_SORTING,
+               eps_num=None, eps_den=None) -> dict:
     """Returns {"threads": best, "ms": {candidate: time}} and records it."""
     G, N, M = _dsg.dsg_batch_info(batch)
-    key = f"{_gpu_name()}|{_shape_class(G, M)}"
+    key = f"{_gpu_name()}|{_shape_class(G, M)}|variant{variant}"
     cache = {}
     if cache_path and os.path.exists(cache_path):
         try:
@@ -46,10 +47,10 @@ def tune_batch(ctx, batch, T, cache_path: str | None = DEFAULT_CACHE, reps: int 
     best = np.zeros(4 * G, np.int64)
     times = {}
     for th in candidates:
-        _dsg.dsg_run_batch(ctx, batch, _dsg.DSG_SORTING, T, th, best)      # warm
+        _dsg.dsg_run_batch(ctx, batch, variant, T, th, best, eps_num=eps_num, eps_den=eps_den)  # warm
         t0 = time.perf_counter()
         for _ in range(reps):
-            _dsg.dsg_run_batch(ctx, batch, _dsg.DSG_SORTING, T, th, best)
+            _dsg.dsg_run_batch(ctx, batch, variant, T, th, best, eps_num=eps_num, eps_den=eps_den)
         times[th] = (time.perf_counter() - t0) / reps * 1e3
     rec = {"threads": min(times, key=times.get), "ms": times, "shape": _shape_class(G, M)}
     cache[key] = rec

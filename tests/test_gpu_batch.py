@@ -1,5 +1,6 @@
-"""Batched PaRSorting++ (one persistent launch over a packed batch of graphs)
-against the oracle run on each graph alone, and against dsg_run per graph."""
+"""Batched PaRSorting++ and PaRGreedy++ (one persistent launch over a packed
+batch of graphs) against the oracle run on each graph alone, and against
+dsg_run per graph."""
 import numpy as np
 import pytest
 
@@ -18,7 +19,7 @@ def env():
     dsg.dsg_destroy(ctx)
 
 
-def _run_batch(dsg, ctx, graphs, T, threads=0):
+def _run_batch(dsg, ctx, graphs, T, threads=0, variant=0, p=None, q=None):
     b = dsg.dsg_upload_batch(ctx, [(g.n, g.off, g.adj) for g in graphs], dsg.DSG_VALIDATE)
     try:
         G, N, M = dsg.dsg_batch_info(b)
@@ -28,16 +29,19 @@ def _run_batch(dsg, ctx, graphs, T, threads=0):
         loads = np.zeros(N, np.int64)
         sets = np.zeros(N, np.int32)
         trace = np.zeros(3 * G * Tmax, np.int64)
-        dsg.dsg_run_batch(ctx, b, dsg.DSG_SORTING, T, threads, best, loads, sets, trace)
+        dsg.dsg_run_batch(ctx, b, variant, T, threads, best, loads, sets, trace, p, q)
     finally:
         dsg.dsg_free_batch(b)
     return best.reshape(G, 4), loads, sets, trace.reshape(G, Tmax, 3)
 
 
-def _check(graphs, T, best, loads, sets, trace):
+def _check(graphs, T, best, loads, sets, trace, variant=0, p=None, q=None):
     base = 0
     for i, g in enumerate(graphs):
-        o = orc.run(g, orc.SORTING, int(T[i]))
+        if variant == 0:
+            o = orc.run(g, orc.SORTING, int(T[i]))
+        else:
+            o = orc.run(g, orc.PEELING, int(T[i]), int(p[i]), int(q[i]))
         assert tuple(best[i, :3]) == (o.best_edges, o.best_vertices, o.best_iter), f"graph {i}"
         assert best[i, 3] == len(o.best_set)
         assert np.array_equal(loads[base:base + g.n], o.loads), f"graph {i} loads"
@@ -83,8 +87,57 @@ def test_batch_rejects_bad_input(env):
     b = dsg.dsg_upload_batch(ctx, [(3, gg.path(3).off, gg.path(3).adj)])
     try:
         with pytest.raises(dsg.DsgError, match="INVALID"):
-            dsg.dsg_run_batch(ctx, b, dsg.DSG_PEELING, [3], 0, np.zeros(4, np.int64))
+            dsg.dsg_run_batch(ctx, b, 7, [3], 0, np.zeros(4, np.int64))
+        with pytest.raises(dsg.DsgError, match="INVALID"):
+            dsg.dsg_run_batch(ctx, b, dsg.DSG_PEELING, [3], 0, np.zeros(4, np.int64), eps_num=[1], eps_den=[0])
+        with pytest.raises(dsg.DsgError, match="OVERFLOW"):
+            dsg.dsg_run_batch(ctx, b, dsg.DSG_PEELING, [3], 0, np.zeros(4, np.int64), eps_num=[1 << 31],
+                              eps_den=[1])
         with pytest.raises(dsg.DsgError, match="INVALID"):
             dsg.dsg_run_batch(ctx, b, dsg.DSG_SORTING, [0], 0, np.zeros(4, np.int64))
     finally:
         dsg.dsg_free_batch(b)
+
+
+def _mixed_graphs():
+    return [gg.er_m(300, 6, 1), gg.complete(40), gg.from_edges(1, []), gg.star(500),
+            gg.er_planted_clique(n=700, p=(1, 100), k=20, seed=3), gg.rmat(11, 8, 5),
+            gg.from_edges(9, [(0, 1), (2, 3)]), gg.chung_lu(2000, 10, 2.1, 4), gg.path(257),
+            gg.chung_lu(3000, 30, 2.1, 8)]
+
+
+@pytest.mark.parametrize("threads", [256, 512, 1024])
+def test_batch_peeling_mixed_graphs(env, threads):
+    """PaRGreedy++ per graph, eps from 0 to 1, against the oracle."""
+    dsg, ctx = env
+    graphs = _mixed_graphs()
+    T = np.array([5, 3, 2, 4, 8, 6, 1, 7, 3, 5], np.int32)
+    p = np.array([1, 1, 0, 1, 1, 1, 1, 0, 1, 1], np.int64)
+    q = np.array([10, 100, 1, 2, 10, 100, 1, 1, 10, 1000], np.int64)
+    _check(graphs, T, *_run_batch(dsg, ctx, graphs, T, threads, 1, p, q), variant=1, p=p, q=q)
+
+
+def test_batch_peeling_recipe_sample(env):
+    dsg, ctx = env
+    graphs = gg.batch_mix(G=40, seed=6, n_hi=5000)
+    G = len(graphs)
+    T = np.full(G, 8, np.int32)
+    p = np.ones(G, np.int64)
+    q = np.where(np.arange(G) % 2 == 0, 10, 100).astype(np.int64)
+    _check(graphs, T, *_run_batch(dsg, ctx, graphs, T, 0, 1, p, q), variant=1, p=p, q=q)
+
+
+def test_batch_peeling_equals_one_graph_per_launch(env):
+    dsg, ctx = env
+    graphs = gg.batch_mix(G=12, seed=10, n_hi=20000)
+    G = len(graphs)
+    T = np.full(G, 6, np.int32)
+    best, loads, sets, trace = _run_batch(dsg, ctx, graphs, T, 1024, 1, np.ones(G, np.int64),
+                                          np.full(G, 20, np.int64))
+    base = 0
+    for i, g in enumerate(graphs):
+        r = dsg.densest(ctx, g.n, g.off, g.adj, dsg.DSG_PEELING, 6, eps=(1, 20))
+        assert (r.best_edges, r.best_vertices, r.best_iter) == tuple(best[i, :3])
+        assert np.array_equal(r.loads, loads[base:base + g.n])
+        assert np.array_equal(r.best_set, sets[base:base + best[i, 3]])
+        base += g.n
