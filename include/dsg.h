@@ -67,6 +67,11 @@ typedef enum {
 /* dsg_result.flags */
 #define DSG_DST_DEVICE  0x1u /* loads/best_set/trace are device pointers */
 #define DSG_INIT_DEVICE 0x2u /* init_loads (dsg_run) is a device pointer */
+#define DSG_PATH_GRID   0x4u /* dsg_run: whole-GPU kernels whatever the graph's size */
+#define DSG_PATH_BLOCK  0x8u /* dsg_run: one thread block carries all T iterations
+                                (default up to 32,768 vertices and 2^20 arcs for
+                                DSG_PEELING, 4,096 vertices and 2^17 arcs for
+                                DSG_SORTING; the two PATH flags are exclusive) */
 
 /* Output of one run.  The caller sets `flags` and the three buffer
  * pointers (each may be NULL to skip that output); the library fills the
@@ -113,7 +118,9 @@ const char *dsg_last_error(const dsg_ctx *ctx);
  * With DSG_VALIDATE the library also checks that every list has no self-loop
  * and no repeated neighbour and that the graph is symmetric; otherwise the
  * caller guarantees it.  Lists need not be sorted.  The graph is copied to
- * device memory together with the tile schedule of the edge scan.
+ * device memory; a graph above 32,768 vertices or 2^20 arcs also gets the
+ * degree-oriented copy and tile schedule of the whole-GPU edge scan (a
+ * smaller one gets them on its first run on the whole-GPU path).
  * Errors: DSG_ERR_INVALID for a malformed graph, DSG_ERR_NOMEM. */
 int dsg_upload_csr(dsg_ctx *ctx, int64_t n, const int64_t *offsets, const int32_t *adj,
                    uint32_t flags, dsg_graph **out);
@@ -122,7 +129,9 @@ int dsg_upload_csr(dsg_ctx *ctx, int64_t n, const int64_t *offsets, const int32_
 int dsg_graph_info(const dsg_graph *g, int64_t *n, int64_t *m, int64_t *max_degree);
 
 /* Run T >= 1 iterations of the refine step `variant` on `g` (Alg. 2 with
- * the ordering of `variant`, the density/load update of Alg. 3).
+ * the ordering of `variant`, the density/load update of Alg. 3).  Both
+ * paths (out->flags DSG_PATH_GRID / DSG_PATH_BLOCK, default by size) give
+ * identical results.
  *   eps_num/eps_den: eps = p/q for DSG_PEELING (p >= 0, q >= 1, p+q < 2^31);
  *     ignored by DSG_SORTING;
  *   init_loads[n]: loads before iteration 1 (NULL: all zero, Alg. 2 lines

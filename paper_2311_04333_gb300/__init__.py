@@ -12,7 +12,7 @@ from dataclasses import dataclass
 import numpy as np
 
 from ._dsg import (DSG_ERR_BUSY, DSG_ERR_CUDA, DSG_ERR_INVALID, DSG_ERR_NOMEM, DSG_ERR_OVERFLOW,
-                   DSG_ERR_TIMEOUT, DSG_OK, DSG_DST_DEVICE, DSG_INIT_DEVICE, DSG_NOALLOC_MAX_VERTICES, DSG_PEELING,
+                   DSG_ERR_TIMEOUT, DSG_OK, DSG_DST_DEVICE, DSG_INIT_DEVICE, DSG_PATH_BLOCK, DSG_PATH_GRID, DSG_NOALLOC_MAX_VERTICES, DSG_PEELING,
                    DSG_SORTING, DSG_SRC_DEVICE, DSG_VALIDATE, DsgError, LIB_PATH, dsg_create,
                    dsg_batch_info, dsg_densest_suffix_noalloc, dsg_destroy, dsg_free_batch,
                    dsg_free_graph, dsg_run_batch, dsg_server_create, dsg_server_destroy,
@@ -21,7 +21,7 @@ from ._dsg import (DSG_ERR_BUSY, DSG_ERR_CUDA, DSG_ERR_INVALID, DSG_ERR_NOMEM, D
                    dsg_upload_csr)
 
 __all__ = ["DSG_OK", "DSG_ERR_INVALID", "DSG_ERR_NOMEM", "DSG_ERR_CUDA", "DSG_ERR_OVERFLOW",
-           "DSG_ERR_TIMEOUT", "DSG_ERR_BUSY", "DSG_SORTING", "DSG_PEELING", "DSG_VALIDATE", "DSG_SRC_DEVICE", "DSG_DST_DEVICE",
+           "DSG_ERR_TIMEOUT", "DSG_ERR_BUSY", "DSG_PATH_GRID", "DSG_PATH_BLOCK", "DSG_SORTING", "DSG_PEELING", "DSG_VALIDATE", "DSG_SRC_DEVICE", "DSG_DST_DEVICE",
            "DSG_INIT_DEVICE", "DsgError", "LIB_PATH", "dsg_create", "dsg_destroy",
            "dsg_free_graph", "dsg_get_stats", "dsg_graph_info", "dsg_last_error", "dsg_run",
            "dsg_set_profiling", "dsg_upload_csr", "dsg_densest_suffix_noalloc",
@@ -42,14 +42,14 @@ class Result:
 
 def densest(ctx, n: int, offsets: np.ndarray, adj: np.ndarray, variant: int = DSG_SORTING,
             T: int = 10, eps: tuple[int, int] = (1, 10), init_loads=None,
-            validate: bool = True) -> Result:
+            validate: bool = True, path: int = 0) -> Result:
     """Upload a host CSR graph, run T refine iterations and read back."""
     g = dsg_upload_csr(ctx, n, offsets, adj, DSG_VALIDATE if validate else 0)
     try:
         loads = np.zeros(n, dtype=np.int64)
         bset = np.zeros(n, dtype=np.int32)
         trace = np.zeros(3 * T, dtype=np.int64)
-        r = dsg_run(ctx, g, variant, T, eps[0], eps[1], init_loads, loads, bset, trace)
+        r = dsg_run(ctx, g, variant, T, eps[0], eps[1], init_loads, loads, bset, trace, path)
     finally:
         dsg_free_graph(g)
     return Result(r["best_edges"], r["best_vertices"], r["best_iter"],

@@ -19,6 +19,7 @@ DSG_OK, DSG_ERR_INVALID, DSG_ERR_NOMEM, DSG_ERR_CUDA, DSG_ERR_OVERFLOW, DSG_ERR_
 DSG_SORTING, DSG_PEELING = 0, 1
 DSG_VALIDATE, DSG_SRC_DEVICE = 0x1, 0x2
 DSG_DST_DEVICE, DSG_INIT_DEVICE = 0x1, 0x2
+DSG_PATH_GRID, DSG_PATH_BLOCK = 0x4, 0x8
 DSG_PHASE_EDGE_SCAN, DSG_PHASE_SORT, DSG_PHASE_OTHER, DSG_PHASE_COUNT = 0, 1, 2, 3
 
 STATUS_NAMES = {0: "DSG_OK", 1: "DSG_ERR_INVALID", 2: "DSG_ERR_NOMEM", 3: "DSG_ERR_CUDA",
@@ -148,10 +149,11 @@ def dsg_graph_info(graph) -> tuple[int, int, int]:
 
 
 def dsg_run(ctx, graph, variant: int, T: int, eps_num: int = 0, eps_den: int = 1,
-            init_loads=None, loads=None, best_set=None, trace=None) -> dict:
+            init_loads=None, loads=None, best_set=None, trace=None, path: int = 0) -> dict:
     """Run T iterations.  `loads` (int64[n]), `best_set` (int32[n]) and
     `trace` (int64[T*3]) are optional output buffers, all on the host or all
-    on the device; `init_loads` (int64[n]) may live on either side."""
+    on the device; `init_loads` (int64[n]) may live on either side.  `path`:
+    0 (by size), DSG_PATH_GRID or DSG_PATH_BLOCK."""
     res = dsg_result()
     pl, dl = _ptr(loads, np.int64)
     ps, ds = _ptr(best_set, np.int32)
@@ -160,7 +162,7 @@ def dsg_run(ctx, graph, variant: int, T: int, eps_num: int = 0, eps_den: int = 1
     dev = {d for p, d in ((pl, dl), (ps, ds), (pt, dt)) if p is not None}
     if len(dev) > 1:
         raise ValueError("output buffers must all be host or all device")
-    res.flags = (DSG_DST_DEVICE if dev == {True} else 0) | (DSG_INIT_DEVICE if di else 0)
+    res.flags = (DSG_DST_DEVICE if dev == {True} else 0) | (DSG_INIT_DEVICE if di else 0) | path
     res.loads, res.best_set, res.trace = pl, ps, pt
     _check(ctx, LIB.dsg_run(graph, variant, T, eps_num, eps_den, pi, ctypes.byref(res)))
     return dict(best_edges=res.best_edges, best_vertices=res.best_vertices,

@@ -52,6 +52,14 @@ struct dsg_graph {
     int32_t *npass_log = nullptr;
     PeelBufs pb{};
     bool pb_ready = false;
+    // whole-GPU structures (degree-oriented copy, chunk schedule): built at
+    // upload for large graphs, on first use of the grid path for compact ones
+    bool grid_ready = false;
+    bool compact = false;
+    int full_check = 0;
+    // single-block path: parameters, run state and output staging
+    void *bk_mem = nullptr;
+    size_t bk_bytes = 0;
 };
 
 struct dsg_batch {
@@ -199,6 +207,140 @@ int ensure_run_bufs(dsg_ctx *ctx, dsg_graph *G, int32_t T)
 
 __global__ void k_log_npass(const Control *ctl, int32_t *log, int t) { log[t - 1] = ctl->npass; }
 
+const char *const kGraphErr[5] = {"offsets are not non-decreasing", "a neighbour id is out of [0, n)",
+                                  "the graph has a self-loop",
+                                  "an adjacency list is not strictly ascending (duplicate or unsorted)",
+                                  "the graph is not symmetric"};
+
+// degree-oriented copy (with the adjacency checks fused into its count pass)
+// and the chunk schedule of the vertices of large out-degree
+int build_grid(dsg_ctx *ctx, dsg_graph *G)
+{
+    cudaError_t e;
+    int32_t h_err[8];
+    const int64_t n = G->g.n;
+    if ((e = build_orientation(G->g, ctx->stream, G->full_check, ctx->err_flags, &G->g.sorted, &G->ooff,
+                               &G->oadj, &G->hub, &G->g.n_hub, &G->hot, &G->g.n_hot)) != cudaSuccess)
+        return cuda_fail(ctx, e, "orientation");
+    cudaMemcpyAsync(h_err, ctx->err_flags, sizeof(h_err), cudaMemcpyDeviceToHost, ctx->stream);
+    if ((e = cudaStreamSynchronize(ctx->stream)) != cudaSuccess) return cuda_fail(ctx, e, "upload");
+    for (int i = 0; i < 5; ++i)
+        if (h_err[i]) return fail(ctx, DSG_ERR_INVALID, "invalid graph: %s", kGraphErr[i]);
+    G->g.ooff = G->ooff;
+    G->g.oadj = G->oadj;
+    G->g.hub_id = G->hub;
+    G->g.hot_id = G->hot;
+    void *tmp = nullptr;
+    const size_t tmp_bytes = (size_t)schedule_tmp_count(n) * sizeof(int64_t);
+    if ((e = cudaMallocAsync(&tmp, tmp_bytes, ctx->stream)) != cudaSuccess) return cuda_fail(ctx, e, "schedule scratch");
+    GraphDev og = G->g;
+    og.off = G->ooff;
+    e = build_schedule(og, tmp, tmp_bytes, ctx->stream, &G->g.n_items, &G->g.n_heavy, &G->items, &G->heavy_mem);
+    cudaFreeAsync(tmp, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "schedule");
+    G->g.items = G->items;
+    G->g.heavy_acc = G->heavy_mem;
+    G->g.heavy_done = G->heavy_mem + (G->g.n_heavy > 0 ? G->g.n_heavy : 1);
+    if ((e = cudaStreamSynchronize(ctx->stream)) != cudaSuccess) return cuda_fail(ctx, e, "upload");
+    ctx->launches[DSG_PHASE_OTHER] += 5;
+    G->grid_ready = true;
+    return DSG_OK;
+}
+
+// parameters of a one-graph launch of the batch kernel
+struct BlockParams {
+    int64_t vbase[2];
+    int64_t pq[2];
+    int32_t T, order;
+    uint32_t ctr, pad;
+};
+
+// All T iterations in one thread block (the batched form's kernel on one
+// graph): no grid-wide synchronisation and a single launch per run.
+int run_block(dsg_ctx *ctx, dsg_graph *G, int variant, int32_t T, int64_t p, int64_t q,
+              const int64_t *init_loads, bool init_dev, dsg_result *out)
+{
+    const int64_t n = G->g.n;
+    cudaStream_t s = ctx->stream;
+    const bool dst_dev = out->flags & DSG_DST_DEVICE;
+    const size_t need = align256(sizeof(BlockParams)) + 4 * align256(4 * (size_t)n) + 2 * align256(8 * (size_t)n)
+                      + 2 * align256(8 * (size_t)n) + align256(4 * (size_t)n) + align256(32)
+                      + align256(24 * (size_t)T);
+    if (G->bk_bytes < need) {
+        if (G->bk_mem) cudaFreeAsync(G->bk_mem, s);
+        G->bk_mem = nullptr;
+        G->bk_bytes = 0;
+        CK(cudaMallocAsync(&G->bk_mem, need, s), "block-path buffers");
+        G->bk_bytes = need;
+    }
+    char *mp = (char *)G->bk_mem;
+    auto take = [&](size_t b) { char *r = mp; mp += align256(b); return (void *)r; };
+    BlockParams *prm = (BlockParams *)take(sizeof(BlockParams));
+    BatchDev bd{};
+    bd.G = 1;
+    bd.Tmax = T;
+    bd.vbase = prm->vbase;
+    bd.off = G->off;
+    bd.adj = G->adj;
+    bd.order = &prm->order;
+    bd.T = &prm->T;
+    bd.pq = prm->pq;
+    bd.loads = (uint32_t *)take(4 * (size_t)n);
+    bd.A = (uint32_t *)take(4 * (size_t)n);
+    bd.best_loads = (uint32_t *)take(4 * (size_t)n);
+    bd.round = (uint32_t *)take(4 * (size_t)n);
+    bd.keys = (uint32_t *)take(8 * (size_t)n);
+    bd.ids = (uint32_t *)take(8 * (size_t)n);
+    int64_t *st_init = (int64_t *)take(8 * (size_t)n);
+    int64_t *st_loads = (int64_t *)take(8 * (size_t)n);
+    int32_t *st_set = (int32_t *)take(4 * (size_t)n);
+    int64_t *st_best = (int64_t *)take(32);
+    int64_t *st_trace = (int64_t *)take(24 * (size_t)T);
+    bd.init = nullptr;
+    if (init_loads) {
+        if (init_dev) bd.init = init_loads;
+        else {
+            CK(cudaMemcpyAsync(st_init, init_loads, 8 * (size_t)n, cudaMemcpyHostToDevice, s), "init loads copy");
+            bd.init = st_init;
+        }
+    }
+    bd.loads_out = out->loads ? (dst_dev ? out->loads : st_loads) : nullptr;
+    bd.sets = out->best_set ? (dst_dev ? out->best_set : st_set) : nullptr;
+    bd.best = st_best;
+    bd.trace = out->trace ? (dst_dev ? out->trace : st_trace) : nullptr;
+    BlockParams h{};
+    h.vbase[0] = 0;
+    h.vbase[1] = n;
+    h.pq[0] = p;
+    h.pq[1] = q;
+    h.T = T;
+    h.order = 0;
+    CK(cudaMemcpyAsync(prm, &h, sizeof h, cudaMemcpyHostToDevice, s), "parameters");
+    const int threads = n <= 1024 ? 256 : (n <= 8192 ? 512 : 1024);
+    {
+        PhaseTimer pt(ctx, DSG_PHASE_OTHER);
+        CK(launch_batch(bd, variant, threads, ctx->sm_count, &prm->ctr, s), "block-path kernel");
+    }
+    ctx->launches[DSG_PHASE_OTHER] += 2;
+    int64_t best[4];
+    CK(cudaMemcpyAsync(best, st_best, 32, cudaMemcpyDeviceToHost, s), "best D2H");
+    if (!dst_dev) {
+        if (out->loads) CK(cudaMemcpyAsync(out->loads, st_loads, 8 * (size_t)n, cudaMemcpyDeviceToHost, s), "loads D2H");
+        if (out->trace) CK(cudaMemcpyAsync(out->trace, st_trace, 24 * (size_t)T, cudaMemcpyDeviceToHost, s), "trace D2H");
+    }
+    CK(cudaStreamSynchronize(s), "run");
+    if (!dst_dev && out->best_set && best[3] > 0) {
+        CK(cudaMemcpyAsync(out->best_set, st_set, 4 * (size_t)best[3], cudaMemcpyDeviceToHost, s), "set D2H");
+        CK(cudaStreamSynchronize(s), "set D2H");
+    }
+    out->best_edges = best[0];
+    out->best_vertices = best[1];
+    out->best_iter = (int32_t)best[2];
+    out->best_set_size = best[3];
+    if (ctx->profiling) collect_timings(ctx);
+    return DSG_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -296,11 +438,36 @@ int dsg_upload_csr(dsg_ctx *ctx, int64_t n, const int64_t *offsets, const int32_
     G->g.arcs = arcs;
     G->g.off = G->off;
     G->g.adj = G->adj;
+    G->full_check = (flags & DSG_VALIDATE) ? 1 : 0;
+    G->compact = is_compact(n, arcs);
+    int32_t h_err[8];
+    if (G->compact && !dev_src) {
+        // offsets and degrees checked on the host; the adjacency by one kernel
+        int64_t maxdeg = 0;
+        for (int64_t u = 0; u < n; ++u) {
+            const int64_t d = offsets[u + 1] - offsets[u];
+            if (d < 0 || offsets[u + 1] > arcs) return bail(fail(ctx, DSG_ERR_INVALID, "invalid graph: %s", kGraphErr[0]));
+            maxdeg = std::max(maxdeg, d);
+        }
+        G->g.max_degree = maxdeg;
+        if ((e = cudaMemsetAsync(ctx->err_flags, 0, 8 * sizeof(int32_t), ctx->stream)) != cudaSuccess)
+            return bail(cuda_fail(ctx, e, "memset"));
+        if ((e = launch_validate_adjacency(G->g, G->full_check, ctx->err_flags, ctx->stream)) != cudaSuccess)
+            return bail(cuda_fail(ctx, e, "validate"));
+        cudaMemcpyAsync(h_err, ctx->err_flags, sizeof(h_err), cudaMemcpyDeviceToHost, ctx->stream);
+        if ((e = cudaStreamSynchronize(ctx->stream)) != cudaSuccess) return bail(cuda_fail(ctx, e, "upload"));
+        for (int i = 1; i < 5; ++i)
+            if (h_err[i]) return bail(fail(ctx, DSG_ERR_INVALID, "invalid graph: %s", kGraphErr[i]));
+        G->g.sorted = h_err[5] ? 0 : 1;
+        ctx->launches[DSG_PHASE_OTHER] += 2;
+        *out = G;
+        return DSG_OK;
+    }
     // validation: offsets first (monotone, inside [0, 2m]); the adjacency
     // (ids in range, no self-loops; with DSG_VALIDATE also strictly ascending
-    // lists and symmetry) is checked in the pass that orients the graph
-    int32_t h_err[8];
-    if ((e = launch_validate(G->g, (flags & DSG_VALIDATE) ? 1 : 0, ctx->err_flags, ctx->stream)) != cudaSuccess)
+    // lists and symmetry) is checked in the pass that orients the graph, or
+    // on its own for a compact graph
+    if ((e = launch_validate(G->g, G->full_check, ctx->err_flags, ctx->stream)) != cudaSuccess)
         return bail(cuda_fail(ctx, e, "validate"));
     if ((e = cudaMemsetAsync(ctx->red, 0, 8, ctx->stream)) != cudaSuccess) return bail(cuda_fail(ctx, e, "memset"));
     if ((e = launch_degree_max(G->off, n, ctx->red, ctx->stream)) != cudaSuccess)
@@ -309,40 +476,23 @@ int dsg_upload_csr(dsg_ctx *ctx, int64_t n, const int64_t *offsets, const int32_
     cudaMemcpyAsync(h_err, ctx->err_flags, sizeof(h_err), cudaMemcpyDeviceToHost, ctx->stream);
     cudaMemcpyAsync(&h_maxdeg, ctx->red, 8, cudaMemcpyDeviceToHost, ctx->stream);
     if ((e = cudaStreamSynchronize(ctx->stream)) != cudaSuccess) return bail(cuda_fail(ctx, e, "upload"));
-    static const char *what[5] = {"offsets are not non-decreasing", "a neighbour id is out of [0, n)",
-                                  "the graph has a self-loop",
-                                  "an adjacency list is not strictly ascending (duplicate or unsorted)",
-                                  "the graph is not symmetric"};
-    for (int i = 0; i < 5; ++i)
-        if (h_err[i]) return bail(fail(ctx, DSG_ERR_INVALID, "invalid graph: %s", what[i]));
+    if (h_err[0]) return bail(fail(ctx, DSG_ERR_INVALID, "invalid graph: %s", kGraphErr[0]));
     G->g.max_degree = (int64_t)h_maxdeg;
-    // degree-oriented copy for the sorting edge scan, and the chunk schedule
-    // of its vertices of large out-degree
-    if ((e = build_orientation(G->g, ctx->stream, (flags & DSG_VALIDATE) ? 1 : 0, ctx->err_flags,
-                               &G->g.sorted, &G->ooff, &G->oadj, &G->hub, &G->g.n_hub, &G->hot,
-                               &G->g.n_hot)) != cudaSuccess)
-        return bail(cuda_fail(ctx, e, "orientation"));
-    cudaMemcpyAsync(h_err, ctx->err_flags, sizeof(h_err), cudaMemcpyDeviceToHost, ctx->stream);
-    if ((e = cudaStreamSynchronize(ctx->stream)) != cudaSuccess) return bail(cuda_fail(ctx, e, "upload"));
-    for (int i = 0; i < 5; ++i)
-        if (h_err[i]) return bail(fail(ctx, DSG_ERR_INVALID, "invalid graph: %s", what[i]));
-    G->g.ooff = G->ooff;
-    G->g.oadj = G->oadj;
-    G->g.hub_id = G->hub;
-    G->g.hot_id = G->hot;
-    void *tmp = nullptr;
-    const size_t tmp_bytes = (size_t)schedule_tmp_count(n) * sizeof(int64_t);
-    if ((e = cudaMallocAsync(&tmp, tmp_bytes, ctx->stream)) != cudaSuccess) return bail(cuda_fail(ctx, e, "schedule scratch"));
-    GraphDev og = G->g;
-    og.off = G->ooff;
-    e = build_schedule(og, tmp, tmp_bytes, ctx->stream, &G->g.n_items, &G->g.n_heavy, &G->items, &G->heavy_mem);
-    cudaFreeAsync(tmp, ctx->stream);
-    if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "schedule"));
-    G->g.items = G->items;
-    G->g.heavy_acc = G->heavy_mem;
-    G->g.heavy_done = G->heavy_mem + (G->g.n_heavy > 0 ? G->g.n_heavy : 1);
-    if ((e = cudaStreamSynchronize(ctx->stream)) != cudaSuccess) return bail(cuda_fail(ctx, e, "upload"));
-    ctx->launches[DSG_PHASE_OTHER] += 7;
+    ctx->launches[DSG_PHASE_OTHER] += 2;
+    if (G->compact) {
+        if ((e = launch_validate_adjacency(G->g, G->full_check, ctx->err_flags, ctx->stream)) != cudaSuccess)
+            return bail(cuda_fail(ctx, e, "validate"));
+        cudaMemcpyAsync(h_err, ctx->err_flags, sizeof(h_err), cudaMemcpyDeviceToHost, ctx->stream);
+        if ((e = cudaStreamSynchronize(ctx->stream)) != cudaSuccess) return bail(cuda_fail(ctx, e, "upload"));
+        for (int i = 1; i < 5; ++i)
+            if (h_err[i]) return bail(fail(ctx, DSG_ERR_INVALID, "invalid graph: %s", kGraphErr[i]));
+        G->g.sorted = h_err[5] ? 0 : 1;
+        ctx->launches[DSG_PHASE_OTHER] += 1;
+        *out = G;
+        return DSG_OK;
+    }
+    const int rc = build_grid(ctx, G);
+    if (rc != DSG_OK) return bail(rc);
     *out = G;
     return DSG_OK;
 }
@@ -372,6 +522,7 @@ void dsg_free_graph(dsg_graph *G)
     if (G->rb_mem) cudaFreeAsync(G->rb_mem, ctx->stream);
     if (G->rb.trace) cudaFreeAsync(G->rb.trace, ctx->stream);
     if (G->npass_log) cudaFreeAsync(G->npass_log, ctx->stream);
+    if (G->bk_mem) cudaFreeAsync(G->bk_mem, ctx->stream);
     peel_free(G->pb, ctx->stream);
     cudaStreamSynchronize(ctx->stream);
     delete G;
@@ -436,6 +587,15 @@ int dsg_run(dsg_graph *G, int variant, int32_t T, int64_t eps_num, int64_t eps_d
     if (max_init + (unsigned long long)T * (unsigned long long)G->g.max_degree >= (1ull << 32))
         return fail(ctx, DSG_ERR_OVERFLOW, "max(init) + T * max_degree = %llu does not fit 32-bit loads",
                     max_init + (unsigned long long)T * (unsigned long long)G->g.max_degree);
+    if ((out->flags & DSG_PATH_GRID) && (out->flags & DSG_PATH_BLOCK))
+        return fail(ctx, DSG_ERR_INVALID, "DSG_PATH_GRID and DSG_PATH_BLOCK are exclusive");
+    const bool block_path = (out->flags & DSG_PATH_BLOCK) ||
+                            (!(out->flags & DSG_PATH_GRID) && block_path_default(variant, n, G->g.arcs));
+    if (block_path) return run_block(ctx, G, variant, T, eps_num, eps_den, init_loads, init_dev, out);
+    if (!G->grid_ready) {
+        const int rg = build_grid(ctx, G);
+        if (rg != DSG_OK) return rg;
+    }
     int rc = ensure_run_bufs(ctx, G, T);
     if (rc) return rc;
     RunBufs &b = G->rb;

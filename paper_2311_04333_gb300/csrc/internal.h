@@ -137,7 +137,25 @@ struct RunBufs {
 };
 
 int edge_scan_sm_count();
+// Default execution path of dsg_run.  Up to these sizes one thread block
+// carrying all T iterations (the kernel of the batched form, on one graph)
+// beats the whole-GPU kernels, whose cost there is launches and grid-wide
+// barriers: PaRGreedy++ up to 32,768 vertices and 2^20 arcs ("compact"
+// graphs, whose upload skips the whole-GPU structures), PaRSorting++ up to
+// 4,096 vertices and 2^17 arcs.
+constexpr int64_t kCompactN = 1 << 15;
+constexpr int64_t kCompactArcs = 1 << 20;
+constexpr int64_t kBlockSortN = 1 << 12;
+constexpr int64_t kBlockSortArcs = 1 << 17;
+inline bool is_compact(int64_t n, int64_t arcs) { return n <= kCompactN && arcs <= kCompactArcs; }
+inline bool block_path_default(int variant, int64_t n, int64_t arcs)
+{
+    return variant == 1 ? is_compact(n, arcs) : (n <= kBlockSortN && arcs <= kBlockSortArcs);
+}
+
 cudaError_t launch_validate(const GraphDev &g, int full, int32_t *err_flags, cudaStream_t s);
+// err[1..5] of the adjacency alone (as the orientation pass records them)
+cudaError_t launch_validate_adjacency(const GraphDev &g, int full, int32_t *err_flags, cudaStream_t s);
 int64_t schedule_tmp_count(int64_t n);
 cudaError_t build_schedule(GraphDev &g, void *tmp, size_t tmp_bytes, cudaStream_t s,
                            int64_t *n_items_out, int64_t *n_heavy_out, WorkItem **items_out,

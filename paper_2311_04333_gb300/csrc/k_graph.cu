@@ -48,6 +48,27 @@ __global__ void k_validate_offsets(const int64_t *__restrict__ off, int64_t n, i
     }
 }
 
+// adjacency checks on their own (warp per vertex), for graphs uploaded
+// without the degree-oriented copy that otherwise carries them
+__global__ void k_validate_adjacency(const int64_t *__restrict__ off, const int32_t *__restrict__ adj,
+                                     int64_t n, int full, int32_t *err)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t u = w0; u < n; u += nw) {
+        const int64_t s = off[u], e = off[u + 1];
+        for (int64_t j = s + lane; j < e; j += 32) check_arc(off, adj, n, u, s, j, full, err);
+    }
+}
+
+cudaError_t launch_validate_adjacency(const GraphDev &g, int full, int32_t *err_flags, cudaStream_t s)
+{
+    const int grid = (int)imax64(1, imin64((g.n + 7) / 8, 152 * 16));
+    k_validate_adjacency<<<grid, 256, 0, s>>>(g.off, g.adj, g.n, full, err_flags);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_validate(const GraphDev &g, int full, int32_t *err_flags, cudaStream_t s)
 {
     cudaMemsetAsync(err_flags, 0, 8 * sizeof(int32_t), s);

@@ -12,8 +12,9 @@
 //
 // PaRGreedy++ runs as one cooperative launch whose blocks meet at grid-wide
 // barriers sized for the whole GPU; two such launches from different slots
-// must not compete for residency, so the server runs at most one PaRGreedy++
-// request at a time (PaRSorting++ requests keep overlapping with it).
+// must not compete for residency, so the server runs at most one such
+// request at a time.  Compact graphs run as one thread block without
+// grid-wide barriers and overlap freely, as do PaRSorting++ requests.
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -25,6 +26,7 @@
 #include <vector>
 
 #include "dsg.h"
+#include "internal.h"
 
 namespace {
 
@@ -91,7 +93,7 @@ void run_request(dsg_server *s, dsg_ctx *ctx, Request *r)
         r->res.loads = r->loads.data();
         r->res.best_set = r->set.data();
         r->res.trace = nullptr;
-        if (r->variant == DSG_PEELING) {
+        if (r->variant == DSG_PEELING && !dsg::is_compact(r->n, 2 * r->m)) {
             std::lock_guard<std::mutex> lk(s->coop_mu);
             rc = dsg_run(g, r->variant, r->T, r->p, r->q, nullptr, &r->res);
         } else {

@@ -6,7 +6,7 @@ import pytest
 import graphgen as gg
 import oracle as orc
 
-from test_gpu_sorting import check  # noqa: F401  (shared exact comparison)
+from test_gpu_sorting import check, path  # noqa: F401  (shared exact comparison, both paths)
 
 pytestmark = pytest.mark.gpu
 
@@ -57,11 +57,11 @@ def test_complete_and_degenerate(dsg, ctx):
     check(dsg, ctx, gg.from_edges(9000, [(i, i + 3) for i in range(0, 8990, 7)]), orc.PEELING, 3, 1, 10)
 
 
-def test_resume(dsg, ctx):
+def test_resume(dsg, ctx, path):
     g = gg.er_m(8000, 10, 31)
-    full = dsg.densest(ctx, g.n, g.off, g.adj, dsg.DSG_PEELING, 7, (1, 10))
-    a = dsg.densest(ctx, g.n, g.off, g.adj, dsg.DSG_PEELING, 3, (1, 10))
-    b = dsg.densest(ctx, g.n, g.off, g.adj, dsg.DSG_PEELING, 4, (1, 10), init_loads=a.loads)
+    full = dsg.densest(ctx, g.n, g.off, g.adj, dsg.DSG_PEELING, 7, (1, 10), path=path)
+    a = dsg.densest(ctx, g.n, g.off, g.adj, dsg.DSG_PEELING, 3, (1, 10), path=path)
+    b = dsg.densest(ctx, g.n, g.off, g.adj, dsg.DSG_PEELING, 4, (1, 10), init_loads=a.loads, path=path)
     assert np.array_equal(b.loads, full.loads)
 
 

@@ -1,7 +1,9 @@
 """Parity of the CUDA PaRSorting++ path (through the C ABI) with the oracle.
 
 Every comparison is exact: final loads, best (edges, vertices, iteration),
-best vertex set and the per-iteration trace must be identical.
+best vertex set and the per-iteration trace must be identical.  Each test
+runs on both execution paths of dsg_run: the whole-GPU kernels and the
+single-block kernel (the default for compact graphs).
 """
 import numpy as np
 import pytest
@@ -26,8 +28,21 @@ def ctx(dsg):
     dsg.dsg_destroy(c)
 
 
+PATHS = {"grid": 0x4, "block": 0x8}
+_CUR = {"path": 0x4}
+BLOCK_PATH_MAX_N = 300_000      # larger graphs take the block path only in dedicated tests
+
+
+@pytest.fixture(params=["grid", "block"], autouse=True)
+def path(request):
+    _CUR["path"] = PATHS[request.param]
+    yield _CUR["path"]
+
+
 def check(dsg, ctx, g, variant=orc.SORTING, T=10, p=1, q=10, init=None):
-    r = dsg.densest(ctx, g.n, g.off, g.adj, variant, T, (p, q), init)
+    if _CUR["path"] == PATHS["block"] and g.n > BLOCK_PATH_MAX_N:
+        pytest.skip("single-block path: covered on smaller graphs")
+    r = dsg.densest(ctx, g.n, g.off, g.adj, variant, T, (p, q), init, path=_CUR["path"])
     o = orc.run(g, variant, T, p, q, init)
     assert (r.best_edges, r.best_vertices, r.best_iter) == (o.best_edges, o.best_vertices, o.best_iter)
     bad = np.flatnonzero(r.loads != o.loads)
@@ -93,11 +108,11 @@ def test_many_ties_and_large_loads(dsg, ctx):
     check(dsg, ctx, g, T=4, init=init)
 
 
-def test_resume_equals_one_run(dsg, ctx):
+def test_resume_equals_one_run(dsg, ctx, path):
     g = gg.er_m(15000, 9, 31)
-    full = dsg.densest(ctx, g.n, g.off, g.adj, dsg.DSG_SORTING, 9)
-    a = dsg.densest(ctx, g.n, g.off, g.adj, dsg.DSG_SORTING, 4)
-    b = dsg.densest(ctx, g.n, g.off, g.adj, dsg.DSG_SORTING, 5, init_loads=a.loads)
+    full = dsg.densest(ctx, g.n, g.off, g.adj, dsg.DSG_SORTING, 9, path=path)
+    a = dsg.densest(ctx, g.n, g.off, g.adj, dsg.DSG_SORTING, 4, path=path)
+    b = dsg.densest(ctx, g.n, g.off, g.adj, dsg.DSG_SORTING, 5, init_loads=a.loads, path=path)
     assert np.array_equal(b.loads, full.loads)
     assert np.array_equal(np.concatenate([a.trace, b.trace]), full.trace)
 
@@ -108,7 +123,7 @@ def test_rmat20_config(dsg, ctx):
     check(dsg, ctx, g, T=20)
 
 
-def test_device_buffers(dsg, ctx):
+def test_device_buffers(dsg, ctx, path):
     import torch
     g = gg.er_m(30000, 10, 41)
     off = torch.from_numpy(g.off).cuda()
@@ -120,7 +135,7 @@ def test_device_buffers(dsg, ctx):
         loads = torch.empty(g.n, dtype=torch.int64, device="cuda")
         bset = torch.empty(g.n, dtype=torch.int32, device="cuda")
         trace = torch.empty(3 * T, dtype=torch.int64, device="cuda")
-        r = dsg.dsg_run(ctx, gr, dsg.DSG_SORTING, T, 0, 1, init, loads, bset, trace)
+        r = dsg.dsg_run(ctx, gr, dsg.DSG_SORTING, T, 0, 1, init, loads, bset, trace, path)
     finally:
         dsg.dsg_free_graph(gr)
     o = orc.run(g, orc.SORTING, T, 0, 1, init.cpu().numpy())
@@ -130,7 +145,7 @@ def test_device_buffers(dsg, ctx):
     assert np.array_equal(trace.cpu().numpy().reshape(T, 3), o.trace)
 
 
-def test_invalid_inputs(dsg, ctx):
+def test_invalid_inputs(dsg, ctx, path):
     ok = gg.complete(4)
     with pytest.raises(dsg.DsgError, match="INVALID"):
         dsg.dsg_upload_csr(ctx, 0, np.zeros(1, np.int64), np.zeros(0, np.int32))
@@ -154,26 +169,30 @@ def test_invalid_inputs(dsg, ctx):
     g = dsg.dsg_upload_csr(ctx, ok.n, ok.off, ok.adj, dsg.DSG_VALIDATE)
     try:
         with pytest.raises(dsg.DsgError, match="INVALID"):
-            dsg.dsg_run(ctx, g, dsg.DSG_SORTING, 0)
+            dsg.dsg_run(ctx, g, dsg.DSG_SORTING, 0, path=path)
         with pytest.raises(dsg.DsgError, match="INVALID"):
-            dsg.dsg_run(ctx, g, 7, 3)
+            dsg.dsg_run(ctx, g, 7, 3, path=path)
+        with pytest.raises(dsg.DsgError, match="INVALID"):
+            dsg.dsg_run(ctx, g, dsg.DSG_SORTING, 3, path=0xC)
         with pytest.raises(dsg.DsgError, match="OVERFLOW"):
-            dsg.dsg_run(ctx, g, dsg.DSG_SORTING, 2, init_loads=np.full(4, 2**32 - 3, np.int64))
+            dsg.dsg_run(ctx, g, dsg.DSG_SORTING, 2, init_loads=np.full(4, 2**32 - 3, np.int64), path=path)
         with pytest.raises(dsg.DsgError, match="INVALID"):
-            dsg.dsg_run(ctx, g, dsg.DSG_SORTING, 2, init_loads=np.array([0, -1, 0, 0], np.int64))
+            dsg.dsg_run(ctx, g, dsg.DSG_SORTING, 2, init_loads=np.array([0, -1, 0, 0], np.int64), path=path)
         # the context still works after the errors
-        r = dsg.dsg_run(ctx, g, dsg.DSG_SORTING, 2)
+        r = dsg.dsg_run(ctx, g, dsg.DSG_SORTING, 2, path=path)
         assert (r["best_edges"], r["best_vertices"]) == (6, 4)
     finally:
         dsg.dsg_free_graph(g)
 
 
-def test_profiling_stats(dsg, ctx):
+def test_profiling_stats(dsg, ctx, path):
+    if path != PATHS["grid"]:
+        pytest.skip("phase statistics of the whole-GPU kernels")
     g = gg.er_m(20000, 8, 51)
     dsg.dsg_get_stats(ctx, reset=True)
     dsg.dsg_set_profiling(ctx, True)
     try:
-        dsg.densest(ctx, g.n, g.off, g.adj, dsg.DSG_SORTING, 3)
+        dsg.densest(ctx, g.n, g.off, g.adj, dsg.DSG_SORTING, 3, path=path)
     finally:
         dsg.dsg_set_profiling(ctx, False)
     st = dsg.dsg_get_stats(ctx, reset=True)
@@ -182,7 +201,7 @@ def test_profiling_stats(dsg, ctx):
     assert st["edge_scan"]["bytes"] == 3 * (8 * g.m + 16 * g.n)
 
 
-def test_unsorted_adjacency_lists(dsg, ctx):
+def test_unsorted_adjacency_lists(dsg, ctx, path):
     """Lists need not be sorted without DSG_VALIDATE: the equal-loads shortcut
     (binary search in a sorted list) is then off and the general scan runs."""
     g = gg.er_m(20000, 10, 71)
@@ -197,7 +216,7 @@ def test_unsorted_adjacency_lists(dsg, ctx):
         loads = np.zeros(g.n, np.int64)
         bset = np.zeros(g.n, np.int32)
         trace = np.zeros(3 * T, np.int64)
-        r = dsg.dsg_run(ctx, gr, dsg.DSG_SORTING, T, 0, 1, None, loads, bset, trace)
+        r = dsg.dsg_run(ctx, gr, dsg.DSG_SORTING, T, 0, 1, None, loads, bset, trace, path)
     finally:
         dsg.dsg_free_graph(gr)
     o = orc.run(g, orc.SORTING, T)
@@ -205,3 +224,32 @@ def test_unsorted_adjacency_lists(dsg, ctx):
     assert (r["best_edges"], r["best_vertices"], r["best_iter"]) == (o.best_edges, o.best_vertices, o.best_iter)
     assert np.array_equal(bset[: r["best_set_size"]].astype(np.int64), o.best_set)
     assert np.array_equal(trace.reshape(T, 3), o.trace)
+
+
+def test_default_path_by_size(dsg, ctx, path):
+    """Without a path flag, compact graphs take the single-block kernel (one
+    launch per run) and larger ones the whole-GPU kernels."""
+    if path != PATHS["grid"]:
+        pytest.skip("checked once")
+    cases = [(gg.er_m(3000, 8, 3), orc.SORTING, True), (gg.er_m(10000, 8, 3), orc.SORTING, False),
+             (gg.er_m(10000, 8, 3), orc.PEELING, True), (gg.er_m(70000, 4, 3), orc.PEELING, False)]
+    for g, variant, one_launch in cases:
+        gr = dsg.dsg_upload_csr(ctx, g.n, g.off, g.adj, 0)
+        try:
+            dsg.dsg_get_stats(ctx, reset=True)
+            r = dsg.dsg_run(ctx, gr, variant, 3, 1, 10)
+            st = dsg.dsg_get_stats(ctx, reset=True)
+        finally:
+            dsg.dsg_free_graph(gr)
+        launches = sum(v["launches"] for v in st.values())
+        assert (launches == 2) == one_launch, (g.n, variant, launches)   # block path: reset + kernel
+        o = orc.run(g, variant, 3, 1, 10)
+        assert (r["best_edges"], r["best_vertices"], r["best_iter"]) == (o.best_edges, o.best_vertices, o.best_iter)
+
+
+def test_block_path_on_a_large_graph(dsg, ctx, path):
+    """The single-block kernel forced on a graph above the compact size."""
+    if path != PATHS["block"]:
+        pytest.skip("checked once")
+    check(dsg, ctx, gg.chung_lu(120000, 12, 2.1, 17), orc.SORTING, 4)
+    check(dsg, ctx, gg.chung_lu(120000, 12, 2.1, 17), orc.PEELING, 3, 1, 10)
