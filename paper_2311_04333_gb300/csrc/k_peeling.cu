@@ -5,14 +5,23 @@
 // key (key*q <= min*(p+q)), all at once; the degree decrements they cause are
 // applied only after the round's set is fixed.  The order is (round, id).
 //
-// One cooperative persistent kernel runs all rounds of an iteration; each
-// round has three phases separated by bounded grid barriers:
-//   A: key of every alive vertex, grid minimum;
-//   B: split the alive list into the round's set F (round[v] = r) and the
-//      next alive list;
-//   C: for v in F, count its later neighbours (alive ones, and same-round
-//      ones with a larger id) -> A[v], l(v) += A[v], and decrement deg_H of
-//      the alive neighbours.
+// One cooperative persistent kernel runs all rounds of an iteration, two
+// bounded grid barriers per round (three when F has vertices of degree
+// above 512):
+//   A:  every alive vertex publishes its key (kept as kv = l + deg_H and
+//       decremented in place) in a snapshot word st = (round | key); grid
+//       minimum of the keys;
+//   BC: the round's set F = {key*q <= thr} is decided from the snapshots,
+//       so a block can split its share of the alive list and at once process
+//       the low-degree F vertices it found: for v in F, count its later
+//       neighbours (alive ones not in F, and ones in F with a larger id)
+//       -> A[v], l(v) += A[v], and decrement kv of the alive neighbours not
+//       in F;
+//   H:  the same for the heavier F vertices, whose arcs are cut into chunks
+//       of 2,048 that all blocks share.
+// Blocks leave as the alive set shrinks (one block per 4,096 alive vertices
+// or 65,536 of their arcs, whichever needs more), down to a single block
+// that rounds with block barriers only.
 // The densest suffix of the (round, id) order then reuses the radix passes
 // of the sorting path with key = round and value = A (Alg. 3 lines 4-7).
 #include <mutex>
@@ -24,18 +33,35 @@
 namespace dsg {
 
 constexpr uint32_t kUnpeeled = 0xffffffffu;
-constexpr int kPeelThreads = 256;
-constexpr int64_t kBigDegree = 2048;     // F vertices above this use a whole block
+constexpr int kPeelThreads = 1024;
+constexpr uint32_t kAlivePerBlock = 4096;   // blocks: one per this many alive vertices
+constexpr int64_t kArcsPerBlock = 65536;    //   or per this many arcs of alive vertices
+constexpr int64_t kLocalDegree = 512;       // F vertices up to this degree: the finding block
+constexpr int64_t kPeelChunk = 2048;        // arcs per work item of the heavier F vertices
+constexpr int kQueueCap = 2048;             // block-local queue of F vertices
+// heavy-list words: (count or vertex) << 33 | chunk index; n < 2^31 and the
+// chunks of one round are fewer than 2^40 / 2048 + n < 2^33
+constexpr int kHeavyShift = 33;
+constexpr unsigned long long kChunkMask = (1ull << kHeavyShift) - 1;
 
 struct PeelCtl {
     unsigned long long mn[2];   // round minimum key, by round parity
+    unsigned long long heavy[2];// heavy F vertices (bits 33..63) and their chunks (bits 0..32)
     uint32_t n_next[2];         // alive-list sizes, by round parity
-    uint32_t n_fs[2], n_fb[2];  // small / big F sizes, by round parity
     uint32_t rounds;
     uint32_t bar_count, bar_gen;
     uint32_t abort;
     unsigned long long work;    // sum over rounds of the alive-list size
+    unsigned long long arcs_alive;  // arcs of the alive vertices
 };
+
+// blocks worth keeping for na alive vertices holding `arcs` arcs
+__host__ __device__ __forceinline__ uint32_t peel_blocks(uint64_t na, uint64_t arcs)
+{
+    const uint64_t a = (na + kAlivePerBlock - 1) / kAlivePerBlock, b = (arcs + kArcsPerBlock - 1) / kArcsPerBlock;
+    const uint64_t x = a > b ? a : b;
+    return x < 1 ? 1u : (x > 0xffffu ? 0xffffu : (uint32_t)x);
+}
 
 __device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t *p)
 {
@@ -44,30 +70,41 @@ __device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t *p)
     return v;
 }
 
-// bounded grid barrier (all blocks are co-resident: cooperative launch)
-__device__ __forceinline__ bool grid_barrier(PeelCtl *pc, Control *ctl, uint32_t nblocks)
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long *p)
+{
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// bounded barrier over the first `nb` blocks (co-resident: cooperative
+// launch); a single block needs only its own barrier
+__device__ __forceinline__ bool grid_barrier(PeelCtl *pc, Control *ctl, uint32_t nb)
 {
     __shared__ int s_ok;
+    if (nb == 1) {
+        __syncthreads();
+        return true;
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
         const uint32_t gen = ld_acquire_u32(&pc->bar_gen);
         __threadfence();
-        if (atomicAdd(&pc->bar_count, 1u) == nblocks - 1) {
+        if (atomicAdd(&pc->bar_count, 1u) == nb - 1) {
             pc->bar_count = 0;
             __threadfence();
             atomicAdd(&pc->bar_gen, 1u);
         } else {
-            uint32_t polls = 0, ns = 32;
+            uint32_t polls = 0;
             while (ld_acquire_u32(&pc->bar_gen) == gen) {
-                if (ld_acquire_u32(&pc->abort) || ++polls > kSpinLimit) {
+                if (++polls > kSpinLimit || ((polls & 255) == 0 && ld_acquire_u32(&pc->abort))) {
                     atomicExch(&pc->abort, 1u);
                     set_error(ctl, DSG_ERR_TIMEOUT, 400);
                     ok = 0;
                     break;
                 }
-                __nanosleep(ns);
-                if (ns < 256) ns <<= 1;
+                if (polls > 64) __nanosleep(64);
             }
         }
         __threadfence();
@@ -78,165 +115,223 @@ __device__ __forceinline__ bool grid_barrier(PeelCtl *pc, Control *ctl, uint32_t
     return s_ok != 0;
 }
 
-__global__ void k_peel_init(const int64_t *__restrict__ off, int64_t n, int32_t *deg,
-                            uint32_t *round, uint32_t *list0, PeelCtl *pc)
+__global__ void k_peel_init(const int64_t *__restrict__ off, const uint32_t *__restrict__ loads, int64_t n,
+                            int64_t arcs, uint32_t *kv, uint32_t *round, uint32_t *list0, PeelCtl *pc)
 {
     for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
          v += (int64_t)gridDim.x * blockDim.x) {
-        deg[v] = (int32_t)(off[v + 1] - off[v]);
+        kv[v] = loads[v] + (uint32_t)(off[v + 1] - off[v]);
         round[v] = kUnpeeled;
         list0[v] = (uint32_t)v;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         pc->mn[0] = pc->mn[1] = ~0ull;
+        pc->heavy[0] = pc->heavy[1] = 0;
         pc->n_next[0] = (uint32_t)n;
         pc->n_next[1] = 0;
-        pc->n_fs[0] = pc->n_fs[1] = 0;
-        pc->n_fb[0] = pc->n_fb[1] = 0;
         pc->rounds = 0;
         pc->bar_count = 0;
         pc->abort = 0;
         pc->work = 0;
+        pc->arcs_alive = (unsigned long long)arcs;
     }
 }
 
-// warp-aggregated append of v (if pred) to list[] through counter *cnt
-__device__ __forceinline__ void warp_append(bool pred, uint32_t v, uint32_t *list, uint32_t *cnt)
+// warp-aggregated slot claim on a counter (all lanes call it)
+__device__ __forceinline__ uint32_t warp_claim(bool pred, uint32_t *cnt)
 {
     const uint32_t m = __ballot_sync(kFull, pred);
-    if (!m) return;
-    const int lane = threadIdx.x & 31;
-    const int leader = __ffs(m) - 1;
+    if (!m) return 0;
+    const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
     uint32_t base = 0;
     if (lane == leader) base = atomicAdd(cnt, (uint32_t)__popc(m));
     base = __shfl_sync(kFull, base, leader);
-    if (pred) list[base + __popc(m & lanemask_lt())] = v;
+    return base + __popc(m & lanemask_lt());
 }
 
-__global__ void __launch_bounds__(kPeelThreads)
+constexpr int64_t kTinyDegree = 8;          // F vertices up to this degree: thread per vertex
+
+struct PeelSmem {
+    unsigned long long red[kPeelThreads / 32];
+    uint32_t queue[kQueueCap];              // F vertices of degree (kTinyDegree, kLocalDegree]
+    uint32_t tiny[kQueueCap];               // F vertices of degree <= kTinyDegree
+    uint32_t nq, nt;
+};
+
+// later-neighbour count of one F vertex over arcs [s, e) with `stride`
+// lanes starting at `first`; decrements kv of the alive neighbours not in F
+__device__ __forceinline__ uint32_t count_arcs(const int32_t *__restrict__ adj, int64_t s, int64_t e, int first,
+                                               int stride, uint32_t v, uint32_t r, unsigned long long thr,
+                                               uint64_t q, const unsigned long long *st, uint32_t *kv)
+{
+    uint32_t c = 0;
+    for (int64_t j = s + first; j < e; j += stride) {
+        const uint32_t w = (uint32_t)adj[j];
+        const unsigned long long sw = st[w];
+        const uint32_t rw = (uint32_t)(sw >> 32);
+        if (rw != kUnpeeled && rw != r) continue;             // peeled in an earlier round
+        const bool w_in_f = rw == r || (sw & 0xffffffffull) * q <= thr;
+        if (!w_in_f) {
+            ++c;
+            atomicSub(&kv[w], 1u);
+        } else if (w > v) {
+            ++c;
+        }
+    }
+    return c;
+}
+
+// the block's queued F vertices of low degree: thread per vertex for the
+// tiny ones, warp per vertex for the others
+__device__ void drain_queue(PeelSmem &S, const int64_t *__restrict__ off, const int32_t *__restrict__ adj,
+                            uint32_t r, unsigned long long thr, uint64_t q, const unsigned long long *st,
+                            uint32_t *kv, uint32_t *loads, uint32_t *A)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int NW = kPeelThreads / 32;
+    const uint32_t nt = S.nt;
+    for (uint32_t f = threadIdx.x; f < nt; f += kPeelThreads) {
+        const uint32_t v = S.tiny[f];
+        const uint32_t c = count_arcs(adj, off[v], off[v + 1], 0, 1, v, r, thr, q, st, kv);
+        A[v] = c;
+        loads[v] += c;
+    }
+    const uint32_t nq = S.nq;
+    for (uint32_t f = warp; f < nq; f += NW) {
+        const uint32_t v = S.queue[f];
+        uint32_t c = count_arcs(adj, off[v], off[v + 1], lane, 32, v, r, thr, q, st, kv);
+        c = __reduce_add_sync(kFull, c);
+        if (lane == 0) {
+            A[v] = c;
+            loads[v] += c;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        S.nq = 0;
+        S.nt = 0;
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(kPeelThreads, 1)
 k_peel(const int64_t *__restrict__ off, const int32_t *__restrict__ adj, int64_t n,
-       uint32_t *loads, uint32_t *A, int32_t *deg, uint32_t *round, uint32_t *list0,
-       uint32_t *list1, uint32_t *flist, unsigned long long *keybuf, uint64_t p, uint64_t q,
+       uint32_t *loads, uint32_t *A, uint32_t *kv, unsigned long long *st, uint32_t *round,
+       uint32_t *list0, uint32_t *list1, unsigned long long *heavy, uint64_t p, uint64_t q,
        PeelCtl *pc, Control *ctl)
 {
-    __shared__ unsigned long long s_min[kPeelThreads / 32];
-    __shared__ uint32_t s_cnt[kPeelThreads / 32];
+    __shared__ PeelSmem S;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const uint32_t nb = gridDim.x;
-    const int64_t gtid = blockIdx.x * (int64_t)blockDim.x + tid;
-    const int64_t gthreads = (int64_t)gridDim.x * blockDim.x;
-    const int64_t gwarp = gtid >> 5, gwarps = gthreads >> 5;
-    uint32_t width = 0;
+    constexpr int NW = kPeelThreads / 32;
     uint32_t r = 0;
+    uint32_t P = gridDim.x;                 // participating blocks
+    if (tid == 0) {
+        S.nq = 0;
+        S.nt = 0;
+    }
     for (;; ++r) {
         const uint32_t na = ld_acquire_u32(&pc->n_next[r & 1]);
         if (na == 0) break;
+        P = min(P, peel_blocks(na, ld_acquire_u64(&pc->arcs_alive)));
+        if (blockIdx.x >= P) break;
         uint32_t *cur = (r & 1) ? list1 : list0;
         uint32_t *nxt = (r & 1) ? list0 : list1;
         if (blockIdx.x == 0 && tid == 0) {
             pc->n_next[(r + 1) & 1] = 0;
             pc->mn[(r + 1) & 1] = ~0ull;
-            pc->n_fs[(r + 1) & 1] = 0;
-            pc->n_fb[(r + 1) & 1] = 0;
+            pc->heavy[(r + 1) & 1] = 0;
             pc->work += na;
         }
-        // ---- phase A: keys and their minimum
+        const uint32_t stride = P * kPeelThreads;
+        // ---- A: snapshot keys, grid minimum
         unsigned long long mn = ~0ull;
-        for (int64_t i = gtid; i < na; i += gthreads) {
+        for (uint32_t i = blockIdx.x * kPeelThreads + tid; i < na; i += stride) {
             const uint32_t v = cur[i];
-            const unsigned long long key = (unsigned long long)loads[v] + (unsigned long long)deg[v];
-            keybuf[i] = key;
-            mn = min(mn, key);
+            const uint32_t k = kv[v];
+            st[v] = ((unsigned long long)kUnpeeled << 32) | k;
+            mn = min(mn, (unsigned long long)k);
         }
         #pragma unroll
         for (int o = 16; o > 0; o >>= 1) mn = min(mn, __shfl_xor_sync(kFull, mn, o));
-        if (lane == 0) s_min[warp] = mn;
+        if (lane == 0) S.red[warp] = mn;
         __syncthreads();
         if (tid == 0) {
             unsigned long long b = ~0ull;
-            for (int i = 0; i < kPeelThreads / 32; ++i) b = min(b, s_min[i]);
+            for (int i = 0; i < NW; ++i) b = min(b, S.red[i]);
             if (b != ~0ull) atomicMin(&pc->mn[r & 1], b);
         }
-        if (!grid_barrier(pc, ctl, nb)) return;
-        // ---- phase B: the round's set F = {key*q <= min*(p+q)}
+        if (!grid_barrier(pc, ctl, P)) return;
+        // ---- BC: split off F; its low-degree vertices are counted here
         const unsigned long long thr = pc->mn[r & 1] * (p + q);
-        for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x; i0 < na; i0 += gthreads) {
-            const int64_t i = i0 + tid;
+        for (uint32_t i0 = blockIdx.x * kPeelThreads; i0 < na; i0 += stride) {
+            const uint32_t i = i0 + tid;
             const bool valid = i < na;
             uint32_t v = 0;
             bool inF = false;
+            int64_t d = 0;
             if (valid) {
                 v = cur[i];
-                inF = keybuf[i] * q <= thr;
-                if (inF) round[v] = r;
-            }
-            const bool big = inF && (off[v + 1] - off[v] > kBigDegree);
-            warp_append(inF && !big, v, flist, &pc->n_fs[r & 1]);
-            // big ones fill flist from the back
-            const uint32_t mb = __ballot_sync(kFull, big);
-            if (mb) {
-                const int leader = __ffs(mb) - 1;
-                uint32_t base = 0;
-                if (lane == leader) base = atomicAdd(&pc->n_fb[r & 1], (uint32_t)__popc(mb));
-                base = __shfl_sync(kFull, base, leader);
-                if (big) flist[n - 1 - (base + __popc(mb & lanemask_lt()))] = v;
-            }
-            warp_append(valid && !inF, v, nxt, &pc->n_next[(r + 1) & 1]);
-        }
-        if (!grid_barrier(pc, ctl, nb)) return;
-        // ---- phase C: later-neighbour counts and delayed degree decrements
-        const uint32_t nfs = pc->n_fs[r & 1], nfb = pc->n_fb[r & 1];
-        for (int64_t f = gwarp; f < nfs; f += gwarps) {
-            const uint32_t v = flist[f];
-            const int64_t s = off[v], e = off[v + 1];
-            uint32_t c = 0;
-            for (int64_t j = s + lane; j < e; j += 32) {
-                const uint32_t w = (uint32_t)adj[j];
-                const uint32_t rw = round[w];
-                if (rw == kUnpeeled) {
-                    ++c;
-                    atomicSub(&deg[w], 1);
-                } else if (rw == r && w > v) {
-                    ++c;
+                const unsigned long long sv = st[v];
+                inF = (sv & 0xffffffffull) * q <= thr;
+                if (inF) {
+                    round[v] = r;
+                    st[v] = ((unsigned long long)r << 32) | (sv & 0xffffffffull);
+                    d = off[v + 1] - off[v];
                 }
             }
-            c = __reduce_add_sync(kFull, c);
-            if (lane == 0) {
-                A[v] = c;
-                loads[v] += c;
-                width = max(width, c);
+            // arcs leaving the alive set with F (one atomic per warp)
+            unsigned long long dsum = (unsigned long long)d;
+            #pragma unroll
+            for (int o = 16; o > 0; o >>= 1) dsum += __shfl_xor_sync(kFull, dsum, o);
+            if (lane == 0 && dsum) atomicAdd(&pc->arcs_alive, ~dsum + 1ull);      // subtract
+            const bool hv = inF && d > kLocalDegree;
+            if (hv) {
+                // heavy: global list entry (v, first chunk); its chunks are
+                // shared by all blocks after the barrier
+                A[v] = 0;
+                const unsigned long long nc = (unsigned long long)((d + kPeelChunk - 1) / kPeelChunk);
+                const unsigned long long old = atomicAdd(&pc->heavy[r & 1], (1ull << kHeavyShift) | nc);
+                heavy[old >> kHeavyShift] = ((unsigned long long)v << kHeavyShift) | (old & kChunkMask);
             }
+            const bool tv = inF && d <= kTinyDegree;
+            const uint32_t ts = warp_claim(tv, &S.nt);
+            if (tv) S.tiny[ts] = v;              // ts, qs < kQueueCap: drained below before they can fill
+            const uint32_t qs = warp_claim(inF && !hv && !tv, &S.nq);
+            if (inF && !hv && !tv) S.queue[qs] = v;
+            const uint32_t ns = warp_claim(valid && !inF, &pc->n_next[(r + 1) & 1]);
+            if (valid && !inF) nxt[ns] = v;
+            __syncthreads();
+            if (S.nq + kPeelThreads > (uint32_t)kQueueCap || S.nt + kPeelThreads > (uint32_t)kQueueCap)
+                drain_queue(S, off, adj, r, thr, q, st, kv, loads, A);
         }
-        for (int64_t f = blockIdx.x; f < nfb; f += gridDim.x) {
-            const uint32_t v = flist[n - 1 - f];
-            const int64_t s = off[v], e = off[v + 1];
-            uint32_t c = 0;
-            for (int64_t j = s + tid; j < e; j += kPeelThreads) {
-                const uint32_t w = (uint32_t)adj[j];
-                const uint32_t rw = round[w];
-                if (rw == kUnpeeled) {
-                    ++c;
-                    atomicSub(&deg[w], 1);
-                } else if (rw == r && w > v) {
-                    ++c;
+        drain_queue(S, off, adj, r, thr, q, st, kv, loads, A);
+        if (!grid_barrier(pc, ctl, P)) return;
+        // ---- H: chunks of the heavier F vertices, over all blocks
+        const unsigned long long hp = ld_acquire_u64(&pc->heavy[r & 1]);
+        const uint32_t nh = (uint32_t)(hp >> kHeavyShift);
+        if (nh > 0) {
+            const unsigned long long nchunks = hp & kChunkMask;
+            for (unsigned long long k = blockIdx.x; k < nchunks; k += P) {
+                // the heavy entry holding chunk k: last with first chunk <= k
+                uint32_t lo = 0, hi = nh - 1;
+                while (lo < hi) {
+                    const uint32_t mid = (lo + hi + 1) >> 1;
+                    if ((heavy[mid] & kChunkMask) <= k) lo = mid; else hi = mid - 1;
+                }
+                const unsigned long long h = heavy[lo];
+                const uint32_t v = (uint32_t)(h >> kHeavyShift);
+                const int64_t s0 = off[v] + (int64_t)(k - (h & kChunkMask)) * kPeelChunk;
+                const int64_t e0 = min(off[v + 1], s0 + kPeelChunk);
+                uint32_t c = count_arcs(adj, s0, e0, tid, kPeelThreads, v, r, thr, q, st, kv);
+                c = __reduce_add_sync(kFull, c);
+                if (lane == 0 && c) {
+                    atomicAdd(&A[v], c);
+                    atomicAdd(&loads[v], c);
                 }
             }
-            c = __reduce_add_sync(kFull, c);
-            if (lane == 0) s_cnt[warp] = c;
-            __syncthreads();
-            if (tid == 0) {
-                uint32_t tot = 0;
-                for (int i = 0; i < kPeelThreads / 32; ++i) tot += s_cnt[i];
-                A[v] = tot;
-                loads[v] += tot;
-                width = max(width, tot);
-            }
-            __syncthreads();
+            if (!grid_barrier(pc, ctl, P)) return;
         }
-        if (!grid_barrier(pc, ctl, nb)) return;
     }
-    width = __reduce_max_sync(kFull, width);
-    if (lane == 0 && width) atomicMax(&ctl->width, width);
     if (blockIdx.x == 0 && tid == 0) pc->rounds = r;
 }
 
@@ -269,6 +364,7 @@ __global__ void k_peel_hist(const uint32_t *__restrict__ round, const uint32_t *
     __shared__ uint32_t h[kMaxPasses][kBuckets];
     __shared__ unsigned long long as[kBuckets];
     const int np = ctl->npass;
+    uint32_t width = 0;                 // largest later-neighbour count (the trace's width)
     for (int i = threadIdx.x; i < kMaxPasses * kBuckets; i += blockDim.x) (&h[0][0])[i] = 0;
     for (int i = threadIdx.x; i < kBuckets; i += blockDim.x) as[i] = 0;
     __syncthreads();
@@ -277,7 +373,10 @@ __global__ void k_peel_hist(const uint32_t *__restrict__ round, const uint32_t *
         const uint32_t x = round[v];
         for (int p = 0; p < np; ++p) atomicAdd(&h[p][(x >> (p * kRadixBits)) & (kBuckets - 1)], 1u);
         atomicAdd(&as[(x >> ((np - 1) * kRadixBits)) & (kBuckets - 1)], (unsigned long long)A[v]);
+        width = max(width, A[v]);
     }
+    width = __reduce_max_sync(kFull, width);
+    if ((threadIdx.x & 31) == 0 && width) atomicMax(&ctl->width, width);
     __syncthreads();
     for (int i = threadIdx.x; i < kBuckets; i += blockDim.x) {
         for (int p = 0; p < np; ++p)
@@ -309,10 +408,9 @@ int peel_run(cudaStream_t s, const GraphDev &g, RunBufs &b, PeelBufs &pb, bool &
 {
     const int64_t n = g.n;
     auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
-    const size_t sz_deg = al(4 * (size_t)n), sz_round = al(4 * (size_t)n), sz_list = al(4 * (size_t)n);
-    const size_t sz_key = al(8 * (size_t)n), sz_pc = al(sizeof(PeelCtl));
+    const size_t sz4 = al(4 * (size_t)n), sz8 = al(8 * (size_t)n), sz_pc = al(sizeof(PeelCtl));
     if (!pb_ready) {
-        const size_t total = sz_deg + sz_round + 3 * sz_list + sz_key + sz_pc;
+        const size_t total = 4 * sz4 + 2 * sz8 + sz_pc;
         cudaError_t e = cudaMallocAsync(&pb.mem, total, s);
         if (e != cudaSuccess) {
             err = std::string("peel buffers: ") + cudaGetErrorString(e);
@@ -323,25 +421,30 @@ int peel_run(cudaStream_t s, const GraphDev &g, RunBufs &b, PeelBufs &pb, bool &
         pb_ready = true;
     }
     char *m = (char *)pb.mem;
-    int32_t *deg = (int32_t *)m;
-    uint32_t *round = (uint32_t *)(m + sz_deg);
-    uint32_t *list0 = (uint32_t *)(m + sz_deg + sz_round);
-    uint32_t *list1 = (uint32_t *)(m + sz_deg + sz_round + sz_list);
-    uint32_t *flist = (uint32_t *)(m + sz_deg + sz_round + 2 * sz_list);
-    unsigned long long *keybuf = (unsigned long long *)(m + sz_deg + sz_round + 3 * sz_list);
-    PeelCtl *pc = (PeelCtl *)(m + sz_deg + sz_round + 3 * sz_list + sz_key);
+    uint32_t *kv = (uint32_t *)m;
+    uint32_t *round = (uint32_t *)(m + sz4);
+    uint32_t *list0 = (uint32_t *)(m + 2 * sz4);
+    uint32_t *list1 = (uint32_t *)(m + 3 * sz4);
+    unsigned long long *st = (unsigned long long *)(m + 4 * sz4);
+    unsigned long long *heavy = (unsigned long long *)(m + 4 * sz4 + sz8);
+    PeelCtl *pc = (PeelCtl *)(m + 4 * sz4 + 2 * sz8);
 
     std::call_once(g_peel_once, [] {
         int nb = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_peel, kPeelThreads, 0);
-        g_peel_blocks_per_sm = nb > 0 ? (nb < 4 ? nb : 4) : 1;
+        g_peel_blocks_per_sm = nb > 0 ? 1 : 0;
     });
-    const int grid = sm_count * g_peel_blocks_per_sm;
+    if (g_peel_blocks_per_sm < 1) {
+        err = "the peel kernel cannot be resident";
+        return DSG_ERR_CUDA;
+    }
+    // blocks: one per SM at most, and no more than the vertices and arcs need
+    const int grid = (int)imin64(sm_count, peel_blocks((uint64_t)n, (uint64_t)g.arcs));
     const int igrid = (int)imin64((n + 255) / 256, (int64_t)sm_count * 8);
     int nl = 0;
     for (int t = 1; t <= T; ++t) {
         k_peel_reset_width<<<1, 1, 0, s>>>(b.ctl);
-        k_peel_init<<<igrid, 256, 0, s>>>(g.off, n, deg, round, list0, pc);
+        k_peel_init<<<igrid, 256, 0, s>>>(g.off, b.loads, n, g.arcs, kv, round, list0, pc);
         const int64_t *off = g.off;
         const int32_t *adj = g.adj;
         uint32_t *loads = b.loads, *A = b.A;
@@ -349,9 +452,8 @@ int peel_run(cudaStream_t s, const GraphDev &g, RunBufs &b, PeelBufs &pb, bool &
         int64_t nn = n;
         Control *ctl = b.ctl;
         void *args[] = {(void *)&off, (void *)&adj, (void *)&nn, (void *)&loads, (void *)&A,
-                        (void *)&deg, (void *)&round, (void *)&list0, (void *)&list1,
-                        (void *)&flist, (void *)&keybuf, (void *)&pp, (void *)&qq, (void *)&pc,
-                        (void *)&ctl};
+                        (void *)&kv, (void *)&st, (void *)&round, (void *)&list0, (void *)&list1,
+                        (void *)&heavy, (void *)&pp, (void *)&qq, (void *)&pc, (void *)&ctl};
         cudaError_t e = cudaLaunchCooperativeKernel((void *)k_peel, grid, kPeelThreads, args, 0, s);
         if (e != cudaSuccess) {
             err = std::string("cooperative peel launch: ") + cudaGetErrorString(e);
