@@ -394,11 +394,18 @@ def main():
     launches = sum(v["launches"] for v in st.values())
     value = m * T * args.steps * ws / (ms_total * 1e-3) / 1e9
     es_ms = st["edge_scan"]["ms"] / (args.steps * T)
-    es_bytes = 8 * m + 16 * n           # algorithmic bytes per edge-scan launch (oriented scan)
+    # algorithmic bytes of one edge scan over the symmetric CSR: 8m adjacency
+    # + 8m neighbour-load gathers (4 B each) + 8(n+1) offsets + 4n own loads
+    # + 4n counts A.  The kernel reads the degree-oriented copy (each edge
+    # once), whose own minimum is 8m + 16n.
+    es_bytes = 16 * m + 16 * n + 8
+    es_bytes_oriented = 8 * m + 16 * n
     peak, peak_kind = _peak_hbm()
     achieved = es_bytes / (es_ms * 1e-3) / 1e9
     sort_ms = st["sort"]["ms"] / (args.steps * T)
     sort_bytes = st["sort"]["bytes"] / (args.steps * T)
+    ms_iter = ms_total / (args.steps * T)
+    it_bytes = es_bytes + sort_bytes
 
     # ---- end to end through the C ABI with host buffers
     off_h = torch.empty(off.numel(), dtype=torch.int64, pin_memory=True)
@@ -458,7 +465,12 @@ def main():
                          "frac": achieved / peak, "peak_kind": peak_kind,
                          "kernel": "k_edge_scan", "ms_per_launch": es_ms,
                          "algorithmic_bytes_per_launch": es_bytes,
+                         "oriented_min_bytes_per_launch": es_bytes_oriented,
                          "traffic": _traffic("k_edge_scan", workload)},
+            "iteration_roofline": {"bytes": it_bytes, "achieved": it_bytes / (ms_iter * 1e-3) / 1e9,
+                                   "peak": peak, "unit": "GB/s",
+                                   "frac": it_bytes / (ms_iter * 1e-3) / 1e9 / peak, "ms": ms_iter,
+                                   "model": "16m + 16n edge scan + counted radix-pass bytes"},
             "phases": {"edge_scan_ms": es_ms, "sort_ms": sort_ms,
                        "sort_gbs": sort_bytes / (sort_ms * 1e-3) / 1e9 if sort_ms else None,
                        "other_ms": st["other"]["ms"] / (args.steps * T)},
