@@ -45,7 +45,7 @@ BATCH_T = 32
 BATCH_T_PEEL = 16
 SERVE_POOL = 48        # request graphs of the serving workload
 SERVE_SEED = 5
-SERVE_SLOTS = 4
+SERVE_SLOTS = 8
 UNIT = "GTEPS"
 
 
@@ -264,7 +264,7 @@ def bench_serving(dsg, pool, device, args) -> dict:
     the host."""
     import numpy as np
     from paper_2311_04333_gb300 import serve
-    srv = dsg.dsg_server_create(device, SERVE_SLOTS, 0)
+    srv = dsg.dsg_server_create(device, args.serve_slots, 0)
     try:
         rng = np.random.default_rng(SERVE_SEED)
         burst = []
@@ -283,7 +283,7 @@ def bench_serving(dsg, pool, device, args) -> dict:
                             f"(R-MAT ef 8 / Chung-Lu gamma 2.1 avg degree 16, m {min(ms)}..{max(ms)}), "
                             "T in {8,16,32}, eps in {1/10,1/100}, PaRSorting++ / PaRGreedy++ 50/50, "
                             "host CSR in, loads and best set out",
-                "slots": SERVE_SLOTS, "burst_capacity_req_s": cap, "burst_ok": ok})
+                "slots": args.serve_slots, "burst_capacity_req_s": cap, "burst_ok": ok})
     return res
 
 
@@ -329,6 +329,7 @@ def main():
     ap.add_argument("--batch-steps", type=int, default=3)
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=8.0)
+    ap.add_argument("--serve-slots", type=int, default=SERVE_SLOTS)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

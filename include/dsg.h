@@ -140,6 +140,10 @@ int dsg_graph_info(const dsg_graph *g, int64_t *n, int64_t *m, int64_t *max_degr
  *     loads of T1 + T2 iterations.
  * Loads are kept as 32-bit unsigned integers on the device:
  * DSG_ERR_OVERFLOW if max(init_loads) + T * max_degree >= 2^32.
+ * On the whole-GPU path DSG_PEELING is one cooperative launch with up to one
+ * block per SM whose blocks wait on one another: do not overlap two such runs
+ * on one GPU from different streams (the server of dsg_server_create shares
+ * the GPU between its slots safely).
  * Synchronises the context stream before returning. */
 int dsg_run(dsg_graph *g, int variant, int32_t T, int64_t eps_num, int64_t eps_den,
             const int64_t *init_loads, dsg_result *out);

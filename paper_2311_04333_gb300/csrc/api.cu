@@ -31,7 +31,12 @@ struct dsg_ctx {
     std::vector<Pending> pending;
     int32_t *err_flags = nullptr;    // device scratch for validation
     unsigned long long *red = nullptr;  // device scratch for reductions
+    int peel_max_blocks = 0;         // cap on the PaRGreedy++ grid (0: one block per SM)
 };
+
+namespace dsg {
+void ctx_set_peel_max_blocks(dsg_ctx *ctx, int blocks) { ctx->peel_max_blocks = blocks; }
+}  // namespace dsg
 
 struct dsg_graph {
     dsg_ctx *ctx = nullptr;
@@ -648,7 +653,8 @@ int dsg_run(dsg_graph *G, int variant, int32_t T, int64_t eps_num, int64_t eps_d
     } else {
         PhaseTimer pt(ctx, DSG_PHASE_OTHER);
         int nl = 0;
-        rc = peel_run(ctx->stream, G->g, b, G->pb, G->pb_ready, ctx->sm_count, T, eps_num, eps_den, &nl,
+        const int peel_blocks = ctx->peel_max_blocks > 0 ? ctx->peel_max_blocks : ctx->sm_count;
+        rc = peel_run(ctx->stream, G->g, b, G->pb, G->pb_ready, ctx->sm_count, peel_blocks, T, eps_num, eps_den, &nl,
                       ctx->err);
         ctx->launches[DSG_PHASE_OTHER] += nl;
         if (rc) return rc;

@@ -49,7 +49,7 @@ struct PeelCtl {
     unsigned long long heavy[2];// heavy F vertices (bits 33..63) and their chunks (bits 0..32)
     uint32_t n_next[2];         // alive-list sizes, by round parity
     uint32_t rounds;
-    uint32_t bar_count, bar_gen;
+    uint32_t bar_count;         // barrier arrivals this iteration
     uint32_t abort;
     unsigned long long work;    // sum over rounds of the alive-list size
     unsigned long long arcs_alive;  // arcs of the alive vertices
@@ -77,38 +77,32 @@ __device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long
     return v;
 }
 
-// bounded barrier over the first `nb` blocks (co-resident: cooperative
-// launch); a single block needs only its own barrier
-__device__ __forceinline__ bool grid_barrier(PeelCtl *pc, Control *ctl, uint32_t nb)
+// Bounded barrier over the first `nb` blocks (co-resident: cooperative
+// launch).  The arrival counter only grows during an iteration: every block
+// adds nb to its own running target before each barrier, arrives, and waits
+// until the counter reaches the target.  A single block needs only its own
+// barrier.
+__device__ __forceinline__ bool grid_barrier(PeelCtl *pc, Control *ctl, uint32_t nb, uint32_t &target)
 {
     __shared__ int s_ok;
-    if (nb == 1) {
-        __syncthreads();
-        return true;
-    }
     __syncthreads();
+    if (nb == 1) return true;
+    target += nb;
     if (threadIdx.x == 0) {
         int ok = 1;
-        const uint32_t gen = ld_acquire_u32(&pc->bar_gen);
         __threadfence();
-        if (atomicAdd(&pc->bar_count, 1u) == nb - 1) {
-            pc->bar_count = 0;
-            __threadfence();
-            atomicAdd(&pc->bar_gen, 1u);
-        } else {
-            uint32_t polls = 0;
-            while (ld_acquire_u32(&pc->bar_gen) == gen) {
-                if (++polls > kSpinLimit || ((polls & 255) == 0 && ld_acquire_u32(&pc->abort))) {
-                    atomicExch(&pc->abort, 1u);
-                    set_error(ctl, DSG_ERR_TIMEOUT, 400);
-                    ok = 0;
-                    break;
-                }
-                if (polls > 64) __nanosleep(64);
+        atomicAdd(&pc->bar_count, 1u);
+        uint32_t polls = 0;
+        while (ld_acquire_u32(&pc->bar_count) < target) {
+            if (++polls > kSpinLimit || ((polls & 255) == 0 && ld_acquire_u32(&pc->abort))) {
+                atomicExch(&pc->abort, 1u);
+                set_error(ctl, DSG_ERR_TIMEOUT, 400);
+                ok = 0;
+                break;
             }
+            if (polls > 64) __nanosleep(32);
         }
-        __threadfence();
-        if (ld_acquire_u32(&pc->abort)) ok = 0;
+        if (ok && ld_acquire_u32(&pc->abort)) ok = 0;
         s_ok = ok;
     }
     __syncthreads();
@@ -225,6 +219,7 @@ k_peel(const int64_t *__restrict__ off, const int32_t *__restrict__ adj, int64_t
     constexpr int NW = kPeelThreads / 32;
     uint32_t r = 0;
     uint32_t P = gridDim.x;                 // participating blocks
+    uint32_t bar_target = 0;
     if (tid == 0) {
         S.nq = 0;
         S.nt = 0;
@@ -260,7 +255,7 @@ k_peel(const int64_t *__restrict__ off, const int32_t *__restrict__ adj, int64_t
             for (int i = 0; i < NW; ++i) b = min(b, S.red[i]);
             if (b != ~0ull) atomicMin(&pc->mn[r & 1], b);
         }
-        if (!grid_barrier(pc, ctl, P)) return;
+        if (!grid_barrier(pc, ctl, P, bar_target)) return;
         // ---- BC: split off F; its low-degree vertices are counted here
         const unsigned long long thr = pc->mn[r & 1] * (p + q);
         for (uint32_t i0 = blockIdx.x * kPeelThreads; i0 < na; i0 += stride) {
@@ -305,7 +300,7 @@ k_peel(const int64_t *__restrict__ off, const int32_t *__restrict__ adj, int64_t
                 drain_queue(S, off, adj, r, thr, q, st, kv, loads, A);
         }
         drain_queue(S, off, adj, r, thr, q, st, kv, loads, A);
-        if (!grid_barrier(pc, ctl, P)) return;
+        if (!grid_barrier(pc, ctl, P, bar_target)) return;
         // ---- H: chunks of the heavier F vertices, over all blocks
         const unsigned long long hp = ld_acquire_u64(&pc->heavy[r & 1]);
         const uint32_t nh = (uint32_t)(hp >> kHeavyShift);
@@ -329,7 +324,7 @@ k_peel(const int64_t *__restrict__ off, const int32_t *__restrict__ adj, int64_t
                     atomicAdd(&loads[v], c);
                 }
             }
-            if (!grid_barrier(pc, ctl, P)) return;
+            if (!grid_barrier(pc, ctl, P, bar_target)) return;
         }
     }
     if (blockIdx.x == 0 && tid == 0) pc->rounds = r;
@@ -404,7 +399,7 @@ static int g_peel_blocks_per_sm = -1;
 static std::once_flag g_peel_once;
 
 int peel_run(cudaStream_t s, const GraphDev &g, RunBufs &b, PeelBufs &pb, bool &pb_ready,
-             int sm_count, int T, int64_t p, int64_t q, int *launches, std::string &err)
+             int sm_count, int max_blocks, int T, int64_t p, int64_t q, int *launches, std::string &err)
 {
     const int64_t n = g.n;
     auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
@@ -438,8 +433,9 @@ int peel_run(cudaStream_t s, const GraphDev &g, RunBufs &b, PeelBufs &pb, bool &
         err = "the peel kernel cannot be resident";
         return DSG_ERR_CUDA;
     }
-    // blocks: one per SM at most, and no more than the vertices and arcs need
-    const int grid = (int)imin64(sm_count, peel_blocks((uint64_t)n, (uint64_t)g.arcs));
+    // blocks: at most max_blocks (one per SM at most), and no more than the
+    // vertices and arcs need
+    const int grid = (int)imin64(imin64(sm_count, max_blocks), peel_blocks((uint64_t)n, (uint64_t)g.arcs));
     const int igrid = (int)imin64((n + 255) / 256, (int64_t)sm_count * 8);
     int nl = 0;
     for (int t = 1; t <= T; ++t) {

@@ -3,6 +3,8 @@
 #include <string>
 #include "internal.h"
 
+struct dsg_ctx;
+
 namespace dsg {
 
 struct PeelBufs {
@@ -12,10 +14,16 @@ struct PeelBufs {
 
 void peel_free(PeelBufs &pb, cudaStream_t s);
 
+// Caps the PaRGreedy++ grid of runs on ctx (0: one block per SM).  Grids
+// whose sizes add up to at most the SM count are co-resident together: each
+// peel block needs an SM of its own, and nothing else waits on them.
+void ctx_set_peel_max_blocks(dsg_ctx *ctx, int blocks);
+
 // Runs T PaRGreedy++ iterations on g with eps = p/q, leaving the same state
-// as the sorting path (loads, best in ctl, best_loads snapshot, trace).
+// as the sorting path (loads, best in ctl, best_loads snapshot, trace).  The
+// cooperative peel uses at most max_blocks blocks (and one per SM at most).
 // Returns a dsg_status; *launches counts kernel launches.
 int peel_run(cudaStream_t s, const GraphDev &g, RunBufs &b, PeelBufs &pb, bool &pb_ready,
-             int sm_count, int T, int64_t p, int64_t q, int *launches, std::string &err);
+             int sm_count, int max_blocks, int T, int64_t p, int64_t q, int *launches, std::string &err);
 
 }  // namespace dsg

@@ -10,14 +10,16 @@
 // up, and the work of different slots overlaps on the device.  Every request
 // runs exactly the computation dsg_run performs on it alone.
 //
-// PaRGreedy++ runs as one cooperative launch whose blocks meet at grid-wide
-// barriers sized for the whole GPU; two such launches from different slots
-// must not compete for residency, so the server runs at most one such
-// request at a time.  Compact graphs run as one thread block without
-// grid-wide barriers and overlap freely, as do PaRSorting++ requests.
+// PaRGreedy++ on a large graph is one cooperative launch whose blocks meet
+// at grid-wide barriers; each such block needs an SM of its own.  Each slot
+// caps that grid at (SM count / slots) blocks, so the grids of all slots fit
+// the GPU together and their barriers never wait on one another's residency.
+// The rounds are latency-bound, so the cap costs little per request and the
+// slots' peels overlap.
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
+#include <algorithm>
 #include <deque>
 #include <mutex>
 #include <string>
@@ -27,6 +29,7 @@
 
 #include "dsg.h"
 #include "internal.h"
+#include "peeling.h"
 
 namespace {
 
@@ -71,7 +74,7 @@ struct dsg_server {
     uint64_t next_id = 1;
     bool stop = false;
     int64_t n_queued = 0, n_running = 0, n_done = 0;
-    std::mutex mu, coop_mu;
+    std::mutex mu;
     std::condition_variable cv_work, cv_done;
     std::deque<Request *> queue;
     std::unordered_map<uint64_t, Request *> reqs;
@@ -93,12 +96,7 @@ void run_request(dsg_server *s, dsg_ctx *ctx, Request *r)
         r->res.loads = r->loads.data();
         r->res.best_set = r->set.data();
         r->res.trace = nullptr;
-        if (r->variant == DSG_PEELING && !dsg::is_compact(r->n, 2 * r->m)) {
-            std::lock_guard<std::mutex> lk(s->coop_mu);
-            rc = dsg_run(g, r->variant, r->T, r->p, r->q, nullptr, &r->res);
-        } else {
-            rc = dsg_run(g, r->variant, r->T, r->p, r->q, nullptr, &r->res);
-        }
+        rc = dsg_run(g, r->variant, r->T, r->p, r->q, nullptr, &r->res);
         dsg_free_graph(g);
     }
     r->status = rc;
@@ -158,6 +156,11 @@ int dsg_server_create(int device, int32_t slots, int64_t hbm_budget_bytes, dsg_s
     if (!s) return DSG_ERR_NOMEM;
     s->device = device;
     s->budget = hbm_budget_bytes ? hbm_budget_bytes : (int64_t)(free_b / 2);
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || sms < 1) {
+        delete s;
+        return DSG_ERR_CUDA;
+    }
     for (int i = 0; i < slots; ++i) {
         cudaStream_t st;
         dsg_ctx *c = nullptr;
@@ -171,6 +174,7 @@ int dsg_server_create(int device, int32_t slots, int64_t hbm_budget_bytes, dsg_s
             dsg_server_destroy(s);
             return rc;
         }
+        dsg::ctx_set_peel_max_blocks(c, std::max(1, sms / slots));
         s->streams.push_back(st);
         s->ctxs.push_back(c);
     }
