@@ -257,6 +257,38 @@ def bench_batch_peeling(dsg, ctx, graphs, args) -> dict:
             "identical_results_on_sample": same}
 
 
+def bench_rmat20(dsg, ctx, gg, stream, args) -> dict:
+    """The R-MAT scale-20 workload (edge factor 16, seed 2) with both
+    variants, T = 20, eps = 1/10 for PaRGreedy++: GTEPS per iteration with the
+    graph resident (whole-GPU path)."""
+    import torch
+    n, off, adj = gg.rmat_cuda(20, 16, 2)
+    g = dsg.dsg_upload_csr(ctx, n, off, adj, dsg.DSG_SRC_DEVICE)
+    _, m, _ = dsg.dsg_graph_info(g)
+    T = 20
+    loads = torch.empty(n, dtype=torch.int64, device="cuda")
+    bset = torch.empty(n, dtype=torch.int32, device="cuda")
+    out = {"workload": f"rmat20_ef16_seed2, n={n}, m={m}, T={T}"}
+    try:
+        for name, variant, p, q in (("sorting", dsg.DSG_SORTING, 0, 1), ("peeling_eps_1_10", dsg.DSG_PEELING, 1, 10)):
+            for _ in range(2):
+                dsg.dsg_run(ctx, g, variant, T, p, q, None, loads, bset, None, dsg.DSG_PATH_GRID)
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            steps = max(1, args.steps)
+            torch.cuda.synchronize()
+            ev0.record(stream)
+            for _ in range(steps):
+                r = dsg.dsg_run(ctx, g, variant, T, p, q, None, loads, bset, None, dsg.DSG_PATH_GRID)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            ms_it = ev0.elapsed_time(ev1) / (steps * T)
+            out[name] = {"gteps": m / (ms_it * 1e-3) / 1e9, "ms_per_iteration": ms_it,
+                         "best": [r["best_edges"], r["best_vertices"], r["best_iter"]]}
+    finally:
+        dsg.dsg_free_graph(g)
+    return out
+
+
 def bench_serving(dsg, pool, device, args) -> dict:
     """The native request loop under Poisson arrivals: capacity from a
     closed burst of the whole request pool, then an open-loop run at 70% of
@@ -444,6 +476,9 @@ def main():
     if not args.no_batch:
         batched = bench_batch(dsg, ctx, graphs_batch, args)
 
+    # ---- R-MAT scale 20: both variants
+    rmat20 = bench_rmat20(dsg, ctx, gg, stream, args)
+
     # ---- serving: Poisson arrivals through the native request loop
     serving = None
     if not args.no_serve:
@@ -481,6 +516,7 @@ def main():
             "gpu_launches": launches,
             "clocks": clk.summary(),
             "batched": batched,
+            "rmat20": rmat20,
             "serving": serving,
         }
         print(json.dumps(out))

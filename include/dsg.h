@@ -103,7 +103,10 @@ typedef struct {
  * be used and DSG_ERR_INVALID if the library was not built for it. */
 int dsg_create(int device, void *cuda_stream, dsg_ctx **out);
 
-/* Release a context.  Graphs and batches created on it must be freed first. */
+/* Release a context.  Graphs and batches created on it must be freed first.
+ * Device memory comes from the device's default stream-ordered pool, which
+ * the library sets to keep freed blocks cached for reuse; this call returns
+ * the unused cached memory to the driver. */
 void dsg_destroy(dsg_ctx *ctx);
 
 /* Text of the last error on `ctx` ("" if none).  Valid until the next call

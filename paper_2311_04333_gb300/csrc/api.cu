@@ -32,6 +32,7 @@ struct dsg_ctx {
     int32_t *err_flags = nullptr;    // device scratch for validation
     unsigned long long *red = nullptr;  // device scratch for reductions
     int peel_max_blocks = 0;         // cap on the PaRGreedy++ grid (0: one block per SM)
+    cudaStream_t cap = nullptr;      // private stream that CUDA graphs are captured on
 };
 
 namespace dsg {
@@ -366,6 +367,16 @@ int dsg_create(int device, void *cuda_stream, dsg_ctx **out)
     ctx->device = device;
     ctx->stream = (cudaStream_t)cuda_stream;
     ctx->sm_count = prop.multiProcessorCount;
+    // Device memory is allocated stream-ordered from the device's default
+    // pool.  Keep what is freed cached in the pool instead of returning it
+    // to the driver at every synchronisation, so that uploading and freeing
+    // graphs of tens of GB does not map and unmap physical memory each time
+    // (dsg_destroy trims the pool).
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+        uint64_t keep = ~0ull;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
     if (cudaMalloc((void **)&ctx->err_flags, 64) != cudaSuccess ||
         cudaMalloc((void **)&ctx->red, 64) != cudaSuccess) {
         cudaFree(ctx->err_flags);
@@ -384,6 +395,9 @@ void dsg_destroy(dsg_ctx *ctx)
     for (auto e : ctx->ev) cudaEventDestroy(e);
     cudaFree(ctx->err_flags);
     cudaFree(ctx->red);
+    if (ctx->cap) cudaStreamDestroy(ctx->cap);
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, ctx->device) == cudaSuccess) cudaMemPoolTrimTo(pool, 0);
     delete ctx;
 }
 
@@ -622,33 +636,58 @@ int dsg_run(dsg_graph *G, int variant, int32_t T, int64_t eps_num, int64_t eps_d
     }
     if (variant == DSG_SORTING) {
         const int es_grid = ctx->sm_count * edge_scan_sm_count();   // also sets the kernel attributes
-        for (int t = 1; t <= T; ++t) {
-            {
-                PhaseTimer pt(ctx, DSG_PHASE_OTHER);
-                CK(launch_plan(G->g, b, t, s), "plan");
-                k_log_npass<<<1, 1, 0, s>>>(b.ctl, G->npass_log, t);
+        radix_prepare();
+        auto iterations = [&](cudaStream_t ss) -> cudaError_t {
+            cudaError_t e = cudaSuccess;
+            for (int t = 1; t <= T && e == cudaSuccess; ++t) {
+                {
+                    PhaseTimer pt(ctx, DSG_PHASE_OTHER);
+                    e = launch_plan(G->g, b, t, ss);
+                    k_log_npass<<<1, 1, 0, ss>>>(b.ctl, G->npass_log, t);
+                }
+                if (e == cudaSuccess) {
+                    PhaseTimer pt(ctx, DSG_PHASE_EDGE_SCAN);
+                    e = launch_edge_scan(G->g, b, es_grid, ss);
+                }
+                if (e == cudaSuccess) {
+                    PhaseTimer pt(ctx, DSG_PHASE_SORT);
+                    e = launch_asum_single_pass(G->g, b, ss);
+                    for (int k = 0; k < kMaxPasses && e == cudaSuccess; ++k)
+                        e = launch_radix_pass(G->g, b, k, t, ss, nullptr, true, true);
+                }
+                if (e == cudaSuccess) {
+                    PhaseTimer pt(ctx, DSG_PHASE_OTHER);
+                    e = launch_snapshot(G->g, b, ss);
+                }
+                // the equal-loads edge scan is one of the two launches (one exits at once)
+                ctx->launches[DSG_PHASE_OTHER] += 3;
+                ctx->launches[DSG_PHASE_EDGE_SCAN] += 2;
+                ctx->launches[DSG_PHASE_SORT] += kMaxPasses + 1;
+                // oriented arcs (4m) + one target load per arc (4m) + oriented
+                // offsets (8n) + own loads (4n) + A (4n)
+                ctx->bytes[DSG_PHASE_EDGE_SCAN] += 8 * m + 16 * n;
             }
-            {
-                PhaseTimer pt(ctx, DSG_PHASE_EDGE_SCAN);
-                CK(launch_edge_scan(G->g, b, es_grid, s), "edge scan");
-            }
-            ctx->launches[DSG_PHASE_EDGE_SCAN] += 1;   // the equal-loads variant (one of the two exits at once)
-            {
-                PhaseTimer pt(ctx, DSG_PHASE_SORT);
-                CK(launch_asum_single_pass(G->g, b, s), "digit sums");
-                for (int k = 0; k < kMaxPasses; ++k)
-                    CK(launch_radix_pass(G->g, b, k, t, s, nullptr, true, true), "radix pass");
-            }
-            {
-                PhaseTimer pt(ctx, DSG_PHASE_OTHER);
-                CK(launch_snapshot(G->g, b, s), "snapshot");
-            }
-            ctx->launches[DSG_PHASE_OTHER] += 3;
-            ctx->launches[DSG_PHASE_EDGE_SCAN] += 1;
-            ctx->launches[DSG_PHASE_SORT] += kMaxPasses + 1;
-            // oriented arcs (4m) + one target load per arc (4m) + oriented
-            // offsets (8n) + own loads (4n) + A (4n)
-            ctx->bytes[DSG_PHASE_EDGE_SCAN] += 8 * m + 16 * n;
+            return e;
+        };
+        // Below kGraphArcs the iteration's dozen launches cost more than
+        // their work: the T iterations are captured once into a CUDA graph
+        // (on a private stream, so any context stream works) and launched as
+        // one on the context stream.
+        if (!ctx->profiling && G->g.arcs <= kGraphArcs) {
+            if (!ctx->cap) CK(cudaStreamCreateWithFlags(&ctx->cap, cudaStreamNonBlocking), "capture stream");
+            cudaGraph_t cg = nullptr;
+            cudaGraphExec_t ge = nullptr;
+            CK(cudaStreamBeginCapture(ctx->cap, cudaStreamCaptureModeThreadLocal), "begin capture");
+            cudaError_t e = iterations(ctx->cap);
+            const cudaError_t ec = cudaStreamEndCapture(ctx->cap, &cg);
+            if (e == cudaSuccess) e = ec;
+            if (e == cudaSuccess) e = cudaGraphInstantiate(&ge, cg, 0);
+            if (e == cudaSuccess) e = cudaGraphLaunch(ge, s);
+            if (ge) cudaGraphExecDestroy(ge);     // freed once the launch completes
+            if (cg) cudaGraphDestroy(cg);
+            CK(e, "iterations (graph)");
+        } else {
+            CK(iterations(s), "iterations");
         }
     } else {
         PhaseTimer pt(ctx, DSG_PHASE_OTHER);

@@ -148,6 +148,8 @@ constexpr int64_t kCompactArcs = 1 << 20;
 constexpr int64_t kBlockSortN = 1 << 12;
 constexpr int64_t kBlockSortArcs = 1 << 17;
 inline bool is_compact(int64_t n, int64_t arcs) { return n <= kCompactN && arcs <= kCompactArcs; }
+// whole-GPU PaRSorting++ runs up to this many arcs are launched as one CUDA graph
+constexpr int64_t kGraphArcs = 1ll << 26;
 inline bool block_path_default(int variant, int64_t n, int64_t arcs)
 {
     return variant == 1 ? is_compact(n, arcs) : (n <= kBlockSortN && arcs <= kBlockSortArcs);
@@ -168,6 +170,8 @@ cudaError_t launch_edge_scan(const GraphDev &g, RunBufs &b, int grid, cudaStream
 // loads) and, if update_loads, writes loads += A.
 // accumulate: pass 0 also reduces the width (max A) and, when it is not the
 // last pass, the per-digit sums of A for the last pass.
+// one-time kernel attributes of the radix pass (call before any capture)
+void radix_prepare();
 cudaError_t launch_radix_pass(const GraphDev &g, RunBufs &b, int k, int t, cudaStream_t s,
                               const uint32_t *key0 = nullptr, bool update_loads = true,
                               bool accumulate = false);

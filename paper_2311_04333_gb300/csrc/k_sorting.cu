@@ -851,13 +851,18 @@ k_radix_pass(const uint32_t *kin, const uint32_t *vin,
 
 static std::once_flag g_pass_once;
 
-cudaError_t launch_radix_pass(const GraphDev &g, RunBufs &b, int k, int t, cudaStream_t s,
-                              const uint32_t *key0, bool update_loads, bool accumulate)
+void radix_prepare()
 {
     std::call_once(g_pass_once, [] {
         cudaFuncSetAttribute(k_radix_pass, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)sizeof(PassSmem));
     });
+}
+
+cudaError_t launch_radix_pass(const GraphDev &g, RunBufs &b, int k, int t, cudaStream_t s,
+                              const uint32_t *key0, bool update_loads, bool accumulate)
+{
+    radix_prepare();
     // pass k reads: k == 0 -> (loads, A) by id; else buffer (k-1)&1; writes buffer k&1
     const uint32_t *kin = k == 0 ? (key0 ? key0 : b.loads) : b.keys[(k - 1) & 1];
     const uint32_t *vin = k == 0 ? b.A : b.vals[(k - 1) & 1];
