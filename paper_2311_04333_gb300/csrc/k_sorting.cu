@@ -547,7 +547,7 @@ __device__ __forceinline__ unsigned long long status_word(uint32_t epoch, uint64
 }
 
 // One LSD pass (digit k of key - lmin) over (key, value) pairs, stable.
-// Each tile of kPassTile elements: load, rank within warps by ballots,
+// Each tile of kPassTile elements: load, rank within warps by match.any,
 // publish its per-digit counts (and, in the last pass, value sums) at once,
 // sort locally in shared memory, then resolve its global offsets by
 // decoupled look-back.  Non-last passes scatter; the last pass evaluates the
@@ -597,7 +597,7 @@ k_radix_pass(const uint32_t *kin, const uint32_t *vin,
         if (last) S.aoff[tid] = block_excl_sum_u64(ctl->asum[tid], S.red, &tot);
     }
 
-    // ---- warp-level stable ranks (bit-sliced match of the digit)
+    // ---- warp-level stable ranks (lanes of equal digit)
     uint32_t lmn = 0xffffffffu, lmx = 0;
     const bool acc = accumulate && k == 0;
     const int shift_last = ctl->shift[np - 1];
@@ -629,12 +629,8 @@ k_radix_pass(const uint32_t *kin, const uint32_t *vin,
             }
         }
         const uint32_t d = ((key - lmin) >> shift) & (kBuckets - 1);
-        uint32_t peers = __ballot_sync(kFull, valid);
-        #pragma unroll
-        for (int bit = 0; bit < kRadixBits; ++bit) {
-            const uint32_t bb = __ballot_sync(kFull, (d >> bit) & 1u);
-            peers &= ((d >> bit) & 1u) ? bb : ~bb;
-        }
+        // lanes with the same digit (invalid lanes match only themselves)
+        uint32_t peers = __match_any_sync(kFull, valid ? d : (uint32_t)kBuckets + lane);
         if (!valid) peers = 0;
         const uint32_t rank = __popc(peers & lanemask_lt());
         const bool leader = valid && (peers >> lane) == 1u;
