@@ -580,14 +580,18 @@ k_radix_pass(const uint32_t *kin, const uint32_t *vin,
     const uint32_t tile = S.tile;
     const int64_t tbase = (int64_t)tile * kPassTile;
 
-    // ---- load 16 rounds of 32 consecutive items per warp (all loads first)
+    // ---- load 16 rounds of 32 consecutive items per warp (all loads first);
+    // indices inside the warp's segment are 32-bit
     uint32_t key_r[kPassIpt], val_r[kPassIpt], dw_r[kPassIpt];
     const int64_t wbase = tbase + warp * (32 * kPassIpt);
+    const int wrem = (int)imax64(0, imin64(n - wbase, (int64_t)(32 * kPassIpt)));   // valid items of the segment
+    const uint32_t *kin_w = kin + wbase;
+    const uint32_t *vin_w = vin + wbase;
     #pragma unroll
     for (int r = 0; r < kPassIpt; ++r) {
-        const int64_t idx = wbase + r * 32 + lane;
-        key_r[r] = idx < n ? kin[idx] : 0u;
-        val_r[r] = idx < n ? vin[idx] : 0u;
+        const int li = r * 32 + lane;
+        key_r[r] = li < wrem ? kin_w[li] : 0u;
+        val_r[r] = li < wrem ? vin_w[li] : 0u;
     }
     // global bucket offsets of this pass's digit (overlaps the loads)
     {
@@ -605,13 +609,13 @@ k_radix_pass(const uint32_t *kin, const uint32_t *vin,
     unsigned long long rs = 0;
     #pragma unroll
     for (int r = 0; r < kPassIpt; ++r) {
-        const int64_t idx = wbase + r * 32 + lane;
-        const bool valid = idx < n;
+        const int li = r * 32 + lane;
+        const bool valid = li < wrem;
         const uint32_t key = key_r[r], val = val_r[r];
         if (valid) {
             if (k == 0 && loads_next) {
                 const uint32_t nl = key + val;
-                loads_next[idx] = nl;
+                loads_next[wbase + li] = nl;
                 lmn = min(lmn, nl);
                 lmx = max(lmx, nl);
             }
@@ -691,6 +695,9 @@ k_radix_pass(const uint32_t *kin, const uint32_t *vin,
         const uint64_t ex = block_excl_sum_u64(tcount, S.red, &tot);
         S.toff[d] = (uint32_t)ex;
         if (d == 0) S.toff[kBuckets] = (uint32_t)tot;
+        // per-warp local start of digit d (thread d owns column d)
+        #pragma unroll
+        for (int w = 0; w < kPassThreads / 32; ++w) S.wcnt[w][d] += (uint32_t)ex;
     }
     __syncthreads();
 
@@ -699,7 +706,7 @@ k_radix_pass(const uint32_t *kin, const uint32_t *vin,
     for (int r = 0; r < kPassIpt; ++r) {
         if (dw_r[r] != 0xffffffffu) {
             const uint32_t dd = dw_r[r] & 0xffu, wr = dw_r[r] >> 8;
-            const uint32_t lp = S.toff[dd] + S.wcnt[warp][dd] + wr;
+            const uint32_t lp = S.wcnt[warp][dd] + wr;
             S.keys[pad(lp)] = key_r[r];
             S.vals[pad(lp)] = val_r[r];
         }
@@ -762,7 +769,9 @@ k_radix_pass(const uint32_t *kin, const uint32_t *vin,
                 st_release(st, status_word(epoch, kFlagIncl, excl + tcount));
             }
         }
-        S.gbase[d] = S.boff[d] + (uint32_t)excl;
+        // global position of local position lp of digit d: gbase[d] + lp
+        // (modulo 2^32; positions stay below n < 2^31)
+        S.gbase[d] = S.boff[d] + (uint32_t)excl - S.toff[d];
         if (last) S.gsum[d] = S.aoff[d] + excl_sum;
         if (abort) S.last_block = 0xdeadu;
     }
@@ -778,7 +787,7 @@ k_radix_pass(const uint32_t *kin, const uint32_t *vin,
             if (lp < tn) {
                 const uint32_t key = S.keys[pad(lp)];
                 const uint32_t dd = ((key - lmin) >> shift) & (kBuckets - 1);
-                const uint32_t gp = S.gbase[dd] + (lp - S.toff[dd]);
+                const uint32_t gp = S.gbase[dd] + lp;
                 if (gp < (uint64_t)n) {
                     kout[gp] = key;
                     vout[gp] = S.vals[pad(lp)];
@@ -799,7 +808,7 @@ k_radix_pass(const uint32_t *kin, const uint32_t *vin,
         if (lp < tn) {
             const uint32_t key = S.keys[pad(lp)];
             const uint32_t dd = ((key - lmin) >> shift) & (kBuckets - 1);
-            const int64_t pos = (int64_t)S.gbase[dd] + (lp - S.toff[dd]);
+            const int64_t pos = (int64_t)(uint32_t)(S.gbase[dd] + lp);
             const uint64_t prefix = S.gsum[dd] + (run - S.dscan[dd]);
             Candidate c{(int64_t)((uint64_t)m - prefix), n - pos, pos, (int64_t)key};
             if (cand_better(c, best)) best = c;
