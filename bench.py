@@ -438,7 +438,11 @@ def main():
     sort_ms = st["sort"]["ms"] / (args.steps * T)
     sort_bytes = st["sort"]["bytes"] / (args.steps * T)
     ms_iter = ms_total / (args.steps * T)
-    it_bytes = es_bytes + sort_bytes
+    # per-iteration algorithmic bytes of the whole PaRSorting++ iteration:
+    # 16m + (16P + 40)n with P the radix passes of the iteration (the
+    # counted sort bytes are (16P - 4)n, which gives the mean P)
+    mean_passes = (sort_bytes / n + 4) / 16
+    it_bytes = 16 * m + (16 * mean_passes + 40) * n
 
     # ---- end to end through the C ABI with host buffers
     off_h = torch.empty(off.numel(), dtype=torch.int64, pin_memory=True)
@@ -506,7 +510,7 @@ def main():
             "iteration_roofline": {"bytes": it_bytes, "achieved": it_bytes / (ms_iter * 1e-3) / 1e9,
                                    "peak": peak, "unit": "GB/s",
                                    "frac": it_bytes / (ms_iter * 1e-3) / 1e9 / peak, "ms": ms_iter,
-                                   "model": "16m + 16n edge scan + counted radix-pass bytes"},
+                                   "model": "16m + (16P + 40)n per iteration", "mean_radix_passes": mean_passes},
             "phases": {"edge_scan_ms": es_ms, "sort_ms": sort_ms,
                        "sort_gbs": sort_bytes / (sort_ms * 1e-3) / 1e9 if sort_ms else None,
                        "other_ms": st["other"]["ms"] / (args.steps * T)},
