@@ -62,6 +62,8 @@ def _lib():
         lib.oracle_maxflow_densest.argtypes = [i64, p, p, p, p]
         lib.oracle_coreness.argtypes = [i64, p, p, p]
         lib.oracle_coreness_by_deletion.argtypes = [i64, p, p, p]
+        lib.oracle_run_pruned.argtypes = [i64, p, p, ctypes.c_int, i64, i64, i64, p, p, p, p, p]
+        lib.oracle_core_subgraph.argtypes = [i64, p, p, p, i64, p, p]
         _lib_handle = lib
     return _lib_handle
 
@@ -184,3 +186,45 @@ def coreness_by_deletion(g) -> np.ndarray:
     core = np.zeros(n, dtype=np.int64)
     _lib().oracle_coreness_by_deletion(n, _p(off), _p(adj), _p(core))
     return core
+
+
+@dataclass
+class PrunedResult:
+    loads: np.ndarray
+    best_edges: int
+    best_vertices: int
+    best_iter: int
+    best_set: np.ndarray
+    trace: np.ndarray        # [T, 3]: refine result (edges, vertices), vertices of the G it ran on
+    k_max: int
+    core_vertices: int       # |V| of the ceil(k_max/2)-core
+    core_edges: int
+    final_vertices: int      # |V| of the final G
+    L: tuple                 # final lower bound (numerator, denominator)
+
+
+def run_pruned(g, variant: int = SORTING, T: int = 1, p: int = 0, q: int = 1) -> PrunedResult:
+    """Alg. 1 (Pruning-and-Refining, exact pruning) with `variant` as Refine."""
+    n, off, adj = _csr(g)
+    loads = np.zeros(n, dtype=np.int64)
+    best = np.zeros(5, dtype=np.int64)
+    bset = np.zeros(n, dtype=np.int64)
+    trace = np.zeros((max(T, 1), 3), dtype=np.int64)
+    info = np.zeros(6, dtype=np.int64)
+    rc = _lib().oracle_run_pruned(n, _p(off), _p(adj), variant, T, p, q, _p(loads), _p(best), _p(bset),
+                                  _p(trace), _p(info))
+    if rc != 0:
+        raise ValueError(f"oracle_run_pruned failed with status {rc}")
+    return PrunedResult(loads, int(best[0]), int(best[1]), int(best[2]), bset[: best[3]].copy(), trace[:T].copy(),
+                        int(info[0]), int(info[1]), int(info[2]), int(info[3]), (int(info[4]), int(info[5])))
+
+
+def core_subgraph_size(g, core, k: int) -> tuple:
+    """(|V|, |E|) of the subgraph induced on {v : core[v] >= k}."""
+    n, off, adj = _csr(g)
+    core = np.ascontiguousarray(core, dtype=np.int64)
+    nn = np.zeros(1, dtype=np.int64)
+    mm = np.zeros(1, dtype=np.int64)
+    if _lib().oracle_core_subgraph(n, _p(off), _p(adj), _p(core), k, _p(nn), _p(mm)) != 0:
+        raise ValueError("oracle_core_subgraph failed")
+    return int(nn[0]), int(mm[0])

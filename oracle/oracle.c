@@ -516,3 +516,138 @@ int oracle_coreness_by_deletion(int64_t n, const int64_t *off, const int32_t *ad
     free(in);
     return OR_OK;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Pruning-and-Refining framework (Alg. 1, Sec. 4) with exact pruning.      */
+
+/* getCore (Alg. 1 lines 3 and 10): the subgraph of G induced on the vertices
+ * with in[v] != 0, relabelled in increasing id (lists keep their order).
+ * old_of[local] = original id.                                             */
+static int induced_subgraph(int64_t n, const int64_t *off, const int32_t *adj, const unsigned char *in,
+                            int64_t *nn_out, int64_t **off_out, int32_t **adj_out, int64_t **old_of_out)
+{
+    int64_t *new_id = malloc(sizeof(int64_t) * (size_t)n);
+    if (!new_id) return OR_ERR_NOMEM;
+    int64_t nn = 0;
+    for (int64_t v = 0; v < n; ++v) new_id[v] = in[v] ? nn++ : -1;
+    int64_t *noff = malloc(sizeof(int64_t) * (size_t)(nn + 1));
+    int64_t *old_of = malloc(sizeof(int64_t) * (size_t)(nn > 0 ? nn : 1));
+    if (!noff || !old_of) { free(new_id); free(noff); free(old_of); return OR_ERR_NOMEM; }
+    int64_t arcs = 0;
+    noff[0] = 0;
+    for (int64_t v = 0; v < n; ++v) {
+        if (!in[v]) continue;
+        old_of[new_id[v]] = v;
+        for (int64_t e = off[v]; e < off[v + 1]; ++e) arcs += in[adj[e]] ? 1 : 0;
+        noff[new_id[v] + 1] = arcs;
+    }
+    int32_t *nadj = malloc(sizeof(int32_t) * (size_t)(arcs > 0 ? arcs : 1));
+    if (!nadj) { free(new_id); free(noff); free(old_of); return OR_ERR_NOMEM; }
+    int64_t k = 0;
+    for (int64_t v = 0; v < n; ++v) {
+        if (!in[v]) continue;
+        for (int64_t e = off[v]; e < off[v + 1]; ++e)
+            if (in[adj[e]]) nadj[k++] = (int32_t)new_id[adj[e]];
+    }
+    free(new_id);
+    *nn_out = nn; *off_out = noff; *adj_out = nadj; *old_of_out = old_of;
+    return OR_OK;
+}
+
+/* ceil(a / b) for a >= 0, b > 0 */
+static int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+/* The k-core of G for the given core numbers: the induced subgraph on
+ * {v : core(v) >= k} (exported for the pins of Lemma "core contains S*"). */
+int oracle_core_subgraph(int64_t n, const int64_t *off, const int32_t *adj, const int64_t *core, int64_t k,
+                         int64_t *nn, int64_t *mm)
+{
+    unsigned char *in = malloc((size_t)n);
+    if (!in) return OR_ERR_NOMEM;
+    for (int64_t v = 0; v < n; ++v) in[v] = core[v] >= k;
+    int64_t *o = NULL, *old_of = NULL;
+    int32_t *a = NULL;
+    int rc = induced_subgraph(n, off, adj, in, nn, &o, &a, &old_of);
+    if (rc == OR_OK) *mm = o[*nn] / 2;
+    free(in); free(o); free(a); free(old_of);
+    return rc;
+}
+
+/* Alg. 1: cores <- Coreness(G); L <- ceil(k_max / 2); G <- L-core; S <- G;
+ * then T times: S' <- Refine(G) (one iteration of the refine step
+ * `variant` on the current G, with the loads of its vertices carried over
+ * from the previous iterations); if rho(S') > rho(S): S <- S',
+ * L <- max(L, rho(S)) and G <- ceil(L)-core (of the core numbers of the
+ * input).  L is kept as an exact rational.
+ * Outputs (original ids): loads[n] = the load of each vertex when it left G
+ * (0 if never in the first core; the final loads for the final G);
+ * best = (edges, vertices, iteration of the last improvement (0: the first
+ * core itself), set size, 0); set = S ascending; trace[3 t ..] = (edges,
+ * vertices) of the refine result of iteration t+1 and the vertex count of
+ * the G it ran on; info = (k_max, |V|, |E| of the first core, |V| of the
+ * final G, L as numerator, denominator).                                  */
+int oracle_run_pruned(int64_t n, const int64_t *off, const int32_t *adj, int variant, int64_t T,
+                      int64_t p, int64_t q, int64_t *loads, int64_t *best, int64_t *set, int64_t *trace,
+                      int64_t *info)
+{
+    if (n < 1 || T < 0 || q <= 0 || p < 0 || variant < 0 || variant > 2) return OR_ERR_INVALID;
+    int64_t *core = malloc(sizeof(int64_t) * (size_t)n);
+    unsigned char *in = malloc((size_t)n);
+    if (!core || !in) { free(core); free(in); return OR_ERR_NOMEM; }
+    int rc = oracle_coreness(n, off, adj, core);
+    if (rc != OR_OK) { free(core); free(in); return rc; }
+    int64_t kmax = 0;
+    for (int64_t v = 0; v < n; ++v) if (core[v] > kmax) kmax = core[v];
+    int64_t Ln = ceil_div(kmax, 2), Ld = 1;              /* Alg. 1 line 2 */
+    int64_t level = Ln;
+    for (int64_t v = 0; v < n; ++v) in[v] = core[v] >= level;
+    int64_t cn = 0, *coff = NULL, *old_of = NULL;
+    int32_t *cadj = NULL;
+    rc = induced_subgraph(n, off, adj, in, &cn, &coff, &cadj, &old_of);   /* line 3 */
+    if (rc != OR_OK) { free(core); free(in); return rc; }
+    for (int64_t v = 0; v < n; ++v) loads[v] = 0;
+    int64_t se = coff[cn] / 2, sv = cn, biter = 0, ssize = cn;          /* line 4: S <- G */
+    for (int64_t i = 0; i < cn; ++i) set[i] = old_of[i];
+    if (info) { info[0] = kmax; info[1] = cn; info[2] = coff[cn] / 2; }
+    int64_t *cl = calloc((size_t)(cn > 0 ? cn : 1), sizeof(int64_t));
+    int64_t *nl = malloc(sizeof(int64_t) * (size_t)(cn > 0 ? cn : 1));
+    int64_t *lset = malloc(sizeof(int64_t) * (size_t)(cn > 0 ? cn : 1));
+    int64_t b[5], tr[3];
+    if (!cl || !nl || !lset) { rc = OR_ERR_NOMEM; goto done; }
+    for (int64_t t = 1; t <= T && cn > 0; ++t) {
+        rc = oracle_run(cn, coff, cadj, variant, 1, p, q, cl, nl, b, lset, tr);   /* line 6 */
+        if (rc != OR_OK) goto done;
+        memcpy(cl, nl, sizeof(int64_t) * (size_t)cn);
+        if (trace) { trace[3 * (t - 1)] = b[0]; trace[3 * (t - 1) + 1] = b[1]; trace[3 * (t - 1) + 2] = cn; }
+        if (!density_gt(b[0], b[1], se, sv)) continue;                      /* line 7 */
+        se = b[0]; sv = b[1]; biter = t; ssize = b[3];                       /* line 8 */
+        for (int64_t i = 0; i < ssize; ++i) set[i] = old_of[lset[i]];
+        if (density_gt(se, sv, Ln, Ld)) { Ln = se; Ld = sv; }                /* line 9 */
+        int64_t nlevel = ceil_div(Ln, Ld);
+        if (nlevel <= level) continue;
+        level = nlevel;                                                      /* line 10 */
+        unsigned char *cin = malloc((size_t)cn);
+        if (!cin) { rc = OR_ERR_NOMEM; goto done; }
+        for (int64_t i = 0; i < cn; ++i) {
+            cin[i] = core[old_of[i]] >= level;
+            if (!cin[i]) loads[old_of[i]] = cl[i];       /* frozen when pruned */
+        }
+        int64_t nn = 0, *noff = NULL, *nold = NULL;
+        int32_t *nadj = NULL;
+        rc = induced_subgraph(cn, coff, cadj, cin, &nn, &noff, &nadj, &nold);
+        if (rc != OR_OK) { free(cin); goto done; }
+        for (int64_t i = 0; i < nn; ++i) {              /* carry the loads, compose the id maps */
+            nl[i] = cl[nold[i]];
+            nold[i] = old_of[nold[i]];
+        }
+        memcpy(cl, nl, sizeof(int64_t) * (size_t)(nn > 0 ? nn : 1));
+        free(cin); free(coff); free(cadj); free(old_of);
+        coff = noff; cadj = nadj; old_of = nold; cn = nn;
+    }
+    for (int64_t i = 0; i < cn; ++i) loads[old_of[i]] = cl[i];
+    best[0] = se; best[1] = sv; best[2] = biter; best[3] = ssize; best[4] = 0;
+    if (info) { info[3] = cn; info[4] = Ln; info[5] = Ld; }
+done:
+    free(core); free(in); free(coff); free(cadj); free(old_of); free(cl); free(nl); free(lset);
+    return rc;
+}

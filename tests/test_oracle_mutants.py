@@ -53,3 +53,33 @@ def test_pins_catch_mutant(name, tmp_path):
                         os.path.join(ROOT, "tests", "test_oracle_pins.py")],
                        env=env, cwd=ROOT, capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, f"mutant {name} survived the pins:\n{r.stdout[-2000:]}"
+
+
+# plausible mistakes in the Pruning-and-Refining run (Alg. 1), caught by
+# the pins in test_oracle_pruned.py
+PRUNE_MUTANTS = {
+    "prune_floor_half": ("int64_t Ln = ceil_div(kmax, 2), Ld = 1;", "int64_t Ln = kmax / 2, Ld = 1;"),
+    "prune_no_repruning": ("if (nlevel <= level) continue;", "continue;"),
+    "prune_loads_reset": ("nl[i] = cl[nold[i]];", "nl[i] = 0;"),
+    "prune_L_not_raised": ("if (density_gt(se, sv, Ln, Ld)) { Ln = se; Ld = sv; }", ";"),
+    "prune_nonstrict_improvement": ("if (!density_gt(b[0], b[1], se, sv)) continue;",
+                                    "if (density_gt(se, sv, b[0], b[1])) continue;"),
+    "prune_frozen_loads_dropped": ("if (!cin[i]) loads[old_of[i]] = cl[i];", ";"),
+}
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("name", sorted(PRUNE_MUTANTS))
+def test_pruned_pins_catch_mutant(name, tmp_path):
+    old, new = PRUNE_MUTANTS[name]
+    src = open(SRC).read()
+    assert src.count(old) == 1, f"mutation site for {name} not unique"
+    mut = tmp_path / "oracle_mut.c"
+    mut.write_text(src.replace(old, new))
+    so = tmp_path / "liboracle_mut.so"
+    subprocess.check_call(["gcc", "-O1", "-std=c11", "-shared", "-fPIC", "-o", str(so), str(mut)])
+    env = dict(os.environ, DSG_ORACLE_SO=str(so))
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                        os.path.join(ROOT, "tests", "test_oracle_pruned.py")],
+                       env=env, cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert r.returncode != 0, f"mutant {name} survived the pins:\n{r.stdout[-2000:]}"
