@@ -151,6 +151,42 @@ int dsg_graph_info(const dsg_graph *g, int64_t *n, int64_t *m, int64_t *max_degr
 int dsg_run(dsg_graph *g, int variant, int32_t T, int64_t eps_num, int64_t eps_den,
             const int64_t *init_loads, dsg_result *out);
 
+/* ---- Pruning-and-Refining framework ----------------------------------- */
+
+/* Core numbers (Sec. 2, Definition of core number) of every vertex of g into
+ * core[n] (int32; a device pointer if flags has DSG_DST_DEVICE) and their
+ * maximum k_max (may be NULL).  Computed by the round peel with eps = 0 from
+ * zero loads: each round removes the alive vertices of minimum induced
+ * degree, and a vertex's core number is the largest round minimum up to its
+ * round.  Synchronises the context stream. */
+int dsg_coreness(dsg_graph *g, int32_t *core, int64_t *k_max, uint32_t flags);
+
+/* What the pruning saw (dsg_run_pruned). */
+typedef struct {
+    int64_t k_max;                       /* largest core number of g */
+    int64_t core_vertices, core_edges;   /* the ceil(k_max/2)-core the refining starts on */
+    int64_t final_vertices;              /* vertices of the core it ends on */
+    int64_t L_num, L_den;                /* final density lower bound L = L_num / L_den */
+} dsg_prune_info;
+
+/* Alg. 1 (Sec. 4, "Pruning-and-Refining Framework") with exact pruning and
+ * T iterations of `variant` as the Refine step: core numbers of g (the
+ * eps = 0 round peel); L = ceil(k_max / 2); G <- the L-core, S <- G; then T
+ * times: one refine iteration on G, its vertices' loads carried over; if its
+ * best suffix S' is strictly denser than S: S <- S', L <- max(L, rho(S)),
+ * G <- the ceil(L)-core (by the core numbers of g).  The paper's
+ * PaRSorting++ / PaRGreedy++ are this with DSG_SORTING / DSG_PEELING.
+ * Outputs, in g's ids: best_edges/best_vertices = rho(S), best_iter = the
+ * iteration of the last improvement (0: S is the first core itself),
+ * best_set[best_set_size] = S ascending; loads[n] = each vertex's load when
+ * it left G (0 if never in the first core); trace[3 t ..] = the refine
+ * result of iteration t+1 (edges, vertices) and the vertex count of the G
+ * it ran on.  out->flags: DSG_DST_DEVICE only (loads start at zero; paths
+ * are chosen by size).  info may be NULL.
+ * Errors as dsg_run; DSG_ERR_OVERFLOW if T * max_degree >= 2^32. */
+int dsg_run_pruned(dsg_graph *g, int variant, int32_t T, int64_t eps_num, int64_t eps_den, dsg_result *out,
+                   dsg_prune_info *info);
+
 /* Free an uploaded graph (stream-ordered release of its device memory). */
 void dsg_free_graph(dsg_graph *g);
 

@@ -39,6 +39,11 @@ class dsg_result(ctypes.Structure):
                 ("best_set", ctypes.c_void_p), ("trace", ctypes.c_void_p)]
 
 
+class dsg_prune_info(ctypes.Structure):
+    _fields_ = [("k_max", ctypes.c_int64), ("core_vertices", ctypes.c_int64), ("core_edges", ctypes.c_int64),
+                ("final_vertices", ctypes.c_int64), ("L_num", ctypes.c_int64), ("L_den", ctypes.c_int64)]
+
+
 class dsg_server_result(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("best_iter", ctypes.c_int32),
                 ("best_edges", ctypes.c_int64), ("best_vertices", ctypes.c_int64),
@@ -74,6 +79,8 @@ def _load():
     lib.dsg_run_batch.argtypes = [P, I, P, P, P, I32, ctypes.POINTER(dsg_batch_result)]
     lib.dsg_free_batch.argtypes = [P]
     lib.dsg_free_batch.restype = None
+    lib.dsg_coreness.argtypes = [P, P, ctypes.POINTER(I64), ctypes.c_uint32]
+    lib.dsg_run_pruned.argtypes = [P, I, I32, I64, I64, ctypes.POINTER(dsg_result), ctypes.POINTER(dsg_prune_info)]
     lib.dsg_server_create.argtypes = [I, I32, I64, ctypes.POINTER(P)]
     lib.dsg_server_submit.argtypes = [P, I64, P, P, I, I32, I64, I64, ctypes.POINTER(ctypes.c_uint64)]
     lib.dsg_server_wait.argtypes = [P, ctypes.c_uint64, I64, ctypes.POINTER(dsg_server_result), P, P]
@@ -167,6 +174,40 @@ def dsg_run(ctx, graph, variant: int, T: int, eps_num: int = 0, eps_den: int = 1
     _check(ctx, LIB.dsg_run(graph, variant, T, eps_num, eps_den, pi, ctypes.byref(res)))
     return dict(best_edges=res.best_edges, best_vertices=res.best_vertices,
                 best_iter=res.best_iter, best_set_size=res.best_set_size)
+
+
+def dsg_coreness(ctx, graph, core=None) -> tuple:
+    """Core numbers (int32[n], host or device buffer; allocated on the host
+    when None) and k_max."""
+    if core is None:
+        n = ctypes.c_int64()
+        LIB.dsg_graph_info(graph, ctypes.byref(n), None, None)
+        core = np.zeros(n.value, dtype=np.int32)
+    pc, dc = _ptr(core, np.int32)
+    km = ctypes.c_int64()
+    _check(ctx, LIB.dsg_coreness(graph, pc, ctypes.byref(km), DSG_DST_DEVICE if dc else 0))
+    return core, km.value
+
+
+def dsg_run_pruned(ctx, graph, variant: int, T: int, eps_num: int = 0, eps_den: int = 1, loads=None,
+                   best_set=None, trace=None) -> dict:
+    """Alg. 1 with `variant` as the refine step; outputs as dsg_run plus the
+    pruning info."""
+    res = dsg_result()
+    pl, dl = _ptr(loads, np.int64)
+    ps, ds = _ptr(best_set, np.int32)
+    pt, dt = _ptr(trace, np.int64)
+    dev = {d for p, d in ((pl, dl), (ps, ds), (pt, dt)) if p is not None}
+    if len(dev) > 1:
+        raise ValueError("output buffers must all be host or all device")
+    res.flags = DSG_DST_DEVICE if dev == {True} else 0
+    res.loads, res.best_set, res.trace = pl, ps, pt
+    info = dsg_prune_info()
+    _check(ctx, LIB.dsg_run_pruned(graph, variant, T, eps_num, eps_den, ctypes.byref(res), ctypes.byref(info)))
+    out = dict(best_edges=res.best_edges, best_vertices=res.best_vertices, best_iter=res.best_iter,
+               best_set_size=res.best_set_size)
+    out.update({f: getattr(info, f) for f, _ in dsg_prune_info._fields_})
+    return out
 
 
 def dsg_free_graph(graph) -> None:
@@ -299,5 +340,5 @@ DSG_NOALLOC_MAX_VERTICES = 262144
 EXPORTED = ["dsg_create", "dsg_destroy", "dsg_last_error", "dsg_upload_csr", "dsg_graph_info",
             "dsg_run", "dsg_free_graph", "dsg_set_profiling", "dsg_get_stats",
             "dsg_densest_suffix_noalloc", "dsg_upload_batch", "dsg_batch_info", "dsg_run_batch",
-            "dsg_free_batch", "dsg_server_create", "dsg_server_submit", "dsg_server_wait",
+            "dsg_free_batch", "dsg_coreness", "dsg_run_pruned", "dsg_server_create", "dsg_server_submit", "dsg_server_wait",
             "dsg_server_stats", "dsg_server_destroy"]

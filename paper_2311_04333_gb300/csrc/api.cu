@@ -13,6 +13,7 @@
 #include "dsg.h"
 #include "internal.h"
 #include "peeling.h"
+#include "prune.h"
 
 using namespace dsg;
 
@@ -107,6 +108,12 @@ int cuda_fail(dsg_ctx *c, cudaError_t e, const char *what)
     } while (0)
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// e1/v1 > e2/v2 (v > 0), exact
+bool dens_gt_host(int64_t e1, int64_t v1, int64_t e2, int64_t v2)
+{
+    return (__int128)e1 * (__int128)v2 > (__int128)e2 * (__int128)v1;
+}
 
 cudaEvent_t ev_get(dsg_ctx *c)
 {
@@ -740,6 +747,155 @@ int dsg_run(dsg_graph *G, int variant, int32_t T, int64_t eps_num, int64_t eps_d
     out->best_set_size = h.set_size;
     if (ctx->profiling) collect_timings(ctx);
     return DSG_OK;
+}
+
+int dsg_coreness(dsg_graph *G, int32_t *core, int64_t *k_max, uint32_t flags)
+{
+    if (!G || !core) return DSG_ERR_INVALID;
+    dsg_ctx *ctx = G->ctx;
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    const int64_t n = G->g.n;
+    cudaStream_t s = ctx->stream;
+    int rc = ensure_run_bufs(ctx, G, 1);
+    if (rc) return rc;
+    int32_t *dst = core;
+    if (!(flags & DSG_DST_DEVICE)) CK(cudaMallocAsync((void **)&dst, 4 * (size_t)n, s), "core buffer");
+    int64_t km = 0;
+    rc = coreness_run(s, G->g, G->rb.ctl, ctx->sm_count, dst, &km, ctx->err);
+    if (rc == DSG_OK && !(flags & DSG_DST_DEVICE)) {
+        cudaError_t e = cudaMemcpyAsync(core, dst, 4 * (size_t)n, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) rc = cuda_fail(ctx, e, "core copy");
+    }
+    if (!(flags & DSG_DST_DEVICE)) cudaFreeAsync(dst, s);
+    if (rc == DSG_ERR_TIMEOUT) return fail(ctx, rc, "coreness: a bounded wait gave up");
+    if (rc) return rc;
+    if (k_max) *k_max = km;
+    return DSG_OK;
+}
+
+int dsg_run_pruned(dsg_graph *G, int variant, int32_t T, int64_t eps_num, int64_t eps_den, dsg_result *out,
+                   dsg_prune_info *info)
+{
+    if (!G || !out) return DSG_ERR_INVALID;
+    dsg_ctx *ctx = G->ctx;
+    if (variant != DSG_SORTING && variant != DSG_PEELING)
+        return fail(ctx, DSG_ERR_INVALID, "unknown variant %d", variant);
+    if (T < 1) return fail(ctx, DSG_ERR_INVALID, "T = %d must be >= 1", T);
+    if (eps_den < 1 || eps_num < 0) return fail(ctx, DSG_ERR_INVALID, "eps = %lld/%lld: need p >= 0, q >= 1",
+                                                (long long)eps_num, (long long)eps_den);
+    if (eps_num + eps_den >= ((int64_t)1 << 31)) return fail(ctx, DSG_ERR_OVERFLOW, "p + q must be < 2^31");
+    if (out->flags & (DSG_INIT_DEVICE | DSG_PATH_GRID | DSG_PATH_BLOCK))
+        return fail(ctx, DSG_ERR_INVALID, "dsg_run_pruned starts from zero loads and picks the paths itself");
+    if ((unsigned long long)T * (unsigned long long)G->g.max_degree >= (1ull << 32))
+        return fail(ctx, DSG_ERR_OVERFLOW, "T * max_degree does not fit 32-bit loads");
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    const int64_t n = G->g.n;
+    cudaStream_t s = ctx->stream;
+    const bool dst_dev = out->flags & DSG_DST_DEVICE;
+    int rc = ensure_run_bufs(ctx, G, 1);
+    if (rc) return rc;
+    // buffers: core numbers, all loads (input ids), the best set (input ids),
+    // the refine step's outputs (local ids)
+    char *mem = nullptr;
+    const size_t need = align256(4 * (size_t)n) + align256(8 * (size_t)n) + align256(4 * (size_t)n) +
+                        align256(4 * (size_t)n) + align256(8 * (size_t)n);
+    CK(cudaMallocAsync((void **)&mem, need, s), "pruning buffers");
+    int32_t *core = (int32_t *)mem;
+    int64_t *loads_all = (int64_t *)(mem + align256(4 * (size_t)n));
+    int32_t *sset = (int32_t *)((char *)loads_all + align256(8 * (size_t)n));
+    int32_t *lset = (int32_t *)((char *)sset + align256(4 * (size_t)n));
+    int64_t *nloads = (int64_t *)((char *)lset + align256(4 * (size_t)n));
+    CoreGraph cur;
+    dsg_graph *cg = nullptr;
+    std::vector<int64_t> trace(3 * (size_t)T, 0);
+    auto finish = [&](int code) {
+        if (cg) dsg_free_graph(cg);
+        free_core(cur, s);
+        cudaFreeAsync(mem, s);
+        cudaStreamSynchronize(s);
+        return code;
+    };
+    cudaError_t e;
+    CK(cudaMemsetAsync(loads_all, 0, 8 * (size_t)n, s), "memset");
+    // Alg. 1 lines 1-4: core numbers, L = ceil(k_max / 2), G <- L-core, S <- G
+    int64_t kmax = 0;
+    {
+        PhaseTimer pt(ctx, DSG_PHASE_OTHER);
+        rc = coreness_run(s, G->g, G->rb.ctl, ctx->sm_count, core, &kmax, ctx->err);
+    }
+    if (rc) return finish(rc == DSG_ERR_TIMEOUT ? fail(ctx, rc, "coreness: a bounded wait gave up") : rc);
+    int64_t Ln = (kmax + 1) / 2, Ld = 1, level = Ln;
+    if ((e = extract_core(s, n, G->g.off, G->g.adj, core, nullptr, level, nullptr, nullptr, &cur)) != cudaSuccess)
+        return finish(cuda_fail(ctx, e, "core extraction"));
+    int64_t se = cur.arcs / 2, sv = cur.n, biter = 0, ssize = cur.n;
+    if ((e = cudaMemcpyAsync(sset, cur.old_of, 4 * (size_t)cur.n, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+        return finish(cuda_fail(ctx, e, "set copy"));
+    if (info) {
+        info->k_max = kmax;
+        info->core_vertices = cur.n;
+        info->core_edges = cur.arcs / 2;
+    }
+    if ((rc = dsg_upload_csr(ctx, cur.n, cur.off, cur.adj, DSG_SRC_DEVICE, &cg)) != DSG_OK) return finish(rc);
+    for (int32_t t = 1; t <= T; ++t) {
+        // line 6: one iteration of the refine step on the current core,
+        // continuing its vertices' loads
+        dsg_result r{};
+        r.flags = DSG_DST_DEVICE | DSG_INIT_DEVICE;
+        r.loads = nloads;
+        r.best_set = lset;
+        if ((rc = dsg_run(cg, variant, 1, eps_num, eps_den, cur.loads, &r)) != DSG_OK) return finish(rc);
+        if ((e = cudaMemcpyAsync(cur.loads, nloads, 8 * (size_t)cur.n, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+            return finish(cuda_fail(ctx, e, "loads copy"));
+        trace[3 * (t - 1)] = r.best_edges;
+        trace[3 * (t - 1) + 1] = r.best_vertices;
+        trace[3 * (t - 1) + 2] = cur.n;
+        // lines 7-10: keep a strictly denser result, raise L, re-prune
+        if (!dens_gt_host(r.best_edges, r.best_vertices, se, sv)) continue;
+        se = r.best_edges;
+        sv = r.best_vertices;
+        biter = t;
+        ssize = r.best_set_size;
+        if ((e = gather_ids(lset, ssize, cur.old_of, sset, s)) != cudaSuccess) return finish(cuda_fail(ctx, e, "set"));
+        if (dens_gt_host(se, sv, Ln, Ld)) {
+            Ln = se;
+            Ld = sv;
+        }
+        const int64_t nlevel = (Ln + Ld - 1) / Ld;
+        if (nlevel <= level) continue;
+        level = nlevel;
+        CoreGraph nx;
+        if ((e = extract_core(s, cur.n, cur.off, cur.adj, core, cur.old_of, level, cur.loads, loads_all, &nx)) !=
+            cudaSuccess)
+            return finish(cuda_fail(ctx, e, "core extraction"));
+        free_core(cur, s);
+        cur = nx;
+        dsg_free_graph(cg);
+        cg = nullptr;
+        if ((rc = dsg_upload_csr(ctx, cur.n, cur.off, cur.adj, DSG_SRC_DEVICE, &cg)) != DSG_OK) return finish(rc);
+    }
+    if ((e = scatter_loads(cur.loads, cur.n, cur.old_of, loads_all, s)) != cudaSuccess)
+        return finish(cuda_fail(ctx, e, "loads"));
+    const cudaMemcpyKind k = dst_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (out->loads && (e = cudaMemcpyAsync(out->loads, loads_all, 8 * (size_t)n, k, s)) != cudaSuccess)
+        return finish(cuda_fail(ctx, e, "loads out"));
+    if (out->best_set && ssize > 0 && (e = cudaMemcpyAsync(out->best_set, sset, 4 * (size_t)ssize, k, s)) != cudaSuccess)
+        return finish(cuda_fail(ctx, e, "set out"));
+    if (out->trace &&
+        (e = cudaMemcpyAsync(out->trace, trace.data(), 24 * (size_t)T,
+                             dst_dev ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost, s)) != cudaSuccess)
+        return finish(cuda_fail(ctx, e, "trace out"));
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return finish(cuda_fail(ctx, e, "pruned run"));
+    out->best_edges = se;
+    out->best_vertices = sv;
+    out->best_iter = (int32_t)biter;
+    out->best_set_size = ssize;
+    if (info) {
+        info->final_vertices = cur.n;
+        info->L_num = Ln;
+        info->L_den = Ld;
+    }
+    return finish(DSG_OK);
 }
 
 int dsg_upload_batch(dsg_ctx *ctx, int32_t G, const int64_t *n_per, const int64_t *const *offsets,

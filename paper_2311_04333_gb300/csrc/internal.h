@@ -155,6 +155,11 @@ inline bool block_path_default(int variant, int64_t n, int64_t arcs)
     return variant == 1 ? is_compact(n, arcs) : (n <= kBlockSortN && arcs <= kBlockSortArcs);
 }
 
+// exclusive scan of int64[count] in place (tmp: scan_tmp_count(count)
+// int64 of scratch); *total_dev receives the sum
+int64_t scan_tmp_count(int64_t count);
+cudaError_t scan_exclusive_i64(int64_t *x, int64_t count, int64_t *total_dev, int64_t *tmp, cudaStream_t s);
+
 cudaError_t launch_validate(const GraphDev &g, int full, int32_t *err_flags, cudaStream_t s);
 // err[1..5] of the adjacency alone (as the orientation pass records them)
 cudaError_t launch_validate_adjacency(const GraphDev &g, int full, int32_t *err_flags, cudaStream_t s);

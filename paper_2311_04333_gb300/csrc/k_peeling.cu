@@ -212,7 +212,7 @@ __global__ void __launch_bounds__(kPeelThreads, 1)
 k_peel(const int64_t *__restrict__ off, const int32_t *__restrict__ adj, int64_t n,
        uint32_t *loads, uint32_t *A, uint32_t *kv, unsigned long long *st, uint32_t *round,
        uint32_t *list0, uint32_t *list1, unsigned long long *heavy, uint64_t p, uint64_t q,
-       PeelCtl *pc, Control *ctl)
+       PeelCtl *pc, Control *ctl, uint32_t *round_min)
 {
     __shared__ PeelSmem S;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -256,6 +256,7 @@ k_peel(const int64_t *__restrict__ off, const int32_t *__restrict__ adj, int64_t
             if (b != ~0ull) atomicMin(&pc->mn[r & 1], b);
         }
         if (!grid_barrier(pc, ctl, P, bar_target)) return;
+        if (round_min && blockIdx.x == 0 && tid == 0) round_min[r] = (uint32_t)pc->mn[r & 1];
         // ---- BC: split off F; its low-degree vertices are counted here
         const unsigned long long thr = pc->mn[r & 1] * (p + q);
         for (uint32_t i0 = blockIdx.x * kPeelThreads; i0 < na; i0 += stride) {
@@ -447,9 +448,10 @@ int peel_run(cudaStream_t s, const GraphDev &g, RunBufs &b, PeelBufs &pb, bool &
         uint64_t pp = (uint64_t)p, qq = (uint64_t)q;
         int64_t nn = n;
         Control *ctl = b.ctl;
+        uint32_t *no_rmin = nullptr;
         void *args[] = {(void *)&off, (void *)&adj, (void *)&nn, (void *)&loads, (void *)&A,
                         (void *)&kv, (void *)&st, (void *)&round, (void *)&list0, (void *)&list1,
-                        (void *)&heavy, (void *)&pp, (void *)&qq, (void *)&pc, (void *)&ctl};
+                        (void *)&heavy, (void *)&pp, (void *)&qq, (void *)&pc, (void *)&ctl, (void *)&no_rmin};
         cudaError_t e = cudaLaunchCooperativeKernel((void *)k_peel, grid, kPeelThreads, args, 0, s);
         if (e != cudaSuccess) {
             err = std::string("cooperative peel launch: ") + cudaGetErrorString(e);
@@ -471,6 +473,108 @@ int peel_run(cudaStream_t s, const GraphDev &g, RunBufs &b, PeelBufs &pb, bool &
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
         err = std::string("peel: ") + cudaGetErrorString(e);
+        return DSG_ERR_CUDA;
+    }
+    return DSG_OK;
+}
+
+// ---- coreness (Sec. 2, Definition of core number): the round peel with
+// eps = 0 from zero loads peels, each round, the alive vertices of minimum
+// induced degree; the core number of a vertex is the largest round minimum
+// up to its round.
+
+// inclusive prefix maximum of x[0..R) (single block)
+__global__ void k_prefix_max(uint32_t *x, int64_t R)
+{
+    __shared__ uint32_t part[1024];
+    const int tid = threadIdx.x;
+    const int64_t per = (R + blockDim.x - 1) / blockDim.x;
+    const int64_t b = tid * per, e = imin64(R, b + per);
+    uint32_t mx = 0;
+    for (int64_t i = b; i < e; ++i) mx = max(mx, x[i]);
+    part[tid] = mx;
+    __syncthreads();
+    if (tid == 0)
+        for (int i = 1; i < (int)blockDim.x; ++i) part[i] = max(part[i], part[i - 1]);
+    __syncthreads();
+    uint32_t run = tid ? part[tid - 1] : 0u;
+    for (int64_t i = b; i < e; ++i) {
+        run = max(run, x[i]);
+        x[i] = run;
+    }
+}
+
+__global__ void k_core_assign(const uint32_t *__restrict__ round, const uint32_t *__restrict__ cmax, int64_t n,
+                              int32_t *core)
+{
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+        core[v] = (int32_t)cmax[round[v]];
+}
+
+int coreness_run(cudaStream_t s, const GraphDev &g, Control *ctl, int sm_count, int32_t *core, int64_t *kmax,
+                 std::string &err)
+{
+    const int64_t n = g.n;
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    const size_t sz4 = al(4 * (size_t)n), sz8 = al(8 * (size_t)n), sz_pc = al(sizeof(PeelCtl));
+    const size_t total = 7 * sz4 + 2 * sz8 + sz_pc;
+    void *mem = nullptr;
+    cudaError_t e = cudaMallocAsync(&mem, total, s);
+    if (e != cudaSuccess) {
+        err = std::string("coreness buffers: ") + cudaGetErrorString(e);
+        return e == cudaErrorMemoryAllocation ? DSG_ERR_NOMEM : DSG_ERR_CUDA;
+    }
+    cudaMemsetAsync(mem, 0, total, s);
+    char *m = (char *)mem;
+    uint32_t *kv = (uint32_t *)m, *round = (uint32_t *)(m + sz4), *list0 = (uint32_t *)(m + 2 * sz4);
+    uint32_t *list1 = (uint32_t *)(m + 3 * sz4), *zl = (uint32_t *)(m + 4 * sz4), *A = (uint32_t *)(m + 5 * sz4);
+    uint32_t *rmin = (uint32_t *)(m + 6 * sz4);
+    unsigned long long *st = (unsigned long long *)(m + 7 * sz4);
+    unsigned long long *heavy = (unsigned long long *)(m + 7 * sz4 + sz8);
+    PeelCtl *pc = (PeelCtl *)(m + 7 * sz4 + 2 * sz8);
+    std::call_once(g_peel_once, [] {
+        int nb = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_peel, kPeelThreads, 0);
+        g_peel_blocks_per_sm = nb > 0 ? 1 : 0;
+    });
+    if (g_peel_blocks_per_sm < 1) {
+        cudaFreeAsync(mem, s);
+        err = "the peel kernel cannot be resident";
+        return DSG_ERR_CUDA;
+    }
+    const int grid = (int)imin64(sm_count, peel_blocks((uint64_t)n, (uint64_t)g.arcs));
+    const int igrid = (int)imin64((n + 255) / 256, (int64_t)sm_count * 8);
+    k_peel_init<<<igrid, 256, 0, s>>>(g.off, zl, n, g.arcs, kv, round, list0, pc);
+    const int64_t *off = g.off;
+    const int32_t *adj = g.adj;
+    uint64_t pp = 0, qq = 1;
+    int64_t nn = n;
+    void *args[] = {(void *)&off, (void *)&adj, (void *)&nn, (void *)&zl, (void *)&A, (void *)&kv, (void *)&st,
+                    (void *)&round, (void *)&list0, (void *)&list1, (void *)&heavy, (void *)&pp, (void *)&qq,
+                    (void *)&pc, (void *)&ctl, (void *)&rmin};
+    e = cudaLaunchCooperativeKernel((void *)k_peel, grid, kPeelThreads, args, 0, s);
+    uint32_t rounds = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&rounds, &pc->rounds, 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess && rounds > 0) {
+        k_prefix_max<<<1, 1024, 0, s>>>(rmin, rounds);
+        k_core_assign<<<igrid, 256, 0, s>>>(round, rmin, n, core);
+        uint32_t km = 0;
+        cudaMemcpyAsync(&km, rmin + rounds - 1, 4, cudaMemcpyDeviceToHost, s);
+        e = cudaStreamSynchronize(s);
+        *kmax = km;
+    }
+    int cerr = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&cerr, &ctl->err, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess && cerr) {
+        cudaFreeAsync(mem, s);
+        err = "coreness: a bounded wait gave up";
+        return cerr;
+    }
+    cudaFreeAsync(mem, s);
+    if (e != cudaSuccess) {
+        err = std::string("coreness: ") + cudaGetErrorString(e);
         return DSG_ERR_CUDA;
     }
     return DSG_OK;

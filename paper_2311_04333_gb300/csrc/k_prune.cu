@@ -1,0 +1,159 @@
+// k_prune.cu -- getCore of the Pruning-and-Refining framework (arXiv
+// 2311.04333, Alg. 1 lines 3 and 10): the subgraph induced on the vertices
+// whose core number (in the input graph) reaches a level, relabelled in
+// increasing id so that every list stays in its order, with the maps that
+// carry loads and ids across the relabelling.
+#include "common.cuh"
+#include "prune.h"
+
+namespace dsg {
+namespace {
+
+// pos[v] = 1 if v is kept (pos[n] = 0); scanned into new ids afterwards
+__global__ void k_ext_flags(const int32_t *__restrict__ core, const int32_t *__restrict__ old_of, int64_t n,
+                            int64_t level, int64_t *pos)
+{
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v <= n; v += (int64_t)gridDim.x * blockDim.x) {
+        int64_t k = 0;
+        if (v < n) k = core[old_of ? old_of[v] : (int32_t)v] >= level ? 1 : 0;
+        pos[v] = k;
+    }
+}
+
+__device__ __forceinline__ bool kept(const int64_t *pos, int64_t v) { return pos[v + 1] != pos[v]; }
+
+// warp per vertex: kept neighbours of each kept vertex
+__global__ void k_ext_deg(const int64_t *__restrict__ off, const int32_t *__restrict__ adj, int64_t n,
+                          const int64_t *__restrict__ pos, int64_t *ndeg)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t v = w0; v < n; v += nw) {
+        if (!kept(pos, v)) continue;
+        uint32_t c = 0;
+        for (int64_t j = off[v] + lane; j < off[v + 1]; j += 32) c += kept(pos, adj[j]) ? 1u : 0u;
+        c = __reduce_add_sync(0xffffffffu, c);
+        if (lane == 0) ndeg[pos[v]] = c;
+    }
+}
+
+// warp per vertex: the kept neighbours' new ids, in list order
+__global__ void k_ext_fill(const int64_t *__restrict__ off, const int32_t *__restrict__ adj, int64_t n,
+                           const int64_t *__restrict__ pos, const int64_t *__restrict__ noff, int32_t *nadj)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t v = w0; v < n; v += nw) {
+        if (!kept(pos, v)) continue;
+        int64_t o = noff[pos[v]];
+        for (int64_t j0 = off[v]; j0 < off[v + 1]; j0 += 32) {
+            const int64_t j = j0 + lane;
+            const bool ok = j < off[v + 1];
+            const int32_t w = ok ? adj[j] : 0;
+            const bool k = ok && kept(pos, w);
+            const uint32_t m = __ballot_sync(0xffffffffu, k);
+            if (k) nadj[o + __popc(m & lanemask_lt())] = (int32_t)pos[w];
+            o += __popc(m);
+        }
+    }
+}
+
+// ids and loads across the relabelling; loads of dropped vertices are
+// written to frozen[] at their original ids
+__global__ void k_ext_map(int64_t n, const int64_t *__restrict__ pos, const int32_t *__restrict__ old_of,
+                          const int64_t *__restrict__ loads, int32_t *nold, int64_t *nloads, int64_t *frozen)
+{
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t o = old_of ? old_of[v] : (int32_t)v;
+        const int64_t l = loads ? loads[v] : 0;
+        if (kept(pos, v)) {
+            nold[pos[v]] = o;
+            nloads[pos[v]] = l;
+        } else if (frozen) {
+            frozen[o] = l;
+        }
+    }
+}
+
+__global__ void k_gather_ids(const int32_t *__restrict__ local, int64_t k, const int32_t *__restrict__ old_of,
+                             int32_t *out)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < k; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = old_of[local[i]];
+}
+
+__global__ void k_scatter_loads(const int64_t *__restrict__ loads, int64_t n, const int32_t *__restrict__ old_of,
+                                int64_t *out)
+{
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+        out[old_of[v]] = loads[v];
+}
+
+}  // namespace
+
+cudaError_t extract_core(cudaStream_t s, int64_t n, const int64_t *off, const int32_t *adj, const int32_t *core,
+                         const int32_t *old_of, int64_t level, const int64_t *loads, int64_t *frozen, CoreGraph *out)
+{
+    cudaError_t e;
+    int64_t *pos = nullptr, *tmp = nullptr;
+    const int64_t ntmp = scan_tmp_count(n + 1) + 2;
+    if ((e = cudaMallocAsync((void **)&pos, 8 * (size_t)(n + 1), s)) != cudaSuccess) return e;
+    if ((e = cudaMallocAsync((void **)&tmp, 8 * (size_t)ntmp, s)) != cudaSuccess) return e;
+    int64_t *total = tmp + ntmp - 1;
+    const int grid = (int)imin64((n + 256) / 256, 152 * 16);
+    const int wgrid = (int)imin64((n * 32 + 255) / 256, 152 * 32);
+    k_ext_flags<<<grid, 256, 0, s>>>(core, old_of, n, level, pos);
+    if ((e = scan_exclusive_i64(pos, n + 1, total, tmp, s)) != cudaSuccess) return e;
+    int64_t nn = 0;
+    cudaMemcpyAsync(&nn, total, 8, cudaMemcpyDeviceToHost, s);
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+    int64_t *noff = nullptr, *nloads = nullptr;
+    int32_t *nold = nullptr, *nadj = nullptr;
+    if ((e = cudaMallocAsync((void **)&noff, 8 * (size_t)(nn + 1), s)) != cudaSuccess ||
+        (e = cudaMallocAsync((void **)&nold, 4 * (size_t)imax64(nn, 1), s)) != cudaSuccess ||
+        (e = cudaMallocAsync((void **)&nloads, 8 * (size_t)imax64(nn, 1), s)) != cudaSuccess)
+        return e;
+    cudaMemsetAsync(noff, 0, 8 * (size_t)(nn + 1), s);
+    k_ext_deg<<<wgrid, 256, 0, s>>>(off, adj, n, pos, noff);
+    if ((e = scan_exclusive_i64(noff, nn + 1, total, tmp, s)) != cudaSuccess) return e;
+    int64_t arcs = 0;
+    cudaMemcpyAsync(&arcs, total, 8, cudaMemcpyDeviceToHost, s);
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+    if ((e = cudaMallocAsync((void **)&nadj, 4 * (size_t)imax64(arcs, 1), s)) != cudaSuccess) return e;
+    k_ext_fill<<<wgrid, 256, 0, s>>>(off, adj, n, pos, noff, nadj);
+    k_ext_map<<<grid, 256, 0, s>>>(n, pos, old_of, loads, nold, nloads, frozen);
+    cudaFreeAsync(pos, s);
+    cudaFreeAsync(tmp, s);
+    out->n = nn;
+    out->arcs = arcs;
+    out->off = noff;
+    out->adj = nadj;
+    out->old_of = nold;
+    out->loads = nloads;
+    return cudaGetLastError();
+}
+
+void free_core(CoreGraph &c, cudaStream_t s)
+{
+    if (c.off) cudaFreeAsync(c.off, s);
+    if (c.adj) cudaFreeAsync(c.adj, s);
+    if (c.old_of) cudaFreeAsync(c.old_of, s);
+    if (c.loads) cudaFreeAsync(c.loads, s);
+    c = CoreGraph{};
+}
+
+cudaError_t gather_ids(const int32_t *local, int64_t k, const int32_t *old_of, int32_t *out, cudaStream_t s)
+{
+    if (k > 0) k_gather_ids<<<(int)imin64((k + 255) / 256, 152 * 8), 256, 0, s>>>(local, k, old_of, out);
+    return cudaGetLastError();
+}
+
+cudaError_t scatter_loads(const int64_t *loads, int64_t n, const int32_t *old_of, int64_t *out, cudaStream_t s)
+{
+    if (n > 0) k_scatter_loads<<<(int)imin64((n + 255) / 256, 152 * 8), 256, 0, s>>>(loads, n, old_of, out);
+    return cudaGetLastError();
+}
+
+}  // namespace dsg

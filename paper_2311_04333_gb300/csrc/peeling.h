@@ -19,6 +19,11 @@ void peel_free(PeelBufs &pb, cudaStream_t s);
 // peel block needs an SM of its own, and nothing else waits on them.
 void ctx_set_peel_max_blocks(dsg_ctx *ctx, int blocks);
 
+// Core numbers of g (int32[n]) and their maximum, by the eps = 0 round peel
+// from zero loads; ctl only receives bounded-wait errors.
+int coreness_run(cudaStream_t s, const GraphDev &g, Control *ctl, int sm_count, int32_t *core, int64_t *kmax,
+                 std::string &err);
+
 // Runs T PaRGreedy++ iterations on g with eps = p/q, leaving the same state
 // as the sorting path (loads, best in ctl, best_loads snapshot, trace).  The
 // cooperative peel uses at most max_blocks blocks (and one per SM at most).

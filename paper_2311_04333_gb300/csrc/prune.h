@@ -1,0 +1,30 @@
+// prune.h -- getCore of the Pruning-and-Refining framework (k_prune.cu).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+#include "internal.h"
+
+namespace dsg {
+
+// A core of the input graph in device memory, relabelled: old_of[local] is
+// the input id, loads[local] the carried loads.
+struct CoreGraph {
+    int64_t n = 0, arcs = 0;
+    int64_t *off = nullptr;
+    int32_t *adj = nullptr;
+    int32_t *old_of = nullptr;
+    int64_t *loads = nullptr;
+};
+
+// The subgraph of (n, off, adj) induced on {v : core[old_of[v]] >= level}
+// (old_of NULL: identity), its maps and carried loads (loads NULL: zeros);
+// the loads of the dropped vertices go to frozen[old id] (if not NULL).
+cudaError_t extract_core(cudaStream_t s, int64_t n, const int64_t *off, const int32_t *adj, const int32_t *core,
+                         const int32_t *old_of, int64_t level, const int64_t *loads, int64_t *frozen, CoreGraph *out);
+void free_core(CoreGraph &c, cudaStream_t s);
+// out[i] = old_of[local[i]]
+cudaError_t gather_ids(const int32_t *local, int64_t k, const int32_t *old_of, int32_t *out, cudaStream_t s);
+// out[old_of[v]] = loads[v]
+cudaError_t scatter_loads(const int64_t *loads, int64_t n, const int32_t *old_of, int64_t *out, cudaStream_t s);
+
+}  // namespace dsg
