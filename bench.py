@@ -257,6 +257,24 @@ def bench_batch_peeling(dsg, ctx, graphs, args) -> dict:
             "identical_results_on_sample": same}
 
 
+def bench_pruned(dsg, g, ctx, stream, T, plain_ms, plain_r) -> dict:
+    """One dsg_run_pruned (core numbers, the ceil(k_max/2)-core, T refine
+    iterations with re-pruning) against one plain dsg_run of T iterations."""
+    import torch
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    r = dsg.dsg_run_pruned(ctx, g, dsg.DSG_SORTING, T)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    return {"variant": "PaRSorting++ with exact pruning (Alg. 1)", "T": T, "ms": ms, "plain_ms": plain_ms,
+            "speedup_vs_plain": plain_ms / ms, "k_max": r["k_max"], "core_vertices": r["core_vertices"],
+            "core_edges": r["core_edges"], "final_vertices": r["final_vertices"],
+            "best": [r["best_edges"], r["best_vertices"], r["best_iter"]],
+            "plain_best": [plain_r["best_edges"], plain_r["best_vertices"], plain_r["best_iter"]]}
+
+
 def bench_rmat20(dsg, ctx, gg, stream, args) -> dict:
     """The R-MAT scale-20 workload (edge factor 16, seed 2) with both
     variants, T = 20, eps = 1/10 for PaRGreedy++: GTEPS per iteration with the
@@ -444,6 +462,9 @@ def main():
     mean_passes = (sort_bytes / n + 4) / 16
     it_bytes = 16 * m + (16 * mean_passes + 40) * n
 
+    # ---- Pruning-and-Refining (Alg. 1) on the same resident graph
+    pruned = bench_pruned(dsg, g, ctx, stream, T, ms_total / args.steps, r)
+
     # ---- end to end through the C ABI with host buffers
     off_h = torch.empty(off.numel(), dtype=torch.int64, pin_memory=True)
     adj_h = torch.empty(adj.numel(), dtype=torch.int32, pin_memory=True)
@@ -521,6 +542,7 @@ def main():
             "clocks": clk.summary(),
             "batched": batched,
             "rmat20": rmat20,
+            "pruned": pruned,
             "serving": serving,
         }
         print(json.dumps(out))

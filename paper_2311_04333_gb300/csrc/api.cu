@@ -818,11 +818,31 @@ int dsg_run_pruned(dsg_graph *G, int variant, int32_t T, int64_t eps_num, int64_
     };
     cudaError_t e;
     CK(cudaMemsetAsync(loads_all, 0, 8 * (size_t)n, s), "memset");
-    // Alg. 1 lines 1-4: core numbers, L = ceil(k_max / 2), G <- L-core, S <- G
-    int64_t kmax = 0;
+    // Alg. 1 lines 1-4: core numbers, L = ceil(k_max / 2), G <- L-core, S <- G.
+    // Only core numbers >= ceil(k_max / 2) are ever used, and those k-cores
+    // lie in H = G[deg >= k_low] for the bound k_low <= ceil(k_max / 2); the
+    // core numbers of H's vertices reaching k_low are those of G, the others
+    // stay below every level used (recorded as 0 outside H).
+    int64_t kmax = 0, k_low = 0;
     {
         PhaseTimer pt(ctx, DSG_PHASE_OTHER);
-        rc = coreness_run(s, G->g, G->rb.ctl, ctx->sm_count, core, &kmax, ctx->err);
+        CoreGraph H;
+        if ((e = degree_core_bound(s, G->g, core, &k_low)) != cudaSuccess)
+            return finish(cuda_fail(ctx, e, "core bound"));
+        if ((e = extract_core(s, n, G->g.off, G->g.adj, core, nullptr, k_low, nullptr, nullptr, &H)) != cudaSuccess)
+            return finish(cuda_fail(ctx, e, "degree core"));
+        GraphDev hg{};
+        hg.n = H.n;
+        hg.arcs = H.arcs;
+        hg.off = H.off;
+        hg.adj = H.adj;
+        int32_t *hcore = lset;      // scratch of n entries, free until the refining starts
+        if (H.n > 0) rc = coreness_run(s, hg, G->rb.ctl, ctx->sm_count, hcore, &kmax, ctx->err);
+        if (rc == DSG_OK) {
+            cudaMemsetAsync(core, 0, 4 * (size_t)n, s);
+            if ((e = scatter_ids(hcore, H.n, H.old_of, core, s)) != cudaSuccess) rc = cuda_fail(ctx, e, "cores");
+        }
+        free_core(H, s);
     }
     if (rc) return finish(rc == DSG_ERR_TIMEOUT ? fail(ctx, rc, "coreness: a bounded wait gave up") : rc);
     int64_t Ln = (kmax + 1) / 2, Ld = 1, level = Ln;

@@ -91,7 +91,78 @@ __global__ void k_scatter_loads(const int64_t *__restrict__ loads, int64_t n, co
         out[old_of[v]] = loads[v];
 }
 
+// degrees as int32
+__global__ void k_deg32(const int64_t *__restrict__ off, int64_t n, int32_t *deg)
+{
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+        deg[v] = (int32_t)(off[v + 1] - off[v]);
+}
+
+__device__ __forceinline__ int ilog2(uint32_t x) { return 31 - __clz(x); }
+
+// warp per vertex: vertices by floor(log2 degree), edges {u, w} (u < w) by
+// floor(log2 min(deg u, deg w))
+__global__ void k_minlog_hist(const int64_t *__restrict__ off, const int32_t *__restrict__ adj,
+                              const int32_t *__restrict__ deg, int64_t n, unsigned long long *vh,
+                              unsigned long long *eh)
+{
+    __shared__ unsigned long long sv[32], se[32];
+    if (threadIdx.x < 32) {
+        sv[threadIdx.x] = 0;
+        se[threadIdx.x] = 0;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t u = w0; u < n; u += nw) {
+        const int32_t du = deg[u];
+        if (du == 0) continue;
+        if (lane == 0) atomicAdd(&sv[ilog2((uint32_t)du)], 1ull);
+        for (int64_t j = off[u] + lane; j < off[u + 1]; j += 32) {
+            const int32_t w = adj[j];
+            if (w > u) atomicAdd(&se[ilog2((uint32_t)min(du, deg[w]))], 1ull);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        if (sv[threadIdx.x]) atomicAdd(&vh[threadIdx.x], sv[threadIdx.x]);
+        if (se[threadIdx.x]) atomicAdd(&eh[threadIdx.x], se[threadIdx.x]);
+    }
+}
+
 }  // namespace
+
+cudaError_t degree_core_bound(cudaStream_t s, const GraphDev &g, int32_t *deg, int64_t *k_low)
+{
+    const int64_t n = g.n;
+    cudaError_t e;
+    unsigned long long *h = nullptr;
+    if ((e = cudaMallocAsync((void **)&h, 64 * 8, s)) != cudaSuccess) return e;
+    cudaMemsetAsync(h, 0, 64 * 8, s);
+    const int grid = (int)imin64((n + 255) / 256, 152 * 16);
+    const int wgrid = (int)imin64((n * 32 + 255) / 256, 152 * 32);
+    k_deg32<<<grid, 256, 0, s>>>(g.off, n, deg);
+    k_minlog_hist<<<wgrid, 256, 0, s>>>(g.off, g.adj, deg, n, h, h + 32);
+    unsigned long long hh[64];
+    cudaMemcpyAsync(hh, h, sizeof hh, cudaMemcpyDeviceToHost, s);
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+    cudaFreeAsync(h, s);
+    // densest of the subgraphs G[deg >= 2^j]: a lower bound on rho*
+    int64_t be = 0, bv = 1;
+    unsigned long long V = 0, E = 0;
+    for (int j = 31; j >= 0; --j) {
+        V += hh[j];
+        E += hh[32 + j];
+        if (V > 0 && (__int128)E * bv > (__int128)be * (__int128)V) {
+            be = (int64_t)E;
+            bv = (int64_t)V;
+        }
+    }
+    const int64_t ceil_rho = (be + bv - 1) / bv;
+    *k_low = (ceil_rho + 1) / 2;
+    return cudaGetLastError();
+}
 
 cudaError_t extract_core(cudaStream_t s, int64_t n, const int64_t *off, const int32_t *adj, const int32_t *core,
                          const int32_t *old_of, int64_t level, const int64_t *loads, int64_t *frozen, CoreGraph *out)
@@ -147,6 +218,20 @@ void free_core(CoreGraph &c, cudaStream_t s)
 cudaError_t gather_ids(const int32_t *local, int64_t k, const int32_t *old_of, int32_t *out, cudaStream_t s)
 {
     if (k > 0) k_gather_ids<<<(int)imin64((k + 255) / 256, 152 * 8), 256, 0, s>>>(local, k, old_of, out);
+    return cudaGetLastError();
+}
+
+namespace {
+__global__ void k_scatter_ids(const int32_t *__restrict__ x, int64_t n, const int32_t *__restrict__ old_of, int32_t *out)
+{
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+        out[old_of[v]] = x[v];
+}
+}  // namespace
+
+cudaError_t scatter_ids(const int32_t *x, int64_t n, const int32_t *old_of, int32_t *out, cudaStream_t s)
+{
+    if (n > 0) k_scatter_ids<<<(int)imin64((n + 255) / 256, 152 * 8), 256, 0, s>>>(x, n, old_of, out);
     return cudaGetLastError();
 }
 

@@ -22,8 +22,15 @@ struct CoreGraph {
 cudaError_t extract_core(cudaStream_t s, int64_t n, const int64_t *off, const int32_t *adj, const int32_t *core,
                          const int32_t *old_of, int64_t level, const int64_t *loads, int64_t *frozen, CoreGraph *out);
 void free_core(CoreGraph &c, cudaStream_t s);
+// deg[n] = degrees (int32), and k_low = ceil(ceil(rho(X)) / 2) for the
+// densest X among the subgraphs induced on {v : deg(v) >= 2^j}: since
+// k_max >= ceil(rho*) >= ceil(rho(X)), k_low <= ceil(k_max / 2), and every
+// k-core with k >= k_low lies in the subgraph induced on {v : deg(v) >= k_low}.
+cudaError_t degree_core_bound(cudaStream_t s, const GraphDev &g, int32_t *deg, int64_t *k_low);
 // out[i] = old_of[local[i]]
 cudaError_t gather_ids(const int32_t *local, int64_t k, const int32_t *old_of, int32_t *out, cudaStream_t s);
+// out[old_of[v]] = x[v]
+cudaError_t scatter_ids(const int32_t *x, int64_t n, const int32_t *old_of, int32_t *out, cudaStream_t s);
 // out[old_of[v]] = loads[v]
 cudaError_t scatter_loads(const int64_t *loads, int64_t n, const int32_t *old_of, int64_t *out, cudaStream_t s);
 
