@@ -45,7 +45,7 @@ BATCH_T = 32
 BATCH_T_PEEL = 16
 SERVE_POOL = 48        # request graphs of the serving workload
 SERVE_SEED = 5
-SERVE_SLOTS = 8
+SERVE_SLOTS = 4
 UNIT = "GTEPS"
 
 
