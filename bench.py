@@ -258,21 +258,30 @@ def bench_batch_peeling(dsg, ctx, graphs, args) -> dict:
 
 
 def bench_pruned(dsg, g, ctx, stream, T, plain_ms, plain_r) -> dict:
-    """One dsg_run_pruned (core numbers, the ceil(k_max/2)-core, T refine
-    iterations with re-pruning) against one plain dsg_run of T iterations."""
+    """dsg_run_pruned (k_max, the ceil(k_max/2)-core, T refine iterations with
+    re-pruning) against plain dsg_run, at T and at 5 T iterations."""
     import torch
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    ev0.record(stream)
-    r = dsg.dsg_run_pruned(ctx, g, dsg.DSG_SORTING, T)
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    ms = ev0.elapsed_time(ev1)
+
+    def timed(fn):
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        out = fn()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        return ev0.elapsed_time(ev1), out
+
+    ms, r = timed(lambda: dsg.dsg_run_pruned(ctx, g, dsg.DSG_SORTING, T))
+    ms5, r5 = timed(lambda: dsg.dsg_run_pruned(ctx, g, dsg.DSG_SORTING, 5 * T))
+    plain5, p5 = timed(lambda: dsg.dsg_run(ctx, g, dsg.DSG_SORTING, 5 * T))
     return {"variant": "PaRSorting++ with exact pruning (Alg. 1)", "T": T, "ms": ms, "plain_ms": plain_ms,
             "speedup_vs_plain": plain_ms / ms, "k_max": r["k_max"], "core_vertices": r["core_vertices"],
             "core_edges": r["core_edges"], "final_vertices": r["final_vertices"],
             "best": [r["best_edges"], r["best_vertices"], r["best_iter"]],
-            "plain_best": [plain_r["best_edges"], plain_r["best_vertices"], plain_r["best_iter"]]}
+            "plain_best": [plain_r["best_edges"], plain_r["best_vertices"], plain_r["best_iter"]],
+            "T5": 5 * T, "ms_T5": ms5, "plain_ms_T5": plain5, "speedup_vs_plain_T5": plain5 / ms5,
+            "best_T5": [r5["best_edges"], r5["best_vertices"], r5["best_iter"]],
+            "plain_best_T5": [p5["best_edges"], p5["best_vertices"], p5["best_iter"]]}
 
 
 def bench_rmat20(dsg, ctx, gg, stream, args) -> dict:

@@ -1,5 +1,6 @@
 // api.cu -- the C ABI of libdsg (include/dsg.h): contexts, graph upload and
 // the host orchestration of one run of T refine iterations.
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -799,13 +800,14 @@ int dsg_run_pruned(dsg_graph *G, int variant, int32_t T, int64_t eps_num, int64_
     // the refine step's outputs (local ids)
     char *mem = nullptr;
     const size_t need = align256(4 * (size_t)n) + align256(8 * (size_t)n) + align256(4 * (size_t)n) +
-                        align256(4 * (size_t)n) + align256(8 * (size_t)n);
+                        align256(4 * (size_t)n) + align256(8 * (size_t)n) + align256(4 * (size_t)n);
     CK(cudaMallocAsync((void **)&mem, need, s), "pruning buffers");
     int32_t *core = (int32_t *)mem;
     int64_t *loads_all = (int64_t *)(mem + align256(4 * (size_t)n));
     int32_t *sset = (int32_t *)((char *)loads_all + align256(8 * (size_t)n));
     int32_t *lset = (int32_t *)((char *)sset + align256(4 * (size_t)n));
     int64_t *nloads = (int64_t *)((char *)lset + align256(4 * (size_t)n));
+    int32_t *kmask = (int32_t *)((char *)nloads + align256(8 * (size_t)n));
     CoreGraph cur;
     dsg_graph *cg = nullptr;
     std::vector<int64_t> trace(3 * (size_t)T, 0);
@@ -818,45 +820,91 @@ int dsg_run_pruned(dsg_graph *G, int variant, int32_t T, int64_t eps_num, int64_
     };
     cudaError_t e;
     CK(cudaMemsetAsync(loads_all, 0, 8 * (size_t)n, s), "memset");
-    // Alg. 1 lines 1-4: core numbers, L = ceil(k_max / 2), G <- L-core, S <- G.
-    // Only core numbers >= ceil(k_max / 2) are ever used, and those k-cores
-    // lie in H = G[deg >= k_low] for the bound k_low <= ceil(k_max / 2); the
-    // core numbers of H's vertices reaching k_low are those of G, the others
-    // stay below every level used (recorded as 0 outside H).
+    // Alg. 1 lines 1-4: k_max, L = ceil(k_max / 2), G <- L-core, S <- G.
+    // Only cores of level >= ceil(k_max / 2) are ever used, and they lie in
+    // H = G[deg >= k_low] for the bound k_low <= ceil(k_max / 2).  k_max is
+    // the largest k whose k-core of H (by deletion) is not empty; each core
+    // the loop needs is taken by deletion too, which is the set of vertices
+    // whose core number in G reaches its level.
     int64_t kmax = 0, k_low = 0;
+    KCoreBufs kb;
+    int32_t *keep = kmask;
+    // chain of nested cores (level, graph): chain[0] = G[deg >= k_low], each
+    // next one the core of a higher level, taken from the one before
+    std::vector<std::pair<int64_t, CoreGraph>> chain;
+    auto kcore = [&](const CoreGraph &c, int64_t k, int64_t *alive) -> int {
+        GraphDev cg_dev{};
+        cg_dev.n = c.n;
+        cg_dev.arcs = c.arcs;
+        cg_dev.off = c.off;
+        cg_dev.adj = c.adj;
+        return kcore_run(s, cg_dev, G->rb.ctl, ctx->sm_count, kb, (int32_t)k, keep, alive, ctx->err);
+    };
+    auto done_k = [&](int code) {
+        for (auto &c : chain) free_core(c.second, s);
+        chain.clear();
+        kcore_free(kb, s);
+        return finish(code == DSG_ERR_TIMEOUT ? fail(ctx, code, "k-core: a bounded wait gave up") : code);
+    };
     {
         PhaseTimer pt(ctx, DSG_PHASE_OTHER);
         CoreGraph H;
-        if ((e = degree_core_bound(s, G->g, core, &k_low)) != cudaSuccess)
-            return finish(cuda_fail(ctx, e, "core bound"));
+        if ((e = degree_core_bound(s, G->g, core, &k_low)) != cudaSuccess) return done_k(cuda_fail(ctx, e, "core bound"));
         if ((e = extract_core(s, n, G->g.off, G->g.adj, core, nullptr, k_low, nullptr, nullptr, &H)) != cudaSuccess)
-            return finish(cuda_fail(ctx, e, "degree core"));
-        GraphDev hg{};
-        hg.n = H.n;
-        hg.arcs = H.arcs;
-        hg.off = H.off;
-        hg.adj = H.adj;
-        int32_t *hcore = lset;      // scratch of n entries, free until the refining starts
-        if (H.n > 0) rc = coreness_run(s, hg, G->rb.ctl, ctx->sm_count, hcore, &kmax, ctx->err);
-        if (rc == DSG_OK) {
-            cudaMemsetAsync(core, 0, 4 * (size_t)n, s);
-            if ((e = scatter_ids(hcore, H.n, H.old_of, core, s)) != cudaSuccess) rc = cuda_fail(ctx, e, "cores");
+            return done_k(cuda_fail(ctx, e, "degree core"));
+        chain.push_back({k_low, H});
+        // k_max: the largest k with a non-empty k-core; search upwards by
+        // doubling from k_low, then by bisection.  The last core of the chain
+        // is the lo-core, which holds every k-core with k >= lo, so each
+        // success shrinks the graph later tests run on.  A k-core has k + 1
+        // vertices and k (k + 1) / 2 edges: k_max < sqrt(2m) + 1.
+        int64_t hi = (int64_t)std::sqrt(2.0 * (double)(G->g.arcs / 2)) + 2;
+        hi = std::min(hi, G->g.max_degree + 1);
+        int64_t lo = k_low;
+        bool doubling = true;
+        while (hi - lo > 1) {
+            const int64_t mid = doubling ? std::min(hi - 1, std::max<int64_t>(lo + 1, 2 * lo)) : lo + (hi - lo) / 2;
+            int64_t alive = 0;
+            const CoreGraph &C = chain.back().second;
+            if ((rc = kcore(C, mid, &alive)) != DSG_OK) return done_k(rc);
+            if (alive == 0) {
+                hi = mid;
+                doubling = false;
+                continue;
+            }
+            lo = mid;
+            CoreGraph nx;
+            if ((e = extract_core(s, C.n, C.off, C.adj, keep, C.old_of, lo, nullptr, nullptr, &nx, true)) !=
+                cudaSuccess)
+                return done_k(cuda_fail(ctx, e, "core extraction"));
+            chain.push_back({lo, nx});
         }
-        free_core(H, s);
+        kmax = lo;
     }
-    if (rc) return finish(rc == DSG_ERR_TIMEOUT ? fail(ctx, rc, "coreness: a bounded wait gave up") : rc);
     int64_t Ln = (kmax + 1) / 2, Ld = 1, level = Ln;
-    if ((e = extract_core(s, n, G->g.off, G->g.adj, core, nullptr, level, nullptr, nullptr, &cur)) != cudaSuccess)
-        return finish(cuda_fail(ctx, e, "core extraction"));
+    {
+        // the L-core, from the highest core of the chain at or below L
+        size_t j = 0;
+        for (size_t i = 0; i < chain.size(); ++i)
+            if (chain[i].first <= level) j = i;
+        const CoreGraph &C = chain[j].second;
+        int64_t alive = 0;
+        if ((rc = kcore(C, level, &alive)) != DSG_OK) return done_k(rc);
+        if ((e = extract_core(s, C.n, C.off, C.adj, keep, C.old_of, level, nullptr, nullptr, &cur, true)) !=
+            cudaSuccess)
+            return done_k(cuda_fail(ctx, e, "core extraction"));
+        for (auto &c : chain) free_core(c.second, s);
+        chain.clear();
+    }
     int64_t se = cur.arcs / 2, sv = cur.n, biter = 0, ssize = cur.n;
     if ((e = cudaMemcpyAsync(sset, cur.old_of, 4 * (size_t)cur.n, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
-        return finish(cuda_fail(ctx, e, "set copy"));
+        return done_k(cuda_fail(ctx, e, "set copy"));
     if (info) {
         info->k_max = kmax;
         info->core_vertices = cur.n;
         info->core_edges = cur.arcs / 2;
     }
-    if ((rc = dsg_upload_csr(ctx, cur.n, cur.off, cur.adj, DSG_SRC_DEVICE, &cg)) != DSG_OK) return finish(rc);
+    if ((rc = dsg_upload_csr(ctx, cur.n, cur.off, cur.adj, DSG_SRC_DEVICE, &cg)) != DSG_OK) return done_k(rc);
     for (int32_t t = 1; t <= T; ++t) {
         // line 6: one iteration of the refine step on the current core,
         // continuing its vertices' loads
@@ -864,9 +912,9 @@ int dsg_run_pruned(dsg_graph *G, int variant, int32_t T, int64_t eps_num, int64_
         r.flags = DSG_DST_DEVICE | DSG_INIT_DEVICE;
         r.loads = nloads;
         r.best_set = lset;
-        if ((rc = dsg_run(cg, variant, 1, eps_num, eps_den, cur.loads, &r)) != DSG_OK) return finish(rc);
+        if ((rc = dsg_run(cg, variant, 1, eps_num, eps_den, cur.loads, &r)) != DSG_OK) return done_k(rc);
         if ((e = cudaMemcpyAsync(cur.loads, nloads, 8 * (size_t)cur.n, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
-            return finish(cuda_fail(ctx, e, "loads copy"));
+            return done_k(cuda_fail(ctx, e, "loads copy"));
         trace[3 * (t - 1)] = r.best_edges;
         trace[3 * (t - 1) + 1] = r.best_vertices;
         trace[3 * (t - 1) + 2] = cur.n;
@@ -876,7 +924,7 @@ int dsg_run_pruned(dsg_graph *G, int variant, int32_t T, int64_t eps_num, int64_
         sv = r.best_vertices;
         biter = t;
         ssize = r.best_set_size;
-        if ((e = gather_ids(lset, ssize, cur.old_of, sset, s)) != cudaSuccess) return finish(cuda_fail(ctx, e, "set"));
+        if ((e = gather_ids(lset, ssize, cur.old_of, sset, s)) != cudaSuccess) return done_k(cuda_fail(ctx, e, "set"));
         if (dens_gt_host(se, sv, Ln, Ld)) {
             Ln = se;
             Ld = sv;
@@ -885,27 +933,29 @@ int dsg_run_pruned(dsg_graph *G, int variant, int32_t T, int64_t eps_num, int64_
         if (nlevel <= level) continue;
         level = nlevel;
         CoreGraph nx;
-        if ((e = extract_core(s, cur.n, cur.off, cur.adj, core, cur.old_of, level, cur.loads, loads_all, &nx)) !=
+        int64_t alive = 0;
+        if ((rc = kcore(cur, level, &alive)) != DSG_OK) return done_k(rc);
+        if ((e = extract_core(s, cur.n, cur.off, cur.adj, keep, cur.old_of, level, cur.loads, loads_all, &nx, true)) !=
             cudaSuccess)
-            return finish(cuda_fail(ctx, e, "core extraction"));
+            return done_k(cuda_fail(ctx, e, "core extraction"));
         free_core(cur, s);
         cur = nx;
         dsg_free_graph(cg);
         cg = nullptr;
-        if ((rc = dsg_upload_csr(ctx, cur.n, cur.off, cur.adj, DSG_SRC_DEVICE, &cg)) != DSG_OK) return finish(rc);
+        if ((rc = dsg_upload_csr(ctx, cur.n, cur.off, cur.adj, DSG_SRC_DEVICE, &cg)) != DSG_OK) return done_k(rc);
     }
     if ((e = scatter_loads(cur.loads, cur.n, cur.old_of, loads_all, s)) != cudaSuccess)
-        return finish(cuda_fail(ctx, e, "loads"));
+        return done_k(cuda_fail(ctx, e, "loads"));
     const cudaMemcpyKind k = dst_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     if (out->loads && (e = cudaMemcpyAsync(out->loads, loads_all, 8 * (size_t)n, k, s)) != cudaSuccess)
-        return finish(cuda_fail(ctx, e, "loads out"));
+        return done_k(cuda_fail(ctx, e, "loads out"));
     if (out->best_set && ssize > 0 && (e = cudaMemcpyAsync(out->best_set, sset, 4 * (size_t)ssize, k, s)) != cudaSuccess)
-        return finish(cuda_fail(ctx, e, "set out"));
+        return done_k(cuda_fail(ctx, e, "set out"));
     if (out->trace &&
         (e = cudaMemcpyAsync(out->trace, trace.data(), 24 * (size_t)T,
                              dst_dev ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost, s)) != cudaSuccess)
-        return finish(cuda_fail(ctx, e, "trace out"));
-    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return finish(cuda_fail(ctx, e, "pruned run"));
+        return done_k(cuda_fail(ctx, e, "trace out"));
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return done_k(cuda_fail(ctx, e, "pruned run"));
     out->best_edges = se;
     out->best_vertices = sv;
     out->best_iter = (int32_t)biter;
@@ -915,7 +965,7 @@ int dsg_run_pruned(dsg_graph *G, int variant, int32_t T, int64_t eps_num, int64_
         info->L_num = Ln;
         info->L_den = Ld;
     }
-    return finish(DSG_OK);
+    return done_k(DSG_OK);
 }
 
 int dsg_upload_batch(dsg_ctx *ctx, int32_t G, const int64_t *n_per, const int64_t *const *offsets,

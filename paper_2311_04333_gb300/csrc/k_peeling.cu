@@ -212,7 +212,7 @@ __global__ void __launch_bounds__(kPeelThreads, 1)
 k_peel(const int64_t *__restrict__ off, const int32_t *__restrict__ adj, int64_t n,
        uint32_t *loads, uint32_t *A, uint32_t *kv, unsigned long long *st, uint32_t *round,
        uint32_t *list0, uint32_t *list1, unsigned long long *heavy, uint64_t p, uint64_t q,
-       PeelCtl *pc, Control *ctl, uint32_t *round_min)
+       PeelCtl *pc, Control *ctl, uint32_t *round_min, uint32_t fixed_k)
 {
     __shared__ PeelSmem S;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -220,6 +220,7 @@ k_peel(const int64_t *__restrict__ off, const int32_t *__restrict__ adj, int64_t
     uint32_t r = 0;
     uint32_t P = gridDim.x;                 // participating blocks
     uint32_t bar_target = 0;
+    uint32_t na_prev = 0;
     if (tid == 0) {
         S.nq = 0;
         S.nt = 0;
@@ -227,6 +228,9 @@ k_peel(const int64_t *__restrict__ off, const int32_t *__restrict__ adj, int64_t
     for (;; ++r) {
         const uint32_t na = ld_acquire_u32(&pc->n_next[r & 1]);
         if (na == 0) break;
+        // fixed threshold (k-core by deletion): stop once a round peels nothing
+        if (fixed_k != kUnpeeled && r > 0 && na == na_prev) break;
+        na_prev = na;
         P = min(P, peel_blocks(na, ld_acquire_u64(&pc->arcs_alive)));
         if (blockIdx.x >= P) break;
         uint32_t *cur = (r & 1) ? list1 : list0;
@@ -258,7 +262,9 @@ k_peel(const int64_t *__restrict__ off, const int32_t *__restrict__ adj, int64_t
         if (!grid_barrier(pc, ctl, P, bar_target)) return;
         if (round_min && blockIdx.x == 0 && tid == 0) round_min[r] = (uint32_t)pc->mn[r & 1];
         // ---- BC: split off F; its low-degree vertices are counted here
-        const unsigned long long thr = pc->mn[r & 1] * (p + q);
+        // F = {key * q <= min * (p + q)}, or {key < fixed_k} (then q = 1)
+        const unsigned long long thr = fixed_k != kUnpeeled ? (unsigned long long)fixed_k - 1ull
+                                                            : pc->mn[r & 1] * (p + q);
         for (uint32_t i0 = blockIdx.x * kPeelThreads; i0 < na; i0 += stride) {
             const uint32_t i = i0 + tid;
             const bool valid = i < na;
@@ -449,9 +455,11 @@ int peel_run(cudaStream_t s, const GraphDev &g, RunBufs &b, PeelBufs &pb, bool &
         int64_t nn = n;
         Control *ctl = b.ctl;
         uint32_t *no_rmin = nullptr;
+        uint32_t no_fixed = kUnpeeled;
         void *args[] = {(void *)&off, (void *)&adj, (void *)&nn, (void *)&loads, (void *)&A,
                         (void *)&kv, (void *)&st, (void *)&round, (void *)&list0, (void *)&list1,
-                        (void *)&heavy, (void *)&pp, (void *)&qq, (void *)&pc, (void *)&ctl, (void *)&no_rmin};
+                        (void *)&heavy, (void *)&pp, (void *)&qq, (void *)&pc, (void *)&ctl, (void *)&no_rmin,
+                        (void *)&no_fixed};
         cudaError_t e = cudaLaunchCooperativeKernel((void *)k_peel, grid, kPeelThreads, args, 0, s);
         if (e != cudaSuccess) {
             err = std::string("cooperative peel launch: ") + cudaGetErrorString(e);
@@ -549,9 +557,10 @@ int coreness_run(cudaStream_t s, const GraphDev &g, Control *ctl, int sm_count, 
     const int32_t *adj = g.adj;
     uint64_t pp = 0, qq = 1;
     int64_t nn = n;
+    uint32_t no_fixed = kUnpeeled;
     void *args[] = {(void *)&off, (void *)&adj, (void *)&nn, (void *)&zl, (void *)&A, (void *)&kv, (void *)&st,
                     (void *)&round, (void *)&list0, (void *)&list1, (void *)&heavy, (void *)&pp, (void *)&qq,
-                    (void *)&pc, (void *)&ctl, (void *)&rmin};
+                    (void *)&pc, (void *)&ctl, (void *)&rmin, (void *)&no_fixed};
     e = cudaLaunchCooperativeKernel((void *)k_peel, grid, kPeelThreads, args, 0, s);
     uint32_t rounds = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&rounds, &pc->rounds, 4, cudaMemcpyDeviceToHost, s);
@@ -578,6 +587,98 @@ int coreness_run(cudaStream_t s, const GraphDev &g, Control *ctl, int sm_count, 
         return DSG_ERR_CUDA;
     }
     return DSG_OK;
+}
+
+// ---- the k-core by deletion (Sec. 2, Definition of k-core): rounds that
+// remove every alive vertex of induced degree < k at once, until a round
+// removes nothing; keep[v] = k for the survivors, 0 for the others.
+__global__ void k_kcore_mark(const uint32_t *__restrict__ round, int64_t n, int32_t k, int32_t *keep)
+{
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+        keep[v] = (!round || round[v] == kUnpeeled) ? k : 0;
+}
+
+KCoreBufs::~KCoreBufs() = default;
+
+int kcore_run(cudaStream_t s, const GraphDev &g, Control *ctl, int sm_count, KCoreBufs &kb, int32_t k,
+              int32_t *keep, int64_t *survivors, std::string &err)
+{
+    const int64_t n = g.n;
+    const int igrid0 = (int)imax64(1, imin64((n + 255) / 256, (int64_t)sm_count * 8));
+    if (k <= 0) {                          // the 0-core is the whole graph
+        k_kcore_mark<<<igrid0, 256, 0, s>>>(nullptr, n, 0, keep);
+        *survivors = n;
+        return cudaGetLastError() == cudaSuccess ? DSG_OK : DSG_ERR_CUDA;
+    }
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    const size_t sz4 = al(4 * (size_t)n), sz8 = al(8 * (size_t)n), sz_pc = al(sizeof(PeelCtl));
+    const size_t total = 6 * sz4 + 2 * sz8 + sz_pc;
+    cudaError_t e;
+    if (kb.bytes < total) {
+        if (kb.mem) cudaFreeAsync(kb.mem, s);
+        kb.mem = nullptr;
+        kb.bytes = 0;
+        if ((e = cudaMallocAsync(&kb.mem, total, s)) != cudaSuccess) {
+            err = std::string("k-core buffers: ") + cudaGetErrorString(e);
+            return e == cudaErrorMemoryAllocation ? DSG_ERR_NOMEM : DSG_ERR_CUDA;
+        }
+        kb.bytes = total;
+    }
+    char *m = (char *)kb.mem;
+    uint32_t *kv = (uint32_t *)m, *round = (uint32_t *)(m + sz4), *list0 = (uint32_t *)(m + 2 * sz4);
+    uint32_t *list1 = (uint32_t *)(m + 3 * sz4), *zl = (uint32_t *)(m + 4 * sz4), *A = (uint32_t *)(m + 5 * sz4);
+    unsigned long long *st = (unsigned long long *)(m + 6 * sz4);
+    unsigned long long *heavy = (unsigned long long *)(m + 6 * sz4 + sz8);
+    PeelCtl *pc = (PeelCtl *)(m + 6 * sz4 + 2 * sz8);
+    cudaMemsetAsync(zl, 0, 4 * (size_t)n, s);
+    std::call_once(g_peel_once, [] {
+        int nb = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_peel, kPeelThreads, 0);
+        g_peel_blocks_per_sm = nb > 0 ? 1 : 0;
+    });
+    if (g_peel_blocks_per_sm < 1) {
+        err = "the peel kernel cannot be resident";
+        return DSG_ERR_CUDA;
+    }
+    const int grid = (int)imin64(sm_count, peel_blocks((uint64_t)n, (uint64_t)g.arcs));
+    const int igrid = (int)imin64((n + 255) / 256, (int64_t)sm_count * 8);
+    k_peel_init<<<igrid, 256, 0, s>>>(g.off, zl, n, g.arcs, kv, round, list0, pc);
+    const int64_t *off = g.off;
+    const int32_t *adj = g.adj;
+    uint64_t pp = 0, qq = 1;
+    int64_t nn = n;
+    uint32_t *no_rmin = nullptr;
+    uint32_t fk = (uint32_t)k;
+    void *args[] = {(void *)&off, (void *)&adj, (void *)&nn, (void *)&zl, (void *)&A, (void *)&kv, (void *)&st,
+                    (void *)&round, (void *)&list0, (void *)&list1, (void *)&heavy, (void *)&pp, (void *)&qq,
+                    (void *)&pc, (void *)&ctl, (void *)&no_rmin, (void *)&fk};
+    e = cudaLaunchCooperativeKernel((void *)k_peel, grid, kPeelThreads, args, 0, s);
+    if (e == cudaSuccess) k_kcore_mark<<<igrid, 256, 0, s>>>(round, n, k, keep);
+    uint32_t alive[2] = {0, 0};
+    int cerr = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(alive, pc->n_next, 8, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&cerr, &ctl->err, sizeof(int), cudaMemcpyDeviceToHost, s);
+    uint32_t rounds = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&rounds, &pc->rounds, 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        err = std::string("k-core: ") + cudaGetErrorString(e);
+        return DSG_ERR_CUDA;
+    }
+    if (cerr) {
+        err = "k-core: a bounded wait gave up";
+        return cerr;
+    }
+    // the survivors are the alive list of the last round
+    *survivors = alive[rounds & 1];
+    return DSG_OK;
+}
+
+void kcore_free(KCoreBufs &kb, cudaStream_t s)
+{
+    if (kb.mem) cudaFreeAsync(kb.mem, s);
+    kb.mem = nullptr;
+    kb.bytes = 0;
 }
 
 }  // namespace dsg

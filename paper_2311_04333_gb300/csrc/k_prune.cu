@@ -10,12 +10,12 @@ namespace dsg {
 namespace {
 
 // pos[v] = 1 if v is kept (pos[n] = 0); scanned into new ids afterwards
-__global__ void k_ext_flags(const int32_t *__restrict__ core, const int32_t *__restrict__ old_of, int64_t n,
-                            int64_t level, int64_t *pos)
+__global__ void k_ext_flags(const int32_t *__restrict__ core, const int32_t *__restrict__ old_of, int key_local,
+                            int64_t n, int64_t level, int64_t *pos)
 {
     for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v <= n; v += (int64_t)gridDim.x * blockDim.x) {
         int64_t k = 0;
-        if (v < n) k = core[old_of ? old_of[v] : (int32_t)v] >= level ? 1 : 0;
+        if (v < n) k = core[(old_of && !key_local) ? old_of[v] : (int32_t)v] >= level ? 1 : 0;
         pos[v] = k;
     }
 }
@@ -119,9 +119,16 @@ __global__ void k_minlog_hist(const int64_t *__restrict__ off, const int32_t *__
         const int32_t du = deg[u];
         if (du == 0) continue;
         if (lane == 0) atomicAdd(&sv[ilog2((uint32_t)du)], 1ull);
-        for (int64_t j = off[u] + lane; j < off[u + 1]; j += 32) {
-            const int32_t w = adj[j];
-            if (w > u) atomicAdd(&se[ilog2((uint32_t)min(du, deg[w]))], 1ull);
+        for (int64_t j0 = off[u]; j0 < off[u + 1]; j0 += 32) {
+            const int64_t j = j0 + lane;
+            int b = 32;                               // no edge
+            if (j < off[u + 1]) {
+                const int32_t w = adj[j];
+                if (w > u) b = ilog2((uint32_t)min(du, deg[w]));
+            }
+            // one shared-memory add per distinct bin of the warp
+            const uint32_t peers = __match_any_sync(0xffffffffu, b);
+            if (b < 32 && (peers & lanemask_lt()) == 0) atomicAdd(&se[b], (unsigned long long)__popc(peers));
         }
     }
     __syncthreads();
@@ -165,7 +172,8 @@ cudaError_t degree_core_bound(cudaStream_t s, const GraphDev &g, int32_t *deg, i
 }
 
 cudaError_t extract_core(cudaStream_t s, int64_t n, const int64_t *off, const int32_t *adj, const int32_t *core,
-                         const int32_t *old_of, int64_t level, const int64_t *loads, int64_t *frozen, CoreGraph *out)
+                         const int32_t *old_of, int64_t level, const int64_t *loads, int64_t *frozen, CoreGraph *out,
+                         bool key_local)
 {
     cudaError_t e;
     int64_t *pos = nullptr, *tmp = nullptr;
@@ -175,7 +183,7 @@ cudaError_t extract_core(cudaStream_t s, int64_t n, const int64_t *off, const in
     int64_t *total = tmp + ntmp - 1;
     const int grid = (int)imin64((n + 256) / 256, 152 * 16);
     const int wgrid = (int)imin64((n * 32 + 255) / 256, 152 * 32);
-    k_ext_flags<<<grid, 256, 0, s>>>(core, old_of, n, level, pos);
+    k_ext_flags<<<grid, 256, 0, s>>>(core, old_of, key_local ? 1 : 0, n, level, pos);
     if ((e = scan_exclusive_i64(pos, n + 1, total, tmp, s)) != cudaSuccess) return e;
     int64_t nn = 0;
     cudaMemcpyAsync(&nn, total, 8, cudaMemcpyDeviceToHost, s);

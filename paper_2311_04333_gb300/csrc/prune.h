@@ -17,10 +17,12 @@ struct CoreGraph {
 };
 
 // The subgraph of (n, off, adj) induced on {v : core[old_of[v]] >= level}
-// (old_of NULL: identity), its maps and carried loads (loads NULL: zeros);
-// the loads of the dropped vertices go to frozen[old id] (if not NULL).
+// (old_of NULL: identity; key_local: core[v] by local id), its maps and
+// carried loads (loads NULL: zeros); the loads of the dropped vertices go
+// to frozen[old id] (if not NULL).
 cudaError_t extract_core(cudaStream_t s, int64_t n, const int64_t *off, const int32_t *adj, const int32_t *core,
-                         const int32_t *old_of, int64_t level, const int64_t *loads, int64_t *frozen, CoreGraph *out);
+                         const int32_t *old_of, int64_t level, const int64_t *loads, int64_t *frozen, CoreGraph *out,
+                         bool key_local = false);
 void free_core(CoreGraph &c, cudaStream_t s);
 // deg[n] = degrees (int32), and k_low = ceil(ceil(rho(X)) / 2) for the
 // densest X among the subgraphs induced on {v : deg(v) >= 2^j}: since
