@@ -175,7 +175,7 @@ int ensure_run_bufs(dsg_ctx *ctx, dsg_graph *G, int32_t T)
             sizeof(Control),                    // ctl
             (size_t)nblk * 8,                   // blk_a
             (size_t)nblk * 8,                   // blk_b
-            (size_t)(G->g.n_hot > 0 ? G->g.n_hot : 1) * 4,  // hot_l
+            (size_t)(G->g.n_hot > 0 ? G->g.n_hot : 1) * 8,  // hot_l, hot_c
             0};
         size_t total = 0;
         for (size_t s : sz) total += align256(s);
@@ -199,6 +199,9 @@ int ensure_run_bufs(dsg_ctx *ctx, dsg_graph *G, int32_t T)
         b.blk_a = (int64_t *)take(sz[8]);
         b.blk_b = (int64_t *)take(sz[9]);
         b.hot_l = (uint32_t *)take(sz[10]);
+        b.hot_c = b.hot_l + (G->g.n_hot > 0 ? G->g.n_hot : 1);
+        CK(cudaMemsetAsync(b.hot_c, 0, sizeof(uint32_t) * (size_t)(G->g.n_hot > 0 ? G->g.n_hot : 1), ctx->stream),
+           "hot counters");
         b.ntiles = ntiles;
         b.nblk64 = nblk;
         CK(cudaMemsetAsync(b.status, 0, sz[4], ctx->stream), "status init");
@@ -667,9 +670,10 @@ int dsg_run(dsg_graph *G, int variant, int32_t T, int64_t eps_num, int64_t eps_d
                     PhaseTimer pt(ctx, DSG_PHASE_OTHER);
                     e = launch_snapshot(G->g, b, ss);
                 }
-                // the equal-loads edge scan is one of the two launches (one exits at once)
+                // the equal-loads edge scan is one of the two launches (one exits at
+                // once); a hot tier adds its refresh and fold
                 ctx->launches[DSG_PHASE_OTHER] += 3;
-                ctx->launches[DSG_PHASE_EDGE_SCAN] += 2;
+                ctx->launches[DSG_PHASE_EDGE_SCAN] += 2 + (G->g.n_hot > 0 ? 2 : 0);
                 ctx->launches[DSG_PHASE_SORT] += kMaxPasses + 1;
                 // oriented arcs (4m) + one target load per arc (4m) + oriented
                 // offsets (8n) + own loads (4n) + A (4n)

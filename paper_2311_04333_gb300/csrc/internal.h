@@ -132,6 +132,7 @@ struct RunBufs {
     int64_t *trace;          // [T * 3] device
     int64_t *blk_a, *blk_b;  // scratch for block-level counts (size nblk64)
     uint32_t *hot_l;         // [n_hot] loads of the hot tier (refreshed per iteration)
+    uint32_t *hot_c;         // [n_hot] counts for the hot tier (zero between scans)
     int64_t nblk64;
     void *scratch;           // >= 8n bytes (output staging)
 };

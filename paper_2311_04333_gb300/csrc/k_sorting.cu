@@ -194,10 +194,11 @@ __device__ __forceinline__ uint32_t target_load(uint32_t t, const uint32_t *__re
 }
 
 // compare target t (load lw) with source (lu, u): count for u, or add one
-// to the target's count
+// to the target's count: shared-memory counters for hubs, the dense hot-tier
+// counters (folded into A after the scan) for the next tier, A otherwise
 __device__ __forceinline__ void settle(uint32_t t, uint32_t lw, uint32_t lu, uint32_t u,
                                        const uint32_t *__restrict__ hot_id, EsSmem &S,
-                                       uint32_t *A, uint32_t &c)
+                                       uint32_t *A, uint32_t *hot_c, uint32_t &c)
 {
     const bool hub = t & kHubBit;
     const bool hot = !hub && (t & S.hot_bit);
@@ -208,7 +209,8 @@ __device__ __forceinline__ void settle(uint32_t t, uint32_t lw, uint32_t lu, uin
     }
     if (later) ++c;
     else if (hub) atomicAdd(&S.hub_c[t & ~kHubBit], 1u);
-    else atomicAdd(&A[hot ? __ldg(hot_id + (t & kSlotMask)) : t], 1u);
+    else if (hot) atomicAdd(&hot_c[t & kSlotMask], 1u);
+    else atomicAdd(&A[t], 1u);
 }
 
 // the warp processes oriented arcs [a0, a1) of source (lu, u); returns this
@@ -217,7 +219,7 @@ __device__ __forceinline__ uint32_t warp_arcs(const uint32_t *__restrict__ oadj,
                                               const uint32_t *__restrict__ loads,
                                               const uint32_t *__restrict__ hot_l,
                                               const uint32_t *__restrict__ hot_id, EsSmem &S,
-                                              uint32_t *A, int64_t a0, int64_t a1, uint32_t lu,
+                                              uint32_t *A, uint32_t *hot_c, int64_t a0, int64_t a1, uint32_t lu,
                                               uint32_t u, int lane, uint64_t pol)
 {
     uint32_t c = 0;
@@ -236,7 +238,7 @@ __device__ __forceinline__ uint32_t warp_arcs(const uint32_t *__restrict__ oadj,
         #pragma unroll
         for (int k = 0; k < kEsUnroll; ++k) {
             const int64_t j = j0 + k * 32 + lane;
-            if (j < a1) settle(t[k], lw[k], lu, u, hot_id, S, A, c);
+            if (j < a1) settle(t[k], lw[k], lu, u, hot_id, S, A, hot_c, c);
         }
     }
     return c;
@@ -247,7 +249,7 @@ k_edge_scan(const int64_t *__restrict__ ooff, const uint32_t *__restrict__ oadj,
             const uint32_t *__restrict__ hub_id, int64_t n_hub,
             const uint32_t *__restrict__ hot_l, const uint32_t *__restrict__ hot_id,
             const WorkItem *__restrict__ items, int64_t n_items, int64_t n,
-            const uint32_t *__restrict__ loads, uint32_t *A, Control *ctl, int sorted)
+            const uint32_t *__restrict__ loads, uint32_t *A, uint32_t *hot_c, Control *ctl, int sorted)
 {
     extern __shared__ __align__(16) unsigned char es_smem_raw[];
     EsSmem &S = *reinterpret_cast<EsSmem *>(es_smem_raw);
@@ -282,7 +284,7 @@ k_edge_scan(const int64_t *__restrict__ ooff, const uint32_t *__restrict__ oadj,
             const WorkItem it = items[unit];
             const uint32_t u = it.u;
             const int64_t a1 = imin64(it.a0 + (int64_t)kChunk, ooff[u + 1]);
-            uint32_t c = warp_arcs(oadj, loads, hot_l, hot_id, S, A, it.a0, a1, loads[u], u, lane, pol);
+            uint32_t c = warp_arcs(oadj, loads, hot_l, hot_id, S, A, hot_c, it.a0, a1, loads[u], u, lane, pol);
             c = __reduce_add_sync(kFull, c);
             if (lane == 0 && c) atomicAdd(&A[u], c);
             continue;
@@ -309,7 +311,7 @@ k_edge_scan(const int64_t *__restrict__ ooff, const uint32_t *__restrict__ oadj,
             mm &= mm - 1;
             const int64_t vs = __shfl_sync(kFull, s, l), ve = __shfl_sync(kFull, e, l);
             const uint32_t vl = __shfl_sync(kFull, lu, l);
-            uint32_t c = warp_arcs(oadj, loads, hot_l, hot_id, S, A, vs, ve, vl, (uint32_t)(g0 + l), lane, pol);
+            uint32_t c = warp_arcs(oadj, loads, hot_l, hot_id, S, A, hot_c, vs, ve, vl, (uint32_t)(g0 + l), lane, pol);
             c = __reduce_add_sync(kFull, c);
             if (lane == l) cnt = c;
         }
@@ -388,7 +390,7 @@ k_edge_scan(const int64_t *__restrict__ ooff, const uint32_t *__restrict__ oadj,
                     const uint32_t j = base + k * 32 + lane;
                     const uint32_t l_src = __shfl_sync(kFull, lu, sl_r[k]);
                     uint32_t one = 0;
-                    if (j < total) settle(t[k], lw[k], l_src, (uint32_t)(g0 + sl_r[k]), hot_id, S, A, one);
+                    if (j < total) settle(t[k], lw[k], l_src, (uint32_t)(g0 + sl_r[k]), hot_id, S, A, hot_c, one);
                     const uint32_t C = __ballot_sync(kFull, one != 0);
                     const int jb = (int)(base + k * 32);
                     const int lo = max((int)start - jb, 0), hi = min((int)incl - jb, 32);
@@ -451,6 +453,20 @@ __global__ void k_edge_scan_equal(const int64_t *__restrict__ off, const int32_t
 }
 
 // dense copy of the hot tier's loads for this iteration
+// A[hot_id[i]] += hot_c[i] (distinct ids; after the scan), and reset hot_c
+__global__ void k_hot_fold(uint32_t *__restrict__ hot_c, const uint32_t *__restrict__ hot_id, int64_t n_hot,
+                           uint32_t *A)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_hot;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t c = hot_c[i];
+        if (c) {
+            A[hot_id[i]] += c;
+            hot_c[i] = 0;
+        }
+    }
+}
+
 __global__ void k_hot_refresh(const uint32_t *__restrict__ loads, const uint32_t *__restrict__ hot_id,
                               int64_t n_hot, uint32_t *__restrict__ hot_l)
 {
@@ -472,7 +488,11 @@ cudaError_t launch_edge_scan(const GraphDev &g, RunBufs &b, int grid, cudaStream
     }
     k_edge_scan<<<grid, kEsThreads, sizeof(EsSmem), s>>>(g.ooff, g.oadj, g.hub_id, g.n_hub, b.hot_l,
                                             g.n_hot > 0 ? g.hot_id : nullptr,
-                                            g.items, g.n_items, g.n, b.loads, b.A, b.ctl, g.sorted);
+                                            g.items, g.n_items, g.n, b.loads, b.A, b.hot_c, b.ctl, g.sorted);
+    if (g.n_hot > 0) {
+        const int hg = (int)imin64((g.n_hot + 255) / 256, 152 * 8);
+        k_hot_fold<<<hg, 256, 0, s>>>(b.hot_c, g.hot_id, g.n_hot, b.A);
+    }
     return cudaGetLastError();
 }
 

@@ -196,7 +196,8 @@ def test_profiling_stats(dsg, ctx, path):
     finally:
         dsg.dsg_set_profiling(ctx, False)
     st = dsg.dsg_get_stats(ctx, reset=True)
-    assert st["edge_scan"]["launches"] == 6 and st["sort"]["launches"] == 15
+    # two edge-scan launches per iteration (one exits at once), two more with a hot tier
+    assert st["edge_scan"]["launches"] in (6, 12) and st["sort"]["launches"] == 15
     assert st["edge_scan"]["ms"] > 0 and st["sort"]["ms"] > 0
     assert st["edge_scan"]["bytes"] == 3 * (8 * g.m + 16 * g.n)
 
