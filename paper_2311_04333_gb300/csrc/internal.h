@@ -34,7 +34,7 @@ constexpr uint32_t kHubBit = 0x80000000u;
 // outside the hubs but inside it are stored as kHotBit | slot (only when
 // n < 2^30, so that plain ids never carry the bit)
 #ifndef DSG_HOT
-#define DSG_HOT (1 << 22)
+#define DSG_HOT (1 << 23)
 #endif
 constexpr int64_t kHot = DSG_HOT;
 constexpr uint32_t kHotBit = 0x40000000u;
