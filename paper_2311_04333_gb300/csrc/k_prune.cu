@@ -138,6 +138,33 @@ __global__ void k_minlog_hist(const int64_t *__restrict__ off, const int32_t *__
     }
 }
 
+// the same histograms from the degree-oriented copy: an edge is stored at
+// its endpoint of smaller (degree, id), so the smaller degree of an edge is
+// the degree of the vertex holding it, and no arc is read
+__global__ void k_minlog_oriented(const int64_t *__restrict__ off, const int64_t *__restrict__ ooff, int64_t n,
+                                  unsigned long long *vh, unsigned long long *eh)
+{
+    __shared__ unsigned long long sv[32], se[32];
+    if (threadIdx.x < 32) {
+        sv[threadIdx.x] = 0;
+        se[threadIdx.x] = 0;
+    }
+    __syncthreads();
+    for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < n; u += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t d = off[u + 1] - off[u];
+        if (d == 0) continue;
+        const int b = ilog2((uint32_t)d);
+        atomicAdd(&sv[b], 1ull);
+        const int64_t od = ooff[u + 1] - ooff[u];
+        if (od) atomicAdd(&se[b], (unsigned long long)od);
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        if (sv[threadIdx.x]) atomicAdd(&vh[threadIdx.x], sv[threadIdx.x]);
+        if (se[threadIdx.x]) atomicAdd(&eh[threadIdx.x], se[threadIdx.x]);
+    }
+}
+
 }  // namespace
 
 cudaError_t degree_core_bound(cudaStream_t s, const GraphDev &g, int32_t *deg, int64_t *k_low)
@@ -150,7 +177,8 @@ cudaError_t degree_core_bound(cudaStream_t s, const GraphDev &g, int32_t *deg, i
     const int grid = (int)imin64((n + 255) / 256, 152 * 16);
     const int wgrid = (int)imin64((n * 32 + 255) / 256, 152 * 32);
     k_deg32<<<grid, 256, 0, s>>>(g.off, n, deg);
-    k_minlog_hist<<<wgrid, 256, 0, s>>>(g.off, g.adj, deg, n, h, h + 32);
+    if (g.ooff) k_minlog_oriented<<<grid, 256, 0, s>>>(g.off, g.ooff, n, h, h + 32);
+    else k_minlog_hist<<<wgrid, 256, 0, s>>>(g.off, g.adj, deg, n, h, h + 32);
     unsigned long long hh[64];
     cudaMemcpyAsync(hh, h, sizeof hh, cudaMemcpyDeviceToHost, s);
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
