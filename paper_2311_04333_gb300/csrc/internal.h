@@ -51,7 +51,10 @@ constexpr int kRadixBits = 8;
 constexpr int kBuckets = 1 << kRadixBits;
 constexpr int kMaxPasses = 4;          // 32-bit keys
 constexpr int kPassThreads = 256;      // == kBuckets (one lookback lane per bucket)
-constexpr int kPassIpt = 16;           // items per thread
+#ifndef DSG_PASS_IPT
+#define DSG_PASS_IPT 24
+#endif
+constexpr int kPassIpt = DSG_PASS_IPT;  // items per thread
 constexpr int kPassTile = kPassThreads * kPassIpt;
 
 // status word of the decoupled look-back: [epoch:16][flag:2][count:46]

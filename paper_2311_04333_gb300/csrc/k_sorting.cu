@@ -559,7 +559,7 @@ struct PassSmem {
 };
 
 #ifndef DSG_PASS_MINBLOCKS
-#define DSG_PASS_MINBLOCKS 4
+#define DSG_PASS_MINBLOCKS 3
 #endif
 __device__ __forceinline__ unsigned long long status_word(uint32_t epoch, uint64_t flag, uint64_t cnt)
 {
@@ -600,7 +600,7 @@ k_radix_pass(const uint32_t *kin, const uint32_t *vin,
     const uint32_t tile = S.tile;
     const int64_t tbase = (int64_t)tile * kPassTile;
 
-    // ---- load 16 rounds of 32 consecutive items per warp (all loads first);
+    // ---- load kPassIpt rounds of 32 consecutive items per warp (all loads first);
     // indices inside the warp's segment are 32-bit
     uint32_t key_r[kPassIpt], val_r[kPassIpt], dw_r[kPassIpt];
     const int64_t wbase = tbase + warp * (32 * kPassIpt);
