@@ -346,6 +346,39 @@ def bench_serving(dsg, pool, device, args) -> dict:
     return res
 
 
+def profile_case(name: str) -> int:
+    """One small run of a kernel for profilers (nothing is timed):
+    edge_scan_rmat25: PaRSorting++ T = 3 on R-MAT 25 (k_edge_scan launches 2 and 3);
+    peel_rmat20: PaRGreedy++ eps = 1/10, T = 2, whole-GPU path, on R-MAT 20;
+    batch_1024: batched PaRSorting++ T = 8 on 1,024 graphs of the batch recipe."""
+    import numpy as np
+    import torch
+    import graphgen as gg
+    import paper_2311_04333_gb300 as dsg
+    ctx = dsg.dsg_create(0, torch.cuda.current_stream().cuda_stream)
+    if name == "edge_scan_rmat25":
+        n, off, adj = gg.rmat_cuda(25, 16, 3)
+        g = dsg.dsg_upload_csr(ctx, n, off, adj, dsg.DSG_SRC_DEVICE)
+        dsg.dsg_run(ctx, g, dsg.DSG_SORTING, 3, 0, 1, None, torch.empty(n, dtype=torch.int64, device="cuda"))
+        dsg.dsg_free_graph(g)
+    elif name == "peel_rmat20":
+        n, off, adj = gg.rmat_cuda(20, 16, 2)
+        g = dsg.dsg_upload_csr(ctx, n, off, adj, dsg.DSG_SRC_DEVICE)
+        dsg.dsg_run(ctx, g, dsg.DSG_PEELING, 2, 1, 10, None, torch.empty(n, dtype=torch.int64, device="cuda"),
+                    path=dsg.DSG_PATH_GRID)
+        dsg.dsg_free_graph(g)
+    else:
+        graphs = gg.batch_mix(G=1024, seed=BATCH_SEED)
+        b = dsg.dsg_upload_batch(ctx, [(x.n, x.off, x.adj) for x in graphs], 0)
+        best = np.zeros(4 * len(graphs), np.int64)
+        dsg.dsg_run_batch(ctx, b, dsg.DSG_SORTING, np.full(len(graphs), 8, np.int32), 1024, best)
+        dsg.dsg_free_batch(b)
+    torch.cuda.synchronize()
+    dsg.dsg_destroy(ctx)
+    print(f"profile case {name}: done")
+    return 0
+
+
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
@@ -389,7 +422,11 @@ def main():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=8.0)
     ap.add_argument("--serve-slots", type=int, default=SERVE_SLOTS)
+    ap.add_argument("--profile-case", choices=["edge_scan_rmat25", "peel_rmat20", "batch_1024"],
+                    help="run one small case for a profiler instead of the benchmark")
     args = ap.parse_args()
+    if args.profile_case:
+        return profile_case(args.profile_case)
     if args.impl == "reference":
         return run_reference(args)
 
