@@ -67,6 +67,23 @@ def _max_over_ranks(x: float, ws: int) -> float:
     return float(t.item())
 
 
+def _sum_over_ranks(x: float, ws: int) -> float:
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64,
+                     device="cuda" if dist.get_backend() == "nccl" else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def replica_throughput(units_local: float, seconds_local: float, ws: int) -> float:
+    """Whole-job throughput of ws independent replicas: the units all ranks
+    processed over the slowest rank's time (every rank gets the same value)."""
+    return _sum_over_ranks(units_local, ws) / _max_over_ranks(seconds_local, ws)
+
+
 def _barrier(ws: int):
     if ws > 1:
         import torch.distributed as dist
@@ -485,11 +502,11 @@ def main():
         torch.cuda.synchronize()
     _barrier(ws)
     dsg.dsg_set_profiling(ctx, False)
-    ms_total = ev0.elapsed_time(ev1)
-    ms_total = _max_over_ranks(ms_total, ws)
+    ms_local = ev0.elapsed_time(ev1)
+    value = replica_throughput(m * T * args.steps, ms_local * 1e-3, ws) / 1e9
+    ms_total = _max_over_ranks(ms_local, ws)
     st = dsg.dsg_get_stats(ctx, reset=True)
     launches = sum(v["launches"] for v in st.values())
-    value = m * T * args.steps * ws / (ms_total * 1e-3) / 1e9
     es_ms = st["edge_scan"]["ms"] / (args.steps * T)
     # algorithmic bytes of one edge scan over the symmetric CSR: 8m adjacency
     # + 8m neighbour-load gathers (4 B each) + 8(n+1) offsets + 4n own loads
@@ -537,8 +554,7 @@ def main():
     for _ in range(args.e2e_steps):
         re = e2e_step()
     torch.cuda.synchronize()
-    e2e_s = _max_over_ranks(time.perf_counter() - t0, ws)
-    e2e_value = m * T * args.e2e_steps * ws / e2e_s / 1e9
+    e2e_value = replica_throughput(m * T * args.e2e_steps, time.perf_counter() - t0, ws) / 1e9
     h2d = 8 * (n + 1) + 4 * 2 * m
     d2h = 8 * n + 4 * re["best_set_size"]
 
