@@ -1,5 +1,7 @@
 // k_graph.cu -- upload-time kernels: CSR validation and the tile schedule
 // of the edge scan, plus small reductions used by the host orchestration.
+#include <vector>
+
 #include "common.cuh"
 
 namespace dsg {
@@ -415,13 +417,48 @@ __global__ void k_orient_fill_big(const int64_t *__restrict__ off, const int32_t
     }
 }
 
-// smallest D >= 2 with #{deg >= D} <= cap (count(deg >= max_degree + 1) = 0)
-static cudaError_t degree_threshold(const GraphDev &g, int64_t cap, unsigned long long *cnt,
-                                    int grid, cudaStream_t s, int64_t *D_out)
+// exact degree histogram up to kDegHist - 1; larger degrees share the last
+// bucket (warp-aggregated shared-memory counts for small degrees)
+constexpr int kDegHist = 1 << 16;
+constexpr int kDegSmem = 2048;
+__global__ void k_degree_hist(const int64_t *__restrict__ off, int64_t n, unsigned int *hist)
 {
-    int64_t lo = 2, hi = g.max_degree + 1;
+    __shared__ unsigned int sh[kDegSmem];
+    for (int i = threadIdx.x; i < kDegSmem; i += blockDim.x) sh[i] = 0;
+    __syncthreads();
+    for (int64_t v0 = blockIdx.x * (int64_t)blockDim.x; v0 < n; v0 += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t v = v0 + threadIdx.x;
+        const int d = v < n ? (int)imin64(off[v + 1] - off[v], kDegHist - 1) : -1;
+        const unsigned peers = __match_any_sync(kFull, d);
+        if (d >= 0 && (peers & lanemask_lt()) == 0) {
+            if (d < kDegSmem) atomicAdd(&sh[d], (unsigned)__popc(peers));
+            else atomicAdd(&hist[d], (unsigned)__popc(peers));
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kDegSmem; i += blockDim.x)
+        if (sh[i]) atomicAdd(&hist[i], sh[i]);
+}
+
+// smallest D >= 2 with #{deg >= D} <= cap (count(deg >= max_degree + 1) = 0),
+// from the degree histogram when the answer lies below its last bucket,
+// otherwise by bisection with counting passes
+static cudaError_t degree_threshold(const GraphDev &g, int64_t cap, const std::vector<unsigned int> &hist,
+                                    unsigned long long *cnt, int grid, cudaStream_t s, int64_t *D_out)
+{
+    if (g.n <= cap) {                           // every vertex of degree >= 2 fits
+        *D_out = 2;
+        return cudaSuccess;
+    }
+    if ((int64_t)hist[kDegHist - 1] <= cap) {
+        int64_t above = hist[kDegHist - 1];     // #{deg >= D} for D = kDegHist - 1
+        int64_t D = kDegHist - 1;
+        while (D > 2 && above + (int64_t)hist[D - 1] <= cap) above += hist[--D];
+        *D_out = D;
+        return cudaSuccess;
+    }
+    int64_t lo = kDegHist - 1, hi = g.max_degree + 1;
     cudaError_t e;
-    if (g.n <= cap) hi = lo;                    // every vertex of degree >= 2 fits
     while (lo < hi) {
         const int64_t mid = lo + (hi - lo) / 2;
         unsigned long long h = 0;
@@ -453,8 +490,18 @@ cudaError_t build_orientation(GraphDev &g, cudaStream_t s, int full, int32_t *er
     if ((e = cudaMallocAsync((void **)&flag, 8 * (size_t)(n + 1), s)) != cudaSuccess) return e;
     if ((e = cudaMallocAsync((void **)&slot_of, 4 * (size_t)n, s)) != cudaSuccess) return e;
     if ((e = cudaMallocAsync((void **)&slot_of_scratch, 4 * (size_t)n, s)) != cudaSuccess) return e;
+    std::vector<unsigned int> dh(kDegHist, 0);
+    {
+        unsigned int *hd = nullptr;
+        if ((e = cudaMallocAsync((void **)&hd, 4 * (size_t)kDegHist, s)) != cudaSuccess) return e;
+        cudaMemsetAsync(hd, 0, 4 * (size_t)kDegHist, s);
+        k_degree_hist<<<grid, 256, 0, s>>>(g.off, n, hd);
+        cudaMemcpyAsync(dh.data(), hd, 4 * (size_t)kDegHist, cudaMemcpyDeviceToHost, s);
+        cudaFreeAsync(hd, s);
+        if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+    }
     int64_t D = 0;
-    if ((e = degree_threshold(g, kHubs, cnt, grid, s, &D)) != cudaSuccess) return e;
+    if ((e = degree_threshold(g, kHubs, dh, cnt, grid, s, &D)) != cudaSuccess) return e;
     k_hub_flags<<<grid, 256, 0, s>>>(g.off, n, D, flag);
     int64_t *total = tmp + ntmp;
     if ((e = scan_exclusive_i64(flag, n, total, tmp, s)) != cudaSuccess) return e;
@@ -470,7 +517,7 @@ cudaError_t build_orientation(GraphDev &g, cudaStream_t s, int full, int32_t *er
     int64_t n_hot = 0;
     if (n < (int64_t)kHotBit && kHot > 0) {
         int64_t Dh = 0;
-        if ((e = degree_threshold(g, kHot, cnt, grid, s, &Dh)) != cudaSuccess) return e;
+        if ((e = degree_threshold(g, kHot, dh, cnt, grid, s, &Dh)) != cudaSuccess) return e;
         if ((e = cudaMallocAsync((void **)&hot_of, 4 * (size_t)n, s)) != cudaSuccess) return e;
         k_hub_flags<<<grid, 256, 0, s>>>(g.off, n, Dh, flag);
         if ((e = scan_exclusive_i64(flag, n, total, tmp, s)) != cudaSuccess) return e;
