@@ -283,7 +283,8 @@ int dsg_server_wait(dsg_server *s, uint64_t ticket, int64_t timeout_ms, dsg_serv
 int dsg_server_stats(dsg_server *s, int64_t *queued, int64_t *running, int64_t *done,
                      int64_t *bytes_in_use, int64_t *budget);
 
-/* Stop the workers (running requests finish, queued ones are dropped). */
+/* Stop the workers (running requests finish, queued ones are dropped) and
+ * free the server.  No other call on this server may be in flight. */
 void dsg_server_destroy(dsg_server *s);
 
 /* ---- instrumentation ---------------------------------------------------- */

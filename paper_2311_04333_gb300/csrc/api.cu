@@ -823,7 +823,7 @@ int dsg_run_pruned(dsg_graph *G, int variant, int32_t T, int64_t eps_num, int64_
         return code;
     };
     cudaError_t e;
-    CK(cudaMemsetAsync(loads_all, 0, 8 * (size_t)n, s), "memset");
+    if ((e = cudaMemsetAsync(loads_all, 0, 8 * (size_t)n, s)) != cudaSuccess) return finish(cuda_fail(ctx, e, "memset"));
     // Alg. 1 lines 1-4: k_max, L = ceil(k_max / 2), G <- L-core, S <- G.
     // Only cores of level >= ceil(k_max / 2) are ever used, and they lie in
     // H = G[deg >= k_low] for the bound k_low <= ceil(k_max / 2).  k_max is
