@@ -418,8 +418,10 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "i64",
         "data": "synthetic",
-        "config": {"workload": f"rmat{SAMPLE_SCALE - 1}_ef{EDGE_FACTOR} PaRSorting++ sample",
-                   "T": T},
+        "config": {"workload": f"rmat{SCALE}_ef{EDGE_FACTOR}_seed{SEED}+10blocks({BLOCKS[0]}..{BLOCKS[-1]},p=1/2)",
+                   "variant": "PaRSorting++", "T": T_ITERS,
+                   "sample": f"each step: rmat{SAMPLE_SCALE - 1}_ef{EDGE_FACTOR}, PaRSorting++ T={T} "
+                             "(the same recipe, bounded to run on the host cores)"},
         "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
     return 0
