@@ -186,6 +186,21 @@ def cpu_baseline(budget_s: float = 20.0) -> dict:
                       f"m={g.m}, PaRSorting++ T={T}, {dt:.1f} s, sequential C oracle"}
 
 
+def cpu_parallel_baseline(T: int = 5) -> dict:
+    """A separately written OpenMP PaRSorting++ (exact, parity-tested
+    against the oracle) on all host cores, on the same bounded sample."""
+    import cpu_baseline as cb
+    import graphgen as gg
+    g = gg.rmat(SAMPLE_SCALE, EDGE_FACTOR, SEED)
+    nt = cb.threads()
+    cb.run(g, 1, nt)
+    t0 = time.perf_counter()
+    cb.run(g, T, nt)
+    dt = time.perf_counter() - t0
+    return {"value": g.m * T / dt / 1e9, "unit": UNIT, "cores": nt, "kind": "openmp",
+            "sample": f"R-MAT scale {SAMPLE_SCALE}, n={g.n}, m={g.m}, PaRSorting++ T={T}, {dt:.2f} s"}
+
+
 def bench_batch(dsg, ctx, graphs, args) -> dict:
     """Graphs/s of the batched launch (autotuned block size) against one
     dsg_run per graph on the same GPU, with identical per-graph results."""
@@ -573,9 +588,10 @@ def main():
     if not args.no_serve:
         serving = bench_serving(dsg, serve_pool, local, args)
 
-    cpu = None
+    cpu = cpu_par = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline()
+        cpu_par = cpu_parallel_baseline()
     if rank == 0:
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -600,6 +616,7 @@ def main():
                        "sort_gbs": sort_bytes / (sort_ms * 1e-3) / 1e9 if sort_ms else None,
                        "other_ms": st["other"]["ms"] / (args.steps * T)},
             "cpu_baseline": cpu,
+            "cpu_parallel_baseline": cpu_par,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "steps": args.e2e_steps},
             "gpu_launches": launches,
