@@ -350,9 +350,9 @@ def bench_rmat20(dsg, ctx, gg, stream, args) -> dict:
 
 def bench_serving(dsg, pool, device, args) -> dict:
     """The native request loop under Poisson arrivals: capacity from a
-    closed burst of the whole request pool, then an open-loop run at 70% of
-    that capacity; latency percentiles are per request, submit to results on
-    the host."""
+    closed burst of four rounds of the request pool, then an open-loop run at
+    70% of that capacity; latency percentiles are per request, submit to
+    results on the host."""
     import numpy as np
     from paper_2311_04333_gb300 import serve
     srv = dsg.dsg_server_create(device, args.serve_slots, 0)
@@ -360,11 +360,14 @@ def bench_serving(dsg, pool, device, args) -> dict:
         rng = np.random.default_rng(SERVE_SEED)
         burst = []
         t0 = time.perf_counter()
-        for g in pool:
-            burst.append(dsg.dsg_server_submit(srv, g.n, g.off, g.adj, int(rng.integers(2)),
-                                               int(rng.choice([8, 16, 32])), 1, int(rng.choice([10, 100]))))
+        # a closed burst of 4 rounds of the pool, so that the slowest request
+        # does not set the capacity alone
+        for _ in range(4):
+            for g in pool:
+                burst.append(dsg.dsg_server_submit(srv, g.n, g.off, g.adj, int(rng.integers(2)),
+                                                   int(rng.choice([8, 16, 32])), 1, int(rng.choice([10, 100]))))
         ok = all(dsg.dsg_server_wait(srv, tk)["status"] == 0 for tk in burst)
-        cap = len(pool) / (time.perf_counter() - t0)
+        cap = len(burst) / (time.perf_counter() - t0)
         rate = 0.7 * cap
         res = serve.poisson_run(srv, pool, rate, args.serve_seconds, warmup=1.0, seed=SERVE_SEED)
     finally:

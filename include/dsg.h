@@ -248,7 +248,7 @@ typedef struct {
     int32_t best_iter;       /* as in dsg_result */
     int64_t best_edges, best_vertices, best_set_size;
     int64_t n, m;
-    int32_t slot;            /* worker that ran it */
+    int32_t slot;            /* worker that ran it (== slots: the batch worker) */
     double queue_ms;         /* submit -> admitted to a slot */
     double run_ms;           /* admitted -> results on the host */
     double latency_ms;       /* submit -> results on the host */
@@ -260,7 +260,10 @@ typedef struct {
  * device memory).  A request is admitted, in arrival order, when a worker is
  * free and its device-memory estimate (about 24m + 128n bytes) fits what the
  * running requests leave of the budget; admitted requests run concurrently
- * on the GPU, and each gives exactly what dsg_run gives on it alone. */
+ * on the GPU.  Requests on graphs of at most 32,768 vertices and 2^20 arcs
+ * go to one more worker instead, which runs all of them queued at the time
+ * it is free as one batch (dsg_run_batch), and so on.  Every request gives
+ * exactly what dsg_run gives on it alone. */
 int dsg_server_create(int device, int32_t slots, int64_t hbm_budget_bytes, dsg_server **out);
 
 /* Queue one request: a host CSR graph (copied; same rules as dsg_upload_csr),

@@ -10,6 +10,14 @@
 // up, and the work of different slots overlaps on the device.  Every request
 // runs exactly the computation dsg_run performs on it alone.
 //
+// Compact requests (graphs that dsg_run would give to a single thread block)
+// bypass the slots: one more worker gathers every compact request queued at
+// the time it is free (up to kMaxBatch, within the budget) and runs them as
+// one batch (dsg_upload_batch / dsg_run_batch, one launch per variant),
+// then picks up the next ones -- continuous batching.  A batch that fails
+// as a whole (a malformed graph, a load overflow) is rerun one request at a
+// time, so a bad request fails alone.
+//
 // PaRGreedy++ on a large graph is one cooperative launch whose blocks meet
 // at grid-wide barriers; each such block needs an SM of its own.  Each slot
 // caps that grid at (SM count / slots) blocks, so the grids of all slots fit
@@ -76,7 +84,9 @@ struct dsg_server {
     int64_t n_queued = 0, n_running = 0, n_done = 0;
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
-    std::deque<Request *> queue;
+    std::deque<Request *> queue;     // requests for the slots
+    std::deque<Request *> cqueue;    // compact requests for the batch worker
+    int n_slots = 0;
     std::unordered_map<uint64_t, Request *> reqs;
     std::vector<std::thread> workers;
     std::vector<cudaStream_t> streams;
@@ -104,6 +114,110 @@ void run_request(dsg_server *s, dsg_ctx *ctx, Request *r)
     else r->set.resize((size_t)r->res.best_set_size);
 }
 
+constexpr size_t kMaxBatch = 1024;
+
+// one batched run of compact requests of one variant; false if the batch
+// failed as a whole
+bool run_batch_group(dsg_ctx *ctx, int variant, const std::vector<Request *> &grp)
+{
+    const int32_t G = (int32_t)grp.size();
+    std::vector<int64_t> n_per(G), p(G), q(G);
+    std::vector<const int64_t *> offs(G);
+    std::vector<const int32_t *> adjs(G);
+    std::vector<int32_t> T(G);
+    static const int32_t no_arcs = 0;
+    int64_t N = 0;
+    for (int32_t g = 0; g < G; ++g) {
+        Request *r = grp[g];
+        n_per[g] = r->n;
+        offs[g] = r->off.data();
+        adjs[g] = r->adj.empty() ? &no_arcs : r->adj.data();
+        T[g] = r->T;
+        p[g] = r->p;
+        q[g] = r->q;
+        N += r->n;
+    }
+    dsg_batch *b = nullptr;
+    if (dsg_upload_batch(ctx, G, n_per.data(), offs.data(), adjs.data(), DSG_VALIDATE, &b) != DSG_OK) return false;
+    std::vector<int64_t> best(4 * (size_t)G), loads((size_t)N);
+    std::vector<int32_t> sets((size_t)N);
+    dsg_batch_result out{};
+    out.flags = 0;
+    out.best = best.data();
+    out.loads = loads.data();
+    out.sets = sets.data();
+    const int rc = dsg_run_batch(b, variant, T.data(), p.data(), q.data(), 0, &out);
+    dsg_free_batch(b);
+    if (rc != DSG_OK) return false;
+    int64_t vb = 0;
+    for (int32_t g = 0; g < G; ++g) {
+        Request *r = grp[g];
+        r->res.best_edges = best[4 * g];
+        r->res.best_vertices = best[4 * g + 1];
+        r->res.best_iter = (int32_t)best[4 * g + 2];
+        r->res.best_set_size = best[4 * g + 3];
+        r->loads.assign(loads.begin() + vb, loads.begin() + vb + r->n);
+        r->set.assign(sets.begin() + vb, sets.begin() + vb + r->res.best_set_size);
+        r->status = DSG_OK;
+        vb += r->n;
+    }
+    return true;
+}
+
+void finish_requests(dsg_server *s, const std::vector<Request *> &rs)
+{
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        for (Request *r : rs) {
+            r->t_end = clock_type::now();
+            r->done = true;
+            std::vector<int64_t>().swap(r->off);
+            std::vector<int32_t>().swap(r->adj);
+            s->in_use -= r->bytes;
+            --s->n_running;
+            ++s->n_done;
+        }
+    }
+    s->cv_done.notify_all();
+    s->cv_work.notify_all();
+}
+
+void batch_loop(dsg_server *s)
+{
+    cudaSetDevice(s->device);
+    dsg_ctx *ctx = s->ctxs[s->n_slots];
+    for (;;) {
+        std::vector<Request *> batch;
+        {
+            std::unique_lock<std::mutex> lk(s->mu);
+            s->cv_work.wait(lk, [&] {
+                return s->stop || (!s->cqueue.empty() && s->in_use + s->cqueue.front()->bytes <= s->budget);
+            });
+            if (s->stop) return;
+            while (!s->cqueue.empty() && batch.size() < kMaxBatch &&
+                   s->in_use + s->cqueue.front()->bytes <= s->budget) {
+                Request *r = s->cqueue.front();
+                s->cqueue.pop_front();
+                s->in_use += r->bytes;
+                --s->n_queued;
+                ++s->n_running;
+                r->t_start = clock_type::now();
+                r->slot = s->n_slots;
+                batch.push_back(r);
+            }
+        }
+        for (int variant : {DSG_SORTING, DSG_PEELING}) {
+            std::vector<Request *> grp;
+            for (Request *r : batch)
+                if (r->variant == variant) grp.push_back(r);
+            if (grp.empty()) continue;
+            if (!run_batch_group(ctx, variant, grp))
+                for (Request *r : grp) run_request(s, ctx, r);
+        }
+        finish_requests(s, batch);
+    }
+}
+
 void worker_loop(dsg_server *s, int slot)
 {
     cudaSetDevice(s->device);
@@ -125,19 +239,7 @@ void worker_loop(dsg_server *s, int slot)
             r->slot = slot;
         }
         run_request(s, s->ctxs[slot], r);
-        {
-            std::lock_guard<std::mutex> lk(s->mu);
-            r->t_end = clock_type::now();
-            r->done = true;
-            // the graph's arrays are no longer needed
-            std::vector<int64_t>().swap(r->off);
-            std::vector<int32_t>().swap(r->adj);
-            s->in_use -= r->bytes;
-            --s->n_running;
-            ++s->n_done;
-        }
-        s->cv_done.notify_all();
-        s->cv_work.notify_all();
+        finish_requests(s, {r});
     }
 }
 
@@ -161,7 +263,8 @@ int dsg_server_create(int device, int32_t slots, int64_t hbm_budget_bytes, dsg_s
         delete s;
         return DSG_ERR_CUDA;
     }
-    for (int i = 0; i < slots; ++i) {
+    s->n_slots = slots;
+    for (int i = 0; i <= slots; ++i) {       // slots, then the batch worker
         cudaStream_t st;
         dsg_ctx *c = nullptr;
         if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
@@ -179,6 +282,7 @@ int dsg_server_create(int device, int32_t slots, int64_t hbm_budget_bytes, dsg_s
         s->ctxs.push_back(c);
     }
     for (int i = 0; i < slots; ++i) s->workers.emplace_back(worker_loop, s, i);
+    s->workers.emplace_back(batch_loop, s);
     *out = s;
     return DSG_OK;
 }
@@ -211,11 +315,12 @@ int dsg_server_submit(dsg_server *s, int64_t n, const int64_t *offsets, const in
         r->id = s->next_id++;
         r->t_submit = clock_type::now();
         s->reqs[r->id] = r;
-        s->queue.push_back(r);
+        if (dsg::is_compact(r->n, arcs)) s->cqueue.push_back(r);
+        else s->queue.push_back(r);
         ++s->n_queued;
         *ticket = r->id;
     }
-    s->cv_work.notify_one();
+    s->cv_work.notify_all();
     return DSG_OK;
 }
 
