@@ -124,6 +124,10 @@ __device__ void block_radix_pass(const uint32_t *kin, const uint32_t *iin, const
 }
 
 constexpr uint32_t kNotPeeled = 0xffffffffu;
+#ifndef DSG_BATCH_THREAD_DEG
+#define DSG_BATCH_THREAD_DEG 32
+#endif
+constexpr int64_t kThreadDeg = DSG_BATCH_THREAD_DEG;   // lists shorter than this: one thread each
 constexpr int64_t kBlockScanDeg = 1024;  // F vertices above this degree: whole-block scan
 constexpr int kBigCap = 64;
 
@@ -296,10 +300,29 @@ k_batch_run(BatchDev B, uint32_t *graph_ctr)
                 range = rounds - 1;
                 src = R;
             } else {
-                // ---- edge scan: warp per vertex
+                // ---- edge scan: thread per vertex below kThreadDeg arcs
+                // (every lane busy on the many small lists), warp per vertex
+                // above
                 uint32_t lmn = 0xffffffffu, lmx = 0;
+                for (uint32_t u = threadIdx.x; u < n; u += NT) {
+                    const int64_t s = off[u], e = off[u + 1];
+                    const uint32_t lu = L[u];
+                    lmn = min(lmn, lu);
+                    lmx = max(lmx, lu);
+                    if (e - s >= kThreadDeg) continue;
+                    uint32_t c = 0;
+                    #pragma unroll 4
+                    for (int64_t j = s; j < e; ++j) {
+                        const uint32_t w = (uint32_t)adj[j];
+                        const uint32_t lw = L[w];
+                        c += (lw > lu) || (lw == lu && w > u);
+                    }
+                    A[u] = c;
+                    width = max(width, c);
+                }
                 for (uint32_t u = warp; u < n; u += NW) {
                     const int64_t s = off[u], e = off[u + 1];
+                    if (e - s < kThreadDeg) continue;
                     const uint32_t lu = L[u];
                     uint32_t c = 0;
                     for (int64_t j = s + lane; j < e; j += 32) {
@@ -310,8 +333,6 @@ k_batch_run(BatchDev B, uint32_t *graph_ctr)
                     c = __reduce_add_sync(kFull, c);
                     if (lane == 0) A[u] = c;
                     width = max(width, c);
-                    lmn = min(lmn, lu);
-                    lmx = max(lmx, lu);
                 }
                 width = block_reduce_u32<NT>(width, true, S);
                 lmin = block_reduce_u32<NT>(lmn, false, S);
