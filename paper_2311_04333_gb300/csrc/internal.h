@@ -143,14 +143,14 @@ struct RunBufs {
 int edge_scan_sm_count();
 // Default execution path of dsg_run.  Up to these sizes one thread block
 // carrying all T iterations (the kernel of the batched form, on one graph)
-// beats the whole-GPU kernels, whose cost there is launches and grid-wide
-// barriers: PaRGreedy++ up to 32,768 vertices and 2^20 arcs ("compact"
-// graphs, whose upload skips the whole-GPU structures), PaRSorting++ up to
-// 4,096 vertices and 2^17 arcs.
-constexpr int64_t kCompactN = 1 << 15;
-constexpr int64_t kCompactArcs = 1 << 20;
-constexpr int64_t kBlockSortN = 1 << 12;
-constexpr int64_t kBlockSortArcs = 1 << 17;
+// beats the whole-GPU kernels, whose cost there is launches, per-tile
+// latency and grid-wide barriers: 16,384 vertices and 2^19 arcs for
+// PaRGreedy++ ("compact" graphs, whose upload skips the whole-GPU
+// structures), 16,384 vertices and 2^18 arcs for PaRSorting++.
+constexpr int64_t kCompactN = 1 << 14;
+constexpr int64_t kCompactArcs = 1 << 19;
+constexpr int64_t kBlockSortN = 1 << 14;
+constexpr int64_t kBlockSortArcs = 1 << 18;
 inline bool is_compact(int64_t n, int64_t arcs) { return n <= kCompactN && arcs <= kCompactArcs; }
 // whole-GPU PaRSorting++ runs up to this many arcs are launched as one CUDA graph
 constexpr int64_t kGraphArcs = 1ll << 26;

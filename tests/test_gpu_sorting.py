@@ -232,7 +232,7 @@ def test_default_path_by_size(dsg, ctx, path):
     launch per run) and larger ones the whole-GPU kernels."""
     if path != PATHS["grid"]:
         pytest.skip("checked once")
-    cases = [(gg.er_m(3000, 8, 3), orc.SORTING, True), (gg.er_m(10000, 8, 3), orc.SORTING, False),
+    cases = [(gg.er_m(10000, 8, 3), orc.SORTING, True), (gg.er_m(20000, 8, 3), orc.SORTING, False),
              (gg.er_m(10000, 8, 3), orc.PEELING, True), (gg.er_m(70000, 4, 3), orc.PEELING, False)]
     for g, variant, one_launch in cases:
         gr = dsg.dsg_upload_csr(ctx, g.n, g.off, g.adj, 0)
