@@ -121,7 +121,7 @@ const char *dsg_last_error(const dsg_ctx *ctx);
  * With DSG_VALIDATE the library also checks that every list has no self-loop
  * and no repeated neighbour and that the graph is symmetric; otherwise the
  * caller guarantees it.  Lists need not be sorted.  The graph is copied to
- * device memory; a graph above 16,384 vertices or 2^19 arcs also gets the
+ * device memory; a graph above 32,768 vertices or 2^20 arcs also gets the
  * degree-oriented copy and tile schedule of the whole-GPU edge scan (a
  * smaller one gets them on its first run on the whole-GPU path).
  * Errors: DSG_ERR_INVALID for a malformed graph, DSG_ERR_NOMEM. */
@@ -260,7 +260,7 @@ typedef struct {
  * device memory).  A request is admitted, in arrival order, when a worker is
  * free and its device-memory estimate (about 24m + 128n bytes) fits what the
  * running requests leave of the budget; admitted requests run concurrently
- * on the GPU.  Requests on graphs of at most 16,384 vertices and 2^19 arcs
+ * on the GPU.  Requests on graphs of at most 32,768 vertices and 2^20 arcs
  * go to one more worker instead, which runs all of them queued at the time
  * it is free as one batch (dsg_run_batch), and so on.  Every request gives
  * exactly what dsg_run gives on it alone. */

@@ -141,22 +141,26 @@ struct RunBufs {
 };
 
 int edge_scan_sm_count();
+// "Compact" graphs (up to 32,768 vertices and 2^20 arcs): their upload
+// skips the whole-GPU structures until a whole-GPU run asks for them, and
+// the server runs them through the batched kernel, where one block per graph
+// is the most work per SM.
+constexpr int64_t kCompactN = 1 << 15;
+constexpr int64_t kCompactArcs = 1 << 20;
+inline bool is_compact(int64_t n, int64_t arcs) { return n <= kCompactN && arcs <= kCompactArcs; }
 // Default execution path of dsg_run.  Up to these sizes one thread block
 // carrying all T iterations (the kernel of the batched form, on one graph)
 // beats the whole-GPU kernels, whose cost there is launches, per-tile
-// latency and grid-wide barriers: 16,384 vertices and 2^19 arcs for
-// PaRGreedy++ ("compact" graphs, whose upload skips the whole-GPU
-// structures), 16,384 vertices and 2^18 arcs for PaRSorting++.
-constexpr int64_t kCompactN = 1 << 14;
-constexpr int64_t kCompactArcs = 1 << 19;
-constexpr int64_t kBlockSortN = 1 << 14;
+// latency and grid-wide barriers: 16,384 vertices for both variants, with
+// 2^18 arcs for PaRSorting++ and 2^19 for PaRGreedy++.
+constexpr int64_t kBlockN = 1 << 14;
 constexpr int64_t kBlockSortArcs = 1 << 18;
-inline bool is_compact(int64_t n, int64_t arcs) { return n <= kCompactN && arcs <= kCompactArcs; }
+constexpr int64_t kBlockPeelArcs = 1 << 19;
 // whole-GPU PaRSorting++ runs up to this many arcs are launched as one CUDA graph
 constexpr int64_t kGraphArcs = 1ll << 26;
 inline bool block_path_default(int variant, int64_t n, int64_t arcs)
 {
-    return variant == 1 ? is_compact(n, arcs) : (n <= kBlockSortN && arcs <= kBlockSortArcs);
+    return n <= kBlockN && arcs <= (variant == 1 ? kBlockPeelArcs : kBlockSortArcs);
 }
 
 // exclusive scan of int64[count] in place (tmp: scan_tmp_count(count)

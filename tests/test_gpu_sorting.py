@@ -228,12 +228,14 @@ def test_unsorted_adjacency_lists(dsg, ctx, path):
 
 
 def test_default_path_by_size(dsg, ctx, path):
-    """Without a path flag, compact graphs take the single-block kernel (one
-    launch per run) and larger ones the whole-GPU kernels."""
+    """Without a path flag, graphs up to 16,384 vertices take the single-block
+    kernel (one launch per run) and larger ones the whole-GPU kernels, which a
+    compact upload (up to 32,768 vertices) builds on first use."""
     if path != PATHS["grid"]:
         pytest.skip("checked once")
     cases = [(gg.er_m(10000, 8, 3), orc.SORTING, True), (gg.er_m(20000, 8, 3), orc.SORTING, False),
-             (gg.er_m(10000, 8, 3), orc.PEELING, True), (gg.er_m(70000, 4, 3), orc.PEELING, False)]
+             (gg.er_m(10000, 8, 3), orc.PEELING, True), (gg.er_m(20000, 8, 3), orc.PEELING, False),
+             (gg.er_m(70000, 4, 3), orc.PEELING, False)]
     for g, variant, one_launch in cases:
         gr = dsg.dsg_upload_csr(ctx, g.n, g.off, g.adj, 0)
         try:
