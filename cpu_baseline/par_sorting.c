@@ -6,12 +6,12 @@
  * library never calls it.
  *
  * Iteration t, loads l (by id):
- *   A[u] = #{w in N(u) : (l[w], w) > (l[u], u)}      (Alg. 3 lines 2-3)
+ *   A[u] = #{w in N(u) : (l[w], w) > (l[u], u)}      (Alg. 3, counts)
  *   order = ids sorted by (l, id): stable LSD radix sort on l - min l,
  *           8-bit digits, per-thread counts, scan, scatter
  *   B[i] = sum_{j >= i} A[order[j]]; first maximum of B[i] / (n - i)
- *           (Alg. 3 lines 4-7), kept if strictly denser than the best
- *   l += A                                            (Alg. 3 lines 8-9)
+ *           (Alg. 3, suffix densities), kept if strictly denser than the best
+ *   l += A                                            (Alg. 3, load update)
  * Exact integer arithmetic; densities compared by 128-bit cross products.
  */
 #include <omp.h>

@@ -8,9 +8,9 @@
  *                Sec. 3.3 "ParallelGreedySorting++"): each iteration orders
  *                the vertices by their load at the start of the iteration
  *                (ties by vertex id), gives every vertex the number of its
- *                neighbours later in the order (Alg. 3 lines 2-3), adds it
- *                to its load (Alg. 3 lines 8-9) and takes the densest suffix
- *                of the order (Alg. 3 lines 4-7).
+ *                neighbours later in the order (Alg. 3, counts), adds it
+ *                to its load (Alg. 3, load update) and takes the densest suffix
+ *                of the order (Alg. 3, suffix densities).
  *   DSG_PEELING  PaRGreedy++ refine step (Sec. 3.3 "ParallelGreedy++"): the
  *                order comes from bucketed peeling by l(v) + deg_H(v); each
  *                round peels every alive vertex whose key is within a factor
@@ -137,8 +137,8 @@ int dsg_graph_info(const dsg_graph *g, int64_t *n, int64_t *m, int64_t *max_degr
  * identical results.
  *   eps_num/eps_den: eps = p/q for DSG_PEELING (p >= 0, q >= 1, p+q < 2^31);
  *     ignored by DSG_SORTING;
- *   init_loads[n]: loads before iteration 1 (NULL: all zero, Alg. 2 lines
- *     1-2); host memory unless out->flags has DSG_INIT_DEVICE.  Passing the
+ *   init_loads[n]: loads before iteration 1 (NULL: all zero, as Alg. 2
+ *     starts); host memory unless out->flags has DSG_INIT_DEVICE.  Passing the
  *     loads of an earlier run resumes it: T1 then T2 iterations give the
  *     loads of T1 + T2 iterations.
  * Loads are kept as 32-bit unsigned integers on the device:
@@ -294,7 +294,7 @@ void dsg_server_destroy(dsg_server *s);
 
 /* Kernel phases timed when profiling is on (dsg_set_profiling). */
 typedef enum {
-    DSG_PHASE_EDGE_SCAN = 0,  /* later-neighbour counts (Alg. 3 lines 2-3) */
+    DSG_PHASE_EDGE_SCAN = 0,  /* later-neighbour counts (Alg. 3, counts) */
     DSG_PHASE_SORT = 1,       /* radix passes + fused densest suffix */
     DSG_PHASE_OTHER = 2,      /* plan, snapshot, best-set, peeling rounds */
     DSG_PHASE_COUNT = 3
@@ -324,8 +324,8 @@ int dsg_get_stats(dsg_ctx *ctx, double *ms, int64_t *launches, int64_t *bytes, i
  *
  * Given loads[n] and A[n] (device pointers, uint32, by vertex id) it orders
  * the vertices by (loads[v], v) and returns the first densest suffix of that
- * order, where a suffix's edge count is the sum of A over it (Alg. 3 lines
- * 4-7 with B = SuffixSum(A)).  When A is the later-neighbour count of the
+ * order, where a suffix's edge count is the sum of A over it (Alg. 3's
+ * suffix step with B = SuffixSum(A)).  When A is the later-neighbour count of the
  * order (the edge scan of dsg_run), m = sum(A) is the graph's edge count.
  *   m: sum of A[0..n-1] (the edges of the whole graph);
  *   result: device pointer to int64[5], written on `cuda_stream`:

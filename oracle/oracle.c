@@ -12,12 +12,12 @@
  * pairs compared by cross-multiplication in 128 bits.
  *
  * Structure (each function names the passage it follows):
- *   - ordering functions O (Alg. 2 line 6): sort by load (Sec. 3.2,
+ *   - ordering functions O (Alg. 2, order of each iteration): sort by load (Sec. 3.2,
  *     "GreedySorting++"), simultaneous round peeling (Sec. 3.3,
  *     "ParallelGreedy++"), and the one-at-a-time load ordering (Sec. 2,
  *     "load ordering"; Greedy++ proper);
  *   - the peel of one iteration in that order, one vertex at a time, exactly
- *     as Alg. 2 lines 7-11 state it (density check, load += induced degree at
+ *     as Alg. 2's inner loop states it (density check, load += induced degree at
  *     peel time, remove the vertex).  This is deliberately NOT Alg. 3's
  *     parallel A[min(j,k)] formulation, so the GPU's Alg. 3 path is checked
  *     against the sequential definition;
@@ -36,7 +36,7 @@
  *   - a round peels every alive v with key(v)*q <= min_key*(p+q), eps = p/q
  *     (eps = 0 is the paper's exact bucket peel of the minimum key only);
  *   - the best subgraph starts as S = G and is replaced only on a strictly
- *     higher density (Alg. 2 lines 5, 8-9), so ties keep the earliest
+ *     higher density (Alg. 2: S starts as G, strict test), so ties keep the earliest
  *     (iteration, position); the empty suffix is never a candidate.
  */
 #include <stdint.h>
@@ -158,7 +158,7 @@ int oracle_load_order(int64_t n, const int64_t *off, const int32_t *adj,
 }
 
 /* ------------------------------------------------------------------------ */
-/* One iteration of Alg. 2 lines 7-11 for a given order v_1..v_n, with H
+/* One iteration of Alg. 2's inner loop for a given order v_1..v_n, with H
  * reset to G: for j = 1..n, if rho(H) > rho(best) then best <- H; then
  * l(v_j) += deg*_H(v_j) (degree of v_j in H when it is peeled) and peel v_j.
  *
@@ -191,15 +191,15 @@ int oracle_peel_iteration(int64_t n, const int64_t *off, const int32_t *adj,
         int64_t v = order[j];
         /* this iteration's own densest suffix: first maximum */
         if (ij < 0 || density_gt(eH, vH, ie, iv)) { ie = eH; iv = vH; ij = j; }
-        /* Alg. 2 line 8: the running best, strict comparison */
+        /* Alg. 2: the running best, strict comparison */
         if (density_gt(eH, vH, *best_e, *best_v)) {
             *best_e = eH; *best_v = vH; *improved_at = j;
         }
         int64_t ds = deg[v];                 /* deg*_H(v_j) */
         degstar[j] = ds;
         if (ds > w) w = ds;
-        loads[v] += ds;                      /* Alg. 2 line 10 */
-        inH[v] = 0;                          /* Alg. 2 line 11 */
+        loads[v] += ds;                      /* Alg. 2: load update */
+        inH[v] = 0;                          /* Alg. 2: peel v */
         for (int64_t e = off[v]; e < off[v + 1]; ++e)
             if (inH[adj[e]]) deg[adj[e]] -= 1;
         eH -= ds;
@@ -216,7 +216,7 @@ int oracle_peel_iteration(int64_t n, const int64_t *off, const int32_t *adj,
  *   variant 0: GreedySorting++ order (PaRSorting++ refine step)
  *   variant 1: ParallelGreedy++ round order with eps = p/q (PaRGreedy++)
  *   variant 2: sequential Greedy++ load order
- * init_loads may be NULL (Alg. 2 lines 1-2: l = 0).  On return loads[n]
+ * init_loads may be NULL (Alg. 2 starts from l = 0).  On return loads[n]
  * holds the final loads, best_e/best_v/best_iter the best density (iteration
  * 0 means S = G was never beaten), set[] the best subgraph's vertex ids in
  * ascending order (set_size of them), and trace[3*t..3*t+2] (if not NULL)
@@ -239,7 +239,7 @@ int oracle_run(int64_t n, const int64_t *off, const int32_t *adj,
     }
     for (int64_t v = 0; v < n; ++v) loads[v] = init_loads ? init_loads[v] : 0;
     int64_t m = off[n] / 2;
-    int64_t be = m, bv = n, biter = 0, bpos = 0;        /* S <- G (Alg. 2 line 5) */
+    int64_t be = m, bv = n, biter = 0, bpos = 0;        /* S <- G (Alg. 2) */
     for (int64_t t = 1; t <= T; ++t) {
         memcpy(start, loads, sizeof(int64_t) * (size_t)n);
         if (variant == 0) oracle_sorting_order(n, start, order);
@@ -520,7 +520,7 @@ int oracle_coreness_by_deletion(int64_t n, const int64_t *off, const int32_t *ad
 /* ------------------------------------------------------------------------ */
 /* Pruning-and-Refining framework (Alg. 1, Sec. 4) with exact pruning.      */
 
-/* getCore (Alg. 1 lines 3 and 10): the subgraph of G induced on the vertices
+/* getCore (Alg. 1, initial and re-pruning): the subgraph of G induced on the vertices
  * with in[v] != 0, relabelled in increasing id (lists keep their order).
  * old_of[local] = original id.                                             */
 static int induced_subgraph(int64_t n, const int64_t *off, const int32_t *adj, const unsigned char *in,
@@ -598,15 +598,15 @@ int oracle_run_pruned(int64_t n, const int64_t *off, const int32_t *adj, int var
     if (rc != OR_OK) { free(core); free(in); return rc; }
     int64_t kmax = 0;
     for (int64_t v = 0; v < n; ++v) if (core[v] > kmax) kmax = core[v];
-    int64_t Ln = ceil_div(kmax, 2), Ld = 1;              /* Alg. 1 line 2 */
+    int64_t Ln = ceil_div(kmax, 2), Ld = 1;              /* Alg. 1: L = ceil(k_max / 2) */
     int64_t level = Ln;
     for (int64_t v = 0; v < n; ++v) in[v] = core[v] >= level;
     int64_t cn = 0, *coff = NULL, *old_of = NULL;
     int32_t *cadj = NULL;
-    rc = induced_subgraph(n, off, adj, in, &cn, &coff, &cadj, &old_of);   /* line 3 */
+    rc = induced_subgraph(n, off, adj, in, &cn, &coff, &cadj, &old_of);   /* G <- L-core */
     if (rc != OR_OK) { free(core); free(in); return rc; }
     for (int64_t v = 0; v < n; ++v) loads[v] = 0;
-    int64_t se = coff[cn] / 2, sv = cn, biter = 0, ssize = cn;          /* line 4: S <- G */
+    int64_t se = coff[cn] / 2, sv = cn, biter = 0, ssize = cn;          /* S <- G */
     for (int64_t i = 0; i < cn; ++i) set[i] = old_of[i];
     if (info) { info[0] = kmax; info[1] = cn; info[2] = coff[cn] / 2; }
     int64_t *cl = calloc((size_t)(cn > 0 ? cn : 1), sizeof(int64_t));
@@ -615,17 +615,17 @@ int oracle_run_pruned(int64_t n, const int64_t *off, const int32_t *adj, int var
     int64_t b[5], tr[3];
     if (!cl || !nl || !lset) { rc = OR_ERR_NOMEM; goto done; }
     for (int64_t t = 1; t <= T && cn > 0; ++t) {
-        rc = oracle_run(cn, coff, cadj, variant, 1, p, q, cl, nl, b, lset, tr);   /* line 6 */
+        rc = oracle_run(cn, coff, cadj, variant, 1, p, q, cl, nl, b, lset, tr);   /* one refine iteration */
         if (rc != OR_OK) goto done;
         memcpy(cl, nl, sizeof(int64_t) * (size_t)cn);
         if (trace) { trace[3 * (t - 1)] = b[0]; trace[3 * (t - 1) + 1] = b[1]; trace[3 * (t - 1) + 2] = cn; }
-        if (!density_gt(b[0], b[1], se, sv)) continue;                      /* line 7 */
-        se = b[0]; sv = b[1]; biter = t; ssize = b[3];                       /* line 8 */
+        if (!density_gt(b[0], b[1], se, sv)) continue;                      /* strictly denser? */
+        se = b[0]; sv = b[1]; biter = t; ssize = b[3];                       /* S <- S' */
         for (int64_t i = 0; i < ssize; ++i) set[i] = old_of[lset[i]];
-        if (density_gt(se, sv, Ln, Ld)) { Ln = se; Ld = sv; }                /* line 9 */
+        if (density_gt(se, sv, Ln, Ld)) { Ln = se; Ld = sv; }                /* raise L */
         int64_t nlevel = ceil_div(Ln, Ld);
         if (nlevel <= level) continue;
-        level = nlevel;                                                      /* line 10 */
+        level = nlevel;                                                      /* re-prune */
         unsigned char *cin = malloc((size_t)cn);
         if (!cin) { rc = OR_ERR_NOMEM; goto done; }
         for (int64_t i = 0; i < cn; ++i) {

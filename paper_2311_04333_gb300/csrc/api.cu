@@ -824,7 +824,7 @@ int dsg_run_pruned(dsg_graph *G, int variant, int32_t T, int64_t eps_num, int64_
     };
     cudaError_t e;
     if ((e = cudaMemsetAsync(loads_all, 0, 8 * (size_t)n, s)) != cudaSuccess) return finish(cuda_fail(ctx, e, "memset"));
-    // Alg. 1 lines 1-4: k_max, L = ceil(k_max / 2), G <- L-core, S <- G.
+    // Alg. 1 set-up: k_max, L = ceil(k_max / 2), G <- L-core, S <- G.
     // Only cores of level >= ceil(k_max / 2) are ever used, and they lie in
     // H = G[deg >= k_low] for the bound k_low <= ceil(k_max / 2).  k_max is
     // the largest k whose k-core of H (by deletion) is not empty; each core
@@ -910,7 +910,7 @@ int dsg_run_pruned(dsg_graph *G, int variant, int32_t T, int64_t eps_num, int64_
     }
     if ((rc = dsg_upload_csr(ctx, cur.n, cur.off, cur.adj, DSG_SRC_DEVICE, &cg)) != DSG_OK) return done_k(rc);
     for (int32_t t = 1; t <= T; ++t) {
-        // line 6: one iteration of the refine step on the current core,
+        // Alg. 1 loop: one iteration of the refine step on the current core,
         // continuing its vertices' loads
         dsg_result r{};
         r.flags = DSG_DST_DEVICE | DSG_INIT_DEVICE;
@@ -922,7 +922,7 @@ int dsg_run_pruned(dsg_graph *G, int variant, int32_t T, int64_t eps_num, int64_
         trace[3 * (t - 1)] = r.best_edges;
         trace[3 * (t - 1) + 1] = r.best_vertices;
         trace[3 * (t - 1) + 2] = cur.n;
-        // lines 7-10: keep a strictly denser result, raise L, re-prune
+        // then keep a strictly denser result, raise L, re-prune
         if (!dens_gt_host(r.best_edges, r.best_vertices, se, sv)) continue;
         se = r.best_edges;
         sv = r.best_vertices;

@@ -11,8 +11,8 @@
 //              digits); the block's warps own contiguous segments: count,
 //              scan in (digit, warp) order, ranked scatter
 //   suffix     B[i] = sum_{j >= i} A[v_j]; first maximum of B[i] / (n - i)
-//              (Alg. 3 lines 4-7); strict update of the graph's best (Alg. 2)
-//   loads      l += A (Alg. 3 lines 8-9; PaRGreedy++ adds each count as its
+//              (Alg. 3, suffix densities); strict update of the graph's best (Alg. 2)
+//   loads      l += A (Alg. 3, load update; PaRGreedy++ adds each count as its
 //              vertex is peeled)
 // and finally extracts the best vertex set.  Graph g owns vertices
 // [vbase[g], vbase[g+1]) and arcs [off[vbase[g]], off[vbase[g+1]]) of the
@@ -161,7 +161,7 @@ __device__ __forceinline__ uint32_t warp_claim(bool pred, uint32_t *cnt)
 // F = {alive v : (l(v) + deg_H(v)) * q <= min * (p + q)}; the decrements of
 // deg_H caused by F are applied after F is fixed.  Fused with the count of
 // later neighbours in the (round, id) order: A[v] = alive neighbours not in
-// F, plus neighbours in F with a larger id; l(v) += A[v] (Alg. 3 lines 8-9).
+// F, plus neighbours in F with a larger id; l(v) += A[v] (Alg. 3, load update).
 // R[v] receives v's round; returns the number of rounds.
 template <int NT>
 __device__ uint32_t block_peel(const int64_t *off, const int32_t *adj, uint32_t n, uint64_t p, uint64_t q,

@@ -23,7 +23,7 @@
 // or 65,536 of their arcs, whichever needs more), down to a single block
 // that rounds with block barriers only.
 // The densest suffix of the (round, id) order then reuses the radix passes
-// of the sorting path with key = round and value = A (Alg. 3 lines 4-7).
+// of the sorting path with key = round and value = A (Alg. 3, suffix densities).
 #include <mutex>
 
 #include "common.cuh"

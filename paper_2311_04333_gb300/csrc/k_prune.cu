@@ -1,5 +1,5 @@
 // k_prune.cu -- getCore of the Pruning-and-Refining framework (arXiv
-// 2311.04333, Alg. 1 lines 3 and 10): the subgraph induced on the vertices
+// 2311.04333, Alg. 1, initial and re-pruning): the subgraph induced on the vertices
 // whose core number (in the input graph) reaches a level, relabelled in
 // increasing id so that every list stays in its order, with the maps that
 // carry loads and ids across the relabelling.

@@ -8,15 +8,15 @@
 //   edge scan  : A[u] = #{w in N(u) : (l_t[w], w) > (l_t[u], u)}, the number
 //                of neighbours of u later in the (load, id) order.  Because
 //                this comparison does not depend on the sorted positions it
-//                runs before the sort (Alg. 3 lines 2-3 without ranks).
+//                runs before the sort (Alg. 3's counts, without ranks).
 //                Also builds the digit histograms of the sort and the
 //                per-digit sums of A used by the fused scan.
 //   radix pass : stable LSD onesweep passes over (key = l_t, value = A) with
 //                decoupled look-back; pass 0 also writes l_{t+1} = l_t + A
-//                (Alg. 3 lines 8-9).  The LAST pass does not scatter: it
+//                (Alg. 3, load update).  The LAST pass does not scatter: it
 //                obtains every element's final position i and its prefix sum
 //                of A from the look-back, so the suffix (n - i vertices,
-//                m - prefix edges) of Alg. 3 lines 4-7 is evaluated in place
+//                m - prefix edges) of Alg. 3's suffix step is evaluated in place
 //                and reduced to the iteration's first densest suffix.
 //   snapshot   : when the iteration beat the best, keeps l_t for the set.
 #include <mutex>
@@ -571,7 +571,7 @@ __device__ __forceinline__ unsigned long long status_word(uint32_t epoch, uint64
 // publish its per-digit counts (and, in the last pass, value sums) at once,
 // sort locally in shared memory, then resolve its global offsets by
 // decoupled look-back.  Non-last passes scatter; the last pass evaluates the
-// suffix starting at every element's final position (Alg. 3 lines 4-7).
+// suffix starting at every element's final position (Alg. 3, suffix densities).
 __global__ void __launch_bounds__(kPassThreads, DSG_PASS_MINBLOCKS)
 k_radix_pass(const uint32_t *kin, const uint32_t *vin,
              uint32_t *__restrict__ kout, uint32_t *__restrict__ vout,
@@ -819,7 +819,7 @@ k_radix_pass(const uint32_t *kin, const uint32_t *vin,
         return;
     }
 
-    // ---- final pass: evaluate every suffix (Alg. 3 lines 4-7) without scattering
+    // ---- final pass: evaluate every suffix (Alg. 3, suffix densities) without scattering
     Candidate best{0, 0, 0, 0};
     uint64_t run = chunk_ex;
     #pragma unroll

@@ -26,7 +26,7 @@ MUTANTS = {
     "round_decrement_immediate_skip": ("if (state[adj[e]] == 0) deg[adj[e]] -= 1;", ";"),
     "best_set_off_by_one": ("for (int64_t j = bpos; j < n; ++j) in[border[j]] = 1;",
                             "for (int64_t j = bpos + 1; j < n; ++j) in[border[j]] = 1;"),
-    "load_update_dropped": ("loads[v] += ds;                      /* Alg. 2 line 10 */", ";"),
+    "load_update_dropped": ("loads[v] += ds;                      /* Alg. 2: load update */", ";"),
     "iteration_best_last_max": ("if (ij < 0 || density_gt(eH, vH, ie, iv))",
                                 "if (ij < 0 || !density_gt(ie, iv, eH, vH))"),
     "bz_nonstrict": ("if (deg[u] > deg[v]) {", "if (deg[u] >= deg[v]) {"),

@@ -119,13 +119,13 @@ def test_sorting_order_is_load_then_id(seed):
 def _check_iteration(g, order, loads_in, out):
     pos = np.empty(g.n, dtype=np.int64)
     pos[order] = np.arange(g.n)
-    # deg*_H(v_j) = number of neighbours later in the order (Alg. 3 lines 2-3)
+    # deg*_H(v_j) = number of neighbours later in the order (Alg. 3, counts)
     later = np.zeros(g.n, dtype=np.int64)
     for a, b in _edges(g):
         later[min(pos[a], pos[b])] += 1
     assert (out["degstar"] == later).all()
     assert int(out["degstar"].sum()) == g.m
-    # loads: l(v_j) += A[j]  (Alg. 3 lines 8-9)
+    # loads: l(v_j) += A[j]  (Alg. 3, load update)
     exp = np.array(loads_in, dtype=np.int64).copy()
     exp[order] += later
     assert (out["loads"] == exp).all()
