@@ -51,7 +51,7 @@ __device__ __forceinline__ bool dens_gt(uint64_t e1, uint64_t v1, uint64_t e2, u
 }
 
 // candidate order: higher density first, then the earlier position (the
-// larger suffix), i.e. the first maximum of Alg. 3 line 7 in order.
+// larger suffix), i.e. the first maximum of the suffix densities in order.
 __device__ __forceinline__ bool cand_better(const Candidate &a, const Candidate &b)
 {
     if (a.v <= 0) return false;

@@ -565,6 +565,16 @@ __device__ __forceinline__ unsigned long long status_word(uint32_t epoch, uint64
 {
     return ((unsigned long long)epoch << 48) | (flag << 46) | (cnt & ((1ull << 46) - 1));
 }
+// value sums of the last pass carry the epoch in their top 16 bits, so a
+// reader that sees a tile's status word before its sum can tell a stale sum
+// (sums stay below m < 2^48)
+constexpr unsigned long long kSumMask = (1ull << 48) - 1;
+__device__ __forceinline__ unsigned long long sum_word(uint32_t epoch, uint64_t sum)
+{
+    return ((unsigned long long)epoch << 48) | (sum & kSumMask);
+}
+// tiles whose status words one look-back step loads at once
+constexpr int kLookWin = 8;
 
 // One LSD pass (digit k of key - lmin) over (key, value) pairs, stable.
 // Each tile of kPassTile elements: load, rank within warps by match.any,
@@ -584,6 +594,10 @@ k_radix_pass(const uint32_t *kin, const uint32_t *vin,
     const int np = ctl->npass;
     if (k >= np) return;
     const bool last = (k == np - 1);
+    if (last && ((uint64_t)m >> 48)) {      // sums must fit the tagged words (every block returns)
+        if (threadIdx.x == 0 && blockIdx.x == 0) set_error(ctl, 3, 400 + k);
+        return;
+    }
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t lmin = ctl->lmin;
     const int shift = ctl->shift[k];
@@ -693,11 +707,11 @@ k_radix_pass(const uint32_t *kin, const uint32_t *vin,
     unsigned long long *st = status + (int64_t)tile * kBuckets + d;
     unsigned long long *ss = status_sum + 2 * ((int64_t)tile * kBuckets + d);
     if (tile == 0) {
-        if (last) st_relaxed(ss + 1, tsum);
-        st_release(st, status_word(epoch, kFlagIncl, tcount));
+        if (last) st_relaxed(ss + 1, sum_word(epoch, tsum));
+        st_relaxed(st, status_word(epoch, kFlagIncl, tcount));
     } else {
-        if (last) st_relaxed(ss, tsum);
-        st_release(st, status_word(epoch, kFlagAgg, tcount));
+        if (last) st_relaxed(ss, sum_word(epoch, tsum));
+        st_relaxed(st, status_word(epoch, kFlagAgg, tcount));
     }
     if (acc) {
         amax = __reduce_max_sync(kFull, amax);
@@ -759,34 +773,69 @@ k_radix_pass(const uint32_t *kin, const uint32_t *vin,
         }
     }
 
-    // ---- decoupled look-back: thread d resolves digit d
+    // ---- decoupled look-back: thread d resolves digit d.  Every status word
+    // carries its own count and every sum its own epoch, so the words need no
+    // ordering among themselves: each step loads the words (and sums) of
+    // kLookWin predecessors at once and consumes them in order up to the
+    // first inclusive one, or up to one not yet published (then reloads).
     {
         uint64_t excl = 0, excl_sum = 0;
         bool abort = false;
         if (tile > 0) {
             int64_t j = (int64_t)tile - 1;
             uint32_t polls = 0, ns = 8;
-            while (j >= 0) {
-                const unsigned long long w = ld_acquire(status + j * kBuckets + d);
-                const uint32_t ep = (uint32_t)(w >> 48);
-                const uint32_t fl = (uint32_t)((w >> 46) & 3u);
-                if (ep != epoch || fl == 0) {
+            bool done = false;
+            while (!done) {
+                unsigned long long wv[kLookWin], sv[kLookWin];
+                #pragma unroll
+                for (int q = 0; q < kLookWin; ++q) {
+                    const int64_t jj = j - q;
+                    wv[q] = jj >= 0 ? ld_relaxed(status + jj * kBuckets + d) : 0ull;
+                }
+                if (last) {
+                    // the sum slot a word's flag selects: aggregate [0], inclusive [1]
+                    #pragma unroll
+                    for (int q = 0; q < kLookWin; ++q) {
+                        const int64_t jj = j - q;
+                        const uint32_t fl = (uint32_t)((wv[q] >> 46) & 3u);
+                        sv[q] = jj >= 0 ? ld_relaxed(status_sum + 2 * (jj * kBuckets + d) + (fl == kFlagIncl ? 1 : 0))
+                                        : 0ull;
+                    }
+                }
+                int used = 0;
+                bool blocked = false;
+                #pragma unroll
+                for (int q = 0; q < kLookWin; ++q) {
+                    if (done || blocked || j - q < 0) continue;
+                    const unsigned long long w = wv[q];
+                    const uint32_t ep = (uint32_t)(w >> 48);
+                    const uint32_t fl = (uint32_t)((w >> 46) & 3u);
+                    if (ep != epoch || fl == 0) { blocked = true; continue; }
+                    if (fl == kFlagAbort) { abort = true; done = true; continue; }
+                    if (last && (uint32_t)(sv[q] >> 48) != epoch) { blocked = true; continue; }
+                    excl += w & ((1ull << 46) - 1);
+                    if (last) excl_sum += sv[q] & kSumMask;
+                    ++used;
+                    if (fl == kFlagIncl) done = true;
+                }
+                j -= used;
+                if (done) break;
+                if (j < 0) {                 // tile 0 is always inclusive: unreachable
+                    abort = true;
+                    set_error(ctl, 5, 200 + k);
+                    break;
+                }
+                if (used == 0) {
                     if (++polls > kSpinLimit) { abort = true; set_error(ctl, 5, 100 + k); break; }
                     __nanosleep(ns);
                     if (ns < 256) ns <<= 1;
-                    continue;
                 }
-                if (fl == kFlagAbort) { abort = true; break; }
-                excl += w & ((1ull << 46) - 1);
-                if (last) excl_sum += ld_relaxed(status_sum + 2 * (j * kBuckets + d) + (fl == kFlagIncl ? 1 : 0));
-                if (fl == kFlagIncl) break;
-                --j;
             }
             if (abort) {
-                st_release(st, status_word(epoch, kFlagAbort, 0));
+                st_relaxed(st, status_word(epoch, kFlagAbort, 0));
             } else {
-                if (last) st_relaxed(ss + 1, excl_sum + tsum);
-                st_release(st, status_word(epoch, kFlagIncl, excl + tcount));
+                if (last) st_relaxed(ss + 1, sum_word(epoch, excl_sum + tsum));
+                st_relaxed(st, status_word(epoch, kFlagIncl, excl + tcount));
             }
         }
         // global position of local position lp of digit d: gbase[d] + lp
@@ -820,20 +869,44 @@ k_radix_pass(const uint32_t *kin, const uint32_t *vin,
     }
 
     // ---- final pass: evaluate every suffix (Alg. 3, suffix densities) without scattering
+    // A thread's elements sit at increasing positions, so on equal density
+    // the one it already holds (the earlier, larger suffix) stays.
     Candidate best{0, 0, 0, 0};
     uint64_t run = chunk_ex;
-    #pragma unroll
-    for (int i = 0; i < kPassIpt; ++i) {
-        const uint32_t lp = tid * kPassIpt + i;
-        if (lp < tn) {
-            const uint32_t key = S.keys[pad(lp)];
-            const uint32_t dd = ((key - lmin) >> shift) & (kBuckets - 1);
-            const int64_t pos = (int64_t)(uint32_t)(S.gbase[dd] + lp);
-            const uint64_t prefix = S.gsum[dd] + (run - S.dscan[dd]);
-            Candidate c{(int64_t)((uint64_t)m - prefix), n - pos, pos, (int64_t)key};
-            if (cand_better(c, best)) best = c;
-            run += S.vals[pad(lp)];
+    if ((uint64_t)m >> 32) {
+        #pragma unroll
+        for (int i = 0; i < kPassIpt; ++i) {
+            const uint32_t lp = tid * kPassIpt + i;
+            if (lp < tn) {
+                const uint32_t key = S.keys[pad(lp)];
+                const uint32_t dd = ((key - lmin) >> shift) & (kBuckets - 1);
+                const int64_t pos = (int64_t)(uint32_t)(S.gbase[dd] + lp);
+                const uint64_t prefix = S.gsum[dd] + (run - S.dscan[dd]);
+                Candidate c{(int64_t)((uint64_t)m - prefix), n - pos, pos, (int64_t)key};
+                if (cand_better(c, best)) best = c;
+                run += S.vals[pad(lp)];
+            }
         }
+    } else {
+        // m < 2^32 and n < 2^31: e * v' < 2^63, so 64-bit cross products
+        // compare the densities exactly
+        uint32_t be = 0, bv = 0, bkey = 0, bpos = 0;
+        #pragma unroll
+        for (int i = 0; i < kPassIpt; ++i) {
+            const uint32_t lp = tid * kPassIpt + i;
+            if (lp < tn) {
+                const uint32_t key = S.keys[pad(lp)];
+                const uint32_t dd = ((key - lmin) >> shift) & (kBuckets - 1);
+                const uint32_t pos = S.gbase[dd] + lp;
+                const uint32_t e = (uint32_t)((uint64_t)m - (S.gsum[dd] + (run - S.dscan[dd])));
+                const uint32_t v = (uint32_t)(n - (int64_t)pos);
+                if (bv == 0 || (uint64_t)e * bv > (uint64_t)be * v) {
+                    be = e; bv = v; bpos = pos; bkey = key;
+                }
+                run += S.vals[pad(lp)];
+            }
+        }
+        if (bv) best = Candidate{(int64_t)be, (int64_t)bv, (int64_t)bpos, (int64_t)bkey};
     }
     best = block_best(best, S.cred);
     if (tid == 0) {
