@@ -35,6 +35,11 @@ struct dsg_ctx {
     unsigned long long *red = nullptr;  // device scratch for reductions
     int peel_max_blocks = 0;         // cap on the PaRGreedy++ grid (0: one block per SM)
     cudaStream_t cap = nullptr;      // private stream that CUDA graphs are captured on
+    // host uploads: the adjacency arrives in chunks on its own stream while
+    // the context stream prepares the oriented copy; events [0, kUploadChunks)
+    // mark the chunks, the last one the allocation they are copied into
+    cudaStream_t copy = nullptr;
+    cudaEvent_t up_ev[kUploadChunks + 1] = {};
 };
 
 namespace dsg {
@@ -231,13 +236,15 @@ const char *const kGraphErr[5] = {"offsets are not non-decreasing", "a neighbour
 
 // degree-oriented copy (with the adjacency checks fused into its count pass)
 // and the chunk schedule of the vertices of large out-degree
-int build_grid(dsg_ctx *ctx, dsg_graph *G)
+int build_grid(dsg_ctx *ctx, dsg_graph *G, const UploadChunks *chunks)
 {
     cudaError_t e;
     int32_t h_err[8];
     const int64_t n = G->g.n;
+    int count_launches = 1;
     if ((e = build_orientation(G->g, ctx->stream, G->full_check, ctx->err_flags, &G->g.sorted, &G->ooff,
-                               &G->oadj, &G->hub, &G->g.n_hub, &G->hot, &G->g.n_hot)) != cudaSuccess)
+                               &G->oadj, &G->hub, &G->g.n_hub, &G->hot, &G->g.n_hot, chunks,
+                               &count_launches)) != cudaSuccess)
         return cuda_fail(ctx, e, "orientation");
     cudaMemcpyAsync(h_err, ctx->err_flags, sizeof(h_err), cudaMemcpyDeviceToHost, ctx->stream);
     if ((e = cudaStreamSynchronize(ctx->stream)) != cudaSuccess) return cuda_fail(ctx, e, "upload");
@@ -259,7 +266,7 @@ int build_grid(dsg_ctx *ctx, dsg_graph *G)
     G->g.heavy_acc = G->heavy_mem;
     G->g.heavy_done = G->heavy_mem + (G->g.n_heavy > 0 ? G->g.n_heavy : 1);
     if ((e = cudaStreamSynchronize(ctx->stream)) != cudaSuccess) return cuda_fail(ctx, e, "upload");
-    ctx->launches[DSG_PHASE_OTHER] += 5;
+    ctx->launches[DSG_PHASE_OTHER] += 4 + count_launches;
     G->grid_ready = true;
     return DSG_OK;
 }
@@ -407,6 +414,11 @@ void dsg_destroy(dsg_ctx *ctx)
     cudaFree(ctx->err_flags);
     cudaFree(ctx->red);
     if (ctx->cap) cudaStreamDestroy(ctx->cap);
+    if (ctx->copy) {
+        cudaStreamSynchronize(ctx->copy);
+        cudaStreamDestroy(ctx->copy);
+        for (auto e : ctx->up_ev) if (e) cudaEventDestroy(e);
+    }
     cudaMemPool_t pool;
     if (cudaDeviceGetDefaultMemPool(&pool, ctx->device) == cudaSuccess) cudaMemPoolTrimTo(pool, 0);
     delete ctx;
@@ -438,10 +450,17 @@ int dsg_upload_csr(dsg_ctx *ctx, int64_t n, const int64_t *offsets, const int32_
         return fail(ctx, DSG_ERR_INVALID, "offsets[n] = %lld must be even and in [0, 2^40)", (long long)arcs);
     if (arcs > 0 && !adj) return fail(ctx, DSG_ERR_INVALID, "adj is NULL");
 
+    // a large host graph is copied in vertex-range chunks on the context's
+    // copy stream, overlapped with the preparation of the oriented copy
+    const bool chunked = !dev_src && !is_compact(n, arcs) && arcs >= kChunkedUploadArcs;
+    bool chunks_issued = false;
+    UploadChunks chunks;
     dsg_graph *G = new (std::nothrow) dsg_graph;
     if (!G) return fail(ctx, DSG_ERR_NOMEM, "host allocation");
     G->ctx = ctx;
     auto bail = [&](int code) {
+        // chunks still in flight finish before their buffer is freed
+        if (chunks_issued) cudaStreamWaitEvent(ctx->stream, ctx->up_ev[kUploadChunks - 1], 0);
         if (G->off) cudaFreeAsync(G->off, ctx->stream);
         if (G->adj) cudaFreeAsync(G->adj, ctx->stream);
         if (G->items) cudaFreeAsync(G->items, ctx->stream);
@@ -462,8 +481,51 @@ int dsg_upload_csr(dsg_ctx *ctx, int64_t n, const int64_t *offsets, const int32_
         return bail(cuda_fail(ctx, e, "adjacency allocation"));
     if ((e = cudaMemcpyAsync(G->off, offsets, sizeof(int64_t) * (size_t)(n + 1), kind, ctx->stream)) != cudaSuccess)
         return bail(cuda_fail(ctx, e, "offsets copy"));
-    if (arcs > 0 && (e = cudaMemcpyAsync(G->adj, adj, sizeof(int32_t) * (size_t)arcs, kind, ctx->stream)) != cudaSuccess)
+    if (chunked) {
+        if (!ctx->copy) {
+            if ((e = cudaStreamCreateWithFlags(&ctx->copy, cudaStreamNonBlocking)) != cudaSuccess)
+                return bail(cuda_fail(ctx, e, "copy stream"));
+            for (int i = 0; i <= kUploadChunks; ++i)
+                if ((e = cudaEventCreateWithFlags(&ctx->up_ev[i], cudaEventDisableTiming)) != cudaSuccess)
+                    return bail(cuda_fail(ctx, e, "upload events"));
+        }
+        // the copies start once the allocation is in place on the context stream
+        if ((e = cudaEventRecord(ctx->up_ev[kUploadChunks], ctx->stream)) != cudaSuccess ||
+            (e = cudaStreamWaitEvent(ctx->copy, ctx->up_ev[kUploadChunks], 0)) != cudaSuccess)
+            return bail(cuda_fail(ctx, e, "upload ordering"));
+        // chunk boundaries at vertices splitting the arcs evenly; the byte
+        // ranges are clamped to [0, arcs) and non-decreasing whatever the
+        // offsets hold (they are validated on the device before any use)
+        chunks.k = kUploadChunks;
+        chunks.v[0] = 0;
+        chunks.v[kUploadChunks] = n;
+        int64_t a[kUploadChunks + 1];
+        a[0] = 0;
+        a[kUploadChunks] = arcs;
+        for (int i = 1; i < kUploadChunks; ++i) {
+            const int64_t target = (int64_t)((__int128)arcs * i / kUploadChunks);
+            int64_t lo = chunks.v[i - 1], hi = n;
+            while (lo < hi) {
+                const int64_t mid = lo + (hi - lo) / 2;
+                if (offsets[mid] < target) lo = mid + 1; else hi = mid;
+            }
+            chunks.v[i] = lo;
+            a[i] = std::min(std::max(offsets[lo], a[i - 1]), arcs);
+        }
+        chunks_issued = true;   // from here on a failure waits for the last chunk event
+        for (int i = 0; i < kUploadChunks; ++i) {
+            if ((a[i + 1] > a[i] &&
+                 (e = cudaMemcpyAsync(G->adj + a[i], adj + a[i], sizeof(int32_t) * (size_t)(a[i + 1] - a[i]),
+                                      cudaMemcpyHostToDevice, ctx->copy)) != cudaSuccess) ||
+                (e = cudaEventRecord(ctx->up_ev[i], ctx->copy)) != cudaSuccess) {
+                cudaEventRecord(ctx->up_ev[kUploadChunks - 1], ctx->copy);
+                return bail(cuda_fail(ctx, e, "adjacency copy"));
+            }
+            chunks.ev[i] = ctx->up_ev[i];
+        }
+    } else if (arcs > 0 && (e = cudaMemcpyAsync(G->adj, adj, sizeof(int32_t) * (size_t)arcs, kind, ctx->stream)) != cudaSuccess) {
         return bail(cuda_fail(ctx, e, "adjacency copy"));
+    }
     G->g.n = n;
     G->g.arcs = arcs;
     G->g.off = G->off;
@@ -521,7 +583,7 @@ int dsg_upload_csr(dsg_ctx *ctx, int64_t n, const int64_t *offsets, const int32_
         *out = G;
         return DSG_OK;
     }
-    const int rc = build_grid(ctx, G);
+    const int rc = build_grid(ctx, G, chunked ? &chunks : nullptr);
     if (rc != DSG_OK) return bail(rc);
     *out = G;
     return DSG_OK;
@@ -623,7 +685,7 @@ int dsg_run(dsg_graph *G, int variant, int32_t T, int64_t eps_num, int64_t eps_d
                             (!(out->flags & DSG_PATH_GRID) && block_path_default(variant, n, G->g.arcs));
     if (block_path) return run_block(ctx, G, variant, T, eps_num, eps_den, init_loads, init_dev, out);
     if (!G->grid_ready) {
-        const int rg = build_grid(ctx, G);
+        const int rg = build_grid(ctx, G, nullptr);
         if (rg != DSG_OK) return rg;
     }
     int rc = ensure_run_bufs(ctx, G, T);

@@ -192,12 +192,29 @@ cudaError_t launch_snapshot(const GraphDev &g, RunBufs &b, cudaStream_t s);
 cudaError_t launch_best_set(const GraphDev &g, RunBufs &b, int32_t *set_dev, cudaStream_t s,
                             int *launches);
 cudaError_t launch_loads_out(const GraphDev &g, RunBufs &b, int64_t *dst, cudaStream_t s);
+// An adjacency that is still arriving from the host: chunk i holds the
+// lists of vertices [v[i], v[i+1]) and is in place once ev[i] has fired.
+constexpr int kUploadChunks = 8;
+#ifndef DSG_CHUNKED_UPLOAD_ARCS
+#define DSG_CHUNKED_UPLOAD_ARCS (1ll << 24)
+#endif
+constexpr int64_t kChunkedUploadArcs = DSG_CHUNKED_UPLOAD_ARCS;   // smaller host graphs: one copy
+struct UploadChunks {
+    int k = 0;                          // 0: the whole adjacency is in place
+    int64_t v[kUploadChunks + 1] = {};
+    cudaEvent_t ev[kUploadChunks] = {};
+};
 // Validates the adjacency (err[1..5] as in launch_validate; full = symmetry
 // and strict order too) while counting the degree-oriented out-degrees, then
-// builds the oriented copy unless an error was found.
+// builds the oriented copy unless an error was found.  With chunks, the work
+// that needs only the offsets runs while the adjacency arrives, and each
+// chunk's counts start as soon as it is in place (all chunks first when
+// full: the symmetry check reads other lists).  Returns the number of
+// kernel launches in *launches.
 cudaError_t build_orientation(GraphDev &g, cudaStream_t s, int full, int32_t *err, int *sorted_out,
                               int64_t **ooff_out, uint32_t **oadj_out, uint32_t **hub_out,
-                              int64_t *n_hub_out, uint32_t **hot_out, int64_t *n_hot_out);
+                              int64_t *n_hub_out, uint32_t **hot_out, int64_t *n_hot_out,
+                              const UploadChunks *chunks, int *launches);
 cudaError_t launch_asum_single_pass(const GraphDev &g, RunBufs &b, cudaStream_t s);
 cudaError_t launch_max_u64_of_i64(const int64_t *src, int64_t n, unsigned long long *dst,
                                   int *neg_flag, cudaStream_t s);

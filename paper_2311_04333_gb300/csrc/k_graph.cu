@@ -300,26 +300,50 @@ __global__ void k_deg_enc(const int64_t *__restrict__ off, int64_t n, const int3
     }
 }
 
+// keep bits of the arcs: bit j of the bitmap is set when arc j (position in
+// the symmetric adjacency) stays in the oriented copy.  A warp's 32 arcs
+// starting at j0 span at most two bitmap words; neighbouring lists share
+// words, hence the atomics.
+__device__ __forceinline__ void set_keep_bits(uint32_t *bits, int64_t j0, uint32_t m, int lane)
+{
+    if (!m) return;
+    const int64_t wi = j0 >> 5;
+    const int sh = (int)(j0 & 31);
+    if (lane == 0) atomicOr(&bits[wi], m << sh);
+    if (lane == 1 && sh && (m >> (32 - sh))) atomicOr(&bits[wi + 1], m >> (32 - sh));
+}
+
+__device__ __forceinline__ bool keep_bit(const uint32_t *__restrict__ bits, int64_t j)
+{
+    return (bits[j >> 5] >> (j & 31)) & 1u;
+}
+
 // validation of the adjacency (ids, self-loops, order, symmetry) fused with
-// the oriented out-degree: warp per vertex of degree <= kBigDeg
+// the oriented out-degree and the keep bits: warp per vertex of degree <= kBigDeg
 __global__ void k_orient_count(const int64_t *__restrict__ off, const int32_t *__restrict__ adj,
-                               int64_t n, const uint32_t *__restrict__ deg32, int full, int32_t *err,
-                               int64_t *ocnt)
+                               int64_t n, int64_t u0, int64_t u1, const uint32_t *__restrict__ deg32,
+                               int full, int32_t *err, int64_t *ocnt, uint32_t *bits)
 {
     const int lane = threadIdx.x & 31;
     const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t u = wid; u < n; u += nw) {
+    for (int64_t u = u0 + wid; u < u1; u += nw) {
         const int64_t s = off[u], e = off[u + 1];
         const uint32_t du = (uint32_t)(e - s);
         if (du > kBigDeg) continue;                         // k_orient_count_big
         uint32_t c = 0;
-        for (int64_t j = s + lane; j < e; j += 32) {
-            check_arc(off, adj, n, u, s, j, full, err);
-            const int32_t w = adj[j];
-            if (w >= 0 && w < n) c += oriented_keep(du, (uint32_t)u, deg32[w], (uint32_t)w);
+        for (int64_t j0 = s; j0 < e; j0 += 32) {
+            const int64_t j = j0 + lane;
+            bool keep = false;
+            if (j < e) {
+                check_arc(off, adj, n, u, s, j, full, err);
+                const int32_t w = adj[j];
+                if (w >= 0 && w < n) keep = oriented_keep(du, (uint32_t)u, deg32[w], (uint32_t)w);
+            }
+            const uint32_t m = __ballot_sync(kFull, keep);
+            c += __popc(m);
+            set_keep_bits(bits, j0, m, lane);
         }
-        c = __reduce_add_sync(kFull, c);
         if (lane == 0) ocnt[u] = c;
     }
 }
@@ -328,21 +352,28 @@ __global__ void k_orient_count(const int64_t *__restrict__ off, const int32_t *_
 __global__ void k_orient_count_big(const int64_t *__restrict__ off, const int32_t *__restrict__ adj,
                                    int64_t n, const uint32_t *__restrict__ deg32,
                                    const uint32_t *__restrict__ big, int64_t n_big, int full,
-                                   int32_t *err, int64_t *ocnt)
+                                   int32_t *err, int64_t *ocnt, uint32_t *bits)
 {
     __shared__ uint32_t red[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int64_t b = blockIdx.x; b < n_big; b += gridDim.x) {
         const int64_t u = big[b], s = off[u], e = off[u + 1];
         const uint32_t du = (uint32_t)(e - s);
         uint32_t c = 0;
-        for (int64_t j = s + threadIdx.x; j < e; j += blockDim.x) {
-            check_arc(off, adj, n, u, s, j, full, err);
-            const int32_t w = adj[j];
-            if (w >= 0 && w < n) c += oriented_keep(du, (uint32_t)u, deg32[w], (uint32_t)w);
+        for (int64_t j0 = s; j0 < e; j0 += blockDim.x) {
+            const int64_t j = j0 + threadIdx.x;
+            bool keep = false;
+            if (j < e) {
+                check_arc(off, adj, n, u, s, j, full, err);
+                const int32_t w = adj[j];
+                if (w >= 0 && w < n) keep = oriented_keep(du, (uint32_t)u, deg32[w], (uint32_t)w);
+            }
+            const uint32_t m = __ballot_sync(kFull, keep);
+            c += __popc(m);
+            set_keep_bits(bits, j0 + 32 * warp, m, lane);
         }
-        c = __reduce_add_sync(kFull, c);
         __syncthreads();
-        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = c;
+        if (lane == 0) red[warp] = c;
         __syncthreads();
         if (threadIdx.x == 0) {
             uint32_t t = 0;
@@ -352,10 +383,11 @@ __global__ void k_orient_count_big(const int64_t *__restrict__ off, const int32_
     }
 }
 
-// warp per vertex of degree <= kBigDeg: the kept targets in list order
+// warp per vertex of degree <= kBigDeg: the kept targets in list order (the
+// keep bits spare a second gather of the targets' degrees)
 __global__ void k_orient_fill(const int64_t *__restrict__ off, const int32_t *__restrict__ adj,
                               int64_t n, const int64_t *__restrict__ ooff,
-                              const uint32_t *__restrict__ deg32, const uint32_t *__restrict__ enc,
+                              const uint32_t *__restrict__ bits, const uint32_t *__restrict__ enc,
                               uint32_t *oadj)
 {
     const int lane = threadIdx.x & 31;
@@ -363,19 +395,13 @@ __global__ void k_orient_fill(const int64_t *__restrict__ off, const int32_t *__
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t u = wid; u < n; u += nw) {
         const int64_t s = off[u], e = off[u + 1];
-        const uint32_t du = (uint32_t)(e - s);
-        if (du > kBigDeg) continue;
+        if ((uint64_t)(e - s) > kBigDeg) continue;
         int64_t o = ooff[u];
         for (int64_t j0 = s; j0 < e; j0 += 32) {
             const int64_t j = j0 + lane;
-            bool keep = false;
-            uint32_t w = 0;
-            if (j < e) {
-                w = (uint32_t)adj[j];
-                keep = oriented_keep(du, (uint32_t)u, deg32[w], w);
-            }
+            const bool keep = j < e && keep_bit(bits, j);
             const uint32_t m = __ballot_sync(kFull, keep);
-            if (keep) oadj[o + __popc(m & lanemask_lt())] = enc[w];
+            if (keep) oadj[o + __popc(m & lanemask_lt())] = enc[adj[j]];
             o += __popc(m);
         }
     }
@@ -383,7 +409,7 @@ __global__ void k_orient_fill(const int64_t *__restrict__ off, const int32_t *__
 
 // one block per vertex of degree > kBigDeg
 __global__ void k_orient_fill_big(const int64_t *__restrict__ off, const int32_t *__restrict__ adj,
-                                  const int64_t *__restrict__ ooff, const uint32_t *__restrict__ deg32,
+                                  const int64_t *__restrict__ ooff, const uint32_t *__restrict__ bits,
                                   const uint32_t *__restrict__ enc, const uint32_t *__restrict__ big,
                                   int64_t n_big, uint32_t *oadj)
 {
@@ -391,16 +417,10 @@ __global__ void k_orient_fill_big(const int64_t *__restrict__ off, const int32_t
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
     for (int64_t b = blockIdx.x; b < n_big; b += gridDim.x) {
         const int64_t u = big[b], s = off[u], e = off[u + 1];
-        const uint32_t du = (uint32_t)(e - s);
         int64_t o = ooff[u];
         for (int64_t j0 = s; j0 < e; j0 += blockDim.x) {
             const int64_t j = j0 + threadIdx.x;
-            bool keep = false;
-            uint32_t w = 0;
-            if (j < e) {
-                w = (uint32_t)adj[j];
-                keep = oriented_keep(du, (uint32_t)u, deg32[w], w);
-            }
+            const bool keep = j < e && keep_bit(bits, j);
             const uint32_t m = __ballot_sync(kFull, keep);
             __syncthreads();
             if (lane == 0) wc[warp] = __popc(m);
@@ -411,7 +431,7 @@ __global__ void k_orient_fill_big(const int64_t *__restrict__ off, const int32_t
                 wc[32] = t;
             }
             __syncthreads();
-            if (keep) oadj[o + wc[warp] + __popc(m & lanemask_lt())] = enc[w];
+            if (keep) oadj[o + wc[warp] + __popc(m & lanemask_lt())] = enc[adj[j]];
             o += wc[32];
         }
     }
@@ -475,10 +495,12 @@ static cudaError_t degree_threshold(const GraphDev &g, int64_t cap, const std::v
 // Builds ooff, oadj, hub_id and hot_id (allocated here, stream-ordered).
 cudaError_t build_orientation(GraphDev &g, cudaStream_t s, int full, int32_t *err, int *sorted_out,
                               int64_t **ooff_out, uint32_t **oadj_out, uint32_t **hub_out,
-                              int64_t *n_hub_out, uint32_t **hot_out, int64_t *n_hot_out)
+                              int64_t *n_hub_out, uint32_t **hot_out, int64_t *n_hot_out,
+                              const UploadChunks *chunks, int *launches)
 {
     const int64_t n = g.n;
     cudaError_t e;
+    int nl = 0;
     const int grid = (int)imin64((n + 255) / 256, 152 * 16);
     // hub threshold: the smallest D >= 2 with #{deg >= D} <= kHubs
     unsigned long long *cnt = nullptr;
@@ -538,11 +560,31 @@ cudaError_t build_orientation(GraphDev &g, cudaStream_t s, int full, int32_t *er
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
     if ((e = cudaMallocAsync((void **)&big, 4 * (size_t)imax64(n_big, 1), s)) != cudaSuccess) return e;
     k_hub_slots<<<grid, 256, 0, s>>>(g.off, n, kBigDeg + 1, flag, slot_of_scratch, big);
+    // keep bits of the arcs, set by the count pass and read by the fill pass
+    uint32_t *bits = nullptr;
+    const size_t nbits_words = (size_t)((g.arcs + 31) / 32) + 1;
+    if ((e = cudaMallocAsync((void **)&bits, 4 * nbits_words, s)) != cudaSuccess) return e;
+    cudaMemsetAsync(bits, 0, 4 * nbits_words, s);
     // validation fused with the oriented out-degrees
     const int wgrid = (int)imin64((n * 32 + 255) / 256, 152 * 32);
     const int bgrid = (int)imin64(imax64(n_big, 1), 152 * 2);
-    k_orient_count<<<wgrid, 256, 0, s>>>(g.off, g.adj, n, deg32, full, err, flag);
-    if (n_big) k_orient_count_big<<<bgrid, 1024, 0, s>>>(g.off, g.adj, n, deg32, big, n_big, full, err, flag);
+    const int nch = chunks ? chunks->k : 0;
+    if (nch > 0 && !full) {
+        for (int i = 0; i < nch; ++i) {
+            if ((e = cudaStreamWaitEvent(s, chunks->ev[i], 0)) != cudaSuccess) return e;
+            const int64_t v0 = chunks->v[i], v1 = chunks->v[i + 1];
+            if (v1 <= v0) continue;
+            const int cgrid = (int)imin64(((v1 - v0) * 32 + 255) / 256, 152 * 32);
+            k_orient_count<<<cgrid, 256, 0, s>>>(g.off, g.adj, n, v0, v1, deg32, full, err, flag, bits);
+            ++nl;
+        }
+    } else {
+        for (int i = 0; i < nch; ++i)
+            if ((e = cudaStreamWaitEvent(s, chunks->ev[i], 0)) != cudaSuccess) return e;
+        k_orient_count<<<wgrid, 256, 0, s>>>(g.off, g.adj, n, 0, n, deg32, full, err, flag, bits);
+        ++nl;
+    }
+    if (n_big) k_orient_count_big<<<bgrid, 1024, 0, s>>>(g.off, g.adj, n, deg32, big, n_big, full, err, flag, bits);
     int32_t h_err[8];
     cudaMemcpyAsync(h_err, err, sizeof(h_err), cudaMemcpyDeviceToHost, s);
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
@@ -557,9 +599,10 @@ cudaError_t build_orientation(GraphDev &g, cudaStream_t s, int full, int32_t *er
         cudaMemcpyAsync(&oarcs, total, 8, cudaMemcpyDeviceToHost, s);
         if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
         if ((e = cudaMallocAsync((void **)&oadj, 4 * (size_t)imax64(oarcs, 1), s)) != cudaSuccess) return e;
-        k_orient_fill<<<wgrid, 256, 0, s>>>(g.off, g.adj, n, flag, deg32, enc, oadj);
-        if (n_big) k_orient_fill_big<<<bgrid, 1024, 0, s>>>(g.off, g.adj, flag, deg32, enc, big, n_big, oadj);
+        k_orient_fill<<<wgrid, 256, 0, s>>>(g.off, g.adj, n, flag, bits, enc, oadj);
+        if (n_big) k_orient_fill_big<<<bgrid, 1024, 0, s>>>(g.off, g.adj, flag, bits, enc, big, n_big, oadj);
     }
+    cudaFreeAsync(bits, s);
     cudaFreeAsync(deg32, s);
     cudaFreeAsync(enc, s);
     cudaFreeAsync(big, s);
@@ -574,6 +617,7 @@ cudaError_t build_orientation(GraphDev &g, cudaStream_t s, int full, int32_t *er
     *n_hub_out = n_hub;
     *hot_out = hot;
     *n_hot_out = n_hot;
+    if (launches) *launches = nl;
     return cudaGetLastError();
 }
 

@@ -256,3 +256,33 @@ def test_block_path_on_a_large_graph(dsg, ctx, path):
         pytest.skip("checked once")
     check(dsg, ctx, gg.chung_lu(120000, 12, 2.1, 17), orc.SORTING, 4)
     check(dsg, ctx, gg.chung_lu(120000, 12, 2.1, 17), orc.PEELING, 3, 1, 10)
+
+
+def test_chunked_host_upload(dsg, ctx, path):
+    """A host graph of at least 2^24 arcs arrives in vertex-range chunks on a
+    copy stream, overlapped with the preparation of the oriented copy; without
+    DSG_VALIDATE each chunk's oriented counts start as soon as it is in place
+    (with it, after the last chunk: test_rmat20_config)."""
+    if path != PATHS["grid"]:
+        pytest.skip("checked once")
+    g = gg.rmat(20, 16, 2)
+    assert 2 * g.m >= 1 << 24
+    T = 3
+    gr = dsg.dsg_upload_csr(ctx, g.n, g.off, g.adj, 0)
+    try:
+        loads = np.zeros(g.n, np.int64)
+        bset = np.zeros(g.n, np.int32)
+        r = dsg.dsg_run(ctx, gr, dsg.DSG_SORTING, T, 0, 1, None, loads, bset)
+    finally:
+        dsg.dsg_free_graph(gr)
+    o = orc.run(g, orc.SORTING, T)
+    assert (r["best_edges"], r["best_vertices"], r["best_iter"]) == (o.best_edges, o.best_vertices, o.best_iter)
+    assert np.array_equal(loads, o.loads)
+    assert np.array_equal(bset[: r["best_set_size"]].astype(np.int64), o.best_set)
+    # a self-loop in the last chunk is still found
+    deg = np.diff(g.off)
+    u = int(np.flatnonzero(deg > 0)[-1])
+    adj = g.adj.copy()
+    adj[g.off[u]] = u
+    with pytest.raises(dsg.DsgError, match="INVALID"):
+        dsg.dsg_upload_csr(ctx, g.n, g.off, adj, 0)
