@@ -63,6 +63,8 @@ def _lib():
         lib.oracle_coreness.argtypes = [i64, p, p, p]
         lib.oracle_coreness_by_deletion.argtypes = [i64, p, p, p]
         lib.oracle_run_pruned.argtypes = [i64, p, p, ctypes.c_int, i64, i64, i64, p, p, p, p, p]
+        lib.oracle_run_pruned_c.argtypes = [i64, p, p, ctypes.c_int, i64, i64, i64, i64, i64, p, p, p, p, p]
+        lib.oracle_apx_coreness.argtypes = [i64, p, p, i64, i64, p]
         lib.oracle_core_subgraph.argtypes = [i64, p, p, p, i64, p, p]
         _lib_handle = lib
     return _lib_handle
@@ -203,18 +205,31 @@ class PrunedResult:
     L: tuple                 # final lower bound (numerator, denominator)
 
 
-def run_pruned(g, variant: int = SORTING, T: int = 1, p: int = 0, q: int = 1) -> PrunedResult:
-    """Alg. 1 (Pruning-and-Refining, exact pruning) with `variant` as Refine."""
+def apx_coreness(g, c: tuple = (3, 2)) -> np.ndarray:
+    """c-approximate core numbers (c = c[0] / c[1] > 1): the smallest level
+    tau_i >= core(v) of tau_0 = 1, tau_{i+1} = ceil(tau_i * c); 0 for core 0."""
+    n, off, adj = _csr(g)
+    out = np.zeros(n, dtype=np.int64)
+    if _lib().oracle_apx_coreness(n, _p(off), _p(adj), c[0], c[1], _p(out)) != 0:
+        raise ValueError("oracle_apx_coreness failed")
+    return out
+
+
+def run_pruned(g, variant: int = SORTING, T: int = 1, p: int = 0, q: int = 1, c: tuple = None) -> PrunedResult:
+    """Alg. 1 (Pruning-and-Refining) with `variant` as Refine: exact pruning,
+    or with c = (c_num, c_den) pruning by the c-approximate decomposition
+    (k_max of the result is then k-hat_max)."""
     n, off, adj = _csr(g)
     loads = np.zeros(n, dtype=np.int64)
     best = np.zeros(5, dtype=np.int64)
     bset = np.zeros(n, dtype=np.int64)
     trace = np.zeros((max(T, 1), 3), dtype=np.int64)
     info = np.zeros(6, dtype=np.int64)
-    rc = _lib().oracle_run_pruned(n, _p(off), _p(adj), variant, T, p, q, _p(loads), _p(best), _p(bset),
-                                  _p(trace), _p(info))
+    cn, cd = c if c else (0, 1)
+    rc = _lib().oracle_run_pruned_c(n, _p(off), _p(adj), variant, T, p, q, cn, cd, _p(loads), _p(best),
+                                    _p(bset), _p(trace), _p(info))
     if rc != 0:
-        raise ValueError(f"oracle_run_pruned failed with status {rc}")
+        raise ValueError(f"oracle_run_pruned_c failed with status {rc}")
     return PrunedResult(loads, int(best[0]), int(best[1]), int(best[2]), bset[: best[3]].copy(), trace[:T].copy(),
                         int(info[0]), int(info[1]), int(info[2]), int(info[3]), (int(info[4]), int(info[5])))
 

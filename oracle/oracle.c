@@ -21,6 +21,9 @@
  *     peel time, remove the vertex).  This is deliberately NOT Alg. 3's
  *     parallel A[min(j,k)] formulation, so the GPU's Alg. 3 path is checked
  *     against the sequential definition;
+ *   - Alg. 1 (Pruning-and-Refining) with exact pruning, or with pruning by
+ *     a c-approximate k-core decomposition (Sec. 2 definition, Sec. 5
+ *     approximate variants) taken at geometric levels of the core numbers;
  *   - exact checkers used to pin the oracle: brute force over all subsets,
  *     Goldberg-style max-flow densest subgraph, Batagelj-Zaversnik coreness,
  *     and the textbook k-core by repeated deletion (Sec. 2, Definitions of
@@ -573,6 +576,35 @@ int oracle_core_subgraph(int64_t n, const int64_t *off, const int32_t *adj, cons
     return rc;
 }
 
+/* c-approximate k-core decomposition (Sec. 2, Def. of the c-approximate
+ * decomposition; c = c_num / c_den > 1), at geometric levels
+ * tau_0 = 1, tau_{i+1} = ceil(tau_i * c): a vertex of core number k >= 1
+ * gets the smallest level >= k, a vertex of core number 0 gets 0.  Since
+ * tau_{i+1} < c * tau_i + 1 <= c * k for k > tau_i, this k-hat satisfies
+ * k <= k-hat < c * k, inside the definition's bounds k / c <= k-hat <= c k.
+ * It is what peeling with the thresholds tau_i yields: the vertices left
+ * after removing, level by level, every vertex of degree <= tau_i are the
+ * (tau_i + 1)-core, and those removed at level i have k in (tau_{i-1}, tau_i]. */
+static int64_t apx_next_level(int64_t tau, int64_t c_num, int64_t c_den)
+{
+    return ceil_div(tau * c_num, c_den);
+}
+
+int oracle_apx_coreness(int64_t n, const int64_t *off, const int32_t *adj, int64_t c_num, int64_t c_den,
+                        int64_t *apx)
+{
+    if (n < 1 || c_den < 1 || c_num <= c_den) return OR_ERR_INVALID;
+    int rc = oracle_coreness(n, off, adj, apx);
+    if (rc != OR_OK) return rc;
+    for (int64_t v = 0; v < n; ++v) {
+        if (apx[v] == 0) continue;
+        int64_t tau = 1;
+        while (tau < apx[v]) tau = apx_next_level(tau, c_num, c_den);
+        apx[v] = tau;
+    }
+    return OR_OK;
+}
+
 /* Alg. 1: cores <- Coreness(G); L <- ceil(k_max / 2); G <- L-core; S <- G;
  * then T times: S' <- Refine(G) (one iteration of the refine step
  * `variant` on the current G, with the loads of its vertices carried over
@@ -586,19 +618,26 @@ int oracle_core_subgraph(int64_t n, const int64_t *off, const int32_t *adj, cons
  * vertices) of the refine result of iteration t+1 and the vertex count of
  * the G it ran on; info = (k_max, |V|, |E| of the first core, |V| of the
  * final G, L as numerator, denominator).                                  */
-int oracle_run_pruned(int64_t n, const int64_t *off, const int32_t *adj, int variant, int64_t T,
-                      int64_t p, int64_t q, int64_t *loads, int64_t *best, int64_t *set, int64_t *trace,
-                      int64_t *info)
+/* With c_num > 0 the same loop runs on the c-approximate decomposition
+ * above (c = c_num / c_den, approximate pruning of Sec. 5): core numbers
+ * become k-hat, k_max becomes k-hat_max, the initial bound is
+ * L = ceil(k-hat_max / (2 c)) (Cor. of the approximate k_max), and every
+ * getCore keeps {v : k-hat(v) >= level}; info[0] is then k-hat_max.        */
+int oracle_run_pruned_c(int64_t n, const int64_t *off, const int32_t *adj, int variant, int64_t T,
+                        int64_t p, int64_t q, int64_t c_num, int64_t c_den, int64_t *loads, int64_t *best,
+                        int64_t *set, int64_t *trace, int64_t *info)
 {
     if (n < 1 || T < 0 || q <= 0 || p < 0 || variant < 0 || variant > 2) return OR_ERR_INVALID;
+    if (c_num != 0 && (c_den < 1 || c_num <= c_den)) return OR_ERR_INVALID;
     int64_t *core = malloc(sizeof(int64_t) * (size_t)n);
     unsigned char *in = malloc((size_t)n);
     if (!core || !in) { free(core); free(in); return OR_ERR_NOMEM; }
-    int rc = oracle_coreness(n, off, adj, core);
+    int rc = c_num ? oracle_apx_coreness(n, off, adj, c_num, c_den, core) : oracle_coreness(n, off, adj, core);
     if (rc != OR_OK) { free(core); free(in); return rc; }
     int64_t kmax = 0;
     for (int64_t v = 0; v < n; ++v) if (core[v] > kmax) kmax = core[v];
-    int64_t Ln = ceil_div(kmax, 2), Ld = 1;              /* Alg. 1: L = ceil(k_max / 2) */
+    /* Alg. 1: L = ceil(k_max / 2), or ceil(k-hat_max / (2c)) */
+    int64_t Ln = c_num ? ceil_div(kmax * c_den, 2 * c_num) : ceil_div(kmax, 2), Ld = 1;
     int64_t level = Ln;
     for (int64_t v = 0; v < n; ++v) in[v] = core[v] >= level;
     int64_t cn = 0, *coff = NULL, *old_of = NULL;
@@ -650,4 +689,11 @@ int oracle_run_pruned(int64_t n, const int64_t *off, const int32_t *adj, int var
 done:
     free(core); free(in); free(coff); free(cadj); free(old_of); free(cl); free(nl); free(lset);
     return rc;
+}
+
+int oracle_run_pruned(int64_t n, const int64_t *off, const int32_t *adj, int variant, int64_t T,
+                      int64_t p, int64_t q, int64_t *loads, int64_t *best, int64_t *set, int64_t *trace,
+                      int64_t *info)
+{
+    return oracle_run_pruned_c(n, off, adj, variant, T, p, q, 0, 1, loads, best, set, trace, info);
 }

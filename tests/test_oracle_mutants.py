@@ -58,7 +58,8 @@ def test_pins_catch_mutant(name, tmp_path):
 # plausible mistakes in the Pruning-and-Refining run (Alg. 1), caught by
 # the pins in test_oracle_pruned.py
 PRUNE_MUTANTS = {
-    "prune_floor_half": ("int64_t Ln = ceil_div(kmax, 2), Ld = 1;", "int64_t Ln = kmax / 2, Ld = 1;"),
+    "prune_floor_half": ("ceil_div(kmax * c_den, 2 * c_num) : ceil_div(kmax, 2), Ld = 1;",
+                         "ceil_div(kmax * c_den, 2 * c_num) : kmax / 2, Ld = 1;"),
     "prune_no_repruning": ("if (nlevel <= level) continue;", "continue;"),
     "prune_loads_reset": ("nl[i] = cl[nold[i]];", "nl[i] = 0;"),
     "prune_L_not_raised": ("if (density_gt(se, sv, Ln, Ld)) { Ln = se; Ld = sv; }", ";"),
@@ -66,6 +67,39 @@ PRUNE_MUTANTS = {
                                     "if (density_gt(se, sv, b[0], b[1])) continue;"),
     "prune_frozen_loads_dropped": ("if (!cin[i]) loads[old_of[i]] = cl[i];", ";"),
 }
+
+
+# approximate pruning: caught by test_oracle_apx.py
+APX_MUTANTS = {
+    "apx_levels_shifted": ("return ceil_div(tau * c_num, c_den);", "return ceil_div(tau * c_num, c_den) + 1;"),
+    "apx_lower_level": ("while (tau < apx[v]) tau = apx_next_level(tau, c_num, c_den);",
+                        "while (apx_next_level(tau, c_num, c_den) <= apx[v]) tau = apx_next_level(tau, c_num, c_den);"),
+    "apx_L_without_c": ("ceil_div(kmax * c_den, 2 * c_num) : ceil_div(kmax, 2), Ld = 1;",
+                        "ceil_div(kmax, 2) : ceil_div(kmax, 2), Ld = 1;"),
+    "apx_exact_cores_in_run": ("int rc = c_num ? oracle_apx_coreness(n, off, adj, c_num, c_den, core) : oracle_coreness(n, off, adj, core);",
+                               "int rc = oracle_coreness(n, off, adj, core);"),
+    "apx_zero_core_gets_level": ("if (apx[v] == 0) continue;", ";"),
+}
+
+
+def _run_mutant(old, new, test_file, tmp_path, name):
+    src = open(SRC).read()
+    assert src.count(old) == 1, f"mutation site for {name} not unique"
+    mut = tmp_path / "oracle_mut.c"
+    mut.write_text(src.replace(old, new))
+    so = tmp_path / "liboracle_mut.so"
+    subprocess.check_call(["gcc", "-O1", "-std=c11", "-shared", "-fPIC", "-o", str(so), str(mut)])
+    env = dict(os.environ, DSG_ORACLE_SO=str(so))
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                        os.path.join(ROOT, "tests", test_file)],
+                       env=env, cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert r.returncode != 0, f"mutant {name} survived the pins:\n{r.stdout[-2000:]}"
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("name", sorted(APX_MUTANTS))
+def test_apx_pins_catch_mutant(name, tmp_path):
+    _run_mutant(*APX_MUTANTS[name], "test_oracle_apx.py", tmp_path, name)
 
 
 @pytest.mark.slow
