@@ -311,6 +311,14 @@ def bench_pruned(dsg, g, ctx, stream, T, plain_ms, plain_r) -> dict:
     ms, r = timed(lambda: dsg.dsg_run_pruned(ctx, g, dsg.DSG_SORTING, T))
     ms5, r5 = timed(lambda: dsg.dsg_run_pruned(ctx, g, dsg.DSG_SORTING, 5 * T))
     plain5, p5 = timed(lambda: dsg.dsg_run(ctx, g, dsg.DSG_SORTING, 5 * T))
+    # PaRApxSorting++: pruning by the 1.5-approximate core numbers
+    msa, ra = timed(lambda: dsg.dsg_run_pruned(ctx, g, dsg.DSG_SORTING, T, c=(3, 2)))
+    msa5, ra5 = timed(lambda: dsg.dsg_run_pruned(ctx, g, dsg.DSG_SORTING, 5 * T, c=(3, 2)))
+    apx = {"variant": "PaRApxSorting++ (approximate pruning, c = 3/2)", "ms": msa, "ms_T5": msa5,
+           "speedup_vs_plain": plain_ms / msa, "speedup_vs_plain_T5": plain5 / msa5,
+           "k_hat_max": ra["k_max"], "core_vertices": ra["core_vertices"], "core_edges": ra["core_edges"],
+           "final_vertices": ra["final_vertices"], "best": [ra["best_edges"], ra["best_vertices"], ra["best_iter"]],
+           "best_T5": [ra5["best_edges"], ra5["best_vertices"], ra5["best_iter"]]}
     return {"variant": "PaRSorting++ with exact pruning (Alg. 1)", "T": T, "ms": ms, "plain_ms": plain_ms,
             "speedup_vs_plain": plain_ms / ms, "k_max": r["k_max"], "core_vertices": r["core_vertices"],
             "core_edges": r["core_edges"], "final_vertices": r["final_vertices"],
@@ -318,7 +326,7 @@ def bench_pruned(dsg, g, ctx, stream, T, plain_ms, plain_r) -> dict:
             "plain_best": [plain_r["best_edges"], plain_r["best_vertices"], plain_r["best_iter"]],
             "T5": 5 * T, "ms_T5": ms5, "plain_ms_T5": plain5, "speedup_vs_plain_T5": plain5 / ms5,
             "best_T5": [r5["best_edges"], r5["best_vertices"], r5["best_iter"]],
-            "plain_best_T5": [p5["best_edges"], p5["best_vertices"], p5["best_iter"]]}
+            "plain_best_T5": [p5["best_edges"], p5["best_vertices"], p5["best_iter"]], "approximate": apx}
 
 
 def bench_rmat20(dsg, ctx, gg, stream, args) -> dict:

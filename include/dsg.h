@@ -187,6 +187,33 @@ typedef struct {
 int dsg_run_pruned(dsg_graph *g, int variant, int32_t T, int64_t eps_num, int64_t eps_den, dsg_result *out,
                    dsg_prune_info *info);
 
+/* c-approximate core numbers (Sec. 2, "c-Approx k-Core Decomposition":
+ * core(v) / c <= k-hat(v) <= c core(v)), c = c_num / c_den with
+ * 1 <= c_den < c_num < 2^31.  The decomposition is taken at the geometric
+ * levels tau_0 = 1, tau_{i+1} = ceil(tau_i * c): k-hat(v) is the smallest
+ * level >= core(v) (0 when core(v) = 0), so core(v) <= k-hat(v) < c core(v).
+ * Computed by peeling level by level (the (tau_i + 1)-core of the previous
+ * core, by deletion), about log_c(k_max) peels instead of k_max.
+ * core[n] (int32) is host memory unless flags has DSG_DST_DEVICE; *k_max
+ * (may be NULL) receives the largest k-hat.  Synchronises the context stream.
+ * Errors: DSG_ERR_INVALID (c out of range), DSG_ERR_NOMEM, DSG_ERR_CUDA,
+ * DSG_ERR_TIMEOUT. */
+int dsg_apx_coreness(dsg_graph *g, int64_t c_num, int64_t c_den, int32_t *core, int64_t *k_max, uint32_t flags);
+
+/* Alg. 1 with approximate pruning (Sec. 5, the approximate variants:
+ * PaRApxSorting++ with DSG_SORTING; c = 1.5 in the paper's experiments):
+ * as dsg_run_pruned, with the core numbers replaced by the c-approximate
+ * ones of dsg_apx_coreness, L = ceil(k-hat_max / (2c)) (the corollary on the
+ * approximate k_max, which keeps the densest subgraph in the first core),
+ * and every getCore keeping {v : k-hat(v) >= ceil(L)}.  Since k-hat >= core,
+ * each such set is an exact core (of order 1 + the largest level below
+ * ceil(L)); k_max is only bracketed, by about log_c of its range of core
+ * tests from the degree bound, instead of located.  info->k_max receives
+ * k-hat_max.  Errors as dsg_run_pruned, and DSG_ERR_INVALID for c as in
+ * dsg_apx_coreness (c_num = 0 is refused: that is dsg_run_pruned). */
+int dsg_run_pruned_apx(dsg_graph *g, int variant, int32_t T, int64_t eps_num, int64_t eps_den, int64_t c_num,
+                       int64_t c_den, dsg_result *out, dsg_prune_info *info);
+
 /* Free an uploaded graph (stream-ordered release of its device memory). */
 void dsg_free_graph(dsg_graph *g);
 

@@ -81,6 +81,9 @@ def _load():
     lib.dsg_free_batch.restype = None
     lib.dsg_coreness.argtypes = [P, P, ctypes.POINTER(I64), ctypes.c_uint32]
     lib.dsg_run_pruned.argtypes = [P, I, I32, I64, I64, ctypes.POINTER(dsg_result), ctypes.POINTER(dsg_prune_info)]
+    lib.dsg_run_pruned_apx.argtypes = [P, I, I32, I64, I64, I64, I64, ctypes.POINTER(dsg_result),
+                                       ctypes.POINTER(dsg_prune_info)]
+    lib.dsg_apx_coreness.argtypes = [P, I64, I64, P, ctypes.POINTER(I64), ctypes.c_uint32]
     lib.dsg_server_create.argtypes = [I, I32, I64, ctypes.POINTER(P)]
     lib.dsg_server_submit.argtypes = [P, I64, P, P, I, I32, I64, I64, ctypes.POINTER(ctypes.c_uint64)]
     lib.dsg_server_wait.argtypes = [P, ctypes.c_uint64, I64, ctypes.POINTER(dsg_server_result), P, P]
@@ -189,10 +192,24 @@ def dsg_coreness(ctx, graph, core=None) -> tuple:
     return core, km.value
 
 
+def dsg_apx_coreness(ctx, graph, c=(3, 2), core=None) -> tuple:
+    """c-approximate core numbers (int32[n], host or device buffer; allocated
+    on the host when None) and their maximum; c = (c_num, c_den)."""
+    if core is None:
+        n = ctypes.c_int64()
+        LIB.dsg_graph_info(graph, ctypes.byref(n), None, None)
+        core = np.zeros(n.value, dtype=np.int32)
+    pc, dc = _ptr(core, np.int32)
+    km = ctypes.c_int64()
+    _check(ctx, LIB.dsg_apx_coreness(graph, c[0], c[1], pc, ctypes.byref(km), DSG_DST_DEVICE if dc else 0))
+    return core, km.value
+
+
 def dsg_run_pruned(ctx, graph, variant: int, T: int, eps_num: int = 0, eps_den: int = 1, loads=None,
-                   best_set=None, trace=None) -> dict:
+                   best_set=None, trace=None, c=None) -> dict:
     """Alg. 1 with `variant` as the refine step; outputs as dsg_run plus the
-    pruning info."""
+    pruning info.  c = (c_num, c_den) prunes by the c-approximate core
+    numbers (dsg_run_pruned_apx) instead of the exact ones."""
     res = dsg_result()
     pl, dl = _ptr(loads, np.int64)
     ps, ds = _ptr(best_set, np.int32)
@@ -203,11 +220,21 @@ def dsg_run_pruned(ctx, graph, variant: int, T: int, eps_num: int = 0, eps_den: 
     res.flags = DSG_DST_DEVICE if dev == {True} else 0
     res.loads, res.best_set, res.trace = pl, ps, pt
     info = dsg_prune_info()
-    _check(ctx, LIB.dsg_run_pruned(graph, variant, T, eps_num, eps_den, ctypes.byref(res), ctypes.byref(info)))
+    if c is None:
+        _check(ctx, LIB.dsg_run_pruned(graph, variant, T, eps_num, eps_den, ctypes.byref(res), ctypes.byref(info)))
+    else:
+        _check(ctx, LIB.dsg_run_pruned_apx(graph, variant, T, eps_num, eps_den, c[0], c[1], ctypes.byref(res),
+                                           ctypes.byref(info)))
     out = dict(best_edges=res.best_edges, best_vertices=res.best_vertices, best_iter=res.best_iter,
                best_set_size=res.best_set_size)
     out.update({f: getattr(info, f) for f, _ in dsg_prune_info._fields_})
     return out
+
+
+def dsg_run_pruned_apx(ctx, graph, variant: int, T: int, eps_num: int = 0, eps_den: int = 1, c_num: int = 3,
+                       c_den: int = 2, loads=None, best_set=None, trace=None) -> dict:
+    """Alg. 1 with pruning by the c-approximate core numbers, c = c_num / c_den."""
+    return dsg_run_pruned(ctx, graph, variant, T, eps_num, eps_den, loads, best_set, trace, c=(c_num, c_den))
 
 
 def dsg_free_graph(graph) -> None:
@@ -340,5 +367,5 @@ DSG_NOALLOC_MAX_VERTICES = 262144
 EXPORTED = ["dsg_create", "dsg_destroy", "dsg_last_error", "dsg_upload_csr", "dsg_graph_info",
             "dsg_run", "dsg_free_graph", "dsg_set_profiling", "dsg_get_stats",
             "dsg_densest_suffix_noalloc", "dsg_upload_batch", "dsg_batch_info", "dsg_run_batch",
-            "dsg_free_batch", "dsg_coreness", "dsg_run_pruned", "dsg_server_create", "dsg_server_submit", "dsg_server_wait",
+            "dsg_free_batch", "dsg_coreness", "dsg_apx_coreness", "dsg_run_pruned", "dsg_run_pruned_apx", "dsg_server_create", "dsg_server_submit", "dsg_server_wait",
             "dsg_server_stats", "dsg_server_destroy"]

@@ -841,11 +841,19 @@ int dsg_coreness(dsg_graph *G, int32_t *core, int64_t *k_max, uint32_t flags)
     return DSG_OK;
 }
 
-int dsg_run_pruned(dsg_graph *G, int variant, int32_t T, int64_t eps_num, int64_t eps_den, dsg_result *out,
-                   dsg_prune_info *info)
+// Alg. 1 with exact pruning (c_num == 0) or with pruning by the
+// c-approximate decomposition (c = c_num / c_den): k-hat(v) is the smallest
+// level tau_i >= core(v), so {v : k-hat(v) >= x} is the exact core of order
+// apx_order(x) and every core this run takes is still a k-core by deletion.
+static int run_pruned(dsg_graph *G, int variant, int32_t T, int64_t eps_num, int64_t eps_den, int64_t c_num,
+                      int64_t c_den, dsg_result *out, dsg_prune_info *info)
 {
     if (!G || !out) return DSG_ERR_INVALID;
     dsg_ctx *ctx = G->ctx;
+    const bool apx = c_num != 0;
+    if (apx && (c_den < 1 || c_num <= c_den || c_num >= ((int64_t)1 << 31)))
+        return fail(ctx, DSG_ERR_INVALID, "c = %lld/%lld: need 1 <= c_den < c_num < 2^31", (long long)c_num,
+                    (long long)c_den);
     if (variant != DSG_SORTING && variant != DSG_PEELING)
         return fail(ctx, DSG_ERR_INVALID, "unknown variant %d", variant);
     if (T < 1) return fail(ctx, DSG_ERR_INVALID, "T = %d must be >= 1", T);
@@ -928,6 +936,7 @@ int dsg_run_pruned(dsg_graph *G, int variant, int32_t T, int64_t eps_num, int64_
         hi = std::min(hi, G->g.max_degree + 1);
         int64_t lo = k_low;
         bool doubling = true;
+        if (apx) hi = lo;      // the search below is the exact one
         while (hi - lo > 1) {
             const int64_t mid = doubling ? std::min(hi - 1, std::max<int64_t>(lo + 1, 2 * lo)) : lo + (hi - lo) / 2;
             int64_t alive = 0;
@@ -946,19 +955,60 @@ int dsg_run_pruned(dsg_graph *G, int variant, int32_t T, int64_t eps_num, int64_
             chain.push_back({lo, nx});
         }
         kmax = lo;
+        if (apx && G->g.arcs == 0) {
+            kmax = 0;
+        } else if (apx) {
+            // k-hat_max, the smallest level >= k_max: probe the core orders
+            // tau_i + 1 upwards from the first one >= k_low (the one below is
+            // not empty: tau_{i-1} + 1 < k_low <= k_max); the first empty one
+            // gives k_max <= tau_i
+            int64_t tau = 1;
+            while (tau + 1 < k_low) tau = apx_next_level(tau, c_num, c_den);
+            for (;;) {
+                int64_t alive = 0;
+                const CoreGraph &C = chain.back().second;
+                if ((rc = kcore(C, tau + 1, &alive)) != DSG_OK) return done_k(rc);
+                if (alive == 0) break;
+                CoreGraph nx;
+                if ((e = extract_core(s, C.n, C.off, C.adj, keep, C.old_of, tau + 1, nullptr, nullptr, &nx, true)) !=
+                    cudaSuccess)
+                    return done_k(cuda_fail(ctx, e, "core extraction"));
+                chain.push_back({tau + 1, nx});
+                tau = apx_next_level(tau, c_num, c_den);
+            }
+            kmax = tau;
+        }
     }
-    int64_t Ln = (kmax + 1) / 2, Ld = 1, level = Ln;
+    // L = ceil(k_max / 2), or ceil(k-hat_max / (2c)) (the corollary on the
+    // approximate k_max); G keeps the core of order `order`
+    int64_t Ln = apx ? (kmax * c_den + 2 * c_num - 1) / (2 * c_num) : (kmax + 1) / 2, Ld = 1, level = Ln;
+    int64_t order = apx ? apx_order(level, c_num, c_den) : level;
     {
-        // the L-core, from the highest core of the chain at or below L
-        size_t j = 0;
-        for (size_t i = 0; i < chain.size(); ++i)
-            if (chain[i].first <= level) j = i;
-        const CoreGraph &C = chain[j].second;
-        int64_t alive = 0;
-        if ((rc = kcore(C, level, &alive)) != DSG_OK) return done_k(rc);
-        if ((e = extract_core(s, C.n, C.off, C.adj, keep, C.old_of, level, nullptr, nullptr, &cur, true)) !=
-            cudaSuccess)
-            return done_k(cuda_fail(ctx, e, "core extraction"));
+        // the first core, from the highest core of the chain at or below its
+        // order (the chain starts at G[deg >= k_low], which holds every core
+        // of order >= k_low), or from G itself below k_low
+        if (order >= chain[0].first) {
+            size_t j = 0;
+            for (size_t i = 0; i < chain.size(); ++i)
+                if (chain[i].first <= order) j = i;
+            const CoreGraph &C = chain[j].second;
+            int64_t alive = 0;
+            if ((rc = kcore(C, order, &alive)) != DSG_OK) return done_k(rc);
+            if ((e = extract_core(s, C.n, C.off, C.adj, keep, C.old_of, order, nullptr, nullptr, &cur, true)) !=
+                cudaSuccess)
+                return done_k(cuda_fail(ctx, e, "core extraction"));
+        } else {
+            CoreGraph whole;
+            whole.n = n;
+            whole.arcs = G->g.arcs;
+            whole.off = G->off;
+            whole.adj = G->adj;
+            int64_t alive = 0;
+            if ((rc = kcore(whole, order, &alive)) != DSG_OK) return done_k(rc);
+            if ((e = extract_core(s, n, G->off, G->adj, keep, nullptr, order, nullptr, nullptr, &cur, true)) !=
+                cudaSuccess)
+                return done_k(cuda_fail(ctx, e, "core extraction"));
+        }
         for (auto &c : chain) free_core(c.second, s);
         chain.clear();
     }
@@ -998,10 +1048,13 @@ int dsg_run_pruned(dsg_graph *G, int variant, int32_t T, int64_t eps_num, int64_
         const int64_t nlevel = (Ln + Ld - 1) / Ld;
         if (nlevel <= level) continue;
         level = nlevel;
+        const int64_t norder = apx ? apx_order(level, c_num, c_den) : level;
+        if (norder <= order) continue;       // the same vertex set
+        order = norder;
         CoreGraph nx;
         int64_t alive = 0;
-        if ((rc = kcore(cur, level, &alive)) != DSG_OK) return done_k(rc);
-        if ((e = extract_core(s, cur.n, cur.off, cur.adj, keep, cur.old_of, level, cur.loads, loads_all, &nx, true)) !=
+        if ((rc = kcore(cur, order, &alive)) != DSG_OK) return done_k(rc);
+        if ((e = extract_core(s, cur.n, cur.off, cur.adj, keep, cur.old_of, order, cur.loads, loads_all, &nx, true)) !=
             cudaSuccess)
             return done_k(cuda_fail(ctx, e, "core extraction"));
         free_core(cur, s);
@@ -1032,6 +1085,85 @@ int dsg_run_pruned(dsg_graph *G, int variant, int32_t T, int64_t eps_num, int64_
         info->L_den = Ld;
     }
     return done_k(DSG_OK);
+}
+
+int dsg_run_pruned(dsg_graph *G, int variant, int32_t T, int64_t eps_num, int64_t eps_den, dsg_result *out,
+                   dsg_prune_info *info)
+{
+    return run_pruned(G, variant, T, eps_num, eps_den, 0, 1, out, info);
+}
+
+int dsg_run_pruned_apx(dsg_graph *G, int variant, int32_t T, int64_t eps_num, int64_t eps_den, int64_t c_num,
+                       int64_t c_den, dsg_result *out, dsg_prune_info *info)
+{
+    if (G && c_num == 0) return fail(G->ctx, DSG_ERR_INVALID, "c_num = 0: use dsg_run_pruned");
+    return run_pruned(G, variant, T, eps_num, eps_den, c_num, c_den, out, info);
+}
+
+int dsg_apx_coreness(dsg_graph *G, int64_t c_num, int64_t c_den, int32_t *core, int64_t *k_max, uint32_t flags)
+{
+    if (!G || !core) return DSG_ERR_INVALID;
+    dsg_ctx *ctx = G->ctx;
+    if (c_den < 1 || c_num <= c_den || c_num >= ((int64_t)1 << 31))
+        return fail(ctx, DSG_ERR_INVALID, "c = %lld/%lld: need 1 <= c_den < c_num < 2^31", (long long)c_num,
+                    (long long)c_den);
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    const int64_t n = G->g.n;
+    cudaStream_t s = ctx->stream;
+    int rc = ensure_run_bufs(ctx, G, 1);
+    if (rc) return rc;
+    const bool dst_dev = flags & DSG_DST_DEVICE;
+    char *mem = nullptr;
+    CK(cudaMallocAsync((void **)&mem, 3 * align256(4 * (size_t)n), s), "apx coreness buffers");
+    int32_t *deg = (int32_t *)mem;
+    int32_t *keep = (int32_t *)(mem + align256(4 * (size_t)n));
+    int32_t *dst = dst_dev ? core : (int32_t *)(mem + 2 * align256(4 * (size_t)n));
+    KCoreBufs kb;
+    CoreGraph C;
+    auto done = [&](int code) {
+        free_core(C, s);
+        kcore_free(kb, s);
+        cudaFreeAsync(mem, s);
+        cudaStreamSynchronize(s);
+        return code == DSG_ERR_TIMEOUT ? fail(ctx, code, "approximate coreness: a bounded wait gave up") : code;
+    };
+    cudaError_t e;
+    int64_t k_low = 0, khat = 0;
+    // level by level: C is the (tau_{i-1} + 1)-core (the 1-core first: the
+    // vertices with an edge); the vertices that its (tau_i + 1)-core drops
+    // have core numbers in (tau_{i-1}, tau_i] and get tau_i
+    if ((e = cudaMemsetAsync(dst, 0, 4 * (size_t)n, s)) != cudaSuccess) return done(cuda_fail(ctx, e, "memset"));
+    if ((e = degree_core_bound(s, G->g, deg, &k_low)) != cudaSuccess) return done(cuda_fail(ctx, e, "degrees"));
+    if ((e = extract_core(s, n, G->off, G->adj, deg, nullptr, 1, nullptr, nullptr, &C)) != cudaSuccess)
+        return done(cuda_fail(ctx, e, "1-core"));
+    int64_t tau = 1;
+    while (C.n > 0) {
+        GraphDev cd{};
+        cd.n = C.n;
+        cd.arcs = C.arcs;
+        cd.off = C.off;
+        cd.adj = C.adj;
+        int64_t alive = 0;
+        if ((rc = kcore_run(s, cd, G->rb.ctl, ctx->sm_count, kb, (int32_t)(tau + 1), keep, &alive, ctx->err)) !=
+            DSG_OK)
+            return done(rc);
+        if (alive < C.n) khat = tau;
+        if ((e = assign_removed(keep, C.n, C.old_of, (int32_t)tau, dst, s)) != cudaSuccess)
+            return done(cuda_fail(ctx, e, "levels"));
+        if (alive == 0) break;
+        CoreGraph nx;
+        if ((e = extract_core(s, C.n, C.off, C.adj, keep, C.old_of, tau + 1, nullptr, nullptr, &nx, true)) !=
+            cudaSuccess)
+            return done(cuda_fail(ctx, e, "core extraction"));
+        free_core(C, s);
+        C = nx;
+        tau = apx_next_level(tau, c_num, c_den);
+    }
+    if (!dst_dev && (e = cudaMemcpyAsync(core, dst, 4 * (size_t)n, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+        return done(cuda_fail(ctx, e, "core copy"));
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return done(cuda_fail(ctx, e, "approximate coreness"));
+    if (k_max) *k_max = khat;
+    return done(DSG_OK);
 }
 
 int dsg_upload_batch(dsg_ctx *ctx, int32_t G, const int64_t *n_per, const int64_t *const *offsets,

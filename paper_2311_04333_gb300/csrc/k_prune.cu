@@ -271,6 +271,22 @@ cudaError_t scatter_ids(const int32_t *x, int64_t n, const int32_t *old_of, int3
     return cudaGetLastError();
 }
 
+namespace {
+__global__ void k_assign_removed(const int32_t *__restrict__ keep, int64_t n, const int32_t *__restrict__ old_of,
+                                 int32_t value, int32_t *out)
+{
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+        if (keep[v] == 0) out[old_of ? old_of[v] : v] = value;
+}
+}  // namespace
+
+cudaError_t assign_removed(const int32_t *keep, int64_t n, const int32_t *old_of, int32_t value, int32_t *out,
+                           cudaStream_t s)
+{
+    if (n > 0) k_assign_removed<<<(int)imin64((n + 255) / 256, 152 * 8), 256, 0, s>>>(keep, n, old_of, value, out);
+    return cudaGetLastError();
+}
+
 cudaError_t scatter_loads(const int64_t *loads, int64_t n, const int32_t *old_of, int64_t *out, cudaStream_t s)
 {
     if (n > 0) k_scatter_loads<<<(int)imin64((n + 255) / 256, 152 * 8), 256, 0, s>>>(loads, n, old_of, out);

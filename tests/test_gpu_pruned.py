@@ -100,3 +100,79 @@ def test_pruned_run_device_buffers(dsg, ctx):
     assert np.array_equal(loads.cpu().numpy(), o.loads)
     assert np.array_equal(bset[:r["best_set_size"]].cpu().numpy().astype(np.int64), o.best_set)
     assert np.array_equal(trace.cpu().numpy().reshape(T, 3), o.trace)
+
+
+@pytest.mark.parametrize("name", list(_graphs()))
+@pytest.mark.parametrize("c", [(3, 2), (2, 1)])
+def test_apx_coreness(dsg, ctx, name, c):
+    """c-approximate core numbers (level-by-level peels) equal the oracle's."""
+    g = _graphs()[name]
+    h = dsg.dsg_upload_csr(ctx, g.n, g.off, g.adj, 0)
+    try:
+        core, khat = dsg.dsg_apx_coreness(ctx, h, c)
+    finally:
+        dsg.dsg_free_graph(h)
+    exp = orc.apx_coreness(g, c)
+    assert np.array_equal(core.astype(np.int64), exp)
+    assert khat == int(exp.max())
+
+
+@pytest.mark.parametrize("name", list(_graphs()))
+@pytest.mark.parametrize("variant,p,q,T,c", [(0, 0, 1, 8, (3, 2)), (1, 1, 10, 6, (3, 2)), (0, 0, 1, 6, (2, 1)),
+                                             (0, 0, 1, 5, (10001, 10000))])
+def test_apx_pruned_run(dsg, ctx, name, variant, p, q, T, c):
+    """Alg. 1 with approximate pruning: every output equals the oracle's."""
+    g = _graphs()[name]
+    h = dsg.dsg_upload_csr(ctx, g.n, g.off, g.adj, 0)
+    loads = np.zeros(g.n, np.int64)
+    bset = np.zeros(g.n, np.int32)
+    trace = np.zeros(3 * T, np.int64)
+    try:
+        r = dsg.dsg_run_pruned(ctx, h, variant, T, p, q, loads, bset, trace, c=c)
+    finally:
+        dsg.dsg_free_graph(h)
+    o = orc.run_pruned(g, variant, T, p, q, c=c)
+    assert (r["best_edges"], r["best_vertices"], r["best_iter"]) == (o.best_edges, o.best_vertices, o.best_iter)
+    assert np.array_equal(bset[:r["best_set_size"]].astype(np.int64), o.best_set)
+    assert np.array_equal(loads, o.loads)
+    assert np.array_equal(trace.reshape(T, 3), o.trace)
+    assert (r["k_max"], r["core_vertices"], r["core_edges"], r["final_vertices"]) == \
+        (o.k_max, o.core_vertices, o.core_edges, o.final_vertices)
+    assert (r["L_num"], r["L_den"]) == o.L
+
+
+def test_apx_large(dsg, ctx):
+    """R-MAT 18: the approximate decomposition and the approximately pruned
+    PaRSorting++ run (whole-GPU k-core peels on the larger cores)."""
+    g = gg.rmat(18, 16, 5)
+    T = 4
+    h = dsg.dsg_upload_csr(ctx, g.n, g.off, g.adj, 0)
+    loads = np.zeros(g.n, np.int64)
+    bset = np.zeros(g.n, np.int32)
+    try:
+        core, khat = dsg.dsg_apx_coreness(ctx, h, (3, 2))
+        r = dsg.dsg_run_pruned(ctx, h, 0, T, 0, 1, loads, bset, None, c=(3, 2))
+    finally:
+        dsg.dsg_free_graph(h)
+    exp = orc.apx_coreness(g, (3, 2))
+    assert np.array_equal(core.astype(np.int64), exp) and khat == int(exp.max())
+    o = orc.run_pruned(g, 0, T, c=(3, 2))
+    assert (r["best_edges"], r["best_vertices"], r["best_iter"]) == (o.best_edges, o.best_vertices, o.best_iter)
+    assert np.array_equal(bset[:r["best_set_size"]].astype(np.int64), o.best_set)
+    assert np.array_equal(loads, o.loads)
+    assert (r["k_max"], r["core_vertices"], r["final_vertices"]) == (o.k_max, o.core_vertices, o.final_vertices)
+
+
+def test_apx_invalid(dsg, ctx):
+    g = gg.complete(5)
+    h = dsg.dsg_upload_csr(ctx, g.n, g.off, g.adj, 0)
+    try:
+        for c in [(1, 1), (2, 3), (3, 0), (1 << 31, 2)]:
+            with pytest.raises(dsg.DsgError, match="INVALID"):
+                dsg.dsg_apx_coreness(ctx, h, c)
+            with pytest.raises(dsg.DsgError, match="INVALID"):
+                dsg.dsg_run_pruned(ctx, h, 0, 2, c=c)
+        with pytest.raises(dsg.DsgError, match="INVALID"):
+            dsg.dsg_run_pruned(ctx, h, 0, 2, c=(0, 1))
+    finally:
+        dsg.dsg_free_graph(h)
