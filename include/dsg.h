@@ -169,7 +169,7 @@ typedef struct {
     int64_t L_num, L_den;                /* final density lower bound L = L_num / L_den */
 } dsg_prune_info;
 
-/* Alg. 1 (Sec. 4, "Pruning-and-Refining Framework") with exact pruning and
+/* Alg. 1 (Sec. 3, "Pruning-and-Refining Framework") with exact pruning and
  * T iterations of `variant` as the Refine step: core numbers of g (the
  * eps = 0 round peel); L = ceil(k_max / 2); G <- the L-core, S <- G; then T
  * times: one refine iteration on G, its vertices' loads carried over; if its
@@ -200,7 +200,7 @@ int dsg_run_pruned(dsg_graph *g, int variant, int32_t T, int64_t eps_num, int64_
  * DSG_ERR_TIMEOUT. */
 int dsg_apx_coreness(dsg_graph *g, int64_t c_num, int64_t c_den, int32_t *core, int64_t *k_max, uint32_t flags);
 
-/* Alg. 1 with approximate pruning (Sec. 5, the approximate variants:
+/* Alg. 1 with approximate pruning (Sec. 4, the approximate variants:
  * PaRApxSorting++ with DSG_SORTING; c = 1.5 in the paper's experiments):
  * as dsg_run_pruned, with the core numbers replaced by the c-approximate
  * ones of dsg_apx_coreness, L = ceil(k-hat_max / (2c)) (the corollary on the

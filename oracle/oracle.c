@@ -22,7 +22,7 @@
  *     parallel A[min(j,k)] formulation, so the GPU's Alg. 3 path is checked
  *     against the sequential definition;
  *   - Alg. 1 (Pruning-and-Refining) with exact pruning, or with pruning by
- *     a c-approximate k-core decomposition (Sec. 2 definition, Sec. 5
+ *     a c-approximate k-core decomposition (Sec. 2 definition, Sec. 4
  *     approximate variants) taken at geometric levels of the core numbers;
  *   - exact checkers used to pin the oracle: brute force over all subsets,
  *     Goldberg-style max-flow densest subgraph, Batagelj-Zaversnik coreness,
@@ -521,7 +521,7 @@ int oracle_coreness_by_deletion(int64_t n, const int64_t *off, const int32_t *ad
 }
 
 /* ------------------------------------------------------------------------ */
-/* Pruning-and-Refining framework (Alg. 1, Sec. 4) with exact pruning.      */
+/* Pruning-and-Refining framework (Alg. 1, Sec. 3) with exact pruning.      */
 
 /* getCore (Alg. 1, initial and re-pruning): the subgraph of G induced on the vertices
  * with in[v] != 0, relabelled in increasing id (lists keep their order).
@@ -619,7 +619,7 @@ int oracle_apx_coreness(int64_t n, const int64_t *off, const int32_t *adj, int64
  * the G it ran on; info = (k_max, |V|, |E| of the first core, |V| of the
  * final G, L as numerator, denominator).                                  */
 /* With c_num > 0 the same loop runs on the c-approximate decomposition
- * above (c = c_num / c_den, approximate pruning of Sec. 5): core numbers
+ * above (c = c_num / c_den, approximate pruning of Sec. 4): core numbers
  * become k-hat, k_max becomes k-hat_max, the initial bound is
  * L = ceil(k-hat_max / (2 c)) (Cor. of the approximate k_max), and every
  * getCore keeps {v : k-hat(v) >= level}; info[0] is then k-hat_max.        */

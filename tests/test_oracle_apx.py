@@ -1,6 +1,6 @@
 """Pins of the oracle's approximate pruning (Sec. 2 definition of a
-c-approximate k-core decomposition; Sec. 4 corollary on the approximate
-k_max; Sec. 5 approximate variants).
+c-approximate k-core decomposition; Sec. 2.1 corollary on the approximate
+k_max; Sec. 4 approximate variants).
 
 They check the decomposition against hand-computed level lists, the
 definition's bounds, a direct simulation of threshold peeling, and cores by

@@ -1,6 +1,6 @@
 """Pins of the oracle's Pruning-and-Refining run (Alg. 1, exact pruning).
 
-They check it against what Sec. 4 fixes: the ceil(k_max/2)-core keeps the
+They check it against what Sec. 2.1 and Alg. 1 (Sec. 3) fix: the ceil(k_max/2)-core keeps the
 densest subgraph (Lemma on cores and Corollary on k_max, via exact max-flow
 on both graphs), the closed forms of graphs the pruning leaves whole or cuts
 to a clique, the lower bound rho >= k_max/2, the self-consistency of the
