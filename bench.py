@@ -572,14 +572,25 @@ def main():
     del off, adj, loads, bset
     torch.cuda.empty_cache()
 
+    # both calls return after their work is done: host clocks split each step
+    # into the upload (host-to-device copy + oriented copy) and the run (T
+    # iterations + read-back)
+    e2e_split = {"upload_ms": [], "run_ms": []}
+
     def e2e_step():
+        ta = time.perf_counter()
         gh = dsg.dsg_upload_csr(ctx, n, off_h, adj_h, 0)
+        tb = time.perf_counter()
         try:
-            return dsg.dsg_run(ctx, gh, dsg.DSG_SORTING, T, 0, 1, None, loads_h, bset_h)
+            rr = dsg.dsg_run(ctx, gh, dsg.DSG_SORTING, T, 0, 1, None, loads_h, bset_h)
+            e2e_split["upload_ms"].append(round(1e3 * (tb - ta), 1))
+            e2e_split["run_ms"].append(round(1e3 * (time.perf_counter() - tb), 1))
+            return rr
         finally:
             dsg.dsg_free_graph(gh)
 
     re = e2e_step()
+    e2e_split = {"upload_ms": [], "run_ms": []}
     assert (re["best_edges"], re["best_vertices"]) == (r["best_edges"], r["best_vertices"])
     _barrier(ws)
     torch.cuda.synchronize()
@@ -634,7 +645,8 @@ def main():
             "cpu_baseline": cpu,
             "cpu_parallel_baseline": cpu_par,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
-                    "d2h_bytes_per_step": d2h, "steps": args.e2e_steps},
+                    "d2h_bytes_per_step": d2h, "steps": args.e2e_steps,
+                    "upload_ms_per_step": e2e_split["upload_ms"], "run_ms_per_step": e2e_split["run_ms"]},
             "gpu_launches": launches,
             "clocks": clk.summary(),
             "batched": batched,

@@ -771,6 +771,7 @@ k_radix_pass(const uint32_t *kin, const uint32_t *vin,
                 run += S.vals[pad(lp)];
             }
         }
+        __syncthreads();     // dscan is read by digit below
     }
 
     // ---- decoupled look-back: thread d resolves digit d.  Every status word
@@ -841,7 +842,10 @@ k_radix_pass(const uint32_t *kin, const uint32_t *vin,
         // global position of local position lp of digit d: gbase[d] + lp
         // (modulo 2^32; positions stay below n < 2^31)
         S.gbase[d] = S.boff[d] + (uint32_t)excl - S.toff[d];
-        if (last) S.gsum[d] = S.aoff[d] + excl_sum;
+        // prefix sum of A before local position lp of digit d: gsum[d] + (the
+        // tile's exclusive value scan at lp); dscan[d] is only set, and gsum[d]
+        // only read, for digits present in the tile
+        if (last) S.gsum[d] = S.aoff[d] + excl_sum - S.dscan[d];
         if (abort) S.last_block = 0xdeadu;
     }
     __syncthreads();
@@ -881,7 +885,7 @@ k_radix_pass(const uint32_t *kin, const uint32_t *vin,
                 const uint32_t key = S.keys[pad(lp)];
                 const uint32_t dd = ((key - lmin) >> shift) & (kBuckets - 1);
                 const int64_t pos = (int64_t)(uint32_t)(S.gbase[dd] + lp);
-                const uint64_t prefix = S.gsum[dd] + (run - S.dscan[dd]);
+                const uint64_t prefix = S.gsum[dd] + run;
                 Candidate c{(int64_t)((uint64_t)m - prefix), n - pos, pos, (int64_t)key};
                 if (cand_better(c, best)) best = c;
                 run += S.vals[pad(lp)];
@@ -890,15 +894,24 @@ k_radix_pass(const uint32_t *kin, const uint32_t *vin,
     } else {
         // m < 2^32 and n < 2^31: e * v' < 2^63, so 64-bit cross products
         // compare the densities exactly
+        // a thread's elements are sorted by digit: the digit's offsets are
+        // reloaded only when it changes
         uint32_t be = 0, bv = 0, bkey = 0, bpos = 0;
+        uint32_t cd = kBuckets, gb = 0;
+        uint64_t gs = 0;
         #pragma unroll
         for (int i = 0; i < kPassIpt; ++i) {
             const uint32_t lp = tid * kPassIpt + i;
             if (lp < tn) {
                 const uint32_t key = S.keys[pad(lp)];
                 const uint32_t dd = ((key - lmin) >> shift) & (kBuckets - 1);
-                const uint32_t pos = S.gbase[dd] + lp;
-                const uint32_t e = (uint32_t)((uint64_t)m - (S.gsum[dd] + (run - S.dscan[dd])));
+                if (dd != cd) {
+                    cd = dd;
+                    gb = S.gbase[dd];
+                    gs = S.gsum[dd];
+                }
+                const uint32_t pos = gb + lp;
+                const uint32_t e = (uint32_t)((uint64_t)m - (gs + run));
                 const uint32_t v = (uint32_t)(n - (int64_t)pos);
                 if (bv == 0 || (uint64_t)e * bv > (uint64_t)be * v) {
                     be = e; bv = v; bpos = pos; bkey = key;
