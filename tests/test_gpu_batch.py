@@ -141,3 +141,45 @@ def test_batch_peeling_equals_one_graph_per_launch(env):
         assert np.array_equal(r.loads, loads[base:base + g.n])
         assert np.array_equal(r.best_set, sets[base:base + best[i, 3]])
         base += g.n
+
+
+def _check_full(graphs, T, best, loads, sets, trace, sample):
+    """Every graph: its loads sum to T m (each iteration charges every edge
+    once) and its best set has the reported size and induced edge count;
+    the sampled graphs: every output equals the oracle's."""
+    bases = np.concatenate([[0], np.cumsum([g.n for g in graphs])])
+    for i, g in enumerate(graphs):
+        b = int(bases[i])
+        assert int(loads[b:b + g.n].sum()) == int(T[i]) * g.m, f"graph {i} load sum"
+        k = int(best[i, 3])
+        assert k == best[i, 1] and 0 < k <= g.n, f"graph {i} set size"
+        s = sets[b:b + k].astype(np.int64)
+        assert np.all(np.diff(s) > 0) and s[0] >= 0 and s[-1] < g.n, f"graph {i} set order"
+        inside = np.zeros(g.n, bool)
+        inside[s] = True
+        c = np.concatenate([[0], np.cumsum(inside[g.adj].astype(np.int64))])
+        deg_in = c[g.off[1:]] - c[g.off[:-1]]          # neighbours inside the set
+        assert int(deg_in[s].sum()) == 2 * int(best[i, 0]), f"graph {i} set edges"
+    for i in sample:
+        g, b = graphs[i], int(bases[i])
+        o = orc.run(g, orc.SORTING, int(T[i]))
+        assert tuple(best[i, :3]) == (o.best_edges, o.best_vertices, o.best_iter), f"graph {i}"
+        assert np.array_equal(loads[b:b + g.n], o.loads), f"graph {i} loads"
+        assert np.array_equal(sets[b:b + len(o.best_set)].astype(np.int64), o.best_set), f"graph {i} set"
+        assert np.array_equal(trace[i, :T[i]], o.trace), f"graph {i} trace"
+
+
+def test_batch_full_config(env):
+    """The batched configuration at full size: 4,096 graphs of the batch
+    recipe (n log-uniform in [50, 50,000]; ER, R-MAT and planted cliques),
+    T = 32 each, in one launch; all graphs checked by their invariants, the
+    8 largest and 24 random ones against the oracle output for output."""
+    import os
+    dsg, ctx = env
+    graphs = gg.batch_mix(G=4096, seed=4, processes=max(1, min(16, os.cpu_count() or 1)))
+    T = np.full(len(graphs), 32, np.int32)
+    best, loads, sets, trace = _run_batch(dsg, ctx, graphs, T)
+    rng = np.random.default_rng(21)
+    largest = sorted(range(len(graphs)), key=lambda i: -graphs[i].m)[:8]
+    sample = sorted(set(largest) | set(rng.choice(len(graphs), 24, replace=False).tolist()))
+    _check_full(graphs, T, best, loads, sets, trace, sample)
