@@ -99,8 +99,11 @@ typedef struct {
 
 /* Create a context on CUDA device `device`, issuing all work on
  * `cuda_stream` (a cudaStream_t; NULL = the legacy default stream).  The
- * stream is borrowed, not owned.  Returns DSG_ERR_CUDA if the device cannot
- * be used and DSG_ERR_INVALID if the library was not built for it. */
+ * stream is borrowed, not owned.  A context serves one host thread at a
+ * time: calls on the same context are not synchronised with one another
+ * (the server below gives each of its workers a context of its own).
+ * Returns DSG_ERR_CUDA if the device cannot be used and DSG_ERR_INVALID if
+ * the library was not built for it. */
 int dsg_create(int device, void *cuda_stream, dsg_ctx **out);
 
 /* Release a context.  Graphs and batches created on it must be freed first.
@@ -124,7 +127,14 @@ const char *dsg_last_error(const dsg_ctx *ctx);
  * device memory; a graph above 32,768 vertices or 2^20 arcs also gets the
  * degree-oriented copy and tile schedule of the whole-GPU edge scan (a
  * smaller one gets them on its first run on the whole-GPU path).
- * Errors: DSG_ERR_INVALID for a malformed graph, DSG_ERR_NOMEM. */
+ * flags: DSG_VALIDATE (above); DSG_SRC_DEVICE: offsets and adj are device
+ * pointers (copied device to device), otherwise host pointers.  A host graph
+ * of at least 2^24 arcs is copied in eight vertex-range chunks on a copy
+ * stream of the context while the oriented copy is prepared (pinned host
+ * memory lets the copies run asynchronously; pageable memory works, without
+ * the overlap).  The call returns after the graph is in place; the caller's
+ * arrays may then be freed.
+ * Errors: DSG_ERR_INVALID for a malformed graph, DSG_ERR_NOMEM, DSG_ERR_CUDA. */
 int dsg_upload_csr(dsg_ctx *ctx, int64_t n, const int64_t *offsets, const int32_t *adj,
                    uint32_t flags, dsg_graph **out);
 
