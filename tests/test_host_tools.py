@@ -1,0 +1,83 @@
+"""Host-side logic of the batch autotuner and the serving workload pool,
+with the library calls replaced by fakes (CPU only)."""
+import json
+import time
+
+import numpy as np
+import pytest
+
+
+@pytest.fixture()
+def tune(monkeypatch):
+    from paper_2311_04333_gb300 import _dsg, tune as t
+    calls = []
+
+    # a batch of 3,000 graphs and 5e6 edges whose launch takes longer with
+    # fewer threads per graph, except for a preferred size
+    def fake_info(batch):
+        return 3000, 10_000_000, 5_000_000
+
+    def fake_run(ctx, batch, variant, T, threads, best, eps_num=None, eps_den=None):
+        calls.append((variant, threads))
+        time.sleep({256: 0.040, 512: 0.005, 1024: 0.020}[threads])
+
+    monkeypatch.setattr(_dsg, "dsg_batch_info", fake_info)
+    monkeypatch.setattr(_dsg, "dsg_run_batch", fake_run)
+    monkeypatch.setattr(t, "_gpu_name", lambda: "fake GPU")
+    return t, calls
+
+
+def test_shape_class_rounds_up_to_powers_of_two():
+    from paper_2311_04333_gb300 import tune as t
+    assert t._shape_class(4096, 223_270_804) == "G2^12_m2^28"
+    assert t._shape_class(3000, 5_000_000) == "G2^12_m2^23"
+    assert t._shape_class(1, 0) == "G2^0_m2^0"
+
+
+def test_tuner_picks_fastest_and_caches(tune, tmp_path):
+    t, calls = tune
+    cache = tmp_path / "c.json"
+    rec = t.tune_batch(None, "batch", np.full(3000, 8, np.int32), cache_path=str(cache), reps=2)
+    assert rec["threads"] == 512
+    assert set(rec["ms"]) == {256, 512, 1024}
+    assert len(calls) == 3 * (1 + 2)                  # one warm-up and two timed runs each
+    stored = json.load(open(cache))
+    assert list(stored) == ["fake GPU|G2^12_m2^23|variant0"]
+    # a second call is served from the cache; force re-times
+    calls.clear()
+    assert t.tune_batch(None, "batch", None, cache_path=str(cache))["threads"] == 512
+    assert calls == []
+    t.tune_batch(None, "batch", None, cache_path=str(cache), force=True)
+    assert len(calls) == 6
+
+
+def test_tuner_keys_by_variant(tune, tmp_path):
+    t, calls = tune
+    cache = tmp_path / "c.json"
+    t.tune_batch(None, "batch", None, cache_path=str(cache), variant=0)
+    t.tune_batch(None, "batch", None, cache_path=str(cache), variant=1, eps_num=np.ones(3000, np.int64),
+                 eps_den=np.full(3000, 10, np.int64))
+    assert sorted(json.load(open(cache))) == ["fake GPU|G2^12_m2^23|variant0", "fake GPU|G2^12_m2^23|variant1"]
+    assert {v for v, _ in calls} == {0, 1}
+
+
+def test_tuner_ignores_a_broken_cache(tune, tmp_path):
+    t, _ = tune
+    cache = tmp_path / "c.json"
+    cache.write_text("{not json")
+    assert t.tune_batch(None, "batch", None, cache_path=str(cache))["threads"] == 512
+    assert "fake GPU|G2^12_m2^23|variant0" in json.load(open(cache))
+
+
+def test_request_pool_is_seeded_and_follows_the_recipe():
+    from paper_2311_04333_gb300 import serve
+    a = serve.request_pool(10, seed=7, m_hi=2e5)
+    b = serve.request_pool(10, seed=7, m_hi=2e5)
+    for x, y in zip(a, b):
+        assert x.n == y.n and np.array_equal(x.off, y.off) and np.array_equal(x.adj, y.adj)
+    c = serve.request_pool(10, seed=8, m_hi=2e5)
+    assert any(x.m != y.m for x, y in zip(a, c))
+    for g in a:
+        assert 16 <= g.n and 100 <= g.m <= 4e5          # log-uniform targets in [1e3, 2e5]
+        deg = np.diff(g.off)
+        assert deg.min() >= 1                           # generators drop isolated vertices
