@@ -1,0 +1,30 @@
+"""Stored expected values (tests/golden/, written by make_golden.py from the
+oracle alone): the oracle must keep producing them, so that a change to its
+arithmetic cannot pass silently.  The stored best of the sorting run is also
+pinned independently: it is the exact optimum by max-flow."""
+import json
+import os
+import sys
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, os.path.join(HERE, "golden"))
+
+import make_golden  # noqa: E402
+import graphgen as gg  # noqa: E402
+import oracle as orc  # noqa: E402
+
+
+def _stored():
+    with open(os.path.join(HERE, "golden", "planted_clique_T10.json")) as f:
+        return json.load(f)
+
+
+def test_oracle_reproduces_the_stored_values():
+    assert make_golden.records() == _stored()
+
+
+def test_stored_best_is_the_exact_optimum():
+    s = _stored()
+    (e, v), _ = orc.maxflow_densest(gg.er_planted_clique())
+    assert e * s["sorting"]["best"][1] == v * s["sorting"]["best"][0]
+    assert (s["graph"]["n"], s["sorting"]["best"][:2]) == (2000, [435, 30])
