@@ -157,6 +157,94 @@ def rmat(scale: int, edge_factor: int = 16, seed: int = 2, blocks: list[int] | N
                                blocks=list(blocks or [])), want_new_id)
 
 
+_SO_LARGE = os.path.join(_BUILD, "libgraphgen_large.so")
+_large_handle = None
+
+
+def _large_lib():
+    """The bucketed CSR builder (rmat_large.c, OpenMP), compiled on first use."""
+    global _large_handle
+    if _large_handle is None:
+        os.makedirs(_BUILD, exist_ok=True)
+        src = os.path.join(_HERE, "rmat_large.c")
+        deps = [src, os.path.join(_HERE, "graphgen.h")]
+        if not (os.path.exists(_SO_LARGE)
+                and all(os.path.getmtime(_SO_LARGE) >= os.path.getmtime(d) for d in deps)):
+            tmp = _SO_LARGE + f".tmp{os.getpid()}"
+            subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-fopenmp", "-shared", "-fPIC",
+                                   "-o", tmp, src])
+            os.replace(tmp, _SO_LARGE)
+        lib = ctypes.CDLL(_SO_LARGE)
+        i64, u64, u32, p = ctypes.c_int64, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_void_p
+        lib.gg_large_count.argtypes = [ctypes.c_int, i64, u64, p, p, i64, p]
+        lib.gg_large_count.restype = None
+        lib.gg_large_bucket.argtypes = [ctypes.c_int, i64, u64, p, p, i64, u32, u32, p, p, i64, p, p]
+        lib.gg_large_bucket.restype = i64
+        _large_handle = lib
+    return _large_handle
+
+
+def rmat_large(scale: int, edge_factor: int = 16, seed: int = 2, blocks: list[int] | None = None,
+               bucket_arcs: int = 1 << 30, log=None) -> Graph:
+    """The `rmat` recipe (isolated vertices dropped) built bucket by bucket of
+    source vertices, so that host memory holds the CSR plus two buffers of
+    `bucket_arcs` 64-bit keys instead of the whole pair list: scale 27 fits in
+    about 40 GB.  Same graph as `rmat`, which a CPU test checks."""
+    lib = _large_lib()
+    E = edge_factor << scale
+    n_raw = 1 << scale
+    if blocks:
+        extra = sum(s * (s - 1) // 2 for s in blocks)
+        cap = int(extra / 2 + 10 * math.sqrt(extra) + 100)
+        xu = np.zeros(cap, dtype=np.uint32)
+        xv = np.zeros(cap, dtype=np.uint32)
+        sz = np.asarray(blocks, dtype=np.int64)
+        nx = _lib().gg_planted_blocks(scale, len(blocks), _ptr(sz), seed, _ptr(xu), _ptr(xv), 0, cap)
+        if nx < 0:
+            raise RuntimeError("edge buffer too small")
+    else:
+        nx = 0
+        xu = xv = np.zeros(1, dtype=np.uint32)
+    cnt = np.zeros(n_raw, dtype=np.uint32)
+    lib.gg_large_count(scale, E, seed, _ptr(xu), _ptr(xv), nx, _ptr(cnt))
+    csum = np.concatenate([[0], np.cumsum(cnt, dtype=np.int64)])
+    raw_arcs = int(csum[-1])
+    bucket_arcs = max(min(bucket_arcs, raw_arcs), int(cnt.max(initial=0)), 1)
+    del cnt
+    adj = np.empty(max(raw_arcs, 1), dtype=np.int32)
+    deg = np.zeros(n_raw, dtype=np.int64)
+    buf = np.empty(bucket_arcs, dtype=np.uint64)
+    tmp = np.empty(bucket_arcs, dtype=np.uint64)
+    at, lo = 0, 0
+    while lo < n_raw:
+        hi = int(np.searchsorted(csum, csum[lo] + bucket_arcs, side="right")) - 1
+        hi = max(min(hi, n_raw), lo + 1)
+        k = lib.gg_large_bucket(scale, E, seed, _ptr(xu), _ptr(xv), nx, lo, hi, _ptr(buf), _ptr(tmp),
+                                bucket_arcs, adj.ctypes.data + 4 * at, deg.ctypes.data + 8 * lo)
+        if k < 0:
+            raise RuntimeError("bucket buffer too small")
+        if log:
+            log(f"bucket [{lo}, {hi}): {k} arcs")
+        at += k
+        lo = hi
+    del buf, tmp, csum
+    keep = deg > 0
+    nid = np.cumsum(keep, dtype=np.int64) - 1
+    nid = nid.astype(np.int32)
+    step = 1 << 28
+    for a in range(0, at, step):
+        b = min(a + step, at)
+        adj[a:b] = nid[adj[a:b]]
+    del nid
+    nk = int(keep.sum())
+    off = np.zeros(nk + 1, dtype=np.int64)
+    np.cumsum(deg[keep], out=off[1:])
+    name = f"rmat{scale}_ef{edge_factor}_s{seed}" + (f"+{len(blocks)}blocks" if blocks else "")
+    return Graph(nk, off, adj[:at], name,
+                 dict(recipe="rmat", scale=scale, edge_factor=edge_factor, blocks=list(blocks or []),
+                      n_raw=n_raw, pairs=E + nx))
+
+
 def block_vertices(scale: int, seed: int, blocks: list[int]) -> list[np.ndarray]:
     """Raw (pre-relabel) vertex ids of each planted block."""
     mul = ctypes.c_uint64(0)
