@@ -12,8 +12,10 @@ e2e   = the same metric through the C ABI with host buffers: each step
 The line also carries the batched form (4,096 small graphs in one persistent
 launch against one dsg_run per graph) and serving (Poisson arrivals through
 the native request loop: p50/p99 latency and throughput).
-Multi-GPU: the path does not shard (replicas only); each rank runs its own
-replica of the workload and value aggregates the replicas.
+Multi-GPU: a single graph does not shard (replicas only): each rank runs its
+own replica of the headline workload and value aggregates the replicas.  The
+batched form shards by graph: each rank runs a contiguous, cost-balanced
+range of the 4,096 graphs and the per-graph results are gathered.
 --impl reference times the CPU oracle (the only reference this build has)
 on a bounded sample of the workload (same recipe at a smaller scale).
 """
@@ -206,88 +208,114 @@ def cpu_parallel_baseline(T: int = 10, reps: int = 3) -> dict:
                       f"fastest of {reps} runs: {dt:.2f} s (slowest {max(dts):.2f} s)"}
 
 
-def bench_batch(dsg, ctx, graphs, args) -> dict:
+def bench_batch(dsg, ctx, graphs, args, ws: int = 1, rank: int = 0) -> dict:
     """Graphs/s of the batched launch (autotuned block size) against one
-    dsg_run per graph on the same GPU, with identical per-graph results."""
+    dsg_run per graph on the same GPU, with identical per-graph results.
+    With N ranks the batch is sharded by graph: rank r runs its contiguous,
+    cost-balanced range (shard.graph_ranges), the job's graphs/s is all G
+    graphs over the slowest rank's time, and the per-graph results are
+    gathered on every rank (no collective on the data path)."""
     import numpy as np
     import torch
-    from paper_2311_04333_gb300 import tune
+    from paper_2311_04333_gb300 import shard, tune
     G = len(graphs)
-    T = np.full(G, BATCH_T, np.int32)
-    b = dsg.dsg_upload_batch(ctx, [(g.n, g.off, g.adj) for g in graphs], 0)
+    lo, hi = shard.my_range([shard.graph_cost(g.n, g.m) for g in graphs], rank, ws)
+    mine = graphs[lo:hi]
+    Gl = len(mine)
+    T = np.full(Gl, BATCH_T, np.int32)
+    b = dsg.dsg_upload_batch(ctx, [(g.n, g.off, g.adj) for g in mine], 0)
     Gb, N, M = dsg.dsg_batch_info(b)
     rec = tune.tune_batch(ctx, b, T, force=True)
     th = rec["threads"]
-    best_b = np.zeros(4 * G, np.int64)
+    best_b = np.zeros(4 * Gl, np.int64)
     dsg.dsg_run_batch(ctx, b, dsg.DSG_SORTING, T, th, best_b)
     torch.cuda.synchronize()
+    _barrier(ws)
     t0 = time.perf_counter()
     for _ in range(args.batch_steps):
         dsg.dsg_run_batch(ctx, b, dsg.DSG_SORTING, T, th, best_b)
-    tb = (time.perf_counter() - t0) / args.batch_steps
+    tb = _max_over_ranks((time.perf_counter() - t0) / args.batch_steps, ws)
     dsg.dsg_free_batch(b)
     # one graph per launch (graphs resident, outputs: the best triple)
-    hs = [dsg.dsg_upload_csr(ctx, g.n, g.off, g.adj, 0) for g in graphs]
-    best_1 = np.zeros((G, 4), np.int64)
+    hs = [dsg.dsg_upload_csr(ctx, g.n, g.off, g.adj, 0) for g in mine]
+    best_1 = np.zeros((Gl, 4), np.int64)
     dsg.dsg_run(ctx, hs[0], dsg.DSG_SORTING, BATCH_T)
     torch.cuda.synchronize()
+    _barrier(ws)
     t0 = time.perf_counter()
     for i, h in enumerate(hs):
         r = dsg.dsg_run(ctx, h, dsg.DSG_SORTING, BATCH_T)
         best_1[i] = (r["best_edges"], r["best_vertices"], r["best_iter"], r["best_set_size"])
-    t1 = time.perf_counter() - t0
+    t1 = _max_over_ranks(time.perf_counter() - t0, ws)
     for h in hs:
         dsg.dsg_free_graph(h)
-    same = bool(np.array_equal(best_b.reshape(G, 4), best_1))
+    all_b = shard.gather_rows(best_b.reshape(Gl, 4), ws)
+    all_1 = shard.gather_rows(best_1, ws)
+    same = bool(all_b.shape == (G, 4) and np.array_equal(all_b, all_1))
+    Mtot = int(_sum_over_ranks(float(M), ws))
+    Ntot = int(_sum_over_ranks(float(N), ws))
     out = {"workload": f"{G} graphs, n log-uniform in [50, 50000] (ER / R-MAT / planted clique), "
-                       f"N={N}, M={M}, PaRSorting++ T={BATCH_T} each",
+                       f"N={Ntot}, M={Mtot}, PaRSorting++ T={BATCH_T} each",
            "graphs_per_s": G / tb, "ms_per_batch": tb * 1e3, "threads_per_graph": th,
            "autotune_ms": rec["ms"], "one_per_launch_graphs_per_s": G / t1,
            "one_per_launch_ms": t1 * 1e3, "speedup": t1 / tb, "identical_results": same,
-           "gteps_batched": M * BATCH_T / tb / 1e9}
-    out["peeling"] = bench_batch_peeling(dsg, ctx, graphs, args)
+           "gteps_batched": Mtot * BATCH_T / tb / 1e9,
+           "sharding": {"ranks": ws, "split": "contiguous graph ranges balanced by 2m + n",
+                        "rank0_range": [lo, hi] if rank == 0 else None}}
+    out["peeling"] = bench_batch_peeling(dsg, ctx, graphs, args, ws, rank)
     return out
 
 
-def bench_batch_peeling(dsg, ctx, graphs, args) -> dict:
-    """Batched PaRGreedy++ (eps = 1/10, T = BATCH_T_PEEL) on the same batch;
-    one dsg_run per graph is timed on a seeded sample of the graphs (it takes
-    minutes on all of them) and compared with the batch's results there."""
+def bench_batch_peeling(dsg, ctx, graphs, args, ws: int = 1, rank: int = 0) -> dict:
+    """Batched PaRGreedy++ (eps = 1/10, T = BATCH_T_PEEL) on the same batch,
+    sharded by graph as above; one dsg_run per graph is timed on a seeded
+    sample of the graphs (it takes minutes on all of them; each rank runs the
+    sampled graphs of its range) and compared with the batch's results there."""
     import numpy as np
     import torch
-    from paper_2311_04333_gb300 import tune
+    from paper_2311_04333_gb300 import shard, tune
     G = len(graphs)
-    T = np.full(G, BATCH_T_PEEL, np.int32)
-    p = np.ones(G, np.int64)
-    q = np.full(G, 10, np.int64)
-    b = dsg.dsg_upload_batch(ctx, [(g.n, g.off, g.adj) for g in graphs], 0)
+    lo, hi = shard.my_range([shard.graph_cost(g.n, g.m) for g in graphs], rank, ws)
+    mine = graphs[lo:hi]
+    Gl = len(mine)
+    T = np.full(Gl, BATCH_T_PEEL, np.int32)
+    p = np.ones(Gl, np.int64)
+    q = np.full(Gl, 10, np.int64)
+    b = dsg.dsg_upload_batch(ctx, [(g.n, g.off, g.adj) for g in mine], 0)
     Gb, N, M = dsg.dsg_batch_info(b)
     rec = tune.tune_batch(ctx, b, T, force=True, variant=dsg.DSG_PEELING, eps_num=p, eps_den=q)
     th = rec["threads"]
-    best_b = np.zeros(4 * G, np.int64)
+    best_b = np.zeros(4 * Gl, np.int64)
     torch.cuda.synchronize()
+    _barrier(ws)
     t0 = time.perf_counter()
     for _ in range(args.batch_steps):
         dsg.dsg_run_batch(ctx, b, dsg.DSG_PEELING, T, th, best_b, eps_num=p, eps_den=q)
-    tb = (time.perf_counter() - t0) / args.batch_steps
+    tb = _max_over_ranks((time.perf_counter() - t0) / args.batch_steps, ws)
     dsg.dsg_free_batch(b)
-    sample = np.random.default_rng(BATCH_SEED).choice(G, size=min(G, 128), replace=False)
-    hs = [dsg.dsg_upload_csr(ctx, graphs[i].n, graphs[i].off, graphs[i].adj, 0) for i in sample]
-    dsg.dsg_run(ctx, hs[0], dsg.DSG_PEELING, BATCH_T_PEEL, 1, 10)
-    best_1 = np.zeros((len(sample), 4), np.int64)
+    sample = np.sort(np.random.default_rng(BATCH_SEED).choice(G, size=min(G, 128), replace=False))
+    local = [int(i) for i in sample if lo <= i < hi]
+    hs = [dsg.dsg_upload_csr(ctx, graphs[i].n, graphs[i].off, graphs[i].adj, 0) for i in local]
+    if hs:
+        dsg.dsg_run(ctx, hs[0], dsg.DSG_PEELING, BATCH_T_PEEL, 1, 10)
+    best_1 = np.zeros((len(local), 4), np.int64)
     torch.cuda.synchronize()
+    _barrier(ws)
     t0 = time.perf_counter()
     for k, h in enumerate(hs):
         r = dsg.dsg_run(ctx, h, dsg.DSG_PEELING, BATCH_T_PEEL, 1, 10)
         best_1[k] = (r["best_edges"], r["best_vertices"], r["best_iter"], r["best_set_size"])
-    t1 = time.perf_counter() - t0
+    t1 = _max_over_ranks(time.perf_counter() - t0, ws)
     for h in hs:
         dsg.dsg_free_graph(h)
     m_sample = sum(graphs[i].m for i in sample)
-    same = bool(np.array_equal(best_b.reshape(G, 4)[sample], best_1))
+    got = shard.gather_rows(best_b.reshape(Gl, 4)[[i - lo for i in local]], ws)
+    want = shard.gather_rows(best_1, ws)
+    same = bool(got.shape == (len(sample), 4) and np.array_equal(got, want))
+    Mtot = int(_sum_over_ranks(float(M), ws))
     return {"workload": f"same {G} graphs, PaRGreedy++ eps=1/10, T={BATCH_T_PEEL} each",
             "graphs_per_s": G / tb, "ms_per_batch": tb * 1e3, "threads_per_graph": th,
-            "autotune_ms": rec["ms"], "gteps_batched": M * BATCH_T_PEEL / tb / 1e9,
+            "autotune_ms": rec["ms"], "gteps_batched": Mtot * BATCH_T_PEEL / tb / 1e9,
             "one_per_launch_sample": len(sample),
             "one_per_launch_graphs_per_s": len(sample) / t1,
             "one_per_launch_gteps": m_sample * BATCH_T_PEEL / t1 / 1e9,
@@ -605,7 +633,7 @@ def main():
     # ---- batched form: 4,096 graphs, one persistent launch vs one graph per launch
     batched = None
     if not args.no_batch:
-        batched = bench_batch(dsg, ctx, graphs_batch, args)
+        batched = bench_batch(dsg, ctx, graphs_batch, args, ws, rank)
 
     # ---- R-MAT scale 20: both variants
     rmat20 = bench_rmat20(dsg, ctx, gg, stream, args)

@@ -1,7 +1,8 @@
 """The multi-rank logic of bench.py on CPU: world_size 2 over gloo (127.0.0.1).
-The path does not shard, so N GPUs run N replicas; the job value is all
-ranks' units over the slowest rank's time, and the reference arm runs on
-rank 0 alone."""
+A single graph does not shard, so N GPUs run N replicas of it; the job value
+is all ranks' units over the slowest rank's time, and the reference arm runs
+on rank 0 alone.  Batched work shards by graph: contiguous, cost-balanced
+graph ranges per rank, results gathered in graph order."""
 import os
 import socket
 import subprocess
@@ -56,3 +57,59 @@ def test_reference_arm_other_ranks_exit_without_work(rank):
                         "--steps", "1", "--warmup", "0"], env=env, cwd=ROOT, capture_output=True, text=True,
                        timeout=120)
     assert r.returncode == 0 and r.stdout.strip() == ""
+
+
+# ---- batched work sharded by graph (contiguous, cost-balanced ranges)
+
+def _shard_worker(rank, ws, port, costs, out):
+    import numpy as np
+    import torch.distributed as dist
+    sys.path.insert(0, ROOT)
+    from paper_2311_04333_gb300 import shard
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank, world_size=ws)
+    try:
+        lo, hi = shard.my_range(costs, rank, ws)
+        # each rank's per-graph result rows: (graph index, cost, rank)
+        rows = np.array([[g, costs[g], rank] for g in range(lo, hi)], dtype=np.int64).reshape(-1, 3)
+        out[rank] = (lo, hi, shard.gather_rows(rows, ws).tolist())
+    finally:
+        dist.destroy_process_group()
+
+
+def test_batch_shards_gathered_over_two_ranks():
+    import numpy as np
+    rng = np.random.default_rng(3)
+    costs = [int(x) for x in rng.integers(1, 10_000, size=37)]
+    ws = 2
+    port = _free_port()
+    out = mp.get_context("spawn").Manager().dict()
+    mp.start_processes(_shard_worker, args=(ws, port, costs, out), nprocs=ws, start_method="spawn", join=True)
+    (lo0, hi0, rows0), (lo1, hi1, rows1) = out[0], out[1]
+    assert (lo0, hi1) == (0, len(costs)) and hi0 == lo1          # disjoint, contiguous, complete
+    assert rows0 == rows1                                        # every rank holds all results
+    assert [r[0] for r in rows0] == list(range(len(costs)))     # in graph order
+    assert [r[2] for r in rows0] == [0] * hi0 + [1] * (len(costs) - hi0)
+    share = [sum(costs[lo0:hi0]), sum(costs[lo1:hi1])]
+    assert abs(share[0] - sum(costs) / 2) <= max(costs)
+
+
+def test_graph_ranges_balance_and_cover():
+    import numpy as np
+    sys.path.insert(0, ROOT)
+    from paper_2311_04333_gb300 import shard
+    rng = np.random.default_rng(4)
+    for ws in (1, 2, 3, 4, 8):
+        for G in (0, 1, 5, 64, 4096):
+            costs = rng.integers(0, 1_000_000, size=G)
+            rs = shard.graph_ranges(costs, ws)
+            assert len(rs) == ws and rs[0][0] == 0 and rs[-1][1] == G
+            assert all(a[1] == b[0] for a, b in zip(rs, rs[1:]))
+            assert all(lo <= hi for lo, hi in rs)
+            tot = int(costs.sum())
+            cmax = int(costs.max()) if G else 0
+            for lo, hi in rs:
+                assert abs(int(costs[lo:hi].sum()) - tot / ws) <= cmax
+    # one graph per rank when costs are equal and the count divides
+    assert shard.graph_ranges([5] * 8, 4) == [(0, 2), (2, 4), (4, 6), (6, 8)]
+    # the cost of a graph is its arcs plus its vertices
+    assert shard.graph_cost(10, 20) == 50
