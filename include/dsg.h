@@ -116,6 +116,40 @@ void dsg_destroy(dsg_ctx *ctx);
  * on the same context. */
 const char *dsg_last_error(const dsg_ctx *ctx);
 
+/* ---- test-only fault hooks ---------------------------------------------- */
+
+/* Knobs that make the library's failure paths run, for tests of failure
+ * detection (the paper has no counterpart: its failures are not modelled).
+ * All are off by default and cost nothing when off.
+ *   DSG_DEBUG_SPIN_LIMIT (ctx): polls before a bounded device-side wait (the
+ *     radix passes' look-back, the PaRGreedy++ grid barrier) gives up, for
+ *     later dsg_run calls on ctx; 0 restores the default (about a second);
+ *   DSG_DEBUG_STALL (ctx): 1 makes tile 0 of every radix pass withhold its
+ *     look-back words, 2 keeps block 1 of the PaRGreedy++ round kernel from
+ *     arriving at its first grid barrier (graphs of 8,192 or more vertices),
+ *     in later dsg_run calls on ctx that take the whole-GPU path; the waits
+ *     on what is withheld then run out after the spin limit, the run
+ *     returns DSG_ERR_TIMEOUT and the context and graph stay usable; 0 turns
+ *     it off;
+ *   DSG_DEBUG_FAIL_ALLOC (process-wide, ctx may be NULL): the value-th
+ *     memory allocation the library makes from now on (device memory, or
+ *     the host context of dsg_create) fails as if memory were exhausted,
+ *     so the call that made it returns DSG_ERR_NOMEM; 0 turns it off;
+ *   DSG_DEBUG_FAIL_UPLOAD (process-wide, ctx may be NULL): the value-th
+ *     host-to-device copy of dsg_upload_csr / dsg_upload_batch from now on
+ *     fails and that call returns DSG_ERR_CUDA; 0 turns it off.
+ * The environment variable DSG_FAULT ("alloc:N", "upload:N", or both
+ * separated by a comma), read when the library is loaded, sets the two
+ * process-wide countdowns the same way.  Returns DSG_ERR_INVALID for an
+ * unknown knob, a value out of range, or a NULL ctx where one is needed. */
+typedef enum {
+    DSG_DEBUG_SPIN_LIMIT = 1,
+    DSG_DEBUG_STALL = 2,
+    DSG_DEBUG_FAIL_ALLOC = 3,
+    DSG_DEBUG_FAIL_UPLOAD = 4
+} dsg_debug_knob;
+int dsg_debug_set(dsg_ctx *ctx, int knob, int64_t value);
+
 /* Upload an undirected simple graph in CSR form (Sec. 2: G = (V, E)).
  *   n: number of vertices, 1 <= n < 2^31;
  *   offsets[n+1]: int64, offsets[0] = 0, non-decreasing, offsets[n] = 2m
@@ -361,27 +395,35 @@ int dsg_get_stats(dsg_ctx *ctx, double *ms, int64_t *launches, int64_t *bytes, i
  *
  * Given loads[n] and A[n] (device pointers, uint32, by vertex id) it orders
  * the vertices by (loads[v], v) and returns the first densest suffix of that
- * order, where a suffix's edge count is the sum of A over it (Alg. 3's
- * suffix step with B = SuffixSum(A)).  When A is the later-neighbour count of the
- * order (the edge scan of dsg_run), m = sum(A) is the graph's edge count.
- *   m: sum of A[0..n-1] (the edges of the whole graph);
+ * order: the suffix, taken among all n non-empty suffixes, whose edge count
+ * (the sum of A over its vertices) divided by its vertex count is largest,
+ * the largest such suffix on ties.  When A counts, for every vertex, its
+ * neighbours later in that order, the edge count of a suffix is the number
+ * of edges of the subgraph it induces.
+ *   m: the sum of A[0..n-1] (the edges of the whole graph), below 2^48.  The
+ *      result is undefined unless m equals that sum;
  *   result: device pointer to int64[5], written on `cuda_stream`:
  *     (edges, vertices) of the densest suffix (largest suffix on ties),
  *     the position of its first vertex in the order, that vertex's load,
- *     and a device status (0, or DSG_ERR_TIMEOUT if a bounded wait gave up).
+ *     and a device status: 0, or DSG_ERR_TIMEOUT if a bounded wait gave up
+ *     (then the first four values are undefined).
  * The call is asynchronous: it only enqueues kernels on `cuda_stream` and
  * never synchronises.  It returns DSG_ERR_INVALID when n < 1,
- * n > DSG_NOALLOC_MAX_VERTICES, m < 0 or a pointer is NULL, and DSG_ERR_CUDA
- * when a launch fails.  loads and A are read only.
+ * n > DSG_NOALLOC_MAX_VERTICES, m < 0, m >= 2^48 or a pointer is NULL, and
+ * DSG_ERR_CUDA when a launch fails or when a CUDA error is already pending
+ * on the calling thread (that error is left in place for its owner and
+ * nothing is launched).  loads and A are read only.
  *
  * Scratch memory: one static device array of about 4.4 MB inside libdsg,
  * held by every GPU that loads the library until the process exits.  Every
- * call uses the same array and leaves its contents behind (the next call
- * resets what must start from zero), so calls whose work overlaps on the GPU
- * (on different streams or from different host threads) race and must be
- * ordered by the caller.  The first call on a device looks up the array's
- * device address (cudaGetSymbolAddress) with that device current; make that
- * first call before any stream capture. */
+ * call uses the same array and leaves its contents behind; each call clears
+ * what must start from zero (its look-back words and control block) before
+ * use, so results never depend on earlier calls.  Calls whose work overlaps
+ * on the GPU (on different streams or from different host threads) race on
+ * the array and must be ordered by the caller.  The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress) with that
+ * device current, once per device even when several host threads make that
+ * first call together; make that first call before any stream capture. */
 int dsg_densest_suffix_noalloc(const uint32_t *loads, const uint32_t *A, int64_t n, int64_t m,
                                int64_t *result, void *cuda_stream);
 

@@ -66,6 +66,7 @@ def _load():
     lib.dsg_destroy.restype = None
     lib.dsg_last_error.argtypes = [P]
     lib.dsg_last_error.restype = ctypes.c_char_p
+    lib.dsg_debug_set.argtypes = [P, I, I64]
     lib.dsg_upload_csr.argtypes = [P, I64, P, P, U32, ctypes.POINTER(P)]
     lib.dsg_graph_info.argtypes = [P, P, P, P]
     lib.dsg_run.argtypes = [P, I, I32, I64, I64, P, ctypes.POINTER(dsg_result)]
@@ -136,6 +137,17 @@ def dsg_destroy(ctx) -> None:
 
 def dsg_last_error(ctx) -> str:
     return LIB.dsg_last_error(ctx).decode()
+
+
+DSG_DEBUG_SPIN_LIMIT, DSG_DEBUG_STALL, DSG_DEBUG_FAIL_ALLOC, DSG_DEBUG_FAIL_UPLOAD = 1, 2, 3, 4
+
+
+def dsg_debug_set(ctx, knob: int, value: int) -> None:
+    """Test-only fault hooks (see dsg.h): spin limit and stalled waits per
+    context, allocation / upload failure countdowns process-wide."""
+    rc = LIB.dsg_debug_set(ctx, knob, value)
+    if rc != DSG_OK:
+        raise DsgError(rc, f"dsg_debug_set(knob={knob}, value={value})")
 
 
 def dsg_upload_csr(ctx, n: int, offsets, adj, flags: int = 0):
@@ -263,8 +275,8 @@ def dsg_densest_suffix_noalloc(loads, A, n: int, m: int, result, stream: int | N
             raise TypeError("dsg_densest_suffix_noalloc takes contiguous CUDA tensors")
     rc = LIB.dsg_densest_suffix_noalloc(loads.data_ptr(), A.data_ptr(), n, m, result.data_ptr(), stream)
     if rc != DSG_OK:
-        raise DsgError(rc, f"dsg_densest_suffix_noalloc(n={n}, m={m}) rejected "
-                           f"(n must be in [1, {DSG_NOALLOC_MAX_VERTICES}])")
+        raise DsgError(rc, f"dsg_densest_suffix_noalloc(n={n}, m={m}) failed "
+                           f"(n must be in [1, {DSG_NOALLOC_MAX_VERTICES}], m in [0, 2^48))")
 
 
 def dsg_upload_batch(ctx, graphs, flags: int = 0):
@@ -364,7 +376,7 @@ def dsg_server_destroy(server) -> None:
 
 DSG_NOALLOC_MAX_VERTICES = 262144
 
-EXPORTED = ["dsg_create", "dsg_destroy", "dsg_last_error", "dsg_upload_csr", "dsg_graph_info",
+EXPORTED = ["dsg_create", "dsg_destroy", "dsg_last_error", "dsg_debug_set", "dsg_upload_csr", "dsg_graph_info",
             "dsg_run", "dsg_free_graph", "dsg_set_profiling", "dsg_get_stats",
             "dsg_densest_suffix_noalloc", "dsg_upload_batch", "dsg_batch_info", "dsg_run_batch",
             "dsg_free_batch", "dsg_coreness", "dsg_apx_coreness", "dsg_run_pruned", "dsg_run_pruned_apx", "dsg_server_create", "dsg_server_submit", "dsg_server_wait",

@@ -40,6 +40,9 @@ struct dsg_ctx {
     // mark the chunks, the last one the allocation they are copied into
     cudaStream_t copy = nullptr;
     cudaEvent_t up_ev[kUploadChunks + 1] = {};
+    // test-only knobs of the bounded waits (dsg_debug_set)
+    uint32_t dbg_spin_limit = 0;
+    int32_t dbg_stall = 0;
 };
 
 namespace dsg {
@@ -185,7 +188,7 @@ int ensure_run_bufs(dsg_ctx *ctx, dsg_graph *G, int32_t T)
         size_t total = 0;
         for (size_t s : sz) total += align256(s);
         char *mem = nullptr;
-        CK(cudaMallocAsync((void **)&mem, total, ctx->stream), "run buffers");
+        CK(dev_malloc((void **)&mem, total, ctx->stream), "run buffers");
         char *p = mem;
         auto take = [&](size_t s) { char *q = p; p += align256(s); return (void *)q; };
         b.loads = (uint32_t *)take(sz[0]);
@@ -220,8 +223,8 @@ int ensure_run_bufs(dsg_ctx *ctx, dsg_graph *G, int32_t T)
         if (G->npass_log) cudaFreeAsync(G->npass_log, ctx->stream);
         b.trace = nullptr;
         G->npass_log = nullptr;
-        CK(cudaMallocAsync((void **)&b.trace, sizeof(int64_t) * 3 * (size_t)T, ctx->stream), "trace");
-        CK(cudaMallocAsync((void **)&G->npass_log, sizeof(int32_t) * (size_t)T, ctx->stream), "npass log");
+        CK(dev_malloc((void **)&b.trace, sizeof(int64_t) * 3 * (size_t)T, ctx->stream), "trace");
+        CK(dev_malloc((void **)&G->npass_log, sizeof(int32_t) * (size_t)T, ctx->stream), "npass log");
         G->trace_cap = T;
     }
     return DSG_OK;
@@ -256,7 +259,7 @@ int build_grid(dsg_ctx *ctx, dsg_graph *G, const UploadChunks *chunks)
     G->g.hot_id = G->hot;
     void *tmp = nullptr;
     const size_t tmp_bytes = (size_t)schedule_tmp_count(n) * sizeof(int64_t);
-    if ((e = cudaMallocAsync(&tmp, tmp_bytes, ctx->stream)) != cudaSuccess) return cuda_fail(ctx, e, "schedule scratch");
+    if ((e = dev_malloc(&tmp, tmp_bytes, ctx->stream)) != cudaSuccess) return cuda_fail(ctx, e, "schedule scratch");
     GraphDev og = G->g;
     og.off = G->ooff;
     e = build_schedule(og, tmp, tmp_bytes, ctx->stream, &G->g.n_items, &G->g.n_heavy, &G->items, &G->heavy_mem);
@@ -294,7 +297,7 @@ int run_block(dsg_ctx *ctx, dsg_graph *G, int variant, int32_t T, int64_t p, int
         if (G->bk_mem) cudaFreeAsync(G->bk_mem, s);
         G->bk_mem = nullptr;
         G->bk_bytes = 0;
-        CK(cudaMallocAsync(&G->bk_mem, need, s), "block-path buffers");
+        CK(dev_malloc(&G->bk_mem, need, s), "block-path buffers");
         G->bk_bytes = need;
     }
     char *mp = (char *)G->bk_mem;
@@ -373,15 +376,17 @@ int dsg_create(int device, void *cuda_stream, dsg_ctx **out)
 {
     if (!out) return DSG_ERR_INVALID;
     *out = nullptr;
-    int ndev = 0;
-    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return DSG_ERR_CUDA;
-    if (device < 0 || device >= ndev) return DSG_ERR_INVALID;
-    if (cudaSetDevice(device) != cudaSuccess) return DSG_ERR_CUDA;
-    cudaDeviceProp prop;
-    if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) return DSG_ERR_CUDA;
-    if (prop.major * 10 + prop.minor < 100) return DSG_ERR_INVALID;   // built for sm_103a only
-    dsg_ctx *ctx = new (std::nothrow) dsg_ctx;
+    // the host-side context first: its failure touches no device
+    dsg_ctx *ctx = host_alloc_fault() ? nullptr : new (std::nothrow) dsg_ctx;
     if (!ctx) return DSG_ERR_NOMEM;
+    auto bail = [&](int code) { delete ctx; return code; };
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return bail(DSG_ERR_CUDA);
+    if (device < 0 || device >= ndev) return bail(DSG_ERR_INVALID);
+    if (cudaSetDevice(device) != cudaSuccess) return bail(DSG_ERR_CUDA);
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) return bail(DSG_ERR_CUDA);
+    if (prop.major * 10 + prop.minor < 100) return bail(DSG_ERR_INVALID);   // built for sm_103a only
     ctx->device = device;
     ctx->stream = (cudaStream_t)cuda_stream;
     ctx->sm_count = prop.multiProcessorCount;
@@ -395,11 +400,10 @@ int dsg_create(int device, void *cuda_stream, dsg_ctx **out)
         uint64_t keep = ~0ull;
         cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
     }
-    if (cudaMalloc((void **)&ctx->err_flags, 64) != cudaSuccess ||
+    if (host_alloc_fault() || cudaMalloc((void **)&ctx->err_flags, 64) != cudaSuccess ||
         cudaMalloc((void **)&ctx->red, 64) != cudaSuccess) {
-        cudaFree(ctx->err_flags);
-        delete ctx;
-        return DSG_ERR_NOMEM;
+        if (ctx->err_flags) cudaFree(ctx->err_flags);
+        return bail(DSG_ERR_NOMEM);
     }
     *out = ctx;
     return DSG_OK;
@@ -425,6 +429,30 @@ void dsg_destroy(dsg_ctx *ctx)
 }
 
 const char *dsg_last_error(const dsg_ctx *ctx) { return ctx ? ctx->err.c_str() : "no context"; }
+
+int dsg_debug_set(dsg_ctx *ctx, int knob, int64_t value)
+{
+    switch (knob) {
+    case DSG_DEBUG_SPIN_LIMIT:
+        if (!ctx || value < 0 || value > 0xffffffffll) return DSG_ERR_INVALID;
+        ctx->dbg_spin_limit = (uint32_t)value;
+        return DSG_OK;
+    case DSG_DEBUG_STALL:
+        if (!ctx || value < 0 || value > 2) return DSG_ERR_INVALID;
+        ctx->dbg_stall = (int32_t)value;
+        return DSG_OK;
+    case DSG_DEBUG_FAIL_ALLOC:
+        if (value < 0) return DSG_ERR_INVALID;
+        set_alloc_fault(value);
+        return DSG_OK;
+    case DSG_DEBUG_FAIL_UPLOAD:
+        if (value < 0) return DSG_ERR_INVALID;
+        set_upload_fault(value);
+        return DSG_OK;
+    default:
+        return ctx ? fail(ctx, DSG_ERR_INVALID, "unknown debug knob %d", knob) : DSG_ERR_INVALID;
+    }
+}
 
 int dsg_upload_csr(dsg_ctx *ctx, int64_t n, const int64_t *offsets, const int32_t *adj,
                    uint32_t flags, dsg_graph **out)
@@ -475,12 +503,15 @@ int dsg_upload_csr(dsg_ctx *ctx, int64_t n, const int64_t *offsets, const int32_
     };
     cudaError_t e;
     const cudaMemcpyKind kind = dev_src ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-    if ((e = cudaMallocAsync((void **)&G->off, sizeof(int64_t) * (size_t)(n + 1), ctx->stream)) != cudaSuccess)
+    if ((e = dev_malloc((void **)&G->off, sizeof(int64_t) * (size_t)(n + 1), ctx->stream)) != cudaSuccess)
         return bail(cuda_fail(ctx, e, "offsets allocation"));
-    if ((e = cudaMallocAsync((void **)&G->adj, sizeof(int32_t) * (size_t)(arcs > 0 ? arcs : 1), ctx->stream)) != cudaSuccess)
+    if ((e = dev_malloc((void **)&G->adj, sizeof(int32_t) * (size_t)(arcs > 0 ? arcs : 1), ctx->stream)) != cudaSuccess)
         return bail(cuda_fail(ctx, e, "adjacency allocation"));
+    if (!dev_src && upload_fault()) return bail(fail(ctx, DSG_ERR_CUDA, "offsets copy: injected upload failure"));
     if ((e = cudaMemcpyAsync(G->off, offsets, sizeof(int64_t) * (size_t)(n + 1), kind, ctx->stream)) != cudaSuccess)
         return bail(cuda_fail(ctx, e, "offsets copy"));
+    if (!dev_src && arcs > 0 && upload_fault())
+        return bail(fail(ctx, DSG_ERR_CUDA, "adjacency copy: injected upload failure"));
     if (chunked) {
         if (!ctx->copy) {
             if ((e = cudaStreamCreateWithFlags(&ctx->copy, cudaStreamNonBlocking)) != cudaSuccess)
@@ -702,6 +733,8 @@ int dsg_run(dsg_graph *G, int variant, int32_t T, int64_t eps_num, int64_t eps_d
         }
     }
     const int64_t m = G->g.arcs / 2;
+    b.spin_limit = ctx->dbg_spin_limit;
+    b.debug_stall = ctx->dbg_stall;
     {
         PhaseTimer pt(ctx, DSG_PHASE_OTHER);
         CK(launch_init(G->g, b, init_ptr, 0, s), "init");
@@ -826,7 +859,7 @@ int dsg_coreness(dsg_graph *G, int32_t *core, int64_t *k_max, uint32_t flags)
     int rc = ensure_run_bufs(ctx, G, 1);
     if (rc) return rc;
     int32_t *dst = core;
-    if (!(flags & DSG_DST_DEVICE)) CK(cudaMallocAsync((void **)&dst, 4 * (size_t)n, s), "core buffer");
+    if (!(flags & DSG_DST_DEVICE)) CK(dev_malloc((void **)&dst, 4 * (size_t)n, s), "core buffer");
     int64_t km = 0;
     rc = coreness_run(s, G->g, G->rb.ctl, ctx->sm_count, dst, &km, ctx->err);
     if (rc == DSG_OK && !(flags & DSG_DST_DEVICE)) {
@@ -875,7 +908,7 @@ static int run_pruned(dsg_graph *G, int variant, int32_t T, int64_t eps_num, int
     char *mem = nullptr;
     const size_t need = align256(4 * (size_t)n) + align256(8 * (size_t)n) + align256(4 * (size_t)n) +
                         align256(4 * (size_t)n) + align256(8 * (size_t)n) + align256(4 * (size_t)n);
-    CK(cudaMallocAsync((void **)&mem, need, s), "pruning buffers");
+    CK(dev_malloc((void **)&mem, need, s), "pruning buffers");
     int32_t *core = (int32_t *)mem;
     int64_t *loads_all = (int64_t *)(mem + align256(4 * (size_t)n));
     int32_t *sset = (int32_t *)((char *)loads_all + align256(8 * (size_t)n));
@@ -1114,7 +1147,7 @@ int dsg_apx_coreness(dsg_graph *G, int64_t c_num, int64_t c_den, int32_t *core, 
     if (rc) return rc;
     const bool dst_dev = flags & DSG_DST_DEVICE;
     char *mem = nullptr;
-    CK(cudaMallocAsync((void **)&mem, 3 * align256(4 * (size_t)n), s), "apx coreness buffers");
+    CK(dev_malloc((void **)&mem, 3 * align256(4 * (size_t)n), s), "apx coreness buffers");
     int32_t *deg = (int32_t *)mem;
     int32_t *keep = (int32_t *)(mem + align256(4 * (size_t)n));
     int32_t *dst = dst_dev ? core : (int32_t *)(mem + 2 * align256(4 * (size_t)n));
@@ -1218,14 +1251,15 @@ int dsg_upload_batch(dsg_ctx *ctx, int32_t G, const int64_t *n_per, const int64_
     auto bail = [&](int code) { dsg_free_batch(B); return code; };
     cudaError_t e;
     cudaStream_t st = ctx->stream;
-    if ((e = cudaMallocAsync((void **)&B->vbase, 8 * (size_t)(G + 1), st)) != cudaSuccess ||
-        (e = cudaMallocAsync((void **)&B->off, 8 * (size_t)(N + 1), st)) != cudaSuccess ||
-        (e = cudaMallocAsync((void **)&B->adj, 4 * adjp.size(), st)) != cudaSuccess ||
-        (e = cudaMallocAsync((void **)&B->order, 4 * (size_t)G, st)) != cudaSuccess ||
-        (e = cudaMallocAsync((void **)&B->T, 4 * (size_t)G, st)) != cudaSuccess ||
-        (e = cudaMallocAsync((void **)&B->pq, 16 * (size_t)G, st)) != cudaSuccess ||
-        (e = cudaMallocAsync((void **)&B->graph_ctr, 4, st)) != cudaSuccess)
+    if ((e = dev_malloc((void **)&B->vbase, 8 * (size_t)(G + 1), st)) != cudaSuccess ||
+        (e = dev_malloc((void **)&B->off, 8 * (size_t)(N + 1), st)) != cudaSuccess ||
+        (e = dev_malloc((void **)&B->adj, 4 * adjp.size(), st)) != cudaSuccess ||
+        (e = dev_malloc((void **)&B->order, 4 * (size_t)G, st)) != cudaSuccess ||
+        (e = dev_malloc((void **)&B->T, 4 * (size_t)G, st)) != cudaSuccess ||
+        (e = dev_malloc((void **)&B->pq, 16 * (size_t)G, st)) != cudaSuccess ||
+        (e = dev_malloc((void **)&B->graph_ctr, 4, st)) != cudaSuccess)
         return bail(cuda_fail(ctx, e, "batch allocation"));
+    if (upload_fault()) return bail(fail(ctx, DSG_ERR_CUDA, "batch copy: injected upload failure"));
     cudaMemcpyAsync(B->vbase, vbase.data(), 8 * (size_t)(G + 1), cudaMemcpyHostToDevice, st);
     cudaMemcpyAsync(B->off, off.data(), 8 * (size_t)(N + 1), cudaMemcpyHostToDevice, st);
     cudaMemcpyAsync(B->adj, adjp.data(), 4 * adjp.size(), cudaMemcpyHostToDevice, st);
@@ -1297,7 +1331,7 @@ int dsg_run_batch(dsg_batch *Bt, int variant, const int32_t *T, const int64_t *e
         if (Bt->run_mem) cudaFreeAsync(Bt->run_mem, st);
         Bt->run_mem = nullptr;
         Bt->run_bytes = 0;
-        CK(cudaMallocAsync(&Bt->run_mem, need, st), "batch run buffers");
+        CK(dev_malloc(&Bt->run_mem, need, st), "batch run buffers");
         Bt->run_bytes = need;
     }
     char *p = (char *)Bt->run_mem;

@@ -10,9 +10,6 @@ constexpr unsigned kFull = 0xffffffffu;
 
 __host__ __device__ __forceinline__ int64_t imin64(int64_t a, int64_t b) { return a < b ? a : b; }
 __host__ __device__ __forceinline__ int64_t imax64(int64_t a, int64_t b) { return a > b ? a : b; }
-// bounded waits: polls before a device-side wait gives up (with back-off of
-// up to 256 ns per poll this is on the order of a second)
-constexpr uint32_t kSpinLimit = 1u << 22;
 
 __device__ __forceinline__ unsigned long long ld_acquire(const unsigned long long *p)
 {

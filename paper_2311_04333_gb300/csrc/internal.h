@@ -1,6 +1,7 @@
 // internal.h -- layouts shared by the host orchestration (api.cu) and the
 // kernels of libdsg.  Not part of the C ABI.
 #pragma once
+#include <cstddef>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -78,6 +79,12 @@ struct Control {
     int32_t improved;        // set by the last pass when this iteration beat the best
     int32_t err;             // dsg_status of a device-side failure (0 = none)
     int32_t err_where;
+    // test-only knobs of the bounded waits (dsg_debug_set): polls before a
+    // wait gives up (0: kSpinLimit), and a wait made to run out on purpose
+    // (1: tile 0 of every radix pass never publishes its look-back words;
+    // 2: block 1 never arrives at the first PaRGreedy++ grid barrier)
+    uint32_t spin_limit;
+    int32_t debug_stall;
     // per-iteration plan (written by the plan kernel)
     uint32_t lmin;           // minimum load at the start of the iteration
     uint32_t lrange;         // max - min load at the start of the iteration
@@ -99,6 +106,10 @@ struct Control {
     int64_t cnt_less;        // #{v : L(v) < best_key}
     int64_t set_size;
 };
+
+// err, err_where, spin_limit and debug_stall are reset together (16 bytes)
+// by the runs that do not re-initialise the whole control block
+static_assert(offsetof(Control, debug_stall) == offsetof(Control, err) + 12, "Control layout");
 
 // ---- host launchers (implemented in kernels_*.cu) --------------------------
 struct GraphDev {
@@ -138,7 +149,27 @@ struct RunBufs {
     uint32_t *hot_c;         // [n_hot] counts for the hot tier (zero between scans)
     int64_t nblk64;
     void *scratch;           // >= 8n bytes (output staging)
+    uint32_t spin_limit = 0; // test-only knobs copied into Control at init
+    int32_t debug_stall = 0;
 };
+
+// ---- test-only fault hooks (dsg_debug_set, or DSG_FAULT in the environment)
+// Process-wide countdowns, off (0) unless a test sets them: when the
+// allocation countdown reaches zero, that device (or host context)
+// allocation fails as if memory were exhausted; when the upload countdown
+// reaches zero, that host-to-device copy of an upload call fails.
+cudaError_t dev_malloc(void **p, size_t bytes, cudaStream_t s);
+template <class T>
+inline cudaError_t dev_malloc(T **p, size_t bytes, cudaStream_t s) { return dev_malloc((void **)p, bytes, s); }
+bool host_alloc_fault();
+bool upload_fault();
+void set_alloc_fault(int64_t nth);
+void set_upload_fault(int64_t nth);
+// bounded waits: polls before a device-side wait gives up (with back-off of
+// up to 256 ns per poll this is on the order of a second); a run's Control
+// may carry a smaller limit (ctl->spin_limit, test-only)
+constexpr uint32_t kSpinLimit = 1u << 22;
+__host__ __device__ inline uint32_t spin_limit_of(uint32_t v) { return v ? v : kSpinLimit; }
 
 int edge_scan_sm_count();
 // "Compact" graphs (up to 32,768 vertices and 2^20 arcs): their upload

@@ -177,9 +177,9 @@ cudaError_t build_schedule(GraphDev &g, void *tmp, size_t tmp_bytes, cudaStream_
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
     WorkItem *items = nullptr;
     uint32_t *hm = nullptr;
-    if ((e = cudaMallocAsync((void **)&items, sizeof(WorkItem) * (size_t)imax64(h_tot[1], 1), s)) != cudaSuccess)
+    if ((e = dev_malloc((void **)&items, sizeof(WorkItem) * (size_t)imax64(h_tot[1], 1), s)) != cudaSuccess)
         return e;
-    if ((e = cudaMallocAsync((void **)&hm, sizeof(uint32_t) * 2 * (size_t)imax64(h_tot[0], 1), s)) != cudaSuccess) {
+    if ((e = dev_malloc((void **)&hm, sizeof(uint32_t) * 2 * (size_t)imax64(h_tot[0], 1), s)) != cudaSuccess) {
         cudaFreeAsync(items, s);
         return e;
     }
@@ -507,15 +507,15 @@ cudaError_t build_orientation(GraphDev &g, cudaStream_t s, int full, int32_t *er
     int64_t *tmp = nullptr, *flag = nullptr;
     int32_t *slot_of = nullptr, *slot_of_scratch = nullptr;
     const int64_t ntmp = scan_tmp_count(n + 1);
-    if ((e = cudaMallocAsync((void **)&cnt, 8, s)) != cudaSuccess) return e;
-    if ((e = cudaMallocAsync((void **)&tmp, 8 * (size_t)(ntmp + 2), s)) != cudaSuccess) return e;
-    if ((e = cudaMallocAsync((void **)&flag, 8 * (size_t)(n + 1), s)) != cudaSuccess) return e;
-    if ((e = cudaMallocAsync((void **)&slot_of, 4 * (size_t)n, s)) != cudaSuccess) return e;
-    if ((e = cudaMallocAsync((void **)&slot_of_scratch, 4 * (size_t)n, s)) != cudaSuccess) return e;
+    if ((e = dev_malloc((void **)&cnt, 8, s)) != cudaSuccess) return e;
+    if ((e = dev_malloc((void **)&tmp, 8 * (size_t)(ntmp + 2), s)) != cudaSuccess) return e;
+    if ((e = dev_malloc((void **)&flag, 8 * (size_t)(n + 1), s)) != cudaSuccess) return e;
+    if ((e = dev_malloc((void **)&slot_of, 4 * (size_t)n, s)) != cudaSuccess) return e;
+    if ((e = dev_malloc((void **)&slot_of_scratch, 4 * (size_t)n, s)) != cudaSuccess) return e;
     std::vector<unsigned int> dh(kDegHist, 0);
     {
         unsigned int *hd = nullptr;
-        if ((e = cudaMallocAsync((void **)&hd, 4 * (size_t)kDegHist, s)) != cudaSuccess) return e;
+        if ((e = dev_malloc((void **)&hd, 4 * (size_t)kDegHist, s)) != cudaSuccess) return e;
         cudaMemsetAsync(hd, 0, 4 * (size_t)kDegHist, s);
         k_degree_hist<<<grid, 256, 0, s>>>(g.off, n, hd);
         cudaMemcpyAsync(dh.data(), hd, 4 * (size_t)kDegHist, cudaMemcpyDeviceToHost, s);
@@ -531,7 +531,7 @@ cudaError_t build_orientation(GraphDev &g, cudaStream_t s, int full, int32_t *er
     cudaMemcpyAsync(&n_hub, total, 8, cudaMemcpyDeviceToHost, s);
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
     uint32_t *hub = nullptr;
-    if ((e = cudaMallocAsync((void **)&hub, 4 * (size_t)imax64(n_hub, 1), s)) != cudaSuccess) return e;
+    if ((e = dev_malloc((void **)&hub, 4 * (size_t)imax64(n_hub, 1), s)) != cudaSuccess) return e;
     k_hub_slots<<<grid, 256, 0, s>>>(g.off, n, D, flag, slot_of, hub);
     // hot tier (only when plain ids stay below kHotBit)
     int32_t *hot_of = nullptr;
@@ -540,30 +540,30 @@ cudaError_t build_orientation(GraphDev &g, cudaStream_t s, int full, int32_t *er
     if (n < (int64_t)kHotBit && kHot > 0) {
         int64_t Dh = 0;
         if ((e = degree_threshold(g, kHot, dh, cnt, grid, s, &Dh)) != cudaSuccess) return e;
-        if ((e = cudaMallocAsync((void **)&hot_of, 4 * (size_t)n, s)) != cudaSuccess) return e;
+        if ((e = dev_malloc((void **)&hot_of, 4 * (size_t)n, s)) != cudaSuccess) return e;
         k_hub_flags<<<grid, 256, 0, s>>>(g.off, n, Dh, flag);
         if ((e = scan_exclusive_i64(flag, n, total, tmp, s)) != cudaSuccess) return e;
         cudaMemcpyAsync(&n_hot, total, 8, cudaMemcpyDeviceToHost, s);
         if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
-        if ((e = cudaMallocAsync((void **)&hot, 4 * (size_t)imax64(n_hot, 1), s)) != cudaSuccess) return e;
+        if ((e = dev_malloc((void **)&hot, 4 * (size_t)imax64(n_hot, 1), s)) != cudaSuccess) return e;
         k_hub_slots<<<grid, 256, 0, s>>>(g.off, n, Dh, flag, hot_of, hot);
     }
     // 32-bit degrees and encoded targets; list of vertices of degree > kBigDeg
     uint32_t *deg32 = nullptr, *enc = nullptr, *big = nullptr;
-    if ((e = cudaMallocAsync((void **)&deg32, 4 * (size_t)n, s)) != cudaSuccess) return e;
-    if ((e = cudaMallocAsync((void **)&enc, 4 * (size_t)n, s)) != cudaSuccess) return e;
+    if ((e = dev_malloc((void **)&deg32, 4 * (size_t)n, s)) != cudaSuccess) return e;
+    if ((e = dev_malloc((void **)&enc, 4 * (size_t)n, s)) != cudaSuccess) return e;
     k_deg_enc<<<grid, 256, 0, s>>>(g.off, n, slot_of, hot_of, deg32, enc);
     k_hub_flags<<<grid, 256, 0, s>>>(g.off, n, kBigDeg + 1, flag);
     if ((e = scan_exclusive_i64(flag, n, total, tmp, s)) != cudaSuccess) return e;
     int64_t n_big = 0;
     cudaMemcpyAsync(&n_big, total, 8, cudaMemcpyDeviceToHost, s);
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
-    if ((e = cudaMallocAsync((void **)&big, 4 * (size_t)imax64(n_big, 1), s)) != cudaSuccess) return e;
+    if ((e = dev_malloc((void **)&big, 4 * (size_t)imax64(n_big, 1), s)) != cudaSuccess) return e;
     k_hub_slots<<<grid, 256, 0, s>>>(g.off, n, kBigDeg + 1, flag, slot_of_scratch, big);
     // keep bits of the arcs, set by the count pass and read by the fill pass
     uint32_t *bits = nullptr;
     const size_t nbits_words = (size_t)((g.arcs + 31) / 32) + 1;
-    if ((e = cudaMallocAsync((void **)&bits, 4 * nbits_words, s)) != cudaSuccess) return e;
+    if ((e = dev_malloc((void **)&bits, 4 * nbits_words, s)) != cudaSuccess) return e;
     cudaMemsetAsync(bits, 0, 4 * nbits_words, s);
     // validation fused with the oriented out-degrees
     const int wgrid = (int)imin64((n * 32 + 255) / 256, 152 * 32);
@@ -598,7 +598,7 @@ cudaError_t build_orientation(GraphDev &g, cudaStream_t s, int full, int32_t *er
         if ((e = scan_exclusive_i64(flag, n + 1, total, tmp, s)) != cudaSuccess) return e;
         cudaMemcpyAsync(&oarcs, total, 8, cudaMemcpyDeviceToHost, s);
         if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
-        if ((e = cudaMallocAsync((void **)&oadj, 4 * (size_t)imax64(oarcs, 1), s)) != cudaSuccess) return e;
+        if ((e = dev_malloc((void **)&oadj, 4 * (size_t)imax64(oarcs, 1), s)) != cudaSuccess) return e;
         k_orient_fill<<<wgrid, 256, 0, s>>>(g.off, g.adj, n, flag, bits, enc, oadj);
         if (n_big) k_orient_fill_big<<<bgrid, 1024, 0, s>>>(g.off, g.adj, flag, bits, enc, big, n_big, oadj);
     }

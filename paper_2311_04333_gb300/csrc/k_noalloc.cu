@@ -3,6 +3,8 @@
 // scratch memory in one file-scope static device array, so that the call
 // allocates nothing.  It drives the same radix-pass kernel (with the fused
 // suffix scan) as dsg_run, on scratch carved out of that array.
+#include <atomic>
+#include <mutex>
 #include "common.cuh"
 #include "dsg.h"
 
@@ -26,7 +28,22 @@ constexpr size_t kNaBytes = kOffTrace + al256(3 * sizeof(int64_t));
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNaBytes];
 
 constexpr int kMaxDevices = 64;
-static unsigned char *g_scratch_ptr[kMaxDevices];   // device address per device
+// device address of the array per device, looked up once (under the mutex)
+static std::atomic<unsigned char *> g_scratch_ptr[kMaxDevices];
+static std::mutex g_scratch_mu;
+
+// The look-back status words and value sums of this call's tiles start at
+// zero (flag 0: not published), so a word left behind by an earlier call
+// can never be taken for one of this call's, whatever its epoch.
+__global__ void k_na_clear(unsigned long long *status, unsigned long long *status_sum, int64_t words)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < words;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        status[i] = 0ull;
+        status_sum[2 * i] = 0ull;
+        status_sum[2 * i + 1] = 0ull;
+    }
+}
 
 __global__ void k_na_reset(Control *ctl)
 {
@@ -38,6 +55,8 @@ __global__ void k_na_reset(Control *ctl)
     ctl->improved = 0;
     ctl->err = 0;
     ctl->err_where = 0;
+    ctl->spin_limit = 0;
+    ctl->debug_stall = 0;
     ctl->mm_min[1] = 0xffffffffu;
     ctl->mm_max[1] = 0;
 }
@@ -101,16 +120,28 @@ using namespace dsg;
 extern "C" int dsg_densest_suffix_noalloc(const uint32_t *loads, const uint32_t *A, int64_t n,
                                           int64_t m, int64_t *result, void *cuda_stream)
 {
-    if (n < 1 || n > kNaMaxN || m < 0 || !loads || !A || !result) return DSG_ERR_INVALID;
+    // m < 2^48: the last radix pass carries prefix sums in 48-bit tagged words
+    if (n < 1 || n > kNaMaxN || m < 0 || (m >> 48) || !loads || !A || !result) return DSG_ERR_INVALID;
+    // an error already pending on this thread belongs to someone else: leave
+    // it in place and launch nothing
+    if (cudaPeekAtLastError() != cudaSuccess) return DSG_ERR_CUDA;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return DSG_ERR_CUDA;
-    if (!g_scratch_ptr[dev]) {
+    unsigned char *base = g_scratch_ptr[dev].load(std::memory_order_acquire);
+    if (!base) {
         // once per device, with that device current
-        unsigned char *p = nullptr;
-        if (cudaGetSymbolAddress((void **)&p, g_noalloc_scratch) != cudaSuccess || !p) return DSG_ERR_CUDA;
-        g_scratch_ptr[dev] = p;
+        std::lock_guard<std::mutex> lock(g_scratch_mu);
+        base = g_scratch_ptr[dev].load(std::memory_order_relaxed);
+        if (!base) {
+            unsigned char *p = nullptr;
+            if (cudaGetSymbolAddress((void **)&p, g_noalloc_scratch) != cudaSuccess || !p) {
+                cudaGetLastError();   // this call's own failure
+                return DSG_ERR_CUDA;
+            }
+            g_scratch_ptr[dev].store(p, std::memory_order_release);
+            base = p;
+        }
     }
-    unsigned char *base = g_scratch_ptr[dev];
     cudaStream_t s = (cudaStream_t)cuda_stream;
     RunBufs b{};
     uint32_t *kv = (uint32_t *)(base + kOffKV);
@@ -130,6 +161,8 @@ extern "C" int dsg_densest_suffix_noalloc(const uint32_t *loads, const uint32_t 
     g.n = n;
     g.arcs = 2 * m;
     const int grid = (int)imin64((n + 255) / 256, 1024);
+    const int64_t words = b.ntiles * kBuckets;
+    k_na_clear<<<(int)imin64((words + 255) / 256, 1024), 256, 0, s>>>(b.status, b.status_sum, words);
     k_na_reset<<<1, 1, 0, s>>>(b.ctl);
     k_na_minmax<<<grid, 256, 0, s>>>(loads, n, b.ctl);
     if (launch_plan(g, b, 1, s) != cudaSuccess) return DSG_ERR_CUDA;

@@ -91,10 +91,13 @@ __device__ __forceinline__ bool grid_barrier(PeelCtl *pc, Control *ctl, uint32_t
     if (threadIdx.x == 0) {
         int ok = 1;
         __threadfence();
-        atomicAdd(&pc->bar_count, 1u);
+        // (test-only: debug_stall 2 keeps block 1 from arriving at the first
+        // barrier, so that every block's wait runs out)
+        if (!(ctl->debug_stall == 2 && blockIdx.x == 1 && target == nb)) atomicAdd(&pc->bar_count, 1u);
+        const uint32_t limit = spin_limit_of(ctl->spin_limit);
         uint32_t polls = 0;
         while (ld_acquire_u32(&pc->bar_count) < target) {
-            if (++polls > kSpinLimit || ((polls & 255) == 0 && ld_acquire_u32(&pc->abort))) {
+            if (++polls > limit || ((polls & 255) == 0 && ld_acquire_u32(&pc->abort))) {
                 atomicExch(&pc->abort, 1u);
                 set_error(ctl, DSG_ERR_TIMEOUT, 400);
                 ok = 0;
@@ -413,7 +416,7 @@ int peel_run(cudaStream_t s, const GraphDev &g, RunBufs &b, PeelBufs &pb, bool &
     const size_t sz4 = al(4 * (size_t)n), sz8 = al(8 * (size_t)n), sz_pc = al(sizeof(PeelCtl));
     if (!pb_ready) {
         const size_t total = 4 * sz4 + 2 * sz8 + sz_pc;
-        cudaError_t e = cudaMallocAsync(&pb.mem, total, s);
+        cudaError_t e = dev_malloc(&pb.mem, total, s);
         if (e != cudaSuccess) {
             err = std::string("peel buffers: ") + cudaGetErrorString(e);
             return e == cudaErrorMemoryAllocation ? DSG_ERR_NOMEM : DSG_ERR_CUDA;
@@ -527,7 +530,7 @@ int coreness_run(cudaStream_t s, const GraphDev &g, Control *ctl, int sm_count, 
     const size_t sz4 = al(4 * (size_t)n), sz8 = al(8 * (size_t)n), sz_pc = al(sizeof(PeelCtl));
     const size_t total = 7 * sz4 + 2 * sz8 + sz_pc;
     void *mem = nullptr;
-    cudaError_t e = cudaMallocAsync(&mem, total, s);
+    cudaError_t e = dev_malloc(&mem, total, s);
     if (e != cudaSuccess) {
         err = std::string("coreness buffers: ") + cudaGetErrorString(e);
         return e == cudaErrorMemoryAllocation ? DSG_ERR_NOMEM : DSG_ERR_CUDA;
@@ -552,6 +555,8 @@ int coreness_run(cudaStream_t s, const GraphDev &g, Control *ctl, int sm_count, 
     }
     const int grid = (int)imin64(sm_count, peel_blocks((uint64_t)n, (uint64_t)g.arcs));
     const int igrid = (int)imin64((n + 255) / 256, (int64_t)sm_count * 8);
+    // a failure status or test knob left by an earlier run does not carry over
+    cudaMemsetAsync(&ctl->err, 0, 16, s);
     k_peel_init<<<igrid, 256, 0, s>>>(g.off, zl, n, g.arcs, kv, round, list0, pc);
     const int64_t *off = g.off;
     const int32_t *adj = g.adj;
@@ -618,7 +623,7 @@ int kcore_run(cudaStream_t s, const GraphDev &g, Control *ctl, int sm_count, KCo
         if (kb.mem) cudaFreeAsync(kb.mem, s);
         kb.mem = nullptr;
         kb.bytes = 0;
-        if ((e = cudaMallocAsync(&kb.mem, total, s)) != cudaSuccess) {
+        if ((e = dev_malloc(&kb.mem, total, s)) != cudaSuccess) {
             err = std::string("k-core buffers: ") + cudaGetErrorString(e);
             return e == cudaErrorMemoryAllocation ? DSG_ERR_NOMEM : DSG_ERR_CUDA;
         }
@@ -642,6 +647,8 @@ int kcore_run(cudaStream_t s, const GraphDev &g, Control *ctl, int sm_count, KCo
     }
     const int grid = (int)imin64(sm_count, peel_blocks((uint64_t)n, (uint64_t)g.arcs));
     const int igrid = (int)imin64((n + 255) / 256, (int64_t)sm_count * 8);
+    // a failure status or test knob left by an earlier run does not carry over
+    cudaMemsetAsync(&ctl->err, 0, 16, s);
     k_peel_init<<<igrid, 256, 0, s>>>(g.off, zl, n, g.arcs, kv, round, list0, pc);
     const int64_t *off = g.off;
     const int32_t *adj = g.adj;

@@ -172,7 +172,7 @@ cudaError_t degree_core_bound(cudaStream_t s, const GraphDev &g, int32_t *deg, i
     const int64_t n = g.n;
     cudaError_t e;
     unsigned long long *h = nullptr;
-    if ((e = cudaMallocAsync((void **)&h, 64 * 8, s)) != cudaSuccess) return e;
+    if ((e = dev_malloc((void **)&h, 64 * 8, s)) != cudaSuccess) return e;
     cudaMemsetAsync(h, 0, 64 * 8, s);
     const int grid = (int)imin64((n + 255) / 256, 152 * 16);
     const int wgrid = (int)imin64((n * 32 + 255) / 256, 152 * 32);
@@ -206,8 +206,8 @@ cudaError_t extract_core(cudaStream_t s, int64_t n, const int64_t *off, const in
     cudaError_t e;
     int64_t *pos = nullptr, *tmp = nullptr;
     const int64_t ntmp = scan_tmp_count(n + 1) + 2;
-    if ((e = cudaMallocAsync((void **)&pos, 8 * (size_t)(n + 1), s)) != cudaSuccess) return e;
-    if ((e = cudaMallocAsync((void **)&tmp, 8 * (size_t)ntmp, s)) != cudaSuccess) return e;
+    if ((e = dev_malloc((void **)&pos, 8 * (size_t)(n + 1), s)) != cudaSuccess) return e;
+    if ((e = dev_malloc((void **)&tmp, 8 * (size_t)ntmp, s)) != cudaSuccess) return e;
     int64_t *total = tmp + ntmp - 1;
     const int grid = (int)imin64((n + 256) / 256, 152 * 16);
     const int wgrid = (int)imin64((n * 32 + 255) / 256, 152 * 32);
@@ -218,9 +218,9 @@ cudaError_t extract_core(cudaStream_t s, int64_t n, const int64_t *off, const in
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
     int64_t *noff = nullptr, *nloads = nullptr;
     int32_t *nold = nullptr, *nadj = nullptr;
-    if ((e = cudaMallocAsync((void **)&noff, 8 * (size_t)(nn + 1), s)) != cudaSuccess ||
-        (e = cudaMallocAsync((void **)&nold, 4 * (size_t)imax64(nn, 1), s)) != cudaSuccess ||
-        (e = cudaMallocAsync((void **)&nloads, 8 * (size_t)imax64(nn, 1), s)) != cudaSuccess)
+    if ((e = dev_malloc((void **)&noff, 8 * (size_t)(nn + 1), s)) != cudaSuccess ||
+        (e = dev_malloc((void **)&nold, 4 * (size_t)imax64(nn, 1), s)) != cudaSuccess ||
+        (e = dev_malloc((void **)&nloads, 8 * (size_t)imax64(nn, 1), s)) != cudaSuccess)
         return e;
     cudaMemsetAsync(noff, 0, 8 * (size_t)(nn + 1), s);
     k_ext_deg<<<wgrid, 256, 0, s>>>(off, adj, n, pos, noff);
@@ -228,7 +228,7 @@ cudaError_t extract_core(cudaStream_t s, int64_t n, const int64_t *off, const in
     int64_t arcs = 0;
     cudaMemcpyAsync(&arcs, total, 8, cudaMemcpyDeviceToHost, s);
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
-    if ((e = cudaMallocAsync((void **)&nadj, 4 * (size_t)imax64(arcs, 1), s)) != cudaSuccess) return e;
+    if ((e = dev_malloc((void **)&nadj, 4 * (size_t)imax64(arcs, 1), s)) != cudaSuccess) return e;
     k_ext_fill<<<wgrid, 256, 0, s>>>(off, adj, n, pos, noff, nadj);
     k_ext_map<<<grid, 256, 0, s>>>(n, pos, old_of, loads, nold, nloads, frozen);
     cudaFreeAsync(pos, s);

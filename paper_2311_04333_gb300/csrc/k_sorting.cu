@@ -27,8 +27,10 @@ namespace dsg {
 
 // ============================================================ init / plan
 
-__global__ void k_init_ctl(Control *ctl, int64_t m, int64_t n)
+__global__ void k_init_ctl(Control *ctl, int64_t m, int64_t n, uint32_t spin_limit, int32_t debug_stall)
 {
+    ctl->spin_limit = spin_limit;
+    ctl->debug_stall = debug_stall;
     ctl->best_e = m;
     ctl->best_v = n;
     ctl->best_pos = 0;
@@ -91,7 +93,7 @@ __global__ void k_plan(Control *ctl, int t)
 cudaError_t launch_init(const GraphDev &g, RunBufs &b, const int64_t *init_dev, int,
                         cudaStream_t s)
 {
-    k_init_ctl<<<1, 1, 0, s>>>(b.ctl, g.arcs / 2, g.n);
+    k_init_ctl<<<1, 1, 0, s>>>(b.ctl, g.arcs / 2, g.n, b.spin_limit, b.debug_stall);
     int grid = (int)imin64((g.n + 255) / 256, 4096);
     k_init_loads<<<grid, 256, 0, s>>>(b.loads, init_dev, g.n, b.ctl);
     return cudaGetLastError();
@@ -707,8 +709,12 @@ k_radix_pass(const uint32_t *kin, const uint32_t *vin,
     unsigned long long *st = status + (int64_t)tile * kBuckets + d;
     unsigned long long *ss = status_sum + 2 * ((int64_t)tile * kBuckets + d);
     if (tile == 0) {
-        if (last) st_relaxed(ss + 1, sum_word(epoch, tsum));
-        st_relaxed(st, status_word(epoch, kFlagIncl, tcount));
+        // (test-only: debug_stall 1 withholds tile 0's words, so that the
+        // look-back of tile 1 waits on words nothing sets and gives up)
+        if (ctl->debug_stall != 1) {
+            if (last) st_relaxed(ss + 1, sum_word(epoch, tsum));
+            st_relaxed(st, status_word(epoch, kFlagIncl, tcount));
+        }
     } else {
         if (last) st_relaxed(ss, sum_word(epoch, tsum));
         st_relaxed(st, status_word(epoch, kFlagAgg, tcount));
@@ -784,6 +790,7 @@ k_radix_pass(const uint32_t *kin, const uint32_t *vin,
         bool abort = false;
         if (tile > 0) {
             int64_t j = (int64_t)tile - 1;
+            const uint32_t limit = spin_limit_of(ctl->spin_limit);
             uint32_t polls = 0, ns = 8;
             bool done = false;
             while (!done) {
@@ -827,7 +834,7 @@ k_radix_pass(const uint32_t *kin, const uint32_t *vin,
                     break;
                 }
                 if (used == 0) {
-                    if (++polls > kSpinLimit) { abort = true; set_error(ctl, 5, 100 + k); break; }
+                    if (++polls > limit) { abort = true; set_error(ctl, 5, 100 + k); break; }
                     __nanosleep(ns);
                     if (ns < 256) ns <<= 1;
                 }
