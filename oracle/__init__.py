@@ -64,6 +64,7 @@ def _lib():
         lib.oracle_coreness_by_deletion.argtypes = [i64, p, p, p]
         lib.oracle_run_pruned.argtypes = [i64, p, p, ctypes.c_int, i64, i64, i64, p, p, p, p, p]
         lib.oracle_run_pruned_c.argtypes = [i64, p, p, ctypes.c_int, i64, i64, i64, i64, i64, p, p, p, p, p]
+        lib.oracle_run_pruned_ax.argtypes = [i64, p, p, ctypes.c_int, i64, i64, i64, i64, i64, p, p, p, p, p]
         lib.oracle_apx_coreness.argtypes = [i64, p, p, i64, i64, p]
         lib.oracle_core_subgraph.argtypes = [i64, p, p, p, i64, p, p]
         _lib_handle = lib
@@ -232,6 +233,27 @@ def run_pruned(g, variant: int = SORTING, T: int = 1, p: int = 0, q: int = 1, c:
         raise ValueError(f"oracle_run_pruned_c failed with status {rc}")
     return PrunedResult(loads, int(best[0]), int(best[1]), int(best[2]), bset[: best[3]].copy(), trace[:T].copy(),
                         int(info[0]), int(info[1]), int(info[2]), int(info[3]), (int(info[4]), int(info[5])))
+
+
+def run_pruned_apx_exact(g, variant: int = PEELING, T: int = 1, p: int = 0, q: int = 1,
+                         c: tuple = (3, 2)) -> tuple:
+    """PaRApxGreedy++'s pruning (Sec. 4): approximate pruning by the
+    c-approximate decomposition to G1 = {k-hat >= ceil(k-hat_max / (2c))},
+    then Alg. 1 with exact pruning on G1.  Returns (PrunedResult, k-hat_max,
+    |V(G1)|, |E(G1)|); k_max and the core sizes in the result are G1's."""
+    n, off, adj = _csr(g)
+    loads = np.zeros(n, dtype=np.int64)
+    best = np.zeros(5, dtype=np.int64)
+    bset = np.zeros(n, dtype=np.int64)
+    trace = np.zeros((max(T, 1), 3), dtype=np.int64)
+    info = np.zeros(9, dtype=np.int64)
+    rc = _lib().oracle_run_pruned_ax(n, _p(off), _p(adj), variant, T, p, q, c[0], c[1], _p(loads), _p(best),
+                                     _p(bset), _p(trace), _p(info))
+    if rc != 0:
+        raise ValueError(f"oracle_run_pruned_ax failed with status {rc}")
+    r = PrunedResult(loads, int(best[0]), int(best[1]), int(best[2]), bset[: best[3]].copy(), trace[:T].copy(),
+                     int(info[0]), int(info[1]), int(info[2]), int(info[3]), (int(info[4]), int(info[5])))
+    return r, int(info[6]), int(info[7]), int(info[8])
 
 
 def core_subgraph_size(g, core, k: int) -> tuple:

@@ -697,3 +697,46 @@ int oracle_run_pruned(int64_t n, const int64_t *off, const int32_t *adj, int var
 {
     return oracle_run_pruned_c(n, off, adj, variant, T, p, q, 0, 1, loads, best, set, trace, info);
 }
+
+/* PaRApxGreedy++'s pruning (Sec. 4, the approximate variants: approximate
+ * k-core pruning followed by exact k-core pruning), read as: the
+ * c-approximate decomposition first prunes G to
+ * G1 = {v : k-hat(v) >= ceil(k-hat_max / (2c))} (the corollary on the
+ * approximate k_max: this bound is at most rho*, so G1 holds S*); then Alg. 1
+ * runs with exact pruning on G1 -- the exact core numbers of G1, its k_max,
+ * L = ceil(k_max / 2), the L-core of G1 and the refine loop with re-pruning
+ * by those core numbers.  Outputs as oracle_run_pruned_c, in the ids of G
+ * (vertices outside G1 keep load 0); info[6..8] = (k-hat_max, |V(G1)|,
+ * |E(G1)|).                                                                 */
+int oracle_run_pruned_ax(int64_t n, const int64_t *off, const int32_t *adj, int variant, int64_t T,
+                         int64_t p, int64_t q, int64_t c_num, int64_t c_den, int64_t *loads, int64_t *best,
+                         int64_t *set, int64_t *trace, int64_t *info)
+{
+    if (n < 1 || c_den < 1 || c_num <= c_den) return OR_ERR_INVALID;
+    int64_t *khat = malloc(sizeof(int64_t) * (size_t)n);
+    unsigned char *in = malloc((size_t)n);
+    if (!khat || !in) { free(khat); free(in); return OR_ERR_NOMEM; }
+    int rc = oracle_apx_coreness(n, off, adj, c_num, c_den, khat);
+    if (rc != OR_OK) { free(khat); free(in); return rc; }
+    int64_t khat_max = 0;
+    for (int64_t v = 0; v < n; ++v) if (khat[v] > khat_max) khat_max = khat[v];
+    const int64_t La = ceil_div(khat_max * c_den, 2 * c_num);      /* approximate stage */
+    for (int64_t v = 0; v < n; ++v) in[v] = khat[v] >= La;
+    int64_t n1 = 0, *off1 = NULL, *old_of = NULL;
+    int32_t *adj1 = NULL;
+    rc = induced_subgraph(n, off, adj, in, &n1, &off1, &adj1, &old_of);
+    free(khat); free(in);
+    if (rc != OR_OK) return rc;
+    int64_t *l1 = malloc(sizeof(int64_t) * (size_t)n1);
+    int64_t *s1 = malloc(sizeof(int64_t) * (size_t)n1);
+    if (!l1 || !s1) { rc = OR_ERR_NOMEM; goto out; }
+    rc = oracle_run_pruned_c(n1, off1, adj1, variant, T, p, q, 0, 1, l1, best, s1, trace, info);  /* exact stage */
+    if (rc != OR_OK) goto out;
+    for (int64_t v = 0; v < n; ++v) loads[v] = 0;
+    for (int64_t i = 0; i < n1; ++i) loads[old_of[i]] = l1[i];
+    for (int64_t i = 0; i < best[3]; ++i) set[i] = old_of[s1[i]];   /* ascending: old_of is increasing */
+    if (info) { info[6] = khat_max; info[7] = n1; info[8] = off1[n1] / 2; }
+out:
+    free(off1); free(adj1); free(old_of); free(l1); free(s1);
+    return rc;
+}
