@@ -258,6 +258,19 @@ int dsg_apx_coreness(dsg_graph *g, int64_t c_num, int64_t c_den, int32_t *core, 
 int dsg_run_pruned_apx(dsg_graph *g, int variant, int32_t T, int64_t eps_num, int64_t eps_den, int64_t c_num,
                        int64_t c_den, dsg_result *out, dsg_prune_info *info);
 
+/* Alg. 1 with approximate pruning followed by exact pruning (Sec. 4, the
+ * approximate variants: PaRApxGreedy++ with DSG_PEELING).  The c-approximate
+ * levels first bracket k_max in (tau_{i-1}, tau_i] with about log_c core tests
+ * on shrinking cores, which prunes G to its (tau_{i-1} + 1)-core; k_max is
+ * then found exactly inside that bracket by bisection over k-cores of that
+ * core, and the run continues as dsg_run_pruned: L = ceil(k_max / 2), exact
+ * cores for every getCore.  The outputs equal dsg_run_pruned's (every core
+ * the loop takes has order >= ceil(k_max / 2), inside the approximate core);
+ * only the work of the set-up differs.  info->k_max receives the exact
+ * k_max.  Errors as dsg_run_pruned_apx. */
+int dsg_run_pruned_apx_exact(dsg_graph *g, int variant, int32_t T, int64_t eps_num, int64_t eps_den,
+                             int64_t c_num, int64_t c_den, dsg_result *out, dsg_prune_info *info);
+
 /* Free an uploaded graph (stream-ordered release of its device memory). */
 void dsg_free_graph(dsg_graph *g);
 

@@ -84,6 +84,8 @@ def _load():
     lib.dsg_run_pruned.argtypes = [P, I, I32, I64, I64, ctypes.POINTER(dsg_result), ctypes.POINTER(dsg_prune_info)]
     lib.dsg_run_pruned_apx.argtypes = [P, I, I32, I64, I64, I64, I64, ctypes.POINTER(dsg_result),
                                        ctypes.POINTER(dsg_prune_info)]
+    lib.dsg_run_pruned_apx_exact.argtypes = [P, I, I32, I64, I64, I64, I64, ctypes.POINTER(dsg_result),
+                                             ctypes.POINTER(dsg_prune_info)]
     lib.dsg_apx_coreness.argtypes = [P, I64, I64, P, ctypes.POINTER(I64), ctypes.c_uint32]
     lib.dsg_server_create.argtypes = [I, I32, I64, ctypes.POINTER(P)]
     lib.dsg_server_submit.argtypes = [P, I64, P, P, I, I32, I64, I64, ctypes.POINTER(ctypes.c_uint64)]
@@ -218,10 +220,12 @@ def dsg_apx_coreness(ctx, graph, c=(3, 2), core=None) -> tuple:
 
 
 def dsg_run_pruned(ctx, graph, variant: int, T: int, eps_num: int = 0, eps_den: int = 1, loads=None,
-                   best_set=None, trace=None, c=None) -> dict:
+                   best_set=None, trace=None, c=None, exact_after: bool = False) -> dict:
     """Alg. 1 with `variant` as the refine step; outputs as dsg_run plus the
     pruning info.  c = (c_num, c_den) prunes by the c-approximate core
-    numbers (dsg_run_pruned_apx) instead of the exact ones."""
+    numbers (dsg_run_pruned_apx) instead of the exact ones; with exact_after
+    the approximate pruning is followed by exact pruning
+    (dsg_run_pruned_apx_exact)."""
     res = dsg_result()
     pl, dl = _ptr(loads, np.int64)
     ps, ds = _ptr(best_set, np.int32)
@@ -234,6 +238,9 @@ def dsg_run_pruned(ctx, graph, variant: int, T: int, eps_num: int = 0, eps_den: 
     info = dsg_prune_info()
     if c is None:
         _check(ctx, LIB.dsg_run_pruned(graph, variant, T, eps_num, eps_den, ctypes.byref(res), ctypes.byref(info)))
+    elif exact_after:
+        _check(ctx, LIB.dsg_run_pruned_apx_exact(graph, variant, T, eps_num, eps_den, c[0], c[1], ctypes.byref(res),
+                                                 ctypes.byref(info)))
     else:
         _check(ctx, LIB.dsg_run_pruned_apx(graph, variant, T, eps_num, eps_den, c[0], c[1], ctypes.byref(res),
                                            ctypes.byref(info)))
@@ -247,6 +254,14 @@ def dsg_run_pruned_apx(ctx, graph, variant: int, T: int, eps_num: int = 0, eps_d
                        c_den: int = 2, loads=None, best_set=None, trace=None) -> dict:
     """Alg. 1 with pruning by the c-approximate core numbers, c = c_num / c_den."""
     return dsg_run_pruned(ctx, graph, variant, T, eps_num, eps_den, loads, best_set, trace, c=(c_num, c_den))
+
+
+def dsg_run_pruned_apx_exact(ctx, graph, variant: int, T: int, eps_num: int = 0, eps_den: int = 1, c_num: int = 3,
+                             c_den: int = 2, loads=None, best_set=None, trace=None) -> dict:
+    """Alg. 1 with approximate pruning followed by exact pruning
+    (PaRApxGreedy++ with DSG_PEELING), c = c_num / c_den."""
+    return dsg_run_pruned(ctx, graph, variant, T, eps_num, eps_den, loads, best_set, trace, c=(c_num, c_den),
+                          exact_after=True)
 
 
 def dsg_free_graph(graph) -> None:
@@ -379,5 +394,5 @@ DSG_NOALLOC_MAX_VERTICES = 262144
 EXPORTED = ["dsg_create", "dsg_destroy", "dsg_last_error", "dsg_debug_set", "dsg_upload_csr", "dsg_graph_info",
             "dsg_run", "dsg_free_graph", "dsg_set_profiling", "dsg_get_stats",
             "dsg_densest_suffix_noalloc", "dsg_upload_batch", "dsg_batch_info", "dsg_run_batch",
-            "dsg_free_batch", "dsg_coreness", "dsg_apx_coreness", "dsg_run_pruned", "dsg_run_pruned_apx", "dsg_server_create", "dsg_server_submit", "dsg_server_wait",
+            "dsg_free_batch", "dsg_coreness", "dsg_apx_coreness", "dsg_run_pruned", "dsg_run_pruned_apx", "dsg_run_pruned_apx_exact", "dsg_server_create", "dsg_server_submit", "dsg_server_wait",
             "dsg_server_stats", "dsg_server_destroy"]

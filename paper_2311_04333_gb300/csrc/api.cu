@@ -878,12 +878,16 @@ int dsg_coreness(dsg_graph *G, int32_t *core, int64_t *k_max, uint32_t flags)
 // c-approximate decomposition (c = c_num / c_den): k-hat(v) is the smallest
 // level tau_i >= core(v), so {v : k-hat(v) >= x} is the exact core of order
 // apx_order(x) and every core this run takes is still a k-core by deletion.
+// With exact_after (PaRApxGreedy++, Sec. 4: approximate pruning followed by
+// exact pruning), the approximate levels only bracket k_max in
+// (tau_{i-1}, tau_i]; k_max itself is then found exactly inside that bracket
+// on the approximate core, and the run continues as with exact pruning.
 static int run_pruned(dsg_graph *G, int variant, int32_t T, int64_t eps_num, int64_t eps_den, int64_t c_num,
-                      int64_t c_den, dsg_result *out, dsg_prune_info *info)
+                      int64_t c_den, dsg_result *out, dsg_prune_info *info, bool exact_after = false)
 {
     if (!G || !out) return DSG_ERR_INVALID;
     dsg_ctx *ctx = G->ctx;
-    const bool apx = c_num != 0;
+    bool apx = c_num != 0;
     if (apx && (c_den < 1 || c_num <= c_den || c_num >= ((int64_t)1 << 31)))
         return fail(ctx, DSG_ERR_INVALID, "c = %lld/%lld: need 1 <= c_den < c_num < 2^31", (long long)c_num,
                     (long long)c_den);
@@ -1010,6 +1014,29 @@ static int run_pruned(dsg_graph *G, int variant, int32_t T, int64_t eps_num, int
                 tau = apx_next_level(tau, c_num, c_den);
             }
             kmax = tau;
+            if (exact_after) {
+                // the exact stage: k_max in (level of the last core of the
+                // chain, tau] by bisection over k-cores of that core
+                int64_t lo2 = chain.back().first, hi2 = tau + 1;
+                while (hi2 - lo2 > 1) {
+                    const int64_t mid = lo2 + (hi2 - lo2) / 2;
+                    int64_t alive = 0;
+                    const CoreGraph &C = chain.back().second;
+                    if ((rc = kcore(C, mid, &alive)) != DSG_OK) return done_k(rc);
+                    if (alive == 0) {
+                        hi2 = mid;
+                        continue;
+                    }
+                    lo2 = mid;
+                    CoreGraph nx;
+                    if ((e = extract_core(s, C.n, C.off, C.adj, keep, C.old_of, lo2, nullptr, nullptr, &nx, true)) !=
+                        cudaSuccess)
+                        return done_k(cuda_fail(ctx, e, "core extraction"));
+                    chain.push_back({lo2, nx});
+                }
+                kmax = lo2;
+                apx = false;      // from here on: exact levels
+            }
         }
     }
     // L = ceil(k_max / 2), or ceil(k-hat_max / (2c)) (the corollary on the
@@ -1131,6 +1158,13 @@ int dsg_run_pruned_apx(dsg_graph *G, int variant, int32_t T, int64_t eps_num, in
 {
     if (G && c_num == 0) return fail(G->ctx, DSG_ERR_INVALID, "c_num = 0: use dsg_run_pruned");
     return run_pruned(G, variant, T, eps_num, eps_den, c_num, c_den, out, info);
+}
+
+int dsg_run_pruned_apx_exact(dsg_graph *G, int variant, int32_t T, int64_t eps_num, int64_t eps_den, int64_t c_num,
+                             int64_t c_den, dsg_result *out, dsg_prune_info *info)
+{
+    if (G && c_num == 0) return fail(G->ctx, DSG_ERR_INVALID, "c_num = 0: use dsg_run_pruned");
+    return run_pruned(G, variant, T, eps_num, eps_den, c_num, c_den, out, info, true);
 }
 
 int dsg_apx_coreness(dsg_graph *G, int64_t c_num, int64_t c_den, int32_t *core, int64_t *k_max, uint32_t flags)

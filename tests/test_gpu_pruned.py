@@ -176,3 +176,47 @@ def test_apx_invalid(dsg, ctx):
             dsg.dsg_run_pruned(ctx, h, 0, 2, c=(0, 1))
     finally:
         dsg.dsg_free_graph(h)
+
+
+@pytest.mark.parametrize("name", list(_graphs()))
+@pytest.mark.parametrize("variant,p,q,T,c", [(1, 1, 10, 6, (3, 2)), (1, 1, 100, 4, (2, 1)), (0, 0, 1, 6, (3, 2)),
+                                             (1, 0, 1, 4, (5, 4))])
+def test_apx_exact_pruned_run(dsg, ctx, name, variant, p, q, T, c):
+    """PaRApxGreedy++'s pruning (approximate, then exact): every output equals
+    the oracle's run of that reading (which equals exact pruning)."""
+    g = _graphs()[name]
+    h = dsg.dsg_upload_csr(ctx, g.n, g.off, g.adj, 0)
+    loads = np.zeros(g.n, np.int64)
+    bset = np.zeros(g.n, np.int32)
+    trace = np.zeros(3 * T, np.int64)
+    try:
+        r = dsg.dsg_run_pruned_apx_exact(ctx, h, variant, T, p, q, c[0], c[1], loads, bset, trace)
+    finally:
+        dsg.dsg_free_graph(h)
+    o, _, _, _ = orc.run_pruned_apx_exact(g, variant, T, p, q, c)
+    assert (r["best_edges"], r["best_vertices"], r["best_iter"]) == (o.best_edges, o.best_vertices, o.best_iter)
+    assert np.array_equal(bset[:r["best_set_size"]].astype(np.int64), o.best_set)
+    assert np.array_equal(loads, o.loads)
+    assert np.array_equal(trace.reshape(T, 3), o.trace)
+    assert (r["k_max"], r["core_vertices"], r["core_edges"], r["final_vertices"]) == \
+        (o.k_max, o.core_vertices, o.core_edges, o.final_vertices)
+    assert (r["L_num"], r["L_den"]) == o.L
+
+
+def test_apx_exact_large(dsg, ctx):
+    """R-MAT 18, PaRApxGreedy++ (eps = 1/10): the exact stage inside the
+    approximate bracket on the whole-GPU k-core peels."""
+    g = gg.rmat(18, 16, 5)
+    T = 3
+    h = dsg.dsg_upload_csr(ctx, g.n, g.off, g.adj, 0)
+    loads = np.zeros(g.n, np.int64)
+    bset = np.zeros(g.n, np.int32)
+    try:
+        r = dsg.dsg_run_pruned_apx_exact(ctx, h, 1, T, 1, 10, 3, 2, loads, bset, None)
+    finally:
+        dsg.dsg_free_graph(h)
+    o, _, _, _ = orc.run_pruned_apx_exact(g, 1, T, 1, 10, (3, 2))
+    assert (r["best_edges"], r["best_vertices"], r["best_iter"]) == (o.best_edges, o.best_vertices, o.best_iter)
+    assert np.array_equal(bset[:r["best_set_size"]].astype(np.int64), o.best_set)
+    assert np.array_equal(loads, o.loads)
+    assert (r["k_max"], r["core_vertices"], r["final_vertices"]) == (o.k_max, o.core_vertices, o.final_vertices)
