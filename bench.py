@@ -48,6 +48,7 @@ BATCH_T_PEEL = 16
 SERVE_POOL = 48        # request graphs of the serving workload
 SERVE_SEED = 5
 SERVE_SLOTS = 4
+SERVE_RATE = 200.0     # Poisson arrival rate of the serving workload, req/s
 UNIT = "GTEPS"
 
 
@@ -392,8 +393,11 @@ def bench_rmat20(dsg, ctx, gg, stream, args) -> dict:
 def bench_serving(dsg, pool, device, args) -> dict:
     """The native request loop under Poisson arrivals: capacity from a
     closed burst of four rounds of the request pool, then an open-loop run at
-    70% of that capacity; latency percentiles are per request, submit to
-    results on the host."""
+    the configured rate (SERVE_RATE req/s) for args.serve_seconds after a
+    warm-up; latency percentiles are per request, submit to results on the
+    host.  When the offered rate is above capacity the queue grows during the
+    run and the line reports that queueing (mean / p99 queue delay, the drain
+    time after the last arrival) and each worker's occupancy."""
     import numpy as np
     from paper_2311_04333_gb300 import serve
     srv = dsg.dsg_server_create(device, args.serve_slots, 0)
@@ -409,8 +413,8 @@ def bench_serving(dsg, pool, device, args) -> dict:
                                                    int(rng.choice([8, 16, 32])), 1, int(rng.choice([10, 100]))))
         ok = all(dsg.dsg_server_wait(srv, tk)["status"] == 0 for tk in burst)
         cap = len(burst) / (time.perf_counter() - t0)
-        rate = 0.7 * cap
-        res = serve.poisson_run(srv, pool, rate, args.serve_seconds, warmup=1.0, seed=SERVE_SEED)
+        rate = args.serve_rate
+        res = serve.poisson_run(srv, pool, rate, args.serve_seconds, warmup=args.serve_warmup, seed=SERVE_SEED)
     finally:
         dsg.dsg_server_destroy(srv)
     ms = [g.m for g in pool]
@@ -418,7 +422,9 @@ def bench_serving(dsg, pool, device, args) -> dict:
                             f"(R-MAT ef 8 / Chung-Lu gamma 2.1 avg degree 16, m {min(ms)}..{max(ms)}), "
                             "T in {8,16,32}, eps in {1/10,1/100}, PaRSorting++ / PaRGreedy++ 50/50, "
                             "host CSR in, loads and best set out",
-                "slots": args.serve_slots, "burst_capacity_req_s": cap, "burst_ok": ok})
+                "slots": args.serve_slots, "burst_capacity_req_s": cap, "burst_ok": ok,
+                "offered_vs_capacity": rate / cap if cap else None,
+                "workers": f"occupancy keys 0..{args.serve_slots - 1} are slots, {args.serve_slots} the batch worker"})
     return res
 
 
@@ -498,7 +504,9 @@ def main():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--batch-steps", type=int, default=3)
     ap.add_argument("--no-serve", action="store_true")
-    ap.add_argument("--serve-seconds", type=float, default=8.0)
+    ap.add_argument("--serve-seconds", type=float, default=10.0)
+    ap.add_argument("--serve-warmup", type=float, default=2.0)
+    ap.add_argument("--serve-rate", type=float, default=SERVE_RATE)
     ap.add_argument("--serve-slots", type=int, default=SERVE_SLOTS)
     ap.add_argument("--profile-case", choices=["edge_scan_rmat25", "peel_rmat20", "batch_1024"],
                     help="run one small case for a profiler instead of the benchmark")

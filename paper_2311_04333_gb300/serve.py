@@ -83,22 +83,48 @@ def poisson_run(server, pool, rate: float, seconds: float, warmup: float = 0.0, 
         variant = int(rng.choice(variants))
         tk = _dsg.dsg_server_submit(server, g.n, g.off, g.adj, variant, T, 1, q)
         with lock:
-            tickets.append((tk, now - t0 >= warmup, g.m, T))
+            tickets.append((tk, now - t0 >= warmup, g.m, T, now - t0))
         t_next += rng.exponential(1.0 / rate)
     t_submit_end = time.perf_counter()
     submitting_done[0] = True
     th.join()
     t_end = time.perf_counter()
-    meas = [(tk, m, T) for tk, w, m, T in tickets if w]
+    meas = [(tk, m, T) for tk, w, m, T, _ in tickets if w]
     lat = np.array([results[tk]["latency_ms"] for tk, _, _ in meas])
     q_ms = np.array([results[tk]["queue_ms"] for tk, _, _ in meas])
     ok = all(results[tk]["status"] == 0 for tk, _, _ in meas)
     edges_iter = sum(m * T for _, m, T in meas)
     span = t_end - (t0 + warmup)
-    return {"requests": len(meas), "rate_req_s": rate, "seconds": seconds, "all_ok": ok,
+    # busy time of each worker (slots 0..K-1, then the batch worker) over the
+    # measured span: the union of its requests' [start, end) intervals
+    # (requests of one batch share theirs)
+    busy = {}
+    for tk, w, _, _, t_sub in tickets:
+        r = results[tk]
+        a = t_sub + r["queue_ms"] / 1e3
+        busy.setdefault(int(r["slot"]), []).append((a, a + r["run_ms"] / 1e3))
+    occ = {}
+    for slot, iv in sorted(busy.items()):
+        iv.sort()
+        tot, cur_a, cur_b = 0.0, None, None
+        for a, b in iv:
+            a, b = max(a, warmup), max(b, warmup)
+            if cur_b is None or a > cur_b:
+                if cur_b is not None:
+                    tot += cur_b - cur_a
+                cur_a, cur_b = a, b
+            else:
+                cur_b = max(cur_b, b)
+        if cur_b is not None:
+            tot += cur_b - cur_a
+        occ[slot] = round(tot / span, 3) if span > 0 else None
+    return {"requests": len(meas), "rate_req_s": rate, "seconds": seconds, "warmup_s": warmup,
+            "all_ok": ok,
             "p50_ms": float(np.percentile(lat, 50)) if len(lat) else None,
             "p99_ms": float(np.percentile(lat, 99)) if len(lat) else None,
             "mean_queue_ms": float(q_ms.mean()) if len(q_ms) else None,
+            "p99_queue_ms": float(np.percentile(q_ms, 99)) if len(q_ms) else None,
             "throughput_req_s": len(meas) / span if span > 0 else None,
             "gteps": edges_iter / span / 1e9 if span > 0 else None,
-            "submit_span_s": t_submit_end - t0}
+            "submit_span_s": t_submit_end - t0, "drain_s": t_end - t_submit_end,
+            "worker_occupancy": occ}
