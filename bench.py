@@ -258,7 +258,8 @@ def bench_batch(dsg, ctx, graphs, args, ws: int = 1, rank: int = 0) -> dict:
     out = {"workload": f"{G} graphs, n log-uniform in [50, 50000] (ER / R-MAT / planted clique), "
                        f"N={Ntot}, M={Mtot}, PaRSorting++ T={BATCH_T} each",
            "graphs_per_s": G / tb, "ms_per_batch": tb * 1e3, "threads_per_graph": th,
-           "autotune_ms": rec["ms"], "one_per_launch_graphs_per_s": G / t1,
+           "autotune": {"threads": th, "thread_degree": rec.get("thread_degree"), "ms": rec["ms"]},
+           "one_per_launch_graphs_per_s": G / t1,
            "one_per_launch_ms": t1 * 1e3, "speedup": t1 / tb, "identical_results": same,
            "gteps_batched": Mtot * BATCH_T / tb / 1e9,
            "sharding": {"ranks": ws, "split": "contiguous graph ranges balanced by 2m + n",
@@ -316,7 +317,8 @@ def bench_batch_peeling(dsg, ctx, graphs, args, ws: int = 1, rank: int = 0) -> d
     Mtot = int(_sum_over_ranks(float(M), ws))
     return {"workload": f"same {G} graphs, PaRGreedy++ eps=1/10, T={BATCH_T_PEEL} each",
             "graphs_per_s": G / tb, "ms_per_batch": tb * 1e3, "threads_per_graph": th,
-            "autotune_ms": rec["ms"], "gteps_batched": Mtot * BATCH_T_PEEL / tb / 1e9,
+            "autotune": {"threads": th, "block_degree": rec.get("block_degree"), "ms": rec["ms"]},
+            "gteps_batched": Mtot * BATCH_T_PEEL / tb / 1e9,
             "one_per_launch_sample": len(sample),
             "one_per_launch_graphs_per_s": len(sample) / t1,
             "one_per_launch_gteps": m_sample * BATCH_T_PEEL / t1 / 1e9,

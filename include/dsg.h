@@ -319,6 +319,17 @@ int dsg_batch_info(const dsg_batch *b, int32_t *G, int64_t *total_n, int64_t *to
 int dsg_run_batch(dsg_batch *b, int variant, const int32_t *T, const int64_t *eps_num,
                   const int64_t *eps_den, int32_t threads_per_graph, dsg_batch_result *out);
 
+/* Tuning of later dsg_run_batch calls on b (the knobs an autotuner sets;
+ * results do not depend on them):
+ *   thread_degree: PaRSorting++ scans lists shorter than this many arcs with
+ *     one thread each and longer ones with a warp (0 = default 32, at most
+ *     2^20);
+ *   block_degree: PaRGreedy++ counts the arcs of a round's peeled vertices
+ *     above this degree with the whole block, the others with a warp each
+ *     (0 = default 1024, at most 2^30).
+ * DSG_ERR_INVALID when a value is out of range. */
+int dsg_set_batch_tuning(dsg_batch *b, int32_t thread_degree, int32_t block_degree);
+
 /* Free a batch. */
 void dsg_free_batch(dsg_batch *b);
 

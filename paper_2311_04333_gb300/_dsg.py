@@ -78,6 +78,7 @@ def _load():
     lib.dsg_upload_batch.argtypes = [P, I32, P, P, P, U32, ctypes.POINTER(P)]
     lib.dsg_batch_info.argtypes = [P, P, P, P]
     lib.dsg_run_batch.argtypes = [P, I, P, P, P, I32, ctypes.POINTER(dsg_batch_result)]
+    lib.dsg_set_batch_tuning.argtypes = [P, I32, I32]
     lib.dsg_free_batch.argtypes = [P]
     lib.dsg_free_batch.restype = None
     lib.dsg_coreness.argtypes = [P, P, ctypes.POINTER(I64), ctypes.c_uint32]
@@ -340,6 +341,12 @@ def dsg_run_batch(ctx, batch, variant: int, T, threads_per_graph: int = 0, best=
                                   threads_per_graph, ctypes.byref(res)))
 
 
+def dsg_set_batch_tuning(ctx, batch, thread_degree: int = 0, block_degree: int = 0) -> None:
+    """Tuning of later dsg_run_batch calls (0 = default): thread-vs-warp list
+    length of the PaRSorting++ scan, whole-block degree of the PaRGreedy++ rounds."""
+    _check(ctx, LIB.dsg_set_batch_tuning(batch, thread_degree, block_degree))
+
+
 def dsg_free_batch(batch) -> None:
     LIB.dsg_free_batch(batch)
 
@@ -394,5 +401,5 @@ DSG_NOALLOC_MAX_VERTICES = 262144
 EXPORTED = ["dsg_create", "dsg_destroy", "dsg_last_error", "dsg_debug_set", "dsg_upload_csr", "dsg_graph_info",
             "dsg_run", "dsg_free_graph", "dsg_set_profiling", "dsg_get_stats",
             "dsg_densest_suffix_noalloc", "dsg_upload_batch", "dsg_batch_info", "dsg_run_batch",
-            "dsg_free_batch", "dsg_coreness", "dsg_apx_coreness", "dsg_run_pruned", "dsg_run_pruned_apx", "dsg_run_pruned_apx_exact", "dsg_server_create", "dsg_server_submit", "dsg_server_wait",
+            "dsg_set_batch_tuning", "dsg_free_batch", "dsg_coreness", "dsg_apx_coreness", "dsg_run_pruned", "dsg_run_pruned_apx", "dsg_run_pruned_apx_exact", "dsg_server_create", "dsg_server_submit", "dsg_server_wait",
             "dsg_server_stats", "dsg_server_destroy"]

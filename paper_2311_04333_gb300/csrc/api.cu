@@ -89,6 +89,8 @@ struct dsg_batch {
     uint32_t *graph_ctr = nullptr;
     void *run_mem = nullptr;         // loads, A, keys, ids, best_loads, staging
     size_t run_bytes = 0;
+    int32_t thread_deg = 32;         // tuning (dsg_set_batch_tuning)
+    int32_t block_deg = 1024;
 };
 
 namespace {
@@ -1394,6 +1396,8 @@ int dsg_run_batch(dsg_batch *Bt, int variant, const int32_t *T, const int64_t *e
     bd.sets = out->sets ? (dev ? out->sets : st_sets) : nullptr;
     bd.best = dev ? out->best : st_best;
     bd.trace = out->trace ? (dev ? out->trace : st_trace) : nullptr;
+    bd.thread_deg = Bt->thread_deg;
+    bd.block_deg = Bt->block_deg;
     CK(cudaMemcpyAsync(Bt->T, T, 4 * (size_t)G, cudaMemcpyHostToDevice, st), "T copy");
     CK(cudaMemcpyAsync(Bt->pq, pq.data(), 16 * (size_t)G, cudaMemcpyHostToDevice, st), "eps copy");
     {
@@ -1409,6 +1413,17 @@ int dsg_run_batch(dsg_batch *Bt, int variant, const int32_t *T, const int64_t *e
     }
     CK(cudaStreamSynchronize(st), "batch run");
     if (ctx->profiling) collect_timings(ctx);
+    return DSG_OK;
+}
+
+int dsg_set_batch_tuning(dsg_batch *b, int32_t thread_degree, int32_t block_degree)
+{
+    if (!b) return DSG_ERR_INVALID;
+    if (thread_degree < 0 || thread_degree > (1 << 20) || block_degree < 0 || block_degree > (1 << 30))
+        return fail(b->ctx, DSG_ERR_INVALID, "thread_degree = %d, block_degree = %d out of range", thread_degree,
+                    block_degree);
+    b->thread_deg = thread_degree ? thread_degree : 32;
+    b->block_deg = block_degree ? block_degree : 1024;
     return DSG_OK;
 }
 

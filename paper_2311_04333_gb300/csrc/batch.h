@@ -26,6 +26,11 @@ struct BatchDev {
     int32_t *sets;            // [N] or nullptr (graph g's set at vbase[g])
     int64_t *best;            // [G][4]: edges, vertices, iteration, set size
     int64_t *trace;           // [G][Tmax][3] or nullptr
+    // tuning knobs (dsg_set_batch_tuning): lists shorter than thread_deg arcs
+    // are scanned by one thread, longer ones by a warp (PaRSorting++); F
+    // vertices above block_deg arcs are counted by the whole block (PaRGreedy++)
+    int32_t thread_deg = 32;
+    int32_t block_deg = 1024;
 };
 
 cudaError_t launch_batch_validate(const BatchDev &B, int full, int32_t *err, cudaStream_t s);

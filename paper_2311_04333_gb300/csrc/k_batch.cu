@@ -124,11 +124,6 @@ __device__ void block_radix_pass(const uint32_t *kin, const uint32_t *iin, const
 }
 
 constexpr uint32_t kNotPeeled = 0xffffffffu;
-#ifndef DSG_BATCH_THREAD_DEG
-#define DSG_BATCH_THREAD_DEG 32
-#endif
-constexpr int64_t kThreadDeg = DSG_BATCH_THREAD_DEG;   // lists shorter than this: one thread each
-constexpr int64_t kBlockScanDeg = 1024;  // F vertices above this degree: whole-block scan
 constexpr int kBigCap = 64;
 
 template <int NT>
@@ -166,7 +161,7 @@ __device__ __forceinline__ uint32_t warp_claim(bool pred, uint32_t *cnt)
 template <int NT>
 __device__ uint32_t block_peel(const int64_t *off, const int32_t *adj, uint32_t n, uint64_t p, uint64_t q,
                                uint32_t *L, uint32_t *A, uint32_t *R, uint32_t *deg, uint32_t *cur,
-                               uint32_t *nxt, uint32_t &width, BatchSmem<NT> &S)
+                               uint32_t *nxt, uint32_t &width, int64_t block_deg, BatchSmem<NT> &S)
 {
     constexpr int NW = NT / 32;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -197,7 +192,7 @@ __device__ uint32_t block_peel(const int64_t *off, const int32_t *adj, uint32_t 
             const uint32_t v = valid ? cur[i] : 0u;
             const bool inF = valid && ((unsigned long long)L[v] + deg[v]) * q <= thr;
             if (inF) R[v] = r;
-            const bool big = inF && off[v + 1] - off[v] > kBlockScanDeg;
+            const bool big = inF && off[v + 1] - off[v] > block_deg;
             const uint32_t bs = warp_claim(big, &S.nbig);
             const bool stored = big && bs < (uint32_t)kBigCap;
             if (stored) S.big[bs] = v;
@@ -295,21 +290,22 @@ k_batch_run(BatchDev B, uint32_t *graph_ctr)
             const uint32_t *src = L;              // sort keys: loads, or rounds
             if (PEEL) {
                 // ---- ordering by rounds of peeling, later-neighbour counts fused
-                const uint32_t rounds = block_peel<NT>(off, adj, n, pp, qq, L, A, R, K0, I0, I1, width, S);
+                const uint32_t rounds = block_peel<NT>(off, adj, n, pp, qq, L, A, R, K0, I0, I1, width, B.block_deg, S);
                 width = block_reduce_u32<NT>(width, true, S);
                 range = rounds - 1;
                 src = R;
             } else {
-                // ---- edge scan: thread per vertex below kThreadDeg arcs
+                // ---- edge scan: thread per vertex below thread_deg arcs
                 // (every lane busy on the many small lists), warp per vertex
                 // above
+                const int64_t thread_deg = B.thread_deg;
                 uint32_t lmn = 0xffffffffu, lmx = 0;
                 for (uint32_t u = threadIdx.x; u < n; u += NT) {
                     const int64_t s = off[u], e = off[u + 1];
                     const uint32_t lu = L[u];
                     lmn = min(lmn, lu);
                     lmx = max(lmx, lu);
-                    if (e - s >= kThreadDeg) continue;
+                    if (e - s >= thread_deg) continue;
                     uint32_t c = 0;
                     #pragma unroll 4
                     for (int64_t j = s; j < e; ++j) {
@@ -322,7 +318,7 @@ k_batch_run(BatchDev B, uint32_t *graph_ctr)
                 }
                 for (uint32_t u = warp; u < n; u += NW) {
                     const int64_t s = off[u], e = off[u + 1];
-                    if (e - s < kThreadDeg) continue;
+                    if (e - s < thread_deg) continue;
                     const uint32_t lu = L[u];
                     uint32_t c = 0;
                     for (int64_t j = s + lane; j < e; j += 32) {

@@ -183,3 +183,30 @@ def test_batch_full_config(env):
     largest = sorted(range(len(graphs)), key=lambda i: -graphs[i].m)[:8]
     sample = sorted(set(largest) | set(rng.choice(len(graphs), 24, replace=False).tolist()))
     _check_full(graphs, T, best, loads, sets, trace, sample)
+
+
+@pytest.mark.parametrize("variant", [0, 1])
+def test_batch_tuning_knobs_do_not_change_results(env, variant):
+    """dsg_set_batch_tuning moves the thread-versus-warp list length and the
+    whole-block degree; every setting gives the oracle's results."""
+    dsg, ctx = env
+    graphs = [gg.er_m(300, 6, 1), gg.complete(40), gg.star(500), gg.rmat(11, 8, 5), gg.chung_lu(2000, 10, 2.1, 4),
+              gg.er_planted_clique(n=700, p=(1, 100), k=20, seed=3)]
+    T = np.array([5, 3, 4, 6, 7, 8], np.int32)
+    p = np.ones(len(graphs), np.int64)
+    q = np.full(len(graphs), 10, np.int64)
+    b = dsg.dsg_upload_batch(ctx, [(g.n, g.off, g.adj) for g in graphs], 0)
+    try:
+        G, N, _ = dsg.dsg_batch_info(b)
+        for td, bd in ((1, 1), (8, 100000), (1000, 64), (0, 0)):
+            dsg.dsg_set_batch_tuning(ctx, b, td, bd)
+            best = np.zeros(4 * G, np.int64)
+            loads = np.zeros(N, np.int64)
+            sets = np.zeros(N, np.int32)
+            trace = np.zeros(3 * G * int(T.max()), np.int64)
+            dsg.dsg_run_batch(ctx, b, variant, T, 512, best, loads, sets, trace, p, q)
+            _check(graphs, T, best.reshape(G, 4), loads, sets, trace.reshape(G, int(T.max()), 3), variant, p, q)
+        with pytest.raises(dsg.DsgError, match="INVALID"):
+            dsg.dsg_set_batch_tuning(ctx, b, -1, 0)
+    finally:
+        dsg.dsg_free_batch(b)

@@ -11,20 +11,27 @@ import pytest
 def tune(monkeypatch):
     from paper_2311_04333_gb300 import _dsg, tune as t
     calls = []
+    knobs = {"thread": 0, "block": 0}
 
     # a batch of 3,000 graphs and 5e6 edges whose launch takes longer with
-    # fewer threads per graph, except for a preferred size
+    # fewer threads per graph, except for a preferred size, and whose
+    # preferred degree knobs are 16 (thread scan) and 4096 (block scan)
     def fake_info(batch):
         return 3000, 10_000_000, 5_000_000
 
+    def fake_tuning(ctx, batch, thread_degree=0, block_degree=0):
+        knobs["thread"], knobs["block"] = thread_degree, block_degree
+
     def fake_run(ctx, batch, variant, T, threads, best, eps_num=None, eps_den=None):
-        calls.append((variant, threads))
-        time.sleep({256: 0.040, 512: 0.005, 1024: 0.020}[threads])
+        calls.append((variant, threads, knobs["thread"], knobs["block"]))
+        extra = 0.004 * (knobs["thread"] not in (0, 16)) if variant == 0 else 0.004 * (knobs["block"] != 4096)
+        time.sleep({256: 0.040, 512: 0.005, 1024: 0.020}[threads] + extra)
 
     monkeypatch.setattr(_dsg, "dsg_batch_info", fake_info)
     monkeypatch.setattr(_dsg, "dsg_run_batch", fake_run)
+    monkeypatch.setattr(_dsg, "dsg_set_batch_tuning", fake_tuning)
     monkeypatch.setattr(t, "_gpu_name", lambda: "fake GPU")
-    return t, calls
+    return t, calls, knobs
 
 
 def test_shape_class_rounds_up_to_powers_of_two():
@@ -35,34 +42,39 @@ def test_shape_class_rounds_up_to_powers_of_two():
 
 
 def test_tuner_picks_fastest_and_caches(tune, tmp_path):
-    t, calls = tune
+    t, calls, knobs = tune
     cache = tmp_path / "c.json"
     rec = t.tune_batch(None, "batch", np.full(3000, 8, np.int32), cache_path=str(cache), reps=2)
-    assert rec["threads"] == 512
-    assert set(rec["ms"]) == {256, 512, 1024}
-    assert len(calls) == 3 * (1 + 2)                  # one warm-up and two timed runs each
+    assert rec["threads"] == 512 and rec["thread_degree"] == 16
+    # block sizes at the default degree, then the other degrees at 512 threads
+    assert {k for k in rec["ms"]} == {"256/32", "512/32", "1024/32", "512/8", "512/16", "512/64", "512/128"}
+    assert len(calls) == 7 * (1 + 2)                  # one warm-up and two timed runs each
+    assert knobs["thread"] == 16                      # the batch is left tuned to the choice
     stored = json.load(open(cache))
     assert list(stored) == ["fake GPU|G2^12_m2^23|variant0"]
-    # a second call is served from the cache; force re-times
+    # a second call is served from the cache (and re-applies it); force re-times
     calls.clear()
-    assert t.tune_batch(None, "batch", None, cache_path=str(cache))["threads"] == 512
+    knobs["thread"] = 0
+    rec2 = t.tune_batch(None, "batch", None, cache_path=str(cache))
+    assert (rec2["threads"], knobs["thread"]) == (512, 16)
     assert calls == []
     t.tune_batch(None, "batch", None, cache_path=str(cache), force=True)
-    assert len(calls) == 6
+    assert len(calls) == 7 * 2
 
 
 def test_tuner_keys_by_variant(tune, tmp_path):
-    t, calls = tune
+    t, calls, knobs = tune
     cache = tmp_path / "c.json"
     t.tune_batch(None, "batch", None, cache_path=str(cache), variant=0)
-    t.tune_batch(None, "batch", None, cache_path=str(cache), variant=1, eps_num=np.ones(3000, np.int64),
-                 eps_den=np.full(3000, 10, np.int64))
+    rec = t.tune_batch(None, "batch", None, cache_path=str(cache), variant=1, eps_num=np.ones(3000, np.int64),
+                       eps_den=np.full(3000, 10, np.int64))
     assert sorted(json.load(open(cache))) == ["fake GPU|G2^12_m2^23|variant0", "fake GPU|G2^12_m2^23|variant1"]
-    assert {v for v, _ in calls} == {0, 1}
+    assert {c[0] for c in calls} == {0, 1}
+    assert rec["block_degree"] == 4096 and knobs["block"] == 4096
 
 
 def test_tuner_ignores_a_broken_cache(tune, tmp_path):
-    t, _ = tune
+    t, _, _ = tune
     cache = tmp_path / "c.json"
     cache.write_text("{not json")
     assert t.tune_batch(None, "batch", None, cache_path=str(cache))["threads"] == 512
