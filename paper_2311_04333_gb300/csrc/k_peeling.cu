@@ -153,6 +153,8 @@ struct PeelSmem {
     uint32_t queue[kQueueCap];              // F vertices of degree (kTinyDegree, kLocalDegree]
     uint32_t tiny[kQueueCap];               // F vertices of degree <= kTinyDegree
     uint32_t nq, nt;
+    uint32_t nsurv, nbase;                  // survivors claimed by the block, their base in the next list
+    unsigned long long arcs_gone;           // arcs of the block's F vertices this round
 };
 
 // later-neighbour count of one F vertex over arcs [s, e) with `stride`
@@ -227,6 +229,8 @@ k_peel(const int64_t *__restrict__ off, const int32_t *__restrict__ adj, int64_t
     if (tid == 0) {
         S.nq = 0;
         S.nt = 0;
+        S.nsurv = 0;
+        S.arcs_gone = 0;
     }
     for (;; ++r) {
         const uint32_t na = ld_acquire_u32(&pc->n_next[r & 1]);
@@ -284,11 +288,12 @@ k_peel(const int64_t *__restrict__ off, const int32_t *__restrict__ adj, int64_t
                     d = off[v + 1] - off[v];
                 }
             }
-            // arcs leaving the alive set with F (one atomic per warp)
+            // arcs leaving the alive set with F (summed per block, one global
+            // atomic per block and round)
             unsigned long long dsum = (unsigned long long)d;
             #pragma unroll
             for (int o = 16; o > 0; o >>= 1) dsum += __shfl_xor_sync(kFull, dsum, o);
-            if (lane == 0 && dsum) atomicAdd(&pc->arcs_alive, ~dsum + 1ull);      // subtract
+            if (lane == 0 && dsum) atomicAdd(&S.arcs_gone, dsum);
             const bool hv = inF && d > kLocalDegree;
             if (hv) {
                 // heavy: global list entry (v, first chunk); its chunks are
@@ -303,13 +308,24 @@ k_peel(const int64_t *__restrict__ off, const int32_t *__restrict__ adj, int64_t
             if (tv) S.tiny[ts] = v;              // ts, qs < kQueueCap: drained below before they can fill
             const uint32_t qs = warp_claim(inF && !hv && !tv, &S.nq);
             if (inF && !hv && !tv) S.queue[qs] = v;
-            const uint32_t ns = warp_claim(valid && !inF, &pc->n_next[(r + 1) & 1]);
-            if (valid && !inF) nxt[ns] = v;
+            // survivors: slots claimed in the block, then one global claim
+            // per block (all warps of the grid on one counter serialise)
+            const uint32_t ns = warp_claim(valid && !inF, &S.nsurv);
             __syncthreads();
+            if (tid == 0) {
+                S.nbase = S.nsurv ? atomicAdd(&pc->n_next[(r + 1) & 1], S.nsurv) : 0u;
+                S.nsurv = 0;
+            }
+            __syncthreads();
+            if (valid && !inF) nxt[S.nbase + ns] = v;
             if (S.nq + kPeelThreads > (uint32_t)kQueueCap || S.nt + kPeelThreads > (uint32_t)kQueueCap)
                 drain_queue(S, off, adj, r, thr, q, st, kv, loads, A);
         }
         drain_queue(S, off, adj, r, thr, q, st, kv, loads, A);
+        if (tid == 0 && S.arcs_gone) {
+            atomicAdd(&pc->arcs_alive, ~S.arcs_gone + 1ull);      // subtract
+            S.arcs_gone = 0;
+        }
         if (!grid_barrier(pc, ctl, P, bar_target)) return;
         // ---- H: chunks of the heavier F vertices, over all blocks
         const unsigned long long hp = ld_acquire_u64(&pc->heavy[r & 1]);
