@@ -24,6 +24,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -350,6 +351,16 @@ def bench_pruned(dsg, g, ctx, stream, T, plain_ms, plain_r) -> dict:
            "k_hat_max": ra["k_max"], "core_vertices": ra["core_vertices"], "core_edges": ra["core_edges"],
            "final_vertices": ra["final_vertices"], "best": [ra["best_edges"], ra["best_vertices"], ra["best_iter"]],
            "best_T5": [ra5["best_edges"], ra5["best_vertices"], ra5["best_iter"]]}
+    # PaRGreedy++ (eps = 1/10) with exact pruning, and PaRApxGreedy++
+    # (approximate pruning followed by exact pruning): identical outputs
+    msg, rg = timed(lambda: dsg.dsg_run_pruned(ctx, g, dsg.DSG_PEELING, T, 1, 10))
+    msga, rga = timed(lambda: dsg.dsg_run_pruned_apx_exact(ctx, g, dsg.DSG_PEELING, T, 1, 10, 3, 2))
+    greedy = {"variant": "PaRGreedy++ eps=1/10 with exact pruning; PaRApxGreedy++ (c = 3/2, then exact)",
+              "T": T, "ms_exact_pruning": msg, "ms_apx_then_exact": msga, "k_max": rga["k_max"],
+              "core_vertices": rga["core_vertices"], "core_edges": rga["core_edges"],
+              "best": [rg["best_edges"], rg["best_vertices"], rg["best_iter"]],
+              "identical": (rg["best_edges"], rg["best_vertices"], rg["best_iter"], rg["core_vertices"]) ==
+                           (rga["best_edges"], rga["best_vertices"], rga["best_iter"], rga["core_vertices"])}
     return {"variant": "PaRSorting++ with exact pruning (Alg. 1)", "T": T, "ms": ms, "plain_ms": plain_ms,
             "speedup_vs_plain": plain_ms / ms, "k_max": r["k_max"], "core_vertices": r["core_vertices"],
             "core_edges": r["core_edges"], "final_vertices": r["final_vertices"],
@@ -357,7 +368,51 @@ def bench_pruned(dsg, g, ctx, stream, T, plain_ms, plain_r) -> dict:
             "plain_best": [plain_r["best_edges"], plain_r["best_vertices"], plain_r["best_iter"]],
             "T5": 5 * T, "ms_T5": ms5, "plain_ms_T5": plain5, "speedup_vs_plain_T5": plain5 / ms5,
             "best_T5": [r5["best_edges"], r5["best_vertices"], r5["best_iter"]],
-            "plain_best_T5": [p5["best_edges"], p5["best_vertices"], p5["best_iter"]], "approximate": apx}
+            "plain_best_T5": [p5["best_edges"], p5["best_vertices"], p5["best_iter"]], "approximate": apx,
+            "greedy": greedy}
+
+
+def peel_bytes(m: int, n: int, rounds_per_iter: float, alive_per_iter: float) -> float:
+    """Algorithmic bytes of one PaRGreedy++ iteration (the byte model of the
+    round peel): 8m (each arc's neighbour id read once when its F vertex is
+    peeled) + 4m (the neighbour's state word) + 8m (at most one atomic
+    decrement per arc, read and write) + 8 per alive vertex per round (key
+    read and snapshot write) + the (round, id) sort with the fused suffix
+    scan over n (12n for one radix pass, 20n + 16n(P - 2) + 8n for P >= 2)."""
+    bits = max(1, math.ceil(math.log2(max(rounds_per_iter, 2))))
+    P = (bits + 7) // 8
+    sort = 12 * n if P == 1 else (20 + 16 * (P - 2) + 8) * n
+    return 20 * m + 8 * alive_per_iter + sort
+
+
+def bench_peeling(dsg, ctx, g, n, m, stream, T, eps=(1, 10), steps=1) -> dict:
+    """PaRGreedy++ (whole-GPU round peel) on a resident graph: GTEPS per
+    iteration, rounds per iteration, microseconds per round, and the
+    fraction of the measured HBM bandwidth by the byte model above."""
+    import torch
+    loads = torch.empty(n, dtype=torch.int64, device="cuda")
+    dsg.dsg_run(ctx, g, dsg.DSG_PEELING, 1, eps[0], eps[1], None, loads, None, None, dsg.DSG_PATH_GRID)
+    dsg.dsg_get_peel_stats(ctx, reset=True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(steps):
+        r = dsg.dsg_run(ctx, g, dsg.DSG_PEELING, T, eps[0], eps[1], None, loads, None, None, dsg.DSG_PATH_GRID)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms_it = ev0.elapsed_time(ev1) / (steps * T)
+    st = dsg.dsg_get_peel_stats(ctx, reset=True)
+    rounds = st["rounds"] / max(st["iterations"], 1)
+    alive = st["alive_sum"] / max(st["iterations"], 1)
+    by = peel_bytes(m, n, rounds, alive)
+    peak, kind = _peak_hbm()
+    return {"eps": f"{eps[0]}/{eps[1]}", "T": T, "gteps": m / (ms_it * 1e-3) / 1e9, "ms_per_iteration": ms_it,
+            "rounds_per_iteration": rounds, "us_per_round": ms_it * 1e3 / max(rounds, 1),
+            "alive_per_round": alive / max(rounds, 1),
+            "roofline": {"bytes_per_iteration": by, "achieved_gbs": by / (ms_it * 1e-3) / 1e9, "peak": peak,
+                         "frac": by / (ms_it * 1e-3) / 1e9 / peak, "peak_kind": kind,
+                         "model": "20m + 8 (alive vertices summed over rounds) + radix bytes of the (round, id) sort"},
+            "best": [r["best_edges"], r["best_vertices"], r["best_iter"]]}
 
 
 def bench_rmat20(dsg, ctx, gg, stream, args) -> dict:
@@ -373,7 +428,7 @@ def bench_rmat20(dsg, ctx, gg, stream, args) -> dict:
     bset = torch.empty(n, dtype=torch.int32, device="cuda")
     out = {"workload": f"rmat20_ef16_seed2, n={n}, m={m}, T={T}"}
     try:
-        for name, variant, p, q in (("sorting", dsg.DSG_SORTING, 0, 1), ("peeling_eps_1_10", dsg.DSG_PEELING, 1, 10)):
+        for name, variant, p, q in (("sorting", dsg.DSG_SORTING, 0, 1),):
             for _ in range(2):
                 dsg.dsg_run(ctx, g, variant, T, p, q, None, loads, bset, None, dsg.DSG_PATH_GRID)
             ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -387,6 +442,8 @@ def bench_rmat20(dsg, ctx, gg, stream, args) -> dict:
             ms_it = ev0.elapsed_time(ev1) / (steps * T)
             out[name] = {"gteps": m / (ms_it * 1e-3) / 1e9, "ms_per_iteration": ms_it,
                          "best": [r["best_edges"], r["best_vertices"], r["best_iter"]]}
+        out["peeling_eps_1_10"] = bench_peeling(dsg, ctx, g, n, m, stream, T, (1, 10), max(1, args.steps // 2))
+        out["peeling_eps_1_100"] = bench_peeling(dsg, ctx, g, n, m, stream, 4, (1, 100), 1)
     finally:
         dsg.dsg_free_graph(g)
     return out
@@ -598,6 +655,8 @@ def main():
 
     # ---- Pruning-and-Refining (Alg. 1) on the same resident graph
     pruned = bench_pruned(dsg, g, ctx, stream, T, ms_total / args.steps, r)
+    # ---- PaRGreedy++ on the same resident graph (a few iterations)
+    peeling27 = bench_peeling(dsg, ctx, g, n, m, stream, 3, (1, 10), 1)
 
     # ---- end to end through the C ABI with host buffers
     off_h = torch.empty(off.numel(), dtype=torch.int64, pin_memory=True)
@@ -690,6 +749,7 @@ def main():
             "batched": batched,
             "rmat20": rmat20,
             "pruned": pruned,
+            "peeling_rmat27": peeling27,
             "serving": serving,
         }
         print(json.dumps(out))

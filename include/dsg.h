@@ -404,6 +404,13 @@ int dsg_set_profiling(dsg_ctx *ctx, int on);
  *   bytes[DSG_PHASE_COUNT]: algorithmic bytes moved per phase (always). */
 int dsg_get_stats(dsg_ctx *ctx, double *ms, int64_t *launches, int64_t *bytes, int reset);
 
+/* PaRGreedy++ telemetry of the whole-GPU dsg_run calls on ctx since the last
+ * reset (Sec. 3.3: the rounds of bucketed peeling; the paper's depth bound
+ * is in the number of rounds): iterations run, rounds peeled in them, and
+ * the alive vertices summed over those rounds (each round touches every
+ * alive vertex once).  Any pointer may be NULL; reset != 0 clears them. */
+int dsg_get_peel_stats(dsg_ctx *ctx, int64_t *iterations, int64_t *rounds, int64_t *alive_sum, int reset);
+
 /* ---- allocation-free entry point ---------------------------------------- */
 
 /* Largest n accepted by dsg_densest_suffix_noalloc. */

@@ -74,6 +74,7 @@ def _load():
     lib.dsg_free_graph.restype = None
     lib.dsg_set_profiling.argtypes = [P, I]
     lib.dsg_get_stats.argtypes = [P, P, P, P, I]
+    lib.dsg_get_peel_stats.argtypes = [P, P, P, P, I]
     lib.dsg_densest_suffix_noalloc.argtypes = [P, P, I64, I64, P, P]
     lib.dsg_upload_batch.argtypes = [P, I32, P, P, P, U32, ctypes.POINTER(P)]
     lib.dsg_batch_info.argtypes = [P, P, P, P]
@@ -282,6 +283,14 @@ def dsg_get_stats(ctx, reset: bool = False) -> dict:
     return {nm: dict(ms=ms[i], launches=la[i], bytes=by[i]) for i, nm in enumerate(names)}
 
 
+def dsg_get_peel_stats(ctx, reset: bool = False) -> dict:
+    """Whole-GPU PaRGreedy++ telemetry: iterations, rounds, alive vertices
+    summed over the rounds."""
+    it, rd, wk = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    _check(ctx, LIB.dsg_get_peel_stats(ctx, ctypes.byref(it), ctypes.byref(rd), ctypes.byref(wk), int(reset)))
+    return {"iterations": it.value, "rounds": rd.value, "alive_sum": wk.value}
+
+
 def dsg_densest_suffix_noalloc(loads, A, n: int, m: int, result, stream: int | None = None) -> None:
     """Enqueue the allocation-free densest-suffix computation.  loads/A are
     uint32 (or int32 bit patterns) CUDA tensors of n entries; result is an
@@ -399,7 +408,7 @@ def dsg_server_destroy(server) -> None:
 DSG_NOALLOC_MAX_VERTICES = 262144
 
 EXPORTED = ["dsg_create", "dsg_destroy", "dsg_last_error", "dsg_debug_set", "dsg_upload_csr", "dsg_graph_info",
-            "dsg_run", "dsg_free_graph", "dsg_set_profiling", "dsg_get_stats",
+            "dsg_run", "dsg_free_graph", "dsg_set_profiling", "dsg_get_stats", "dsg_get_peel_stats",
             "dsg_densest_suffix_noalloc", "dsg_upload_batch", "dsg_batch_info", "dsg_run_batch",
             "dsg_set_batch_tuning", "dsg_free_batch", "dsg_coreness", "dsg_apx_coreness", "dsg_run_pruned", "dsg_run_pruned_apx", "dsg_run_pruned_apx_exact", "dsg_server_create", "dsg_server_submit", "dsg_server_wait",
             "dsg_server_stats", "dsg_server_destroy"]

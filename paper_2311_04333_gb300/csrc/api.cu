@@ -34,6 +34,7 @@ struct dsg_ctx {
     int32_t *err_flags = nullptr;    // device scratch for validation
     unsigned long long *red = nullptr;  // device scratch for reductions
     int peel_max_blocks = 0;         // cap on the PaRGreedy++ grid (0: one block per SM)
+    int64_t peel_iters = 0, peel_rounds = 0, peel_work = 0;   // whole-GPU PaRGreedy++ telemetry
     cudaStream_t cap = nullptr;      // private stream that CUDA graphs are captured on
     // host uploads: the adjacency arrives in chunks on its own stream while
     // the context stream prepares the oriented copy; events [0, kUploadChunks)
@@ -660,6 +661,16 @@ int dsg_set_profiling(dsg_ctx *ctx, int on)
     return DSG_OK;
 }
 
+int dsg_get_peel_stats(dsg_ctx *ctx, int64_t *iterations, int64_t *rounds, int64_t *alive_sum, int reset)
+{
+    if (!ctx) return DSG_ERR_INVALID;
+    if (iterations) *iterations = ctx->peel_iters;
+    if (rounds) *rounds = ctx->peel_rounds;
+    if (alive_sum) *alive_sum = ctx->peel_work;
+    if (reset) ctx->peel_iters = ctx->peel_rounds = ctx->peel_work = 0;
+    return DSG_OK;
+}
+
 int dsg_get_stats(dsg_ctx *ctx, double *ms, int64_t *launches, int64_t *bytes, int reset)
 {
     if (!ctx) return DSG_ERR_INVALID;
@@ -832,6 +843,11 @@ int dsg_run(dsg_graph *G, int variant, int32_t T, int64_t eps_num, int64_t eps_d
         CK(cudaMemcpyAsync(np.data(), G->npass_log, sizeof(int32_t) * T, cudaMemcpyDeviceToHost, s), "npass D2H");
     CK(cudaStreamSynchronize(s), "run");
     if (h.err) return fail(ctx, h.err, "device-side failure %d at site %d (a bounded wait gave up)", h.err, h.err_where);
+    if (variant == DSG_PEELING) {
+        ctx->peel_iters += T;
+        ctx->peel_rounds += (int64_t)h.peel_rounds;
+        ctx->peel_work += (int64_t)h.peel_work;
+    }
     for (int32_t p : np) {
         // pass 0 reads (l, A) and writes l + A; scatter passes read and write
         // (key, value); the last pass reads only.

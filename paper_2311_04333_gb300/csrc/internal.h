@@ -101,6 +101,8 @@ struct Control {
     // histograms of the iteration (written by the edge scan)
     uint32_t hist[kMaxPasses][kBuckets];    // counts per digit of (l - lmin)
     unsigned long long asum[kBuckets];       // sum of deg* per digit of the last pass
+    // PaRGreedy++ telemetry of the run: rounds, and alive vertices summed over rounds
+    unsigned long long peel_rounds, peel_work;
     // best-set materialisation
     int64_t thr_id;          // id of the best suffix's first vertex
     int64_t cnt_less;        // #{v : L(v) < best_key}

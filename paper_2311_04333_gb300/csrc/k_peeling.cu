@@ -373,6 +373,8 @@ __global__ void k_peel_plan(Control *ctl, const PeelCtl *pc)
         ctl->done_ctr = 0;
         ctl->improved = 0;
         ctl->epoch += kMaxPasses;
+        ctl->peel_rounds += pc->rounds;
+        ctl->peel_work += pc->work;
     }
 }
 

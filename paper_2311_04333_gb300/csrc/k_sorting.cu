@@ -31,6 +31,8 @@ __global__ void k_init_ctl(Control *ctl, int64_t m, int64_t n, uint32_t spin_lim
 {
     ctl->spin_limit = spin_limit;
     ctl->debug_stall = debug_stall;
+    ctl->peel_rounds = 0;
+    ctl->peel_work = 0;
     ctl->best_e = m;
     ctl->best_v = n;
     ctl->best_pos = 0;

@@ -69,3 +69,27 @@ def test_resume(dsg, ctx, path):
 def test_rmat20_config(dsg, ctx):
     """R-MAT scale 20, eps = 1/10, T = 20 (the second workload, PaRGreedy++)."""
     check(dsg, ctx, gg.rmat(20, 16, 2), orc.PEELING, 20, 1, 10)
+
+
+def test_round_telemetry_matches_the_oracle(dsg, ctx):
+    """dsg_get_peel_stats: rounds per iteration and alive vertices summed over
+    the rounds of the whole-GPU peel equal the oracle's round structure."""
+    g = gg.rmat(14, 8, 3)
+    T, p, q = 3, 1, 10
+    loads = np.zeros(g.n, np.int64)
+    rounds = alive = 0
+    for _ in range(T):
+        order, rof, rmin = orc.round_order(g, loads, p, q)
+        R = len(rmin)
+        sizes = np.bincount(rof, minlength=R)
+        rounds += R
+        alive += int((g.n - np.concatenate([[0], np.cumsum(sizes)[:-1]])).sum())
+        loads = orc.iteration(g, order, loads)["loads"]
+    h = dsg.dsg_upload_csr(ctx, g.n, g.off, g.adj, 0)
+    try:
+        dsg.dsg_get_peel_stats(ctx, reset=True)
+        dsg.dsg_run(ctx, h, dsg.DSG_PEELING, T, p, q, path=dsg.DSG_PATH_GRID)
+        st = dsg.dsg_get_peel_stats(ctx, reset=True)
+    finally:
+        dsg.dsg_free_graph(h)
+    assert st == {"iterations": T, "rounds": rounds, "alive_sum": alive}
