@@ -490,6 +490,8 @@ def bench_serving(dsg, pool, device, args) -> dict:
 def profile_case(name: str) -> int:
     """One small run of a kernel for profilers (nothing is timed):
     edge_scan_rmat25: PaRSorting++ T = 3 on R-MAT 25 (k_edge_scan launches 2 and 3);
+    edge_scan_rmat27: the same on the benchmarked R-MAT 27 workload (for
+      single-pass counters only: it holds about 30 GB on the device);
     peel_rmat20: PaRGreedy++ eps = 1/10, T = 2, whole-GPU path, on R-MAT 20;
     batch_1024: batched PaRSorting++ T = 8 on 1,024 graphs of the batch recipe."""
     import numpy as np
@@ -497,8 +499,11 @@ def profile_case(name: str) -> int:
     import graphgen as gg
     import paper_2311_04333_gb300 as dsg
     ctx = dsg.dsg_create(0, torch.cuda.current_stream().cuda_stream)
-    if name == "edge_scan_rmat25":
-        n, off, adj = gg.rmat_cuda(25, 16, 3)
+    if name in ("edge_scan_rmat25", "edge_scan_rmat27"):
+        if name == "edge_scan_rmat25":
+            n, off, adj = gg.rmat_cuda(25, 16, 3)
+        else:
+            n, off, adj = gg.rmat_cuda(SCALE, EDGE_FACTOR, SEED, blocks=BLOCKS)
         g = dsg.dsg_upload_csr(ctx, n, off, adj, dsg.DSG_SRC_DEVICE)
         dsg.dsg_run(ctx, g, dsg.DSG_SORTING, 3, 0, 1, None, torch.empty(n, dtype=torch.int64, device="cuda"))
         dsg.dsg_free_graph(g)
@@ -567,7 +572,7 @@ def main():
     ap.add_argument("--serve-warmup", type=float, default=2.0)
     ap.add_argument("--serve-rate", type=float, default=SERVE_RATE)
     ap.add_argument("--serve-slots", type=int, default=SERVE_SLOTS)
-    ap.add_argument("--profile-case", choices=["edge_scan_rmat25", "peel_rmat20", "batch_1024"],
+    ap.add_argument("--profile-case", choices=["edge_scan_rmat25", "edge_scan_rmat27", "peel_rmat20", "batch_1024"],
                     help="run one small case for a profiler instead of the benchmark")
     args = ap.parse_args()
     if args.profile_case:
