@@ -272,9 +272,13 @@ k_peel(const int64_t *__restrict__ off, const int32_t *__restrict__ adj, int64_t
         // F = {key * q <= min * (p + q)}, or {key < fixed_k} (then q = 1)
         const unsigned long long thr = fixed_k != kUnpeeled ? (unsigned long long)fixed_k - 1ull
                                                             : pc->mn[r & 1] * (p + q);
-        for (uint32_t i0 = blockIdx.x * kPeelThreads; i0 < na; i0 += stride) {
-            const uint32_t i = i0 + tid;
-            const bool valid = i < na;
+        // the alive list is dealt out to the blocks in chunks of 32 entries,
+        // round robin, so that consecutive ids (R-MAT's high-degree vertices
+        // have the smallest ids) spread over the blocks
+        for (uint32_t c0 = 0; (uint64_t)(blockIdx.x + (uint64_t)P * c0) * 32 < na; c0 += NW) {
+            const uint64_t chunk = blockIdx.x + (uint64_t)P * (c0 + warp);
+            const uint32_t i = (uint32_t)min(chunk * 32 + lane, (uint64_t)0xffffffffu);
+            const bool valid = chunk * 32 + lane < na;
             uint32_t v = 0;
             bool inF = false;
             int64_t d = 0;
