@@ -121,6 +121,18 @@ int cuda_fail(dsg_ctx *c, cudaError_t e, const char *what)
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// the device view of a pinned (page-locked, mapped) host pointer, or NULL
+// for pageable memory
+const void *pinned_view(const void *p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return (a.type == cudaMemoryTypeHost && a.devicePointer) ? a.devicePointer : nullptr;
+}
+
 // e1/v1 > e2/v2 (v > 0), exact
 bool dens_gt_host(int64_t e1, int64_t v1, int64_t e2, int64_t v2)
 {
@@ -511,8 +523,18 @@ int dsg_upload_csr(dsg_ctx *ctx, int64_t n, const int64_t *offsets, const int32_
     if ((e = dev_malloc((void **)&G->adj, sizeof(int32_t) * (size_t)(arcs > 0 ? arcs : 1), ctx->stream)) != cudaSuccess)
         return bail(cuda_fail(ctx, e, "adjacency allocation"));
     if (!dev_src && upload_fault()) return bail(fail(ctx, DSG_ERR_CUDA, "offsets copy: injected upload failure"));
-    if ((e = cudaMemcpyAsync(G->off, offsets, sizeof(int64_t) * (size_t)(n + 1), kind, ctx->stream)) != cudaSuccess)
+    // pinned host arrays of a large graph are copied by the SMs (steady at the
+    // link's rate, where the copy engines' rate varies several-fold)
+    const void *off_view = (!dev_src && chunked) ? pinned_view(offsets) : nullptr;
+    const void *adj_view = (!dev_src && chunked) ? pinned_view(adj) : nullptr;
+    if (off_view) {
+        if ((e = launch_copy_h2d(off_view, G->off, sizeof(int64_t) * (size_t)(n + 1), ctx->sm_count, ctx->stream)) !=
+            cudaSuccess)
+            return bail(cuda_fail(ctx, e, "offsets copy"));
+    } else if ((e = cudaMemcpyAsync(G->off, offsets, sizeof(int64_t) * (size_t)(n + 1), kind, ctx->stream)) !=
+               cudaSuccess) {
         return bail(cuda_fail(ctx, e, "offsets copy"));
+    }
     if (!dev_src && arcs > 0 && upload_fault())
         return bail(fail(ctx, DSG_ERR_CUDA, "adjacency copy: injected upload failure"));
     if (chunked) {
@@ -548,9 +570,12 @@ int dsg_upload_csr(dsg_ctx *ctx, int64_t n, const int64_t *offsets, const int32_
         }
         chunks_issued = true;   // from here on a failure waits for the last chunk event
         for (int i = 0; i < kUploadChunks; ++i) {
+            const size_t cb = sizeof(int32_t) * (size_t)(a[i + 1] - a[i]);
             if ((a[i + 1] > a[i] &&
-                 (e = cudaMemcpyAsync(G->adj + a[i], adj + a[i], sizeof(int32_t) * (size_t)(a[i + 1] - a[i]),
-                                      cudaMemcpyHostToDevice, ctx->copy)) != cudaSuccess) ||
+                 (e = adj_view ? launch_copy_h2d((const int32_t *)adj_view + a[i], G->adj + a[i], cb, ctx->sm_count,
+                                                 ctx->copy)
+                               : cudaMemcpyAsync(G->adj + a[i], adj + a[i], cb, cudaMemcpyHostToDevice, ctx->copy)) !=
+                     cudaSuccess) ||
                 (e = cudaEventRecord(ctx->up_ev[i], ctx->copy)) != cudaSuccess) {
                 cudaEventRecord(ctx->up_ev[kUploadChunks - 1], ctx->copy);
                 return bail(cuda_fail(ctx, e, "adjacency copy"));
@@ -820,16 +845,21 @@ int dsg_run(dsg_graph *G, int variant, int32_t T, int64_t eps_num, int64_t eps_d
     }
     // outputs: best set, loads, trace
     int nl = 0;
+    // pinned host outputs are written by the kernels directly (no staging)
+    int32_t *set_view = (!dst_dev && out->best_set) ? (int32_t *)pinned_view(out->best_set) : nullptr;
+    int64_t *loads_view = (!dst_dev && out->loads) ? (int64_t *)pinned_view(out->loads) : nullptr;
     int32_t *set_dst = nullptr;
-    if (out->best_set) set_dst = dst_dev ? out->best_set : (int32_t *)((char *)b.scratch + 8 * (size_t)n);
+    if (out->best_set)
+        set_dst = dst_dev ? out->best_set : (set_view ? set_view : (int32_t *)((char *)b.scratch + 8 * (size_t)n));
     {
         PhaseTimer pt(ctx, DSG_PHASE_OTHER);
         CK(launch_best_set(G->g, b, set_dst, s, &nl), "best set");
         if (out->loads) {
-            int64_t *ldst = dst_dev ? out->loads : (int64_t *)b.scratch;
+            int64_t *ldst = dst_dev ? out->loads : (loads_view ? loads_view : (int64_t *)b.scratch);
             CK(launch_loads_out(G->g, b, ldst, s), "loads out");
             ++nl;
-            if (!dst_dev) CK(cudaMemcpyAsync(out->loads, ldst, sizeof(int64_t) * (size_t)n, cudaMemcpyDeviceToHost, s), "loads D2H");
+            if (!dst_dev && !loads_view)
+                CK(cudaMemcpyAsync(out->loads, ldst, sizeof(int64_t) * (size_t)n, cudaMemcpyDeviceToHost, s), "loads D2H");
         }
         if (out->trace)
             CK(cudaMemcpyAsync(out->trace, b.trace, sizeof(int64_t) * 3 * (size_t)T,
@@ -854,7 +884,7 @@ int dsg_run(dsg_graph *G, int variant, int32_t T, int64_t eps_num, int64_t eps_d
         int64_t by = 12 * n + (p > 1 ? 8 * n : 0) + (p > 2 ? 16 * n * (p - 2) : 0) + (p > 1 ? 8 * n : 0);
         ctx->bytes[DSG_PHASE_SORT] += by;
     }
-    if (!dst_dev && out->best_set && h.set_size > 0) {
+    if (!dst_dev && out->best_set && h.set_size > 0 && !set_view) {
         CK(cudaMemcpyAsync(out->best_set, set_dst, sizeof(int32_t) * (size_t)h.set_size, cudaMemcpyDeviceToHost, s),
            "set D2H");
         CK(cudaStreamSynchronize(s), "set D2H");

@@ -248,6 +248,9 @@ cudaError_t build_orientation(GraphDev &g, cudaStream_t s, int full, int32_t *er
                               int64_t **ooff_out, uint32_t **oadj_out, uint32_t **hub_out,
                               int64_t *n_hub_out, uint32_t **hot_out, int64_t *n_hot_out,
                               const UploadChunks *chunks, int *launches);
+// copy of bytes (a multiple of 4, 4-byte aligned) from pinned host memory,
+// given by its device view, to device memory, by the SMs
+cudaError_t launch_copy_h2d(const void *src_dev_view, void *dst, size_t bytes, int sm_count, cudaStream_t s);
 cudaError_t launch_asum_single_pass(const GraphDev &g, RunBufs &b, cudaStream_t s);
 cudaError_t launch_max_u64_of_i64(const int64_t *src, int64_t n, unsigned long long *dst,
                                   int *neg_flag, cudaStream_t s);

@@ -112,3 +112,34 @@ def test_benchmarked_rmat27_T20_matches_oracle():
     finally:
         dsg.dsg_free_graph(g)
         dsg.dsg_destroy(ctx)
+
+
+@pytest.mark.parametrize("shift", [0, 1], ids=["aligned", "misaligned"])
+def test_cold_tier_from_pinned_host_memory(shift):
+    """The same graph uploaded from pinned (page-locked) host buffers, which
+    the SMs copy in chunks; `shift` offsets the adjacency by one word inside
+    its buffer so that host and device addresses differ mod 16 (word copies).
+    The loads and the best set come back into pinned buffers, which the
+    kernels write directly."""
+    import torch
+    import paper_2311_04333_gb300 as dsg
+    stored = _stored("cold_tier")
+    c = mg.COLD_TIER
+    g = gg.er_m(c["n"], c["avg_degree"], c["seed"])
+    off_h = torch.from_numpy(g.off).pin_memory()
+    buf = torch.empty(g.adj.size + shift, dtype=torch.int32).pin_memory()
+    adj_h = buf[shift:]
+    adj_h.copy_(torch.from_numpy(g.adj))
+    rec = stored["sorting"]
+    ctx = dsg.dsg_create(0)
+    gr = dsg.dsg_upload_csr(ctx, g.n, off_h.numpy(), adj_h.numpy())
+    try:
+        T = rec["T"]
+        loads = torch.full((g.n,), -1, dtype=torch.int64).pin_memory().numpy()
+        bset = torch.full((g.n,), -1, dtype=torch.int32).pin_memory().numpy()
+        trace = np.zeros(3 * T, dtype=np.int64)
+        r = dsg.dsg_run(ctx, gr, 0, T, 0, 1, None, loads, bset, trace, dsg.DSG_PATH_GRID)
+        _compare(r, loads, bset, trace, rec, T)
+    finally:
+        dsg.dsg_free_graph(gr)
+        dsg.dsg_destroy(ctx)
