@@ -137,7 +137,10 @@ const char *dsg_last_error(const dsg_ctx *ctx);
  *     so the call that made it returns DSG_ERR_NOMEM; 0 turns it off;
  *   DSG_DEBUG_FAIL_UPLOAD (process-wide, ctx may be NULL): the value-th
  *     host-to-device copy of dsg_upload_csr / dsg_upload_batch from now on
- *     fails and that call returns DSG_ERR_CUDA; 0 turns it off.
+ *     fails and that call returns DSG_ERR_CUDA; 0 turns it off;
+ *   DSG_DEBUG_PEEL_BLOCKS (ctx): at most this many blocks in the whole-GPU
+ *     PaRGreedy++ round kernel of later runs on ctx (the cap each server slot
+ *     sets on its own context; results do not depend on it); 0 = one per SM.
  * The environment variable DSG_FAULT ("alloc:N", "upload:N", or both
  * separated by a comma), read when the library is loaded, sets the two
  * process-wide countdowns the same way.  Returns DSG_ERR_INVALID for an
@@ -146,7 +149,8 @@ typedef enum {
     DSG_DEBUG_SPIN_LIMIT = 1,
     DSG_DEBUG_STALL = 2,
     DSG_DEBUG_FAIL_ALLOC = 3,
-    DSG_DEBUG_FAIL_UPLOAD = 4
+    DSG_DEBUG_FAIL_UPLOAD = 4,
+    DSG_DEBUG_PEEL_BLOCKS = 5
 } dsg_debug_knob;
 int dsg_debug_set(dsg_ctx *ctx, int knob, int64_t value);
 

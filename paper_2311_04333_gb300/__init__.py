@@ -19,7 +19,7 @@ from ._dsg import (DSG_ERR_BUSY, DSG_ERR_CUDA, DSG_ERR_INVALID, DSG_ERR_NOMEM, D
                    dsg_server_stats, dsg_server_submit, dsg_server_wait, dsg_upload_batch,
                    dsg_get_stats, dsg_get_peel_stats, dsg_graph_info, dsg_last_error, dsg_run, dsg_set_profiling,
                    dsg_upload_csr, dsg_debug_set, DSG_DEBUG_SPIN_LIMIT, DSG_DEBUG_STALL,
-                   DSG_DEBUG_FAIL_ALLOC, DSG_DEBUG_FAIL_UPLOAD)
+                   DSG_DEBUG_FAIL_ALLOC, DSG_DEBUG_FAIL_UPLOAD, DSG_DEBUG_PEEL_BLOCKS)
 
 __all__ = ["DSG_OK", "DSG_ERR_INVALID", "DSG_ERR_NOMEM", "DSG_ERR_CUDA", "DSG_ERR_OVERFLOW",
            "DSG_ERR_TIMEOUT", "DSG_ERR_BUSY", "DSG_PATH_GRID", "DSG_PATH_BLOCK", "DSG_SORTING", "DSG_PEELING", "DSG_VALIDATE", "DSG_SRC_DEVICE", "DSG_DST_DEVICE",
@@ -29,7 +29,8 @@ __all__ = ["DSG_OK", "DSG_ERR_INVALID", "DSG_ERR_NOMEM", "DSG_ERR_CUDA", "DSG_ER
            "DSG_NOALLOC_MAX_VERTICES", "dsg_upload_batch", "dsg_batch_info", "dsg_run_batch",
            "dsg_free_batch", "dsg_set_batch_tuning", "dsg_coreness", "dsg_apx_coreness", "dsg_run_pruned", "dsg_run_pruned_apx", "dsg_run_pruned_apx_exact", "dsg_server_create", "dsg_server_submit", "dsg_server_wait",
            "dsg_server_stats", "dsg_server_destroy", "Result", "densest", "dsg_debug_set",
-           "DSG_DEBUG_SPIN_LIMIT", "DSG_DEBUG_STALL", "DSG_DEBUG_FAIL_ALLOC", "DSG_DEBUG_FAIL_UPLOAD"]
+           "DSG_DEBUG_SPIN_LIMIT", "DSG_DEBUG_STALL", "DSG_DEBUG_FAIL_ALLOC", "DSG_DEBUG_FAIL_UPLOAD",
+           "DSG_DEBUG_PEEL_BLOCKS"]
 
 
 @dataclass

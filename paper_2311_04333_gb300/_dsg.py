@@ -144,6 +144,7 @@ def dsg_last_error(ctx) -> str:
 
 
 DSG_DEBUG_SPIN_LIMIT, DSG_DEBUG_STALL, DSG_DEBUG_FAIL_ALLOC, DSG_DEBUG_FAIL_UPLOAD = 1, 2, 3, 4
+DSG_DEBUG_PEEL_BLOCKS = 5
 
 
 def dsg_debug_set(ctx, knob: int, value: int) -> None:

@@ -464,6 +464,10 @@ int dsg_debug_set(dsg_ctx *ctx, int knob, int64_t value)
         if (value < 0) return DSG_ERR_INVALID;
         set_upload_fault(value);
         return DSG_OK;
+    case DSG_DEBUG_PEEL_BLOCKS:
+        if (!ctx || value < 0 || value > 65535) return DSG_ERR_INVALID;
+        ctx->peel_max_blocks = (int)value;
+        return DSG_OK;
     default:
         return ctx ? fail(ctx, DSG_ERR_INVALID, "unknown debug knob %d", knob) : DSG_ERR_INVALID;
     }

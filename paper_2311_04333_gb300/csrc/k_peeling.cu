@@ -38,7 +38,8 @@ constexpr uint32_t kAlivePerBlock = 4096;   // blocks: one per this many alive v
 constexpr int64_t kArcsPerBlock = 65536;    //   or per this many arcs of alive vertices
 constexpr int64_t kLocalDegree = 512;       // F vertices up to this degree: the finding block
 constexpr int64_t kPeelChunk = 2048;        // arcs per work item of the heavier F vertices
-constexpr int kQueueCap = 2048;             // block-local queue of F vertices
+constexpr int kQueueCap = 4096;             // block-local queue of F vertices
+constexpr int kSplitK = 2;                  // alive entries per thread per step of the split
 // heavy-list words: (count or vertex) << 33 | chunk index; n < 2^31 and the
 // chunks of one round are fewer than 2^40 / 2048 + n < 2^33
 constexpr int kHeavyShift = 33;
@@ -251,11 +252,23 @@ k_peel(const int64_t *__restrict__ off, const int32_t *__restrict__ adj, int64_t
         const uint32_t stride = P * kPeelThreads;
         // ---- A: snapshot keys, grid minimum
         unsigned long long mn = ~0ull;
-        for (uint32_t i = blockIdx.x * kPeelThreads + tid; i < na; i += stride) {
-            const uint32_t v = cur[i];
-            const uint32_t k = kv[v];
-            st[v] = ((unsigned long long)kUnpeeled << 32) | k;
-            mn = min(mn, (unsigned long long)k);
+        // four entries per thread in flight: their list entries, then their keys
+        for (uint32_t i0 = blockIdx.x * kPeelThreads + tid; i0 < na; i0 += 4 * stride) {
+            uint32_t vv[4], kk[4];
+            #pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const uint64_t i = i0 + (uint64_t)u * stride;
+                vv[u] = i < na ? cur[i] : 0u;
+            }
+            #pragma unroll
+            for (int u = 0; u < 4; ++u) kk[u] = i0 + (uint64_t)u * stride < na ? kv[vv[u]] : 0u;
+            #pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (i0 + (uint64_t)u * stride < na) {
+                    st[vv[u]] = ((unsigned long long)kUnpeeled << 32) | kk[u];
+                    mn = min(mn, (unsigned long long)kk[u]);
+                }
+            }
         }
         #pragma unroll
         for (int o = 16; o > 0; o >>= 1) mn = min(mn, __shfl_xor_sync(kFull, mn, o));
@@ -275,54 +288,70 @@ k_peel(const int64_t *__restrict__ off, const int32_t *__restrict__ adj, int64_t
         // the alive list is dealt out to the blocks in chunks of 32 entries,
         // round robin, so that consecutive ids (R-MAT's high-degree vertices
         // have the smallest ids) spread over the blocks
-        for (uint32_t c0 = 0; (uint64_t)(blockIdx.x + (uint64_t)P * c0) * 32 < na; c0 += NW) {
-            const uint64_t chunk = blockIdx.x + (uint64_t)P * (c0 + warp);
-            const uint32_t i = (uint32_t)min(chunk * 32 + lane, (uint64_t)0xffffffffu);
-            const bool valid = chunk * 32 + lane < na;
-            uint32_t v = 0;
-            bool inF = false;
-            int64_t d = 0;
-            if (valid) {
-                v = cur[i];
-                const unsigned long long sv = st[v];
-                inF = (sv & 0xffffffffull) * q <= thr;
-                if (inF) {
-                    round[v] = r;
-                    st[v] = ((unsigned long long)r << 32) | (sv & 0xffffffffull);
-                    d = off[v + 1] - off[v];
+        for (uint32_t c0 = 0; (uint64_t)(blockIdx.x + (uint64_t)P * c0) * 32 < na; c0 += NW * kSplitK) {
+            // kSplitK entries per thread: their list entries, snapshot words
+            // and degrees are loaded together
+            uint32_t v[kSplitK];
+            bool valid[kSplitK], inF[kSplitK];
+            unsigned long long sv[kSplitK];
+            int64_t d[kSplitK];
+            #pragma unroll
+            for (int k = 0; k < kSplitK; ++k) {
+                const uint64_t chunk = blockIdx.x + (uint64_t)P * (c0 + warp + (uint64_t)NW * k);
+                const uint64_t i = chunk * 32 + lane;
+                valid[k] = i < na;
+                v[k] = valid[k] ? cur[i] : 0u;
+            }
+            #pragma unroll
+            for (int k = 0; k < kSplitK; ++k) sv[k] = valid[k] ? st[v[k]] : 0ull;
+            #pragma unroll
+            for (int k = 0; k < kSplitK; ++k) {
+                inF[k] = valid[k] && (sv[k] & 0xffffffffull) * q <= thr;
+                d[k] = 0;
+                if (inF[k]) {
+                    round[v[k]] = r;
+                    st[v[k]] = ((unsigned long long)r << 32) | (sv[k] & 0xffffffffull);
+                    d[k] = off[v[k] + 1] - off[v[k]];
                 }
             }
-            // arcs leaving the alive set with F (summed per block, one global
-            // atomic per block and round)
-            unsigned long long dsum = (unsigned long long)d;
+            uint32_t ns[kSplitK];
             #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) dsum += __shfl_xor_sync(kFull, dsum, o);
-            if (lane == 0 && dsum) atomicAdd(&S.arcs_gone, dsum);
-            const bool hv = inF && d > kLocalDegree;
-            if (hv) {
-                // heavy: global list entry (v, first chunk); its chunks are
-                // shared by all blocks after the barrier
-                A[v] = 0;
-                const unsigned long long nc = (unsigned long long)((d + kPeelChunk - 1) / kPeelChunk);
-                const unsigned long long old = atomicAdd(&pc->heavy[r & 1], (1ull << kHeavyShift) | nc);
-                heavy[old >> kHeavyShift] = ((unsigned long long)v << kHeavyShift) | (old & kChunkMask);
+            for (int k = 0; k < kSplitK; ++k) {
+                // arcs leaving the alive set with F (summed per block, one
+                // global atomic per block and round)
+                unsigned long long dsum = (unsigned long long)d[k];
+                #pragma unroll
+                for (int o = 16; o > 0; o >>= 1) dsum += __shfl_xor_sync(kFull, dsum, o);
+                if (lane == 0 && dsum) atomicAdd(&S.arcs_gone, dsum);
+                const bool hv = inF[k] && d[k] > kLocalDegree;
+                if (hv) {
+                    // heavy: global list entry (v, first chunk); its chunks are
+                    // shared by all blocks after the barrier
+                    A[v[k]] = 0;
+                    const unsigned long long nc = (unsigned long long)((d[k] + kPeelChunk - 1) / kPeelChunk);
+                    const unsigned long long old = atomicAdd(&pc->heavy[r & 1], (1ull << kHeavyShift) | nc);
+                    heavy[old >> kHeavyShift] = ((unsigned long long)v[k] << kHeavyShift) | (old & kChunkMask);
+                }
+                const bool tv = inF[k] && d[k] <= kTinyDegree;
+                const uint32_t ts = warp_claim(tv, &S.nt);
+                if (tv) S.tiny[ts] = v[k];       // ts, qs < kQueueCap: drained below before they can fill
+                const uint32_t qs = warp_claim(inF[k] && !hv && !tv, &S.nq);
+                if (inF[k] && !hv && !tv) S.queue[qs] = v[k];
+                // survivors: slots claimed in the block, then one global claim
+                // per block (all warps of the grid on one counter serialise)
+                ns[k] = warp_claim(valid[k] && !inF[k], &S.nsurv);
             }
-            const bool tv = inF && d <= kTinyDegree;
-            const uint32_t ts = warp_claim(tv, &S.nt);
-            if (tv) S.tiny[ts] = v;              // ts, qs < kQueueCap: drained below before they can fill
-            const uint32_t qs = warp_claim(inF && !hv && !tv, &S.nq);
-            if (inF && !hv && !tv) S.queue[qs] = v;
-            // survivors: slots claimed in the block, then one global claim
-            // per block (all warps of the grid on one counter serialise)
-            const uint32_t ns = warp_claim(valid && !inF, &S.nsurv);
             __syncthreads();
             if (tid == 0) {
                 S.nbase = S.nsurv ? atomicAdd(&pc->n_next[(r + 1) & 1], S.nsurv) : 0u;
                 S.nsurv = 0;
             }
             __syncthreads();
-            if (valid && !inF) nxt[S.nbase + ns] = v;
-            if (S.nq + kPeelThreads > (uint32_t)kQueueCap || S.nt + kPeelThreads > (uint32_t)kQueueCap)
+            #pragma unroll
+            for (int k = 0; k < kSplitK; ++k)
+                if (valid[k] && !inF[k]) nxt[S.nbase + ns[k]] = v[k];
+            if (S.nq + kSplitK * kPeelThreads > (uint32_t)kQueueCap ||
+                S.nt + kSplitK * kPeelThreads > (uint32_t)kQueueCap)
                 drain_queue(S, off, adj, r, thr, q, st, kv, loads, A);
         }
         drain_queue(S, off, adj, r, thr, q, st, kv, loads, A);
