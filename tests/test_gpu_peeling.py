@@ -93,3 +93,29 @@ def test_round_telemetry_matches_the_oracle(dsg, ctx):
     finally:
         dsg.dsg_free_graph(h)
     assert st == {"iterations": T, "rounds": rounds, "alive_sum": alive}
+
+
+@pytest.mark.parametrize("blocks", [1, 4, 38])
+def test_capped_grid_matches_oracle(dsg, ctx, blocks):
+    """The round kernel with its grid capped (as each server slot caps it):
+    every block carries a long share of the alive list and long queues of
+    peeled vertices, drained with their arcs laid end to end."""
+    g = gg.rmat(16, 16, 4)
+    dsg.dsg_debug_set(ctx, dsg.DSG_DEBUG_PEEL_BLOCKS, blocks)
+    try:
+        for p, q in ((1, 10), (1, 100)):
+            loads = np.zeros(g.n, np.int64)
+            bset = np.zeros(g.n, np.int32)
+            trace = np.zeros(3 * 4, np.int64)
+            h = dsg.dsg_upload_csr(ctx, g.n, g.off, g.adj, 0)
+            try:
+                r = dsg.dsg_run(ctx, h, dsg.DSG_PEELING, 4, p, q, None, loads, bset, trace, dsg.DSG_PATH_GRID)
+            finally:
+                dsg.dsg_free_graph(h)
+            o = orc.run(g, orc.PEELING, 4, p, q)
+            assert np.array_equal(loads, o.loads)
+            assert (r["best_edges"], r["best_vertices"], r["best_iter"]) == (o.best_edges, o.best_vertices, o.best_iter)
+            assert np.array_equal(bset[: r["best_set_size"]].astype(np.int64), o.best_set)
+            assert np.array_equal(trace.reshape(4, 3), o.trace)
+    finally:
+        dsg.dsg_debug_set(ctx, dsg.DSG_DEBUG_PEEL_BLOCKS, 0)
