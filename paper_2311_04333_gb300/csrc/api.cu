@@ -185,14 +185,14 @@ int ensure_run_bufs(dsg_ctx *ctx, dsg_graph *G, int32_t T)
     const int64_t n = G->g.n;
     RunBufs &b = G->rb;
     if (!G->rb_ready) {
-        const int64_t ntiles = (n + kPassTile - 1) / kPassTile;
+        const int64_t ntiles = pass_tiles_last(n), stiles = pass_tiles_max(n);
         const int64_t nblk = (n + 4095) / 4096 + 1;
         size_t sz[12] = {
             (size_t)n * 4,                      // loads
             (size_t)n * 4,                      // A
             (size_t)n * 16,                     // keys[2], vals[2] (also output staging)
             (size_t)n * 4,                      // best_loads
-            (size_t)ntiles * kBuckets * 8,      // status
+            (size_t)stiles * kBuckets * 8,      // status
             (size_t)ntiles * kBuckets * 16,     // status_sum
             (size_t)ntiles * sizeof(Candidate), // cand
             sizeof(Control),                    // ctl

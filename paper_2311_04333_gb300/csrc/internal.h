@@ -55,8 +55,21 @@ constexpr int kPassThreads = 256;      // == kBuckets (one lookback lane per buc
 #ifndef DSG_PASS_IPT
 #define DSG_PASS_IPT 24
 #endif
-constexpr int kPassIpt = DSG_PASS_IPT;  // items per thread
+constexpr int kPassIpt = DSG_PASS_IPT;  // items per thread of the last pass
 constexpr int kPassTile = kPassThreads * kPassIpt;
+#ifndef DSG_PASS_IPT_SCATTER
+#define DSG_PASS_IPT_SCATTER 24
+#endif
+constexpr int kPassIptS = DSG_PASS_IPT_SCATTER;   // items per thread of the scatter passes
+constexpr int kPassTileS = kPassThreads * kPassIptS;
+// tiles of the last pass, and of whichever pass has more (the look-back
+// status words are indexed by tile)
+__host__ __device__ constexpr int64_t pass_tiles_last(int64_t n) { return (n + kPassTile - 1) / kPassTile; }
+__host__ __device__ constexpr int64_t pass_tiles_scatter(int64_t n) { return (n + kPassTileS - 1) / kPassTileS; }
+__host__ __device__ constexpr int64_t pass_tiles_max(int64_t n)
+{
+    return pass_tiles_last(n) > pass_tiles_scatter(n) ? pass_tiles_last(n) : pass_tiles_scatter(n);
+}
 
 // status word of the decoupled look-back: [epoch:16][flag:2][count:46]
 constexpr uint64_t kFlagAgg = 1, kFlagIncl = 2, kFlagAbort = 3;

@@ -12,7 +12,7 @@ namespace dsg {
 namespace {
 
 constexpr int64_t kNaMaxN = DSG_NOALLOC_MAX_VERTICES;
-constexpr int64_t kNaTiles = (kNaMaxN + kPassTile - 1) / kPassTile;
+constexpr int64_t kNaTiles = pass_tiles_max(kNaMaxN);
 constexpr size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 constexpr size_t kOffKV = 0;                                        // keys[2], vals[2]
 constexpr size_t kOffStatus = kOffKV + al256(16 * (size_t)kNaMaxN);
@@ -156,12 +156,12 @@ extern "C" int dsg_densest_suffix_noalloc(const uint32_t *loads, const uint32_t 
     b.cand = (Candidate *)(base + kOffCand);
     b.ctl = (Control *)(base + kOffCtl);
     b.trace = (int64_t *)(base + kOffTrace);
-    b.ntiles = (n + kPassTile - 1) / kPassTile;
+    b.ntiles = pass_tiles_last(n);
     GraphDev g{};
     g.n = n;
     g.arcs = 2 * m;
     const int grid = (int)imin64((n + 255) / 256, 1024);
-    const int64_t words = b.ntiles * kBuckets;
+    const int64_t words = pass_tiles_max(n) * kBuckets;
     k_na_clear<<<(int)imin64((words + 255) / 256, 1024), 256, 0, s>>>(b.status, b.status_sum, words);
     k_na_reset<<<1, 1, 0, s>>>(b.ctl);
     k_na_minmax<<<grid, 256, 0, s>>>(loads, n, b.ctl);

@@ -538,25 +538,29 @@ cudaError_t launch_asum_single_pass(const GraphDev &g, RunBufs &b, cudaStream_t 
 
 // ============================================================ radix passes
 
-constexpr int kPassTilePad = kPassTile + kPassTile / 32;
 // one pad word every 32 entries: thread-contiguous and striped accesses
 // to the tile are both free of bank conflicts
 __device__ __forceinline__ uint32_t pad(uint32_t lp) { return lp + (lp >> 5); }
 
+// shared memory of a pass with IPT items per thread; the per-digit value
+// sums and candidates only exist in the last pass
+template <int IPT, bool LAST>
 struct PassSmem {
-    uint32_t keys[kPassTilePad];
-    uint32_t vals[kPassTilePad];
+    static constexpr int kTile = kPassThreads * IPT;
+    static constexpr int kLastB = LAST ? kBuckets : 1;
+    uint32_t keys[kTile + kTile / 32];
+    uint32_t vals[kTile + kTile / 32];
     uint32_t wcnt[kPassThreads / 32][kBuckets];
     uint32_t toff[kBuckets + 1];
     uint32_t boff[kBuckets];
     uint32_t gbase[kBuckets];
-    unsigned long long aoff[kBuckets];
-    unsigned long long gsum[kBuckets];
-    unsigned long long dscan[kBuckets];
-    unsigned long long dsum[kBuckets];       // per-digit sum of the tile's values (last pass)
+    unsigned long long aoff[kLastB];
+    unsigned long long gsum[kLastB];
+    unsigned long long dscan[kLastB];
+    unsigned long long dsum[kLastB];       // per-digit sum of the tile's values (last pass)
     unsigned long long asum_acc[kBuckets];
     unsigned long long red[33];
-    Candidate cred[32];
+    Candidate cred[LAST ? 32 : 1];
     uint32_t tile;
     uint32_t last_block;
     uint32_t mn[kPassThreads / 32], mx[kPassThreads / 32];
@@ -564,6 +568,9 @@ struct PassSmem {
 
 #ifndef DSG_PASS_MINBLOCKS
 #define DSG_PASS_MINBLOCKS 3
+#endif
+#ifndef DSG_PASS_MINBLOCKS_SCATTER
+#define DSG_PASS_MINBLOCKS_SCATTER 3
 #endif
 __device__ __forceinline__ unsigned long long status_word(uint32_t epoch, uint64_t flag, uint64_t cnt)
 {
@@ -586,18 +593,25 @@ constexpr int kLookWin = 8;
 // sort locally in shared memory, then resolve its global offsets by
 // decoupled look-back.  Non-last passes scatter; the last pass evaluates the
 // suffix starting at every element's final position (Alg. 3, suffix densities).
-__global__ void __launch_bounds__(kPassThreads, DSG_PASS_MINBLOCKS)
+// Scatter passes and the last pass are separate instantiations (LAST), each
+// with its own tile (IPT items per thread) and residency; the host launches
+// both for every pass index and the one whose role it is not returns at once.
+template <int IPT, bool LAST>
+__global__ void __launch_bounds__(kPassThreads, LAST ? DSG_PASS_MINBLOCKS : DSG_PASS_MINBLOCKS_SCATTER)
 k_radix_pass(const uint32_t *kin, const uint32_t *vin,
              uint32_t *__restrict__ kout, uint32_t *__restrict__ vout,
              uint32_t *loads_next, unsigned long long *status, unsigned long long *status_sum,
              Candidate *cand, int64_t ntiles, int64_t n, int64_t m, Control *ctl, int k, int t,
              int64_t *trace, int accumulate)
 {
+    constexpr int kPassIpt = IPT;
+    constexpr int kPassTile = kPassThreads * IPT;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    PassSmem &S = *reinterpret_cast<PassSmem *>(smem_raw);
+    PassSmem<IPT, LAST> &S = *reinterpret_cast<PassSmem<IPT, LAST> *>(smem_raw);
     const int np = ctl->npass;
     if (k >= np) return;
-    const bool last = (k == np - 1);
+    if ((k == np - 1) != LAST) return;
+    constexpr bool last = LAST;
     if (last && ((uint64_t)m >> 48)) {      // sums must fit the tagged words (every block returns)
         if (threadIdx.x == 0 && blockIdx.x == 0) set_error(ctl, 3, 400 + k);
         return;
@@ -970,12 +984,16 @@ k_radix_pass(const uint32_t *kin, const uint32_t *vin,
 }
 
 static std::once_flag g_pass_once;
+using PassScatter = PassSmem<kPassIptS, false>;
+using PassLast = PassSmem<kPassIpt, true>;
 
 void radix_prepare()
 {
     std::call_once(g_pass_once, [] {
-        cudaFuncSetAttribute(k_radix_pass, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)sizeof(PassSmem));
+        cudaFuncSetAttribute(k_radix_pass<kPassIptS, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sizeof(PassScatter));
+        cudaFuncSetAttribute(k_radix_pass<kPassIpt, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sizeof(PassLast));
     });
 }
 
@@ -986,10 +1004,15 @@ cudaError_t launch_radix_pass(const GraphDev &g, RunBufs &b, int k, int t, cudaS
     // pass k reads: k == 0 -> (loads, A) by id; else buffer (k-1)&1; writes buffer k&1
     const uint32_t *kin = k == 0 ? (key0 ? key0 : b.loads) : b.keys[(k - 1) & 1];
     const uint32_t *vin = k == 0 ? b.A : b.vals[(k - 1) & 1];
-    k_radix_pass<<<(unsigned)b.ntiles, kPassThreads, sizeof(PassSmem), s>>>(
-        kin, vin, b.keys[k & 1], b.vals[k & 1], update_loads ? b.loads : nullptr, b.status,
-        b.status_sum, b.cand,
-        b.ntiles, g.n, g.arcs / 2, b.ctl, k, t, b.trace, accumulate ? 1 : 0);
+    // the last pass can only be pass k when k < kMaxPasses; a scatter pass
+    // only when k < kMaxPasses - 1
+    if (k < kMaxPasses - 1)
+        k_radix_pass<kPassIptS, false><<<(unsigned)pass_tiles_scatter(g.n), kPassThreads, sizeof(PassScatter), s>>>(
+            kin, vin, b.keys[k & 1], b.vals[k & 1], update_loads ? b.loads : nullptr, b.status, b.status_sum,
+            b.cand, pass_tiles_scatter(g.n), g.n, g.arcs / 2, b.ctl, k, t, b.trace, accumulate ? 1 : 0);
+    k_radix_pass<kPassIpt, true><<<(unsigned)pass_tiles_last(g.n), kPassThreads, sizeof(PassLast), s>>>(
+        kin, vin, b.keys[k & 1], b.vals[k & 1], update_loads ? b.loads : nullptr, b.status, b.status_sum,
+        b.cand, pass_tiles_last(g.n), g.n, g.arcs / 2, b.ctl, k, t, b.trace, accumulate ? 1 : 0);
     return cudaGetLastError();
 }
 
