@@ -227,7 +227,11 @@ int ensure_run_bufs(dsg_ctx *ctx, dsg_graph *G, int32_t T)
            "hot counters");
         b.ntiles = ntiles;
         b.nblk64 = nblk;
+        // look-back words start at epoch 0, which no pass uses: memory that
+        // held another graph's words (whose epochs restart with its own
+        // control block) must not be taken for this graph's
         CK(cudaMemsetAsync(b.status, 0, sz[4], ctx->stream), "status init");
+        CK(cudaMemsetAsync(b.status_sum, 0, sz[5], ctx->stream), "status sum init");
         CK(cudaMemsetAsync(b.ctl, 0, sizeof(Control), ctx->stream), "ctl init");
         CK(cudaMemsetAsync(b.A, 0, sz[1], ctx->stream), "A init");
         G->rb_mem = mem;

@@ -627,14 +627,15 @@ k_radix_pass(const uint32_t *kin, const uint32_t *vin,
     }
     for (int i = tid; i < (kPassThreads / 32) * kBuckets; i += kPassThreads) (&S.wcnt[0][0])[i] = 0;
     S.asum_acc[tid] = 0;
-    S.dsum[tid] = 0;
     __syncthreads();
     const uint32_t tile = S.tile;
     const int64_t tbase = (int64_t)tile * kPassTile;
 
-    // ---- load kPassIpt rounds of 32 consecutive items per warp (all loads first);
-    // indices inside the warp's segment are 32-bit
-    uint32_t key_r[kPassIpt], val_r[kPassIpt], dw_r[kPassIpt];
+    // ---- keys: kPassIpt rounds of 32 consecutive items per warp (all loads
+    // first; indices inside the warp's segment are 32-bit).  The values are
+    // loaded once the keys are ranked, so the ranking loop holds only the
+    // keys and their ranks.
+    uint32_t key_r[kPassIpt], rk_r[(kPassIpt + 1) / 2];
     const int64_t wbase = tbase + warp * (32 * kPassIpt);
     const int wrem = (int)imax64(0, imin64(n - wbase, (int64_t)(32 * kPassIpt)));   // valid items of the segment
     const uint32_t *kin_w = kin + wbase;
@@ -643,7 +644,6 @@ k_radix_pass(const uint32_t *kin, const uint32_t *vin,
     for (int r = 0; r < kPassIpt; ++r) {
         const int li = r * 32 + lane;
         key_r[r] = li < wrem ? kin_w[li] : 0u;
-        val_r[r] = li < wrem ? vin_w[li] : 0u;
     }
     // global bucket offsets of this pass's digit (overlaps the loads)
     {
@@ -653,66 +653,32 @@ k_radix_pass(const uint32_t *kin, const uint32_t *vin,
         if (last) S.aoff[tid] = block_excl_sum_u64(ctl->asum[tid], S.red, &tot);
     }
 
-    // ---- warp-level stable ranks (lanes of equal digit)
-    uint32_t lmn = 0xffffffffu, lmx = 0;
-    const bool acc = accumulate && k == 0;
-    const int shift_last = ctl->shift[np - 1];
-    uint32_t amax = 0, rb = 0;
-    unsigned long long rs = 0;
+    // ---- warp-level stable ranks (lanes of equal digit); a rank is below
+    // 32 * kPassIpt, so two fit one register
     #pragma unroll
     for (int r = 0; r < kPassIpt; ++r) {
         const int li = r * 32 + lane;
         const bool valid = li < wrem;
-        const uint32_t key = key_r[r], val = val_r[r];
-        if (valid) {
-            if (k == 0 && loads_next) {
-                const uint32_t nl = key + val;
-                loads_next[wbase + li] = nl;
-                lmn = min(lmn, nl);
-                lmx = max(lmx, nl);
-            }
-            if (acc) {
-                amax = max(amax, val);
-                if (!last) {
-                    const uint32_t dl = ((key - lmin) >> shift_last) & (kBuckets - 1);
-                    if (dl != rb) {
-                        if (rs) atomicAdd(&S.asum_acc[rb], rs);
-                        rb = dl;
-                        rs = 0;
-                    }
-                    rs += val;
-                }
-            }
-        }
-        const uint32_t d = ((key - lmin) >> shift) & (kBuckets - 1);
+        const uint32_t d = ((key_r[r] - lmin) >> shift) & (kBuckets - 1);
         // lanes with the same digit (invalid lanes match only themselves)
         uint32_t peers = __match_any_sync(kFull, valid ? d : (uint32_t)kBuckets + lane);
         if (!valid) peers = 0;
         const uint32_t rank = __popc(peers & lanemask_lt());
         const bool leader = valid && (peers >> lane) == 1u;
-        if (last) {
-            // per-digit value sums of the tile (16-bit halves keep warp sums exact)
-            const uint32_t pm = valid ? peers : (1u << lane);
-            const uint32_t lo = __reduce_add_sync(pm, val & 0xffffu);
-            const uint32_t hi = __reduce_add_sync(pm, val >> 16);
-            if (leader) atomicAdd(&S.dsum[d], (unsigned long long)lo + ((unsigned long long)hi << 16));
-        }
         uint32_t before = 0;
         if (valid) before = S.wcnt[warp][d];
         __syncwarp();
         if (leader) S.wcnt[warp][d] = before + __popc(peers);
         __syncwarp();
-        dw_r[r] = valid ? (d | ((before + rank) << 8)) : 0xffffffffu;
-    }
-    if (acc && rs) atomicAdd(&S.asum_acc[rb], rs);
-    if (k == 0 && loads_next) {
-        lmn = __reduce_min_sync(kFull, lmn);
-        lmx = __reduce_max_sync(kFull, lmx);
-        if (lane == 0) { S.mn[warp] = lmn; S.mx[warp] = lmx; }
+        const uint32_t wr = before + rank;
+        if (r & 1) rk_r[r >> 1] |= wr << 16;
+        else rk_r[r >> 1] = wr;
     }
     __syncthreads();
 
-    // ---- per-digit tile counts; publish the aggregate at once
+    // ---- per-digit tile counts; publish the count aggregate at once (the
+    // last pass publishes its value sums after the local scan below; a
+    // reader checks each word's epoch, so the two need no ordering)
     const int d = tid;
     uint32_t tcount = 0;
     #pragma unroll
@@ -721,31 +687,12 @@ k_radix_pass(const uint32_t *kin, const uint32_t *vin,
         S.wcnt[w][d] = tcount;
         tcount += c;
     }
-    const uint64_t tsum = last ? (uint64_t)S.dsum[d] : 0ull;
     unsigned long long *st = status + (int64_t)tile * kBuckets + d;
     unsigned long long *ss = status_sum + 2 * ((int64_t)tile * kBuckets + d);
-    if (tile == 0) {
-        // (test-only: debug_stall 1 withholds tile 0's words, so that the
-        // look-back of tile 1 waits on words nothing sets and gives up)
-        if (ctl->debug_stall != 1) {
-            if (last) st_relaxed(ss + 1, sum_word(epoch, tsum));
-            st_relaxed(st, status_word(epoch, kFlagIncl, tcount));
-        }
-    } else {
-        if (last) st_relaxed(ss, sum_word(epoch, tsum));
-        st_relaxed(st, status_word(epoch, kFlagAgg, tcount));
-    }
-    if (acc) {
-        amax = __reduce_max_sync(kFull, amax);
-        if (lane == 0 && amax) atomicMax(&ctl->width, amax);
-        if (!last && S.asum_acc[tid]) atomicAdd(&ctl->asum[tid], S.asum_acc[tid]);
-    }
-    if (k == 0 && loads_next && tid == 0) {
-        uint32_t a = 0xffffffffu, b = 0;
-        for (int i = 0; i < kPassThreads / 32; ++i) { a = min(a, S.mn[i]); b = max(b, S.mx[i]); }
-        atomicMin(&ctl->mm_min[(t + 1) & 1], a);
-        atomicMax(&ctl->mm_max[(t + 1) & 1], b);
-    }
+    // (test-only: debug_stall 1 withholds tile 0's words, so that the
+    // look-back of tile 1 waits on words nothing sets and gives up)
+    const bool withhold = tile == 0 && ctl->debug_stall == 1;
+    if (!withhold) st_relaxed(st, status_word(epoch, tile == 0 ? kFlagIncl : kFlagAgg, tcount));
     {
         uint64_t tot;
         const uint64_t ex = block_excl_sum_u64(tcount, S.red, &tot);
@@ -757,23 +704,89 @@ k_radix_pass(const uint32_t *kin, const uint32_t *vin,
     }
     __syncthreads();
 
-    // ---- local stable sort of the tile into shared memory
+    // ---- local stable sort of the tile into shared memory: the keys from
+    // registers (each item's local position replaces its rank), then the
+    // values, loaded now.  The first pass also writes the next loads l + A by
+    // id and gathers the statistics of the loaded pairs.
     #pragma unroll
     for (int r = 0; r < kPassIpt; ++r) {
-        if (dw_r[r] != 0xffffffffu) {
-            const uint32_t dd = dw_r[r] & 0xffu, wr = dw_r[r] >> 8;
-            const uint32_t lp = S.wcnt[warp][dd] + wr;
-            S.keys[pad(lp)] = key_r[r];
-            S.vals[pad(lp)] = val_r[r];
+        const int li = r * 32 + lane;
+        const uint32_t half = (rk_r[r >> 1] >> ((r & 1) * 16)) & 0xffffu;
+        uint32_t lp = 0;
+        if (li < wrem) {
+            const uint32_t key = key_r[r];
+            const uint32_t dd = ((key - lmin) >> shift) & (kBuckets - 1);
+            lp = S.wcnt[warp][dd] + half;
+            S.keys[pad(lp)] = key;
         }
+        if (r & 1) rk_r[r >> 1] = (rk_r[r >> 1] & 0xffffu) | (lp << 16);
+        else rk_r[r >> 1] = (rk_r[r >> 1] & 0xffff0000u) | lp;
+    }
+    uint32_t lmn = 0xffffffffu, lmx = 0, amax = 0, rb = 0;
+    unsigned long long rs = 0;
+    const bool acc = accumulate && k == 0;
+    const int shift_last = ctl->shift[np - 1];
+    uint32_t val_r[kPassIpt];
+    #pragma unroll
+    for (int r = 0; r < kPassIpt; ++r) {
+        const int li = r * 32 + lane;
+        val_r[r] = li < wrem ? vin_w[li] : 0u;
+    }
+    #pragma unroll
+    for (int r = 0; r < kPassIpt; ++r) {
+        const int li = r * 32 + lane;
+        if (li < wrem) {
+            const uint32_t val = val_r[r];
+            const uint32_t lp = (rk_r[r >> 1] >> ((r & 1) * 16)) & 0xffffu;
+            S.vals[pad(lp)] = val;
+            if (k == 0 && (loads_next || acc)) {
+                const uint32_t key = S.keys[pad(lp)];
+                if (loads_next) {
+                    const uint32_t nl = key + val;
+                    loads_next[wbase + li] = nl;
+                    lmn = min(lmn, nl);
+                    lmx = max(lmx, nl);
+                }
+                if (acc) {
+                    amax = max(amax, val);
+                    if (!last) {
+                        const uint32_t dl = ((key - lmin) >> shift_last) & (kBuckets - 1);
+                        if (dl != rb) {
+                            if (rs) atomicAdd(&S.asum_acc[rb], rs);
+                            rb = dl;
+                            rs = 0;
+                        }
+                        rs += val;
+                    }
+                }
+            }
+        }
+    }
+    if (acc) {
+        if (!last && rs) atomicAdd(&S.asum_acc[rb], rs);
+        amax = __reduce_max_sync(kFull, amax);
+        if (lane == 0 && amax) atomicMax(&ctl->width, amax);
+    }
+    if (k == 0 && loads_next) {
+        lmn = __reduce_min_sync(kFull, lmn);
+        lmx = __reduce_max_sync(kFull, lmx);
+        if (lane == 0) { S.mn[warp] = lmn; S.mx[warp] = lmx; }
     }
     __syncthreads();
     const uint32_t tn = S.toff[kBuckets];
+    if (acc && !last && S.asum_acc[tid]) atomicAdd(&ctl->asum[tid], S.asum_acc[tid]);
+    if (k == 0 && loads_next && tid == 0) {
+        uint32_t a = 0xffffffffu, b = 0;
+        for (int i = 0; i < kPassThreads / 32; ++i) { a = min(a, S.mn[i]); b = max(b, S.mx[i]); }
+        atomicMin(&ctl->mm_min[(t + 1) & 1], a);
+        atomicMax(&ctl->mm_max[(t + 1) & 1], b);
+    }
 
     // last pass: exclusive scan of the values over the locally sorted tile;
     // each thread keeps only its chunk's offset (the per-element values are
-    // recomputed after the look-back)
-    uint64_t chunk_ex = 0;
+    // recomputed after the look-back).  The scan at a digit's first and last
+    // element gives the digit's offset in the tile and its value sum.
+    uint64_t chunk_ex = 0, tsum = 0;
     if (last) {
         uint64_t run = 0;
         #pragma unroll
@@ -791,11 +804,13 @@ k_radix_pass(const uint32_t *kin, const uint32_t *vin,
                 const uint32_t dd = ((S.keys[pad(lp)] - lmin) >> shift) & (kBuckets - 1);
                 if (lp == S.toff[dd]) S.dscan[dd] = run;
                 run += S.vals[pad(lp)];
+                if (lp + 1 == S.toff[dd + 1]) S.dsum[dd] = run;      // inclusive scan at the digit's end
             }
         }
-        __syncthreads();     // dscan is read by digit below
+        __syncthreads();     // dscan and dsum are read by digit below
+        tsum = S.toff[d + 1] > S.toff[d] ? (uint64_t)(S.dsum[d] - S.dscan[d]) : 0ull;
+        if (!withhold) st_relaxed(tile == 0 ? ss + 1 : ss, sum_word(epoch, tsum));
     }
-
     // ---- decoupled look-back: thread d resolves digit d.  Every status word
     // carries its own count and every sum its own epoch, so the words need no
     // ordering among themselves: each step loads the words (and sums) of

@@ -286,3 +286,16 @@ def test_chunked_host_upload(dsg, ctx, path):
     adj[g.off[u]] = u
     with pytest.raises(dsg.DsgError, match="INVALID"):
         dsg.dsg_upload_csr(ctx, g.n, g.off, adj, 0)
+
+
+def test_graphs_of_one_size_back_to_back(dsg, ctx):
+    """Graphs of one size, uploaded and freed one after the other, get device
+    memory the previous graph just gave back; the look-back words left there
+    (whose epochs repeat, since every graph's count restarts) must not be
+    taken for the new graph's."""
+    for seed in range(6):
+        g = gg.er_m(60000, 10, 100 + seed)
+        if seed % 2:
+            check(dsg, ctx, g, orc.PEELING, T=3, p=1, q=10)
+        else:
+            check(dsg, ctx, g, orc.SORTING, T=3)
