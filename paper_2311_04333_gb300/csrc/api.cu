@@ -804,8 +804,7 @@ int dsg_run(dsg_graph *G, int variant, int32_t T, int64_t eps_num, int64_t eps_d
                 if (e == cudaSuccess) {
                     PhaseTimer pt(ctx, DSG_PHASE_SORT);
                     e = launch_asum_single_pass(G->g, b, ss);
-                    for (int k = 0; k < kMaxPasses && e == cudaSuccess; ++k)
-                        e = launch_radix_pass(G->g, b, k, t, ss, nullptr, true, true);
+                    if (e == cudaSuccess) e = launch_radix_passes(G->g, b, t, ss, nullptr, true, true);
                 }
                 if (e == cudaSuccess) {
                     PhaseTimer pt(ctx, DSG_PHASE_OTHER);

@@ -225,15 +225,21 @@ cudaError_t launch_init(const GraphDev &g, RunBufs &b, const int64_t *init_dev, 
                         cudaStream_t s);
 cudaError_t launch_plan(const GraphDev &g, RunBufs &b, int t, cudaStream_t s);
 cudaError_t launch_edge_scan(const GraphDev &g, RunBufs &b, int grid, cudaStream_t s);
-// pass k of the radix sort of (key, A); pass 0 reads key0 (default: the
-// loads) and, if update_loads, writes loads += A.
+// the passes of the radix sort of (key, A) for the plan of iteration t: the
+// scatter passes, then the last pass (which evaluates every suffix); pass 0
+// reads key0 (default: the loads) and, if update_loads, writes loads += A.
 // accumulate: pass 0 also reduces the width (max A) and, when it is not the
-// last pass, the per-digit sums of A for the last pass.
+// last pass, the per-digit sums of A for the last pass.  kMaxPasses launches.
+// inputs and ping-pong buffers of the passes
+struct PassIo {
+    const uint32_t *key0, *val0;
+    uint32_t *keys0, *keys1, *vals0, *vals1;
+};
 // one-time kernel attributes of the radix pass (call before any capture)
 void radix_prepare();
-cudaError_t launch_radix_pass(const GraphDev &g, RunBufs &b, int k, int t, cudaStream_t s,
-                              const uint32_t *key0 = nullptr, bool update_loads = true,
-                              bool accumulate = false);
+cudaError_t launch_radix_passes(const GraphDev &g, RunBufs &b, int t, cudaStream_t s,
+                                const uint32_t *key0 = nullptr, bool update_loads = true,
+                                bool accumulate = false);
 cudaError_t launch_snapshot(const GraphDev &g, RunBufs &b, cudaStream_t s);
 cudaError_t launch_best_set(const GraphDev &g, RunBufs &b, int32_t *set_dev, cudaStream_t s,
                             int *launches);

@@ -167,8 +167,7 @@ extern "C" int dsg_densest_suffix_noalloc(const uint32_t *loads, const uint32_t 
     k_na_minmax<<<grid, 256, 0, s>>>(loads, n, b.ctl);
     if (launch_plan(g, b, 1, s) != cudaSuccess) return DSG_ERR_CUDA;
     k_na_hist<<<grid, 256, 0, s>>>(loads, A, n, b.ctl);
-    for (int k = 0; k < kMaxPasses; ++k)
-        if (launch_radix_pass(g, b, k, 1, s, loads, false) != cudaSuccess) return DSG_ERR_CUDA;
+    if (launch_radix_passes(g, b, 1, s, loads, false) != cudaSuccess) return DSG_ERR_CUDA;
     k_na_out<<<1, 1, 0, s>>>(b.ctl, b.trace, result);
     return cudaGetLastError() == cudaSuccess ? DSG_OK : DSG_ERR_CUDA;
 }

@@ -521,12 +521,10 @@ int peel_run(cudaStream_t s, const GraphDev &g, RunBufs &b, PeelBufs &pb, bool &
         }
         k_peel_plan<<<1, 256, 0, s>>>(b.ctl, pc);
         k_peel_hist<<<igrid, 256, 0, s>>>(round, b.A, n, b.ctl);
-        for (int k = 0; k < kMaxPasses; ++k) {
-            e = launch_radix_pass(g, b, k, t, s, round, false);
-            if (e != cudaSuccess) {
-                err = std::string("radix pass: ") + cudaGetErrorString(e);
-                return DSG_ERR_CUDA;
-            }
+        e = launch_radix_passes(g, b, t, s, round, false);
+        if (e != cudaSuccess) {
+            err = std::string("radix pass: ") + cudaGetErrorString(e);
+            return DSG_ERR_CUDA;
         }
         k_peel_snapshot<<<igrid, 256, 0, s>>>(round, b.best_loads, n, b.ctl);
         nl += 6 + kMaxPasses;

@@ -550,7 +550,7 @@ struct PassSmem {
     static constexpr int kLastB = LAST ? kBuckets : 1;
     uint32_t keys[kTile + kTile / 32];
     uint32_t vals[kTile + kTile / 32];
-    uint32_t wcnt[kPassThreads / 32][kBuckets];
+    alignas(8) uint32_t wcnt[kPassThreads / 32][kBuckets];   // (last pass: chunk offsets after the local sort)
     uint32_t toff[kBuckets + 1];
     uint32_t boff[kBuckets];
     uint32_t gbase[kBuckets];
@@ -594,14 +594,14 @@ constexpr int kLookWin = 8;
 // decoupled look-back.  Non-last passes scatter; the last pass evaluates the
 // suffix starting at every element's final position (Alg. 3, suffix densities).
 // Scatter passes and the last pass are separate instantiations (LAST), each
-// with its own tile (IPT items per thread) and residency; the host launches
-// both for every pass index and the one whose role it is not returns at once.
+// with its own tile (IPT items per thread) and residency.  The host launches
+// the scatter instantiation for passes 0 .. kMaxPasses - 2 (a launch whose
+// pass is not a scatter pass returns at once) and the last instantiation
+// once, which takes its pass index np - 1 from the plan on the device.
 template <int IPT, bool LAST>
 __global__ void __launch_bounds__(kPassThreads, LAST ? DSG_PASS_MINBLOCKS : DSG_PASS_MINBLOCKS_SCATTER)
-k_radix_pass(const uint32_t *kin, const uint32_t *vin,
-             uint32_t *__restrict__ kout, uint32_t *__restrict__ vout,
-             uint32_t *loads_next, unsigned long long *status, unsigned long long *status_sum,
-             Candidate *cand, int64_t ntiles, int64_t n, int64_t m, Control *ctl, int k, int t,
+k_radix_pass(PassIo io, uint32_t *loads_next, unsigned long long *status, unsigned long long *status_sum,
+             Candidate *cand, int64_t ntiles, int64_t n, int64_t m, Control *ctl, int kk, int t,
              int64_t *trace, int accumulate)
 {
     constexpr int kPassIpt = IPT;
@@ -609,8 +609,14 @@ k_radix_pass(const uint32_t *kin, const uint32_t *vin,
     extern __shared__ __align__(16) unsigned char smem_raw[];
     PassSmem<IPT, LAST> &S = *reinterpret_cast<PassSmem<IPT, LAST> *>(smem_raw);
     const int np = ctl->npass;
-    if (k >= np) return;
-    if ((k == np - 1) != LAST) return;
+    const int k = LAST ? np - 1 : kk;
+    if (LAST ? (k < 0 || k >= kMaxPasses) : k >= np - 1) return;
+    // pass k reads (key0, val0) by id when k == 0, else the buffers pass
+    // k - 1 wrote; it writes buffer k & 1
+    const uint32_t *kin = k == 0 ? io.key0 : (((k - 1) & 1) ? io.keys1 : io.keys0);
+    const uint32_t *vin = k == 0 ? io.val0 : (((k - 1) & 1) ? io.vals1 : io.vals0);
+    uint32_t *__restrict__ kout = (k & 1) ? io.keys1 : io.keys0;
+    uint32_t *__restrict__ vout = (k & 1) ? io.vals1 : io.vals0;
     constexpr bool last = LAST;
     if (last && ((uint64_t)m >> 48)) {      // sums must fit the tagged words (every block returns)
         if (threadIdx.x == 0 && blockIdx.x == 0) set_error(ctl, 3, 400 + k);
@@ -784,8 +790,9 @@ k_radix_pass(const uint32_t *kin, const uint32_t *vin,
 
     // last pass: exclusive scan of the values over the locally sorted tile;
     // each thread keeps only its chunk's offset (the per-element values are
-    // recomputed after the look-back).  The scan at a digit's first and last
-    // element gives the digit's offset in the tile and its value sum.
+    // recomputed after the look-back).  dscan[d] = the scan at digit d's
+    // first local position toff[d], found from the chunk holding it, so the
+    // digit's value sum is dscan[d + 1] - dscan[d].
     uint64_t chunk_ex = 0, tsum = 0;
     if (last) {
         uint64_t run = 0;
@@ -796,19 +803,21 @@ k_radix_pass(const uint32_t *kin, const uint32_t *vin,
         }
         uint64_t tot;
         chunk_ex = block_excl_sum_u64(run, S.red, &tot);
-        run = chunk_ex;
-        #pragma unroll
-        for (int i = 0; i < kPassIpt; ++i) {
-            const uint32_t lp = tid * kPassIpt + i;
-            if (lp < tn) {
-                const uint32_t dd = ((S.keys[pad(lp)] - lmin) >> shift) & (kBuckets - 1);
-                if (lp == S.toff[dd]) S.dscan[dd] = run;
-                run += S.vals[pad(lp)];
-                if (lp + 1 == S.toff[dd + 1]) S.dsum[dd] = run;      // inclusive scan at the digit's end
+        unsigned long long *cex = reinterpret_cast<unsigned long long *>(&S.wcnt[0][0]);   // free after the local sort
+        cex[tid] = chunk_ex;
+        __syncthreads();
+        {
+            const uint32_t p0 = S.toff[d];
+            uint64_t P = tot;
+            if (p0 < tn) {
+                const uint32_t ct = p0 / kPassIpt, ci = p0 - ct * kPassIpt;
+                P = cex[ct];
+                for (uint32_t j = 0; j < ci; ++j) P += S.vals[pad(ct * kPassIpt + j)];
             }
+            S.dscan[d] = P;
         }
-        __syncthreads();     // dscan and dsum are read by digit below
-        tsum = S.toff[d + 1] > S.toff[d] ? (uint64_t)(S.dsum[d] - S.dscan[d]) : 0ull;
+        __syncthreads();     // dscan is read by digit below
+        tsum = (d + 1 < kBuckets ? (uint64_t)S.dscan[d + 1] : tot) - S.dscan[d];
         if (!withhold) st_relaxed(tile == 0 ? ss + 1 : ss, sum_word(epoch, tsum));
     }
     // ---- decoupled look-back: thread d resolves digit d.  Every status word
@@ -881,8 +890,7 @@ k_radix_pass(const uint32_t *kin, const uint32_t *vin,
         // (modulo 2^32; positions stay below n < 2^31)
         S.gbase[d] = S.boff[d] + (uint32_t)excl - S.toff[d];
         // prefix sum of A before local position lp of digit d: gsum[d] + (the
-        // tile's exclusive value scan at lp); dscan[d] is only set, and gsum[d]
-        // only read, for digits present in the tile
+        // tile's exclusive value scan at lp)
         if (last) S.gsum[d] = S.aoff[d] + excl_sum - S.dscan[d];
         if (abort) S.last_block = 0xdeadu;
     }
@@ -930,34 +938,38 @@ k_radix_pass(const uint32_t *kin, const uint32_t *vin,
             }
         }
     } else {
-        // m < 2^32 and n < 2^31: e * v' < 2^63, so 64-bit cross products
-        // compare the densities exactly
-        // a thread's elements are sorted by digit: the digit's offsets are
-        // reloaded only when it changes
-        uint32_t be = 0, bv = 0, bkey = 0, bpos = 0;
-        uint32_t cd = kBuckets, gb = 0;
-        uint64_t gs = 0;
-        #pragma unroll
-        for (int i = 0; i < kPassIpt; ++i) {
-            const uint32_t lp = tid * kPassIpt + i;
-            if (lp < tn) {
-                const uint32_t key = S.keys[pad(lp)];
-                const uint32_t dd = ((key - lmin) >> shift) & (kBuckets - 1);
-                if (dd != cd) {
-                    cd = dd;
-                    gb = S.gbase[dd];
-                    gs = S.gsum[dd];
+        // m < 2^32 and n < 2^31: every prefix sum and count fits 32 bits (the
+        // sums modulo 2^32 are exact), and e * v' < 2^63, so 64-bit cross
+        // products compare the densities exactly.  A thread's elements are
+        // sorted by digit: its digit advances at the tile's digit starts.
+        const uint32_t lp0 = tid * kPassIpt;
+        if (lp0 < tn) {
+            uint32_t cd = ((S.keys[pad(lp0)] - lmin) >> shift) & (kBuckets - 1);
+            uint32_t nb = S.toff[cd + 1];
+            uint32_t gb = S.gbase[cd];
+            uint32_t gs = (uint32_t)S.gsum[cd] + (uint32_t)chunk_ex;
+            const uint32_t m32 = (uint32_t)m, n32 = (uint32_t)n;
+            uint32_t be = 0, bv = 0, blp = 0, bpos = 0, run32 = 0;
+            #pragma unroll
+            for (int i = 0; i < kPassIpt; ++i) {
+                const uint32_t lp = lp0 + i;
+                if (lp < tn) {
+                    if (lp >= nb) {
+                        do { ++cd; nb = S.toff[cd + 1]; } while (lp >= nb);
+                        gb = S.gbase[cd];
+                        gs = (uint32_t)S.gsum[cd] + (uint32_t)chunk_ex;
+                    }
+                    const uint32_t pos = gb + lp;
+                    const uint32_t e = m32 - (gs + run32);
+                    const uint32_t v = n32 - pos;
+                    if (bv == 0 || (uint64_t)e * bv > (uint64_t)be * v) {
+                        be = e; bv = v; bpos = pos; blp = lp;
+                    }
+                    run32 += S.vals[pad(lp)];
                 }
-                const uint32_t pos = gb + lp;
-                const uint32_t e = (uint32_t)((uint64_t)m - (gs + run));
-                const uint32_t v = (uint32_t)(n - (int64_t)pos);
-                if (bv == 0 || (uint64_t)e * bv > (uint64_t)be * v) {
-                    be = e; bv = v; bpos = pos; bkey = key;
-                }
-                run += S.vals[pad(lp)];
             }
+            if (bv) best = Candidate{(int64_t)be, (int64_t)bv, (int64_t)bpos, (int64_t)S.keys[pad(blp)]};
         }
-        if (bv) best = Candidate{(int64_t)be, (int64_t)bv, (int64_t)bpos, (int64_t)bkey};
     }
     best = block_best(best, S.cred);
     if (tid == 0) {
@@ -1012,22 +1024,19 @@ void radix_prepare()
     });
 }
 
-cudaError_t launch_radix_pass(const GraphDev &g, RunBufs &b, int k, int t, cudaStream_t s,
-                              const uint32_t *key0, bool update_loads, bool accumulate)
+cudaError_t launch_radix_passes(const GraphDev &g, RunBufs &b, int t, cudaStream_t s,
+                                const uint32_t *key0, bool update_loads, bool accumulate)
 {
     radix_prepare();
-    // pass k reads: k == 0 -> (loads, A) by id; else buffer (k-1)&1; writes buffer k&1
-    const uint32_t *kin = k == 0 ? (key0 ? key0 : b.loads) : b.keys[(k - 1) & 1];
-    const uint32_t *vin = k == 0 ? b.A : b.vals[(k - 1) & 1];
-    // the last pass can only be pass k when k < kMaxPasses; a scatter pass
-    // only when k < kMaxPasses - 1
-    if (k < kMaxPasses - 1)
+    const PassIo io{key0 ? key0 : b.loads, b.A, b.keys[0], b.keys[1], b.vals[0], b.vals[1]};
+    uint32_t *ln = update_loads ? b.loads : nullptr;
+    for (int k = 0; k < kMaxPasses - 1; ++k)
         k_radix_pass<kPassIptS, false><<<(unsigned)pass_tiles_scatter(g.n), kPassThreads, sizeof(PassScatter), s>>>(
-            kin, vin, b.keys[k & 1], b.vals[k & 1], update_loads ? b.loads : nullptr, b.status, b.status_sum,
-            b.cand, pass_tiles_scatter(g.n), g.n, g.arcs / 2, b.ctl, k, t, b.trace, accumulate ? 1 : 0);
+            io, ln, b.status, b.status_sum, b.cand, pass_tiles_scatter(g.n), g.n, g.arcs / 2, b.ctl, k, t, b.trace,
+            accumulate ? 1 : 0);
     k_radix_pass<kPassIpt, true><<<(unsigned)pass_tiles_last(g.n), kPassThreads, sizeof(PassLast), s>>>(
-        kin, vin, b.keys[k & 1], b.vals[k & 1], update_loads ? b.loads : nullptr, b.status, b.status_sum,
-        b.cand, pass_tiles_last(g.n), g.n, g.arcs / 2, b.ctl, k, t, b.trace, accumulate ? 1 : 0);
+        io, ln, b.status, b.status_sum, b.cand, pass_tiles_last(g.n), g.n, g.arcs / 2, b.ctl, -1, t, b.trace,
+        accumulate ? 1 : 0);
     return cudaGetLastError();
 }
 
