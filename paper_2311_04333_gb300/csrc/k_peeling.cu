@@ -365,16 +365,40 @@ k_peel(const int64_t *__restrict__ off, const int32_t *__restrict__ adj, int64_t
         const uint32_t nh = (uint32_t)(hp >> kHeavyShift);
         if (nh > 0) {
             const unsigned long long nchunks = hp & kChunkMask;
+            // the heavy list's first chunks and vertices in shared memory (the
+            // queues are empty here), so that a chunk finds its vertex without
+            // a dependent global load per search step; longer lists (rare)
+            // are searched in global memory
+            const bool local = nh <= (uint32_t)kQueueCap && nchunks <= 0xffffffffull;
+            if (local && blockIdx.x < nchunks) {
+                for (uint32_t i = tid; i < nh; i += kPeelThreads) {
+                    const unsigned long long h = heavy[i];
+                    S.queue[i] = (uint32_t)(h & kChunkMask);
+                    S.tiny[i] = (uint32_t)(h >> kHeavyShift);
+                }
+                __syncthreads();
+            }
             for (unsigned long long k = blockIdx.x; k < nchunks; k += P) {
                 // the heavy entry holding chunk k: last with first chunk <= k
-                uint32_t lo = 0, hi = nh - 1;
-                while (lo < hi) {
-                    const uint32_t mid = (lo + hi + 1) >> 1;
-                    if ((heavy[mid] & kChunkMask) <= k) lo = mid; else hi = mid - 1;
+                uint32_t lo = 0, hi = nh - 1, v;
+                unsigned long long first;
+                if (local) {
+                    while (lo < hi) {
+                        const uint32_t mid = (lo + hi + 1) >> 1;
+                        if (S.queue[mid] <= k) lo = mid; else hi = mid - 1;
+                    }
+                    v = S.tiny[lo];
+                    first = S.queue[lo];
+                } else {
+                    while (lo < hi) {
+                        const uint32_t mid = (lo + hi + 1) >> 1;
+                        if ((heavy[mid] & kChunkMask) <= k) lo = mid; else hi = mid - 1;
+                    }
+                    const unsigned long long h = heavy[lo];
+                    v = (uint32_t)(h >> kHeavyShift);
+                    first = h & kChunkMask;
                 }
-                const unsigned long long h = heavy[lo];
-                const uint32_t v = (uint32_t)(h >> kHeavyShift);
-                const int64_t s0 = off[v] + (int64_t)(k - (h & kChunkMask)) * kPeelChunk;
+                const int64_t s0 = off[v] + (int64_t)(k - first) * kPeelChunk;
                 const int64_t e0 = min(off[v + 1], s0 + kPeelChunk);
                 uint32_t c = count_arcs(adj, s0, e0, tid, kPeelThreads, v, r, thr, q, st, kv);
                 c = __reduce_add_sync(kFull, c);
