@@ -49,15 +49,11 @@ __device__ __forceinline__ uint32_t block_reduce_u32(uint32_t x, bool is_max, Ba
     return r;
 }
 
-// lanes (among the valid ones) holding the same 8-bit digit (bit-sliced match)
+// lanes (among the valid ones) holding the same 8-bit digit (invalid lanes
+// match only themselves)
 __device__ __forceinline__ uint32_t digit_peers(uint32_t d, bool valid)
 {
-    uint32_t peers = __ballot_sync(kFull, valid);
-    #pragma unroll
-    for (int bit = 0; bit < kRadixBits; ++bit) {
-        const uint32_t bb = __ballot_sync(kFull, (d >> bit) & 1u);
-        peers &= ((d >> bit) & 1u) ? bb : ~bb;
-    }
+    const uint32_t peers = __match_any_sync(kFull, valid ? d : (uint32_t)kBuckets + (threadIdx.x & 31));
     return valid ? peers : 0u;
 }
 
@@ -124,6 +120,7 @@ __device__ void block_radix_pass(const uint32_t *kin, const uint32_t *iin, const
 }
 
 constexpr uint32_t kNotPeeled = 0xffffffffu;
+constexpr int kScanK = 8;            // positions per thread of the suffix scan
 constexpr int kBigCap = 64;
 
 template <int NT>
@@ -356,16 +353,29 @@ k_batch_run(BatchDev B, uint32_t *graph_ctr)
                 keys = kin;
             }
             // ---- densest suffix: scan of A in order, first maximum
+            // kScanK consecutive positions per thread, one block scan per
+            // NT * kScanK positions
             Candidate best{0, 0, 0, 0};
             uint64_t carry = 0;
-            for (uint32_t c0 = 0; c0 < n; c0 += NT) {
-                const uint32_t pos = c0 + threadIdx.x;
-                const uint64_t a = pos < n ? A[ids[pos]] : 0u;
+            for (uint32_t c0 = 0; c0 < n; c0 += NT * kScanK) {
+                const uint32_t p0 = c0 + threadIdx.x * kScanK;
+                uint32_t a[kScanK];
+                uint64_t run = 0;
+                #pragma unroll
+                for (int k = 0; k < kScanK; ++k) {
+                    a[k] = p0 + k < n ? A[ids[p0 + k]] : 0u;
+                    run += a[k];
+                }
                 uint64_t tot;
-                const uint64_t ex = block_excl_sum_u64(a, S.red, &tot);
-                if (pos < n) {
-                    Candidate cd{(int64_t)((uint64_t)m - (carry + ex)), (int64_t)(n - pos), (int64_t)pos, 0};
-                    if (cand_better(cd, best)) best = cd;
+                uint64_t pre = carry + block_excl_sum_u64(run, S.red, &tot);
+                #pragma unroll
+                for (int k = 0; k < kScanK; ++k) {
+                    const uint32_t pos = p0 + k;
+                    if (pos < n) {
+                        Candidate cd{(int64_t)((uint64_t)m - pre), (int64_t)(n - pos), (int64_t)pos, 0};
+                        if (cand_better(cd, best)) best = cd;
+                        pre += a[k];
+                    }
                 }
                 carry += tot;
             }
