@@ -263,10 +263,25 @@ def bench_batch(dsg, ctx, graphs, args, ws: int = 1, rank: int = 0) -> dict:
            "one_per_launch_graphs_per_s": G / t1,
            "one_per_launch_ms": t1 * 1e3, "speedup": t1 / tb, "identical_results": same,
            "gteps_batched": Mtot * BATCH_T / tb / 1e9,
+           "roofline": _batch_roofline(Mtot, Ntot, BATCH_T, tb),
            "sharding": {"ranks": ws, "split": "contiguous graph ranges balanced by 2m + n",
                         "rank0_range": [lo, hi] if rank == 0 else None}}
     out["peeling"] = bench_batch_peeling(dsg, ctx, graphs, args, ws, rank)
     return out
+
+
+def _batch_roofline(M: int, N: int, T: int, seconds: float) -> dict:
+    """The batch against HBM by the symmetric-CSR edge-scan model of one
+    iteration, 16m + 16n bytes per graph (each of the 2m arcs read once and
+    its target's load gathered once; offsets, own load and count per
+    vertex), times T iterations: the bytes one batched launch would move if
+    every access went to DRAM.  Each block keeps its graph in L2, so the
+    fraction shows how far the latency-bound blocks are from that rate."""
+    peak, kind = _peak_hbm()
+    by = (16 * M + 16 * N) * T
+    ach = by / seconds / 1e9
+    return {"bound": "hbm", "model": "(16m + 16n) per graph and iteration", "bytes_per_batch": by,
+            "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak, "peak_kind": kind}
 
 
 def bench_batch_peeling(dsg, ctx, graphs, args, ws: int = 1, rank: int = 0) -> dict:
