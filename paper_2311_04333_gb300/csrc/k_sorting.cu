@@ -742,10 +742,17 @@ k_radix_pass(PassIo io, uint32_t *loads_next, unsigned long long *status, unsign
     for (int r = 0; r < kPassIpt; ++r) {
         const int li = r * 32 + lane;
         if (li < wrem) {
-            const uint32_t val = val_r[r];
             const uint32_t lp = (rk_r[r >> 1] >> ((r & 1) * 16)) & 0xffffu;
-            S.vals[pad(lp)] = val;
-            if (k == 0 && (loads_next || acc)) {
+            S.vals[pad(lp)] = val_r[r];
+        }
+    }
+    if (k == 0 && (loads_next || acc)) {
+        #pragma unroll
+        for (int r = 0; r < kPassIpt; ++r) {
+            const int li = r * 32 + lane;
+            if (li < wrem) {
+                const uint32_t val = val_r[r];
+                const uint32_t lp = (rk_r[r >> 1] >> ((r & 1) * 16)) & 0xffffu;
                 const uint32_t key = S.keys[pad(lp)];
                 if (loads_next) {
                     const uint32_t nl = key + val;
