@@ -245,6 +245,21 @@ cudaError_t scan_exclusive_i64(int64_t *x, int64_t count, int64_t *total_dev, in
     return cudaGetLastError();
 }
 
+// x[0, count) += *base, and then (second kernel) *base += *add: the running
+// base of scans taken range by range
+__global__ void k_add_base(int64_t *x, int64_t count, const int64_t *base)
+{
+    const int64_t b = *base;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+        x[i] += b;
+}
+
+__global__ void k_advance(int64_t *base, const int64_t *add, int64_t *copy_to)
+{
+    *base += *add;
+    if (copy_to) *copy_to = *base;
+}
+
 // ============================================================ degree orientation
 // Each undirected edge {u, w} is stored once, at the endpoint with the
 // smaller (degree, id); the other endpoint is the arc's target.  Targets
@@ -350,14 +365,16 @@ __global__ void k_orient_count(const int64_t *__restrict__ off, const int32_t *_
 
 // the same, one block per vertex of degree > kBigDeg
 __global__ void k_orient_count_big(const int64_t *__restrict__ off, const int32_t *__restrict__ adj,
-                                   int64_t n, const uint32_t *__restrict__ deg32,
+                                   int64_t n, int64_t u0, int64_t u1, const uint32_t *__restrict__ deg32,
                                    const uint32_t *__restrict__ big, int64_t n_big, int full,
                                    int32_t *err, int64_t *ocnt, uint32_t *bits)
 {
     __shared__ uint32_t red[32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int64_t b = blockIdx.x; b < n_big; b += gridDim.x) {
-        const int64_t u = big[b], s = off[u], e = off[u + 1];
+        const int64_t u = big[b];
+        if (u < u0 || u >= u1) continue;                    // the block's uniform choice
+        const int64_t s = off[u], e = off[u + 1];
         const uint32_t du = (uint32_t)(e - s);
         uint32_t c = 0;
         for (int64_t j0 = s; j0 < e; j0 += blockDim.x) {
@@ -383,17 +400,18 @@ __global__ void k_orient_count_big(const int64_t *__restrict__ off, const int32_
     }
 }
 
-// warp per vertex of degree <= kBigDeg: the kept targets in list order (the
-// keep bits spare a second gather of the targets' degrees)
+// warp per vertex of degree <= kBigDeg in [u0, u1): the kept targets in list
+// order (the keep bits spare a second gather of the targets' degrees).  A
+// position at or beyond cap (oadj's size) is not written; it sets *ovf.
 __global__ void k_orient_fill(const int64_t *__restrict__ off, const int32_t *__restrict__ adj,
-                              int64_t n, const int64_t *__restrict__ ooff,
+                              int64_t u0, int64_t u1, const int64_t *__restrict__ ooff,
                               const uint32_t *__restrict__ bits, const uint32_t *__restrict__ enc,
-                              uint32_t *oadj)
+                              uint32_t *oadj, int64_t cap, int32_t *ovf)
 {
     const int lane = threadIdx.x & 31;
     const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t u = wid; u < n; u += nw) {
+    for (int64_t u = u0 + wid; u < u1; u += nw) {
         const int64_t s = off[u], e = off[u + 1];
         if ((uint64_t)(e - s) > kBigDeg) continue;
         int64_t o = ooff[u];
@@ -401,7 +419,11 @@ __global__ void k_orient_fill(const int64_t *__restrict__ off, const int32_t *__
             const int64_t j = j0 + lane;
             const bool keep = j < e && keep_bit(bits, j);
             const uint32_t m = __ballot_sync(kFull, keep);
-            if (keep) oadj[o + __popc(m & lanemask_lt())] = enc[adj[j]];
+            if (keep) {
+                const int64_t pos = o + __popc(m & lanemask_lt());
+                if (pos < cap) oadj[pos] = enc[adj[j]];
+                else atomicExch(ovf, 1);
+            }
             o += __popc(m);
         }
     }
@@ -409,14 +431,17 @@ __global__ void k_orient_fill(const int64_t *__restrict__ off, const int32_t *__
 
 // one block per vertex of degree > kBigDeg
 __global__ void k_orient_fill_big(const int64_t *__restrict__ off, const int32_t *__restrict__ adj,
-                                  const int64_t *__restrict__ ooff, const uint32_t *__restrict__ bits,
-                                  const uint32_t *__restrict__ enc, const uint32_t *__restrict__ big,
-                                  int64_t n_big, uint32_t *oadj)
+                                  int64_t u0, int64_t u1, const int64_t *__restrict__ ooff,
+                                  const uint32_t *__restrict__ bits, const uint32_t *__restrict__ enc,
+                                  const uint32_t *__restrict__ big, int64_t n_big, uint32_t *oadj, int64_t cap,
+                                  int32_t *ovf)
 {
     __shared__ uint32_t wc[33];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
     for (int64_t b = blockIdx.x; b < n_big; b += gridDim.x) {
-        const int64_t u = big[b], s = off[u], e = off[u + 1];
+        const int64_t u = big[b];
+        if (u < u0 || u >= u1) continue;                    // the block's uniform choice
+        const int64_t s = off[u], e = off[u + 1];
         int64_t o = ooff[u];
         for (int64_t j0 = s; j0 < e; j0 += blockDim.x) {
             const int64_t j = j0 + threadIdx.x;
@@ -431,7 +456,11 @@ __global__ void k_orient_fill_big(const int64_t *__restrict__ off, const int32_t
                 wc[32] = t;
             }
             __syncthreads();
-            if (keep) oadj[o + wc[warp] + __popc(m & lanemask_lt())] = enc[adj[j]];
+            if (keep) {
+                const int64_t pos = o + wc[warp] + __popc(m & lanemask_lt());
+                if (pos < cap) oadj[pos] = enc[adj[j]];
+                else atomicExch(ovf, 1);
+            }
             o += wc[32];
         }
     }
@@ -508,7 +537,7 @@ cudaError_t build_orientation(GraphDev &g, cudaStream_t s, int full, int32_t *er
     int32_t *slot_of = nullptr, *slot_of_scratch = nullptr;
     const int64_t ntmp = scan_tmp_count(n + 1);
     if ((e = dev_malloc((void **)&cnt, 8, s)) != cudaSuccess) return e;
-    if ((e = dev_malloc((void **)&tmp, 8 * (size_t)(ntmp + 2), s)) != cudaSuccess) return e;
+    if ((e = dev_malloc((void **)&tmp, 8 * (size_t)(ntmp + 4), s)) != cudaSuccess) return e;
     if ((e = dev_malloc((void **)&flag, 8 * (size_t)(n + 1), s)) != cudaSuccess) return e;
     if ((e = dev_malloc((void **)&slot_of, 4 * (size_t)n, s)) != cudaSuccess) return e;
     if ((e = dev_malloc((void **)&slot_of_scratch, 4 * (size_t)n, s)) != cudaSuccess) return e;
@@ -569,38 +598,83 @@ cudaError_t build_orientation(GraphDev &g, cudaStream_t s, int full, int32_t *er
     const int wgrid = (int)imin64((n * 32 + 255) / 256, 152 * 32);
     const int bgrid = (int)imin64(imax64(n_big, 1), 152 * 2);
     const int nch = chunks ? chunks->k : 0;
+    int64_t *run = tmp + ntmp + 1;                                  // running base of the chunk scans
+    int32_t *ovf = reinterpret_cast<int32_t *>(tmp + ntmp + 2);     // a fill position beyond oadj's size
+    int64_t oarcs = 0;
+    uint32_t *oadj = nullptr;
+    bool pipelined = false;
+    const int64_t cap = g.arcs / 2;
     if (nch > 0 && !full) {
+        // a host upload in chunks: as soon as a chunk lands, its vertices are
+        // counted, their oriented offsets scanned onto the running base and
+        // their kept arcs filled, while the later chunks are still copied.
+        // oadj gets m entries, exactly the oriented arcs of a symmetric graph;
+        // one that needs more (asymmetric input, accepted without
+        // DSG_VALIDATE) is counted and filled again below at its own size
+        if ((e = dev_malloc((void **)&oadj, 4 * (size_t)imax64(cap, 1), s)) != cudaSuccess) return e;
+        cudaMemsetAsync(run, 0, 16, s);                             // run and ovf
+        pipelined = true;
         for (int i = 0; i < nch; ++i) {
             if ((e = cudaStreamWaitEvent(s, chunks->ev[i], 0)) != cudaSuccess) return e;
             const int64_t v0 = chunks->v[i], v1 = chunks->v[i + 1];
             if (v1 <= v0) continue;
             const int cgrid = (int)imin64(((v1 - v0) * 32 + 255) / 256, 152 * 32);
+            const int agrid = (int)imin64((v1 - v0 + 255) / 256, 152 * 8);
             k_orient_count<<<cgrid, 256, 0, s>>>(g.off, g.adj, n, v0, v1, deg32, full, err, flag, bits);
-            ++nl;
+            if (n_big)
+                k_orient_count_big<<<bgrid, 1024, 0, s>>>(g.off, g.adj, n, v0, v1, deg32, big, n_big, full, err, flag,
+                                                          bits);
+            if ((e = scan_exclusive_i64(flag + v0, v1 - v0, total, tmp, s)) != cudaSuccess) return e;
+            k_add_base<<<agrid, 256, 0, s>>>(flag + v0, v1 - v0, run);
+            k_advance<<<1, 1, 0, s>>>(run, total, flag + n);
+            k_orient_fill<<<cgrid, 256, 0, s>>>(g.off, g.adj, v0, v1, flag, bits, enc, oadj, cap, ovf);
+            if (n_big)
+                k_orient_fill_big<<<bgrid, 1024, 0, s>>>(g.off, g.adj, v0, v1, flag, bits, enc, big, n_big, oadj, cap,
+                                                         ovf);
+            nl += 8 + (n_big ? 2 : 0);
         }
     } else {
         for (int i = 0; i < nch; ++i)
             if ((e = cudaStreamWaitEvent(s, chunks->ev[i], 0)) != cudaSuccess) return e;
         k_orient_count<<<wgrid, 256, 0, s>>>(g.off, g.adj, n, 0, n, deg32, full, err, flag, bits);
         ++nl;
+        if (n_big)
+            k_orient_count_big<<<bgrid, 1024, 0, s>>>(g.off, g.adj, n, 0, n, deg32, big, n_big, full, err, flag, bits);
     }
-    if (n_big) k_orient_count_big<<<bgrid, 1024, 0, s>>>(g.off, g.adj, n, deg32, big, n_big, full, err, flag, bits);
     int32_t h_err[8];
+    int32_t h_ovf = 0;
     cudaMemcpyAsync(h_err, err, sizeof(h_err), cudaMemcpyDeviceToHost, s);
+    if (pipelined) {
+        cudaMemcpyAsync(&oarcs, run, 8, cudaMemcpyDeviceToHost, s);
+        cudaMemcpyAsync(&h_ovf, ovf, 4, cudaMemcpyDeviceToHost, s);
+    }
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
     bool bad = false;
     for (int i = 0; i < 5; ++i) bad |= h_err[i] != 0;
     *sorted_out = h_err[5] ? 0 : 1;
-    int64_t oarcs = 0;
-    uint32_t *oadj = nullptr;
-    if (!bad) {
+    if (pipelined && (bad || h_ovf || oarcs > cap)) {
+        cudaFreeAsync(oadj, s);
+        oadj = nullptr;
+        pipelined = false;
+        if (!bad) {
+            // more oriented arcs than m: the scans replaced the counts, so
+            // count again (the keep bits are set again to the same values)
+            k_orient_count<<<wgrid, 256, 0, s>>>(g.off, g.adj, n, 0, n, deg32, full, err, flag, bits);
+            if (n_big)
+                k_orient_count_big<<<bgrid, 1024, 0, s>>>(g.off, g.adj, n, 0, n, deg32, big, n_big, full, err, flag,
+                                                          bits);
+            nl += 1 + (n_big ? 1 : 0);
+        }
+    }
+    if (!bad && !pipelined) {
         cudaMemsetAsync(flag + n, 0, 8, s);
         if ((e = scan_exclusive_i64(flag, n + 1, total, tmp, s)) != cudaSuccess) return e;
         cudaMemcpyAsync(&oarcs, total, 8, cudaMemcpyDeviceToHost, s);
         if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
         if ((e = dev_malloc((void **)&oadj, 4 * (size_t)imax64(oarcs, 1), s)) != cudaSuccess) return e;
-        k_orient_fill<<<wgrid, 256, 0, s>>>(g.off, g.adj, n, flag, bits, enc, oadj);
-        if (n_big) k_orient_fill_big<<<bgrid, 1024, 0, s>>>(g.off, g.adj, flag, bits, enc, big, n_big, oadj);
+        k_orient_fill<<<wgrid, 256, 0, s>>>(g.off, g.adj, 0, n, flag, bits, enc, oadj, oarcs, ovf);
+        if (n_big)
+            k_orient_fill_big<<<bgrid, 1024, 0, s>>>(g.off, g.adj, 0, n, flag, bits, enc, big, n_big, oadj, oarcs, ovf);
     }
     cudaFreeAsync(bits, s);
     cudaFreeAsync(deg32, s);
@@ -703,7 +777,7 @@ cudaError_t launch_copy_h2d(const void *src_dev_view, void *dst, size_t bytes, i
 {
     if (bytes == 0) return cudaSuccess;
     if ((bytes & 3) || ((uintptr_t)src_dev_view & 3) || ((uintptr_t)dst & 3)) return cudaErrorInvalidValue;
-    const int grid = sm_count * 4;
+    const int grid = sm_count;    // one block per SM: the link is saturated and the other SM slots stay free
     const uintptr_t sa = (uintptr_t)src_dev_view, da = (uintptr_t)dst;
     if ((sa & 15) != (da & 15)) {
         k_copy_words<<<grid, 512, 0, s>>>((const uint32_t *)src_dev_view, (uint32_t *)dst, bytes / 4);

@@ -288,6 +288,52 @@ def test_chunked_host_upload(dsg, ctx, path):
         dsg.dsg_upload_csr(ctx, g.n, g.off, adj, 0)
 
 
+def test_chunked_upload_of_asymmetric_lists_without_validation(dsg, ctx, path):
+    """Without DSG_VALIDATE the lists are taken as given, symmetric or not.
+    A host upload in chunks fills the oriented arcs into m slots as the
+    chunks land, which is exact for a symmetric graph; here two arcs have no
+    reverse and both are kept by the orientation, m + 1 oriented arcs in all,
+    so the upload counts and fills again at that size.  The run equals the
+    one on the same arrays uploaded from device memory in one pass."""
+    if path != PATHS["grid"]:
+        pytest.skip("checked once")
+    import torch
+    g = gg.rmat(20, 16, 2)
+    off, adj = g.off.astype(np.int64), g.adj.astype(np.int32)
+    deg = np.diff(off)
+    a = int(np.argmax(deg))
+    nb_a = adj[off[a]:off[a + 1]]
+    x = int(nb_a[np.argmin(deg[nb_a])])             # a's neighbour of least degree
+    others = np.flatnonzero((deg > 0) & (np.arange(g.n) != a) & (np.arange(g.n) != x))
+    b = int(others[np.argmin(deg[others])])         # a vertex of least degree, not next to a
+    assert a not in set(adj[off[b]:off[b + 1]].tolist())
+    lists = [adj[off[u]:off[u + 1]] for u in range(g.n)]
+    lists[a] = lists[a][lists[a] != x]              # x -> a stays, a -> x goes
+    lists[b] = np.sort(np.append(lists[b], a))      # b -> a without a -> b
+    off2 = np.zeros(g.n + 1, np.int64)
+    off2[1:] = np.cumsum([len(l) for l in lists])
+    adj2 = np.concatenate(lists).astype(np.int32)
+    assert off2[-1] == off[-1] and off2[-1] >= 1 << 24
+    T = 3
+    outs = []
+    for src in ("host", "device"):
+        if src == "host":
+            gr = dsg.dsg_upload_csr(ctx, g.n, off2, adj2, 0)
+        else:
+            gr = dsg.dsg_upload_csr(ctx, g.n, torch.from_numpy(off2).cuda(), torch.from_numpy(adj2).cuda(),
+                                    dsg.DSG_SRC_DEVICE)
+        try:
+            loads = np.zeros(g.n, np.int64)
+            trace = np.zeros(3 * T, np.int64)
+            r = dsg.dsg_run(ctx, gr, dsg.DSG_SORTING, T, 0, 1, None, loads, None, trace)
+        finally:
+            dsg.dsg_free_graph(gr)
+        outs.append(((r["best_edges"], r["best_vertices"], r["best_iter"]), loads, trace))
+    assert outs[0][0] == outs[1][0]
+    assert np.array_equal(outs[0][1], outs[1][1])
+    assert np.array_equal(outs[0][2], outs[1][2])
+
+
 def test_graphs_of_one_size_back_to_back(dsg, ctx):
     """Graphs of one size, uploaded and freed one after the other, get device
     memory the previous graph just gave back; the look-back words left there
