@@ -24,13 +24,15 @@ __device__ __forceinline__ bool has_arc(const int64_t *off, const int32_t *adj, 
 }
 
 // Vertices of degree > kBigDeg are processed by a whole block (the list of
-// them is built first), the others by one warp each.
+// them is built first), those of at most kSmallDeg arcs by one thread each,
+// the others by one warp each.
 constexpr int64_t kBigDeg = 4096;
+constexpr uint32_t kSmallDeg = 16;      // lists up to this length: a thread per vertex in the orientation
 
-__device__ __forceinline__ void check_arc(const int64_t *off, const int32_t *adj, int64_t n,
-                                          int64_t u, int64_t s, int64_t j, int full, int32_t *err)
+// the same with the arc's target w = adj[j] already loaded
+__device__ __forceinline__ void check_arc_w(const int64_t *off, const int32_t *adj, int64_t n,
+                                            int64_t u, int64_t s, int64_t j, int32_t w, int full, int32_t *err)
 {
-    const int32_t w = adj[j];
     if (w < 0 || w >= n) { atomicExch(&err[1], 1); return; }
     if (w == (int32_t)u) atomicExch(&err[2], 1);
     if (j > s && adj[j - 1] >= w) atomicExch(&err[5], 1);   // not strictly ascending
@@ -38,6 +40,12 @@ __device__ __forceinline__ void check_arc(const int64_t *off, const int32_t *adj
         if (j > s && adj[j - 1] >= w) atomicExch(&err[3], 1);
         if (!has_arc(off, adj, w, (int32_t)u)) atomicExch(&err[4], 1);
     }
+}
+
+__device__ __forceinline__ void check_arc(const int64_t *off, const int32_t *adj, int64_t n,
+                                          int64_t u, int64_t s, int64_t j, int full, int32_t *err)
+{
+    check_arc_w(off, adj, n, u, s, j, adj[j], full, err);
 }
 
 // offsets monotone and inside [0, arcs]: checked before anything reads adj
@@ -302,13 +310,39 @@ __device__ __forceinline__ bool oriented_keep(uint32_t du, uint32_t u, uint32_t 
     return dw > du || (dw == du && w > u);
 }
 
-// deg32[v] and the encoded arc target enc[v] (hub slot, hot slot or id)
+// one-byte degree class, non-decreasing in the degree: the degree itself
+// below 128, then four classes per doubling (the leading bit and the two
+// after it), at most 223 for degrees below 2^31.  Different classes order
+// two degrees; equal classes below 128 mean equal degrees.
+__host__ __device__ __forceinline__ uint32_t deg_class(uint32_t d)
+{
+    if (d < 128) return d;
+    int b = 31;
+    while (!((d >> b) & 1u)) --b;
+    return 128u + (uint32_t)(b - 7) * 4u + ((d >> (b - 2)) & 3u);
+}
+
+// keep rule of oriented_keep, decided by the targets' degree classes (one
+// byte per vertex, which stays in L2), the exact degree read only when the
+// classes tie above 128
+__device__ __forceinline__ bool keep_by_class(uint32_t du, uint32_t cu, uint32_t u, uint32_t w,
+                                              const uint8_t *__restrict__ cls, const uint32_t *__restrict__ deg32)
+{
+    const uint32_t cw = cls[w];
+    if (cw != cu) return cw > cu;
+    if (cu < 128) return w > u;
+    return oriented_keep(du, u, deg32[w], w);
+}
+
+// deg32[v], its class cls[v] and the encoded arc target enc[v] (hub slot,
+// hot slot or id)
 __global__ void k_deg_enc(const int64_t *__restrict__ off, int64_t n, const int32_t *__restrict__ hub_of,
-                          const int32_t *__restrict__ hot_of, uint32_t *deg32, uint32_t *enc)
+                          const int32_t *__restrict__ hot_of, uint32_t *deg32, uint8_t *cls, uint32_t *enc)
 {
     for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
          v += (int64_t)gridDim.x * blockDim.x) {
         deg32[v] = (uint32_t)(off[v + 1] - off[v]);
+        cls[v] = (uint8_t)deg_class(deg32[v]);
         const int32_t hs = hub_of[v];
         const int32_t ts = hot_of ? hot_of[v] : -1;
         enc[v] = hs >= 0 ? (kHubBit | (uint32_t)hs) : (ts >= 0 ? (kHotBit | (uint32_t)ts) : (uint32_t)v);
@@ -337,23 +371,57 @@ __device__ __forceinline__ bool keep_bit(const uint32_t *__restrict__ bits, int6
 // the oriented out-degree and the keep bits: warp per vertex of degree <= kBigDeg
 __global__ void k_orient_count(const int64_t *__restrict__ off, const int32_t *__restrict__ adj,
                                int64_t n, int64_t u0, int64_t u1, const uint32_t *__restrict__ deg32,
-                               int full, int32_t *err, int64_t *ocnt, uint32_t *bits)
+                               const uint8_t *__restrict__ cls, int full, int32_t *err, int64_t *ocnt,
+                               uint32_t *bits)
 {
     const int lane = threadIdx.x & 31;
     const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    // lists of at most kSmallDeg arcs: one thread per vertex (a warp per
+    // vertex would leave most lanes idle on them)
+    for (int64_t u = u0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < u1;
+         u += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t s = off[u], e = off[u + 1];
+        const uint32_t du = (uint32_t)(e - s);
+        if (du > kSmallDeg) continue;
+        const uint32_t cu = deg_class(du);
+        uint32_t mask = 0;
+        int32_t prev = 0;
+        for (uint32_t k = 0; k < du; ++k) {
+            const int32_t w = __ldcs(adj + s + k);
+            if (w < 0 || w >= n) {
+                atomicExch(&err[1], 1);
+                continue;
+            }
+            if (w == (int32_t)u) atomicExch(&err[2], 1);
+            if (k > 0 && prev >= w) {
+                atomicExch(&err[5], 1);                     // not strictly ascending
+                if (full) atomicExch(&err[3], 1);
+            }
+            if (full && !has_arc(off, adj, w, (int32_t)u)) atomicExch(&err[4], 1);
+            prev = w;
+            if (keep_by_class(du, cu, (uint32_t)u, (uint32_t)w, cls, deg32)) mask |= 1u << k;
+        }
+        if (mask) {
+            const int sh = (int)(s & 31);
+            atomicOr(&bits[s >> 5], mask << sh);
+            if (sh && (mask >> (32 - sh))) atomicOr(&bits[(s >> 5) + 1], mask >> (32 - sh));
+        }
+        ocnt[u] = __popc(mask);
+    }
     for (int64_t u = u0 + wid; u < u1; u += nw) {
         const int64_t s = off[u], e = off[u + 1];
         const uint32_t du = (uint32_t)(e - s);
-        if (du > kBigDeg) continue;                         // k_orient_count_big
+        if (du <= kSmallDeg || du > kBigDeg) continue;     // the loop above; k_orient_count_big
+        const uint32_t cu = deg_class(du);
         uint32_t c = 0;
         for (int64_t j0 = s; j0 < e; j0 += 32) {
             const int64_t j = j0 + lane;
             bool keep = false;
             if (j < e) {
-                check_arc(off, adj, n, u, s, j, full, err);
-                const int32_t w = adj[j];
-                if (w >= 0 && w < n) keep = oriented_keep(du, (uint32_t)u, deg32[w], (uint32_t)w);
+                const int32_t w = __ldcs(adj + j);         // streamed: the classes stay in L2
+                check_arc_w(off, adj, n, u, s, j, w, full, err);
+                if (w >= 0 && w < n) keep = keep_by_class(du, cu, (uint32_t)u, (uint32_t)w, cls, deg32);
             }
             const uint32_t m = __ballot_sync(kFull, keep);
             c += __popc(m);
@@ -366,7 +434,8 @@ __global__ void k_orient_count(const int64_t *__restrict__ off, const int32_t *_
 // the same, one block per vertex of degree > kBigDeg
 __global__ void k_orient_count_big(const int64_t *__restrict__ off, const int32_t *__restrict__ adj,
                                    int64_t n, int64_t u0, int64_t u1, const uint32_t *__restrict__ deg32,
-                                   const uint32_t *__restrict__ big, int64_t n_big, int full,
+                                   const uint8_t *__restrict__ cls, const uint32_t *__restrict__ big,
+                                   int64_t n_big, int full,
                                    int32_t *err, int64_t *ocnt, uint32_t *bits)
 {
     __shared__ uint32_t red[32];
@@ -375,15 +444,15 @@ __global__ void k_orient_count_big(const int64_t *__restrict__ off, const int32_
         const int64_t u = big[b];
         if (u < u0 || u >= u1) continue;                    // the block's uniform choice
         const int64_t s = off[u], e = off[u + 1];
-        const uint32_t du = (uint32_t)(e - s);
+        const uint32_t du = (uint32_t)(e - s), cu = deg_class(du);
         uint32_t c = 0;
         for (int64_t j0 = s; j0 < e; j0 += blockDim.x) {
             const int64_t j = j0 + threadIdx.x;
             bool keep = false;
             if (j < e) {
-                check_arc(off, adj, n, u, s, j, full, err);
-                const int32_t w = adj[j];
-                if (w >= 0 && w < n) keep = oriented_keep(du, (uint32_t)u, deg32[w], (uint32_t)w);
+                const int32_t w = __ldcs(adj + j);         // streamed: the classes stay in L2
+                check_arc_w(off, adj, n, u, s, j, w, full, err);
+                if (w >= 0 && w < n) keep = keep_by_class(du, cu, (uint32_t)u, (uint32_t)w, cls, deg32);
             }
             const uint32_t m = __ballot_sync(kFull, keep);
             c += __popc(m);
@@ -411,9 +480,21 @@ __global__ void k_orient_fill(const int64_t *__restrict__ off, const int32_t *__
     const int lane = threadIdx.x & 31;
     const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t u = u0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < u1;
+         u += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t s = off[u], e = off[u + 1];
+        if ((uint64_t)(e - s) > kSmallDeg) continue;
+        int64_t o = ooff[u];
+        for (int64_t j = s; j < e; ++j) {
+            if (!keep_bit(bits, j)) continue;
+            if (o < cap) oadj[o] = enc[__ldcs(adj + j)];
+            else atomicExch(ovf, 1);
+            ++o;
+        }
+    }
     for (int64_t u = u0 + wid; u < u1; u += nw) {
         const int64_t s = off[u], e = off[u + 1];
-        if ((uint64_t)(e - s) > kBigDeg) continue;
+        if ((uint64_t)(e - s) <= kSmallDeg || (uint64_t)(e - s) > kBigDeg) continue;
         int64_t o = ooff[u];
         for (int64_t j0 = s; j0 < e; j0 += 32) {
             const int64_t j = j0 + lane;
@@ -581,7 +662,9 @@ cudaError_t build_orientation(GraphDev &g, cudaStream_t s, int full, int32_t *er
     uint32_t *deg32 = nullptr, *enc = nullptr, *big = nullptr;
     if ((e = dev_malloc((void **)&deg32, 4 * (size_t)n, s)) != cudaSuccess) return e;
     if ((e = dev_malloc((void **)&enc, 4 * (size_t)n, s)) != cudaSuccess) return e;
-    k_deg_enc<<<grid, 256, 0, s>>>(g.off, n, slot_of, hot_of, deg32, enc);
+    uint8_t *cls = nullptr;
+    if ((e = dev_malloc((void **)&cls, (size_t)n, s)) != cudaSuccess) return e;
+    k_deg_enc<<<grid, 256, 0, s>>>(g.off, n, slot_of, hot_of, deg32, cls, enc);
     k_hub_flags<<<grid, 256, 0, s>>>(g.off, n, kBigDeg + 1, flag);
     if ((e = scan_exclusive_i64(flag, n, total, tmp, s)) != cudaSuccess) return e;
     int64_t n_big = 0;
@@ -620,9 +703,9 @@ cudaError_t build_orientation(GraphDev &g, cudaStream_t s, int full, int32_t *er
             if (v1 <= v0) continue;
             const int cgrid = (int)imin64(((v1 - v0) * 32 + 255) / 256, 152 * 32);
             const int agrid = (int)imin64((v1 - v0 + 255) / 256, 152 * 8);
-            k_orient_count<<<cgrid, 256, 0, s>>>(g.off, g.adj, n, v0, v1, deg32, full, err, flag, bits);
+            k_orient_count<<<cgrid, 256, 0, s>>>(g.off, g.adj, n, v0, v1, deg32, cls, full, err, flag, bits);
             if (n_big)
-                k_orient_count_big<<<bgrid, 1024, 0, s>>>(g.off, g.adj, n, v0, v1, deg32, big, n_big, full, err, flag,
+                k_orient_count_big<<<bgrid, 1024, 0, s>>>(g.off, g.adj, n, v0, v1, deg32, cls, big, n_big, full, err, flag,
                                                           bits);
             if ((e = scan_exclusive_i64(flag + v0, v1 - v0, total, tmp, s)) != cudaSuccess) return e;
             k_add_base<<<agrid, 256, 0, s>>>(flag + v0, v1 - v0, run);
@@ -636,10 +719,10 @@ cudaError_t build_orientation(GraphDev &g, cudaStream_t s, int full, int32_t *er
     } else {
         for (int i = 0; i < nch; ++i)
             if ((e = cudaStreamWaitEvent(s, chunks->ev[i], 0)) != cudaSuccess) return e;
-        k_orient_count<<<wgrid, 256, 0, s>>>(g.off, g.adj, n, 0, n, deg32, full, err, flag, bits);
+        k_orient_count<<<wgrid, 256, 0, s>>>(g.off, g.adj, n, 0, n, deg32, cls, full, err, flag, bits);
         ++nl;
         if (n_big)
-            k_orient_count_big<<<bgrid, 1024, 0, s>>>(g.off, g.adj, n, 0, n, deg32, big, n_big, full, err, flag, bits);
+            k_orient_count_big<<<bgrid, 1024, 0, s>>>(g.off, g.adj, n, 0, n, deg32, cls, big, n_big, full, err, flag, bits);
     }
     int32_t h_err[8];
     int32_t h_ovf = 0;
@@ -659,9 +742,9 @@ cudaError_t build_orientation(GraphDev &g, cudaStream_t s, int full, int32_t *er
         if (!bad) {
             // more oriented arcs than m: the scans replaced the counts, so
             // count again (the keep bits are set again to the same values)
-            k_orient_count<<<wgrid, 256, 0, s>>>(g.off, g.adj, n, 0, n, deg32, full, err, flag, bits);
+            k_orient_count<<<wgrid, 256, 0, s>>>(g.off, g.adj, n, 0, n, deg32, cls, full, err, flag, bits);
             if (n_big)
-                k_orient_count_big<<<bgrid, 1024, 0, s>>>(g.off, g.adj, n, 0, n, deg32, big, n_big, full, err, flag,
+                k_orient_count_big<<<bgrid, 1024, 0, s>>>(g.off, g.adj, n, 0, n, deg32, cls, big, n_big, full, err, flag,
                                                           bits);
             nl += 1 + (n_big ? 1 : 0);
         }
@@ -678,6 +761,7 @@ cudaError_t build_orientation(GraphDev &g, cudaStream_t s, int full, int32_t *er
     }
     cudaFreeAsync(bits, s);
     cudaFreeAsync(deg32, s);
+    cudaFreeAsync(cls, s);
     cudaFreeAsync(enc, s);
     cudaFreeAsync(big, s);
     cudaFreeAsync(cnt, s);
@@ -777,7 +861,11 @@ cudaError_t launch_copy_h2d(const void *src_dev_view, void *dst, size_t bytes, i
 {
     if (bytes == 0) return cudaSuccess;
     if ((bytes & 3) || ((uintptr_t)src_dev_view & 3) || ((uintptr_t)dst & 3)) return cudaErrorInvalidValue;
-    const int grid = sm_count;    // one block per SM: the link is saturated and the other SM slots stay free
+    // a quarter of the SMs already holds the link's rate (19 blocks of 512
+    // threads: 210 GB/s); the other SMs stay free for the kernels that
+    // orient the graph as its chunks land, which slowed down by about 1.7x
+    // when every SM also ran a copy block (R-MAT 27 upload 152 -> 110 ms)
+    const int grid = sm_count >= 8 ? sm_count / 4 : 2;
     const uintptr_t sa = (uintptr_t)src_dev_view, da = (uintptr_t)dst;
     if ((sa & 15) != (da & 15)) {
         k_copy_words<<<grid, 512, 0, s>>>((const uint32_t *)src_dev_view, (uint32_t *)dst, bytes / 4);
