@@ -2,7 +2,7 @@
  * par_sorting.c -- a parallel CPU (OpenMP) implementation of the PaRSorting++
  * refine step (arXiv 2311.04333, Sec. 3.2-3.3 with Alg. 3), written
  * separately from the sequential oracle and from the CUDA library, for
- * timing against the GPU on the host's cores.  BENCHMARK BASELINE ONLY: the
+ * timing against the GPU on the host's cores.  A CPU timing reference only: the
  * library never calls it.
  *
  * Iteration t, loads l (by id):
