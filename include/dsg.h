@@ -138,9 +138,10 @@ const char *dsg_last_error(const dsg_ctx *ctx);
  *   DSG_DEBUG_FAIL_UPLOAD (process-wide, ctx may be NULL): the value-th
  *     host-to-device copy of dsg_upload_csr / dsg_upload_batch from now on
  *     fails and that call returns DSG_ERR_CUDA; 0 turns it off;
- *   DSG_DEBUG_PEEL_BLOCKS (ctx): at most this many blocks in the whole-GPU
- *     PaRGreedy++ round kernel of later runs on ctx (the cap each server slot
- *     sets on its own context; results do not depend on it); 0 = one per SM.
+ *   DSG_DEBUG_PEEL_BLOCKS (ctx): the whole-GPU PaRGreedy++ round kernel of
+ *     later runs on ctx uses at most this many SMs' worth of blocks (two
+ *     blocks per SM; the cap each server slot sets on its own context;
+ *     results do not depend on it); 0 = every SM.
  * The environment variable DSG_FAULT ("alloc:N", "upload:N", or both
  * separated by a comma), read when the library is loaded, sets the two
  * process-wide countdowns the same way.  Returns DSG_ERR_INVALID for an

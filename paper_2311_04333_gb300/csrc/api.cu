@@ -33,7 +33,7 @@ struct dsg_ctx {
     std::vector<Pending> pending;
     int32_t *err_flags = nullptr;    // device scratch for validation
     unsigned long long *red = nullptr;  // device scratch for reductions
-    int peel_max_blocks = 0;         // cap on the PaRGreedy++ grid (0: one block per SM)
+    int peel_max_blocks = 0;         // SMs the PaRGreedy++ grid may use (0: all of them)
     int64_t peel_iters = 0, peel_rounds = 0, peel_work = 0;   // whole-GPU PaRGreedy++ telemetry
     cudaStream_t cap = nullptr;      // private stream that CUDA graphs are captured on
     // host uploads: the adjacency arrives in chunks on its own stream while

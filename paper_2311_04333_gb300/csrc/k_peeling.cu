@@ -19,8 +19,9 @@
 //       in F;
 //   H:  the same for the heavier F vertices, whose arcs are cut into chunks
 //       of 2,048 that all blocks share.
-// Blocks leave as the alive set shrinks (one block per 4,096 alive vertices
-// or 65,536 of their arcs, whichever needs more), down to a single block
+// Blocks of 512 threads, two per SM; they leave as the alive set shrinks
+// (one block per 2,048 alive vertices or 32,768 of their arcs, whichever
+// needs more), down to a single block
 // that rounds with block barriers only.
 // The densest suffix of the (round, id) order then reuses the radix passes
 // of the sorting path with key = round and value = A (Alg. 3, suffix densities).
@@ -33,9 +34,9 @@
 namespace dsg {
 
 constexpr uint32_t kUnpeeled = 0xffffffffu;
-constexpr int kPeelThreads = 1024;
-constexpr uint32_t kAlivePerBlock = 4096;   // blocks: one per this many alive vertices
-constexpr int64_t kArcsPerBlock = 65536;    //   or per this many arcs of alive vertices
+constexpr int kPeelThreads = 512;
+constexpr uint32_t kAlivePerBlock = 2048;   // blocks: one per this many alive vertices
+constexpr int64_t kArcsPerBlock = 32768;    //   or per this many arcs of alive vertices
 constexpr int64_t kLocalDegree = 512;       // F vertices up to this degree: the finding block
 constexpr int64_t kPeelChunk = 2048;        // arcs per work item of the heavier F vertices
 constexpr int kQueueCap = 4096;             // block-local queue of F vertices
@@ -214,7 +215,7 @@ __device__ void drain_queue(PeelSmem &S, const int64_t *__restrict__ off, const 
     __syncthreads();
 }
 
-__global__ void __launch_bounds__(kPeelThreads, 1)
+__global__ void __launch_bounds__(kPeelThreads, 2)
 k_peel(const int64_t *__restrict__ off, const int32_t *__restrict__ adj, int64_t n,
        uint32_t *loads, uint32_t *A, uint32_t *kv, unsigned long long *st, uint32_t *round,
        uint32_t *list0, uint32_t *list1, unsigned long long *heavy, uint64_t p, uint64_t q,
@@ -512,15 +513,15 @@ int peel_run(cudaStream_t s, const GraphDev &g, RunBufs &b, PeelBufs &pb, bool &
     std::call_once(g_peel_once, [] {
         int nb = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_peel, kPeelThreads, 0);
-        g_peel_blocks_per_sm = nb > 0 ? 1 : 0;
+        g_peel_blocks_per_sm = nb >= 2 ? 2 : (nb > 0 ? 1 : 0);
     });
     if (g_peel_blocks_per_sm < 1) {
         err = "the peel kernel cannot be resident";
         return DSG_ERR_CUDA;
     }
-    // blocks: at most max_blocks (one per SM at most), and no more than the
-    // vertices and arcs need
-    const int grid = (int)imin64(imin64(sm_count, max_blocks), peel_blocks((uint64_t)n, (uint64_t)g.arcs));
+    // blocks: the resident blocks of at most max_blocks SMs (two per SM),
+    // and no more than the vertices and arcs need
+    const int grid = (int)imin64(imin64((int64_t)sm_count, max_blocks) * g_peel_blocks_per_sm, peel_blocks((uint64_t)n, (uint64_t)g.arcs));
     const int igrid = (int)imin64((n + 255) / 256, (int64_t)sm_count * 8);
     int nl = 0;
     for (int t = 1; t <= T; ++t) {
@@ -619,14 +620,14 @@ int coreness_run(cudaStream_t s, const GraphDev &g, Control *ctl, int sm_count, 
     std::call_once(g_peel_once, [] {
         int nb = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_peel, kPeelThreads, 0);
-        g_peel_blocks_per_sm = nb > 0 ? 1 : 0;
+        g_peel_blocks_per_sm = nb >= 2 ? 2 : (nb > 0 ? 1 : 0);
     });
     if (g_peel_blocks_per_sm < 1) {
         cudaFreeAsync(mem, s);
         err = "the peel kernel cannot be resident";
         return DSG_ERR_CUDA;
     }
-    const int grid = (int)imin64(sm_count, peel_blocks((uint64_t)n, (uint64_t)g.arcs));
+    const int grid = (int)imin64((int64_t)sm_count * g_peel_blocks_per_sm, peel_blocks((uint64_t)n, (uint64_t)g.arcs));
     const int igrid = (int)imin64((n + 255) / 256, (int64_t)sm_count * 8);
     // a failure status or test knob left by an earlier run does not carry over
     cudaMemsetAsync(&ctl->err, 0, 16, s);
@@ -712,13 +713,13 @@ int kcore_run(cudaStream_t s, const GraphDev &g, Control *ctl, int sm_count, KCo
     std::call_once(g_peel_once, [] {
         int nb = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_peel, kPeelThreads, 0);
-        g_peel_blocks_per_sm = nb > 0 ? 1 : 0;
+        g_peel_blocks_per_sm = nb >= 2 ? 2 : (nb > 0 ? 1 : 0);
     });
     if (g_peel_blocks_per_sm < 1) {
         err = "the peel kernel cannot be resident";
         return DSG_ERR_CUDA;
     }
-    const int grid = (int)imin64(sm_count, peel_blocks((uint64_t)n, (uint64_t)g.arcs));
+    const int grid = (int)imin64((int64_t)sm_count * g_peel_blocks_per_sm, peel_blocks((uint64_t)n, (uint64_t)g.arcs));
     const int igrid = (int)imin64((n + 255) / 256, (int64_t)sm_count * 8);
     // a failure status or test knob left by an earlier run does not carry over
     cudaMemsetAsync(&ctl->err, 0, 16, s);
