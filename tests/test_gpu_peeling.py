@@ -97,9 +97,9 @@ def test_round_telemetry_matches_the_oracle(dsg, ctx):
 
 @pytest.mark.parametrize("blocks", [1, 4, 38])
 def test_capped_grid_matches_oracle(dsg, ctx, blocks):
-    """The round kernel with its grid capped (as each server slot caps it):
-    every block carries a long share of the alive list and long queues of
-    peeled vertices, drained with their arcs laid end to end."""
+    """The round kernel with its grid capped to 1, 4 and 38 SMs' worth of
+    blocks (as each server slot caps it): every block carries a long share
+    of the alive list and long queues of peeled vertices."""
     g = gg.rmat(16, 16, 4)
     dsg.dsg_debug_set(ctx, dsg.DSG_DEBUG_PEEL_BLOCKS, blocks)
     try:
