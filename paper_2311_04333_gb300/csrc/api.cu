@@ -264,30 +264,58 @@ int build_grid(dsg_ctx *ctx, dsg_graph *G, const UploadChunks *chunks)
     int32_t h_err[8];
     const int64_t n = G->g.n;
     int count_launches = 1;
+    // on failure the oriented copy and the schedule are freed again, so that
+    // a later call (the grid path of a compact graph is built on its first
+    // grid run) starts from nothing
+    auto undo = [&](int code) {
+        cudaStream_t s = ctx->stream;
+        if (G->ooff) cudaFreeAsync(G->ooff, s);
+        if (G->oadj) cudaFreeAsync(G->oadj, s);
+        if (G->hub) cudaFreeAsync(G->hub, s);
+        if (G->hot) cudaFreeAsync(G->hot, s);
+        if (G->items) cudaFreeAsync(G->items, s);
+        if (G->heavy_mem) cudaFreeAsync(G->heavy_mem, s);
+        G->ooff = nullptr;
+        G->oadj = nullptr;
+        G->hub = G->hot = nullptr;
+        G->items = nullptr;
+        G->heavy_mem = nullptr;
+        G->g.ooff = nullptr;
+        G->g.oadj = nullptr;
+        G->g.hub_id = G->g.hot_id = nullptr;
+        G->g.items = nullptr;
+        G->g.heavy_acc = G->g.heavy_done = nullptr;
+        return code;
+    };
+    // the count pass only raises flags: clear those another graph's upload
+    // left (an upload's own offsets flag is already checked by now)
+    if ((e = cudaMemsetAsync(ctx->err_flags, 0, 8 * sizeof(int32_t), ctx->stream)) != cudaSuccess)
+        return undo(cuda_fail(ctx, e, "memset"));
     if ((e = build_orientation(G->g, ctx->stream, G->full_check, ctx->err_flags, &G->g.sorted, &G->ooff,
                                &G->oadj, &G->hub, &G->g.n_hub, &G->hot, &G->g.n_hot, chunks,
                                &count_launches)) != cudaSuccess)
-        return cuda_fail(ctx, e, "orientation");
+        return undo(cuda_fail(ctx, e, "orientation"));
     cudaMemcpyAsync(h_err, ctx->err_flags, sizeof(h_err), cudaMemcpyDeviceToHost, ctx->stream);
-    if ((e = cudaStreamSynchronize(ctx->stream)) != cudaSuccess) return cuda_fail(ctx, e, "upload");
+    if ((e = cudaStreamSynchronize(ctx->stream)) != cudaSuccess) return undo(cuda_fail(ctx, e, "upload"));
     for (int i = 0; i < 5; ++i)
-        if (h_err[i]) return fail(ctx, DSG_ERR_INVALID, "invalid graph: %s", kGraphErr[i]);
+        if (h_err[i]) return undo(fail(ctx, DSG_ERR_INVALID, "invalid graph: %s", kGraphErr[i]));
     G->g.ooff = G->ooff;
     G->g.oadj = G->oadj;
     G->g.hub_id = G->hub;
     G->g.hot_id = G->hot;
     void *tmp = nullptr;
     const size_t tmp_bytes = (size_t)schedule_tmp_count(n) * sizeof(int64_t);
-    if ((e = dev_malloc(&tmp, tmp_bytes, ctx->stream)) != cudaSuccess) return cuda_fail(ctx, e, "schedule scratch");
+    if ((e = dev_malloc(&tmp, tmp_bytes, ctx->stream)) != cudaSuccess)
+        return undo(cuda_fail(ctx, e, "schedule scratch"));
     GraphDev og = G->g;
     og.off = G->ooff;
     e = build_schedule(og, tmp, tmp_bytes, ctx->stream, &G->g.n_items, &G->g.n_heavy, &G->items, &G->heavy_mem);
     cudaFreeAsync(tmp, ctx->stream);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "schedule");
+    if (e != cudaSuccess) return undo(cuda_fail(ctx, e, "schedule"));
     G->g.items = G->items;
     G->g.heavy_acc = G->heavy_mem;
     G->g.heavy_done = G->heavy_mem + (G->g.n_heavy > 0 ? G->g.n_heavy : 1);
-    if ((e = cudaStreamSynchronize(ctx->stream)) != cudaSuccess) return cuda_fail(ctx, e, "upload");
+    if ((e = cudaStreamSynchronize(ctx->stream)) != cudaSuccess) return undo(cuda_fail(ctx, e, "upload"));
     ctx->launches[DSG_PHASE_OTHER] += 4 + count_launches;
     G->grid_ready = true;
     return DSG_OK;

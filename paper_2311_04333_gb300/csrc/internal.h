@@ -176,6 +176,55 @@ struct RunBufs {
 cudaError_t dev_malloc(void **p, size_t bytes, cudaStream_t s);
 template <class T>
 inline cudaError_t dev_malloc(T **p, size_t bytes, cudaStream_t s) { return dev_malloc((void **)p, bytes, s); }
+
+// The device buffers one host function allocates on a stream: each is freed
+// (stream-ordered, after the work already queued on that stream) when the
+// holder goes out of scope, unless handed to the caller with keep().  Every
+// return path, including an allocation that fails halfway, so frees what
+// the function took and did not hand over.
+class DevAllocs {
+public:
+    explicit DevAllocs(cudaStream_t s) : s_(s) {}
+    DevAllocs(const DevAllocs &) = delete;
+    DevAllocs &operator=(const DevAllocs &) = delete;
+    ~DevAllocs()
+    {
+        for (int i = 0; i < k_; ++i)
+            if (p_[i]) cudaFreeAsync(p_[i], s_);
+    }
+    template <class T>
+    cudaError_t get(T **out, size_t bytes)
+    {
+        *out = nullptr;
+        if (k_ == kMax) return cudaErrorInvalidValue;   // more buffers than one holder tracks
+        void *q = nullptr;
+        const cudaError_t e = dev_malloc(&q, bytes, s_);
+        if (e != cudaSuccess) return e;
+        p_[k_++] = q;
+        *out = static_cast<T *>(q);
+        return cudaSuccess;
+    }
+    void keep(const void *q)
+    {
+        for (int i = 0; i < k_; ++i)
+            if (p_[i] == q) p_[i] = nullptr;
+    }
+    void release(void *q)
+    {
+        for (int i = 0; i < k_; ++i)
+            if (p_[i] == q) {
+                cudaFreeAsync(q, s_);
+                p_[i] = nullptr;
+            }
+    }
+
+private:
+    static constexpr int kMax = 32;
+    cudaStream_t s_;
+    void *p_[kMax] = {};
+    int k_ = 0;
+};
+
 bool host_alloc_fault();
 bool upload_fault();
 void set_alloc_fault(int64_t nth);

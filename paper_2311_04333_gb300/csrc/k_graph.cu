@@ -612,24 +612,25 @@ cudaError_t build_orientation(GraphDev &g, cudaStream_t s, int full, int32_t *er
     cudaError_t e;
     int nl = 0;
     const int grid = (int)imin64((n + 255) / 256, 152 * 16);
+    DevAllocs A(s);
     // hub threshold: the smallest D >= 2 with #{deg >= D} <= kHubs
     unsigned long long *cnt = nullptr;
     int64_t *tmp = nullptr, *flag = nullptr;
     int32_t *slot_of = nullptr, *slot_of_scratch = nullptr;
     const int64_t ntmp = scan_tmp_count(n + 1);
-    if ((e = dev_malloc((void **)&cnt, 8, s)) != cudaSuccess) return e;
-    if ((e = dev_malloc((void **)&tmp, 8 * (size_t)(ntmp + 4), s)) != cudaSuccess) return e;
-    if ((e = dev_malloc((void **)&flag, 8 * (size_t)(n + 1), s)) != cudaSuccess) return e;
-    if ((e = dev_malloc((void **)&slot_of, 4 * (size_t)n, s)) != cudaSuccess) return e;
-    if ((e = dev_malloc((void **)&slot_of_scratch, 4 * (size_t)n, s)) != cudaSuccess) return e;
+    if ((e = A.get(&cnt, 8)) != cudaSuccess) return e;
+    if ((e = A.get(&tmp, 8 * (size_t)(ntmp + 4))) != cudaSuccess) return e;
+    if ((e = A.get(&flag, 8 * (size_t)(n + 1))) != cudaSuccess) return e;
+    if ((e = A.get(&slot_of, 4 * (size_t)n)) != cudaSuccess) return e;
+    if ((e = A.get(&slot_of_scratch, 4 * (size_t)n)) != cudaSuccess) return e;
     std::vector<unsigned int> dh(kDegHist, 0);
     {
         unsigned int *hd = nullptr;
-        if ((e = dev_malloc((void **)&hd, 4 * (size_t)kDegHist, s)) != cudaSuccess) return e;
+        if ((e = A.get(&hd, 4 * (size_t)kDegHist)) != cudaSuccess) return e;
         cudaMemsetAsync(hd, 0, 4 * (size_t)kDegHist, s);
         k_degree_hist<<<grid, 256, 0, s>>>(g.off, n, hd);
         cudaMemcpyAsync(dh.data(), hd, 4 * (size_t)kDegHist, cudaMemcpyDeviceToHost, s);
-        cudaFreeAsync(hd, s);
+        A.release(hd);
         if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
     }
     int64_t D = 0;
@@ -641,7 +642,7 @@ cudaError_t build_orientation(GraphDev &g, cudaStream_t s, int full, int32_t *er
     cudaMemcpyAsync(&n_hub, total, 8, cudaMemcpyDeviceToHost, s);
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
     uint32_t *hub = nullptr;
-    if ((e = dev_malloc((void **)&hub, 4 * (size_t)imax64(n_hub, 1), s)) != cudaSuccess) return e;
+    if ((e = A.get(&hub, 4 * (size_t)imax64(n_hub, 1))) != cudaSuccess) return e;
     k_hub_slots<<<grid, 256, 0, s>>>(g.off, n, D, flag, slot_of, hub);
     // hot tier (only when plain ids stay below kHotBit)
     int32_t *hot_of = nullptr;
@@ -650,32 +651,32 @@ cudaError_t build_orientation(GraphDev &g, cudaStream_t s, int full, int32_t *er
     if (n < (int64_t)kHotBit && kHot > 0) {
         int64_t Dh = 0;
         if ((e = degree_threshold(g, kHot, dh, cnt, grid, s, &Dh)) != cudaSuccess) return e;
-        if ((e = dev_malloc((void **)&hot_of, 4 * (size_t)n, s)) != cudaSuccess) return e;
+        if ((e = A.get(&hot_of, 4 * (size_t)n)) != cudaSuccess) return e;
         k_hub_flags<<<grid, 256, 0, s>>>(g.off, n, Dh, flag);
         if ((e = scan_exclusive_i64(flag, n, total, tmp, s)) != cudaSuccess) return e;
         cudaMemcpyAsync(&n_hot, total, 8, cudaMemcpyDeviceToHost, s);
         if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
-        if ((e = dev_malloc((void **)&hot, 4 * (size_t)imax64(n_hot, 1), s)) != cudaSuccess) return e;
+        if ((e = A.get(&hot, 4 * (size_t)imax64(n_hot, 1))) != cudaSuccess) return e;
         k_hub_slots<<<grid, 256, 0, s>>>(g.off, n, Dh, flag, hot_of, hot);
     }
     // 32-bit degrees and encoded targets; list of vertices of degree > kBigDeg
     uint32_t *deg32 = nullptr, *enc = nullptr, *big = nullptr;
-    if ((e = dev_malloc((void **)&deg32, 4 * (size_t)n, s)) != cudaSuccess) return e;
-    if ((e = dev_malloc((void **)&enc, 4 * (size_t)n, s)) != cudaSuccess) return e;
+    if ((e = A.get(&deg32, 4 * (size_t)n)) != cudaSuccess) return e;
+    if ((e = A.get(&enc, 4 * (size_t)n)) != cudaSuccess) return e;
     uint8_t *cls = nullptr;
-    if ((e = dev_malloc((void **)&cls, (size_t)n, s)) != cudaSuccess) return e;
+    if ((e = A.get(&cls, (size_t)n)) != cudaSuccess) return e;
     k_deg_enc<<<grid, 256, 0, s>>>(g.off, n, slot_of, hot_of, deg32, cls, enc);
     k_hub_flags<<<grid, 256, 0, s>>>(g.off, n, kBigDeg + 1, flag);
     if ((e = scan_exclusive_i64(flag, n, total, tmp, s)) != cudaSuccess) return e;
     int64_t n_big = 0;
     cudaMemcpyAsync(&n_big, total, 8, cudaMemcpyDeviceToHost, s);
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
-    if ((e = dev_malloc((void **)&big, 4 * (size_t)imax64(n_big, 1), s)) != cudaSuccess) return e;
+    if ((e = A.get(&big, 4 * (size_t)imax64(n_big, 1))) != cudaSuccess) return e;
     k_hub_slots<<<grid, 256, 0, s>>>(g.off, n, kBigDeg + 1, flag, slot_of_scratch, big);
     // keep bits of the arcs, set by the count pass and read by the fill pass
     uint32_t *bits = nullptr;
     const size_t nbits_words = (size_t)((g.arcs + 31) / 32) + 1;
-    if ((e = dev_malloc((void **)&bits, 4 * nbits_words, s)) != cudaSuccess) return e;
+    if ((e = A.get(&bits, 4 * nbits_words)) != cudaSuccess) return e;
     cudaMemsetAsync(bits, 0, 4 * nbits_words, s);
     // validation fused with the oriented out-degrees
     const int wgrid = (int)imin64((n * 32 + 255) / 256, 152 * 32);
@@ -694,7 +695,7 @@ cudaError_t build_orientation(GraphDev &g, cudaStream_t s, int full, int32_t *er
         // oadj gets m entries, exactly the oriented arcs of a symmetric graph;
         // one that needs more (asymmetric input, accepted without
         // DSG_VALIDATE) is counted and filled again below at its own size
-        if ((e = dev_malloc((void **)&oadj, 4 * (size_t)imax64(cap, 1), s)) != cudaSuccess) return e;
+        if ((e = A.get(&oadj, 4 * (size_t)imax64(cap, 1))) != cudaSuccess) return e;
         cudaMemsetAsync(run, 0, 16, s);                             // run and ovf
         pipelined = true;
         for (int i = 0; i < nch; ++i) {
@@ -736,7 +737,7 @@ cudaError_t build_orientation(GraphDev &g, cudaStream_t s, int full, int32_t *er
     for (int i = 0; i < 5; ++i) bad |= h_err[i] != 0;
     *sorted_out = h_err[5] ? 0 : 1;
     if (pipelined && (bad || h_ovf || oarcs > cap)) {
-        cudaFreeAsync(oadj, s);
+        A.release(oadj);
         oadj = nullptr;
         pipelined = false;
         if (!bad) {
@@ -754,21 +755,17 @@ cudaError_t build_orientation(GraphDev &g, cudaStream_t s, int full, int32_t *er
         if ((e = scan_exclusive_i64(flag, n + 1, total, tmp, s)) != cudaSuccess) return e;
         cudaMemcpyAsync(&oarcs, total, 8, cudaMemcpyDeviceToHost, s);
         if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
-        if ((e = dev_malloc((void **)&oadj, 4 * (size_t)imax64(oarcs, 1), s)) != cudaSuccess) return e;
+        if ((e = A.get(&oadj, 4 * (size_t)imax64(oarcs, 1))) != cudaSuccess) return e;
         k_orient_fill<<<wgrid, 256, 0, s>>>(g.off, g.adj, 0, n, flag, bits, enc, oadj, oarcs, ovf);
         if (n_big)
             k_orient_fill_big<<<bgrid, 1024, 0, s>>>(g.off, g.adj, 0, n, flag, bits, enc, big, n_big, oadj, oarcs, ovf);
     }
-    cudaFreeAsync(bits, s);
-    cudaFreeAsync(deg32, s);
-    cudaFreeAsync(cls, s);
-    cudaFreeAsync(enc, s);
-    cudaFreeAsync(big, s);
-    cudaFreeAsync(cnt, s);
-    cudaFreeAsync(tmp, s);
-    cudaFreeAsync(slot_of, s);
-    cudaFreeAsync(slot_of_scratch, s);
-    if (hot_of) cudaFreeAsync(hot_of, s);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    // the outputs go to the caller; A frees the rest (stream-ordered)
+    A.keep(flag);
+    A.keep(oadj);
+    A.keep(hub);
+    A.keep(hot);
     *ooff_out = flag;         // n + 1 exclusive prefix sums = oriented offsets
     *oadj_out = oadj;
     *hub_out = hub;
@@ -776,7 +773,7 @@ cudaError_t build_orientation(GraphDev &g, cudaStream_t s, int full, int32_t *er
     *hot_out = hot;
     *n_hot_out = n_hot;
     if (launches) *launches = nl;
-    return cudaGetLastError();
+    return cudaSuccess;
 }
 
 // ============================================================ reductions

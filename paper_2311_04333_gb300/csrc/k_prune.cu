@@ -171,8 +171,9 @@ cudaError_t degree_core_bound(cudaStream_t s, const GraphDev &g, int32_t *deg, i
 {
     const int64_t n = g.n;
     cudaError_t e;
+    DevAllocs A(s);
     unsigned long long *h = nullptr;
-    if ((e = dev_malloc((void **)&h, 64 * 8, s)) != cudaSuccess) return e;
+    if ((e = A.get(&h, 64 * 8)) != cudaSuccess) return e;
     cudaMemsetAsync(h, 0, 64 * 8, s);
     const int grid = (int)imin64((n + 255) / 256, 152 * 16);
     const int wgrid = (int)imin64((n * 32 + 255) / 256, 152 * 32);
@@ -182,7 +183,6 @@ cudaError_t degree_core_bound(cudaStream_t s, const GraphDev &g, int32_t *deg, i
     unsigned long long hh[64];
     cudaMemcpyAsync(hh, h, sizeof hh, cudaMemcpyDeviceToHost, s);
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
-    cudaFreeAsync(h, s);
     // densest of the subgraphs G[deg >= 2^j]: a lower bound on rho*
     int64_t be = 0, bv = 1;
     unsigned long long V = 0, E = 0;
@@ -204,10 +204,11 @@ cudaError_t extract_core(cudaStream_t s, int64_t n, const int64_t *off, const in
                          bool key_local)
 {
     cudaError_t e;
+    DevAllocs A(s);
     int64_t *pos = nullptr, *tmp = nullptr;
     const int64_t ntmp = scan_tmp_count(n + 1) + 2;
-    if ((e = dev_malloc((void **)&pos, 8 * (size_t)(n + 1), s)) != cudaSuccess) return e;
-    if ((e = dev_malloc((void **)&tmp, 8 * (size_t)ntmp, s)) != cudaSuccess) return e;
+    if ((e = A.get(&pos, 8 * (size_t)(n + 1))) != cudaSuccess) return e;
+    if ((e = A.get(&tmp, 8 * (size_t)ntmp)) != cudaSuccess) return e;
     int64_t *total = tmp + ntmp - 1;
     const int grid = (int)imin64((n + 256) / 256, 152 * 16);
     const int wgrid = (int)imin64((n * 32 + 255) / 256, 152 * 32);
@@ -218,9 +219,9 @@ cudaError_t extract_core(cudaStream_t s, int64_t n, const int64_t *off, const in
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
     int64_t *noff = nullptr, *nloads = nullptr;
     int32_t *nold = nullptr, *nadj = nullptr;
-    if ((e = dev_malloc((void **)&noff, 8 * (size_t)(nn + 1), s)) != cudaSuccess ||
-        (e = dev_malloc((void **)&nold, 4 * (size_t)imax64(nn, 1), s)) != cudaSuccess ||
-        (e = dev_malloc((void **)&nloads, 8 * (size_t)imax64(nn, 1), s)) != cudaSuccess)
+    if ((e = A.get(&noff, 8 * (size_t)(nn + 1))) != cudaSuccess ||
+        (e = A.get(&nold, 4 * (size_t)imax64(nn, 1))) != cudaSuccess ||
+        (e = A.get(&nloads, 8 * (size_t)imax64(nn, 1))) != cudaSuccess)
         return e;
     cudaMemsetAsync(noff, 0, 8 * (size_t)(nn + 1), s);
     k_ext_deg<<<wgrid, 256, 0, s>>>(off, adj, n, pos, noff);
@@ -228,18 +229,22 @@ cudaError_t extract_core(cudaStream_t s, int64_t n, const int64_t *off, const in
     int64_t arcs = 0;
     cudaMemcpyAsync(&arcs, total, 8, cudaMemcpyDeviceToHost, s);
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
-    if ((e = dev_malloc((void **)&nadj, 4 * (size_t)imax64(arcs, 1), s)) != cudaSuccess) return e;
+    if ((e = A.get(&nadj, 4 * (size_t)imax64(arcs, 1))) != cudaSuccess) return e;
     k_ext_fill<<<wgrid, 256, 0, s>>>(off, adj, n, pos, noff, nadj);
     k_ext_map<<<grid, 256, 0, s>>>(n, pos, old_of, loads, nold, nloads, frozen);
-    cudaFreeAsync(pos, s);
-    cudaFreeAsync(tmp, s);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    // the core's arrays go to the caller; A frees pos and tmp (stream-ordered)
+    A.keep(noff);
+    A.keep(nadj);
+    A.keep(nold);
+    A.keep(nloads);
     out->n = nn;
     out->arcs = arcs;
     out->off = noff;
     out->adj = nadj;
     out->old_of = nold;
     out->loads = nloads;
-    return cudaGetLastError();
+    return cudaSuccess;
 }
 
 void free_core(CoreGraph &c, cudaStream_t s)

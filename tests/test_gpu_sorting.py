@@ -145,6 +145,29 @@ def test_device_buffers(dsg, ctx, path):
     assert np.array_equal(trace.cpu().numpy().reshape(T, 3), o.trace)
 
 
+def test_grid_path_of_a_compact_graph_after_an_invalid_upload(dsg, ctx):
+    """A compact graph builds its degree-oriented copy on its first grid run,
+    with the adjacency checks of that copy's count pass; flags that an
+    invalid graph's upload raised in between belong to that graph alone."""
+    g = gg.er_m(2_000, 6, 24)
+    gr = dsg.dsg_upload_csr(ctx, g.n, g.off, g.adj)
+    try:
+        with pytest.raises(dsg.DsgError, match="self-loop"):
+            dsg.dsg_upload_csr(ctx, 2, np.array([0, 2, 2], np.int64), np.array([0, 1], np.int32), 0)
+        T = 3
+        loads = np.zeros(g.n, np.int64)
+        bset = np.zeros(g.n, np.int32)
+        trace = np.zeros(3 * T, np.int64)
+        r = dsg.dsg_run(ctx, gr, dsg.DSG_SORTING, T, 0, 1, None, loads, bset, trace, dsg.DSG_PATH_GRID)
+    finally:
+        dsg.dsg_free_graph(gr)
+    o = orc.run(g, orc.SORTING, T)
+    assert np.array_equal(loads, o.loads)
+    assert (r["best_edges"], r["best_vertices"], r["best_iter"]) == (o.best_edges, o.best_vertices, o.best_iter)
+    assert np.array_equal(bset[: r["best_set_size"]].astype(np.int64), o.best_set)
+    assert np.array_equal(trace.reshape(T, 3), o.trace)
+
+
 def test_invalid_inputs(dsg, ctx, path):
     ok = gg.complete(4)
     with pytest.raises(dsg.DsgError, match="INVALID"):
