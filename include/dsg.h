@@ -377,7 +377,8 @@ int dsg_server_submit(dsg_server *s, int64_t n, const int64_t *offsets, const in
 /* Wait up to timeout_ms (< 0: forever) for a request; DSG_ERR_BUSY if it is
  * not finished in time.  On return the result is filled (loads[n] and
  * best_set[best_set_size] are copied if the pointers are not NULL) and the
- * ticket is released. */
+ * ticket is released.  Only one waiter gets a ticket's result: a ticket that
+ * is unknown, or that another thread released first, gives DSG_ERR_INVALID. */
 int dsg_server_wait(dsg_server *s, uint64_t ticket, int64_t timeout_ms, dsg_server_result *out,
                     int64_t *loads, int32_t *best_set);
 

@@ -19,9 +19,10 @@
 // time, so a bad request fails alone.
 //
 // PaRGreedy++ on a large graph is one cooperative launch whose blocks meet
-// at grid-wide barriers; each such block needs an SM of its own.  Each slot
-// caps that grid at (SM count / slots) blocks, so the grids of all slots fit
-// the GPU together and their barriers never wait on one another's residency.
+// at grid-wide barriers, so all its blocks must be resident at once.  Each
+// slot caps that grid at (SM count / slots) SMs' worth of blocks, so the
+// grids of all slots fit the GPU together and their barriers never wait on
+// one another's residency.
 // The rounds are latency-bound, so the cap costs little per request and the
 // slots' peels overlap.
 #include <chrono>
@@ -331,14 +332,21 @@ int dsg_server_wait(dsg_server *s, uint64_t ticket, int64_t timeout_ms, dsg_serv
     Request *r = nullptr;
     {
         std::unique_lock<std::mutex> lk(s->mu);
+        if (s->reqs.find(ticket) == s->reqs.end()) return DSG_ERR_INVALID;
+        // looked up again at every wake-up: another thread waiting on the
+        // same ticket may have released it in the meantime
+        auto ready = [&] {
+            auto f = s->reqs.find(ticket);
+            return f == s->reqs.end() || f->second->done;
+        };
+        if (timeout_ms < 0) s->cv_done.wait(lk, ready);
+        else if (!s->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), ready)) return DSG_ERR_BUSY;
         auto it = s->reqs.find(ticket);
         if (it == s->reqs.end()) return DSG_ERR_INVALID;
         r = it->second;
-        auto ready = [&] { return r->done; };
-        if (timeout_ms < 0) s->cv_done.wait(lk, ready);
-        else if (!s->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), ready)) return DSG_ERR_BUSY;
         s->reqs.erase(it);
     }
+    s->cv_done.notify_all();      // other waiters on this ticket see it released
     out->status = r->status;
     out->best_iter = r->res.best_iter;
     out->best_edges = r->res.best_edges;
