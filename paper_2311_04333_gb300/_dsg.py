@@ -121,6 +121,24 @@ def _ptr(x, dtype) -> tuple[int | None, bool]:
     return x.ctypes.data, False
 
 
+def _count(x) -> int:
+    return int(x.numel()) if _is_torch(x) else int(x.size)
+
+
+def _need(x, count: int, what: str) -> None:
+    """The C call reads or writes `count` entries of x: refuse a smaller
+    buffer here rather than let the library run past its end."""
+    if x is not None and _count(x) < count:
+        raise ValueError(f"{what} holds {_count(x)} entries; the call uses {count}")
+
+
+def _graph_n(graph) -> int | None:
+    """Vertex count of an uploaded graph (None for a handle the library
+    rejects; the call itself then reports that)."""
+    n = ctypes.c_int64()
+    return n.value if LIB.dsg_graph_info(graph, ctypes.byref(n), None, None) == DSG_OK else None
+
+
 def _check(ctx, rc: int) -> None:
     if rc != DSG_OK:
         raise DsgError(rc, LIB.dsg_last_error(ctx).decode())
@@ -158,6 +176,9 @@ def dsg_debug_set(ctx, knob: int, value: int) -> None:
 def dsg_upload_csr(ctx, n: int, offsets, adj, flags: int = 0):
     po, do = _ptr(offsets, np.int64)
     pa, da = _ptr(adj, np.int32)
+    _need(offsets, max(int(n), 0) + 1, "offsets")
+    if not do and n >= 0:
+        _need(adj, int(offsets[n]), "adj")
     if do != da and pa is not None and int(offsets[-1]) > 0:
         raise ValueError("offsets and adj must both live on the host or both on the device")
     if do:
@@ -175,6 +196,15 @@ def dsg_graph_info(graph) -> tuple[int, int, int]:
     return n.value, m.value, d.value
 
 
+def _need_run_buffers(graph, T, loads, best_set, trace, init_loads=None) -> None:
+    n = _graph_n(graph)
+    if n is not None:
+        _need(loads, n, "loads")
+        _need(best_set, n, "best_set")
+        _need(init_loads, n, "init_loads")
+    _need(trace, 3 * max(int(T), 0), "trace")
+
+
 def dsg_run(ctx, graph, variant: int, T: int, eps_num: int = 0, eps_den: int = 1,
             init_loads=None, loads=None, best_set=None, trace=None, path: int = 0) -> dict:
     """Run T iterations.  `loads` (int64[n]), `best_set` (int32[n]) and
@@ -186,6 +216,7 @@ def dsg_run(ctx, graph, variant: int, T: int, eps_num: int = 0, eps_den: int = 1
     ps, ds = _ptr(best_set, np.int32)
     pt, dt = _ptr(trace, np.int64)
     pi, di = _ptr(init_loads, np.int64)
+    _need_run_buffers(graph, T, loads, best_set, trace, init_loads)
     dev = {d for p, d in ((pl, dl), (ps, ds), (pt, dt)) if p is not None}
     if len(dev) > 1:
         raise ValueError("output buffers must all be host or all device")
@@ -204,6 +235,9 @@ def dsg_coreness(ctx, graph, core=None) -> tuple:
         LIB.dsg_graph_info(graph, ctypes.byref(n), None, None)
         core = np.zeros(n.value, dtype=np.int32)
     pc, dc = _ptr(core, np.int32)
+    n = _graph_n(graph)
+    if n is not None:
+        _need(core, n, "core")
     km = ctypes.c_int64()
     _check(ctx, LIB.dsg_coreness(graph, pc, ctypes.byref(km), DSG_DST_DEVICE if dc else 0))
     return core, km.value
@@ -217,6 +251,9 @@ def dsg_apx_coreness(ctx, graph, c=(3, 2), core=None) -> tuple:
         LIB.dsg_graph_info(graph, ctypes.byref(n), None, None)
         core = np.zeros(n.value, dtype=np.int32)
     pc, dc = _ptr(core, np.int32)
+    n = _graph_n(graph)
+    if n is not None:
+        _need(core, n, "core")
     km = ctypes.c_int64()
     _check(ctx, LIB.dsg_apx_coreness(graph, c[0], c[1], pc, ctypes.byref(km), DSG_DST_DEVICE if dc else 0))
     return core, km.value
@@ -233,6 +270,7 @@ def dsg_run_pruned(ctx, graph, variant: int, T: int, eps_num: int = 0, eps_den: 
     pl, dl = _ptr(loads, np.int64)
     ps, ds = _ptr(best_set, np.int32)
     pt, dt = _ptr(trace, np.int64)
+    _need_run_buffers(graph, T, loads, best_set, trace)
     dev = {d for p, d in ((pl, dl), (ps, ds), (pt, dt)) if p is not None}
     if len(dev) > 1:
         raise ValueError("output buffers must all be host or all device")
@@ -340,6 +378,14 @@ def dsg_run_batch(ctx, batch, variant: int, T, threads_per_graph: int = 0, best=
     pl, dl = _ptr(loads, np.int64)
     ps, ds = _ptr(sets, np.int32)
     pt, dt = _ptr(trace, np.int64)
+    Gb, N = ctypes.c_int32(), ctypes.c_int64()
+    if LIB.dsg_batch_info(batch, ctypes.byref(Gb), ctypes.byref(N), None) == DSG_OK:
+        G = Gb.value
+        _need(T, G, "T")
+        _need(best, 4 * G, "best")
+        _need(loads, N.value, "loads")
+        _need(sets, N.value, "sets")
+        _need(trace, 3 * G * max(int(T[:G].max()), 0), "trace")
     dev = {d for p, d in ((pb, db), (pl, dl), (ps, ds), (pt, dt)) if p is not None}
     if len(dev) > 1:
         raise ValueError("output buffers must all be host or all device")
@@ -373,6 +419,9 @@ def dsg_server_submit(server, n: int, offsets, adj, variant: int, T: int, eps_nu
                       eps_den: int = 1) -> int:
     po, _ = _ptr(offsets, np.int64)
     pa, _ = _ptr(adj, np.int32)
+    _need(offsets, max(int(n), 0) + 1, "offsets")
+    if n >= 0:
+        _need(adj, int(offsets[n]), "adj")
     t = ctypes.c_uint64(0)
     rc = LIB.dsg_server_submit(server, n, po, pa, variant, T, eps_num, eps_den, ctypes.byref(t))
     if rc != DSG_OK:
