@@ -1,4 +1,5 @@
-"""Host-side logic of the batch autotuner and the serving workload pool,
+"""Host-side logic of the batch autotuner, the serving workload pool and the
+Poisson arrival driver,
 with the library calls replaced by fakes (CPU only)."""
 import json
 import time
@@ -93,3 +94,42 @@ def test_request_pool_is_seeded_and_follows_the_recipe():
         assert 16 <= g.n and 100 <= g.m <= 4e5          # log-uniform targets in [1e3, 2e5]
         deg = np.diff(g.off)
         assert deg.min() >= 1                           # generators drop isolated vertices
+
+
+def test_poisson_driver_counts_latency_queueing_and_occupancy(monkeypatch):
+    """The serving benchmark's driver against a fake server that finishes
+    every request 10 ms after its submission (2 ms queued, 8 ms running) on
+    one of three workers: the arrival count follows the rate, the statistics
+    cover the requests after the warm-up only, and each worker's occupancy is
+    the union of its requests' run intervals over the measured span."""
+    from paper_2311_04333_gb300 import _dsg, serve
+    import graphgen as gg
+    sub = {}
+
+    def fake_submit(server, n, off, adj, variant, T, p, q):
+        tk = len(sub) + 1
+        sub[tk] = (time.perf_counter(), n)
+        return tk
+
+    def fake_wait(server, tk, timeout_ms=-1, loads=None, best_set=None):
+        t, n = sub[tk]
+        if time.perf_counter() - t < 0.010:
+            return None
+        return {"status": 0, "latency_ms": 10.0, "queue_ms": 2.0, "run_ms": 8.0, "slot": tk % 3, "n": n}
+
+    monkeypatch.setattr(_dsg, "dsg_server_submit", fake_submit)
+    monkeypatch.setattr(_dsg, "dsg_server_wait", fake_wait)
+    pool = [gg.er_m(100, 4, s) for s in range(4)]
+    rate, seconds, warmup = 300.0, 0.6, 0.2
+    r = serve.poisson_run(None, pool, rate, seconds, warmup, seed=3)
+    # Poisson count over 0.6 s at 300/s: mean 180, standard deviation about 13
+    assert 180 - 6 * 14 <= r["requests"] <= 180 + 6 * 14
+    assert len(sub) > r["requests"]                  # the warm-up's requests are left out
+    assert r["all_ok"] and r["p50_ms"] == 10.0 and r["p99_ms"] == 10.0 and r["mean_queue_ms"] == 2.0
+    span = r["submit_span_s"] + r["drain_s"] - warmup
+    assert r["throughput_req_s"] == pytest.approx(r["requests"] / span, rel=0.05)
+    occ = r["worker_occupancy"]
+    assert set(occ) == {0, 1, 2}
+    for slot in occ:
+        # a third of the arrivals, 8 ms each, overlaps merged: at most 8 ms x rate / 3 per second
+        assert 0.0 < occ[slot] <= min(1.0, 0.008 * rate / 3 * 1.6)
