@@ -1,6 +1,5 @@
 """Host-side logic of the batch autotuner, the serving workload pool and the
-Poisson arrival driver,
-with the library calls replaced by fakes (CPU only)."""
+Poisson arrival driver, with the library calls replaced by fakes (CPU only)."""
 import json
 import time
 
