@@ -45,3 +45,57 @@ def test_product_path_does_not_import_oracle():
                 src = open(os.path.join(dirpath, f)).read()
                 assert not re.search(r"^\s*(import|from)\s+oracle\b", src, re.M), f
                 assert "oracle.c" not in src and "liboracle" not in src, f
+
+
+def test_null_handles_and_bad_sizes_are_rejected_before_any_device_work():
+    """Every entry point checks its handles and sizes first: NULL contexts,
+    graphs, batches and servers, and out-of-range sizes, give DSG_ERR_INVALID
+    (the void calls return) without touching a device, so this runs on the
+    CPU.  The argument types are the binding's."""
+    from paper_2311_04333_gb300 import _dsg
+    L, BAD = _dsg.LIB, _dsg.DSG_ERR_INVALID
+    res, info = _dsg.dsg_result(), _dsg.dsg_prune_info()
+    bres, sres = _dsg.dsg_batch_result(), _dsg.dsg_server_result()
+    out, km, tk = ctypes.c_void_p(), ctypes.c_int64(), ctypes.c_uint64()
+    one = (ctypes.c_int64 * 2)(0, 0)
+    buf = (ctypes.c_int32 * 8)()
+    codes = {
+        "create(out=NULL)": L.dsg_create(0, None, None),
+        "upload_csr(ctx=NULL)": L.dsg_upload_csr(None, 1, one, None, 0, ctypes.byref(out)),
+        "graph_info(NULL)": L.dsg_graph_info(None, None, None, None),
+        "run(NULL)": L.dsg_run(None, 0, 1, 0, 1, None, ctypes.byref(res)),
+        "coreness(NULL)": L.dsg_coreness(None, buf, ctypes.byref(km), 0),
+        "apx_coreness(NULL)": L.dsg_apx_coreness(None, 3, 2, buf, ctypes.byref(km), 0),
+        "run_pruned(NULL)": L.dsg_run_pruned(None, 0, 1, 0, 1, ctypes.byref(res), ctypes.byref(info)),
+        "run_pruned_apx(NULL)": L.dsg_run_pruned_apx(None, 0, 1, 0, 1, 3, 2, ctypes.byref(res), ctypes.byref(info)),
+        "run_pruned_apx_exact(NULL)": L.dsg_run_pruned_apx_exact(None, 0, 1, 0, 1, 3, 2, ctypes.byref(res),
+                                                                 ctypes.byref(info)),
+        "set_profiling(NULL)": L.dsg_set_profiling(None, 1),
+        "get_stats(NULL)": L.dsg_get_stats(None, None, None, None, 0),
+        "get_peel_stats(NULL)": L.dsg_get_peel_stats(None, None, None, None, 0),
+        "upload_batch(ctx=NULL)": L.dsg_upload_batch(None, 1, one, None, None, 0, ctypes.byref(out)),
+        "batch_info(NULL)": L.dsg_batch_info(None, None, None, None),
+        "run_batch(NULL)": L.dsg_run_batch(None, 0, None, None, None, 0, ctypes.byref(bres)),
+        "set_batch_tuning(NULL)": L.dsg_set_batch_tuning(None, 0, 0),
+        "server_create(slots=0)": L.dsg_server_create(0, 0, 0, ctypes.byref(out)),
+        "server_create(budget<0)": L.dsg_server_create(0, 2, -1, ctypes.byref(out)),
+        "server_submit(NULL)": L.dsg_server_submit(None, 1, one, None, 0, 1, 0, 1, ctypes.byref(tk)),
+        "server_wait(NULL)": L.dsg_server_wait(None, 1, 0, ctypes.byref(sres), None, None),
+        "server_stats(NULL)": L.dsg_server_stats(None, None, None, None, None, None),
+        "debug_set(spin limit, ctx=NULL)": L.dsg_debug_set(None, _dsg.DSG_DEBUG_SPIN_LIMIT, 10),
+        "debug_set(unknown knob)": L.dsg_debug_set(None, 99, 0),
+        "debug_set(alloc countdown < 0)": L.dsg_debug_set(None, _dsg.DSG_DEBUG_FAIL_ALLOC, -1),
+        "noalloc(n=0)": L.dsg_densest_suffix_noalloc(buf, buf, 0, 0, one, None),
+        "noalloc(n too large)": L.dsg_densest_suffix_noalloc(buf, buf, _dsg.DSG_NOALLOC_MAX_VERTICES + 1, 0, one,
+                                                             None),
+        "noalloc(m >= 2^48)": L.dsg_densest_suffix_noalloc(buf, buf, 4, 1 << 48, one, None),
+        "noalloc(NULL loads)": L.dsg_densest_suffix_noalloc(None, buf, 4, 0, one, None),
+    }
+    wrong = {k: v for k, v in codes.items() if v != BAD}
+    assert not wrong, wrong
+    assert out.value is None
+    L.dsg_destroy(None)
+    L.dsg_free_graph(None)
+    L.dsg_free_batch(None)
+    L.dsg_server_destroy(None)
+    assert L.dsg_last_error(None) == b"no context"
