@@ -99,3 +99,29 @@ def test_null_handles_and_bad_sizes_are_rejected_before_any_device_work():
     L.dsg_free_batch(None)
     L.dsg_server_destroy(None)
     assert L.dsg_last_error(None) == b"no context"
+
+
+def test_header_is_plain_c_and_a_c_program_links_against_the_library(tmp_path):
+    """include/dsg.h compiles as C99 with every warning an error, and a C
+    program built against it links with libdsg.so and calls entry points
+    that need no device."""
+    import subprocess
+    import paper_2311_04333_gb300 as dsg
+    src = tmp_path / "use_dsg.c"
+    src.write_text(
+        "#include <stdio.h>\n#include \"dsg.h\"\n"
+        "int main(void) {\n"
+        "    int64_t n = -1;\n"
+        "    dsg_ctx *ctx = 0;\n"
+        "    if (dsg_graph_info(0, &n, 0, 0) != DSG_ERR_INVALID || n != -1) return 1;\n"
+        "    if (dsg_create(0, 0, 0) != DSG_ERR_INVALID) return 2;\n"
+        "    (void)ctx;\n"
+        "    printf(\"%s\\n\", dsg_last_error(0));\n"
+        "    return 0;\n"
+        "}\n")
+    exe = tmp_path / "use_dsg"
+    lib = dsg.LIB_PATH
+    subprocess.run(["gcc", "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I", os.path.join(ROOT, "include"),
+                    str(src), "-o", str(exe), lib, "-Wl,-rpath," + os.path.dirname(lib)], check=True)
+    run = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
+    assert run.returncode == 0 and run.stdout.strip() == "no context", (run.returncode, run.stdout, run.stderr)
