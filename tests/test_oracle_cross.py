@@ -108,7 +108,8 @@ def _cases():
 
 @pytest.mark.parametrize("ci", range(6))
 @pytest.mark.parametrize("variant,p,q", [(orc.SORTING, 0, 1), (orc.PEELING, 0, 1), (orc.PEELING, 1, 10),
-                                         (orc.PEELING, 1, 2), (orc.GREEDY, 0, 1)])
+                                         (orc.PEELING, 1, 2), (orc.PEELING, 3, 2), (orc.PEELING, 5, 1),
+                                         (orc.GREEDY, 0, 1)])
 @pytest.mark.parametrize("seeded_init", [False, True])
 def test_c_oracle_equals_python_restatement(ci, variant, p, q, seeded_init):
     name, g = _cases()[ci]
