@@ -47,6 +47,33 @@ def test_equals_exact_pruning(variant, p, q, c):
         _same(ax, orc.run_pruned(g, variant, 8, p, q))
 
 
+def test_equals_exact_pruning_on_random_graphs():
+    """The same equality on 150 seeded random graphs (G(n, p) of 5..90
+    vertices, half of them beside a clique of 3..11), T of 1..7, each
+    variant and each c in turn; and each run's best set has the reported
+    density, at most rho* by exact max-flow."""
+    rng = np.random.default_rng(7)
+    for i in range(150):
+        n = int(rng.integers(5, 90))
+        pr = float(rng.choice([0.05, 0.1, 0.3]))
+        keep = rng.random((n, n)) < pr
+        g = gg.from_edges(n, [(u, w) for u in range(n) for w in range(u + 1, n) if keep[u, w]])
+        if rng.random() < 0.5:
+            g = gg.disjoint_union(g, gg.complete(int(rng.integers(3, 12))))
+        if g.m == 0:
+            continue
+        variant, p, q = [(orc.SORTING, 0, 1), (orc.PEELING, 1, 10), (orc.PEELING, 0, 1)][i % 3]
+        T = int(rng.integers(1, 8))
+        ex = orc.run_pruned(g, variant, T, p, q)
+        ax, _, _, _ = orc.run_pruned_apx_exact(g, variant, T, p, q, [(3, 2), (2, 1), (5, 4)][i % 3])
+        _same(ax, ex)
+        s = set(ex.best_set.tolist())
+        e_in = sum(1 for u in s for j in range(g.off[u], g.off[u + 1]) if int(g.adj[j]) in s) // 2
+        assert (e_in, len(s)) == (ex.best_edges, ex.best_vertices)
+        (re, rv), _ = orc.maxflow_densest(g)
+        assert ex.best_edges * rv <= re * ex.best_vertices
+
+
 @pytest.mark.parametrize("c", [(3, 2), (2, 1), (5, 4)])
 def test_approximate_stage_bounds(c):
     for g in _graphs():
