@@ -123,3 +123,24 @@ def test_c_oracle_equals_python_restatement(ci, variant, p, q, seeded_init):
     assert o.trace.tolist() == [list(x) for x in trace], name
     # each iteration charges every edge to exactly one endpoint
     assert sum(loads) == sum(int(x) for x in init) + T * g.m
+
+
+def test_c_oracle_equals_python_restatement_on_random_cases():
+    """300 seeded random cases: G(n, p) of 2..69 vertices, T of 1..8, every
+    ordering (ParallelGreedy++ rounds at eps = 0, 1/10, 3/2 and 5), zero or
+    seeded initial loads."""
+    rng = np.random.default_rng(123)
+    orders = [(orc.SORTING, 0, 1), (orc.PEELING, 0, 1), (orc.PEELING, 1, 10), (orc.PEELING, 3, 2),
+              (orc.PEELING, 5, 1), (orc.GREEDY, 0, 1)]
+    for i in range(300):
+        n = int(rng.integers(2, 70))
+        g = _random_graph(n, float(rng.choice([0.03, 0.08, 0.2, 0.5])), 1000 + i)
+        variant, p, q = orders[i % len(orders)]
+        T = int(rng.integers(1, 9))
+        init = rng.integers(0, 6, size=g.n) if i % 2 else np.zeros(g.n, np.int64)
+        loads, (be, bv), bit, bset, trace = _py_run(g, variant, T, p, q, init)
+        o = orc.run(g, variant, T, p, q, init if i % 2 else None)
+        assert np.array_equal(o.loads, np.array(loads, np.int64)), i
+        assert (o.best_edges, o.best_vertices, o.best_iter) == (be, bv, bit), i
+        assert o.best_set.tolist() == bset, i
+        assert o.trace.tolist() == [list(x) for x in trace], i
