@@ -28,3 +28,22 @@ def test_stored_best_is_the_exact_optimum():
     (e, v), _ = orc.maxflow_densest(gg.er_planted_clique())
     assert e * s["sorting"]["best"][1] == v * s["sorting"]["best"][0]
     assert (s["graph"]["n"], s["sorting"]["best"][:2]) == (2000, [435, 30])
+
+
+def test_oracle_reproduces_the_stored_full_size_sorting_record():
+    """The GPU's full-size parity test compares against fullsize_cold_tier.json;
+    the oracle as it stands must still write the same graph and PaRSorting++
+    record (12M vertices, T = 4; about half a minute on one core).  The
+    PaRGreedy++ record and the R-MAT 27 one take minutes to tens of minutes
+    and are left to their script."""
+    import make_golden_fullsize as mg
+    with open(os.path.join(HERE, "golden", "fullsize_cold_tier.json")) as f:
+        stored = json.load(f)
+    c = mg.COLD_TIER
+    g = gg.er_m(c["n"], c["avg_degree"], c["seed"])
+    gr = mg._graph_record(g, stored["graph"]["recipe"])
+    assert gr == stored["graph"]
+    rec = mg._record(g, orc.SORTING, c["T"], 0, 1)
+    rec.pop("oracle_seconds")
+    want = {k: v for k, v in stored["sorting"].items() if k != "oracle_seconds"}
+    assert rec == want
