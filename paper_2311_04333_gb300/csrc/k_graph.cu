@@ -79,7 +79,9 @@ cudaError_t launch_validate_adjacency(const GraphDev &g, int full, int32_t *err_
     return cudaGetLastError();
 }
 
-cudaError_t launch_validate(const GraphDev &g, int full, int32_t *err_flags, cudaStream_t s)
+// clears the flags and checks the offsets; the adjacency checks (the `full`
+// ones too) run in the orientation's count pass or launch_validate_adjacency
+cudaError_t launch_validate(const GraphDev &g, int, int32_t *err_flags, cudaStream_t s)
 {
     cudaMemsetAsync(err_flags, 0, 8 * sizeof(int32_t), s);
     const int grid = (int)imin64((g.n + 255) / 256, 152 * 16);

@@ -96,7 +96,7 @@ struct dsg_server {
 
 namespace {
 
-void run_request(dsg_server *s, dsg_ctx *ctx, Request *r)
+void run_request(dsg_ctx *ctx, Request *r)
 {
     dsg_graph *g = nullptr;
     int rc = dsg_upload_csr(ctx, r->n, r->off.data(), r->adj.empty() ? nullptr : r->adj.data(), DSG_VALIDATE, &g);
@@ -213,7 +213,7 @@ void batch_loop(dsg_server *s)
                 if (r->variant == variant) grp.push_back(r);
             if (grp.empty()) continue;
             if (!run_batch_group(ctx, variant, grp))
-                for (Request *r : grp) run_request(s, ctx, r);
+                for (Request *r : grp) run_request(ctx, r);
         }
         finish_requests(s, batch);
     }
@@ -239,7 +239,7 @@ void worker_loop(dsg_server *s, int slot)
             r->t_start = clock_type::now();
             r->slot = slot;
         }
-        run_request(s, s->ctxs[slot], r);
+        run_request(s->ctxs[slot], r);
         finish_requests(s, {r});
     }
 }
