@@ -3,6 +3,7 @@ A single graph does not shard, so N GPUs run N replicas of it; the job value
 is all ranks' units over the slowest rank's time, and the reference arm runs
 on rank 0 alone.  Batched work shards by graph: contiguous, cost-balanced
 graph ranges per rank, results gathered in graph order."""
+import json
 import os
 import socket
 import subprocess
@@ -57,6 +58,28 @@ def test_reference_arm_other_ranks_exit_without_work(rank):
                         "--steps", "1", "--warmup", "0"], env=env, cwd=ROOT, capture_output=True, text=True,
                        timeout=120)
     assert r.returncode == 0 and r.stdout.strip() == ""
+
+
+def test_reference_arm_rank_zero_prints_one_contract_line():
+    """Rank 0 (or a single process) times the oracle on its bounded sample
+    and prints exactly one JSON line carrying the keys the driver reads."""
+    env = {k: v for k, v in os.environ.items() if k not in ("RANK", "WORLD_SIZE", "LOCAL_RANK")}
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                        "--warmup", "1"], env=env, cwd=ROOT, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [x for x in r.stdout.splitlines() if x.strip()]
+    assert len(lines) == 1
+    line = json.loads(lines[0])
+    for k in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+              "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert k in line, k
+    assert line["impl"] == "reference" and line["n_gpus"] == 1 and line["steps"] == 1 and line["warmup"] == 1
+    assert line["value"] > 0 and line["higher_is_better"] is True
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["value"] == line["value"] and cb["cores"] >= 1 and cb["sample"]
+    e2e = line["e2e"]
+    assert (e2e["value"], e2e["unit"]) == (line["value"], line["unit"])
+    assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
 
 
 # ---- batched work sharded by graph (contiguous, cost-balanced ranges)
